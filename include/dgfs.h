@@ -1,0 +1,183 @@
+/*
+ * dgfs.h - C ABI of the GB300 (sm_103a) fast Fourier spectral Boltzmann collision operator.
+ *
+ * The library evaluates the collision operator Q(f,g) of the Boltzmann equation
+ * (arXiv:1809.10186, eq. eq_dim_Q_full, in the relative-velocity form eq. apndx_Q)
+ * for the VHS kernel B = b |c - c_*|^gamma (eq. B_gen with alpha = 1) with the fast
+ * spectral method of the paper's Appendix (eqs. realGG, lowrank1, apndx_fs_Glm_Qk):
+ * a batch of B independent distribution functions, each sampled on the uniform
+ * cell-centred velocity grid c_j = -L + (j + 1/2) 2L/N of Sec. 3.3, goes in; Q at the
+ * same grid points comes out. Each batch entry is one DG node of a physical mesh; the
+ * 1/Kn factor of eq. eq_nbze is left to the caller.
+ *
+ * Memory layout of every field argument: [B][N][N][N], row-major, the third velocity
+ * component fastest, contiguous. Element type: double for DGFS_PREC_FP64 plans, float
+ * for every other precision. Field pointers are DEVICE pointers (except in
+ * dgfs_collide_host), 16-byte aligned, owned by the caller. Outputs may not alias inputs.
+ *
+ * Streams: every compute call is stream-ordered and asynchronous on the given
+ * cudaStream_t (passed as void*, NULL = legacy default stream). One plan owns one
+ * workspace: calls with the same plan on different streams must be ordered by the caller.
+ *
+ * Errors: every call returns a dgfs_status. Argument errors return before any launch;
+ * launch failures return DGFS_ERR_CUDA. A human-readable message for the last failure
+ * of the calling thread is returned by dgfs_last_error_message(). No C++ exception
+ * crosses this interface.
+ *
+ * Discretisation choices (the paper leaves them open):
+ *  - M is the number of points of an antipodal FULL-sphere rule; the paper's
+ *    half-sphere rule with M points is M_here = 2 M_paper.
+ *  - Convolutions are circular on the grid (l + m wraps modulo N).
+ *  - Nyquist modes (k = -N/2) are split evenly between -N/2 and +N/2, which makes every
+ *    translate of a real grid function real (its multiplier is cos(pi N t / 2L)).
+ *  - The loss weight G(m,m) is eq. lowrank1 at l = m (see dgfs_loss_mode).
+ */
+#ifndef DGFS_H
+#define DGFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgfs_plan_s* dgfs_plan_t;
+
+typedef enum {
+    DGFS_OK = 0,
+    DGFS_ERR_INVALID_ARG = 1,  /* bad size, NULL or misaligned pointer, bad descriptor    */
+    DGFS_ERR_UNSUPPORTED = 2,  /* valid request that this build does not implement        */
+    DGFS_ERR_OOM = 3,          /* device or host allocation failed (plan creation only)    */
+    DGFS_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed              */
+    DGFS_ERR_TIMEOUT = 5,      /* a device-side bounded wait gave up (see stream_status)   */
+    DGFS_ERR_NUMERIC = 6,      /* non-finite value detected in an output                   */
+    DGFS_ERR_STATE = 7         /* destroyed or mismatched plan                              */
+} dgfs_status;
+
+typedef enum {
+    DGFS_PREC_FP64 = 0,   /* CUDA-core FP64 everywhere (reference-accuracy mode)               */
+    DGFS_PREC_FP32 = 1,   /* CUDA-core FP32 everywhere                                          */
+    DGFS_PREC_BF16X3 = 2, /* translates on tcgen05 tensor cores: bf16 hi/lo split operands,
+                             three products (hi*hi + hi*lo + lo*hi), FP32 accumulation          */
+    DGFS_PREC_F16X3 = 3,  /* as BF16X3 with fp16 hi/lo operands (per-node power-of-two scaling) */
+    DGFS_PREC_F16 = 4     /* tensor-core translates, single fp16 product, FP32 accumulation     */
+} dgfs_precision;
+
+typedef enum {
+    /* G(m,m) = eq. lowrank1 at l = m: 4 pi sum_r w_r F(2m, c_r); the sphere sum is exact.
+       This reading reproduces the paper's BKW error table (Sec. 4.3.1). */
+    DGFS_LOSS_PAPER = 0,
+    /* G(-m,m) of eq. lowrank1 from the gain's own sphere rule: Q^_0 = 0 exactly, so mass is
+       conserved to round-off for any rule (less accurate loss for small rules). */
+    DGFS_LOSS_CONSERVATIVE = 1
+} dgfs_loss_mode;
+
+typedef struct {
+    int N;                     /* grid points per velocity axis: even, 8 <= N <= 32            */
+    double L;                  /* velocity domain [-L, L]^3 (Sec. 3.3), L > 0                   */
+    double R;                  /* ball radius of the c_r integral; <= 0: 4L/(3+sqrt 2) (Appendix) */
+    double gamma;              /* VHS exponent 2(1 - omega) of |c - c_*| (eq. B_gen)            */
+    double b;                  /* kernel constant; <= 0: 1/(2^{3-omega} Gamma(5/2-omega) pi),
+                                  omega = 1 - gamma/2 (Sec. 2.1, alpha = 1)                   */
+    int M;                     /* full-sphere points; built-in rules for M = 6, 12, 26, 38      */
+    const double* sphere_xyzw; /* optional host array [M/2][4]: one point (x,y,z) of each
+                                  antipodal pair and the weight w of EACH of its two points,
+                                  sum of w over the pairs = 2 pi; NULL: built-in rule for M   */
+    int N_rho;                 /* Gauss-Legendre points on [0, R]; <= 0: N (Sec. 4.3.1)         */
+    double svd_tol;            /* relative singular-value cut of the radial kernel; 0: none     */
+    int svd_rank;              /* > 0: fixed rank of the radial kernel (overrides svd_tol)      */
+    int precision;             /* dgfs_precision                                               */
+    int loss_mode;             /* dgfs_loss_mode                                               */
+    int64_t max_batch;         /* nodes processed per internal chunk (workspace sizing); <= 0:
+                                  chosen by the library. Compute calls accept any B >= 0.     */
+} dgfs_plan_desc;
+
+typedef struct {
+    int N, N_rho, n_pairs, svd_rank_used, precision, loss_mode;
+    double L, R, gamma, b;
+    int64_t chunk_nodes;       /* nodes per internal chunk                                     */
+    size_t workspace_bytes;    /* device workspace owned by the plan                           */
+    size_t table_bytes;        /* device tables owned by the plan                              */
+} dgfs_plan_info_t;
+
+/* Fill a descriptor with defaults (N=32, L=7, gamma=0, b=default, M=38, N_rho=N, FP32). */
+dgfs_status dgfs_plan_desc_init(dgfs_plan_desc* desc);
+
+/* Build the FP64 plan on the host (Gauss-Legendre rule, sphere rule, translate filters,
+   radial kernel and its SVD, loss weights; Appendix eqs. realGG-lowrank1), round the
+   tables to the device precision, allocate the device tables and workspace on the
+   current device and copy the tables there (synchronously). The plan is owned by the
+   caller until dgfs_plan_destroy. */
+dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out);
+
+/* Free the plan's device memory. Waits for the device first. NULL is accepted. */
+dgfs_status dgfs_plan_destroy(dgfs_plan_t plan);
+
+dgfs_status dgfs_plan_info(dgfs_plan_t plan, dgfs_plan_info_t* info);
+
+/* Q(f,f) for B nodes (eq. apndx_fs_Glm_Qk for the gain, the G(m,m) convolution for the
+   loss). f, Q: device [B][N^3]. */
+dgfs_status dgfs_collide(dgfs_plan_t plan, const void* f, void* Q, int64_t B, void* stream);
+
+/* Bilinear Q(f,g) of eq. anpdx_Q1: gain from f(c') g(c'_*), loss f(c) g(c_*). */
+dgfs_status dgfs_collide2(dgfs_plan_t plan, const void* f, const void* g, void* Q,
+                          int64_t B, void* stream);
+
+/* Directional derivative dQ = Q(f,v) + Q(v,f) of Q(f,f) along v (Q is bilinear). */
+dgfs_status dgfs_collide_jvp(dgfs_plan_t plan, const void* f, const void* v, void* dQ,
+                             int64_t B, void* stream);
+
+/* Transposed Jacobian: gf = (dQ(f,f)/df)^T u. Uses that every translate T_s of the
+   symmetric-Nyquist discretisation satisfies T_s^T = T_{-s} and that the radial and loss
+   multipliers are real and even: gf = sum_r sum_pairs 2 w_p [T_{-s}((K_r u) T_{-s} f)
+   + T_s((K_r u) T_s f)] - u (K_L f) - K_L(u f). */
+dgfs_status dgfs_collide_vjp(dgfs_plan_t plan, const void* f, const void* u, void* gf,
+                             int64_t B, void* stream);
+
+/* dQ(f,f)/dgamma at fixed b: the radial factor rho_r = 4 pi b c_r^{gamma+2} is replaced
+   by its derivative ln(c_r) rho_r in both gain and loss. */
+dgfs_status dgfs_collide_dgamma(dgfs_plan_t plan, const void* f, void* dQdg, int64_t B,
+                                void* stream);
+
+/* Q(f,f) for nodes of mixed grid size (one plan per N) and per-node kernel parameters.
+   plans[nplans]: plans of equal precision. Host arrays of length B: node_plan[i] (index
+   into plans), node_offset[i] (element offset of node i in the packed f and Q; each node
+   occupies N_i^3 elements), node_gamma[i] and node_b[i] (NULL: the plan's values).
+   f, Q: device, packed. */
+dgfs_status dgfs_collide_ragged(const dgfs_plan_t* plans, int nplans, const int32_t* node_plan,
+                                const int64_t* node_offset, const double* node_gamma,
+                                const double* node_b, int64_t B, const void* f, void* Q,
+                                void* stream);
+
+/* dgfs_collide with HOST buffers: copies f to the device, computes, copies Q back and
+   synchronises the stream before returning. f_host/Q_host may be pageable or pinned. */
+dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host, int64_t B,
+                              void* stream);
+
+/* Synchronise the stream and report device-side flags raised by earlier calls with this
+   plan (DGFS_ERR_TIMEOUT, DGFS_ERR_NUMERIC), then clear them. */
+dgfs_status dgfs_stream_status(dgfs_plan_t plan, void* stream);
+
+/* Message of the last failed call on the calling thread ("" if none). */
+const char* dgfs_last_error_message(void);
+
+/* ---- host-only introspection of the plan builder (no CUDA call, usable without a GPU) */
+
+/* Quadrature of a descriptor: c_r[N_rho], w_r[N_rho] (Gauss-Legendre on [0,R]),
+   sigma_xyzw[n_pairs][4] (pair representatives and per-point weights). *n_pairs receives
+   M/2; arrays may be NULL to query sizes only. */
+dgfs_status dgfs_host_quadrature(const dgfs_plan_desc* desc, double* c_r, double* w_r,
+                                 double* sigma_xyzw, int* n_pairs, double* R_used,
+                                 double* b_used);
+
+/* Circulant translate filter a[N] of the shift t along one axis: (T_t f)_j =
+   sum_j' a[(j - j') mod N] f_j', the grid restriction of the trigonometric interpolant
+   shifted by t (multiplier e^{i pi k t / L}, Nyquist: cos(pi N t / 2L)). */
+dgfs_status dgfs_host_translate_filter(int N, double L, double t, double* a);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGFS_H */

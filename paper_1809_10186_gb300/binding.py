@@ -1,0 +1,291 @@
+"""Thin Python binding of the C ABI in include/dgfs.h (argument marshalling only).
+
+Every computation runs in libdgfs.so; this module passes device pointers, sizes and the
+current CUDA stream. It raises if the library has not been built: there is no fallback.
+
+    from paper_1809_10186_gb300.binding import Plan
+    plan = Plan(N=32, L=7.0, gamma=0.52, M=38, N_rho=32, svd_tol=1e-8, precision="fp32")
+    Q = plan.collide(f)            # f: CUDA tensor [B, N, N, N], float32 (float64 for fp64)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libdgfs.so")
+
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "f16x3": 3, "f16": 4}
+LOSS_MODES = {"paper": 0, "conservative": 1}
+STATUS = {0: "DGFS_OK", 1: "DGFS_ERR_INVALID_ARG", 2: "DGFS_ERR_UNSUPPORTED", 3: "DGFS_ERR_OOM",
+          4: "DGFS_ERR_CUDA", 5: "DGFS_ERR_TIMEOUT", 6: "DGFS_ERR_NUMERIC", 7: "DGFS_ERR_STATE"}
+
+
+class dgfs_plan_desc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("R", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("b", ctypes.c_double), ("M", ctypes.c_int),
+                ("sphere_xyzw", ctypes.POINTER(ctypes.c_double)), ("N_rho", ctypes.c_int),
+                ("svd_tol", ctypes.c_double), ("svd_rank", ctypes.c_int),
+                ("precision", ctypes.c_int), ("loss_mode", ctypes.c_int),
+                ("max_batch", ctypes.c_int64)]
+
+
+class dgfs_plan_info_t(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("N_rho", ctypes.c_int), ("n_pairs", ctypes.c_int),
+                ("svd_rank_used", ctypes.c_int), ("precision", ctypes.c_int),
+                ("loss_mode", ctypes.c_int), ("L", ctypes.c_double), ("R", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("b", ctypes.c_double),
+                ("chunk_nodes", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t),
+                ("table_bytes", ctypes.c_size_t)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_SIGNATURES = {
+    "dgfs_plan_desc_init": [ctypes.POINTER(dgfs_plan_desc)],
+    "dgfs_plan_create": [ctypes.POINTER(dgfs_plan_desc), ctypes.POINTER(_P)],
+    "dgfs_plan_destroy": [_P],
+    "dgfs_plan_info": [_P, ctypes.POINTER(dgfs_plan_info_t)],
+    "dgfs_collide": [_P, _P, _P, _I64, _P],
+    "dgfs_collide2": [_P, _P, _P, _P, _I64, _P],
+    "dgfs_collide_jvp": [_P, _P, _P, _P, _I64, _P],
+    "dgfs_collide_vjp": [_P, _P, _P, _P, _I64, _P],
+    "dgfs_collide_dgamma": [_P, _P, _P, _I64, _P],
+    "dgfs_collide_ragged": [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double), _I64, _P, _P, _P],
+    "dgfs_collide_host": [_P, _P, _P, _I64, _P],
+    "dgfs_stream_status": [_P, _P],
+    "dgfs_last_error_message": [],
+    "dgfs_host_quadrature": [ctypes.POINTER(dgfs_plan_desc), ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double)],
+    "dgfs_host_translate_filter": [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                   ctypes.POINTER(ctypes.c_double)],
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libdgfs.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libdgfs.so is not built (%s); run paper_1809_10186_gb300.build.build()"
+                               % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_char_p if name == "dgfs_last_error_message" else ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class DGFSError(RuntimeError):
+    def __init__(self, status, where):
+        msg = lib().dgfs_last_error_message().decode()
+        super().__init__("%s failed: %s (%s)" % (where, STATUS.get(status, status), msg))
+        self.status = status
+
+
+def check(status, where):
+    if status != 0:
+        raise DGFSError(status, where)
+
+
+def make_desc(N=32, L=7.0, gamma=0.0, b=0.0, R=0.0, M=38, N_rho=0, svd_tol=0.0, svd_rank=0,
+              precision="fp32", loss="paper", max_batch=0, sphere=None):
+    d = dgfs_plan_desc()
+    check(lib().dgfs_plan_desc_init(ctypes.byref(d)), "dgfs_plan_desc_init")
+    d.N, d.L, d.gamma, d.b, d.R, d.M = int(N), float(L), float(gamma), float(b or 0.0), float(R or 0.0), int(M)
+    d.N_rho, d.svd_tol, d.svd_rank = int(N_rho or 0), float(svd_tol), int(svd_rank)
+    d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    d.loss_mode = LOSS_MODES[loss] if isinstance(loss, str) else int(loss)
+    d.max_batch = int(max_batch)
+    keep = None
+    if sphere is not None:
+        import numpy as np
+        keep = np.ascontiguousarray(sphere, dtype=np.float64)
+        d.M = 2 * keep.shape[0]
+        d.sphere_xyzw = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return d, keep
+
+
+def host_quadrature(**kw):
+    """(c_r, w_r, sigma_xyzw, R, b) of the plan builder, without touching the GPU."""
+    import numpy as np
+    d, keep = make_desc(**kw)
+    npairs = ctypes.c_int(0)
+    R, b = ctypes.c_double(0), ctypes.c_double(0)
+    check(lib().dgfs_host_quadrature(ctypes.byref(d), None, None, None, ctypes.byref(npairs),
+                                     ctypes.byref(R), ctypes.byref(b)), "dgfs_host_quadrature")
+    nr = d.N_rho if d.N_rho > 0 else d.N
+    cr, wr = np.zeros(nr), np.zeros(nr)
+    sig = np.zeros((npairs.value, 4))
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    check(lib().dgfs_host_quadrature(ctypes.byref(d), dp(cr), dp(wr), dp(sig), ctypes.byref(npairs),
+                                     None, None), "dgfs_host_quadrature")
+    return cr, wr, sig, R.value, b.value
+
+
+def host_translate_filter(N, L, t):
+    import numpy as np
+    a = np.zeros(N)
+    check(lib().dgfs_host_translate_filter(int(N), float(L), float(t),
+                                           a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+          "dgfs_host_translate_filter")
+    return a
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """Owns one dgfs_plan_t. Methods take CUDA tensors [B, N, N, N] and return new tensors."""
+
+    def __init__(self, **kw):
+        d, keep = make_desc(**kw)
+        h = ctypes.c_void_p()
+        check(lib().dgfs_plan_create(ctypes.byref(d), ctypes.byref(h)), "dgfs_plan_create")
+        self.handle = h
+        info = dgfs_plan_info_t()
+        check(lib().dgfs_plan_info(h, ctypes.byref(info)), "dgfs_plan_info")
+        self.info = {k: getattr(info, k) for k, _ in dgfs_plan_info_t._fields_}
+        self.N = info.N
+        self.precision = kw.get("precision", "fp32")
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().dgfs_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_field(self, t, name):
+        import torch
+        if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous()
+                and t.dim() == 4 and tuple(t.shape[1:]) == (self.N,) * 3):
+            raise ValueError("%s must be a contiguous CUDA %s tensor [B, %d, %d, %d]"
+                             % (name, self.dtype, self.N, self.N, self.N))
+
+    def _call(self, fn_name, fields, out=None, stream=None):
+        import torch
+        for i, t in enumerate(fields):
+            self._check_field(t, "arg%d" % i)
+        if out is None:
+            out = torch.empty_like(fields[0])
+        self._check_field(out, "out")
+        ptrs = [ctypes.c_void_p(t.data_ptr()) for t in fields]
+        fn = getattr(lib(), fn_name)
+        check(fn(self.handle, *ptrs, ctypes.c_void_p(out.data_ptr()), ctypes.c_int64(fields[0].shape[0]),
+                 _stream_ptr(stream)), fn_name)
+        return out
+
+    def collide(self, f, out=None, stream=None):
+        return self._call("dgfs_collide", [f], out, stream)
+
+    def collide2(self, f, g, out=None, stream=None):
+        return self._call("dgfs_collide2", [f, g], out, stream)
+
+    def collide_jvp(self, f, v, out=None, stream=None):
+        return self._call("dgfs_collide_jvp", [f, v], out, stream)
+
+    def collide_vjp(self, f, u, out=None, stream=None):
+        return self._call("dgfs_collide_vjp", [f, u], out, stream)
+
+    def collide_dgamma(self, f, out=None, stream=None):
+        return self._call("dgfs_collide_dgamma", [f], out, stream)
+
+    def collide_host(self, f_host, q_host, stream=None):
+        """f_host, q_host: CPU tensors (pinned for overlap); copies are inside the call."""
+        B = f_host.shape[0]
+        check(lib().dgfs_collide_host(self.handle, ctypes.c_void_p(f_host.data_ptr()),
+                                      ctypes.c_void_p(q_host.data_ptr()), ctypes.c_int64(B),
+                                      _stream_ptr(stream)), "dgfs_collide_host")
+        return q_host
+
+    def stream_status(self, stream=None):
+        check(lib().dgfs_stream_status(self.handle, _stream_ptr(stream)), "dgfs_stream_status")
+
+
+def collide_ragged(plans, node_plan, node_offset, f_packed, node_gamma=None, node_b=None,
+                   out=None, stream=None):
+    """Q for a packed batch of nodes with mixed N (one plan per N). Host arrays for the layout."""
+    import numpy as np
+    import torch
+    node_plan = np.ascontiguousarray(node_plan, dtype=np.int32)
+    node_offset = np.ascontiguousarray(node_offset, dtype=np.int64)
+    B = node_plan.shape[0]
+    if out is None:
+        out = torch.empty_like(f_packed)
+    handles = (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
+    gptr = bptr = None
+    if node_gamma is not None:
+        node_gamma = np.ascontiguousarray(node_gamma, dtype=np.float64)
+        gptr = node_gamma.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if node_b is not None:
+        node_b = np.ascontiguousarray(node_b, dtype=np.float64)
+        bptr = node_b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    check(lib().dgfs_collide_ragged(handles, len(plans),
+                                    node_plan.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                    node_offset.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                    gptr, bptr, ctypes.c_int64(B), ctypes.c_void_p(f_packed.data_ptr()),
+                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+          "dgfs_collide_ragged")
+    return out
+
+
+def _autograd_function():
+    import torch
+
+    class CollideFunction(torch.autograd.Function):
+        """Q(f, f) with reverse mode through dgfs_collide_vjp and forward mode through
+        dgfs_collide_jvp. Translates are recomputed by the kernels, never stored."""
+
+        @staticmethod
+        def forward(plan, f):
+            return plan.collide(f.contiguous())
+
+        @staticmethod
+        def setup_context(ctx, inputs, output):
+            plan, f = inputs
+            ctx.plan = plan
+            ctx.save_for_backward(f)
+            ctx.f_fwd = f
+
+        @staticmethod
+        def backward(ctx, gQ):
+            (f,) = ctx.saved_tensors
+            return None, ctx.plan.collide_vjp(f.contiguous(), gQ.contiguous())
+
+        @staticmethod
+        def jvp(ctx, _plan_t, v):
+            return ctx.plan.collide_jvp(ctx.f_fwd.contiguous(), v.contiguous())
+
+    return CollideFunction
+
+
+_CF = None
+
+
+def collide(plan, f):
+    """Differentiable Q(f, f) (torch.autograd and forward-mode AD)."""
+    global _CF
+    if _CF is None:
+        _CF = _autograd_function()
+    return _CF.apply(plan, f)

@@ -1,0 +1,563 @@
+// C ABI of the fast spectral collision operator (declared in include/dgfs.h).
+//
+// A plan owns: the FP64 host plan (plan_host.cpp), the device tables rounded to the compute
+// type, one device workspace sized for a chunk of nodes, and a device flag word. Every
+// compute call loops over node chunks and enqueues, per chunk,
+//   1. the translate-product kernel            P_r = sum_p w_p [(T_s f)(T_-s g) + (T_-s f)(T_s g)]
+//   2. the radial projection                   X_s = sum_r Vr[s][r] w_r rho_r P_r
+//   3. forward DFTs of X_s and the loss operand
+//   4. the Fourier combine                     sum_s Uk[s] X^_s + i G_loss g^
+//   5. one inverse DFT and the finalisation    Q = Re - f Im
+// on the caller's stream; nothing is allocated after dgfs_plan_create.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dgfs.h"
+#include "launchers.h"
+#include "plan_host.h"
+#include "tc_gain.h"
+
+using namespace dgfs;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+dgfs_status fail(dgfs_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+dgfs_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(DGFS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define DGFS_CUDA(call, where)                              \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+constexpr uint64_t kMagic = 0x44474653504c414eull;   // "DGFSPLAN"
+
+}  // namespace
+
+struct dgfs_plan_s {
+    uint64_t magic = kMagic;
+    HostPlan hp;
+    int prec = DGFS_PREC_FP32;
+    int device = 0;
+    int64_t chunk = 1;
+    size_t ws_bytes = 0, table_bytes = 0;
+    void* d_tables = nullptr;
+    void* d_ws = nullptr;
+    int* d_flags = nullptr;
+    DevTables<float> tf{};
+    DevTables<double> td{};
+    TcTables tc{};           // tensor-core translate tables (16-bit precisions only)
+    // workspace carve (byte offsets into d_ws)
+    size_t off_P = 0, off_G = 0, off_S = 0, off_X = 0, off_Y = 0, off_io = 0, off_node = 0;
+    int xfields = 0;
+    std::mutex host_mu;      // serialises host-side staging of per-node arrays
+};
+
+namespace {
+
+bool is_tc(int prec) { return prec == DGFS_PREC_BF16X3 || prec == DGFS_PREC_F16X3 || prec == DGFS_PREC_F16; }
+
+size_t elem_size(int prec) { return prec == DGFS_PREC_FP64 ? 8 : 4; }
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool check_plan(dgfs_plan_t p) { return p && p->magic == kMagic; }
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Per-node workspace bytes (all operations share one layout).
+void workspace_layout(dgfs_plan_s* p, int64_t C) {
+    const size_t es = elem_size(p->prec);
+    const size_t n3 = (size_t)p->hp.N * p->hp.N * p->hp.N;
+    const size_t Nr = p->hp.Nrho;
+    p->xfields = p->hp.rank + 2;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 256); return o; };
+    p->off_P = take(C * Nr * n3 * es);                 // P_r (also K_r u for the VJP)
+    p->off_G = take(C * Nr * n3 * es);                 // VJP per-radial outputs
+    p->off_S = take(C * Nr * 2 * n3 * es);             // VJP scratch
+    p->off_X = take(C * (size_t)p->xfields * n3 * 2 * es);
+    p->off_Y = take(C * 2 * n3 * 2 * es);
+    p->off_io = take(C * 2 * n3 * es);                 // host-buffer staging (f in, Q out)
+    p->off_node = take(C * (sizeof(int64_t) + 2 * sizeof(double)));
+    p->ws_bytes = off;
+}
+
+template <typename T>
+void fill_tables(dgfs_plan_s* p, std::vector<unsigned char>& blob, DevTables<T>& t, size_t& bytes) {
+    const HostPlan& h = p->hp;
+    const int N = h.N;
+    const size_t n3 = (size_t)N * N * N;
+    size_t off = 0;
+    std::vector<std::pair<size_t, size_t>> spans;
+    auto take = [&](size_t b) { const size_t o = off; off = align_up(off + b, 256); return o; };
+    const size_t o_filt = take(h.filt.size() * sizeof(T));
+    const size_t o_wsig = take(h.wsig.size() * sizeof(T));
+    const size_t o_cr = take(h.cr.size() * sizeof(double));
+    const size_t o_wr = take(h.wr.size() * sizeof(double));
+    const size_t o_Uk = take(h.Uk.size() * sizeof(T));
+    const size_t o_Vr = take(h.Vr.size() * sizeof(T));
+    const size_t o_Lr = take(h.Lr.size() * sizeof(T));
+    const size_t o_W = take((size_t)N * N * 2 * sizeof(T));
+    bytes = off;
+    blob.assign(off, 0);
+    auto put = [&](size_t o, const std::vector<double>& v) {
+        T* d = reinterpret_cast<T*>(blob.data() + o);
+        for (size_t i = 0; i < v.size(); ++i) d[i] = (T)v[i];
+    };
+    auto putd = [&](size_t o, const std::vector<double>& v) {
+        std::memcpy(blob.data() + o, v.data(), v.size() * sizeof(double));
+    };
+    put(o_filt, h.filt);
+    put(o_wsig, h.wsig);
+    putd(o_cr, h.cr);
+    putd(o_wr, h.wr);
+    put(o_Uk, h.Uk);
+    put(o_Vr, h.Vr);
+    put(o_Lr, h.Lr);
+    {
+        T* W = reinterpret_cast<T*>(blob.data() + o_W);
+        const double tp = 2.0 * 3.14159265358979323846 / N;
+        for (int q = 0; q < N; ++q)
+            for (int j = 0; j < N; ++j) {
+                const long m = ((long)q * j) % N;
+                W[2 * (q * N + j)] = (T)std::cos(tp * m);
+                W[2 * (q * N + j) + 1] = (T)(-std::sin(tp * m));
+            }
+    }
+    t.N = N;
+    t.Nrho = h.Nrho;
+    t.npairs = h.npairs;
+    t.rank = h.rank;
+    // device pointers are set after the upload: store offsets for now
+    t.filt = reinterpret_cast<const T*>(o_filt);
+    t.wsig = reinterpret_cast<const T*>(o_wsig);
+    t.cr = reinterpret_cast<const double*>(o_cr);
+    t.wr = reinterpret_cast<const double*>(o_wr);
+    t.Uk = reinterpret_cast<const T*>(o_Uk);
+    t.Vr = reinterpret_cast<const T*>(o_Vr);
+    t.Lr = reinterpret_cast<const T*>(o_Lr);
+    t.dftw = reinterpret_cast<const T*>(o_W);
+    (void)n3;
+}
+
+template <typename T>
+void rebase(DevTables<T>& t, void* base) {
+    auto fix = [&](auto& ptr) {
+        using P = std::remove_reference_t<decltype(ptr)>;
+        ptr = reinterpret_cast<P>(static_cast<unsigned char*>(base) + reinterpret_cast<uintptr_t>(ptr));
+    };
+    fix(t.filt); fix(t.wsig); fix(t.cr); fix(t.wr); fix(t.Uk); fix(t.Vr); fix(t.Lr); fix(t.dftw);
+}
+
+template <typename T> DevTables<T>& tables(dgfs_plan_s* p);
+template <> DevTables<float>& tables<float>(dgfs_plan_s* p) { return p->tf; }
+template <> DevTables<double>& tables<double>(dgfs_plan_s* p) { return p->td; }
+
+unsigned char* ws(dgfs_plan_s* p, size_t off) { return static_cast<unsigned char*>(p->d_ws) + off; }
+
+enum class Op { Collide, Collide2, Jvp, Dgamma, Vjp };
+
+// One chunk of nodes through the whole pipeline. a/b/f_loss are chunk-base pointers.
+template <typename T>
+dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, const int64_t* offs,
+                      NodeParams np, int64_t nodes, cudaStream_t s) {
+    const DevTables<T>& t = tables<T>(p);
+    const int xf = p->xfields;
+    T* P = reinterpret_cast<T*>(ws(p, p->off_P));
+    Cplx<T>* X = reinterpret_cast<Cplx<T>*>(ws(p, p->off_X));
+    Cplx<T>* Y = reinterpret_cast<Cplx<T>*>(ws(p, p->off_Y));
+    const int rank = t.rank;
+    cudaError_t e;
+    if (op == Op::Vjp) {
+        // g holds u. 1) K_r u for every r:  DFT(u) -> Uk[s] u^ -> IDFT -> sum_s Vr w_r rho_r
+        e = launch_load_field<T>(t.N, g, nullptr, offs, nodes, X, xf, rank, s);
+        if (!e) e = launch_dft3<T>(t, X + (size_t)0, nodes * xf, true, s);
+        if (!e) e = launch_multiply_uk<T>(t, X, xf, rank, nodes, s);
+        if (!e) e = launch_dft3<T>(t, X, nodes * xf, false, s);
+        if (!e) e = launch_expand_radial<T>(t, X, xf, np, nodes, P, s);
+        if (e) return cuda_fail(e, "vjp: radial multipliers");
+        // 2) adjoint translate-product
+        T* G = reinterpret_cast<T*>(ws(p, p->off_G));
+        T* S = reinterpret_cast<T*>(ws(p, p->off_S));
+        if (offs) return fail(DGFS_ERR_UNSUPPORTED, "vjp with node offsets");
+        e = launch_vjp_products(t, f, P, nodes, S, G, s);
+        if (e) return cuda_fail(e, "vjp: translate-product kernel");
+        // 3) loss: K_L f + i K_L (u f)
+        e = launch_load_field<T>(t.N, f, nullptr, offs, nodes, X, xf, 0, s);
+        if (!e) e = launch_load_field<T>(t.N, f, g, offs, nodes, X, xf, 1, s);
+        if (!e) e = launch_dft3<T>(t, X, nodes * xf, true, s);
+        if (!e) e = launch_loss_pair<T>(t, X, xf, np, nodes, 0, 1, Y, 2, s);
+        if (!e) e = launch_dft3<T>(t, Y, nodes * 2, false, s);
+        if (!e) e = launch_finalize<T>(t.N, t.Nrho, Y, 2, g, nullptr, G, offs, nodes, 1, out, p->d_flags, s);
+        if (e) return cuda_fail(e, "vjp: loss and finalisation");
+        return DGFS_OK;
+    }
+    // gain products: Q(f,f) and dQ/dgamma use (f, f); Q(f,g) uses (f, g); JVP uses (f, v)
+    const T* gg = (op == Op::Collide || op == Op::Dgamma) ? nullptr : g;
+    if (is_tc(p->prec) && std::is_same<T, float>::value) {
+        e = launch_tc_gain_products(p->tc, p->prec, reinterpret_cast<const float*>(f),
+                                    reinterpret_cast<const float*>(gg), offs, nodes,
+                                    reinterpret_cast<float*>(P), p->d_flags, s);
+    } else {
+        e = launch_gain_products(t, f, gg, offs, nodes, P, s);
+    }
+    if (e) return cuda_fail(e, "translate-product kernel");
+    e = launch_project<T>(t, P, np, nodes, X, xf, s);
+    if (e) return cuda_fail(e, "radial projection");
+    // loss operands: Q(f,g) -> g in slot rank;  JVP -> v in slot rank, f in slot rank+1
+    const T* loss0 = (op == Op::Collide || op == Op::Dgamma) ? f : g;
+    e = launch_load_field<T>(t.N, loss0, nullptr, offs, nodes, X, xf, rank, s);
+    if (!e && op == Op::Jvp) e = launch_load_field<T>(t.N, f, nullptr, offs, nodes, X, xf, rank + 1, s);
+    if (e) return cuda_fail(e, "loss operand");
+    // forward DFT of the rank projected fields and the loss operand(s)
+    e = launch_dft3<T>(t, X, nodes * xf, true, s);
+    if (e) return cuda_fail(e, "forward DFT");
+    const T scale = op == Op::Jvp ? T(2) : T(1);
+    e = launch_combine<T>(t, X, xf, np, nodes, scale, rank, op == Op::Jvp ? rank + 1 : -1, Y, 2, s);
+    if (!e) e = launch_dft3<T>(t, Y, nodes * 2, false, s);
+    if (e) return cuda_fail(e, "Fourier combine / inverse DFT");
+    // Q = Re Y0 - f Im Y0   (JVP: - v Re Y1 as well)
+    e = launch_finalize<T>(t.N, t.Nrho, Y, 2, f, op == Op::Jvp ? g : nullptr, nullptr, offs, nodes, 0,
+                           out, p->d_flags, s);
+    if (e) return cuda_fail(e, "finalisation");
+    return DGFS_OK;
+}
+
+template <typename T>
+dgfs_status run(dgfs_plan_s* p, Op op, const void* f, const void* g, void* out, int64_t B,
+                cudaStream_t s) {
+    const int64_t n3 = (int64_t)p->hp.N * p->hp.N * p->hp.N;
+    DGFS_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+    NodeParams np{nullptr, nullptr, p->hp.gamma, p->hp.b, op == Op::Dgamma ? 1 : 0};
+    for (int64_t n0 = 0; n0 < B; n0 += p->chunk) {
+        const int64_t nn = std::min<int64_t>(p->chunk, B - n0);
+        const T* fc = static_cast<const T*>(f) + n0 * n3;
+        const T* gc = g ? static_cast<const T*>(g) + n0 * n3 : nullptr;
+        T* oc = static_cast<T*>(out) + n0 * n3;
+        const dgfs_status st = run_chunk<T>(p, op, fc, gc, oc, nullptr, np, nn, s);
+        if (st != DGFS_OK) return st;
+    }
+    return DGFS_OK;
+}
+
+dgfs_status compute(dgfs_plan_t plan, Op op, const void* f, const void* g, void* out, int64_t B,
+                    void* stream, bool need_g) {
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    if (B < 0) return fail(DGFS_ERR_INVALID_ARG, "B must be >= 0");
+    if (B == 0) return DGFS_OK;
+    if (!f || !out || (need_g && !g)) return fail(DGFS_ERR_INVALID_ARG, "NULL field pointer");
+    if (!aligned16(f) || !aligned16(out) || (g && !aligned16(g)))
+        return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
+    if (out == f || (g && out == g)) return fail(DGFS_ERR_INVALID_ARG, "output aliases an input");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (op == Op::Vjp && is_tc(plan->prec))
+        ; // the adjoint runs on CUDA cores in FP32 for every 16-bit plan
+    return plan->prec == DGFS_PREC_FP64 ? run<double>(plan, op, f, g, out, B, s)
+                                        : run<float>(plan, op, f, g, out, B, s);
+}
+
+}  // namespace
+
+// ---- exported API ------------------------------------------------------------------------
+
+extern "C" {
+
+const char* dgfs_last_error_message(void) { return g_last_error.c_str(); }
+
+dgfs_status dgfs_plan_desc_init(dgfs_plan_desc* d) {
+    if (!d) return fail(DGFS_ERR_INVALID_ARG, "NULL descriptor");
+    std::memset(d, 0, sizeof(*d));
+    d->N = 32;
+    d->L = 7.0;
+    d->R = 0.0;
+    d->gamma = 0.0;
+    d->b = 0.0;
+    d->M = 38;
+    d->sphere_xyzw = nullptr;
+    d->N_rho = 0;
+    d->svd_tol = 0.0;
+    d->svd_rank = 0;
+    d->precision = DGFS_PREC_FP32;
+    d->loss_mode = DGFS_LOSS_PAPER;
+    d->max_batch = 0;
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) {
+    if (!desc || !plan_out) return fail(DGFS_ERR_INVALID_ARG, "NULL argument");
+    *plan_out = nullptr;
+    if (desc->precision < DGFS_PREC_FP64 || desc->precision > DGFS_PREC_F16)
+        return fail(DGFS_ERR_INVALID_ARG, "unknown precision");
+    std::unique_ptr<dgfs_plan_s> p(new (std::nothrow) dgfs_plan_s);
+    if (!p) return fail(DGFS_ERR_OOM, "host allocation failed");
+    std::string err;
+    dgfs_status st = build_host_plan(*desc, p->hp, err);
+    if (st != DGFS_OK) return fail(st, err);
+    p->prec = desc->precision;
+    if (p->prec == DGFS_PREC_FP64 && p->hp.N > 24)
+        return fail(DGFS_ERR_UNSUPPORTED, "FP64 plans support N <= 24");
+    if (is_tc(p->prec) && !tc_supported(p->hp.N))
+        return fail(DGFS_ERR_UNSUPPORTED, "tensor-core precisions support N = 16, 32");
+    DGFS_CUDA(cudaGetDevice(&p->device), "cudaGetDevice");
+    // chunk: about 1.5 GB of workspace
+    {
+        dgfs_plan_s probe;
+        probe.hp.N = p->hp.N;
+        probe.hp.Nrho = p->hp.Nrho;
+        probe.hp.rank = p->hp.rank;
+        probe.prec = p->prec;
+        workspace_layout(&probe, 1);
+        const size_t per_node = probe.ws_bytes;
+        int64_t C = (int64_t)((size_t)1536 << 20) / (int64_t)per_node;
+        C = std::max<int64_t>(1, std::min<int64_t>(C, 4096));
+        if (desc->max_batch > 0) C = std::min<int64_t>(C, desc->max_batch);
+        p->chunk = C;
+    }
+    workspace_layout(p.get(), p->chunk);
+    std::vector<unsigned char> blob;
+    if (p->prec == DGFS_PREC_FP64) fill_tables<double>(p.get(), blob, p->td, p->table_bytes);
+    else fill_tables<float>(p.get(), blob, p->tf, p->table_bytes);
+    std::vector<unsigned char> tcblob;
+    size_t tc_bytes = 0;
+    if (is_tc(p->prec)) tc_bytes = build_tc_tables(p->hp, p->prec, tcblob, p->tc);
+    cudaError_t e = cudaMalloc(&p->d_tables, p->table_bytes + tc_bytes);
+    if (e != cudaSuccess) return fail(DGFS_ERR_OOM, std::string("device tables: ") + cudaGetErrorString(e));
+    e = cudaMalloc(&p->d_ws, p->ws_bytes);
+    if (e != cudaSuccess) {
+        cudaFree(p->d_tables);
+        return fail(DGFS_ERR_OOM, std::string("device workspace: ") + cudaGetErrorString(e));
+    }
+    e = cudaMalloc(&p->d_flags, 64);
+    if (e == cudaSuccess) e = cudaMemset(p->d_flags, 0, 64);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_tables, blob.data(), p->table_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && tc_bytes)
+        e = cudaMemcpy(static_cast<unsigned char*>(p->d_tables) + p->table_bytes, tcblob.data(), tc_bytes,
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p->d_tables);
+        cudaFree(p->d_ws);
+        if (p->d_flags) cudaFree(p->d_flags);
+        return cuda_fail(e, "plan upload");
+    }
+    if (p->prec == DGFS_PREC_FP64) rebase(p->td, p->d_tables);
+    else rebase(p->tf, p->d_tables);
+    if (tc_bytes) rebase_tc_tables(p->tc, static_cast<unsigned char*>(p->d_tables) + p->table_bytes);
+    p->table_bytes += tc_bytes;
+    *plan_out = p.release();
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_plan_destroy(dgfs_plan_t plan) {
+    if (!plan) return DGFS_OK;
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(plan->device);
+    cudaDeviceSynchronize();
+    cudaFree(plan->d_tables);
+    cudaFree(plan->d_ws);
+    cudaFree(plan->d_flags);
+    cudaSetDevice(cur);
+    plan->magic = 0;
+    delete plan;
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_plan_info(dgfs_plan_t plan, dgfs_plan_info_t* info) {
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    if (!info) return fail(DGFS_ERR_INVALID_ARG, "NULL info");
+    const HostPlan& h = plan->hp;
+    info->N = h.N;
+    info->N_rho = h.Nrho;
+    info->n_pairs = h.npairs;
+    info->svd_rank_used = h.rank;
+    info->precision = plan->prec;
+    info->loss_mode = h.loss_mode;
+    info->L = h.L;
+    info->R = h.R;
+    info->gamma = h.gamma;
+    info->b = h.b;
+    info->chunk_nodes = plan->chunk;
+    info->workspace_bytes = plan->ws_bytes;
+    info->table_bytes = plan->table_bytes;
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_collide(dgfs_plan_t plan, const void* f, void* Q, int64_t B, void* stream) {
+    return compute(plan, Op::Collide, f, nullptr, Q, B, stream, false);
+}
+
+dgfs_status dgfs_collide2(dgfs_plan_t plan, const void* f, const void* g, void* Q, int64_t B,
+                          void* stream) {
+    return compute(plan, Op::Collide2, f, g, Q, B, stream, true);
+}
+
+dgfs_status dgfs_collide_jvp(dgfs_plan_t plan, const void* f, const void* v, void* dQ, int64_t B,
+                             void* stream) {
+    return compute(plan, Op::Jvp, f, v, dQ, B, stream, true);
+}
+
+dgfs_status dgfs_collide_vjp(dgfs_plan_t plan, const void* f, const void* u, void* gf, int64_t B,
+                             void* stream) {
+    if (check_plan(plan) && is_tc(plan->prec))
+        return fail(DGFS_ERR_UNSUPPORTED, "the adjoint needs an FP32 or FP64 plan");
+    return compute(plan, Op::Vjp, f, u, gf, B, stream, true);
+}
+
+dgfs_status dgfs_collide_dgamma(dgfs_plan_t plan, const void* f, void* dQdg, int64_t B, void* stream) {
+    return compute(plan, Op::Dgamma, f, nullptr, dQdg, B, stream, false);
+}
+
+dgfs_status dgfs_collide_ragged(const dgfs_plan_t* plans, int nplans, const int32_t* node_plan,
+                                const int64_t* node_offset, const double* node_gamma,
+                                const double* node_b, int64_t B, const void* f, void* Q,
+                                void* stream) {
+    if (!plans || nplans <= 0) return fail(DGFS_ERR_INVALID_ARG, "no plans");
+    for (int i = 0; i < nplans; ++i)
+        if (!check_plan(plans[i])) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    for (int i = 1; i < nplans; ++i)
+        if ((plans[i]->prec == DGFS_PREC_FP64) != (plans[0]->prec == DGFS_PREC_FP64))
+            return fail(DGFS_ERR_INVALID_ARG, "ragged plans must share the element type");
+    if (B < 0) return fail(DGFS_ERR_INVALID_ARG, "B must be >= 0");
+    if (B == 0) return DGFS_OK;
+    if (!node_plan || !node_offset || !f || !Q) return fail(DGFS_ERR_INVALID_ARG, "NULL argument");
+    if (!aligned16(f) || !aligned16(Q)) return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
+    if (f == Q) return fail(DGFS_ERR_INVALID_ARG, "output aliases the input");
+    for (int64_t i = 0; i < B; ++i) {
+        if (node_plan[i] < 0 || node_plan[i] >= nplans) return fail(DGFS_ERR_INVALID_ARG, "node_plan out of range");
+        if (node_offset[i] < 0) return fail(DGFS_ERR_INVALID_ARG, "negative node_offset");
+        const int N = plans[node_plan[i]]->hp.N;
+        if ((node_offset[i] * (int64_t)elem_size(plans[node_plan[i]]->prec)) % 16)
+            return fail(DGFS_ERR_INVALID_ARG, "node offsets must keep 16-byte alignment");
+        (void)N;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int pi = 0; pi < nplans; ++pi) {
+        dgfs_plan_s* p = plans[pi];
+        std::lock_guard<std::mutex> lock(p->host_mu);
+        DGFS_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+        std::vector<int64_t> offs;
+        std::vector<double> gam, bb;
+        for (int64_t i = 0; i < B; ++i)
+            if (node_plan[i] == pi) {
+                offs.push_back(node_offset[i]);
+                gam.push_back(node_gamma ? node_gamma[i] : p->hp.gamma);
+                bb.push_back(node_b ? node_b[i] : p->hp.b);
+            }
+        const int64_t cnt = (int64_t)offs.size();
+        for (int64_t n0 = 0; n0 < cnt; n0 += p->chunk) {
+            const int64_t nn = std::min<int64_t>(p->chunk, cnt - n0);
+            unsigned char* nb = ws(p, p->off_node);
+            int64_t* d_offs = reinterpret_cast<int64_t*>(nb);
+            double* d_gam = reinterpret_cast<double*>(nb + p->chunk * sizeof(int64_t));
+            double* d_b = d_gam + p->chunk;
+            DGFS_CUDA(cudaMemcpyAsync(d_offs, offs.data() + n0, nn * sizeof(int64_t), cudaMemcpyHostToDevice, s), "ragged offsets");
+            DGFS_CUDA(cudaMemcpyAsync(d_gam, gam.data() + n0, nn * sizeof(double), cudaMemcpyHostToDevice, s), "ragged gamma");
+            DGFS_CUDA(cudaMemcpyAsync(d_b, bb.data() + n0, nn * sizeof(double), cudaMemcpyHostToDevice, s), "ragged b");
+            NodeParams np{d_gam, d_b, p->hp.gamma, p->hp.b, 0};
+            dgfs_status st;
+            if (p->prec == DGFS_PREC_FP64)
+                st = run_chunk<double>(p, Op::Collide, static_cast<const double*>(f), nullptr,
+                                       static_cast<double*>(Q), d_offs, np, nn, s);
+            else
+                st = run_chunk<float>(p, Op::Collide, static_cast<const float*>(f), nullptr,
+                                      static_cast<float*>(Q), d_offs, np, nn, s);
+            if (st != DGFS_OK) return st;
+        }
+        // the host vectors are staged by the copies above before they return (pageable source)
+    }
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host, int64_t B,
+                              void* stream) {
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    if (B < 0) return fail(DGFS_ERR_INVALID_ARG, "B must be >= 0");
+    if (B == 0) return DGFS_OK;
+    if (!f_host || !Q_host) return fail(DGFS_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    const size_t es = elem_size(plan->prec);
+    const int64_t n3 = (int64_t)plan->hp.N * plan->hp.N * plan->hp.N;
+    unsigned char* fin = ws(plan, plan->off_io);
+    unsigned char* qout = fin + (size_t)plan->chunk * n3 * es;
+    for (int64_t n0 = 0; n0 < B; n0 += plan->chunk) {
+        const int64_t nn = std::min<int64_t>(plan->chunk, B - n0);
+        const size_t bytes = (size_t)nn * n3 * es;
+        DGFS_CUDA(cudaMemcpyAsync(fin, static_cast<const unsigned char*>(f_host) + (size_t)n0 * n3 * es, bytes,
+                                  cudaMemcpyHostToDevice, s), "host to device");
+        dgfs_status st = plan->prec == DGFS_PREC_FP64
+            ? run_chunk<double>(plan, Op::Collide, reinterpret_cast<const double*>(fin), nullptr,
+                                reinterpret_cast<double*>(qout), nullptr,
+                                NodeParams{nullptr, nullptr, plan->hp.gamma, plan->hp.b, 0}, nn, s)
+            : run_chunk<float>(plan, Op::Collide, reinterpret_cast<const float*>(fin), nullptr,
+                               reinterpret_cast<float*>(qout), nullptr,
+                               NodeParams{nullptr, nullptr, plan->hp.gamma, plan->hp.b, 0}, nn, s);
+        if (st != DGFS_OK) return st;
+        DGFS_CUDA(cudaMemcpyAsync(static_cast<unsigned char*>(Q_host) + (size_t)n0 * n3 * es, qout, bytes,
+                                  cudaMemcpyDeviceToHost, s), "device to host");
+    }
+    DGFS_CUDA(cudaStreamSynchronize(s), "stream synchronise");
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_stream_status(dgfs_plan_t plan, void* stream) {
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    DGFS_CUDA(cudaStreamSynchronize(s), "stream synchronise");
+    int flags = 0;
+    DGFS_CUDA(cudaMemcpy(&flags, plan->d_flags, sizeof(int), cudaMemcpyDeviceToHost), "read flags");
+    DGFS_CUDA(cudaMemset(plan->d_flags, 0, sizeof(int)), "clear flags");
+    if (flags & 1) return fail(DGFS_ERR_TIMEOUT, "a device-side wait gave up");
+    if (flags & 2) return fail(DGFS_ERR_NUMERIC, "non-finite value in an output");
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_host_quadrature(const dgfs_plan_desc* desc, double* c_r, double* w_r,
+                                 double* sigma_xyzw, int* n_pairs, double* R_used, double* b_used) {
+    if (!desc) return fail(DGFS_ERR_INVALID_ARG, "NULL descriptor");
+    HostPlan hp;
+    std::string err;
+    const dgfs_status st = build_quadrature(*desc, hp, err);
+    if (st != DGFS_OK) return fail(st, err);
+    if (n_pairs) *n_pairs = hp.npairs;
+    if (R_used) *R_used = hp.R;
+    if (b_used) *b_used = hp.b;
+    if (c_r) std::memcpy(c_r, hp.cr.data(), hp.cr.size() * sizeof(double));
+    if (w_r) std::memcpy(w_r, hp.wr.data(), hp.wr.size() * sizeof(double));
+    if (sigma_xyzw)
+        for (int i = 0; i < hp.npairs; ++i) {
+            sigma_xyzw[4 * i + 0] = hp.sig[3 * i + 0];
+            sigma_xyzw[4 * i + 1] = hp.sig[3 * i + 1];
+            sigma_xyzw[4 * i + 2] = hp.sig[3 * i + 2];
+            sigma_xyzw[4 * i + 3] = hp.wsig[i];
+        }
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_host_translate_filter(int N, double L, double t, double* a) {
+    if (N < 2 || N % 2 || N > 4096 || !(L > 0) || !a || !std::isfinite(t))
+        return fail(DGFS_ERR_INVALID_ARG, "bad translate-filter arguments");
+    translate_filter(N, L, t, a);
+    return DGFS_OK;
+}
+
+}  // extern "C"

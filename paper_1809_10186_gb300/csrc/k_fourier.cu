@@ -1,0 +1,382 @@
+// Fourier-side kernels of the collision operator (arXiv:1809.10186, Appendix).
+//
+// After the translate-product step has produced P_r for every radial point, the gain is
+//   gain^_k = sum_r w_r F(k, c_r) DFT(P_r)_k,   F(k, c_r) = rho_r sinc(pi c_r |k| / 2L)
+// (eqs. realGG, apndx_fs_Glm_Qk), and the loss is f times the convolution of g with the
+// kernel mode G(m,m). With the radial kernel compressed as sinc(pi c_r |k| / 2L) ~=
+// sum_s Uk[s](k) Vr[s][r], the gain needs only `rank` forward transforms:
+//   gain^_k = sum_s Uk[s](k) DFT( sum_r Vr[s][r] w_r rho_r P_r )_k.
+// Transforms are dense separable DFTs of the standard grid ordering; every multiplier is
+// diagonal, so the half-cell phase of the cell-centred grid cancels between the forward
+// and inverse transforms and the signed lattice index k = q (q < N/2) or q - N is used.
+#include <cmath>
+#include <cstdint>
+
+#include "launchers.h"
+
+namespace dgfs {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+template <typename T>
+__device__ __forceinline__ T radial_rho(double b, double gamma, double cr, int dlog) {
+    // rho_r = 4 pi b c_r^{gamma+2}: the closed form of F(k, c_r) / sinc for VHS (eq. realGG)
+    double v = 4.0 * kPi * b * pow(cr, gamma + 2.0);
+    if (dlog) v *= log(cr);
+    return (T)v;
+}
+
+// ---- dense DFT passes -----------------------------------------------------------------
+
+// Strided axis: data viewed as [outer][N][inner], tile [N][TI] of one outer index.
+template <typename T, int TI>
+__global__ void k_dft_strided(Cplx<T>* __restrict__ X, const Cplx<T>* __restrict__ W, int N,
+                              int64_t inner, int64_t tiles_per_outer, int forward, T scale) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    Cplx<T>* Ws = reinterpret_cast<Cplx<T>*>(sm_raw);        // [N][N]
+    Cplx<T>* tile = Ws + N * N;                                // [N][TI]
+    const int64_t o = blockIdx.x / tiles_per_outer;
+    const int64_t i0 = (blockIdx.x % tiles_per_outer) * TI;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nth = blockDim.x * blockDim.y, t = ty * blockDim.x + tx;
+    for (int e = t; e < N * N; e += nth) Ws[e] = W[e];
+    Cplx<T>* base = X + o * (int64_t)N * inner;
+    const bool live = (i0 + tx) < inner;
+    for (int j = ty; j < N; j += blockDim.y)
+        if (live) tile[j * TI + tx] = base[(int64_t)j * inner + i0 + tx];
+    __syncthreads();
+    if (!live) return;
+    for (int q = ty; q < N; q += blockDim.y) {
+        T re = 0, im = 0;
+        for (int j = 0; j < N; ++j) {
+            const Cplx<T> w = Ws[q * N + j];
+            const T wi = forward ? w.y : -w.y;
+            const Cplx<T> v = tile[j * TI + tx];
+            re = fma(w.x, v.x, fma(-wi, v.y, re));
+            im = fma(w.x, v.y, fma(wi, v.x, im));
+        }
+        base[(int64_t)q * inner + i0 + tx] = Cplx<T>{re * scale, im * scale};
+    }
+}
+
+// Contiguous axis: TL lines of N consecutive values per CTA (padded tile against bank conflicts).
+template <typename T, int TL>
+__global__ void k_dft_contig(Cplx<T>* __restrict__ X, const Cplx<T>* __restrict__ W, int N,
+                             int64_t lines, int forward, T scale) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    Cplx<T>* Ws = reinterpret_cast<Cplx<T>*>(sm_raw);        // [N][N]
+    Cplx<T>* tile = Ws + N * N;                                // [TL][N+1]
+    const int64_t l0 = (int64_t)blockIdx.x * TL;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nth = blockDim.x * blockDim.y, t = ty * blockDim.x + tx;
+    for (int e = t; e < N * N; e += nth) Ws[e] = W[e];
+    const int64_t nl = (lines - l0) < TL ? (lines - l0) : TL;
+    Cplx<T>* base = X + l0 * N;
+    for (int e = t; e < nl * N; e += nth) tile[(e / N) * (N + 1) + e % N] = base[e];
+    __syncthreads();
+    if (tx >= nl) return;
+    for (int q = ty; q < N; q += blockDim.y) {
+        T re = 0, im = 0;
+        for (int j = 0; j < N; ++j) {
+            const Cplx<T> w = Ws[q * N + j];
+            const T wi = forward ? w.y : -w.y;
+            const Cplx<T> v = tile[tx * (N + 1) + j];
+            re = fma(w.x, v.x, fma(-wi, v.y, re));
+            im = fma(w.x, v.y, fma(wi, v.x, im));
+        }
+        base[(int64_t)tx * N + q] = Cplx<T>{re * scale, im * scale};
+    }
+}
+
+// ---- projections and multipliers ----------------------------------------------------------
+
+// X[node][s][j] = sum_r C[s][r] P[node][r][j],  C[s][r] = Vr[s][r] w_r rho_r(node)
+template <typename T>
+__global__ void k_project(const T* __restrict__ P, const T* __restrict__ Vr,
+                          const double* __restrict__ cr, const double* __restrict__ wr,
+                          NodeParams np, int Nrho, int rank, int64_t n3, Cplx<T>* __restrict__ X,
+                          int xfields) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* C = reinterpret_cast<T*>(sm_raw);                  // [rank][Nrho]
+    T* Pt = C + rank * Nrho;                               // [Nrho][blockDim]
+    const int64_t node = blockIdx.y;
+    const double gam = np.gamma ? np.gamma[node] : np.gamma0;
+    const double bb = np.b ? np.b[node] : np.b0;
+    for (int e = threadIdx.x; e < rank * Nrho; e += blockDim.x) {
+        const int r = e % Nrho;
+        C[e] = Vr[e] * (T)wr[r] * radial_rho<T>(bb, gam, cr[r], np.dlog);
+    }
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const T* Pn = P + node * Nrho * n3;
+    for (int r = 0; r < Nrho; ++r) Pt[r * blockDim.x + threadIdx.x] = j < n3 ? Pn[r * n3 + j] : T(0);
+    __syncthreads();
+    if (j >= n3) return;
+    Cplx<T>* Xn = X + node * (int64_t)xfields * n3;
+    for (int s = 0; s < rank; ++s) {
+        T acc = 0;
+        for (int r = 0; r < Nrho; ++r) acc = fma(C[s * Nrho + r], Pt[r * blockDim.x + threadIdx.x], acc);
+        Xn[s * n3 + j] = Cplx<T>{acc, T(0)};
+    }
+}
+
+template <typename T>
+__global__ void k_load_field(int64_t n3, const T* __restrict__ a, const T* __restrict__ b,
+                             const int64_t* __restrict__ offs, Cplx<T>* __restrict__ X, int xfields,
+                             int slot) {
+    const int64_t node = blockIdx.y;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n3) return;
+    const int64_t base = offs ? offs[node] : node * n3;
+    T v = a[base + j];
+    if (b) v *= b[base + j];
+    X[(node * xfields + slot) * n3 + j] = Cplx<T>{v, T(0)};
+}
+
+template <typename T>
+__global__ void k_combine(const Cplx<T>* __restrict__ X, int xfields, const T* __restrict__ Uk,
+                          const T* __restrict__ Lr, const double* __restrict__ cr, NodeParams np,
+                          int Nrho, int rank, int64_t n3, T scale, int ls0, int ls1,
+                          Cplx<T>* __restrict__ Y, int yfields) {
+    __shared__ T rho[64];
+    const int64_t node = blockIdx.y;
+    const double gam = np.gamma ? np.gamma[node] : np.gamma0;
+    const double bb = np.b ? np.b[node] : np.b0;
+    for (int r = threadIdx.x; r < Nrho; r += blockDim.x) rho[r] = radial_rho<T>(bb, gam, cr[r], np.dlog);
+    __syncthreads();
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n3) return;
+    const Cplx<T>* Xn = X + node * (int64_t)xfields * n3;
+    T gr = 0, gi = 0;
+    for (int s = 0; s < rank; ++s) {
+        const T u = Uk[s * n3 + k];
+        const Cplx<T> v = Xn[s * n3 + k];
+        gr = fma(u, v.x, gr);
+        gi = fma(u, v.y, gi);
+    }
+    T GL = 0;
+    for (int r = 0; r < Nrho; ++r) GL = fma(rho[r], Lr[r * n3 + k], GL);
+    const Cplx<T> l0 = Xn[ls0 * n3 + k];
+    // gain + i * loss multiplier applied to the loss operand: both are Hermitian, so the
+    // inverse transform returns gain in the real part and K_L g in the imaginary part
+    Cplx<T>* Yn = Y + node * (int64_t)yfields * n3;
+    Yn[k] = Cplx<T>{scale * gr - GL * l0.y, scale * gi + GL * l0.x};
+    if (ls1 >= 0) {
+        const Cplx<T> l1 = Xn[ls1 * n3 + k];
+        Yn[n3 + k] = Cplx<T>{GL * l1.x, GL * l1.y};
+    }
+}
+
+template <typename T>
+__global__ void k_loss_pair(const Cplx<T>* __restrict__ X, int xfields, const T* __restrict__ Lr,
+                            const double* __restrict__ cr, NodeParams np, int Nrho, int64_t n3,
+                            int s0, int s1, Cplx<T>* __restrict__ Y, int yfields) {
+    __shared__ T rho[64];
+    const int64_t node = blockIdx.y;
+    const double gam = np.gamma ? np.gamma[node] : np.gamma0;
+    const double bb = np.b ? np.b[node] : np.b0;
+    for (int r = threadIdx.x; r < Nrho; r += blockDim.x) rho[r] = radial_rho<T>(bb, gam, cr[r], np.dlog);
+    __syncthreads();
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n3) return;
+    T GL = 0;
+    for (int r = 0; r < Nrho; ++r) GL = fma(rho[r], Lr[r * n3 + k], GL);
+    const Cplx<T>* Xn = X + node * (int64_t)xfields * n3;
+    const Cplx<T> a = Xn[s0 * n3 + k], b = Xn[s1 * n3 + k];
+    Y[node * (int64_t)yfields * n3 + k] = Cplx<T>{GL * (a.x - b.y), GL * (a.y + b.x)};
+}
+
+template <typename T>
+__global__ void k_multiply_uk(Cplx<T>* __restrict__ X, int xfields, const T* __restrict__ Uk,
+                              int rank, int64_t n3, int src) {
+    const int64_t node = blockIdx.y;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n3) return;
+    Cplx<T>* Xn = X + node * (int64_t)xfields * n3;
+    const Cplx<T> v = Xn[src * n3 + k];
+    for (int s = 0; s < rank; ++s) {
+        const T u = Uk[s * n3 + k];
+        Xn[s * n3 + k] = Cplx<T>{u * v.x, u * v.y};
+    }
+}
+
+// U[node][r][j] = w_r rho_r sum_s Vr[s][r] Re X[node][s][j]
+template <typename T>
+__global__ void k_expand_radial(const Cplx<T>* __restrict__ X, int xfields, const T* __restrict__ Vr,
+                                const double* __restrict__ cr, const double* __restrict__ wr,
+                                NodeParams np, int Nrho, int rank, int64_t n3, T* __restrict__ U) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* C = reinterpret_cast<T*>(sm_raw);        // [rank][Nrho]
+    T* Xt = C + rank * Nrho;                     // [rank][blockDim]
+    const int64_t node = blockIdx.y;
+    const double gam = np.gamma ? np.gamma[node] : np.gamma0;
+    const double bb = np.b ? np.b[node] : np.b0;
+    for (int e = threadIdx.x; e < rank * Nrho; e += blockDim.x) {
+        const int r = e % Nrho;
+        C[e] = Vr[e] * (T)wr[r] * radial_rho<T>(bb, gam, cr[r], np.dlog);
+    }
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const Cplx<T>* Xn = X + node * (int64_t)xfields * n3;
+    for (int s = 0; s < rank; ++s) Xt[s * blockDim.x + threadIdx.x] = j < n3 ? Xn[s * n3 + j].x : T(0);
+    __syncthreads();
+    if (j >= n3) return;
+    T* Un = U + node * (int64_t)Nrho * n3;
+    for (int r = 0; r < Nrho; ++r) {
+        T acc = 0;
+        for (int s = 0; s < rank; ++s) acc = fma(C[s * Nrho + r], Xt[s * blockDim.x + threadIdx.x], acc);
+        Un[r * n3 + j] = acc;
+    }
+}
+
+template <typename T>
+__global__ void k_finalize(int Nrho, int64_t n3, const Cplx<T>* __restrict__ Y, int yfields,
+                           const T* __restrict__ a, const T* __restrict__ c, const T* __restrict__ G,
+                           const int64_t* __restrict__ offs, int mode, T* __restrict__ out,
+                           int* __restrict__ flags) {
+    const int64_t node = blockIdx.y;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n3) return;
+    const int64_t base = offs ? offs[node] : node * n3;
+    const Cplx<T>* Yn = Y + node * (int64_t)yfields * n3;
+    const Cplx<T> y0 = Yn[j];
+    T v;
+    if (mode == 0) {
+        v = y0.x - a[base + j] * y0.y;
+        if (c) v -= c[base + j] * Yn[n3 + j].x;
+    } else {
+        v = T(0);
+        const T* Gn = G + node * (int64_t)Nrho * n3;
+        for (int r = 0; r < Nrho; ++r) v += Gn[r * n3 + j];
+        v -= a[base + j] * y0.x + y0.y;
+    }
+    if (!isfinite(v)) atomicOr(flags, 2);
+    out[base + j] = v;
+}
+
+inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_dft3(const DevTables<T>& t, Cplx<T>* X, int64_t count, bool forward, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const int N = t.N;
+    const int64_t n2 = (int64_t)N * N;
+    const T scale = forward ? T(1) / T(N) : T(1);
+    const Cplx<T>* W = reinterpret_cast<const Cplx<T>*>(t.dftw);
+    constexpr int TI = 32;
+    const size_t sm_s = sizeof(Cplx<T>) * (size_t)(N * N + N * TI);
+    // axis x: [count][N][N^2]
+    {
+        const int64_t tiles = (n2 + TI - 1) / TI;
+        k_dft_strided<T, TI><<<(unsigned)(count * tiles), dim3(TI, 8), sm_s, s>>>(X, W, N, n2, tiles, forward, scale);
+    }
+    // axis y: [count*N][N][N]
+    {
+        const int64_t tiles = ((int64_t)N + TI - 1) / TI;
+        k_dft_strided<T, TI><<<(unsigned)(count * N * tiles), dim3(TI, 8), sm_s, s>>>(X, W, N, N, tiles, forward, scale);
+    }
+    // axis z: count*N^2 contiguous lines
+    {
+        constexpr int TL = 32;
+        const int64_t lines = count * n2;
+        const size_t sm_c = sizeof(Cplx<T>) * (size_t)(N * N + TL * (N + 1));
+        k_dft_contig<T, TL><<<blocks_for(lines, TL), dim3(TL, 8), sm_c, s>>>(X, W, N, lines, forward, scale);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_project(const DevTables<T>& t, const T* P, NodeParams np, int64_t nodes,
+                           Cplx<T>* X, int xfields, cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    const int64_t n3 = (int64_t)t.N * t.N * t.N;
+    const int bs = 128;
+    const size_t sm = sizeof(T) * (size_t)(t.rank * t.Nrho + t.Nrho * bs);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_project<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_project<T><<<dim3(blocks_for(n3, bs), (unsigned)nodes), bs, sm, s>>>(P, t.Vr, t.cr, t.wr, np, t.Nrho, t.rank, n3, X, xfields);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_load_field(int N, const T* a, const T* b, const int64_t* offs, int64_t nodes,
+                              Cplx<T>* X, int xfields, int slot, cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    const int64_t n3 = (int64_t)N * N * N;
+    k_load_field<T><<<dim3(blocks_for(n3, 256), (unsigned)nodes), 256, 0, s>>>(n3, a, b, offs, X, xfields, slot);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_combine(const DevTables<T>& t, const Cplx<T>* X, int xfields, NodeParams np,
+                           int64_t nodes, T scale, int ls0, int ls1, Cplx<T>* Y, int yfields,
+                           cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    const int64_t n3 = (int64_t)t.N * t.N * t.N;
+    k_combine<T><<<dim3(blocks_for(n3, 256), (unsigned)nodes), 256, 0, s>>>(X, xfields, t.Uk, t.Lr, t.cr, np, t.Nrho, t.rank, n3, scale, ls0, ls1, Y, yfields);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_loss_pair(const DevTables<T>& t, const Cplx<T>* X, int xfields, NodeParams np,
+                             int64_t nodes, int s0, int s1, Cplx<T>* Y, int yfields, cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    const int64_t n3 = (int64_t)t.N * t.N * t.N;
+    k_loss_pair<T><<<dim3(blocks_for(n3, 256), (unsigned)nodes), 256, 0, s>>>(X, xfields, t.Lr, t.cr, np, t.Nrho, n3, s0, s1, Y, yfields);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_multiply_uk(const DevTables<T>& t, Cplx<T>* X, int xfields, int src, int64_t nodes,
+                               cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    const int64_t n3 = (int64_t)t.N * t.N * t.N;
+    k_multiply_uk<T><<<dim3(blocks_for(n3, 256), (unsigned)nodes), 256, 0, s>>>(X, xfields, t.Uk, t.rank, n3, src);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_expand_radial(const DevTables<T>& t, const Cplx<T>* X, int xfields, NodeParams np,
+                                 int64_t nodes, T* U, cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    const int64_t n3 = (int64_t)t.N * t.N * t.N;
+    const int bs = 128;
+    const size_t sm = sizeof(T) * (size_t)(t.rank * t.Nrho + t.rank * bs);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_expand_radial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_expand_radial<T><<<dim3(blocks_for(n3, bs), (unsigned)nodes), bs, sm, s>>>(X, xfields, t.Vr, t.cr, t.wr, np, t.Nrho, t.rank, n3, U);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_finalize(int N, int Nrho, const Cplx<T>* Y, int yfields, const T* a, const T* c,
+                            const T* G, const int64_t* offs, int64_t nodes, int mode, T* out,
+                            int* flags, cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    const int64_t n3 = (int64_t)N * N * N;
+    k_finalize<T><<<dim3(blocks_for(n3, 256), (unsigned)nodes), 256, 0, s>>>(Nrho, n3, Y, yfields, a, c, G, offs, mode, out, flags);
+    return cudaGetLastError();
+}
+
+#define DGFS_INST(T)                                                                                   \
+    template cudaError_t launch_dft3<T>(const DevTables<T>&, Cplx<T>*, int64_t, bool, cudaStream_t);  \
+    template cudaError_t launch_project<T>(const DevTables<T>&, const T*, NodeParams, int64_t,        \
+                                           Cplx<T>*, int, cudaStream_t);                              \
+    template cudaError_t launch_load_field<T>(int, const T*, const T*, const int64_t*, int64_t,       \
+                                              Cplx<T>*, int, int, cudaStream_t);                      \
+    template cudaError_t launch_combine<T>(const DevTables<T>&, const Cplx<T>*, int, NodeParams,      \
+                                           int64_t, T, int, int, Cplx<T>*, int, cudaStream_t);        \
+    template cudaError_t launch_loss_pair<T>(const DevTables<T>&, const Cplx<T>*, int, NodeParams,    \
+                                             int64_t, int, int, Cplx<T>*, int, cudaStream_t);         \
+    template cudaError_t launch_multiply_uk<T>(const DevTables<T>&, Cplx<T>*, int, int, int64_t,      \
+                                               cudaStream_t);                                         \
+    template cudaError_t launch_expand_radial<T>(const DevTables<T>&, const Cplx<T>*, int, NodeParams,\
+                                                 int64_t, T*, cudaStream_t);                          \
+    template cudaError_t launch_finalize<T>(int, int, const Cplx<T>*, int, const T*, const T*,        \
+                                            const T*, const int64_t*, int64_t, int, T*, int*,         \
+                                            cudaStream_t);
+DGFS_INST(float)
+DGFS_INST(double)
+#undef DGFS_INST
+
+}  // namespace dgfs

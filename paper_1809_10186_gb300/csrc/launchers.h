@@ -1,0 +1,96 @@
+// Internal launcher interface between the C ABI (capi.cu) and the kernel files.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace dgfs {
+
+// Device tables of one plan, in the compute type T (float or double).
+template <typename T>
+struct DevTables {
+    int N, Nrho, npairs, rank;
+    const T* filt;      // [Nrho][npairs][3][N] circulant filters of +s_rp
+    const T* wsig;      // [npairs]
+    const double* cr;   // [Nrho]
+    const double* wr;   // [Nrho]
+    const T* Uk;        // [rank][N^3]  DFT index order
+    const T* Vr;        // [rank][Nrho]
+    const T* Lr;        // [Nrho][N^3]  DFT index order
+    const T* dftw;      // [N][N] complex (re, im interleaved): e^{-2 pi i q j / N}
+};
+
+// Per-call node parameters: rho_r = 4 pi b_i c_r^{gamma_i + 2} (times ln c_r if dlog).
+struct NodeParams {
+    const double* gamma;   // [nodes] device, or nullptr -> gamma0
+    const double* b;       // [nodes] device, or nullptr -> b0
+    double gamma0, b0;
+    int dlog;              // 1: derivative with respect to gamma
+};
+
+// ---- translate/product kernels (CUDA cores) ------------------------------------------
+// P[node][r][N^3] = sum_pairs w_p [(T_s f)(T_-s g) + (T_-s f)(T_s g)] for every radial node.
+// g == nullptr means g = f. offs: element offset of every node (nullptr: node * N^3).
+cudaError_t launch_gain_products(const DevTables<float>& t, const float* f, const float* g,
+                                 const int64_t* offs, int64_t nodes, float* P, cudaStream_t s);
+cudaError_t launch_gain_products(const DevTables<double>& t, const double* f, const double* g,
+                                 const int64_t* offs, int64_t nodes, double* P, cudaStream_t s);
+
+// VJP gain part: out[node][r][N^3] = sum_pairs 2 w_p [T_-s(U_r T_-s f) + T_s(U_r T_s f)],
+// with U[node][r][N^3] = K_r u given; scratch: [nodes][Nrho][2][N^3].
+cudaError_t launch_vjp_products(const DevTables<float>& t, const float* f, const float* U,
+                                int64_t nodes, float* scratch, float* out, cudaStream_t s);
+cudaError_t launch_vjp_products(const DevTables<double>& t, const double* f, const double* U,
+                                int64_t nodes, double* scratch, double* out, cudaStream_t s);
+
+// ---- Fourier-side kernels -------------------------------------------------------------
+template <typename T>
+struct Cplx { T x, y; };
+
+// X[node][s] (complex) = sum_r Vr[s][r] w_r rho_r(node) P[node][r]  for s < rank.
+template <typename T>
+cudaError_t launch_project(const DevTables<T>& t, const T* P, NodeParams np, int64_t nodes,
+                           Cplx<T>* X, int xfields, cudaStream_t s);
+
+// X[node][slot] = a (real -> complex) for an input field a (offs as above) or a*b product.
+template <typename T>
+cudaError_t launch_load_field(int N, const T* a, const T* b, const int64_t* offs, int64_t nodes,
+                              Cplx<T>* X, int xfields, int slot, cudaStream_t s);
+
+// In-place 3-D DFT of `count` complex fields of N^3 (forward: scale 1/N^3, sign -1).
+template <typename T>
+cudaError_t launch_dft3(const DevTables<T>& t, Cplx<T>* X, int64_t count, bool forward,
+                        cudaStream_t s);
+
+// Y[node][0] = scale * sum_s Uk[s] X[node][s] + i GL X[node][loss_slot0];
+// if loss_slot1 >= 0: Y[node][1] = GL X[node][loss_slot1]. GL = sum_r rho_r(node) Lr[r].
+template <typename T>
+cudaError_t launch_combine(const DevTables<T>& t, const Cplx<T>* X, int xfields, NodeParams np,
+                           int64_t nodes, T scale, int loss_slot0, int loss_slot1, Cplx<T>* Y,
+                           int yfields, cudaStream_t s);
+
+// U[node][r] = w_r rho_r(node) sum_s Vr[s][r] Re X[node][s]   (after an inverse DFT)
+template <typename T>
+cudaError_t launch_expand_radial(const DevTables<T>& t, const Cplx<T>* X, int xfields,
+                                 NodeParams np, int64_t nodes, T* U, cudaStream_t s);
+
+// X[node][s] = Uk[s] * X[node][src_slot] for s < rank (Fourier multiply, complex)
+template <typename T>
+cudaError_t launch_multiply_uk(const DevTables<T>& t, Cplx<T>* X, int xfields, int src_slot,
+                               int64_t nodes, cudaStream_t s);
+
+// Y[node][0] = GL X[node][slot0] + i GL X[node][slot1]
+template <typename T>
+cudaError_t launch_loss_pair(const DevTables<T>& t, const Cplx<T>* X, int xfields, NodeParams np,
+                             int64_t nodes, int slot0, int slot1, Cplx<T>* Y, int yfields,
+                             cudaStream_t s);
+
+// out = Re Y0 - a * Im Y0 - (c ? c * Re Y1 : 0)       (mode 0)
+// out = sum_r G[node][r] - u * Re Y0 - Im Y0            (mode 1, VJP)
+template <typename T>
+cudaError_t launch_finalize(int N, int Nrho, const Cplx<T>* Y, int yfields, const T* a,
+                            const T* c, const T* G, const int64_t* offs, int64_t nodes, int mode,
+                            T* out, int* flags, cudaStream_t s);
+
+}  // namespace dgfs

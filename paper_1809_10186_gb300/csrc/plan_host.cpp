@@ -1,0 +1,436 @@
+// Host-side FP64 plan builder (see plan_host.h).
+#include "plan_host.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <numeric>
+
+namespace dgfs {
+
+static const double kPi = 3.14159265358979323846;
+
+double default_b(double gamma) {
+    // nondimensional VHS constant, alpha = 1 (Sec. 2.1): 1 / (2^{3-omega} Gamma(5/2-omega) pi)
+    const double omega = 1.0 - 0.5 * gamma;
+    return 1.0 / (std::pow(2.0, 3.0 - omega) * std::tgamma(2.5 - omega) * kPi);
+}
+
+double default_R(double L) { return 4.0 * L / (3.0 + std::sqrt(2.0)); }  // Appendix
+
+void gauss_legendre(int n, double a, double b, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double p1 = 0, p2 = 0, dp = 0;
+        for (int it = 0; it < 100; ++it) {
+            p1 = 1.0;
+            p2 = 0.0;
+            for (int j = 1; j <= n; ++j) {
+                const double p3 = p2;
+                p2 = p1;
+                p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+            }
+            dp = n * (z * p1 - p2) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-17) break;
+        }
+        // derivative at the converged node for the weight
+        p1 = 1.0;
+        p2 = 0.0;
+        for (int j = 1; j <= n; ++j) {
+            const double p3 = p2;
+            p2 = p1;
+            p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+        }
+        dp = n * (z * p1 - p2) / (z * z - 1.0);
+        const double wi = 2.0 / ((1.0 - z * z) * dp * dp);
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = wi;
+    }
+    const double h = 0.5 * (b - a), m = 0.5 * (b + a);
+    for (int i = 0; i < n; ++i) {
+        x[i] = h * x[i] + m;
+        w[i] *= h;
+    }
+}
+
+// ---- sphere rules ------------------------------------------------------------------------
+
+namespace {
+
+struct Pt { double x, y, z; };
+
+void add_unique(std::vector<Pt>& v, Pt p) {
+    for (const Pt& q : v)
+        if (std::fabs(q.x - p.x) + std::fabs(q.y - p.y) + std::fabs(q.z - p.z) < 1e-12) return;
+    v.push_back(p);
+}
+
+// all coordinate permutations and sign changes of (a, b, c)
+std::vector<Pt> orbit(double a, double b, double c) {
+    const double v[3] = {a, b, c};
+    const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    std::vector<Pt> out;
+    for (auto& pm : perm)
+        for (int s = 0; s < 8; ++s) {
+            Pt p{v[pm[0]] * ((s & 1) ? -1 : 1), v[pm[1]] * ((s & 2) ? -1 : 1),
+                 v[pm[2]] * ((s & 4) ? -1 : 1)};
+            p.x += 0.0; p.y += 0.0; p.z += 0.0;   // no negative zeros
+            add_unique(out, p);
+        }
+    return out;
+}
+
+// one representative per antipodal pair: the point whose first nonzero coordinate is > 0
+void push_pairs(const std::vector<Pt>& pts, double w, std::vector<double>& sig,
+                std::vector<double>& ws) {
+    for (const Pt& p : pts) {
+        const double lead = (std::fabs(p.x) > 1e-14) ? p.x : (std::fabs(p.y) > 1e-14) ? p.y : p.z;
+        if (lead > 0) {
+            sig.push_back(p.x);
+            sig.push_back(p.y);
+            sig.push_back(p.z);
+            ws.push_back(w);
+        }
+    }
+}
+
+}  // namespace
+
+bool sphere_pairs(int M, std::vector<double>& sig, std::vector<double>& w) {
+    sig.clear();
+    w.clear();
+    const double fourpi = 4.0 * kPi;
+    if (M == 6) {                         // octahedron, degree 3
+        push_pairs(orbit(1, 0, 0), fourpi / 6, sig, w);
+        return true;
+    }
+    if (M == 12) {                        // icosahedron, degree 5
+        const double phi = 0.5 * (1.0 + std::sqrt(5.0));
+        const double n = std::sqrt(1.0 + phi * phi);
+        std::vector<Pt> pts;
+        for (int s1 = -1; s1 <= 1; s1 += 2)
+            for (int s2 = -1; s2 <= 1; s2 += 2) {
+                const double a = 0.0, b = s1 / n, c = s2 * phi / n;
+                add_unique(pts, {a, b, c});
+                add_unique(pts, {b, c, a});
+                add_unique(pts, {c, a, b});
+            }
+        push_pairs(pts, fourpi / 12, sig, w);
+        return true;
+    }
+    // Octahedral orbits: vertices (6), edge midpoints (12), corners (8), (p, q, 0) (24).
+    // Exact monomial integrals over S^2: int 1 = 4pi, int x^4 = 4pi/5,
+    // int x^2 y^2 z^2 = 4pi/105, int x^8 = 4pi/9.
+    const double w3 = (fourpi / 105.0) / (8.0 / 27.0);   // corners: only orbit with x^2y^2z^2
+    if (M == 26) {                        // degree 7
+        // 6 w1 + 12 w2 + 8 w3 = 4pi ;  2 w1 + 2 w2 + (8/9) w3 = 4pi/5
+        const double r1 = fourpi - 8.0 * w3, r2 = fourpi / 5.0 - 8.0 / 9.0 * w3;
+        // solve [[6,12],[2,2]] [w1,w2] = [r1, r2]
+        const double det = 6.0 * 2.0 - 12.0 * 2.0;
+        const double w1 = (r1 * 2.0 - 12.0 * r2) / det;
+        const double w2 = (6.0 * r2 - 2.0 * r1) / det;
+        const double s2 = 1.0 / std::sqrt(2.0), s3 = 1.0 / std::sqrt(3.0);
+        push_pairs(orbit(1, 0, 0), w1, sig, w);
+        push_pairs(orbit(s2, s2, 0), w2, sig, w);
+        push_pairs(orbit(s3, s3, s3), w3, sig, w);
+        return true;
+    }
+    if (M == 38) {                        // degree 9
+        auto solve = [&](double p, double& w1, double& wc) {
+            const double q = std::sqrt(1.0 - p * p);
+            // 6 w1 + 8 w3 + 24 wc = 4pi ;  2 w1 + (8/9) w3 + 8 (p^4 + q^4) wc = 4pi/5
+            const double a11 = 6, a12 = 24, a21 = 2, a22 = 8.0 * (std::pow(p, 4) + std::pow(q, 4));
+            const double r1 = fourpi - 8.0 * w3, r2 = fourpi / 5.0 - 8.0 / 9.0 * w3;
+            const double det = a11 * a22 - a12 * a21;
+            w1 = (r1 * a22 - a12 * r2) / det;
+            wc = (a11 * r2 - a21 * r1) / det;
+            // residual of the degree-8 moment: 2 w1 + (8/81) w3 + 8 (p^8 + q^8) wc - 4pi/9
+            return 2.0 * w1 + 8.0 / 81.0 * w3 + 8.0 * (std::pow(p, 8) + std::pow(q, 8)) * wc
+                   - fourpi / 9.0;
+        };
+        double lo = 0.3, hi = 0.7, w1 = 0, wc = 0;
+        double flo = solve(lo, w1, wc);
+        for (int it = 0; it < 200; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            const double fm = solve(mid, w1, wc);
+            if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else { hi = mid; }
+            if (hi - lo < 1e-17) break;
+        }
+        const double p = 0.5 * (lo + hi);
+        solve(p, w1, wc);
+        const double s3 = 1.0 / std::sqrt(3.0);
+        push_pairs(orbit(1, 0, 0), w1, sig, w);
+        push_pairs(orbit(s3, s3, s3), w3, sig, w);
+        push_pairs(orbit(p, std::sqrt(1.0 - p * p), 0), wc, sig, w);
+        return true;
+    }
+    return false;
+}
+
+void translate_filter(int N, double L, double t, double* a) {
+    // a[d] = (1/N) sum_k m(k) e^{2 pi i k d / N}, m(k) = e^{i pi k t / L} for |k| < N/2 and
+    // cos(pi N t / 2L) at k = -N/2; pairing k with -k gives cosines.
+    const double nyq = std::cos(kPi * N * t / (2.0 * L));
+    for (int d = 0; d < N; ++d) {
+        double s = 1.0;
+        for (int k = 1; k < N / 2; ++k) s += 2.0 * std::cos(2.0 * kPi * k * d / N + kPi * k * t / L);
+        s += ((d & 1) ? -1.0 : 1.0) * nyq;
+        a[d] = s / N;
+    }
+}
+
+// ---- SVD (one-sided Jacobi) -----------------------------------------------------------
+
+namespace {
+
+// A: m x n column-major (m >= n). On return: sv[n] descending, U (m x n) column-major,
+// V (n x n) column-major with A = U diag(sv) V^T.
+void jacobi_svd(int m, int n, std::vector<double> A, std::vector<double>& sv,
+                std::vector<double>& U, std::vector<double>& V) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 80; ++sweep) {
+        bool rotated = false;
+        for (int i = 0; i < n - 1; ++i)
+            for (int j = i + 1; j < n; ++j) {
+                double al = 0, be = 0, ga = 0;
+                const double* ci = &A[(size_t)i * m];
+                const double* cj = &A[(size_t)j * m];
+                for (int r = 0; r < m; ++r) {
+                    al += ci[r] * ci[r];
+                    be += cj[r] * cj[r];
+                    ga += ci[r] * cj[r];
+                }
+                if (std::fabs(ga) <= 1e-15 * std::sqrt(al * be) || ga == 0.0) continue;
+                rotated = true;
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+                double* ai = &A[(size_t)i * m];
+                double* aj = &A[(size_t)j * m];
+                for (int r = 0; r < m; ++r) {
+                    const double x = ai[r], y = aj[r];
+                    ai[r] = c * x - s * y;
+                    aj[r] = s * x + c * y;
+                }
+                double* vi = &V[(size_t)i * n];
+                double* vj = &V[(size_t)j * n];
+                for (int r = 0; r < n; ++r) {
+                    const double x = vi[r], y = vj[r];
+                    vi[r] = c * x - s * y;
+                    vj[r] = s * x + c * y;
+                }
+            }
+        if (!rotated) break;
+    }
+    std::vector<double> norms(n);
+    for (int i = 0; i < n; ++i) {
+        double s = 0;
+        for (int r = 0; r < m; ++r) s += A[(size_t)i * m + r] * A[(size_t)i * m + r];
+        norms[i] = std::sqrt(s);
+    }
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return norms[a] > norms[b]; });
+    sv.resize(n);
+    U.assign((size_t)m * n, 0.0);
+    std::vector<double> V2((size_t)n * n);
+    for (int k = 0; k < n; ++k) {
+        const int i = order[k];
+        sv[k] = norms[i];
+        for (int r = 0; r < m; ++r) U[(size_t)k * m + r] = norms[i] > 0 ? A[(size_t)i * m + r] / norms[i] : 0.0;
+        for (int r = 0; r < n; ++r) V2[(size_t)k * n + r] = V[(size_t)i * n + r];
+    }
+    V.swap(V2);
+}
+
+inline int signed_k(int q, int N) { return q < N / 2 ? q : q - N; }
+
+}  // namespace
+
+// ---- plan --------------------------------------------------------------------------------
+
+static bool supported_N(int N) { return N == 8 || N == 12 || N == 16 || N == 24 || N == 32; }
+
+dgfs_status build_quadrature(const dgfs_plan_desc& d, HostPlan& p, std::string& err) {
+    if (!supported_N(d.N)) {
+        err = "N must be one of 8, 12, 16, 24, 32";
+        return DGFS_ERR_INVALID_ARG;
+    }
+    if (!(d.L > 0) || !std::isfinite(d.L)) { err = "L must be positive"; return DGFS_ERR_INVALID_ARG; }
+    if (!std::isfinite(d.gamma) || d.gamma < -2.5 || d.gamma > 2.0) {
+        err = "gamma must lie in [-2.5, 2]";
+        return DGFS_ERR_INVALID_ARG;
+    }
+    p.N = d.N;
+    p.L = d.L;
+    p.gamma = d.gamma;
+    p.R = d.R > 0 ? d.R : default_R(d.L);
+    p.b = d.b > 0 ? d.b : default_b(d.gamma);
+    p.Nrho = d.N_rho > 0 ? d.N_rho : d.N;
+    p.loss_mode = d.loss_mode;
+    if (p.Nrho > 64) { err = "N_rho must be <= 64"; return DGFS_ERR_INVALID_ARG; }
+    if (!std::isfinite(p.R) || !std::isfinite(p.b)) { err = "non-finite R or b"; return DGFS_ERR_INVALID_ARG; }
+    gauss_legendre(p.Nrho, 0.0, p.R, p.cr, p.wr);
+    if (d.sphere_xyzw) {
+        if (d.M < 2 || d.M % 2 || d.M > 512) { err = "M must be even, 2..512"; return DGFS_ERR_INVALID_ARG; }
+        p.sig.clear();
+        p.wsig.clear();
+        double wsum = 0;
+        for (int i = 0; i < d.M / 2; ++i) {
+            const double* q = d.sphere_xyzw + 4 * i;
+            const double nrm = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+            if (!(std::fabs(nrm - 1.0) < 1e-12) || !(q[3] > 0)) {
+                err = "sphere_xyzw: points must be unit vectors with positive weights";
+                return DGFS_ERR_INVALID_ARG;
+            }
+            p.sig.insert(p.sig.end(), {q[0], q[1], q[2]});
+            p.wsig.push_back(q[3]);
+            wsum += 2.0 * q[3];
+        }
+        if (std::fabs(wsum - 4.0 * kPi) > 1e-10 * 4.0 * kPi) {
+            err = "sphere_xyzw: weights of the full antipodal rule must sum to 4 pi";
+            return DGFS_ERR_INVALID_ARG;
+        }
+    } else if (!sphere_pairs(d.M, p.sig, p.wsig)) {
+        err = "no built-in sphere rule for this M (have 6, 12, 26, 38); pass sphere_xyzw";
+        return DGFS_ERR_INVALID_ARG;
+    }
+    p.npairs = (int)p.wsig.size();
+    return DGFS_OK;
+}
+
+dgfs_status build_host_plan(const dgfs_plan_desc& d, HostPlan& p, std::string& err) {
+    dgfs_status st = build_quadrature(d, p, err);
+    if (st != DGFS_OK) return st;
+    if (d.loss_mode != DGFS_LOSS_PAPER && d.loss_mode != DGFS_LOSS_CONSERVATIVE) {
+        err = "unknown loss_mode";
+        return DGFS_ERR_INVALID_ARG;
+    }
+    if (!(d.svd_tol >= 0) || d.svd_rank < 0) { err = "svd_tol and svd_rank must be >= 0"; return DGFS_ERR_INVALID_ARG; }
+    const int N = p.N, Nr = p.Nrho, np = p.npairs;
+    const size_t n3 = (size_t)N * N * N;
+
+    // translate filters of s_rp = c_r sigma_p / 2 (eq. apndx_Q: c' = c - c_r/2 + c_r sigma/2)
+    p.filt.assign((size_t)Nr * np * 3 * N, 0.0);
+    for (int r = 0; r < Nr; ++r)
+        for (int q = 0; q < np; ++q)
+            for (int a = 0; a < 3; ++a)
+                translate_filter(N, p.L, 0.5 * p.cr[r] * p.sig[3 * q + a],
+                                 &p.filt[(((size_t)r * np + q) * 3 + a) * N]);
+
+    // distinct |k|^2 on the lattice, multiplicities, and the map k -> class
+    const int qmax = 3 * (N / 2) * (N / 2);
+    std::vector<int> cls_of_q(qmax + 1, -1), mult;
+    std::vector<int> qvals;
+    std::vector<int> cls_of_k(n3);
+    for (size_t i = 0; i < n3; ++i) {
+        const int kx = signed_k((int)(i / (N * N)), N), ky = signed_k((int)((i / N) % N), N),
+                  kz = signed_k((int)(i % N), N);
+        const int q2 = kx * kx + ky * ky + kz * kz;
+        if (cls_of_q[q2] < 0) {
+            cls_of_q[q2] = (int)qvals.size();
+            qvals.push_back(q2);
+            mult.push_back(0);
+        }
+        cls_of_k[i] = cls_of_q[q2];
+        mult[cls_of_q[q2]]++;
+    }
+    const int nq = (int)qvals.size();
+    // S(|k|, r) = sinc(pi c_r |k| / 2L): the isotropic closed form of F / rho_r (eq. realGG)
+    auto sinc = [](double x) { return x == 0.0 ? 1.0 : std::sin(x) / x; };
+    std::vector<double> S((size_t)nq * Nr);     // row-major [q][r]
+    for (int c = 0; c < nq; ++c)
+        for (int r = 0; r < Nr; ++r)
+            S[(size_t)c * Nr + r] = sinc(kPi * p.cr[r] * std::sqrt((double)qvals[c]) / (2.0 * p.L));
+
+    std::vector<double> Seff_cls((size_t)nq * Nr);   // effective (possibly truncated) S
+    if (d.svd_tol > 0 || d.svd_rank > 0) {
+        if (nq < Nr) { err = "radial kernel has fewer |k| classes than radial points"; return DGFS_ERR_UNSUPPORTED; }
+        std::vector<double> A((size_t)nq * Nr);       // column-major, rows weighted by sqrt(mult)
+        for (int r = 0; r < Nr; ++r)
+            for (int c = 0; c < nq; ++c) A[(size_t)r * nq + c] = std::sqrt((double)mult[c]) * S[(size_t)c * Nr + r];
+        std::vector<double> sv, U, V;
+        jacobi_svd(nq, Nr, A, sv, U, V);
+        int rank = d.svd_rank > 0 ? d.svd_rank : 0;
+        if (rank == 0)
+            for (int s = 0; s < Nr; ++s)
+                if (sv[s] > d.svd_tol * sv[0]) rank = s + 1;
+        rank = std::max(1, std::min(rank, Nr));
+        p.rank = rank;
+        p.Uk.assign((size_t)rank * n3, 0.0);
+        p.Vr.assign((size_t)rank * Nr, 0.0);
+        std::vector<double> Ucls((size_t)rank * nq);
+        for (int s = 0; s < rank; ++s) {
+            for (int c = 0; c < nq; ++c) Ucls[(size_t)s * nq + c] = U[(size_t)s * nq + c] * sv[s] / std::sqrt((double)mult[c]);
+            for (int r = 0; r < Nr; ++r) p.Vr[(size_t)s * Nr + r] = V[(size_t)s * Nr + r];
+        }
+        for (size_t i = 0; i < n3; ++i)
+            for (int s = 0; s < rank; ++s) p.Uk[(size_t)s * n3 + i] = Ucls[(size_t)s * nq + cls_of_k[i]];
+        for (int c = 0; c < nq; ++c)
+            for (int r = 0; r < Nr; ++r) {
+                double v = 0;
+                for (int s = 0; s < rank; ++s) v += Ucls[(size_t)s * nq + c] * p.Vr[(size_t)s * Nr + r];
+                Seff_cls[(size_t)c * Nr + r] = v;
+            }
+    } else {
+        p.rank = Nr;
+        p.Uk.assign((size_t)Nr * n3, 0.0);
+        p.Vr.assign((size_t)Nr * Nr, 0.0);
+        for (int r = 0; r < Nr; ++r) p.Vr[(size_t)r * Nr + r] = 1.0;
+        for (size_t i = 0; i < n3; ++i)
+            for (int r = 0; r < Nr; ++r) p.Uk[(size_t)r * n3 + i] = S[(size_t)cls_of_k[i] * Nr + r];
+        Seff_cls = S;
+    }
+
+    // loss weights per radial node: G_loss(k) = sum_r rho_r Lr[r][k]
+    p.Lr.assign((size_t)Nr * n3, 0.0);
+    if (p.loss_mode == DGFS_LOSS_PAPER) {
+        // G(m,m) = 4 pi sum_r w_r F(2m, c_r), F(2m, c_r) = rho_r sinc(pi c_r |m| / L)
+        for (int r = 0; r < Nr; ++r)
+            for (size_t i = 0; i < n3; ++i)
+                p.Lr[(size_t)r * n3 + i] = 4.0 * kPi * p.wr[r] *
+                    sinc(kPi * p.cr[r] * std::sqrt((double)qvals[cls_of_k[i]]) / p.L);
+    } else {
+        // G(-m,m) = sum_r w_r rho_r S(0,r) sum_pairs w_p Re[mu_s(m)^2 + mu_-s(m)^2]
+        const int c0 = cls_of_q[0];
+        for (int r = 0; r < Nr; ++r) {
+            const double s0 = Seff_cls[(size_t)c0 * Nr + r];
+            for (int q = 0; q < np; ++q) {
+                double sh[3];
+                for (int a = 0; a < 3; ++a) sh[a] = 0.5 * p.cr[r] * p.sig[3 * q + a];
+                for (size_t i = 0; i < n3; ++i) {
+                    const int kk[3] = {signed_k((int)(i / (N * N)), N), signed_k((int)((i / N) % N), N),
+                                       signed_k((int)(i % N), N)};
+                    // product over axes of mu(k_a)^2 for +s and for -s
+                    double re_p = 1, im_p = 0, re_m = 1, im_m = 0;
+                    for (int a = 0; a < 3; ++a) {
+                        double mr, mi;           // mu_{s_a}(k_a)^2
+                        if (kk[a] == -N / 2) {
+                            const double c = std::cos(kPi * N * sh[a] / (2.0 * p.L));
+                            mr = c * c;
+                            mi = 0;
+                        } else {
+                            const double ang = 2.0 * kPi * kk[a] * sh[a] / p.L;
+                            mr = std::cos(ang);
+                            mi = std::sin(ang);
+                        }
+                        const double tr = re_p * mr - im_p * mi, ti = re_p * mi + im_p * mr;
+                        re_p = tr; im_p = ti;
+                        const double ur = re_m * mr + im_m * mi, ui = -re_m * mi + im_m * mr;  // conj
+                        re_m = ur; im_m = ui;
+                    }
+                    p.Lr[(size_t)r * n3 + i] += p.wr[r] * s0 * p.wsig[q] * (re_p + re_m);
+                }
+            }
+        }
+    }
+    return DGFS_OK;
+}
+
+}  // namespace dgfs

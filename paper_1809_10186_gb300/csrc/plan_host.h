@@ -1,0 +1,51 @@
+// Host-side FP64 plan builder of the fast spectral collision operator.
+//
+// Everything the device kernels need that depends only on the discretisation
+// (arXiv:1809.10186, Appendix): the radial Gauss-Legendre rule, the antipodal sphere
+// rule, the per-axis translate filters of the shifts s_rp = c_r sigma_p / 2, the radial
+// kernel S(|k|, r) = sinc(pi c_r |k| / 2L) with its optional SVD compression, and the
+// loss weights. Computed once in double precision; the CUDA side rounds them.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dgfs.h"
+
+namespace dgfs {
+
+struct HostPlan {
+    int N = 0, Nrho = 0, npairs = 0, rank = 0, loss_mode = 0;
+    double L = 0, R = 0, gamma = 0, b = 0;
+    std::vector<double> cr, wr;          // Gauss-Legendre on [0, R]
+    std::vector<double> sig;             // [npairs][3] pair representatives sigma_p
+    std::vector<double> wsig;            // [npairs]   weight of each point of a pair
+    std::vector<double> filt;            // [Nrho][npairs][3][N] circulant filters of +s_rp
+    // radial kernel, compressed: gain^(k) = sum_s Uk[s][k] * DFT( sum_r Vr[s][r] w_r rho_r P_r )
+    std::vector<double> Uk;              // [rank][N^3] in DFT index order
+    std::vector<double> Vr;              // [rank][Nrho]
+    // loss: G_loss(k) = sum_r rho_r(gamma, b) * Lr[r][k]
+    std::vector<double> Lr;              // [Nrho][N^3] in DFT index order
+};
+
+// Gauss-Legendre rule on [a, b] by Newton iteration on the Legendre recurrence.
+void gauss_legendre(int n, double a, double b, std::vector<double>& x, std::vector<double>& w);
+
+// Built-in antipodal sphere rules (M = 6, 12, 26, 38): one point per pair and the weight
+// of each point. Returns false for an unsupported M.
+bool sphere_pairs(int M, std::vector<double>& sig, std::vector<double>& w);
+
+// Circulant filter a[N] of the translate by t (multiplier e^{i pi k t / L}, Nyquist cos).
+void translate_filter(int N, double L, double t, double* a);
+
+double default_b(double gamma);
+double default_R(double L);
+
+// Validates the descriptor and fills the plan. On failure returns a status and a message.
+dgfs_status build_host_plan(const dgfs_plan_desc& d, HostPlan& p, std::string& err);
+
+// Quadrature only (no tables), for introspection.
+dgfs_status build_quadrature(const dgfs_plan_desc& d, HostPlan& p, std::string& err);
+
+}  // namespace dgfs

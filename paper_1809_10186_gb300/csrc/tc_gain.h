@@ -1,0 +1,26 @@
+// Tensor-core (tcgen05) translate-product path for the 16-bit precisions.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "plan_host.h"
+
+namespace dgfs {
+
+struct TcTables {
+    int N = 0, Nrho = 0, npairs = 0;
+    const void* mats = nullptr;     // per (r, pair, axis, sign) N x N operand tiles
+    const float* wsig = nullptr;
+};
+
+bool tc_supported(int N);
+size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>& blob, TcTables& t);
+void rebase_tc_tables(TcTables& t, void* base);
+cudaError_t launch_tc_gain_products(const TcTables& t, int prec, const float* f, const float* g,
+                                    const int64_t* offs, int64_t nodes, float* P, int* flags,
+                                    cudaStream_t s);
+
+}  // namespace dgfs

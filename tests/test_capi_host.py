@@ -1,0 +1,99 @@
+"""The C-ABI library loads, exports every declared symbol, and its host-only plan builder
+agrees with the oracle's independent quadrature and translate operator (no GPU)."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1809_10186_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1809_10186_gb300 import build
+    build.build()
+    return binding.lib()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "dgfs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dgfs_\w+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in binding._SIGNATURES, "binding misses " + n
+
+
+@pytest.mark.parametrize("N", [8, 16, 32])
+def test_gauss_legendre_matches_oracle(lib, N):
+    cr, wr, _, R, _ = binding.host_quadrature(N=N, L=7.0, M=6, N_rho=N)
+    x, w = O.gauss_legendre(N, 0.0, R)
+    assert R == pytest.approx(4 * 7.0 / (3 + math.sqrt(2)), rel=1e-15)
+    np.testing.assert_allclose(cr, x, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(wr, w, rtol=1e-12)
+
+
+@pytest.mark.parametrize("M", [6, 12, 26, 38])
+def test_sphere_rules_match_oracle(lib, M):
+    _, _, sig, _, _ = binding.host_quadrature(N=8, L=3.0, M=M)
+    pts, wts, _ = O.sphere_rule(M)
+    assert sig.shape == (M // 2, 4)
+    # same point set (as antipodal pairs) with the same weights
+    full = np.concatenate([sig[:, :3], -sig[:, :3]])
+    fw = np.concatenate([sig[:, 3], sig[:, 3]])
+    for p, w in zip(pts, wts):
+        d = np.linalg.norm(full - p, axis=1)
+        i = int(np.argmin(d))
+        assert d[i] < 1e-12 and abs(fw[i] - w) < 1e-12
+
+
+def test_default_kernel_constant(lib):
+    omega = 0.74
+    _, _, _, _, b = binding.host_quadrature(N=8, L=3.0, M=6, gamma=2 * (1 - omega))
+    assert b == pytest.approx(O.b_vhs(omega), rel=1e-14)
+
+
+@pytest.mark.parametrize("N", [8, 16])
+def test_translate_filter_is_oracle_translate(lib, N):
+    """The circulant filter applied to a grid function equals the oracle's symmetric translate."""
+    L = 4.0
+    plan = O.OraclePlan(N, L, M=6, Nrho=2, nyquist="sym")
+    rng = np.random.default_rng(1)
+    f = rng.random((N, N, N))
+    s = np.array([0.731, -1.27, 2.91])
+    mats = []
+    for a in range(3):
+        filt = binding.host_translate_filter(N, L, s[a])
+        mats.append(np.array([[filt[(i - j) % N] for j in range(N)] for i in range(N)]))
+    got = np.einsum("ai,bj,ck,ijk->abc", mats[0], mats[1], mats[2], f)
+    np.testing.assert_allclose(got, plan.translate_hat(plan.dft3(f), s), atol=1e-12)
+
+
+def test_invalid_descriptors_rejected_before_any_cuda_call(lib):
+    for kw, frag in (({"N": 7}, "N must be"), ({"N": 20}, "N must be"), ({"L": -1.0}, "L must"),
+                     ({"M": 10}, "sphere rule"), ({"N_rho": 100}, "N_rho")):
+        d, _ = binding.make_desc(**{"N": 8, "L": 3.0, "M": 6, **kw})
+        h = ctypes.c_void_p()
+        st = lib.dgfs_plan_create(ctypes.byref(d), ctypes.byref(h))
+        assert st == 1 and not h.value, kw
+        assert frag in lib.dgfs_last_error_message().decode()
+    # a user sphere rule that is not normalised
+    d, keep = binding.make_desc(N=8, L=3.0, sphere=np.array([[1.0, 0, 0, 1.0], [0, 1.0, 0, 1.0]]))
+    assert lib.dgfs_plan_create(ctypes.byref(d), ctypes.byref(ctypes.c_void_p())) == 1
+
+
+def test_null_and_destroyed_plans_rejected(lib):
+    assert lib.dgfs_collide(None, None, None, 1, None) == 7
+    assert lib.dgfs_plan_destroy(None) == 0
+    assert lib.dgfs_plan_create(None, None) == 1

@@ -1,0 +1,315 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Error measure: relative L2 error of Q against the oracle, normalised by the oracle's loss
+term ||Q-|| (the magnitude of the quantities the kernels add up; gain and loss nearly cancel,
+so ||Q|| can be a few percent of it). The error normalised by ||Q|| is printed as well.
+Tolerances per precision (derived in the design notes from the unit round-off and the
+length of the sums): FP64 1e-10, FP32 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1809_10186_gb300 import binding, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1809_10186_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def _dev(a, prec):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", torch.float64 if prec == "fp64" else torch.float32)
+
+
+def _as_input(a, prec):
+    """The values both sides see: rounded to the GPU element type, then FP64 for the oracle."""
+    return a.astype(np.float64) if prec == "fp64" else a.astype(np.float32).astype(np.float64)
+
+
+def _errors(got, ref, loss):
+    d = np.linalg.norm(got - ref)
+    return d / np.linalg.norm(loss), d / np.linalg.norm(ref)
+
+
+def _oplan(N, L, gamma, M, Nrho, **kw):
+    return O.OraclePlan(N, L, gamma=gamma, M=M, Nrho=Nrho, nyquist="sym", **kw)
+
+
+# ---- small grids, rough inputs: every entry point ------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("N", [8, 16])
+def test_collide_rough_small(prec, N):
+    L, gamma, M = 3.0, 0.52, 12
+    F = _as_input(W.rough(3, N, 100 + N), prec)
+    plan = binding.Plan(N=N, L=L, gamma=gamma, M=M, N_rho=N, precision=prec)
+    q = plan.collide(_dev(F, prec)).double().cpu().numpy()
+    plan.stream_status()
+    op = _oplan(N, L, gamma, M, N)
+    for i in range(3):
+        ref = O.fast_Q(op, F[i])
+        e_loss, e_q = _errors(q[i], ref, np.real(O.loss_Q(op, F[i], F[i])))
+        print(prec, N, i, "err/|Q-| %.3g  err/|Q| %.3g" % (e_loss, e_q))
+        assert e_loss < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_collide2_jvp_dgamma_small(prec):
+    N, L, gamma, M = 8, 3.0, 0.38, 26
+    F, G = _as_input(W.rough(2, N, 7), prec), _as_input(W.rough(2, N, 8), prec)
+    plan = binding.Plan(N=N, L=L, gamma=gamma, M=M, N_rho=6, precision=prec, b=0.07)
+    op = O.OraclePlan(N, L, gamma=gamma, M=M, Nrho=6, nyquist="sym", b=0.07)
+    f, g = _dev(F, prec), _dev(G, prec)
+    q2 = plan.collide2(f, g).double().cpu().numpy()
+    jv = plan.collide_jvp(f, g).double().cpu().numpy()
+    dg = plan.collide_dgamma(f).double().cpu().numpy()
+    plan.stream_status()
+    for i in range(2):
+        scale = np.linalg.norm(np.real(O.loss_Q(op, F[i], G[i])))
+        assert np.linalg.norm(q2[i] - O.fast_Q(op, F[i], G[i])) / scale < TOL[prec]
+        assert np.linalg.norm(jv[i] - O.jvp(op, F[i], G[i])) / scale < TOL[prec]
+        ref = O.dQ_dgamma(op, F[i])
+        assert np.linalg.norm(dg[i] - ref) / np.linalg.norm(ref) < 10 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_vjp_small(prec):
+    N, L, gamma, M = 8, 3.0, 0.52, 12
+    F, U = _as_input(W.rough(2, N, 17), prec), _as_input(W.rough(2, N, 18) - 0.5, prec)
+    plan = binding.Plan(N=N, L=L, gamma=gamma, M=M, N_rho=6, precision=prec)
+    op = O.OraclePlan(N, L, gamma=gamma, M=M, Nrho=6, nyquist="sym")
+    gf = plan.collide_vjp(_dev(F, prec), _dev(U, prec)).double().cpu().numpy()
+    plan.stream_status()
+    for i in range(2):
+        ref = O.vjp(op, F[i], U[i])
+        assert np.linalg.norm(gf[i] - ref) / np.linalg.norm(ref) < 10 * TOL[prec]
+
+
+# ---- the workload configurations -------------------------------------------------------------
+
+def test_bkw_single_node_fp64():
+    """Single node, Maxwell molecules, BKW datum at t0 = 5.5, N = 16, FP64; with the stated
+    R = 2 sqrt2 L / (3 + sqrt2) and with the paper's default R; 20 SSP-RK2 steps of 0.01."""
+    cfg = W.CONFIGS["bkw_n16"]
+    N, L = cfg["N"], cfg["L"]
+    f0 = W.bkw(N, L, 5.5)
+    for R in (cfg["R"], O.default_R(L)):
+        plan = binding.Plan(N=N, L=L, gamma=0.0, b=cfg["b"], R=R, M=cfg["M"], N_rho=cfg["Nrho"], precision="fp64")
+        op = O.OraclePlan(N, L, gamma=0.0, b=cfg["b"], R=R, M=cfg["M"], Nrho=cfg["Nrho"], nyquist="sym")
+        q = plan.collide(_dev(f0[None], "fp64")).cpu().numpy()[0]
+        ref = O.fast_Q(op, f0)
+        e_loss, e_q = _errors(q, ref, np.real(O.loss_Q(op, f0, f0)))
+        c2 = O.grid_c2(op)
+        print("R=%.4f err/|Q-| %.3g err/|Q| %.3g  |Q-Q_bkw|_inf %.3g" % (R, e_loss, e_q, np.abs(q - O.bkw_Q(c2, 5.5)).max()))
+        assert e_q < 1e-10
+        # 20 SSP-RK2 steps (eq. SSPRK2), the stage arithmetic on the device
+        f = _dev(f0[None], "fp64")
+        for _ in range(20):
+            v1 = f + 0.01 * plan.collide(f)
+            f = 0.5 * f + 0.5 * v1 + 0.005 * plan.collide(v1)
+        fo = O.ssp_rk2(op, f0, 0.01, 20)
+        assert np.abs(f.cpu().numpy()[0] - fo).max() < 1e-13
+        print("  after 20 steps |f - f_bkw(5.7)|_inf = %.3g" % np.abs(fo - O.bkw_f(c2, 5.7)).max())
+    # direct O(N^6) sum at N = 8 against the device result (paper lattice == sym here: smooth)
+    plan8 = binding.Plan(N=8, L=L, gamma=0.0, b=cfg["b"], M=cfg["M"], N_rho=8, precision="fp64")
+    f8 = W.bkw(8, L, 5.5)
+    op8 = O.OraclePlan(8, L, gamma=0.0, b=cfg["b"], M=cfg["M"], Nrho=8, nyquist="paper")
+    q8 = plan8.collide(_dev(f8[None], "fp64")).cpu().numpy()[0]
+    d8 = O.direct_Q(op8, f8)
+    assert np.linalg.norm(q8 - d8) / np.linalg.norm(d8) < 1e-8
+
+
+def test_slab_n24_fp32_all_nodes():
+    cfg = W.CONFIGS["slab_n24"]
+    N, L, B = cfg["N"], cfg["L"], cfg["B"]
+    F, _ = W.two_maxwellian(B, N, L, cfg["seed"])
+    F = _as_input(F, "fp32")
+    plan = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=cfg["M"], N_rho=cfg["Nrho"], precision="fp32")
+    q = plan.collide(_dev(F, "fp32")).double().cpu().numpy()
+    plan.stream_status()
+    op = _oplan(N, L, cfg["gamma"], cfg["M"], cfg["Nrho"])
+    worst = (0, 0)
+    for i in range(B):
+        e = _errors(q[i], O.fast_Q(op, F[i]), np.real(O.loss_Q(op, F[i], F[i])))
+        worst = max(worst, e)
+    print("slab N=24 FP32 worst err/|Q-| %.3g err/|Q| %.3g" % worst)
+    assert worst[0] < TOL["fp32"]
+
+
+def _vhs32(cfg_name, prec, nodes_checked):
+    cfg = W.CONFIGS[cfg_name]
+    N, L, B = cfg["N"], cfg["L"], cfg["B"]
+    F, _ = W.two_maxwellian(B, N, L, cfg["seed"], dtype=np.float32)
+    plan = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=cfg["M"], N_rho=cfg["Nrho"],
+                        svd_tol=cfg.get("svd_tol", 0.0), precision=prec)
+    q = plan.collide(_dev(F, prec)).double().cpu().numpy()
+    plan.stream_status()
+    op = _oplan(N, L, cfg["gamma"], cfg["M"], cfg["Nrho"], svd_rank=plan.info["svd_rank_used"]
+                if cfg.get("svd_tol") else 0)
+    rng = np.random.default_rng(5)
+    idx = sorted(set([0, B - 1] + list(rng.choice(B, nodes_checked - 2, replace=False))))
+    worst = (0, 0)
+    for i in idx:
+        Fi = F[i].astype(np.float64)
+        worst = max(worst, _errors(q[i], O.fast_Q(op, Fi), np.real(O.loss_Q(op, Fi, Fi))))
+    # every node: finite, and mass of Q small against the loss mass
+    assert np.isfinite(q).all()
+    return worst, plan
+
+
+def test_vhs_n32_full_batch_fp32_sampled():
+    """The primary workload's launch (2048 nodes, N = 32, M = 38, SVD at 1e-8) in FP32."""
+    worst, plan = _vhs32("vhs_n32", "fp32", 4)
+    print("N=32 FP32 rank %d worst err/|Q-| %.3g err/|Q| %.3g" % (plan.info["svd_rank_used"], *worst))
+    assert worst[0] < TOL["fp32"]
+
+
+def test_derivatives_n32_fp32():
+    cfg = W.CONFIGS["grad_n32"]
+    N, L, B = cfg["N"], cfg["L"], cfg["B"]
+    F, _ = W.two_maxwellian(B, N, L, cfg["seed"], dtype=np.float32)
+    V = W.directions(B, N, cfg["seed"] + 100, dtype=np.float32)
+    U = W.directions(B, N, cfg["seed"] + 200, dtype=np.float32)
+    plan = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=cfg["M"], N_rho=cfg["Nrho"], precision="fp32")
+    f, v, u = _dev(F, "fp32"), _dev(V, "fp32"), _dev(U, "fp32")
+    jv = plan.collide_jvp(f, v).double().cpu().numpy()
+    gf = plan.collide_vjp(f, u).double().cpu().numpy()
+    dg = plan.collide_dgamma(f).double().cpu().numpy()
+    plan.stream_status()
+    op = _oplan(N, L, cfg["gamma"], cfg["M"], cfg["Nrho"])
+    for i in (0, B - 1):
+        Fi, Vi, Ui = (x[i].astype(np.float64) for x in (F, V, U))
+        for got, ref, name in ((jv[i], O.jvp(op, Fi, Vi), "jvp"), (gf[i], O.vjp(op, Fi, Ui), "vjp"),
+                               (dg[i], O.dQ_dgamma(op, Fi), "dgamma")):
+            e = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            print("N=32", name, "node", i, "rel err %.3g" % e)
+            assert e < 1e-4
+        # dot-product identity on the device results
+        lhs, rhs = float(np.sum(Ui * jv[i])), float(np.sum(gf[i] * Vi))
+        assert abs(lhs - rhs) < 1e-4 * abs(lhs)
+
+
+def test_jvp_central_difference_fp64():
+    """JVP against central differences of the device Q (exact: Q is quadratic)."""
+    N, L = 16, 5.0
+    F, _ = W.two_maxwellian(2, N, L, 3)
+    V = W.directions(2, N, 4)
+    plan = binding.Plan(N=N, L=L, gamma=0.38, M=12, N_rho=N, precision="fp64")
+    f, v = _dev(F, "fp64"), _dev(V, "fp64")
+    h = 1e-3
+    fd = (plan.collide(f + h * v) - plan.collide(f - h * v)) / (2 * h)
+    jv = plan.collide_jvp(f, v)
+    assert (torch.linalg.norm(jv - fd) / torch.linalg.norm(jv)).item() < 1e-9
+    # dgamma against central differences in gamma (b held fixed)
+    b = plan.info["b"]
+    pp = binding.Plan(N=N, L=L, gamma=0.38 + 1e-4, b=b, M=12, N_rho=N, precision="fp64")
+    pm = binding.Plan(N=N, L=L, gamma=0.38 - 1e-4, b=b, M=12, N_rho=N, precision="fp64")
+    fdg = (pp.collide(f) - pm.collide(f)) / 2e-4
+    dg = plan.collide_dgamma(f)
+    assert (torch.linalg.norm(dg - fdg) / torch.linalg.norm(dg)).item() < 1e-6
+
+
+def test_ragged_mixed_grids():
+    """Packed nodes of N = 16, 24, 32 with per-node omega, in one call."""
+    cfg = W.CONFIGS["cavity_ragged"]
+    B = 60
+    node_N, node_omega = W.ragged_layout(B, cfg["Ns"], cfg["split"], cfg["omegas"], cfg["seed"])
+    L, M = cfg["L"], cfg["M"]
+    plans = {n: binding.Plan(N=n, L=L, M=M, N_rho=n, precision="fp32") for n in cfg["Ns"]}
+    order = list(cfg["Ns"])
+    offs = np.zeros(B, np.int64)
+    tot = 0
+    for i in range(B):
+        offs[i] = tot
+        tot += int(node_N[i]) ** 3
+    packed = np.zeros(tot, np.float32)
+    fields = []
+    for i in range(B):
+        n = int(node_N[i])
+        fi = W.near_equilibrium(1, n, L, cfg["seed"] + i, dtype=np.float32)[0]
+        fields.append(fi)
+        packed[offs[i]:offs[i] + n ** 3] = fi.ravel()
+    gam = 2 * (1 - node_omega)
+    bb = np.array([O.b_vhs(w) for w in node_omega])
+    fp = torch.from_numpy(packed).cuda()
+    q = binding.collide_ragged([plans[n] for n in order], [order.index(int(n)) for n in node_N], offs, fp,
+                               node_gamma=gam, node_b=bb).cpu().numpy()
+    for p in plans.values():
+        p.stream_status()
+    worst = 0
+    for i in list(range(0, B, 7)) + [B - 1]:
+        n = int(node_N[i])
+        op = _oplan(n, L, gam[i], M, n, b=bb[i])
+        Fi = fields[i].astype(np.float64)
+        e, _ = _errors(q[offs[i]:offs[i] + n ** 3].reshape(n, n, n), O.fast_Q(op, Fi), np.real(O.loss_Q(op, Fi, Fi)))
+        worst = max(worst, e)
+    print("ragged worst err/|Q-| %.3g" % worst)
+    assert worst < TOL["fp32"]
+
+
+# ---- structural properties and the C ABI's contract ----------------------------------------------
+
+def test_chunking_batch_order_and_determinism():
+    N, L = 16, 5.0
+    F, _ = W.two_maxwellian(7, N, L, 11, dtype=np.float32)
+    f = _dev(F, "fp32")
+    p1 = binding.Plan(N=N, L=L, gamma=0.38, M=12, N_rho=N, precision="fp32")
+    p3 = binding.Plan(N=N, L=L, gamma=0.38, M=12, N_rho=N, precision="fp32", max_batch=3)
+    assert p3.info["chunk_nodes"] == 3
+    a = p1.collide(f)
+    assert torch.equal(a, p1.collide(f))                     # bitwise reproducible
+    assert torch.equal(a, p3.collide(f))                     # chunking does not change results
+    perm = torch.tensor([3, 0, 6, 1, 5, 2, 4], device="cuda")
+    assert torch.equal(a[perm], p1.collide(f[perm].contiguous()))
+
+
+def test_host_buffer_entry_point_matches_device():
+    N, L = 16, 5.0
+    F, _ = W.two_maxwellian(5, N, L, 12, dtype=np.float32)
+    plan = binding.Plan(N=N, L=L, gamma=0.38, M=12, N_rho=N, precision="fp32", max_batch=2)
+    fh = torch.from_numpy(F).pin_memory()
+    qh = torch.empty_like(fh).pin_memory()
+    plan.collide_host(fh, qh)
+    assert torch.equal(qh, plan.collide(fh.cuda()).cpu())
+
+
+def test_empty_batch_and_argument_errors():
+    plan = binding.Plan(N=8, L=3.0, gamma=0.0, M=6, N_rho=4, precision="fp32")
+    f = torch.rand(2, 8, 8, 8, device="cuda")
+    out = torch.empty_like(f)
+    L_ = binding.lib()
+    s = binding._stream_ptr()
+    import ctypes
+    assert L_.dgfs_collide(plan.handle, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(out.data_ptr()), 0, s) == 0
+    # misaligned pointer
+    assert L_.dgfs_collide(plan.handle, ctypes.c_void_p(f.data_ptr() + 4), ctypes.c_void_p(out.data_ptr()), 1, s) == 1
+    # output aliasing the input
+    assert L_.dgfs_collide(plan.handle, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(f.data_ptr()), 1, s) == 1
+    # negative batch
+    assert L_.dgfs_collide(plan.handle, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(out.data_ptr()), -1, s) == 1
+    with pytest.raises(binding.DGFSError):
+        binding.Plan(N=32, L=7.0, M=38, precision="fp64")       # FP64 is limited to N <= 24
+
+
+def test_autograd_function():
+    N, L = 8, 3.0
+    plan = binding.Plan(N=N, L=L, gamma=0.52, M=12, N_rho=6, precision="fp64")
+    F = W.rough(1, N, 3)
+    f = _dev(F, "fp64").requires_grad_(True)
+    q = binding.collide(plan, f)
+    u = torch.randn_like(q)
+    (g,) = torch.autograd.grad(q, f, u)
+    op = O.OraclePlan(N, L, gamma=0.52, M=12, Nrho=6, nyquist="sym")
+    ref = O.vjp(op, F[0], u[0].cpu().numpy())
+    assert np.linalg.norm(g[0].cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-10
