@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Throughput of batched Q(f, f) on the N = 32 VHS workload (node evaluations per second).
+
+Workload ("vhs_n32"): 2048 DG nodes per GPU, each a seeded two-Maxwellian mixture on an
+N = 32 grid over [-7, 7]^3; VHS omega = 0.74 (gamma = 0.52); N_rho = 32 Gauss-Legendre
+radial points on [0, R], R = 4L/(3 + sqrt 2); M = 38 sphere points (19 antipodal pairs);
+radial kernel SVD-truncated at 1e-8. One step = one dgfs_collide over the whole batch.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|bf16x3|f16x3|f16]
+  python bench.py --impl reference ...      # the FP64 CPU oracle on the host cores
+
+Multi-GPU (torchrun, one process per GPU): nodes are independent, every rank evaluates its
+own 2048 nodes (weak scaling) and no data-path collective is used; the timed region is
+bracketed by barriers and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Q(f,f) node-evals/s at N=32 VHS, % roofline, mixed-prec vs FP32 at stated err"
+WORKLOAD = "vhs_n32"
+SMS = 152                 # GB300 streaming multiprocessors
+FP32_LANES = 128          # FP32 FMA lanes per SM
+SM_MAX_MHZ = 2070.0
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default=None, help="fp32 | bf16x3 | f16x3 | f16 (default: fastest built mode)")
+    ap.add_argument("--nodes", type=int, default=None, help="nodes per GPU (default 2048)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---- CPU oracle leg (the only place bench.py runs oracle/) ---------------------------------
+
+def _oracle_job(args):
+    """Runs in a spawned worker: Q of the given nodes with the FP64 oracle (unchanged)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import numpy as np
+    import oracle as O
+    from paper_1809_10186_gb300 import workloads as W
+    cfg = W.CONFIGS[WORKLOAD]
+    idx, B, seed, rank = args
+    F, _ = W.two_maxwellian(B, cfg["N"], cfg["L"], seed, dtype=np.float32)
+    plan = O.OraclePlan(cfg["N"], cfg["L"], gamma=cfg["gamma"], M=cfg["M"], Nrho=cfg["Nrho"],
+                        nyquist="sym", svd_rank=rank)
+    out = []
+    t0 = time.perf_counter()
+    for i in idx:
+        Fi = F[i].astype(np.float64)
+        q = O.fast_Q(plan, Fi)
+        loss = np.real(O.loss_Q(plan, Fi, Fi))
+        out.append((i, q, loss))
+    return out, time.perf_counter() - t0
+
+
+def oracle_sample(nodes_idx, B, seed, rank, procs):
+    """Evaluate the oracle on `nodes_idx` with `procs` single-threaded spawned workers."""
+    import multiprocessing as mp
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        chunks = [nodes_idx[i::procs] for i in range(procs) if nodes_idx[i::procs]]
+        with ctx.Pool(len(chunks)) as pool:
+            # plan construction happens inside each job; the timed part is reported per job
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_job, [(c, B, seed, rank) for c in chunks])
+            wall = time.perf_counter() - t0
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    results = [r for part, _ in res for r in part]
+    compute_wall = max(t for _, t in res)       # slowest worker's evaluation time
+    return results, compute_wall, wall, len(chunks)
+
+
+# ---- clocks during the timed region ----------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            v = [x.strip() for x in line.split(",")]
+            if len(v) < 9:
+                continue
+            try:
+                sm.append(float(v[1]))
+                smax.append(float(v[2]))
+            except ValueError:
+                continue
+            for n, flag in zip(names, v[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---- roofline bookkeeping ----------------------------------------------------------------------
+
+def translate_flops_per_node(N, Nrho, npairs, prec):
+    """Flops the chosen formulation executes in the translate-product kernel, per node.
+
+    Per (radial point, pair): two 3-D translates, each three dense N x N circulant passes over
+    N^2 lines (2 N^4 flops per pass), then the product and weighted accumulation (3 N^3).
+    Split 16-bit modes execute three products per contraction; F16 one.
+    """
+    mma = 12.0 * N ** 4
+    elem = 3.0 * N ** 3
+    mult = {"fp32": 1, "fp64": 1, "bf16x3": 3, "f16x3": 3, "f16": 1}[prec]
+    return Nrho * npairs * (mult * mma + elem)
+
+
+def fft_algorithmic_flops_per_node(N, Nrho, npairs):
+    """The method's work counted with radix-2 FFTs (one complex 3-D IDFT per pair gives both
+    real translates; 5 N^3 log2 N^3 flops) plus ~20 flops per point per pair of phase,
+    product and accumulation."""
+    return Nrho * npairs * (5.0 * N ** 3 * math.log2(N ** 3) + 20.0 * N ** 3)
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---- the reference arm: the FP64 CPU oracle ----------------------------------------------------
+
+def run_reference(a):
+    import numpy as np  # noqa: F401
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1809_10186_gb300 import workloads as W
+    cfg = W.CONFIGS[WORKLOAD]
+    cores = os.cpu_count() or 1
+    B = cfg["B"]
+    per_step = max(1, min(cores, 16))
+    times = []
+    total = 0
+    node = 0
+    for step in range(a.warmup + a.steps):
+        idx = [(node + i) % B for i in range(per_step)]
+        node += per_step
+        _, comp, _, procs = oracle_sample(idx, B, cfg["seed"], 0, per_step)
+        if step >= a.warmup:
+            times.append(comp)
+            total += len(idx)
+    val = total / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "node-evals/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "%s: 2048-node batch, sampled %d nodes per step" % (WORKLOAD, per_step),
+                       "N": cfg["N"], "M": cfg["M"], "N_rho": cfg["Nrho"], "nodes_per_step": per_step},
+            "cpu_baseline": {"value": val, "unit": "node-evals/s", "cores": procs, "kind": "oracle",
+                             "sample": "%d nodes per step, one single-threaded process per node" % per_step},
+            "e2e": {"value": val, "unit": "node-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---- our arm -----------------------------------------------------------------------------------
+
+def main():
+    a = _args()
+    if a.oracle_worker:
+        return 0
+    if a.impl == "reference":
+        return run_reference(a)
+    import numpy as np
+    import torch
+    from paper_1809_10186_gb300 import binding, workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    binding.lib()
+
+    cfg = W.CONFIGS[WORKLOAD]
+    N, L, M, Nr = cfg["N"], cfg["L"], cfg["M"], cfg["Nrho"]
+    B = a.nodes or cfg["B"]
+    prec = a.prec or "fp32"
+    F, _ = W.two_maxwellian(B, N, L, cfg["seed"] + rank, dtype=np.float32)
+    f = torch.from_numpy(F).cuda()
+    q = torch.empty_like(f)
+    plan = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=M, N_rho=Nr, svd_tol=cfg["svd_tol"], precision=prec)
+    npairs = plan.info["n_pairs"]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(p, steps, warmup):
+        for _ in range(warmup):
+            p.collide(f, out=q)
+        barrier()
+        sampler = ClockSampler(local)
+        sampler.start()
+        p.profile_begin()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            p.collide(f, out=q)
+        e1.record()
+        torch.cuda.synchronize()
+        prof = p.profile_end()
+        clocks = sampler.stop()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        p.stream_status()
+        return ms, prof, clocks
+
+    ms, prof, clocks = timed(plan, a.steps, a.warmup)
+    value = world * B * a.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel (translate-product), from the library's own events
+    per_launch_ms = prof["gain_ms"] / max(1, prof["gain_timed"])
+    nodes_per_launch = prof["nodes"] / max(1, prof["gain_launches"])
+    flops_node = translate_flops_per_node(N, Nr, npairs, prec)
+    achieved = flops_node * nodes_per_launch / (per_launch_ms / 1e3) / 1e12
+    peaks = _peaks()
+    if prec in ("fp32", "fp64"):
+        peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12 * (1.0 if prec == "fp32" else 1 / 64)
+        roof = {"bound": "alu", "peak_source": "152 SMs x 128 FP32 FMA lanes x 2 flops x 2070 MHz"}
+    else:
+        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        roof = {"bound": "tensor", "peak_source": "measured bf16 (sustained)"}
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                 "traffic": None, "kernel": "translate-product",
+                 "kernel_share": prof["gain_ms"] / ms if ms else None,
+                 "flops_per_node": flops_node, "nodes_per_launch": nodes_per_launch,
+                 "fft_algorithmic_tflops": fft_algorithmic_flops_per_node(N, Nr, npairs) * value / world / 1e12})
+
+    line = {"metric": METRIC, "value": value, "unit": "node-evals/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp64": "f64", "bf16x3": "bf16x3/f32", "f16x3": "f16x3/f32",
+                      "f16": "f16/f32"}[prec],
+            "data": "synthetic",
+            "config": {"workload": "%s: %d two-Maxwellian nodes/GPU, N=32 on [-7,7]^3, omega=0.74, "
+                                   "N_rho=32, M=38, SVD 1e-8" % (WORKLOAD, B),
+                       "nodes_per_gpu": B, "N": N, "M": M, "N_rho": Nr,
+                       "svd_rank": plan.info["svd_rank_used"], "precision": prec,
+                       "chunk_nodes": plan.info["chunk_nodes"],
+                       "l2": "inputs (%d MB) larger than L2 (129 MB)" % (f.numel() * 4 >> 20),
+                       "parallelism": "dp%d" % world},
+            "gpu_launches": prof["launches"], "clocks": clocks, "roofline": roof}
+
+    # end to end through the host-buffer entry point (pinned host memory, copies inside)
+    if not a.no_e2e:
+        fh = torch.from_numpy(F).pin_memory()
+        qh = torch.empty_like(fh).pin_memory()
+        plan.collide_host(fh, qh)
+        barrier()
+        t0 = time.perf_counter()
+        ke = max(1, min(a.steps, 3))
+        for _ in range(ke):
+            plan.collide_host(fh, qh)
+        barrier()
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        line["e2e"] = {"value": world * B * ke / dt, "unit": "node-evals/s",
+                       "h2d_bytes_per_step": fh.numel() * 4, "d2h_bytes_per_step": qh.numel() * 4}
+
+    # the plain FP32 GPU form beside a 16-bit mode
+    if prec != "fp32" and not a.no_compare:
+        p32 = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=M, N_rho=Nr, svd_tol=cfg["svd_tol"], precision="fp32")
+        ms32, _, _ = timed(p32, max(1, a.steps // 2), 1)
+        line["compare"] = {"fp32": {"value": world * B * max(1, a.steps // 2) / (ms32 / 1e3)}}
+
+    # CPU baseline: the oracle on a bounded sample of the same nodes (rank 0, N = 1 only)
+    if world == 1 and not a.no_cpu:
+        plan.collide(f, out=q)
+        torch.cuda.synchronize()
+        cores = os.cpu_count() or 1
+        procs = max(1, min(cores, 16))
+        rng = np.random.default_rng(0)
+        idx = sorted(rng.choice(B, procs, replace=False).tolist())
+        res, comp, wall, used = oracle_sample(idx, B, cfg["seed"], plan.info["svd_rank_used"], procs)
+        qc = q.double().cpu().numpy()
+        e_loss, e_q, mass = [], [], []
+        for i, qo, loss in res:
+            d = np.linalg.norm(qc[i] - qo)
+            e_loss.append(d / np.linalg.norm(loss))
+            e_q.append(d / np.linalg.norm(qo))
+            mass.append(abs(qc[i].sum()) / np.abs(loss).sum())
+        line["cpu_baseline"] = {"value": len(idx) / comp, "unit": "node-evals/s", "cores": used,
+                                "kind": "oracle",
+                                "sample": "%d of the %d nodes, one single-threaded FP64 process each" % (len(idx), B)}
+        line["accuracy"] = {"vs": "FP64 oracle on the cpu_baseline sample", "nodes": len(idx),
+                            "rel_l2_vs_loss_max": max(e_loss), "rel_l2_vs_Q_max": max(e_q),
+                            "mass_drift_max": max(mass)}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -159,6 +159,21 @@ dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host
    plan (DGFS_ERR_TIMEOUT, DGFS_ERR_NUMERIC), then clear them. */
 dgfs_status dgfs_stream_status(dgfs_plan_t plan, void* stream);
 
+/* Profiling of one plan: between begin and end the library counts its kernel launches and
+   brackets every launch of the translate-product kernel (the dominant kernel) with CUDA
+   events on the call's stream. end synchronises those events and reports the totals.
+   At most 65536 bracketed launches per session; later ones are counted, not timed. */
+typedef struct {
+    int64_t launches;         /* kernels launched by compute calls of this plan             */
+    int64_t gain_launches;    /* translate-product kernel launches                           */
+    int64_t gain_timed;       /* of which bracketed by events                                */
+    double gain_ms;           /* summed event time of the bracketed launches                 */
+    int64_t nodes;            /* node evaluations requested                                  */
+} dgfs_profile_t;
+
+dgfs_status dgfs_profile_begin(dgfs_plan_t plan);
+dgfs_status dgfs_profile_end(dgfs_plan_t plan, dgfs_profile_t* out);
+
 /* Message of the last failed call on the calling thread ("" if none). */
 const char* dgfs_last_error_message(void);
 

@@ -39,6 +39,11 @@ class dgfs_plan_info_t(ctypes.Structure):
                 ("table_bytes", ctypes.c_size_t)]
 
 
+class dgfs_profile_t(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("gain_launches", ctypes.c_int64),
+                ("gain_timed", ctypes.c_int64), ("gain_ms", ctypes.c_double), ("nodes", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _SIGNATURES = {
@@ -56,6 +61,8 @@ _SIGNATURES = {
                             ctypes.POINTER(ctypes.c_double), _I64, _P, _P, _P],
     "dgfs_collide_host": [_P, _P, _P, _I64, _P],
     "dgfs_stream_status": [_P, _P],
+    "dgfs_profile_begin": [_P],
+    "dgfs_profile_end": [_P, ctypes.POINTER(dgfs_profile_t)],
     "dgfs_last_error_message": [],
     "dgfs_host_quadrature": [ctypes.POINTER(dgfs_plan_desc), ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -218,6 +225,14 @@ class Plan:
                                       ctypes.c_void_p(q_host.data_ptr()), ctypes.c_int64(B),
                                       _stream_ptr(stream)), "dgfs_collide_host")
         return q_host
+
+    def profile_begin(self):
+        check(lib().dgfs_profile_begin(self.handle), "dgfs_profile_begin")
+
+    def profile_end(self):
+        out = dgfs_profile_t()
+        check(lib().dgfs_profile_end(self.handle, ctypes.byref(out)), "dgfs_profile_end")
+        return {k: getattr(out, k) for k, _ in dgfs_profile_t._fields_}
 
     def stream_status(self, stream=None):
         check(lib().dgfs_stream_status(self.handle, _stream_ptr(stream)), "dgfs_stream_status")

@@ -67,6 +67,10 @@ struct dgfs_plan_s {
     size_t off_P = 0, off_G = 0, off_S = 0, off_X = 0, off_Y = 0, off_io = 0, off_node = 0;
     int xfields = 0;
     std::mutex host_mu;      // serialises host-side staging of per-node arrays
+    // profiling session
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;   // pairs
+    int64_t prof_launches = 0, prof_gain = 0, prof_timed = 0, prof_nodes = 0;
 };
 
 namespace {
@@ -93,7 +97,7 @@ void workspace_layout(dgfs_plan_s* p, int64_t C) {
     p->off_G = take(C * Nr * n3 * es);                 // VJP per-radial outputs
     p->off_S = take(C * Nr * 2 * n3 * es);             // VJP scratch
     p->off_X = take(C * (size_t)p->xfields * n3 * 2 * es);
-    p->off_Y = take(C * 2 * n3 * 2 * es);
+    p->off_Y = take(C * 3 * n3 * 2 * es);
     p->off_io = take(C * 2 * n3 * es);                 // host-buffer staging (f in, Q out)
     p->off_node = take(C * (sizeof(int64_t) + 2 * sizeof(double)));
     p->ws_bytes = off;
@@ -114,6 +118,8 @@ void fill_tables(dgfs_plan_s* p, std::vector<unsigned char>& blob, DevTables<T>&
     const size_t o_Uk = take(h.Uk.size() * sizeof(T));
     const size_t o_Vr = take(h.Vr.size() * sizeof(T));
     const size_t o_Lr = take(h.Lr.size() * sizeof(T));
+    const size_t o_GL0 = take(n3 * sizeof(T));
+    const size_t o_GLd = take(n3 * sizeof(T));
     const size_t o_W = take((size_t)N * N * 2 * sizeof(T));
     bytes = off;
     blob.assign(off, 0);
@@ -131,6 +137,20 @@ void fill_tables(dgfs_plan_s* p, std::vector<unsigned char>& blob, DevTables<T>&
     put(o_Uk, h.Uk);
     put(o_Vr, h.Vr);
     put(o_Lr, h.Lr);
+    {
+        // loss multiplier of the plan's kernel and its gamma-derivative, summed over r in FP64
+        std::vector<double> g0(n3, 0.0), gd(n3, 0.0);
+        for (int r = 0; r < h.Nrho; ++r) {
+            const double rho = 4.0 * 3.14159265358979323846 * h.b * std::pow(h.cr[r], h.gamma + 2.0);
+            const double lrho = std::log(h.cr[r]) * rho;
+            for (size_t i = 0; i < n3; ++i) {
+                g0[i] += rho * h.Lr[(size_t)r * n3 + i];
+                gd[i] += lrho * h.Lr[(size_t)r * n3 + i];
+            }
+        }
+        put(o_GL0, g0);
+        put(o_GLd, gd);
+    }
     {
         T* W = reinterpret_cast<T*>(blob.data() + o_W);
         const double tp = 2.0 * 3.14159265358979323846 / N;
@@ -153,8 +173,9 @@ void fill_tables(dgfs_plan_s* p, std::vector<unsigned char>& blob, DevTables<T>&
     t.Uk = reinterpret_cast<const T*>(o_Uk);
     t.Vr = reinterpret_cast<const T*>(o_Vr);
     t.Lr = reinterpret_cast<const T*>(o_Lr);
+    t.GL0 = reinterpret_cast<const T*>(o_GL0);
+    t.GLd = reinterpret_cast<const T*>(o_GLd);
     t.dftw = reinterpret_cast<const T*>(o_W);
-    (void)n3;
 }
 
 template <typename T>
@@ -163,7 +184,8 @@ void rebase(DevTables<T>& t, void* base) {
         using P = std::remove_reference_t<decltype(ptr)>;
         ptr = reinterpret_cast<P>(static_cast<unsigned char*>(base) + reinterpret_cast<uintptr_t>(ptr));
     };
-    fix(t.filt); fix(t.wsig); fix(t.cr); fix(t.wr); fix(t.Uk); fix(t.Vr); fix(t.Lr); fix(t.dftw);
+    fix(t.filt); fix(t.wsig); fix(t.cr); fix(t.wr); fix(t.Uk); fix(t.Vr); fix(t.Lr); fix(t.GL0); fix(t.GLd);
+    fix(t.dftw);
 }
 
 template <typename T> DevTables<T>& tables(dgfs_plan_s* p);
@@ -197,6 +219,10 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
         T* G = reinterpret_cast<T*>(ws(p, p->off_G));
         T* S = reinterpret_cast<T*>(ws(p, p->off_S));
         if (offs) return fail(DGFS_ERR_UNSUPPORTED, "vjp with node offsets");
+        if (p->prof) {
+            p->prof_launches += 20;
+            p->prof_nodes += nodes;
+        }
         e = launch_vjp_products(t, f, P, nodes, S, G, s);
         if (e) return cuda_fail(e, "vjp: translate-product kernel");
         // 3) loss: K_L f + i K_L (u f)
@@ -211,6 +237,12 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
     }
     // gain products: Q(f,f) and dQ/dgamma use (f, f); Q(f,g) uses (f, g); JVP uses (f, v)
     const T* gg = (op == Op::Collide || op == Op::Dgamma) ? nullptr : g;
+    if (p->prof) {
+        p->prof_launches += 11 + (op == Op::Jvp ? 1 : 0) + tc_extra_launches(p->prec);
+        p->prof_gain += 1;
+        p->prof_nodes += nodes;
+        if (p->prof_timed < (int64_t)p->ev.size() / 2) cudaEventRecord(p->ev[2 * p->prof_timed], s);
+    }
     if (is_tc(p->prec) && std::is_same<T, float>::value) {
         e = launch_tc_gain_products(p->tc, p->prec, reinterpret_cast<const float*>(f),
                                     reinterpret_cast<const float*>(gg), offs, nodes,
@@ -219,6 +251,10 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
         e = launch_gain_products(t, f, gg, offs, nodes, P, s);
     }
     if (e) return cuda_fail(e, "translate-product kernel");
+    if (p->prof && p->prof_timed < (int64_t)p->ev.size() / 2) {
+        cudaEventRecord(p->ev[2 * p->prof_timed + 1], s);
+        p->prof_timed += 1;
+    }
     e = launch_project<T>(t, P, np, nodes, X, xf, s);
     if (e) return cuda_fail(e, "radial projection");
     // loss operands: Q(f,g) -> g in slot rank;  JVP -> v in slot rank, f in slot rank+1
@@ -230,11 +266,12 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
     e = launch_dft3<T>(t, X, nodes * xf, true, s);
     if (e) return cuda_fail(e, "forward DFT");
     const T scale = op == Op::Jvp ? T(2) : T(1);
-    e = launch_combine<T>(t, X, xf, np, nodes, scale, rank, op == Op::Jvp ? rank + 1 : -1, Y, 2, s);
-    if (!e) e = launch_dft3<T>(t, Y, nodes * 2, false, s);
+    const int yf = op == Op::Jvp ? 3 : 2;
+    e = launch_combine<T>(t, X, xf, np, nodes, scale, rank, op == Op::Jvp ? rank + 1 : -1, Y, yf, s);
+    if (!e) e = launch_dft3<T>(t, Y, nodes * yf, false, s);
     if (e) return cuda_fail(e, "Fourier combine / inverse DFT");
-    // Q = Re Y0 - f Im Y0   (JVP: - v Re Y1 as well)
-    e = launch_finalize<T>(t.N, t.Nrho, Y, 2, f, op == Op::Jvp ? g : nullptr, nullptr, offs, nodes, 0,
+    // Q = gain - f (K_L g)   (JVP: 2 gain(f,v) - f K_L v - v K_L f)
+    e = launch_finalize<T>(t.N, t.Nrho, Y, yf, f, op == Op::Jvp ? g : nullptr, nullptr, offs, nodes, 0,
                            out, p->d_flags, s);
     if (e) return cuda_fail(e, "finalisation");
     return DGFS_OK;
@@ -374,6 +411,7 @@ dgfs_status dgfs_plan_destroy(dgfs_plan_t plan) {
     cudaFree(plan->d_tables);
     cudaFree(plan->d_ws);
     cudaFree(plan->d_flags);
+    for (auto& e : plan->ev) cudaEventDestroy(e);
     cudaSetDevice(cur);
     plan->magic = 0;
     delete plan;
@@ -515,6 +553,38 @@ dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host
                                   cudaMemcpyDeviceToHost, s), "device to host");
     }
     DGFS_CUDA(cudaStreamSynchronize(s), "stream synchronise");
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_profile_begin(dgfs_plan_t plan) {
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    if (plan->ev.empty()) {
+        plan->ev.resize(2 * 65536);
+        for (auto& e : plan->ev) DGFS_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+    }
+    plan->prof = true;
+    plan->prof_launches = plan->prof_gain = plan->prof_timed = plan->prof_nodes = 0;
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_profile_end(dgfs_plan_t plan, dgfs_profile_t* out) {
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    if (!out) return fail(DGFS_ERR_INVALID_ARG, "NULL output");
+    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    double ms = 0;
+    for (int64_t i = 0; i < plan->prof_timed; ++i) {
+        DGFS_CUDA(cudaEventSynchronize(plan->ev[2 * i + 1]), "cudaEventSynchronize");
+        float t = 0;
+        DGFS_CUDA(cudaEventElapsedTime(&t, plan->ev[2 * i], plan->ev[2 * i + 1]), "cudaEventElapsedTime");
+        ms += t;
+    }
+    out->launches = plan->prof_launches;
+    out->gain_launches = plan->prof_gain;
+    out->gain_timed = plan->prof_timed;
+    out->gain_ms = ms;
+    out->nodes = plan->prof_nodes;
+    plan->prof = false;
     return DGFS_OK;
 }
 

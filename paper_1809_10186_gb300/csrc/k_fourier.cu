@@ -28,6 +28,18 @@ __device__ __forceinline__ T radial_rho(double b, double gamma, double cr, int d
     return (T)v;
 }
 
+// Loss multiplier at index k of one node. The radial sum of oscillating sinc terms cancels
+// strongly at large |k|, so it is taken from the FP64-built table or accumulated in FP64.
+template <typename T>
+__device__ __forceinline__ T loss_multiplier(const T* __restrict__ GL0, const T* __restrict__ GLd,
+                                             const T* __restrict__ Lr, const double* __restrict__ rho,
+                                             bool per_node, int dlog, int Nrho, int64_t n3, int64_t k) {
+    if (!per_node) return dlog ? GLd[k] : GL0[k];
+    double g = 0.0;
+    for (int r = 0; r < Nrho; ++r) g = fma(rho[r], (double)Lr[r * n3 + k], g);
+    return (T)g;
+}
+
 // ---- dense DFT passes -----------------------------------------------------------------
 
 // Strided axis: data viewed as [outer][N][inner], tile [N][TI] of one outer index.
@@ -136,14 +148,16 @@ __global__ void k_load_field(int64_t n3, const T* __restrict__ a, const T* __res
 
 template <typename T>
 __global__ void k_combine(const Cplx<T>* __restrict__ X, int xfields, const T* __restrict__ Uk,
-                          const T* __restrict__ Lr, const double* __restrict__ cr, NodeParams np,
-                          int Nrho, int rank, int64_t n3, T scale, int ls0, int ls1,
-                          Cplx<T>* __restrict__ Y, int yfields) {
-    __shared__ T rho[64];
+                          const T* __restrict__ Lr, const T* __restrict__ GL0, const T* __restrict__ GLd,
+                          const double* __restrict__ cr, NodeParams np, int Nrho, int rank, int64_t n3,
+                          T scale, int ls0, int ls1, Cplx<T>* __restrict__ Y, int yfields) {
+    __shared__ double rho[64];
     const int64_t node = blockIdx.y;
+    const bool per_node = np.gamma || np.b;
     const double gam = np.gamma ? np.gamma[node] : np.gamma0;
     const double bb = np.b ? np.b[node] : np.b0;
-    for (int r = threadIdx.x; r < Nrho; r += blockDim.x) rho[r] = radial_rho<T>(bb, gam, cr[r], np.dlog);
+    if (per_node)
+        for (int r = threadIdx.x; r < Nrho; r += blockDim.x) rho[r] = radial_rho<double>(bb, gam, cr[r], np.dlog);
     __syncthreads();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n3) return;
@@ -155,36 +169,41 @@ __global__ void k_combine(const Cplx<T>* __restrict__ X, int xfields, const T* _
         gr = fma(u, v.x, gr);
         gi = fma(u, v.y, gi);
     }
-    T GL = 0;
-    for (int r = 0; r < Nrho; ++r) GL = fma(rho[r], Lr[r * n3 + k], GL);
-    const Cplx<T> l0 = Xn[ls0 * n3 + k];
-    // gain + i * loss multiplier applied to the loss operand: both are Hermitian, so the
-    // inverse transform returns gain in the real part and K_L g in the imaginary part
+    const T GL = loss_multiplier<T>(GL0, GLd, Lr, rho, per_node, np.dlog, Nrho, n3, k);
+    // the gain and each loss convolution get their own field: packing two real results of
+    // very different size into one complex transform would leak the rounding of the larger
+    // one (K_L g ~ n everywhere) into the smaller one (the gain, tiny in the tails)
     Cplx<T>* Yn = Y + node * (int64_t)yfields * n3;
-    Yn[k] = Cplx<T>{scale * gr - GL * l0.y, scale * gi + GL * l0.x};
+    Yn[k] = Cplx<T>{scale * gr, scale * gi};
+    const Cplx<T> l0 = Xn[ls0 * n3 + k];
+    Yn[n3 + k] = Cplx<T>{GL * l0.x, GL * l0.y};
     if (ls1 >= 0) {
         const Cplx<T> l1 = Xn[ls1 * n3 + k];
-        Yn[n3 + k] = Cplx<T>{GL * l1.x, GL * l1.y};
+        Yn[2 * n3 + k] = Cplx<T>{GL * l1.x, GL * l1.y};
     }
 }
 
 template <typename T>
 __global__ void k_loss_pair(const Cplx<T>* __restrict__ X, int xfields, const T* __restrict__ Lr,
+                            const T* __restrict__ GL0, const T* __restrict__ GLd,
                             const double* __restrict__ cr, NodeParams np, int Nrho, int64_t n3,
                             int s0, int s1, Cplx<T>* __restrict__ Y, int yfields) {
-    __shared__ T rho[64];
+    __shared__ double rho[64];
     const int64_t node = blockIdx.y;
+    const bool per_node = np.gamma || np.b;
     const double gam = np.gamma ? np.gamma[node] : np.gamma0;
     const double bb = np.b ? np.b[node] : np.b0;
-    for (int r = threadIdx.x; r < Nrho; r += blockDim.x) rho[r] = radial_rho<T>(bb, gam, cr[r], np.dlog);
+    if (per_node)
+        for (int r = threadIdx.x; r < Nrho; r += blockDim.x) rho[r] = radial_rho<double>(bb, gam, cr[r], np.dlog);
     __syncthreads();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n3) return;
-    T GL = 0;
-    for (int r = 0; r < Nrho; ++r) GL = fma(rho[r], Lr[r * n3 + k], GL);
+    const T GL = loss_multiplier<T>(GL0, GLd, Lr, rho, per_node, np.dlog, Nrho, n3, k);
     const Cplx<T>* Xn = X + node * (int64_t)xfields * n3;
     const Cplx<T> a = Xn[s0 * n3 + k], b = Xn[s1 * n3 + k];
-    Y[node * (int64_t)yfields * n3 + k] = Cplx<T>{GL * (a.x - b.y), GL * (a.y + b.x)};
+    Cplx<T>* Yn = Y + node * (int64_t)yfields * n3;
+    Yn[k] = Cplx<T>{GL * a.x, GL * a.y};
+    Yn[n3 + k] = Cplx<T>{GL * b.x, GL * b.y};
 }
 
 template <typename T>
@@ -239,16 +258,16 @@ __global__ void k_finalize(int Nrho, int64_t n3, const Cplx<T>* __restrict__ Y, 
     if (j >= n3) return;
     const int64_t base = offs ? offs[node] : node * n3;
     const Cplx<T>* Yn = Y + node * (int64_t)yfields * n3;
-    const Cplx<T> y0 = Yn[j];
+    const Cplx<T> y0 = Yn[j], y1 = Yn[n3 + j];
     T v;
     if (mode == 0) {
-        v = y0.x - a[base + j] * y0.y;
-        if (c) v -= c[base + j] * Yn[n3 + j].x;
+        v = y0.x - a[base + j] * y1.x;
+        if (c) v -= c[base + j] * Yn[2 * n3 + j].x;
     } else {
         v = T(0);
         const T* Gn = G + node * (int64_t)Nrho * n3;
         for (int r = 0; r < Nrho; ++r) v += Gn[r * n3 + j];
-        v -= a[base + j] * y0.x + y0.y;
+        v -= a[base + j] * y0.x + y1.x;
     }
     if (!isfinite(v)) atomicOr(flags, 2);
     out[base + j] = v;
@@ -314,7 +333,7 @@ cudaError_t launch_combine(const DevTables<T>& t, const Cplx<T>* X, int xfields,
                            cudaStream_t s) {
     if (nodes <= 0) return cudaSuccess;
     const int64_t n3 = (int64_t)t.N * t.N * t.N;
-    k_combine<T><<<dim3(blocks_for(n3, 256), (unsigned)nodes), 256, 0, s>>>(X, xfields, t.Uk, t.Lr, t.cr, np, t.Nrho, t.rank, n3, scale, ls0, ls1, Y, yfields);
+    k_combine<T><<<dim3(blocks_for(n3, 256), (unsigned)nodes), 256, 0, s>>>(X, xfields, t.Uk, t.Lr, t.GL0, t.GLd, t.cr, np, t.Nrho, t.rank, n3, scale, ls0, ls1, Y, yfields);
     return cudaGetLastError();
 }
 
@@ -323,7 +342,7 @@ cudaError_t launch_loss_pair(const DevTables<T>& t, const Cplx<T>* X, int xfield
                              int64_t nodes, int s0, int s1, Cplx<T>* Y, int yfields, cudaStream_t s) {
     if (nodes <= 0) return cudaSuccess;
     const int64_t n3 = (int64_t)t.N * t.N * t.N;
-    k_loss_pair<T><<<dim3(blocks_for(n3, 256), (unsigned)nodes), 256, 0, s>>>(X, xfields, t.Lr, t.cr, np, t.Nrho, n3, s0, s1, Y, yfields);
+    k_loss_pair<T><<<dim3(blocks_for(n3, 256), (unsigned)nodes), 256, 0, s>>>(X, xfields, t.Lr, t.GL0, t.GLd, t.cr, np, t.Nrho, n3, s0, s1, Y, yfields);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,8 @@ struct DevTables {
     const T* Uk;        // [rank][N^3]  DFT index order
     const T* Vr;        // [rank][Nrho]
     const T* Lr;        // [Nrho][N^3]  DFT index order
+    const T* GL0;       // [N^3] sum_r rho_r(gamma, b) Lr[r]: loss multiplier of the plan's kernel
+    const T* GLd;       // [N^3] sum_r ln(c_r) rho_r Lr[r]: its derivative with respect to gamma
     const T* dftw;      // [N][N] complex (re, im interleaved): e^{-2 pi i q j / N}
 };
 
@@ -63,8 +65,10 @@ template <typename T>
 cudaError_t launch_dft3(const DevTables<T>& t, Cplx<T>* X, int64_t count, bool forward,
                         cudaStream_t s);
 
-// Y[node][0] = scale * sum_s Uk[s] X[node][s] + i GL X[node][loss_slot0];
-// if loss_slot1 >= 0: Y[node][1] = GL X[node][loss_slot1]. GL = sum_r rho_r(node) Lr[r].
+// Y[node][0] = scale * sum_s Uk[s] X[node][s];  Y[node][1] = GL X[node][loss_slot0];
+// if loss_slot1 >= 0: Y[node][2] = GL X[node][loss_slot1]. GL = sum_r rho_r(node) Lr[r]: the
+// plan's FP64-built table when no per-node parameters are given, else summed in FP64 (the
+// radial sum cancels strongly at large |k|, so it is never accumulated in FP32).
 template <typename T>
 cudaError_t launch_combine(const DevTables<T>& t, const Cplx<T>* X, int xfields, NodeParams np,
                            int64_t nodes, T scale, int loss_slot0, int loss_slot1, Cplx<T>* Y,
@@ -80,14 +84,14 @@ template <typename T>
 cudaError_t launch_multiply_uk(const DevTables<T>& t, Cplx<T>* X, int xfields, int src_slot,
                                int64_t nodes, cudaStream_t s);
 
-// Y[node][0] = GL X[node][slot0] + i GL X[node][slot1]
+// Y[node][0] = GL X[node][slot0];  Y[node][1] = GL X[node][slot1]
 template <typename T>
 cudaError_t launch_loss_pair(const DevTables<T>& t, const Cplx<T>* X, int xfields, NodeParams np,
                              int64_t nodes, int slot0, int slot1, Cplx<T>* Y, int yfields,
                              cudaStream_t s);
 
-// out = Re Y0 - a * Im Y0 - (c ? c * Re Y1 : 0)       (mode 0)
-// out = sum_r G[node][r] - u * Re Y0 - Im Y0            (mode 1, VJP)
+// out = Re Y0 - a * Re Y1 - (c ? c * Re Y2 : 0)       (mode 0)
+// out = sum_r G[node][r] - a * Re Y0 - Re Y1            (mode 1, VJP; a = u)
 template <typename T>
 cudaError_t launch_finalize(int N, int Nrho, const Cplx<T>* Y, int yfields, const T* a,
                             const T* c, const T* G, const int64_t* offs, int64_t nodes, int mode,

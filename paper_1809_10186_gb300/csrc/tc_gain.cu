@@ -6,6 +6,8 @@ namespace dgfs {
 
 bool tc_supported(int) { return false; }
 
+int tc_extra_launches(int) { return 0; }
+
 size_t build_tc_tables(const HostPlan&, int, std::vector<unsigned char>& blob, TcTables&) {
     blob.clear();
     return 0;

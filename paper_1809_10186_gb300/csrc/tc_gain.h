@@ -17,6 +17,7 @@ struct TcTables {
 };
 
 bool tc_supported(int N);
+int tc_extra_launches(int prec);   // launches the tensor-core path adds per chunk (beyond one)
 size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>& blob, TcTables& t);
 void rebase_tc_tables(TcTables& t, void* base);
 cudaError_t launch_tc_gain_products(const TcTables& t, int prec, const float* f, const float* g,
