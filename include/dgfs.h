@@ -56,12 +56,12 @@ typedef enum {
 } dgfs_status;
 
 typedef enum {
-    DGFS_PREC_FP64 = 0,   /* CUDA-core FP64 everywhere (reference-accuracy mode)               */
-    DGFS_PREC_FP32 = 1,   /* CUDA-core FP32 everywhere                                          */
-    DGFS_PREC_BF16X3 = 2, /* translates on tcgen05 tensor cores: bf16 hi/lo split operands,
-                             three products (hi*hi + hi*lo + lo*hi), FP32 accumulation          */
-    DGFS_PREC_F16X3 = 3,  /* as BF16X3 with fp16 hi/lo operands (per-node power-of-two scaling) */
-    DGFS_PREC_F16 = 4     /* tensor-core translates, single fp16 product, FP32 accumulation     */
+    DGFS_PREC_FP64 = 0,   /* CUDA-core FP64 everywhere (reference-accuracy mode; N <= 24)          */
+    DGFS_PREC_FP32 = 1,   /* CUDA-core FP32 everywhere                                              */
+    DGFS_PREC_F16S = 2,   /* translates on tcgen05 tensor cores: fp16 data operands with a per-node
+                             power-of-two scale, every filter split into fp16 hi + lo parts (two
+                             products), FP32 accumulation in tensor memory; FP32 elsewhere. N = 16, 32 */
+    DGFS_PREC_BF16S = 3   /* as F16S with bf16 operands (no scaling)                                 */
 } dgfs_precision;
 
 typedef enum {
@@ -74,7 +74,7 @@ typedef enum {
 } dgfs_loss_mode;
 
 typedef struct {
-    int N;                     /* grid points per velocity axis: even, 8 <= N <= 32            */
+    int N;                     /* grid points per velocity axis: 8, 16, 24 or 32                */
     double L;                  /* velocity domain [-L, L]^3 (Sec. 3.3), L > 0                   */
     double R;                  /* ball radius of the c_r integral; <= 0: 4L/(3+sqrt 2) (Appendix) */
     double gamma;              /* VHS exponent 2(1 - omega) of |c - c_*| (eq. B_gen)            */

@@ -16,6 +16,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -75,7 +76,7 @@ struct dgfs_plan_s {
 
 namespace {
 
-bool is_tc(int prec) { return prec == DGFS_PREC_BF16X3 || prec == DGFS_PREC_F16X3 || prec == DGFS_PREC_F16; }
+bool is_tc(int prec) { return prec == DGFS_PREC_F16S || prec == DGFS_PREC_BF16S; }
 
 size_t elem_size(int prec) { return prec == DGFS_PREC_FP64 ? 8 : 4; }
 
@@ -243,7 +244,7 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
         p->prof_nodes += nodes;
         if (p->prof_timed < (int64_t)p->ev.size() / 2) cudaEventRecord(p->ev[2 * p->prof_timed], s);
     }
-    if (is_tc(p->prec) && std::is_same<T, float>::value) {
+    if (is_tc(p->prec) && std::is_same<T, float>::value && gg == nullptr) {
         e = launch_tc_gain_products(p->tc, p->prec, reinterpret_cast<const float*>(f),
                                     reinterpret_cast<const float*>(gg), offs, nodes,
                                     reinterpret_cast<float*>(P), p->d_flags, s);
@@ -304,8 +305,6 @@ dgfs_status compute(dgfs_plan_t plan, Op op, const void* f, const void* g, void*
         return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
     if (out == f || (g && out == g)) return fail(DGFS_ERR_INVALID_ARG, "output aliases an input");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (op == Op::Vjp && is_tc(plan->prec))
-        ; // the adjoint runs on CUDA cores in FP32 for every 16-bit plan
     return plan->prec == DGFS_PREC_FP64 ? run<double>(plan, op, f, g, out, B, s)
                                         : run<float>(plan, op, f, g, out, B, s);
 }
@@ -340,7 +339,7 @@ dgfs_status dgfs_plan_desc_init(dgfs_plan_desc* d) {
 dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) {
     if (!desc || !plan_out) return fail(DGFS_ERR_INVALID_ARG, "NULL argument");
     *plan_out = nullptr;
-    if (desc->precision < DGFS_PREC_FP64 || desc->precision > DGFS_PREC_F16)
+    if (desc->precision < DGFS_PREC_FP64 || desc->precision > DGFS_PREC_BF16S)
         return fail(DGFS_ERR_INVALID_ARG, "unknown precision");
     std::unique_ptr<dgfs_plan_s> p(new (std::nothrow) dgfs_plan_s);
     if (!p) return fail(DGFS_ERR_OOM, "host allocation failed");
@@ -351,7 +350,7 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
     if (p->prec == DGFS_PREC_FP64 && p->hp.N > 24)
         return fail(DGFS_ERR_UNSUPPORTED, "FP64 plans support N <= 24");
     if (is_tc(p->prec) && !tc_supported(p->hp.N))
-        return fail(DGFS_ERR_UNSUPPORTED, "tensor-core precisions support N = 16, 32");
+        return fail(DGFS_ERR_UNSUPPORTED, "tensor-core precisions support N = 16 and 32");
     DGFS_CUDA(cudaGetDevice(&p->device), "cudaGetDevice");
     // chunk: about 1.5 GB of workspace
     {
@@ -454,8 +453,6 @@ dgfs_status dgfs_collide_jvp(dgfs_plan_t plan, const void* f, const void* v, voi
 
 dgfs_status dgfs_collide_vjp(dgfs_plan_t plan, const void* f, const void* u, void* gf, int64_t B,
                              void* stream) {
-    if (check_plan(plan) && is_tc(plan->prec))
-        return fail(DGFS_ERR_UNSUPPORTED, "the adjoint needs an FP32 or FP64 plan");
     return compute(plan, Op::Vjp, f, u, gf, B, stream, true);
 }
 

@@ -104,32 +104,51 @@ __global__ void k_dft_contig(Cplx<T>* __restrict__ X, const Cplx<T>* __restrict_
 
 // ---- projections and multipliers ----------------------------------------------------------
 
-// X[node][s][j] = sum_r C[s][r] P[node][r][j],  C[s][r] = Vr[s][r] w_r rho_r(node)
+// X[node][s][j] = sum_r C[s][r] P[node][r][j],  C[s][r] = Vr[s][r] w_r rho_r(node).
+// Each thread owns 4 consecutive j and accumulates 8 outputs s at a time from register-held
+// P values, with the coefficients broadcast from shared memory (stored [r][s]).
 template <typename T>
 __global__ void k_project(const T* __restrict__ P, const T* __restrict__ Vr,
                           const double* __restrict__ cr, const double* __restrict__ wr,
                           NodeParams np, int Nrho, int rank, int64_t n3, Cplx<T>* __restrict__ X,
                           int xfields) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    T* C = reinterpret_cast<T*>(sm_raw);                  // [rank][Nrho]
-    T* Pt = C + rank * Nrho;                               // [Nrho][blockDim]
+    T* CT = reinterpret_cast<T*>(sm_raw);                 // [Nrho][rank8]
+    const int rank8 = (rank + 7) & ~7;
     const int64_t node = blockIdx.y;
     const double gam = np.gamma ? np.gamma[node] : np.gamma0;
     const double bb = np.b ? np.b[node] : np.b0;
-    for (int e = threadIdx.x; e < rank * Nrho; e += blockDim.x) {
-        const int r = e % Nrho;
-        C[e] = Vr[e] * (T)wr[r] * radial_rho<T>(bb, gam, cr[r], np.dlog);
+    for (int e = threadIdx.x; e < Nrho * rank8; e += blockDim.x) {
+        const int r = e / rank8, sidx = e % rank8;
+        CT[e] = sidx < rank ? Vr[sidx * Nrho + r] * (T)wr[r] * radial_rho<T>(bb, gam, cr[r], np.dlog) : T(0);
     }
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const T* Pn = P + node * Nrho * n3;
-    for (int r = 0; r < Nrho; ++r) Pt[r * blockDim.x + threadIdx.x] = j < n3 ? Pn[r * n3 + j] : T(0);
     __syncthreads();
-    if (j >= n3) return;
-    Cplx<T>* Xn = X + node * (int64_t)xfields * n3;
-    for (int s = 0; s < rank; ++s) {
-        T acc = 0;
-        for (int r = 0; r < Nrho; ++r) acc = fma(C[s * Nrho + r], Pt[r * blockDim.x + threadIdx.x], acc);
-        Xn[s * n3 + j] = Cplx<T>{acc, T(0)};
+    const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (j0 >= n3) return;
+    const T* Pn = P + node * Nrho * n3 + j0;
+    Cplx<T>* Xn = X + node * (int64_t)xfields * n3 + j0;
+    for (int s0 = 0; s0 < rank; s0 += 8) {
+        T acc[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[i][v] = T(0);
+        for (int r = 0; r < Nrho; ++r) {
+            T pv[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) pv[v] = Pn[(int64_t)r * n3 + v];
+            const T* c = CT + r * rank8 + s0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[i][v] = fma(c[i], pv[v], acc[i][v]);
+        }
+        const int ns = rank - s0 < 8 ? rank - s0 : 8;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (i < ns)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) Xn[(int64_t)(s0 + i) * n3 + v] = Cplx<T>{acc[i][v], T(0)};
     }
 }
 
@@ -310,11 +329,11 @@ template <typename T>
 cudaError_t launch_project(const DevTables<T>& t, const T* P, NodeParams np, int64_t nodes,
                            Cplx<T>* X, int xfields, cudaStream_t s) {
     if (nodes <= 0) return cudaSuccess;
-    const int64_t n3 = (int64_t)t.N * t.N * t.N;
+    const int64_t n3 = (int64_t)t.N * t.N * t.N;      // a multiple of 4 for every supported N
     const int bs = 128;
-    const size_t sm = sizeof(T) * (size_t)(t.rank * t.Nrho + t.Nrho * bs);
+    const size_t sm = sizeof(T) * (size_t)(t.Nrho * ((t.rank + 7) & ~7));
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_project<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_project<T><<<dim3(blocks_for(n3, bs), (unsigned)nodes), bs, sm, s>>>(P, t.Vr, t.cr, t.wr, np, t.Nrho, t.rank, n3, X, xfields);
+    k_project<T><<<dim3(blocks_for(n3 / 4, bs), (unsigned)nodes), bs, sm, s>>>(P, t.Vr, t.cr, t.wr, np, t.Nrho, t.rank, n3, X, xfields);
     return cudaGetLastError();
 }
 

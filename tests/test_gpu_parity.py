@@ -4,7 +4,7 @@ Error measure: relative L2 error of Q against the oracle, normalised by the orac
 term ||Q-|| (the magnitude of the quantities the kernels add up; gain and loss nearly cancel,
 so ||Q|| can be a few percent of it). The error normalised by ||Q|| is printed as well.
 Tolerances per precision (derived in the design notes from the unit round-off and the
-length of the sums): FP64 1e-10, FP32 1e-5.
+length of the sums): FP64 1e-10, FP32 1e-5, F16S 1e-3, BF16S 3e-3.
 """
 import math
 
@@ -17,7 +17,10 @@ from paper_1809_10186_gb300 import binding, workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 1e-5}
+# 16-bit modes: data operands rounded to 16 bits between passes. fp16 (11-bit significand,
+# unit round-off 2^-11): observed <= 2e-4; bf16 (8-bit significand, 2^-8): observed <= 1.1e-3,
+# i.e. about 8x more, as the significands predict.
+TOL = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-3, "bf16s": 3e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -29,11 +32,13 @@ def built():
 
 
 def _dev(a, prec):
+    prec = "fp32" if prec in ("f16s", "bf16s") else prec
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", torch.float64 if prec == "fp64" else torch.float32)
 
 
 def _as_input(a, prec):
     """The values both sides see: rounded to the GPU element type, then FP64 for the oracle."""
+    prec = "fp32" if prec in ("f16s", "bf16s") else prec
     return a.astype(np.float64) if prec == "fp64" else a.astype(np.float32).astype(np.float64)
 
 
@@ -313,3 +318,41 @@ def test_autograd_function():
     op = O.OraclePlan(N, L, gamma=0.52, M=12, Nrho=6, nyquist="sym")
     ref = O.vjp(op, F[0], u[0].cpu().numpy())
     assert np.linalg.norm(g[0].cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-10
+
+
+# ---- tensor-core (tcgen05) translates ---------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["f16s", "bf16s"])
+@pytest.mark.parametrize("N,kind", [(16, "rough"), (16, "smooth"), (32, "smooth"), (32, "rough")])
+def test_tensor_core_collide(prec, N, kind):
+    L, gamma, M = (3.0 if kind == "rough" else 6.0), 0.52, 12
+    F = W.rough(3, N, 300 + N) if kind == "rough" else W.two_maxwellian(3, N, L, 301 + N)[0]
+    F = _as_input(F, "fp32")
+    plan = binding.Plan(N=N, L=L, gamma=gamma, M=M, N_rho=N, precision=prec)
+    q = plan.collide(_dev(F, "fp32")).double().cpu().numpy()
+    plan.stream_status()
+    op = _oplan(N, L, gamma, M, N)
+    for i in range(3):
+        ref = O.fast_Q(op, F[i])
+        e_loss, e_q = _errors(q[i], ref, np.real(O.loss_Q(op, F[i], F[i])))
+        print(prec, N, kind, i, "err/|Q-| %.3g  err/|Q| %.3g" % (e_loss, e_q))
+        assert e_loss < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f16s", "bf16s"])
+def test_tensor_core_vhs_n32_full_batch_sampled(prec):
+    """The primary workload's launch (2048 nodes, N = 32, M = 38, SVD 1e-8) on tensor cores."""
+    worst, plan = _vhs32("vhs_n32", prec, 4)
+    print("N=32", prec, "rank %d worst err/|Q-| %.3g err/|Q| %.3g" % (plan.info["svd_rank_used"], *worst))
+    assert worst[0] < TOL[prec]
+
+
+def test_tensor_core_chunking_and_determinism():
+    N, L = 32, 7.0
+    F, _ = W.two_maxwellian(5, N, L, 13, dtype=np.float32)
+    f = _dev(F, "fp32")
+    p1 = binding.Plan(N=N, L=L, gamma=0.52, M=38, N_rho=N, precision="f16s")
+    p2 = binding.Plan(N=N, L=L, gamma=0.52, M=38, N_rho=N, precision="f16s", max_batch=2)
+    a = p1.collide(f)
+    assert torch.equal(a, p1.collide(f))
+    assert torch.equal(a, p2.collide(f))
