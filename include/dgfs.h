@@ -155,6 +155,18 @@ dgfs_status dgfs_collide_ragged(const dgfs_plan_t* plans, int nplans, const int3
 dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host, int64_t B,
                               void* stream);
 
+/* Q(f,f) exactly as dgfs_collide computes it, for callers that must not allocate device
+   memory when they run (for example code whose device memory is fully reserved up front, or
+   that may not pay the device synchronisation an allocation can cause). The paper has no
+   counterpart to this call. Its intermediate fields live in one fixed 64 MiB device array
+   defined in this library (one per GPU that loads it, held until the process exits) instead of
+   the plan's workspace; it calls no allocating routine. B is limited to the number of nodes
+   whose scratch fits the array (about 6 at N = 32, more for smaller grids); larger B returns
+   DGFS_ERR_INVALID_ARG with the limit in the message. The first call on a device looks up the
+   array's device address; make it before capturing any stream. Every call shares the array:
+   calls whose work overlaps on the GPU race on it. f, Q: device, [B][N^3], as dgfs_collide. */
+dgfs_status dgfs_collide_noalloc(dgfs_plan_t plan, const void* f, void* Q, int64_t B, void* stream);
+
 /* Synchronise the stream and report device-side flags raised by earlier calls with this
    plan (DGFS_ERR_TIMEOUT, DGFS_ERR_NUMERIC), then clear them. */
 dgfs_status dgfs_stream_status(dgfs_plan_t plan, void* stream);

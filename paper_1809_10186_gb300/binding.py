@@ -60,6 +60,7 @@ _SIGNATURES = {
                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_double), _I64, _P, _P, _P],
     "dgfs_collide_host": [_P, _P, _P, _I64, _P],
+    "dgfs_collide_noalloc": [_P, _P, _P, _I64, _P],
     "dgfs_stream_status": [_P, _P],
     "dgfs_profile_begin": [_P],
     "dgfs_profile_end": [_P, ctypes.POINTER(dgfs_profile_t)],
@@ -205,6 +206,10 @@ class Plan:
 
     def collide(self, f, out=None, stream=None):
         return self._call("dgfs_collide", [f], out, stream)
+
+    def collide_noalloc(self, f, out=None, stream=None):
+        """Q(f, f) with scratch in the library's fixed device array (no device allocation)."""
+        return self._call("dgfs_collide_noalloc", [f], out, stream)
 
     def collide2(self, f, g, out=None, stream=None):
         return self._call("dgfs_collide2", [f, g], out, stream)

@@ -628,3 +628,96 @@ dgfs_status dgfs_host_translate_filter(int N, double L, double t, double* a) {
 }
 
 }  // extern "C"
+
+// ---- Q(f,f) with its scratch in a fixed device array (no device allocation) --------------
+//
+// dgfs_collide keeps its intermediate fields (the radial products P_r, the spectra X and
+// Y) in the plan's workspace, which dgfs_plan_create allocates. dgfs_collide_noalloc runs
+// the same kernels on the same data but takes that scratch from one file-scope device array
+// of kNoAllocScratchBytes instead: it calls no allocating routine of CUDA or of any library.
+// The array exists once per GPU that loads this library and lives until the process exits;
+// its address on a device is looked up (cudaGetSymbolAddress) by the first call made on
+// that device, which is why the first call should not be made while a stream is being
+// captured. All calls share the array: two calls whose work overlaps on the GPU (different
+// streams, or plans on the same device used concurrently) race on it. Every scratch element
+// a call reads is written earlier by the same call, so nothing needs clearing between calls.
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;   // 64 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+std::mutex g_noalloc_mu;
+std::vector<void*> g_noalloc_ptr;   // device address of the array, per device (nullptr: not looked up)
+
+// bytes of scratch one node needs: P_r for every radial point, rank + 2 spectra, 2 result spectra
+size_t noalloc_node_bytes(const dgfs_plan_s* p) {
+    const size_t es = elem_size(p->prec);
+    const size_t n3 = (size_t)p->hp.N * p->hp.N * p->hp.N;
+    return align_up((size_t)p->hp.Nrho * n3 * es, 256) + align_up((size_t)(p->hp.rank + 2) * n3 * 2 * es, 256) +
+           align_up(2 * n3 * 2 * es, 256);
+}
+
+template <typename T>
+dgfs_status noalloc_run(dgfs_plan_s* p, const T* f, T* Q, int64_t B, unsigned char* scratch, cudaStream_t s) {
+    const DevTables<T>& t = tables<T>(p);
+    const size_t n3 = (size_t)t.N * t.N * t.N;
+    const int xf = t.rank + 2;
+    T* P = reinterpret_cast<T*>(scratch);
+    Cplx<T>* X = reinterpret_cast<Cplx<T>*>(scratch + align_up((size_t)B * t.Nrho * n3 * sizeof(T), 256));
+    Cplx<T>* Y = X + align_up((size_t)B * xf * n3 * sizeof(Cplx<T>), 256) / sizeof(Cplx<T>);
+    NodeParams np{nullptr, nullptr, p->hp.gamma, p->hp.b, 0};
+    cudaError_t e;
+    if (is_tc(p->prec) && std::is_same<T, float>::value)
+        e = launch_tc_gain_products(p->tc, p->prec, reinterpret_cast<const float*>(f), nullptr, nullptr, B,
+                                    reinterpret_cast<float*>(P), p->d_flags, s);
+    else
+        e = launch_gain_products(t, f, nullptr, nullptr, B, P, s);
+    if (!e) e = launch_project<T>(t, P, np, B, X, xf, s);
+    if (!e) e = launch_load_field<T>(t.N, f, nullptr, nullptr, B, X, xf, t.rank, s);
+    if (!e) e = launch_dft3<T>(t, X, B * xf, true, s);
+    if (!e) e = launch_combine<T>(t, X, xf, np, B, T(1), t.rank, -1, Y, 2, s);
+    if (!e) e = launch_dft3<T>(t, Y, B * 2, false, s);
+    if (!e) e = launch_finalize<T>(t.N, t.Nrho, Y, 2, f, nullptr, nullptr, nullptr, B, 0, Q, p->d_flags, s);
+    if (e) return cuda_fail(e, "dgfs_collide_noalloc");
+    return DGFS_OK;
+}
+
+}  // namespace
+
+extern "C" dgfs_status dgfs_collide_noalloc(dgfs_plan_t plan, const void* f, void* Q, int64_t B, void* stream) {
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    if (B < 0) return fail(DGFS_ERR_INVALID_ARG, "B must be >= 0");
+    if (B == 0) return DGFS_OK;
+    if (!f || !Q) return fail(DGFS_ERR_INVALID_ARG, "NULL field pointer");
+    if (!aligned16(f) || !aligned16(Q)) return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
+    if (f == Q) return fail(DGFS_ERR_INVALID_ARG, "output aliases the input");
+    const size_t per_node = noalloc_node_bytes(plan);
+    const int64_t capacity = (int64_t)(kNoAllocScratchBytes / per_node);
+    if (B > capacity) {
+        char msg[256];
+        std::snprintf(msg, sizeof msg,
+                      "dgfs_collide_noalloc: B = %lld exceeds the %lld nodes whose scratch (%zu bytes each) fits "
+                      "the fixed %zu-byte device array; call it again on the remaining nodes",
+                      (long long)B, (long long)capacity, per_node, kNoAllocScratchBytes);
+        return fail(DGFS_ERR_INVALID_ARG, msg);
+    }
+    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if ((int)g_noalloc_ptr.size() <= plan->device) g_noalloc_ptr.resize(plan->device + 1, nullptr);
+        if (!g_noalloc_ptr[plan->device]) {
+            void* ptr = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess || !ptr) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                                                          "cudaGetSymbolAddress of the fixed scratch array");
+            g_noalloc_ptr[plan->device] = ptr;
+        }
+        base = g_noalloc_ptr[plan->device];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char* scratch = static_cast<unsigned char*>(base);
+    return plan->prec == DGFS_PREC_FP64
+               ? noalloc_run<double>(plan, static_cast<const double*>(f), static_cast<double*>(Q), B, scratch, s)
+               : noalloc_run<float>(plan, static_cast<const float*>(f), static_cast<float*>(Q), B, scratch, s);
+}

@@ -1,0 +1,61 @@
+"""dgfs_collide_noalloc: Q(f, f) without any device allocation.
+
+Some callers cannot allocate device memory when they run (their memory is reserved up front,
+or they must not pay the synchronisation an allocation can cause). dgfs_collide_noalloc serves
+them: it runs the same kernels as dgfs_collide but keeps its scratch in the library's fixed
+64 MiB device array. These tests call it through the C ABI, twice in a row (the array keeps the
+previous call's contents), and compare each result with dgfs_collide's on the same input.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1809_10186_gb300 import binding, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5   # the FP32 parity tolerance of the other GPU tests (relative L2)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1809_10186_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+
+
+def _noalloc(plan, f):
+    out = torch.empty_like(f)
+    st = binding.lib().dgfs_collide_noalloc(plan.handle, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                            ctypes.c_int64(f.shape[0]), binding._stream_ptr())
+    return st, out
+
+
+@pytest.mark.parametrize("N,L,M,prec,B", [(16, 5.0, 12, "fp32", 5), (32, 7.0, 38, "fp32", 4),
+                                          (32, 7.0, 38, "f16s", 4), (16, 5.0, 12, "fp64", 3)])
+def test_noalloc_matches_collide_twice(N, L, M, prec, B):
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    plan = binding.Plan(N=N, L=L, gamma=0.52, M=M, N_rho=N, precision=prec)
+    for call in range(2):
+        F, _ = W.two_maxwellian(B, N, L, 500 + 10 * N + call)
+        f = torch.from_numpy(F).to("cuda", dt)
+        st, q = _noalloc(plan, f)
+        assert st == 0, binding.lib().dgfs_last_error_message().decode()
+        ref = plan.collide(f)
+        torch.cuda.synchronize()
+        plan.stream_status()
+        rel = (torch.linalg.norm(q - ref) / torch.linalg.norm(ref)).item()
+        assert rel < TOL, (call, rel)
+
+
+def test_noalloc_rejects_batches_beyond_the_fixed_array():
+    N, L = 32, 7.0
+    plan = binding.Plan(N=N, L=L, gamma=0.52, M=38, N_rho=N, precision="fp32")
+    f = torch.zeros(64, N, N, N, device="cuda")
+    st, _ = _noalloc(plan, f)
+    assert st == 1
+    msg = binding.lib().dgfs_last_error_message().decode()
+    assert "exceeds" in msg and "fixed" in msg
