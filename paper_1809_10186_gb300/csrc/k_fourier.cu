@@ -102,6 +102,98 @@ __global__ void k_dft_contig(Cplx<T>* __restrict__ X, const Cplx<T>* __restrict_
     }
 }
 
+// ---- radix-2 FFT passes (power-of-two N) -------------------------------------------------
+//
+// One thread transforms one line of N complex values held in registers: decimation in time
+// on bit-reversed input, N/2 log2 N butterflies, twiddles e^{-+2 pi i j / N} taken from the
+// plan's DFT table (row 1) through shared memory. Same result as the dense passes, in
+// 5 N log2 N instead of 8 N^2 flops per line.
+
+template <int N>
+__device__ __forceinline__ constexpr int bitrev(int i) {
+    int r = 0;
+    for (int b = 1, k = N >> 1; b < N; b <<= 1, k >>= 1)
+        if (i & b) r |= k;
+    return r;
+}
+
+// In-place butterflies; the caller loads element k of the line into a[bitrev(k)].
+template <typename T, int N>
+__device__ __forceinline__ void fft_line(Cplx<T> (&a)[N], const Cplx<T>* __restrict__ tw, bool forward) {
+#pragma unroll
+    for (int len = 2; len <= N; len <<= 1) {
+        const int half = len >> 1, step = N / len;
+#pragma unroll
+        for (int i = 0; i < N; i += len)
+#pragma unroll
+            for (int j = 0; j < half; ++j) {
+                const Cplx<T> w = tw[j * step];
+                const T wi = forward ? w.y : -w.y;
+                const Cplx<T> u = a[i + j], v0 = a[i + j + half];
+                const Cplx<T> v{v0.x * w.x - v0.y * wi, v0.x * wi + v0.y * w.x};
+                a[i + j] = Cplx<T>{u.x + v.x, u.y + v.y};
+                a[i + j + half] = Cplx<T>{u.x - v.x, u.y - v.y};
+            }
+    }
+}
+
+// Strided axes: line l of the field group starts at base(l) and has stride S; consecutive
+// threads take consecutive lines whose elements are adjacent in memory (coalesced).
+template <typename T, int N>
+__global__ void __launch_bounds__(128)
+k_fft_strided(Cplx<T>* __restrict__ X, const Cplx<T>* __restrict__ W, int64_t lines, int64_t inner,
+              int64_t stride, int forward, T scale) {
+    __shared__ Cplx<T> tw[N];
+    if (threadIdx.x < N) tw[threadIdx.x] = W[N + threadIdx.x];      // row q = 1 of the DFT table
+    __syncthreads();
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= lines) return;
+    // line l = (outer o, inner i): base = o * N * stride + i   (inner < stride)
+    const int64_t o = l / inner, i = l % inner;
+    Cplx<T>* base = X + o * (int64_t)N * stride + i;
+    Cplx<T> a[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) a[bitrev<N>(k)] = base[(int64_t)k * stride];
+    fft_line<T, N>(a, tw, forward != 0);
+#pragma unroll
+    for (int k = 0; k < N; ++k) base[(int64_t)k * stride] = Cplx<T>{a[k].x * scale, a[k].y * scale};
+}
+
+// Contiguous axis: 128 lines staged through shared memory so global accesses stay coalesced.
+template <typename T, int N>
+__global__ void __launch_bounds__(128)
+k_fft_contig(Cplx<T>* __restrict__ X, const Cplx<T>* __restrict__ W, int64_t lines, int forward, T scale) {
+    __shared__ Cplx<T> tw[N];
+    __shared__ Cplx<T> tile[128 * (N + 1)];
+    if (threadIdx.x < N) tw[threadIdx.x] = W[N + threadIdx.x];
+    const int64_t l0 = (int64_t)blockIdx.x * 128;
+    const int nl = (int)((lines - l0) < 128 ? (lines - l0) : 128);
+    Cplx<T>* base = X + l0 * N;
+    for (int e = threadIdx.x; e < nl * N; e += 128) tile[(e / N) * (N + 1) + e % N] = base[e];
+    __syncthreads();
+    if (threadIdx.x < nl) {
+        Cplx<T> a[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) a[bitrev<N>(k)] = tile[threadIdx.x * (N + 1) + k];
+        fft_line<T, N>(a, tw, forward != 0);
+#pragma unroll
+        for (int k = 0; k < N; ++k) tile[threadIdx.x * (N + 1) + k] = Cplx<T>{a[k].x * scale, a[k].y * scale};
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nl * N; e += 128) base[e] = tile[(e / N) * (N + 1) + e % N];
+}
+
+template <typename T, int N>
+cudaError_t fft3(Cplx<T>* X, const Cplx<T>* W, int64_t count, bool forward, T scale, cudaStream_t s) {
+    const int64_t n2 = (int64_t)N * N;
+    const int64_t lines = count * n2;
+    const unsigned blocks = (unsigned)((lines + 127) / 128);
+    k_fft_strided<T, N><<<blocks, 128, 0, s>>>(X, W, lines, n2, n2, forward, scale);   // axis x
+    k_fft_strided<T, N><<<blocks, 128, 0, s>>>(X, W, lines, N, N, forward, scale);     // axis y
+    k_fft_contig<T, N><<<blocks, 128, 0, s>>>(X, W, lines, forward, scale);            // axis z
+    return cudaGetLastError();
+}
+
 // ---- projections and multipliers ----------------------------------------------------------
 
 // X[node][s][j] = sum_r C[s][r] P[node][r][j],  C[s][r] = Vr[s][r] w_r rho_r(node).
@@ -303,6 +395,10 @@ cudaError_t launch_dft3(const DevTables<T>& t, Cplx<T>* X, int64_t count, bool f
     const int64_t n2 = (int64_t)N * N;
     const T scale = forward ? T(1) / T(N) : T(1);
     const Cplx<T>* W = reinterpret_cast<const Cplx<T>*>(t.dftw);
+    if (N == 8) return fft3<T, 8>(X, W, count, forward, scale, s);
+    if (N == 16) return fft3<T, 16>(X, W, count, forward, scale, s);
+    if constexpr (sizeof(T) == 4)                       // FP64 plans stop at N = 24
+        if (N == 32) return fft3<T, 32>(X, W, count, forward, scale, s);
     constexpr int TI = 32;
     const size_t sm_s = sizeof(Cplx<T>) * (size_t)(N * N + N * TI);
     // axis x: [count][N][N^2]
