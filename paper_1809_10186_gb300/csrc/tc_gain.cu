@@ -17,9 +17,11 @@
 // The - filter is the transpose of the + filter (T_-s = T_s^T): the same shared-memory matrix
 // is read as an MN-major operand.
 //
-// One CTA of 256 threads per (radial point, node); thread 0 issues the MMAs; every wait on an
-// mbarrier is bounded: on timeout the kernel raises flag bit 0, drains its own MMAs and copies
-// (bounded), frees TMEM and returns without writing P.
+// One CTA of 288 threads per (radial point, node), warp-specialised: one warp issues the MMAs
+// and copies, two warpgroups convert accumulator tiles into the next pass's operands and form
+// the products; all hand-offs are mbarriers. Every wait is bounded: on timeout the CTA raises
+// flag bit 0, every role stops, the MMAs and copies in flight are drained (bounded), TMEM is
+// freed and P is not written.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -44,7 +46,8 @@ struct Geo {
     static constexpr int ZT = 128 / N;         // z values per pass-1/2 tile
     static constexpr int KSTEPS = N / 16;      // K = 16 steps of one contraction
     static constexpr int KG = N / 8;           // core-matrix groups along K
-    static constexpr int HALF = N / 2;         // TMEM columns read per thread
+    static constexpr int HALF = N / 2;         // columns of the product per warpgroup
+    static constexpr int ND1 = 3, ND2 = 2, ND3 = 2;   // TMEM buffers of passes 1, 2, 3 (- sign)
     // A1 = f, K-major: rows m1 = z*N + y, k = x
     static constexpr uint32_t A1_LBO = 128, A1_SBO = 16 * N;
     static constexpr uint32_t A1_TILE = 16 * A1_SBO, A1_BYTES = N2 * N * 2;
@@ -56,11 +59,12 @@ struct Geo {
     static constexpr uint32_t A3_BYTES = KG * A3_LBO;
     // filters: K-major N x N (row = output index, k = input index), [axis][hi|lo]
     static constexpr uint32_t F_LBO = 128, F_SBO = 16 * N, F_MAT = N2 * 2, F_BLOCK = 6 * F_MAT;
-    // TMEM columns: D1[2], D2[2], + translate (all tiles), - translate tile [2]
-    static constexpr uint32_t C_D1 = 0, C_D2 = 2 * N, C_D3P = 4 * N, C_D3M = 4 * N + TILES * N;
-    static constexpr uint32_t C_USED = C_D3M + 2 * N;
+    // TMEM columns
+    static constexpr uint32_t C_D1 = 0, C_D2 = ND1 * N, C_D3P = C_D2 + ND2 * N, C_D3M = C_D3P + TILES * N;
+    static constexpr uint32_t C_USED = C_D3M + ND3 * N;
     static constexpr uint32_t TMEM_COLS = C_USED <= 32 ? 32 : C_USED <= 64 ? 64 : C_USED <= 128 ? 128
                                           : C_USED <= 256 ? 256 : 512;
+    static_assert(C_USED <= 512, "TMEM budget");
     // shared memory
     static constexpr uint32_t S_A1 = 0, S_A2 = S_A1 + A1_BYTES, S_A3 = S_A2 + 2 * A2_BYTES;
     static constexpr uint32_t S_F = (S_A3 + A3_BYTES + 127) / 128 * 128;
@@ -78,35 +82,52 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
     }
 }
 
+// Barriers of the pipeline (mbarriers in shared memory).
+struct Bars {
+    uint64_t d1_full[3], d1_free[3];   // pass-1 accumulator: MMA -> WG0, WG0 -> MMA
+    uint64_t a2_full[2];               // pass-2 operand written: WG0 -> MMA
+    uint64_t d2_full[2], d2_free[2];   // pass-2 accumulator (its completion also frees A2)
+    uint64_t a3_full, a3_free;         // pass-3 operand: WG1 -> MMA, MMA completion -> WG1
+    uint64_t d3p_full, d3p_free;       // + translate in TMEM: MMA -> WGs, WGs -> MMA
+    uint64_t d3m_full[2], d3m_free[2]; // - translate tiles
+    uint64_t pair_done;                // all MMAs of a pair complete: its filter buffer is free
+    uint64_t filt[2], drain;
+};
+
+// Warp roles: warps 0-3 (WG0) turn pass-1 tiles into pass-2 operands, warps 4-7 (WG1) turn
+// pass-2 tiles into the pass-3 operand, both warpgroups form the products (half the columns
+// each), warp 8 allocates TMEM and issues the MMAs and copies.
 template <int N, bool BF>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(288, 1)
 k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs,
           const unsigned char* __restrict__ filt, const float* __restrict__ wsig, int npairs, int Nrho,
           float* __restrict__ P, int* __restrict__ flags) {
     using G = Geo<N>;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mb_p1[2], mb_p2[2], mb_p3[2], mb_p3all, mb_filt[2], mb_drain;
+    __shared__ __align__(8) Bars bars;
     __shared__ uint32_t s_tmem;
     __shared__ float s_red[8];
     __shared__ int s_abort;
+    volatile int* abort = &s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q = warp & 3, h = warp >> 2;
-    const int lrow = 32 * q + lane;            // TMEM lane of this thread
+    const int wg = warp >> 2, q = warp & 3;     // warpgroup (0, 1; 2 = MMA warp), lane quarter
+    const int lrow = 32 * q + lane;              // TMEM lane (row) of this thread
     const int r = blockIdx.x;
     const int64_t node = blockIdx.y;
     const int64_t n3 = (int64_t)N * N * N;
     const float* fb = f + (offs ? offs[node] : node * n3);
     const uint32_t sb = tc::smem_u32(smem);
 
-    // ---- per-node scale (fp16: max |f| * sf in (256, 512]) ----------------------------------
+    // ---- set-up: scale, f -> A1 (warps 0-7); barriers, TMEM, first filter copies (warp 8) --
     float sf = 1.f;
     if (!BF) {
         float mx = 0.f;
-        for (int e = tid; e < n3; e += 256) mx = fmaxf(mx, fabsf(__ldg(fb + e)));
+        if (warp < 8)
+            for (int e = tid; e < n3; e += 256) mx = fmaxf(mx, fabsf(__ldg(fb + e)));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) s_red[warp] = mx;
+        if (lane == 0 && warp < 8) s_red[warp] = mx;
         __syncthreads();
         mx = s_red[0];
 #pragma unroll
@@ -116,250 +137,295 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs,
     const float pass_scale = BF ? 1.f : exp2f(-(float)kFilterShift);   // undo the filter scaling
     const float out_scale = BF ? 1.f : exp2f(-2.f * kFilterShift) / (sf * sf);
 
-    // ---- f -> A1 (K-major 16-bit, rows (z, y), k = x) ---------------------------------------
-    for (int it = tid; it < G::N2 * G::KG; it += 256) {
-        const int z = it % N, y = (it / N) % N, kg = it / G::N2;
-        const int m1 = z * N + y;
-        float v[8];
+    if (warp < 8) {
+        for (int it = tid; it < G::N2 * G::KG; it += 256) {
+            const int z = it % N, y = (it / N) % N, kg = it / G::N2;
+            const int m1 = z * N + y;
+            float v[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = __ldg(fb + (size_t)(kg * 8 + i) * G::N2 + y * N + z) * sf;
-        tc::st_shared_v4(sb + G::S_A1 + (m1 >> 3) * G::A1_SBO + kg * G::A1_LBO + (m1 & 7) * 16,
-                         pack2<BF>(v[0], v[1]), pack2<BF>(v[2], v[3]), pack2<BF>(v[4], v[5]), pack2<BF>(v[6], v[7]));
-    }
-
-    if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
-            tc::mbar_init(&mb_p1[i], 1);
-            tc::mbar_init(&mb_p2[i], 1);
-            tc::mbar_init(&mb_p3[i], 1);
-            tc::mbar_init(&mb_filt[i], 1);
+            for (int i = 0; i < 8; ++i) v[i] = __ldg(fb + (size_t)(kg * 8 + i) * G::N2 + y * N + z) * sf;
+            tc::st_shared_v4(sb + G::S_A1 + (m1 >> 3) * G::A1_SBO + kg * G::A1_LBO + (m1 & 7) * 16,
+                             pack2<BF>(v[0], v[1]), pack2<BF>(v[2], v[3]), pack2<BF>(v[4], v[5]), pack2<BF>(v[6], v[7]));
         }
-        tc::mbar_init(&mb_p3all, 1);
-        tc::mbar_init(&mb_drain, 1);
-        tc::fence_mbar_init();
-        s_abort = 0;
+    } else {
+        if (lane == 0) {
+            for (int i = 0; i < 3; ++i) {
+                tc::mbar_init(&bars.d1_full[i], 1);
+                tc::mbar_init(&bars.d1_free[i], 4);
+            }
+            for (int i = 0; i < 2; ++i) {
+                tc::mbar_init(&bars.a2_full[i], 4);
+                tc::mbar_init(&bars.d2_full[i], 1);
+                tc::mbar_init(&bars.d2_free[i], 4);
+                tc::mbar_init(&bars.d3m_full[i], 1);
+                tc::mbar_init(&bars.d3m_free[i], 8);
+                tc::mbar_init(&bars.filt[i], 1);
+            }
+            tc::mbar_init(&bars.a3_full, 4);
+            tc::mbar_init(&bars.a3_free, 1);
+            tc::mbar_init(&bars.d3p_full, 1);
+            tc::mbar_init(&bars.d3p_free, 8);
+            tc::mbar_init(&bars.pair_done, 1);
+            tc::mbar_init(&bars.drain, 1);
+            tc::fence_mbar_init();
+            s_abort = 0;
+            for (int p = 0; p < 2 && p < npairs; ++p) {
+                tc::mbar_expect_tx(&bars.filt[p], G::F_BLOCK);
+                tc::bulk_g2s(smem + G::S_F + p * G::F_BLOCK, filt + ((size_t)r * npairs + p) * G::F_BLOCK,
+                             G::F_BLOCK, &bars.filt[p]);
+            }
+        }
+        __syncwarp();
+        tc::tmem_alloc(&s_tmem, G::TMEM_COLS);
     }
-    if (warp == 0) tc::tmem_alloc(&s_tmem, G::TMEM_COLS);
     tc::fence_proxy_async();
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    int filt_issued[2] = {0, 0}, filt_waited[2] = {0, 0};
-    if (tid == 0) {
-        for (int p = 0; p < 2 && p < npairs; ++p) {
-            tc::mbar_expect_tx(&mb_filt[p], G::F_BLOCK);
-            tc::bulk_g2s(smem + G::S_F + p * G::F_BLOCK, filt + ((size_t)r * npairs + p) * G::F_BLOCK,
-                         G::F_BLOCK, &mb_filt[p]);
-        }
-    }
-    for (int p = 0; p < 2 && p < npairs; ++p) filt_issued[p] = 1;
-
-    // MMA issue (thread 0): one contraction = KSTEPS x {hi, lo} instructions
-    auto issue = [&](uint32_t dcol, uint32_t a_start, uint32_t a_lbo, uint32_t a_sbo, bool a_mn, int axis,
-                     int fbuf, int sg) {
-        const uint32_t idesc = tc::idesc_f16(BF, a_mn, sg == 1, N, 128);
-#pragma unroll
-        for (int ks = 0; ks < G::KSTEPS; ++ks)
-#pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-                const uint64_t da = tc::sdesc(a_start + ks * 2 * a_lbo, a_lbo, a_sbo);
-                const uint32_t fbase = sb + G::S_F + fbuf * G::F_BLOCK + (axis * 2 + pp) * G::F_MAT;
-                const uint64_t db = sg == 0 ? tc::sdesc(fbase + ks * 2 * G::F_LBO, G::F_LBO, G::F_SBO)
-                                            : tc::sdesc(fbase + ks * 2 * G::F_SBO, G::F_SBO, G::F_LBO);
-                tc::mma_f16(tmem + dcol, da, db, idesc, (ks | pp) != 0);
-            }
-    };
-    auto issue_p1 = [&](int t, int b, int fbuf, int sg) {
-        issue(G::C_D1 + b * N, sb + G::S_A1 + t * G::A1_TILE, G::A1_LBO, G::A1_SBO, false, 0, fbuf, sg);
-    };
-    auto issue_p2 = [&](int b, int fbuf, int sg) {
-        issue(G::C_D2 + b * N, sb + G::S_A2 + b * G::A2_BYTES, G::A2_LBO, G::A2_SBO, true, 1, fbuf, sg);
-    };
-    auto issue_p3 = [&](int u, uint32_t dcol, int fbuf, int sg) {
-        issue(dcol, sb + G::S_A3 + u * G::A3_TS, G::A3_LBO, G::A3_SBO, true, 2, fbuf, sg);
-    };
-    const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + h * G::HALF;   // this thread's TMEM slice
-    auto tload = [&](uint32_t col, float* v) {
-        if constexpr (G::HALF == 16) {
-            tc::tmem_ld16(trow + col, *reinterpret_cast<float(*)[16]>(v));
-        } else {
-            tc::tmem_ld8(trow + col, *reinterpret_cast<float(*)[8]>(v));
-        }
-    };
-    // pass-1 epilogue: D1 row (z, y), columns x' -> A2 rows (zl, x'), K-row y
-    auto epi1 = [&](int t, int b) {
-        float v[G::HALF];
-        tload(G::C_D1 + b * N, v);
-        tc::tmem_wait_ld();
-        const int m1 = t * 128 + lrow, y = m1 % N, zl = lrow / N;
-#pragma unroll
-        for (int c = 0; c < G::HALF / 8; ++c) {
-            const int mg = (zl * N + h * G::HALF + 8 * c) >> 3;
-            const float* w = v + 8 * c;
-            tc::st_shared_v4(sb + G::S_A2 + b * G::A2_BYTES + mg * G::A2_SBO + (y >> 3) * G::A2_LBO + (y & 7) * 16,
-                             pack2<BF>(w[0] * pass_scale, w[1] * pass_scale), pack2<BF>(w[2] * pass_scale, w[3] * pass_scale),
-                             pack2<BF>(w[4] * pass_scale, w[5] * pass_scale), pack2<BF>(w[6] * pass_scale, w[7] * pass_scale));
-        }
-    };
-    // pass-2 epilogue: D2 row (zl, x'), columns y' -> A3 rows (x', y'), K-row z
-    auto epi2 = [&](int t, int b) {
-        float v[G::HALF];
-        tload(G::C_D2 + b * N, v);
-        tc::tmem_wait_ld();
-        const int zl = lrow / N, xp = lrow % N, z = t * G::ZT + zl;
-#pragma unroll
-        for (int c = 0; c < G::HALF / 8; ++c) {
-            const int mg = (xp * N + h * G::HALF + 8 * c) >> 3;
-            const int u = mg >> 4, mgl = mg & 15;
-            const float* w = v + 8 * c;
-            tc::st_shared_v4(sb + G::S_A3 + u * G::A3_TS + mgl * G::A3_SBO + (z >> 3) * G::A3_LBO + (z & 7) * 16,
-                             pack2<BF>(w[0] * pass_scale, w[1] * pass_scale), pack2<BF>(w[2] * pass_scale, w[3] * pass_scale),
-                             pack2<BF>(w[4] * pass_scale, w[5] * pass_scale), pack2<BF>(w[6] * pass_scale, w[7] * pass_scale));
-        }
-    };
-    auto fail = [&]() { s_abort = 1; if (lane == 0) atomicOr(flags, 1); };
-    auto sync = [&]() {
-        tc::tc_fence_before();
-        __syncthreads();
-        tc::tc_fence_after();
-    };
-
     float acc[G::TILES][G::HALF];
 #pragma unroll
     for (int u = 0; u < G::TILES; ++u)
 #pragma unroll
         for (int j = 0; j < G::HALF; ++j) acc[u][j] = 0.f;
-    uint32_t ph1[2] = {0, 0}, ph2[2] = {0, 0}, ph3[2] = {0, 0}, ph3all = 0;
 
-    for (int p = 0; p < npairs; ++p) {
-        const int fbuf = p & 1;
-        if (!tc::mbar_wait(&mb_filt[fbuf], (uint32_t)(filt_waited[fbuf] & 1))) fail();
-        filt_waited[fbuf]++;
-        const float w2 = 2.f * wsig[p];
-        for (int sg = 0; sg < 2; ++sg) {
-            if (tid == 0) {
-                issue_p1(0, 0, fbuf, sg);
-                tc::mma_commit(&mb_p1[0]);
-                if (G::TILES > 1) {
-                    issue_p1(1, 1, fbuf, sg);
-                    tc::mma_commit(&mb_p1[1]);
-                }
-            }
-            for (int t = 0; t < G::TILES; ++t) {
-                const int b = t & 1;
-                if (!tc::mbar_wait(&mb_p1[b], ph1[b])) fail();
-                ph1[b] ^= 1;
-                tc::tc_fence_after();
-                epi1(t, b);
-                tc::fence_proxy_async();
-                sync();
-                if (s_abort) goto drain;
-                if (tid == 0) {
-                    issue_p2(b, fbuf, sg);
-                    tc::mma_commit(&mb_p2[b]);
-                    if (t + 2 < G::TILES) {
-                        issue_p1(t + 2, b, fbuf, sg);
-                        tc::mma_commit(&mb_p1[b]);
+    // filter copies issued and waited per buffer (only warp 8, lane 0 uses these)
+    int filt_copies[2] = {npairs > 0 ? 1 : 0, npairs > 1 ? 1 : 0}, filt_waited[2] = {0, 0};
+
+    if (warp == 8) {
+        // ================================ MMA warp ======================================
+        if (lane == 0) {
+            int d1_use[3] = {0, 0, 0}, d2_use[2] = {0, 0}, d3m_use[2] = {0, 0};
+            uint32_t ph_d1free[3] = {0, 0, 0}, ph_a2full[2] = {0, 0}, ph_d2free[2] = {0, 0};
+            uint32_t ph_a3full = 0, ph_d3pfree = 0, ph_d3mfree[2] = {0, 0}, ph_pair = 0;
+            auto issue = [&](uint32_t dcol, uint32_t a_start, uint32_t a_lbo, uint32_t a_sbo, bool a_mn, int axis,
+                             int fbuf, int sg) {
+                const uint32_t idesc = tc::idesc_f16(BF, a_mn, sg == 1, N, 128);
+#pragma unroll
+                for (int ks = 0; ks < G::KSTEPS; ++ks)
+#pragma unroll
+                    for (int pp = 0; pp < 2; ++pp) {
+                        const uint64_t da = tc::sdesc(a_start + ks * 2 * a_lbo, a_lbo, a_sbo);
+                        const uint32_t fbase = sb + G::S_F + fbuf * G::F_BLOCK + (axis * 2 + pp) * G::F_MAT;
+                        const uint64_t db = sg == 0 ? tc::sdesc(fbase + ks * 2 * G::F_LBO, G::F_LBO, G::F_SBO)
+                                                    : tc::sdesc(fbase + ks * 2 * G::F_SBO, G::F_SBO, G::F_LBO);
+                        tc::mma_f16(tmem + dcol, da, db, idesc, (ks | pp) != 0);
                     }
-                }
-                if (t >= 1) {
-                    const int b2 = (t - 1) & 1;
-                    if (sg == 1 && t == 1) {        // the + pass 3 must be done with A3
-                        if (!tc::mbar_wait(&mb_p3all, ph3all)) fail();
-                        ph3all ^= 1;
+            };
+            for (int p = 0; p < npairs; ++p) {
+                const int fbuf = p & 1;
+                if (!tc::mbar_wait_or_abort(&bars.filt[fbuf], (uint32_t)(filt_waited[fbuf] & 1), abort)) goto mma_done;
+                filt_waited[fbuf]++;
+                for (int sg = 0; sg < 2; ++sg) {
+                    for (int step = 0; step <= G::TILES; ++step) {
+                        if (step < G::TILES) {                       // pass 1, tile t
+                            const int t = step, b = t % 3;
+                            if (d1_use[b]++ > 0) {
+                                if (!tc::mbar_wait_or_abort(&bars.d1_free[b], ph_d1free[b], abort)) goto mma_done;
+                                ph_d1free[b] ^= 1;
+                            }
+                            tc::tc_fence_after();
+                            issue(G::C_D1 + b * N, sb + G::S_A1 + t * G::A1_TILE, G::A1_LBO, G::A1_SBO, false, 0, fbuf, sg);
+                            tc::mma_commit(&bars.d1_full[b]);
+                            // once pair p - 1 is complete its filter buffer takes pair p + 1
+                            // (waited here, after the first tiles of pair p are queued, so the
+                            // tensor pipe never drains; every pair_done phase is waited in order)
+                            if (sg == 0 && t == 0 && p >= 1) {
+                                if (!tc::mbar_wait_or_abort(&bars.pair_done, ph_pair, abort)) goto mma_done;
+                                ph_pair ^= 1;
+                                if (p + 1 < npairs) {
+                                    const int nb = (p + 1) & 1;
+                                    tc::mbar_expect_tx(&bars.filt[nb], G::F_BLOCK);
+                                    tc::bulk_g2s(smem + G::S_F + nb * G::F_BLOCK,
+                                                 filt + ((size_t)r * npairs + p + 1) * G::F_BLOCK, G::F_BLOCK,
+                                                 &bars.filt[nb]);
+                                    filt_copies[nb]++;
+                                }
+                            }
+                        }
+                        if (step >= 1) {                             // pass 2, tile t - 1
+                            const int t = step - 1, b = t & 1;
+                            if (!tc::mbar_wait_or_abort(&bars.a2_full[b], ph_a2full[b], abort)) goto mma_done;
+                            ph_a2full[b] ^= 1;
+                            if (d2_use[b]++ > 0) {
+                                if (!tc::mbar_wait_or_abort(&bars.d2_free[b], ph_d2free[b], abort)) goto mma_done;
+                                ph_d2free[b] ^= 1;
+                            }
+                            tc::tc_fence_after();
+                            issue(G::C_D2 + b * N, sb + G::S_A2 + b * G::A2_BYTES, G::A2_LBO, G::A2_SBO, true, 1, fbuf, sg);
+                            tc::mma_commit(&bars.d2_full[b]);
+                        }
                     }
-                    if (!tc::mbar_wait(&mb_p2[b2], ph2[b2])) fail();
-                    ph2[b2] ^= 1;
+                    if (!tc::mbar_wait_or_abort(&bars.a3_full, ph_a3full, abort)) goto mma_done;
+                    ph_a3full ^= 1;
                     tc::tc_fence_after();
-                    epi2(t - 1, b2);
-                }
-            }
-            {
-                const int b2 = (G::TILES - 1) & 1;
-                if (!tc::mbar_wait(&mb_p2[b2], ph2[b2])) fail();
-                ph2[b2] ^= 1;
-                tc::tc_fence_after();
-                epi2(G::TILES - 1, b2);
-            }
-            tc::fence_proxy_async();
-            sync();
-            if (s_abort) goto drain;
-            if (sg == 0) {
-                if (tid == 0) {
-#pragma unroll
-                    for (int u = 0; u < G::TILES; ++u) issue_p3(u, G::C_D3P + u * N, fbuf, 0);
-                    tc::mma_commit(&mb_p3all);
-                }
-            } else {
-                if (tid == 0) {
-                    issue_p3(0, G::C_D3M, fbuf, 1);
-                    tc::mma_commit(&mb_p3[0]);
-                    if (G::TILES > 1) {
-                        issue_p3(1, G::C_D3M + N, fbuf, 1);
-                        tc::mma_commit(&mb_p3[1]);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < G::TILES; ++u) {
-                    const int b = u & 1;
-                    if (!tc::mbar_wait(&mb_p3[b], ph3[b])) fail();
-                    ph3[b] ^= 1;
-                    tc::tc_fence_after();
-                    float fm[G::HALF], fp[G::HALF];
-                    tload(G::C_D3M + b * N, fm);
-                    tload(G::C_D3P + u * N, fp);
-                    tc::tmem_wait_ld();
-#pragma unroll
-                    for (int j = 0; j < G::HALF; ++j) acc[u][j] = fmaf(w2 * fp[j], fm[j], acc[u][j]);
-                    sync();
-                    if (s_abort) goto drain;
-                    if (tid == 0 && u + 2 < G::TILES) {
-                        issue_p3(u + 2, G::C_D3M + b * N, fbuf, 1);
-                        tc::mma_commit(&mb_p3[b]);
+                    if (sg == 0) {
+                        if (p > 0) {                                 // the previous pair's products are done
+                            if (!tc::mbar_wait_or_abort(&bars.d3p_free, ph_d3pfree, abort)) goto mma_done;
+                            ph_d3pfree ^= 1;
+                        }
+                        for (int u = 0; u < G::TILES; ++u)
+                            issue(G::C_D3P + u * N, sb + G::S_A3 + u * G::A3_TS, G::A3_LBO, G::A3_SBO, true, 2, fbuf, 0);
+                        tc::mma_commit(&bars.d3p_full);
+                        tc::mma_commit(&bars.a3_free);
+                    } else {
+                        for (int u = 0; u < G::TILES; ++u) {
+                            const int b = u & 1;
+                            if (d3m_use[b]++ > 0) {
+                                if (!tc::mbar_wait_or_abort(&bars.d3m_free[b], ph_d3mfree[b], abort)) goto mma_done;
+                                ph_d3mfree[b] ^= 1;
+                            }
+                            tc::tc_fence_after();
+                            issue(G::C_D3M + b * N, sb + G::S_A3 + u * G::A3_TS, G::A3_LBO, G::A3_SBO, true, 2, fbuf, 1);
+                            tc::mma_commit(&bars.d3m_full[b]);
+                        }
+                        tc::mma_commit(&bars.a3_free);
+                        tc::mma_commit(&bars.pair_done);
                     }
                 }
             }
+        mma_done:;
         }
-        // every MMA of pair p has completed: its filter buffer can take pair p + 2
-        if (p + 2 < npairs) {
-            if (tid == 0) {
-                tc::mbar_expect_tx(&mb_filt[fbuf], G::F_BLOCK);
-                tc::bulk_g2s(smem + G::S_F + fbuf * G::F_BLOCK, filt + ((size_t)r * npairs + p + 2) * G::F_BLOCK,
-                             G::F_BLOCK, &mb_filt[fbuf]);
+        __syncwarp();
+    } else {
+        // ============================ epilogue warpgroups ==================================
+        uint32_t ph_d1full[3] = {0, 0, 0}, ph_d2full[2] = {0, 0}, ph_a3free = 0, ph_d3pfull = 0;
+        uint32_t ph_d3mfull[2] = {0, 0};
+        int a2_use[2] = {0, 0};
+        int signs_done = 0;
+        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+        for (int p = 0; p < npairs; ++p) {
+            const float w2 = 2.f * wsig[p];
+            for (int sg = 0; sg < 2; ++sg) {
+                if (wg == 0) {
+                    // pass-1 tiles -> pass-2 operands
+                    for (int t = 0; t < G::TILES; ++t) {
+                        const int b = t % 3, b2 = t & 1;
+                        if (!tc::mbar_wait_or_abort(&bars.d1_full[b], ph_d1full[b], abort)) goto epi_done;
+                        ph_d1full[b] ^= 1;
+                        tc::tc_fence_after();
+                        float v[N];
+                        if constexpr (N == 32) tc::tmem_ld32(trow + G::C_D1 + b * N, v);
+                        else tc::tmem_ld16(trow + G::C_D1 + b * N, *reinterpret_cast<float(*)[16]>(v));
+                        tc::tmem_wait_ld();
+                        tc::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&bars.d1_free[b]);
+                        // A2[b2] is free once the pass-2 MMA of its previous tile has completed
+                        if (a2_use[b2]++ > 0) {
+                            if (!tc::mbar_wait_or_abort(&bars.d2_full[b2], ph_d2full[b2], abort)) goto epi_done;
+                            ph_d2full[b2] ^= 1;
+                        }
+                        const int m1 = t * 128 + lrow, y = m1 % N, zl = lrow / N;
+#pragma unroll
+                        for (int c = 0; c < N / 8; ++c) {
+                            const int mg = (zl * N + 8 * c) >> 3;
+                            const float* w = v + 8 * c;
+                            tc::st_shared_v4(sb + G::S_A2 + b2 * G::A2_BYTES + mg * G::A2_SBO + (y >> 3) * G::A2_LBO + (y & 7) * 16,
+                                             pack2<BF>(w[0] * pass_scale, w[1] * pass_scale), pack2<BF>(w[2] * pass_scale, w[3] * pass_scale),
+                                             pack2<BF>(w[4] * pass_scale, w[5] * pass_scale), pack2<BF>(w[6] * pass_scale, w[7] * pass_scale));
+                        }
+                        tc::fence_proxy_async();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&bars.a2_full[b2]);
+                    }
+                } else {
+                    // pass-2 tiles -> the pass-3 operand (A3 must be free of the last pass 3)
+                    if (signs_done > 0) {
+                        if (!tc::mbar_wait_or_abort(&bars.a3_free, ph_a3free, abort)) goto epi_done;
+                        ph_a3free ^= 1;
+                    }
+                    for (int t = 0; t < G::TILES; ++t) {
+                        const int b = t & 1;
+                        if (!tc::mbar_wait_or_abort(&bars.d2_full[b], ph_d2full[b], abort)) goto epi_done;
+                        ph_d2full[b] ^= 1;
+                        tc::tc_fence_after();
+                        float v[N];
+                        if constexpr (N == 32) tc::tmem_ld32(trow + G::C_D2 + b * N, v);
+                        else tc::tmem_ld16(trow + G::C_D2 + b * N, *reinterpret_cast<float(*)[16]>(v));
+                        tc::tmem_wait_ld();
+                        tc::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&bars.d2_free[b]);
+                        const int zl = lrow / N, xp = lrow % N, z = t * G::ZT + zl;
+#pragma unroll
+                        for (int c = 0; c < N / 8; ++c) {
+                            const int mg = (xp * N + 8 * c) >> 3;
+                            const int u = mg >> 4, mgl = mg & 15;
+                            const float* w = v + 8 * c;
+                            tc::st_shared_v4(sb + G::S_A3 + u * G::A3_TS + mgl * G::A3_SBO + (z >> 3) * G::A3_LBO + (z & 7) * 16,
+                                             pack2<BF>(w[0] * pass_scale, w[1] * pass_scale), pack2<BF>(w[2] * pass_scale, w[3] * pass_scale),
+                                             pack2<BF>(w[4] * pass_scale, w[5] * pass_scale), pack2<BF>(w[6] * pass_scale, w[7] * pass_scale));
+                        }
+                    }
+                    tc::fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&bars.a3_full);
+                }
+                signs_done++;
+                if (sg == 1) {
+                    // products of the two translates, half of the columns per warpgroup
+                    if (!tc::mbar_wait_or_abort(&bars.d3p_full, ph_d3pfull, abort)) goto epi_done;
+                    ph_d3pfull ^= 1;
+#pragma unroll
+                    for (int u = 0; u < G::TILES; ++u) {
+                        const int b = u & 1;
+                        if (!tc::mbar_wait_or_abort(&bars.d3m_full[b], ph_d3mfull[b], abort)) goto epi_done;
+                        ph_d3mfull[b] ^= 1;
+                        tc::tc_fence_after();
+                        float fm[G::HALF], fp[G::HALF];
+                        if constexpr (G::HALF == 16) {
+                            tc::tmem_ld16(trow + G::C_D3M + b * N + wg * G::HALF, *reinterpret_cast<float(*)[16]>(fm));
+                            tc::tmem_ld16(trow + G::C_D3P + u * N + wg * G::HALF, *reinterpret_cast<float(*)[16]>(fp));
+                        } else {
+                            tc::tmem_ld8(trow + G::C_D3M + b * N + wg * G::HALF, *reinterpret_cast<float(*)[8]>(fm));
+                            tc::tmem_ld8(trow + G::C_D3P + u * N + wg * G::HALF, *reinterpret_cast<float(*)[8]>(fp));
+                        }
+                        tc::tmem_wait_ld();
+                        tc::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&bars.d3m_free[b]);
+#pragma unroll
+                        for (int j = 0; j < G::HALF; ++j) acc[u][j] = fmaf(w2 * fp[j], fm[j], acc[u][j]);
+                    }
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&bars.d3p_free);
+                }
             }
-            filt_issued[fbuf]++;
         }
+        if (!*abort) {   // results: P[node][r][x'][y'][z'] = acc * out_scale (this warpgroup's half)
+            float* dst = P + ((size_t)node * Nrho + r) * n3;
+#pragma unroll
+            for (int u = 0; u < G::TILES; ++u) {
+                const int m3 = u * 128 + lrow;
+                float4* o = reinterpret_cast<float4*>(dst + (size_t)m3 * N + wg * G::HALF);
+#pragma unroll
+                for (int j = 0; j < G::HALF; j += 4)
+                    o[j / 4] = make_float4(acc[u][j] * out_scale, acc[u][j + 1] * out_scale,
+                                           acc[u][j + 2] * out_scale, acc[u][j + 3] * out_scale);
+            }
+        }
+    epi_done:;
     }
 
-    {   // results: P[node][r][x'][y'][z'] = acc * out_scale
-        float* dst = P + ((size_t)node * Nrho + r) * n3;
-#pragma unroll
-        for (int u = 0; u < G::TILES; ++u) {
-            const int m3 = u * 128 + lrow;
-            float4* o = reinterpret_cast<float4*>(dst + (size_t)m3 * N + h * G::HALF);
-#pragma unroll
-            for (int j = 0; j < G::HALF; j += 4)
-                o[j / 4] = make_float4(acc[u][j] * out_scale, acc[u][j + 1] * out_scale, acc[u][j + 2] * out_scale,
-                                       acc[u][j + 3] * out_scale);
+    // ---- drain: no MMA or copy of this CTA may be in flight when TMEM is freed -----------
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        if (lane == 0) {
+            if (*abort) atomicOr(flags, 1);
+            tc::mma_commit(&bars.drain);
+            if (!tc::mbar_wait(&bars.drain, 0)) atomicOr(flags, 1);
+            // wait for every issued filter copy that the pipeline did not wait for
+            for (int i = 0; i < 2; ++i)
+                for (int k = filt_waited[i]; k < filt_copies[i]; ++k)
+                    if (!tc::mbar_wait(&bars.filt[i], (uint32_t)(k & 1))) { atomicOr(flags, 1); break; }
         }
+        __syncwarp();
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, G::TMEM_COLS);
     }
-
-drain:
-    // make sure no MMA or copy of this CTA is still in flight before TMEM is freed
-    sync();
-    if (tid == 0) {
-        tc::mma_commit(&mb_drain);
-        if (!tc::mbar_wait(&mb_drain, 0)) atomicOr(flags, 1);
-        for (int i = 0; i < 2; ++i)
-            while (filt_waited[i] < filt_issued[i]) {
-                if (!tc::mbar_wait(&mb_filt[i], (uint32_t)(filt_waited[i] & 1))) { atomicOr(flags, 1); break; }
-                filt_waited[i]++;
-            }
-    }
-    sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, G::TMEM_COLS);
 }
 
 template <int N, bool BF>
@@ -372,7 +438,7 @@ cudaError_t launch_n(const TcTables& t, const float* f, const int64_t* offs, int
     const int64_t n3 = (int64_t)N * N * N;
     for (int64_t n0 = 0; n0 < nodes; n0 += 65535) {
         const int64_t nn = nodes - n0 < 65535 ? nodes - n0 : 65535;
-        kern<<<dim3(t.Nrho, (unsigned)nn), 256, G::S_TOTAL, s>>>(
+        kern<<<dim3(t.Nrho, (unsigned)nn), 288, G::S_TOTAL, s>>>(
             f + (offs ? 0 : n0 * n3), offs ? offs + n0 : nullptr, static_cast<const unsigned char*>(t.mats),
             t.wsig, t.npairs, t.Nrho, P + n0 * t.Nrho * n3, flags);
         e = cudaGetLastError();

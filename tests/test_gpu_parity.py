@@ -356,3 +356,27 @@ def test_tensor_core_chunking_and_determinism():
     a = p1.collide(f)
     assert torch.equal(a, p1.collide(f))
     assert torch.equal(a, p2.collide(f))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16s"])
+def test_cuda_graph_capture_equals_eager(prec):
+    """dgfs_collide enqueues kernels only, so a captured call replays to the eager result."""
+    N, L = 32, 7.0
+    F, _ = W.two_maxwellian(3, N, L, 77, dtype=np.float32)
+    plan = binding.Plan(N=N, L=L, gamma=0.52, M=12, N_rho=N, precision=prec)
+    f = _dev(F, "fp32")
+    eager = plan.collide(f)
+    q = torch.empty_like(f)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.collide(f, out=q)                      # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.collide(f, out=q)
+    q.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(q, eager)
