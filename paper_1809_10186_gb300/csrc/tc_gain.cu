@@ -1,27 +1,27 @@
 // Tensor-core (tcgen05) translate-product kernel for the 16-bit precisions.
 //
 // Computes, like the CUDA-core kernel, P_r = sum_pairs 2 w_p (T_s f)(T_-s f) for Q(f, f)
-// (arXiv:1809.10186, Appendix, eqs. lowrank1 and apndx_fs_Glm_Qk), with every dense circulant
-// pass of the translates T_{+-s} run as tcgen05.mma (M = 128, N = grid size, K = grid size)
-// with FP32 accumulators in tensor memory:
+// (arXiv:1809.10186, Appendix, eqs. lowrank1 and apndx_fs_Glm_Qk). The translates are separable
+// circulant operators; their three dense passes run as tcgen05.mma with FP32 accumulators in
+// tensor memory, in the order x, z, y:
 //
-//   pass 1 (x): D1[(z,y)][x'] = sum_x f[x][y][z] A_x[x'][x]      A = f (K-major, resident)
-//   pass 2 (y): D2[(z,x')][y'] = sum_y D1[(z,y)][x'] A_y[y'][y]  A = MN-major tile of D1
-//   pass 3 (z): D3[(x',y')][z'] = sum_z D2[(z,x')][y'] A_z[z'][z] A = MN-major full field
+//   pass 1 (x): D1[(y,z)][x'] = sum_x f[x][y][z] Fx[x'][x]       A = f, held in TMEM
+//   pass 2 (z): D2[(y,x')][z'] = sum_z D1[(y,z)][x'] Fz[z'][z]   A = MN-major tile in SMEM
+//   pass 3 (y): D3[(x',z')][y'] = sum_y D2[(y,x')][z'] Fy[y'][y] A = MN-major full field in SMEM
 //
-// Data operands are 16-bit (fp16 with a per-node power-of-two scale, or bf16); every filter
-// matrix is split into hi + lo 16-bit parts (two products per contraction). Each pass's
-// epilogue reads its TMEM tile (one row per thread), rescales, rounds to 16 bits and writes
-// the next pass's operand with 16-byte shared-memory stores. The + translate of all tiles
-// stays in TMEM while the - translate is computed; their products accumulate in registers.
-// The - filter is the transpose of the + filter (T_-s = T_s^T): the same shared-memory matrix
-// is read as an MN-major operand.
+// Data operands are 16-bit (fp16 with a per-node power-of-two scale, or bf16). Every filter F is
+// split into a hi and a lo 16-bit part, and the parts are stacked along the MMA's N dimension, so
+// one MMA yields both products: pass 1 stacks {+hi, +lo, -hi, -lo} (N = 4 n), passes 2 and 3 stack
+// {hi, lo} of one sign (N = 2 n). The epilogue combines hi + 2^-e lo in FP32. The + sign's x filter
+// carries the factor 2 w_p, so the products need no further weighting.
 //
-// One CTA of 288 threads per (radial point, node), warp-specialised: one warp issues the MMAs
-// and copies, two warpgroups convert accumulator tiles into the next pass's operands and form
-// the products; all hand-offs are mbarriers. Every wait is bounded: on timeout the CTA raises
-// flag bit 0, every role stops, the MMAs and copies in flight are drained (bounded), TMEM is
-// freed and P is not written.
+// One CTA per (radial point, node): 4 n/8 epilogue warpgroups (each owns 8 of the n output
+// columns of every tile) and one MMA warp. Three 4n-column TMEM slots hold the accumulators; the
+// slots alternate between the passes so that an MMA never waits for the epilogue of the
+// accumulator it is about to overwrite when another slot is free. Both signs' pass-3 operands
+// (full fields) stay in shared memory until the products of the pair are formed. All hand-offs
+// are mbarriers; every wait is bounded: on timeout the CTA raises flag bit 0, every role stops,
+// the MMAs and copies in flight are drained (bounded), TMEM is freed and P is not written.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -36,43 +36,50 @@ namespace dgfs {
 
 namespace {
 
-constexpr int kFilterShift = 8;   // fp16 filters are stored times 2^8 (keeps the lo parts normal)
+// lo filter parts are stored times 2^e (keeps them normal in fp16; bf16 has the exponent range)
+constexpr int kLoShiftF16 = 11;
+constexpr int kLoShiftBF16 = 8;
 
 template <int N>
 struct Geo {
     static_assert(N == 16 || N == 32, "tensor-core translates support N = 16 and 32");
     static constexpr int N2 = N * N;
-    static constexpr int TILES = N2 / 128;    // 128-row M tiles of one field
-    static constexpr int ZT = 128 / N;         // z values per pass-1/2 tile
-    static constexpr int KSTEPS = N / 16;      // K = 16 steps of one contraction
-    static constexpr int KG = N / 8;           // core-matrix groups along K
-    static constexpr int HALF = N / 2;         // columns of the product per warpgroup
-    static constexpr int ND1 = 3, ND2 = 2, ND3 = 2;   // TMEM buffers of passes 1, 2, 3 (- sign)
-    // A1 = f, K-major: rows m1 = z*N + y, k = x
-    static constexpr uint32_t A1_LBO = 128, A1_SBO = 16 * N;
-    static constexpr uint32_t A1_TILE = 16 * A1_SBO, A1_BYTES = N2 * N * 2;
-    // A2, MN-major, one tile: rows m2 = zl*N + x', k = y
+    static constexpr int T = N2 / 128;           // 128-row tiles of one field
+    static constexpr int ZT = 128 / N;            // y values per pass-1/2 tile
+    static constexpr int KSTEPS = N / 16;         // K = 16 steps of one contraction
+    static constexpr int KG = N / 8;              // core-matrix groups along K
+    static constexpr int NWG = N / 8;             // epilogue warpgroups (8 output columns each)
+    static constexpr int EPI_WARPS = 4 * NWG;
+    static constexpr int THREADS = 32 * EPI_WARPS + 32;
+    static constexpr int ISSUER = EPI_WARPS;      // warp index of the MMA warp
+    // filter block of one (r, pair), K-major B operands: row n, column k at
+    // (n/8) FB_SBO + (k/8) FB_LBO + (n%8) 16 + (k%8) 2
+    static constexpr uint32_t FB_LBO = 128, FB_SBO = 16 * N;
+    static constexpr uint32_t B1_BYTES = 4 * N2 * 2, B23_BYTES = 2 * N2 * 2;
+    static constexpr uint32_t OFF_B1 = 0, OFF_B2 = B1_BYTES, OFF_B3 = B1_BYTES + 2 * B23_BYTES;
+    static constexpr uint32_t F_BLOCK = B1_BYTES + 4 * B23_BYTES;
+    // A2: pass-2 operand of one tile and sign, MN-major: rows m2 = yl N + x', k = z
     static constexpr uint32_t A2_SBO = 128, A2_LBO = 16 * 128, A2_BYTES = KG * A2_LBO;
-    // A3, MN-major, whole field: rows m3 = x'*N + y', k = z; padded m-group and tile strides
-    // spread the 16-byte stores of one 8-lane phase over more bank groups
-    static constexpr uint32_t A3_SBO = 144, A3_TS = 16 * 144 + 16, A3_LBO = TILES * A3_TS;
+    // A3: pass-3 operand of one sign (whole field), MN-major: rows m3 = x' N + z', k = y. The
+    // padded m-group and tile strides spread one warp's 16-byte stores over all bank groups.
+    static constexpr uint32_t A3_SBO = 144, A3_TS = 16 * 144 + 16, A3_LBO = T * A3_TS;
     static constexpr uint32_t A3_BYTES = KG * A3_LBO;
-    // filters: K-major N x N (row = output index, k = input index), [axis][hi|lo]
-    static constexpr uint32_t F_LBO = 128, F_SBO = 16 * N, F_MAT = N2 * 2, F_BLOCK = 6 * F_MAT;
-    // TMEM columns
-    static constexpr uint32_t C_D1 = 0, C_D2 = ND1 * N, C_D3P = C_D2 + ND2 * N, C_D3M = C_D3P + TILES * N;
-    static constexpr uint32_t C_USED = C_D3M + ND3 * N;
+    // TMEM columns: three accumulator slots of 4 N columns, then f (N/2 columns per tile)
+    static constexpr uint32_t SLOT = 4 * N;
+    static constexpr uint32_t C_F = 3 * SLOT, F_COLS = T * (N / 2);
+    static constexpr uint32_t C_USED = C_F + F_COLS;
     static constexpr uint32_t TMEM_COLS = C_USED <= 32 ? 32 : C_USED <= 64 ? 64 : C_USED <= 128 ? 128
                                           : C_USED <= 256 ? 256 : 512;
     static_assert(C_USED <= 512, "TMEM budget");
-    // shared memory
-    static constexpr uint32_t S_A1 = 0, S_A2 = S_A1 + A1_BYTES, S_A3 = S_A2 + 2 * A2_BYTES;
-    static constexpr uint32_t S_F = (S_A3 + A3_BYTES + 127) / 128 * 128;
+    // shared memory: A2 [slot 2][sign 2], A3 [sign 2], filters [buffer 2]
+    static constexpr uint32_t S_A2 = 0, S_A3 = S_A2 + 4 * A2_BYTES;
+    static constexpr uint32_t S_F = (S_A3 + 2 * A3_BYTES + 127) / 128 * 128;
     static constexpr uint32_t S_TOTAL = S_F + 2 * F_BLOCK;
+    static_assert(S_TOTAL + 512 <= 232448, "shared-memory budget");
 };
 
 template <bool BF>
-__device__ __forceinline__ uint32_t pack2(float a, float b) {
+__device__ __forceinline__ uint32_t pack2(float a, float b) {   // a -> low half, b -> high half
     if (BF) {
         __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
         return *reinterpret_cast<uint32_t*>(&v);
@@ -82,328 +89,324 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
     }
 }
 
-// Barriers of the pipeline (mbarriers in shared memory).
 struct Bars {
-    uint64_t d1_full[3], d1_free[3];   // pass-1 accumulator: MMA -> WG0, WG0 -> MMA
-    uint64_t a2_full[2];               // pass-2 operand written: WG0 -> MMA
-    uint64_t d2_full[2], d2_free[2];   // pass-2 accumulator (its completion also frees A2)
-    uint64_t a3_full, a3_free;         // pass-3 operand: WG1 -> MMA, MMA completion -> WG1
-    uint64_t d3p_full, d3p_free;       // + translate in TMEM: MMA -> WGs, WGs -> MMA
-    uint64_t d3m_full[2], d3m_free[2]; // - translate tiles
-    uint64_t pair_done;                // all MMAs of a pair complete: its filter buffer is free
-    uint64_t filt[2], drain;
+    uint64_t full[3], freeb[3];        // TMEM slots: MMA completion -> epilogue, epilogue drained -> MMA
+    uint64_t a2_full[2], a2_free[2];   // pass-2 operand tiles: epilogue -> MMA, MMA completion -> epilogue
+    uint64_t a3_full, a3_free;         // pass-3 operands (both signs)
+    uint64_t filt[2], fdone[2];        // filter buffers: copy landed; all MMAs of the pair using it done
+    uint64_t drain;
 };
 
-// Warp roles: warps 0-3 (WG0) turn pass-1 tiles into pass-2 operands, warps 4-7 (WG1) turn
-// pass-2 tiles into the pass-3 operand, both warpgroups form the products (half the columns
-// each), warp 8 allocates TMEM and issues the MMAs and copies.
+// 8 columns of this thread's lane of the hi and lo parts (at c and c + N), combined as
+// hi + eps lo in FP32; one sign at a time keeps 16 loaded values live next to the accumulators.
+template <int N>
+__device__ __forceinline__ void load_combined(uint32_t taddr, float eps, float (&v)[8]) {
+    float hi[8], lo[8];
+    tc::tmem_ld8(taddr, hi);
+    tc::tmem_ld8(taddr + N, lo);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = fmaf(lo[j], eps, hi[j]);
+}
+
+template <bool BF>
+__device__ __forceinline__ void pack8(const float (&v)[8], uint32_t (&u)[4]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) u[j] = pack2<BF>(v[2 * j], v[2 * j + 1]);
+}
+
 template <int N, bool BF>
-__global__ void __launch_bounds__(288, 1)
-k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs,
-          const unsigned char* __restrict__ filt, const float* __restrict__ wsig, int npairs, int Nrho,
-          float* __restrict__ P, int* __restrict__ flags) {
+__global__ void __launch_bounds__(Geo<N>::THREADS, 1)
+k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const unsigned char* __restrict__ filt,
+          int npairs, int Nrho, float* __restrict__ P, int* __restrict__ flags) {
     using G = Geo<N>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) Bars bars;
     __shared__ uint32_t s_tmem;
-    __shared__ float s_red[8];
+    __shared__ float s_red[G::EPI_WARPS];
     __shared__ int s_abort;
     volatile int* abort = &s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wg = warp >> 2, q = warp & 3;     // warpgroup (0, 1; 2 = MMA warp), lane quarter
-    const int lrow = 32 * q + lane;              // TMEM lane (row) of this thread
+    const bool issuer = warp == G::ISSUER;
     const int r = blockIdx.x;
     const int64_t node = blockIdx.y;
-    const int64_t n3 = (int64_t)N * N * N;
+    constexpr int64_t n3 = (int64_t)N * N * N;
     const float* fb = f + (offs ? offs[node] : node * n3);
     const uint32_t sb = tc::smem_u32(smem);
+    const unsigned char* fglob = filt + (size_t)r * npairs * G::F_BLOCK;
 
-    // ---- set-up: scale, f -> A1 (warps 0-7); barriers, TMEM, first filter copies (warp 8) --
-    float sf = 1.f;
-    if (!BF) {
-        float mx = 0.f;
-        if (warp < 8)
-            for (int e = tid; e < n3; e += 256) mx = fmaxf(mx, fabsf(__ldg(fb + e)));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0 && warp < 8) s_red[warp] = mx;
-        __syncthreads();
-        mx = s_red[0];
-#pragma unroll
-        for (int i = 1; i < 8; ++i) mx = fmaxf(mx, s_red[i]);
-        if (mx > 0.f && isfinite(mx)) sf = exp2f(fminf(60.f, fmaxf(-60.f, floorf(log2f(512.f / mx)))));
-    }
-    const float pass_scale = BF ? 1.f : exp2f(-(float)kFilterShift);   // undo the filter scaling
-    const float out_scale = BF ? 1.f : exp2f(-2.f * kFilterShift) / (sf * sf);
+    // filter copies issued and waited per buffer 0 / 1 (used by the MMA warp and the drain)
+    int copies0 = npairs > 0 ? 1 : 0, copies1 = npairs > 1 ? 1 : 0, waited0 = 0, waited1 = 0;
 
-    if (warp < 8) {
-        for (int it = tid; it < G::N2 * G::KG; it += 256) {
-            const int z = it % N, y = (it / N) % N, kg = it / G::N2;
-            const int m1 = z * N + y;
-            float v[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = __ldg(fb + (size_t)(kg * 8 + i) * G::N2 + y * N + z) * sf;
-            tc::st_shared_v4(sb + G::S_A1 + (m1 >> 3) * G::A1_SBO + kg * G::A1_LBO + (m1 & 7) * 16,
-                             pack2<BF>(v[0], v[1]), pack2<BF>(v[2], v[3]), pack2<BF>(v[4], v[5]), pack2<BF>(v[6], v[7]));
-        }
-    } else {
+    // ---- set-up: barriers, first filter copies, TMEM (MMA warp); max |f| (epilogue warps) -----
+    if (issuer) {
         if (lane == 0) {
             for (int i = 0; i < 3; ++i) {
-                tc::mbar_init(&bars.d1_full[i], 1);
-                tc::mbar_init(&bars.d1_free[i], 4);
+                tc::mbar_init(&bars.full[i], 1);
+                tc::mbar_init(&bars.freeb[i], G::EPI_WARPS);
             }
             for (int i = 0; i < 2; ++i) {
-                tc::mbar_init(&bars.a2_full[i], 4);
-                tc::mbar_init(&bars.d2_full[i], 1);
-                tc::mbar_init(&bars.d2_free[i], 4);
-                tc::mbar_init(&bars.d3m_full[i], 1);
-                tc::mbar_init(&bars.d3m_free[i], 8);
+                tc::mbar_init(&bars.a2_full[i], G::EPI_WARPS);
+                tc::mbar_init(&bars.a2_free[i], 1);
                 tc::mbar_init(&bars.filt[i], 1);
+                tc::mbar_init(&bars.fdone[i], 1);
             }
-            tc::mbar_init(&bars.a3_full, 4);
+            tc::mbar_init(&bars.a3_full, G::EPI_WARPS);
             tc::mbar_init(&bars.a3_free, 1);
-            tc::mbar_init(&bars.d3p_full, 1);
-            tc::mbar_init(&bars.d3p_free, 8);
-            tc::mbar_init(&bars.pair_done, 1);
             tc::mbar_init(&bars.drain, 1);
             tc::fence_mbar_init();
             s_abort = 0;
             for (int p = 0; p < 2 && p < npairs; ++p) {
                 tc::mbar_expect_tx(&bars.filt[p], G::F_BLOCK);
-                tc::bulk_g2s(smem + G::S_F + p * G::F_BLOCK, filt + ((size_t)r * npairs + p) * G::F_BLOCK,
-                             G::F_BLOCK, &bars.filt[p]);
+                tc::bulk_g2s(smem + G::S_F + p * G::F_BLOCK, fglob + (size_t)p * G::F_BLOCK, G::F_BLOCK, &bars.filt[p]);
             }
         }
         __syncwarp();
         tc::tmem_alloc(&s_tmem, G::TMEM_COLS);
+    } else if (!BF) {
+        float mx = 0.f;
+        for (int e = tid; e < n3; e += 32 * G::EPI_WARPS) mx = fmaxf(mx, fabsf(__ldg(fb + e)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) s_red[warp] = mx;
     }
-    tc::fence_proxy_async();
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    float acc[G::TILES][G::HALF];
+    float sf = 1.f;
+    if (!BF) {
+        float mx = s_red[0];
 #pragma unroll
-    for (int u = 0; u < G::TILES; ++u)
-#pragma unroll
-        for (int j = 0; j < G::HALF; ++j) acc[u][j] = 0.f;
+        for (int i = 1; i < G::EPI_WARPS; ++i) mx = fmaxf(mx, s_red[i]);
+        if (mx > 0.f && isfinite(mx)) sf = exp2f(fminf(60.f, fmaxf(-60.f, floorf(log2f(512.f / mx)))));
+    }
+    const float eps = exp2f(-(float)(BF ? kLoShiftBF16 : kLoShiftF16));
+    const float out_scale = BF ? 1.f : 1.f / (sf * sf);
 
-    // filter copies issued and waited per buffer (only warp 8, lane 0 uses these)
-    int filt_copies[2] = {npairs > 0 ? 1 : 0, npairs > 1 ? 1 : 0}, filt_waited[2] = {0, 0};
+    // ---- f -> TMEM as the pass-1 A operand: tile t, lane l = yl N + z holds f[0..N)[t ZT + yl][z] --
+    if (!issuer) {
+        const int q = warp & 3, w = warp >> 2, l = 32 * q + lane, yl = l / N, z = l % N;
+        for (int t = w; t < G::T; t += G::NWG) {
+            const float* src = fb + (size_t)(t * G::ZT + yl) * N + z;
+            uint32_t v[N / 2];
+#pragma unroll
+            for (int c = 0; c < N / 2; ++c)
+                v[c] = pack2<BF>(__ldg(src + (size_t)(2 * c) * G::N2) * sf, __ldg(src + (size_t)(2 * c + 1) * G::N2) * sf);
+            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + G::C_F + t * (N / 2);
+            if constexpr (N == 32) tc::tmem_st16(ta, v);
+            else tc::tmem_st8(ta, v);
+        }
+        tc::tmem_wait_st();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
 
-    if (warp == 8) {
-        // ================================ MMA warp ======================================
-        if (lane == 0) {
-            int d1_use[3] = {0, 0, 0}, d2_use[2] = {0, 0}, d3m_use[2] = {0, 0};
-            uint32_t ph_d1free[3] = {0, 0, 0}, ph_a2full[2] = {0, 0}, ph_d2free[2] = {0, 0};
-            uint32_t ph_a3full = 0, ph_d3pfree = 0, ph_d3mfree[2] = {0, 0}, ph_pair = 0;
-            auto issue = [&](uint32_t dcol, uint32_t a_start, uint32_t a_lbo, uint32_t a_sbo, bool a_mn, int axis,
-                             int fbuf, int sg) {
-                const uint32_t idesc = tc::idesc_f16(BF, a_mn, sg == 1, N, 128);
+    if (issuer) {
+        // ================================ MMA warp (converged) ================================
+        // per-slot / per-buffer state as bit masks (bit i = slot or buffer i), kept in registers
+        uint32_t used = 0, ph_free = 0, ph_a2full = 0, ph_a3full = 0, ph_fdone = 0;
+        constexpr uint32_t id1 = tc::idesc_f16(BF, false, false, 4 * N, 128);
+        constexpr uint32_t id23 = tc::idesc_f16(BF, true, false, 2 * N, 128);
+#define DGFS_WAITW(bar, ph)                                             \
+    do {                                                                \
+        if (!tc::warp_wait((bar), (ph), abort)) goto mma_done;          \
+    } while (0)
+#define DGFS_ACQUIRE(s)                                                 \
+    do {                                                                \
+        if (used & (1u << (s))) {                                       \
+            DGFS_WAITW(&bars.freeb[s], (ph_free >> (s)) & 1u);          \
+            ph_free ^= 1u << (s);                                       \
+        }                                                               \
+        used |= 1u << (s);                                              \
+        tc::tc_fence_after();                                           \
+    } while (0)
+        for (int p = 0; p < npairs; ++p) {
+            const int fbuf = p & 1;
+            DGFS_WAITW(&bars.filt[fbuf], (uint32_t)((fbuf ? waited1 : waited0) & 1));
+            if (fbuf) ++waited1;
+            else ++waited0;
+            tc::tc_fence_after();
+            const uint32_t fsm = sb + G::S_F + fbuf * G::F_BLOCK;
+            // front: pass 1 of tile t (slot 0) and pass 2 of tile t - 1 (slot 1 + (t - 1) % 2)
+            for (int t = 0; t <= G::T; ++t) {
+                if (t < G::T) {
+                    DGFS_ACQUIRE(0);
 #pragma unroll
-                for (int ks = 0; ks < G::KSTEPS; ++ks)
-#pragma unroll
-                    for (int pp = 0; pp < 2; ++pp) {
-                        const uint64_t da = tc::sdesc(a_start + ks * 2 * a_lbo, a_lbo, a_sbo);
-                        const uint32_t fbase = sb + G::S_F + fbuf * G::F_BLOCK + (axis * 2 + pp) * G::F_MAT;
-                        const uint64_t db = sg == 0 ? tc::sdesc(fbase + ks * 2 * G::F_LBO, G::F_LBO, G::F_SBO)
-                                                    : tc::sdesc(fbase + ks * 2 * G::F_SBO, G::F_SBO, G::F_LBO);
-                        tc::mma_f16(tmem + dcol, da, db, idesc, (ks | pp) != 0);
-                    }
-            };
-            for (int p = 0; p < npairs; ++p) {
-                const int fbuf = p & 1;
-                if (!tc::mbar_wait_or_abort(&bars.filt[fbuf], (uint32_t)(filt_waited[fbuf] & 1), abort)) goto mma_done;
-                filt_waited[fbuf]++;
-                for (int sg = 0; sg < 2; ++sg) {
-                    for (int step = 0; step <= G::TILES; ++step) {
-                        if (step < G::TILES) {                       // pass 1, tile t
-                            const int t = step, b = t % 3;
-                            if (d1_use[b]++ > 0) {
-                                if (!tc::mbar_wait_or_abort(&bars.d1_free[b], ph_d1free[b], abort)) goto mma_done;
-                                ph_d1free[b] ^= 1;
-                            }
-                            tc::tc_fence_after();
-                            issue(G::C_D1 + b * N, sb + G::S_A1 + t * G::A1_TILE, G::A1_LBO, G::A1_SBO, false, 0, fbuf, sg);
-                            tc::mma_commit(&bars.d1_full[b]);
-                            // once pair p - 1 is complete its filter buffer takes pair p + 1
-                            // (waited here, after the first tiles of pair p are queued, so the
-                            // tensor pipe never drains; every pair_done phase is waited in order)
-                            if (sg == 0 && t == 0 && p >= 1) {
-                                if (!tc::mbar_wait_or_abort(&bars.pair_done, ph_pair, abort)) goto mma_done;
-                                ph_pair ^= 1;
-                                if (p + 1 < npairs) {
-                                    const int nb = (p + 1) & 1;
-                                    tc::mbar_expect_tx(&bars.filt[nb], G::F_BLOCK);
-                                    tc::bulk_g2s(smem + G::S_F + nb * G::F_BLOCK,
-                                                 filt + ((size_t)r * npairs + p + 1) * G::F_BLOCK, G::F_BLOCK,
-                                                 &bars.filt[nb]);
-                                    filt_copies[nb]++;
-                                }
-                            }
+                    for (int ks = 0; ks < G::KSTEPS; ++ks)
+                        tc::mma_ts_warp(tmem, tmem + G::C_F + t * (N / 2) + 8 * ks,
+                                        tc::sdesc(fsm + G::OFF_B1 + ks * 2 * G::FB_LBO, G::FB_LBO, G::FB_SBO), id1, ks);
+                    tc::mma_commit_warp(&bars.full[0]);
+                    // the other filter buffer (pair p - 1, whose MMAs are complete by now) takes pair p + 1
+                    if (t == 0 && p >= 1 && p + 1 < npairs) {
+                        const int nb = (p + 1) & 1;
+                        DGFS_WAITW(&bars.fdone[nb], (ph_fdone >> nb) & 1u);
+                        ph_fdone ^= 1u << nb;
+                        if (tc::elect_one()) {
+                            tc::mbar_expect_tx(&bars.filt[nb], G::F_BLOCK);
+                            tc::bulk_g2s(smem + G::S_F + nb * G::F_BLOCK, fglob + (size_t)(p + 1) * G::F_BLOCK,
+                                         G::F_BLOCK, &bars.filt[nb]);
                         }
-                        if (step >= 1) {                             // pass 2, tile t - 1
-                            const int t = step - 1, b = t & 1;
-                            if (!tc::mbar_wait_or_abort(&bars.a2_full[b], ph_a2full[b], abort)) goto mma_done;
-                            ph_a2full[b] ^= 1;
-                            if (d2_use[b]++ > 0) {
-                                if (!tc::mbar_wait_or_abort(&bars.d2_free[b], ph_d2free[b], abort)) goto mma_done;
-                                ph_d2free[b] ^= 1;
-                            }
-                            tc::tc_fence_after();
-                            issue(G::C_D2 + b * N, sb + G::S_A2 + b * G::A2_BYTES, G::A2_LBO, G::A2_SBO, true, 1, fbuf, sg);
-                            tc::mma_commit(&bars.d2_full[b]);
-                        }
-                    }
-                    if (!tc::mbar_wait_or_abort(&bars.a3_full, ph_a3full, abort)) goto mma_done;
-                    ph_a3full ^= 1;
-                    tc::tc_fence_after();
-                    if (sg == 0) {
-                        if (p > 0) {                                 // the previous pair's products are done
-                            if (!tc::mbar_wait_or_abort(&bars.d3p_free, ph_d3pfree, abort)) goto mma_done;
-                            ph_d3pfree ^= 1;
-                        }
-                        for (int u = 0; u < G::TILES; ++u)
-                            issue(G::C_D3P + u * N, sb + G::S_A3 + u * G::A3_TS, G::A3_LBO, G::A3_SBO, true, 2, fbuf, 0);
-                        tc::mma_commit(&bars.d3p_full);
-                        tc::mma_commit(&bars.a3_free);
-                    } else {
-                        for (int u = 0; u < G::TILES; ++u) {
-                            const int b = u & 1;
-                            if (d3m_use[b]++ > 0) {
-                                if (!tc::mbar_wait_or_abort(&bars.d3m_free[b], ph_d3mfree[b], abort)) goto mma_done;
-                                ph_d3mfree[b] ^= 1;
-                            }
-                            tc::tc_fence_after();
-                            issue(G::C_D3M + b * N, sb + G::S_A3 + u * G::A3_TS, G::A3_LBO, G::A3_SBO, true, 2, fbuf, 1);
-                            tc::mma_commit(&bars.d3m_full[b]);
-                        }
-                        tc::mma_commit(&bars.a3_free);
-                        tc::mma_commit(&bars.pair_done);
+                        __syncwarp();
+                        if (nb) ++copies1;
+                        else ++copies0;
                     }
                 }
+                if (t >= 1) {
+                    const int a = (t - 1) & 1, s = 1 + a;
+                    DGFS_WAITW(&bars.a2_full[a], (ph_a2full >> a) & 1u);
+                    ph_a2full ^= 1u << a;
+                    DGFS_ACQUIRE(s);
+#pragma unroll
+                    for (int g = 0; g < 2; ++g)
+#pragma unroll
+                        for (int ks = 0; ks < G::KSTEPS; ++ks)
+                            tc::mma_ss_warp(tmem + s * G::SLOT + g * 2 * N,
+                                            tc::sdesc(sb + G::S_A2 + (a * 2 + g) * G::A2_BYTES + ks * 2 * G::A2_LBO,
+                                                      G::A2_LBO, G::A2_SBO),
+                                            tc::sdesc(fsm + G::OFF_B2 + g * G::B23_BYTES + ks * 2 * G::FB_LBO, G::FB_LBO,
+                                                      G::FB_SBO),
+                                            id23, ks);
+                    tc::mma_commit_warp(&bars.full[s]);
+                    tc::mma_commit_warp(&bars.a2_free[a]);
+                }
             }
-        mma_done:;
+            // back: pass 3 of tile u into slot 2 (u even) or 0 (u odd)
+            DGFS_WAITW(&bars.a3_full, ph_a3full);
+            ph_a3full ^= 1;
+            tc::tc_fence_after();
+            for (int u = 0; u < G::T; ++u) {
+                const int s = (u & 1) ? 0 : 2;
+                DGFS_ACQUIRE(s);
+#pragma unroll
+                for (int g = 0; g < 2; ++g)
+#pragma unroll
+                    for (int ks = 0; ks < G::KSTEPS; ++ks)
+                        tc::mma_ss_warp(tmem + s * G::SLOT + g * 2 * N,
+                                        tc::sdesc(sb + G::S_A3 + g * G::A3_BYTES + u * G::A3_TS + ks * 2 * G::A3_LBO,
+                                                  G::A3_LBO, G::A3_SBO),
+                                        tc::sdesc(fsm + G::OFF_B3 + g * G::B23_BYTES + ks * 2 * G::FB_LBO, G::FB_LBO,
+                                                  G::FB_SBO),
+                                        id23, ks);
+                tc::mma_commit_warp(&bars.full[s]);
+            }
+            tc::mma_commit_warp(&bars.a3_free);
+            tc::mma_commit_warp(&bars.fdone[fbuf]);
         }
-        __syncwarp();
+#undef DGFS_ACQUIRE
+#undef DGFS_WAITW
+    mma_done:;
     } else {
-        // ============================ epilogue warpgroups ==================================
-        uint32_t ph_d1full[3] = {0, 0, 0}, ph_d2full[2] = {0, 0}, ph_a3free = 0, ph_d3pfull = 0;
-        uint32_t ph_d3mfull[2] = {0, 0};
-        int a2_use[2] = {0, 0};
-        int signs_done = 0;
+        // ============================== epilogue warpgroups ===================================
+        const int q = warp & 3, w = warp >> 2, c0 = 8 * w;
+        const int l = 32 * q + lane, yl = l / N, lz = l % N;   // tile row: (yl, z) in pass 1, (yl, x') in pass 2
         const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+        // store offsets: A2 unit (rows yl N + c0 .. +8, k = z = lz); A3 unit (rows lz N + c0 .. +8)
+        const uint32_t a2_off = ((uint32_t)(yl * N + c0) >> 3) * G::A2_SBO + (lz >> 3) * G::A2_LBO + (lz & 7) * 16;
+        const int mg3 = (lz * N + c0) >> 3;
+        const uint32_t a3_off = (mg3 >> 4) * G::A3_TS + (mg3 & 15) * G::A3_SBO;
+        uint32_t ph_full = 0, ph_a2free = 0, a2_used = 0, ph_a3free = 0;   // bit masks, as in the MMA warp
+        float acc[G::T][8];
+#pragma unroll
+        for (int u = 0; u < G::T; ++u)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[u][j] = 0.f;
+#define DGFS_WAITE(bar, ph)                                             \
+    do {                                                                \
+        if (!tc::warp_wait((bar), (ph), abort)) goto epi_done;          \
+    } while (0)
         for (int p = 0; p < npairs; ++p) {
-            const float w2 = 2.f * wsig[p];
-            for (int sg = 0; sg < 2; ++sg) {
-                if (wg == 0) {
-                    // pass-1 tiles -> pass-2 operands
-                    for (int t = 0; t < G::TILES; ++t) {
-                        const int b = t % 3, b2 = t & 1;
-                        if (!tc::mbar_wait_or_abort(&bars.d1_full[b], ph_d1full[b], abort)) goto epi_done;
-                        ph_d1full[b] ^= 1;
-                        tc::tc_fence_after();
-                        float v[N];
-                        if constexpr (N == 32) tc::tmem_ld32(trow + G::C_D1 + b * N, v);
-                        else tc::tmem_ld16(trow + G::C_D1 + b * N, *reinterpret_cast<float(*)[16]>(v));
-                        tc::tmem_wait_ld();
-                        tc::tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&bars.d1_free[b]);
-                        // A2[b2] is free once the pass-2 MMA of its previous tile has completed
-                        if (a2_use[b2]++ > 0) {
-                            if (!tc::mbar_wait_or_abort(&bars.d2_full[b2], ph_d2full[b2], abort)) goto epi_done;
-                            ph_d2full[b2] ^= 1;
-                        }
-                        const int m1 = t * 128 + lrow, y = m1 % N, zl = lrow / N;
-#pragma unroll
-                        for (int c = 0; c < N / 8; ++c) {
-                            const int mg = (zl * N + 8 * c) >> 3;
-                            const float* w = v + 8 * c;
-                            tc::st_shared_v4(sb + G::S_A2 + b2 * G::A2_BYTES + mg * G::A2_SBO + (y >> 3) * G::A2_LBO + (y & 7) * 16,
-                                             pack2<BF>(w[0] * pass_scale, w[1] * pass_scale), pack2<BF>(w[2] * pass_scale, w[3] * pass_scale),
-                                             pack2<BF>(w[4] * pass_scale, w[5] * pass_scale), pack2<BF>(w[6] * pass_scale, w[7] * pass_scale));
-                        }
-                        tc::fence_proxy_async();
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&bars.a2_full[b2]);
+            for (int t = 0; t <= G::T; ++t) {
+                if (t < G::T) {
+                    // pass-1 tile t -> pass-2 operands of both signs
+                    DGFS_WAITE(&bars.full[0], ph_full & 1u);
+                    ph_full ^= 1u;
+                    tc::tc_fence_after();
+                    uint32_t up[4], um[4];
+                    {
+                        float v[8];
+                        load_combined<N>(trow + c0, eps, v);
+                        pack8<BF>(v, up);
+                        load_combined<N>(trow + 2 * N + c0, eps, v);
+                        pack8<BF>(v, um);
                     }
-                } else {
-                    // pass-2 tiles -> the pass-3 operand (A3 must be free of the last pass 3)
-                    if (signs_done > 0) {
-                        if (!tc::mbar_wait_or_abort(&bars.a3_free, ph_a3free, abort)) goto epi_done;
-                        ph_a3free ^= 1;
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&bars.freeb[0]);
+                    const int a = t & 1;
+                    if (a2_used & (1u << a)) {
+                        DGFS_WAITE(&bars.a2_free[a], (ph_a2free >> a) & 1u);
+                        ph_a2free ^= 1u << a;
                     }
-                    for (int t = 0; t < G::TILES; ++t) {
-                        const int b = t & 1;
-                        if (!tc::mbar_wait_or_abort(&bars.d2_full[b], ph_d2full[b], abort)) goto epi_done;
-                        ph_d2full[b] ^= 1;
-                        tc::tc_fence_after();
-                        float v[N];
-                        if constexpr (N == 32) tc::tmem_ld32(trow + G::C_D2 + b * N, v);
-                        else tc::tmem_ld16(trow + G::C_D2 + b * N, *reinterpret_cast<float(*)[16]>(v));
-                        tc::tmem_wait_ld();
-                        tc::tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&bars.d2_free[b]);
-                        const int zl = lrow / N, xp = lrow % N, z = t * G::ZT + zl;
-#pragma unroll
-                        for (int c = 0; c < N / 8; ++c) {
-                            const int mg = (xp * N + 8 * c) >> 3;
-                            const int u = mg >> 4, mgl = mg & 15;
-                            const float* w = v + 8 * c;
-                            tc::st_shared_v4(sb + G::S_A3 + u * G::A3_TS + mgl * G::A3_SBO + (z >> 3) * G::A3_LBO + (z & 7) * 16,
-                                             pack2<BF>(w[0] * pass_scale, w[1] * pass_scale), pack2<BF>(w[2] * pass_scale, w[3] * pass_scale),
-                                             pack2<BF>(w[4] * pass_scale, w[5] * pass_scale), pack2<BF>(w[6] * pass_scale, w[7] * pass_scale));
-                        }
-                    }
+                    a2_used |= 1u << a;
+                    const uint32_t dst = sb + G::S_A2 + a * 2 * G::A2_BYTES + a2_off;
+                    tc::st_shared_v4(dst, up[0], up[1], up[2], up[3]);
+                    tc::st_shared_v4(dst + G::A2_BYTES, um[0], um[1], um[2], um[3]);
                     tc::fence_proxy_async();
                     __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&bars.a3_full);
+                    if (lane == 0) tc::mbar_arrive(&bars.a2_full[a]);
                 }
-                signs_done++;
-                if (sg == 1) {
-                    // products of the two translates, half of the columns per warpgroup
-                    if (!tc::mbar_wait_or_abort(&bars.d3p_full, ph_d3pfull, abort)) goto epi_done;
-                    ph_d3pfull ^= 1;
-#pragma unroll
-                    for (int u = 0; u < G::TILES; ++u) {
-                        const int b = u & 1;
-                        if (!tc::mbar_wait_or_abort(&bars.d3m_full[b], ph_d3mfull[b], abort)) goto epi_done;
-                        ph_d3mfull[b] ^= 1;
-                        tc::tc_fence_after();
-                        float fm[G::HALF], fp[G::HALF];
-                        if constexpr (G::HALF == 16) {
-                            tc::tmem_ld16(trow + G::C_D3M + b * N + wg * G::HALF, *reinterpret_cast<float(*)[16]>(fm));
-                            tc::tmem_ld16(trow + G::C_D3P + u * N + wg * G::HALF, *reinterpret_cast<float(*)[16]>(fp));
-                        } else {
-                            tc::tmem_ld8(trow + G::C_D3M + b * N + wg * G::HALF, *reinterpret_cast<float(*)[8]>(fm));
-                            tc::tmem_ld8(trow + G::C_D3P + u * N + wg * G::HALF, *reinterpret_cast<float(*)[8]>(fp));
-                        }
-                        tc::tmem_wait_ld();
-                        tc::tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&bars.d3m_free[b]);
-#pragma unroll
-                        for (int j = 0; j < G::HALF; ++j) acc[u][j] = fmaf(w2 * fp[j], fm[j], acc[u][j]);
+                if (t >= 1) {
+                    // pass-2 tile t - 1 -> rows of the pass-3 operands of both signs
+                    const int tt = t - 1, s = 1 + (tt & 1);
+                    DGFS_WAITE(&bars.full[s], (ph_full >> s) & 1u);
+                    ph_full ^= 1u << s;
+                    tc::tc_fence_after();
+                    uint32_t up[4], um[4];
+                    {
+                        float v[8];
+                        load_combined<N>(trow + s * G::SLOT + c0, eps, v);
+                        pack8<BF>(v, up);
+                        load_combined<N>(trow + s * G::SLOT + 2 * N + c0, eps, v);
+                        pack8<BF>(v, um);
                     }
+                    tc::tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&bars.d3p_free);
+                    if (lane == 0) tc::mbar_arrive(&bars.freeb[s]);
+                    if (tt == 0 && p > 0) {   // the previous pair's pass 3 has read the operands
+                        DGFS_WAITE(&bars.a3_free, ph_a3free);
+                        ph_a3free ^= 1;
+                    }
+                    const int y = tt * G::ZT + yl;
+                    const uint32_t dst = sb + G::S_A3 + a3_off + (y >> 3) * G::A3_LBO + (y & 7) * 16;
+                    tc::st_shared_v4(dst, up[0], up[1], up[2], up[3]);
+                    tc::st_shared_v4(dst + G::A3_BYTES, um[0], um[1], um[2], um[3]);
+                    if (tt == G::T - 1) {
+                        tc::fence_proxy_async();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&bars.a3_full);
+                    }
                 }
             }
+            // pass-3 tiles: products of the two translates
+#pragma unroll
+            for (int u = 0; u < G::T; ++u) {
+                const int s = (u & 1) ? 0 : 2;
+                DGFS_WAITE(&bars.full[s], (ph_full >> s) & 1u);
+                ph_full ^= 1u << s;
+                tc::tc_fence_after();
+                float vp[8], vm[8];
+                load_combined<N>(trow + s * G::SLOT + c0, eps, vp);
+                load_combined<N>(trow + s * G::SLOT + 2 * N + c0, eps, vm);
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&bars.freeb[s]);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[u][j] = fmaf(vp[j], vm[j], acc[u][j]);
+            }
         }
-        if (!*abort) {   // results: P[node][r][x'][y'][z'] = acc * out_scale (this warpgroup's half)
+#undef DGFS_WAITE
+        if (!*abort) {   // P[node][r][x'][y'][z'], row m3 = x' N + z' of tile u, column y' = c0 + j
             float* dst = P + ((size_t)node * Nrho + r) * n3;
 #pragma unroll
-            for (int u = 0; u < G::TILES; ++u) {
-                const int m3 = u * 128 + lrow;
-                float4* o = reinterpret_cast<float4*>(dst + (size_t)m3 * N + wg * G::HALF);
+            for (int u = 0; u < G::T; ++u) {
+                const int m3 = u * 128 + l, xp = m3 / N, zp = m3 % N;
+                float* o = dst + (size_t)xp * G::N2 + (size_t)c0 * N + zp;
 #pragma unroll
-                for (int j = 0; j < G::HALF; j += 4)
-                    o[j / 4] = make_float4(acc[u][j] * out_scale, acc[u][j + 1] * out_scale,
-                                           acc[u][j + 2] * out_scale, acc[u][j + 3] * out_scale);
+                for (int j = 0; j < 8; ++j) o[(size_t)j * N] = acc[u][j] * out_scale;
             }
         }
     epi_done:;
@@ -412,15 +415,17 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs,
     // ---- drain: no MMA or copy of this CTA may be in flight when TMEM is freed -----------
     tc::tc_fence_before();
     __syncthreads();
-    if (warp == 8) {
-        if (lane == 0) {
+    if (issuer) {
+        if (tc::elect_one()) {   // the lane that issued every MMA and copy
             if (*abort) atomicOr(flags, 1);
             tc::mma_commit(&bars.drain);
             if (!tc::mbar_wait(&bars.drain, 0)) atomicOr(flags, 1);
-            // wait for every issued filter copy that the pipeline did not wait for
             for (int i = 0; i < 2; ++i)
-                for (int k = filt_waited[i]; k < filt_copies[i]; ++k)
-                    if (!tc::mbar_wait(&bars.filt[i], (uint32_t)(k & 1))) { atomicOr(flags, 1); break; }
+                for (int k = i ? waited1 : waited0; k < (i ? copies1 : copies0); ++k)
+                    if (!tc::mbar_wait(&bars.filt[i], (uint32_t)(k & 1))) {
+                        atomicOr(flags, 1);
+                        break;
+                    }
         }
         __syncwarp();
         tc::tc_fence_after();
@@ -438,9 +443,9 @@ cudaError_t launch_n(const TcTables& t, const float* f, const int64_t* offs, int
     const int64_t n3 = (int64_t)N * N * N;
     for (int64_t n0 = 0; n0 < nodes; n0 += 65535) {
         const int64_t nn = nodes - n0 < 65535 ? nodes - n0 : 65535;
-        kern<<<dim3(t.Nrho, (unsigned)nn), 288, G::S_TOTAL, s>>>(
+        kern<<<dim3(t.Nrho, (unsigned)nn), G::THREADS, G::S_TOTAL, s>>>(
             f + (offs ? 0 : n0 * n3), offs ? offs + n0 : nullptr, static_cast<const unsigned char*>(t.mats),
-            t.wsig, t.npairs, t.Nrho, P + n0 * t.Nrho * n3, flags);
+            t.npairs, t.Nrho, P + n0 * t.Nrho * n3, flags);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -449,7 +454,7 @@ cudaError_t launch_n(const TcTables& t, const float* f, const int64_t* offs, int
 
 // host-side rounding of a double to the 16-bit operand types
 uint16_t to_half_bits(double x) {
-    __half h = __double2half((double)x);
+    __half h = __double2half(x);
     uint16_t b;
     std::memcpy(&b, &h, 2);
     return b;
@@ -480,42 +485,57 @@ int tc_extra_launches(int) { return 0; }
 size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>& blob, TcTables& t) {
     const int N = hp.N, np = hp.npairs, Nr = hp.Nrho;
     const bool bf = prec == DGFS_PREC_BF16S;
-    const double fscale = bf ? 1.0 : std::ldexp(1.0, kFilterShift);
-    const size_t mat = (size_t)N * N * 2, block = 6 * mat;
-    const size_t mats_bytes = (size_t)Nr * np * block;
-    const size_t wsig_off = (mats_bytes + 255) / 256 * 256;
-    const size_t total = wsig_off + (size_t)np * sizeof(float);
-    blob.assign(total, 0);
-    const uint32_t lbo = 128, sbo = 16 * N;
+    const double lo_scale = std::ldexp(1.0, bf ? kLoShiftBF16 : kLoShiftF16);
+    const size_t n2b = (size_t)N * N * 2;            // bytes of one N x N 16-bit matrix
+    const size_t b1 = 4 * n2b, b23 = 2 * n2b, block = b1 + 4 * b23;
+    blob.assign((size_t)Nr * np * block, 0);
+    const size_t sbo = 16 * (size_t)N, lbo = 128;
+    // K-major core-matrix layout of a B operand: row n (output index), column k (input index)
+    auto put = [&](unsigned char* base, int n, int k, uint16_t bits) {
+        std::memcpy(base + (n / 8) * sbo + (k / 8) * lbo + (n % 8) * 16 + (k % 8) * 2, &bits, 2);
+    };
+    // hi + 2^-e lo split of v, both rounded to the operand type
+    auto split = [&](double v, uint16_t& hi, uint16_t& lo) {
+        hi = bf ? to_bf16_bits(v) : to_half_bits(v);
+        const double hv = bf ? bf16_bits_value(hi) : half_bits_value(hi);
+        lo = bf ? to_bf16_bits((v - hv) * lo_scale) : to_half_bits((v - hv) * lo_scale);
+    };
     for (int r = 0; r < Nr; ++r)
-        for (int p = 0; p < np; ++p)
-            for (int a = 0; a < 3; ++a) {
-                const double* fl = &hp.filt[(((size_t)r * np + p) * 3 + a) * N];
+        for (int p = 0; p < np; ++p) {
+            unsigned char* blk = blob.data() + ((size_t)r * np + p) * block;
+            // F_+[i][j] = a[(i - j) mod N] (translate by +s along the axis); F_- = F_+^T (T_-s = T_s^T)
+            auto F = [&](int axis, int sign, int i, int j) {
+                const double* fl = &hp.filt[(((size_t)r * np + p) * 3 + axis) * N];
+                const int d = sign == 0 ? i - j : j - i;
+                return fl[((d % N) + N) % N];
+            };
+            const double w2 = 2.0 * hp.wsig[p];
+            for (int g = 0; g < 2; ++g)
                 for (int i = 0; i < N; ++i)
                     for (int j = 0; j < N; ++j) {
-                        const double v = fl[((i - j) % N + N) % N] * fscale;   // A_+[i][j] = a[(i - j) mod N]
-                        const uint16_t hi = bf ? to_bf16_bits(v) : to_half_bits(v);
-                        const double hv = bf ? bf16_bits_value(hi) : half_bits_value(hi);
-                        const uint16_t lo = bf ? to_bf16_bits(v - hv) : to_half_bits(v - hv);
-                        const size_t off = (i / 8) * sbo + (j / 8) * lbo + (i % 8) * 16 + (j % 8) * 2;
-                        unsigned char* bp = blob.data() + ((size_t)r * np + p) * block + (size_t)(a * 2) * mat;
-                        std::memcpy(bp + off, &hi, 2);
-                        std::memcpy(bp + mat + off, &lo, 2);
+                        uint16_t hi, lo;
+                        // pass 1 (x, axis 0): parts (+hi, +lo, -hi, -lo); the + filter carries 2 w_p
+                        split(F(0, g, i, j) * (g == 0 ? w2 : 1.0), hi, lo);
+                        put(blk, (2 * g) * N + i, j, hi);
+                        put(blk, (2 * g + 1) * N + i, j, lo);
+                        // pass 2 (z, axis 2) and pass 3 (y, axis 1): parts (hi, lo) per sign
+                        split(F(2, g, i, j), hi, lo);
+                        put(blk + b1 + g * b23, i, j, hi);
+                        put(blk + b1 + g * b23, N + i, j, lo);
+                        split(F(1, g, i, j), hi, lo);
+                        put(blk + b1 + 2 * b23 + g * b23, i, j, hi);
+                        put(blk + b1 + 2 * b23 + g * b23, N + i, j, lo);
                     }
-            }
-    float* w = reinterpret_cast<float*>(blob.data() + wsig_off);
-    for (int p = 0; p < np; ++p) w[p] = (float)hp.wsig[p];
+        }
     t.N = N;
     t.Nrho = Nr;
     t.npairs = np;
     t.mats = reinterpret_cast<const void*>((uintptr_t)0);
-    t.wsig = reinterpret_cast<const float*>((uintptr_t)wsig_off);
-    return total;
+    return blob.size();
 }
 
 void rebase_tc_tables(TcTables& t, void* base) {
     t.mats = static_cast<unsigned char*>(base) + reinterpret_cast<uintptr_t>(t.mats);
-    t.wsig = reinterpret_cast<const float*>(static_cast<unsigned char*>(base) + reinterpret_cast<uintptr_t>(t.wsig));
 }
 
 cudaError_t launch_tc_gain_products(const TcTables& t, int prec, const float* f, const float* g,
