@@ -10,18 +10,23 @@
 //   pass 3 (y): D3[(x',z')][y'] = sum_y D2[(y,x')][z'] Fy[y'][y] A = MN-major full field in SMEM
 //
 // Data operands are 16-bit (fp16 with a per-node power-of-two scale, or bf16). Every filter F is
-// split into a hi and a lo 16-bit part, and the parts are stacked along the MMA's N dimension, so
-// one MMA yields both products: pass 1 stacks {+hi, +lo, -hi, -lo} (N = 4 n), passes 2 and 3 stack
-// {hi, lo} of one sign (N = 2 n). The epilogue combines hi + 2^-e lo in FP32. The + sign's x filter
-// carries the factor 2 w_p, so the products need no further weighting.
+// split into a hi and a lo 16-bit part. Pass 1 stacks the two signs along the MMA's N dimension
+// (N = 2 n) and accumulates hi and lo in the same accumulator (two MMAs; both parts carry 2^8 in
+// fp16, undone in the epilogue); its A operand comes from TMEM, so these MMAs are compute-bound.
+// Passes 2 and 3 stack {hi, lo} of one sign along N (N = 2 n): one MMA per K step reads the
+// shared-memory A operand once, and the epilogue combines hi + 2^-e lo in FP32. The + sign's x
+// filter carries the factor 2 w_p, so the products need no further weighting.
 //
-// One CTA per (radial point, node): 4 n/8 epilogue warpgroups (each owns 8 of the n output
-// columns of every tile) and one MMA warp. Three 4n-column TMEM slots hold the accumulators; the
-// slots alternate between the passes so that an MMA never waits for the epilogue of the
-// accumulator it is about to overwrite when another slot is free. Both signs' pass-3 operands
-// (full fields) stay in shared memory until the products of the pair are formed. All hand-offs
-// are mbarriers; every wait is bounded: on timeout the CTA raises flag bit 0, every role stops,
-// the MMAs and copies in flight are drained (bounded), TMEM is freed and P is not written.
+// One CTA per (radial point, node): two epilogue warpgroups and one MMA warp. Warpgroup w owns the
+// tiles t = w (mod 2) of every pass (all n columns, one TMEM lane per thread), so the two
+// warpgroups form two independent pipelines whose MMA <-> epilogue hand-offs overlap. Each
+// warpgroup has its own TMEM slots: one for pass 1 (2n columns) and one shared by passes 2 and 3
+// (4n columns). Both signs' pass-3 operands (full fields) stay in shared memory until the
+// products are formed. All hand-offs
+// are mbarriers; every lane of the epilogue warps arrives and every wait loop branches on warp
+// votes only, so no branch diverges around the .sync.aligned tcgen05 instructions. Every wait is
+// bounded: on timeout the CTA raises flag bit 0, every role stops, the MMAs and copies in flight
+// are drained (bounded), TMEM is freed and P is not written.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -36,7 +41,9 @@ namespace dgfs {
 
 namespace {
 
-// lo filter parts are stored times 2^e (keeps them normal in fp16; bf16 has the exponent range)
+// fp16 filters: pass 1 stores hi and lo times 2^8, passes 2 and 3 store lo times 2^11 (both keep
+// the lo parts normal); bf16 has the exponent range and stores pass-2/3 lo parts times 2^8
+constexpr int kP1ShiftF16 = 8;
 constexpr int kLoShiftF16 = 11;
 constexpr int kLoShiftBF16 = 8;
 
@@ -48,12 +55,13 @@ struct Geo {
     static constexpr int ZT = 128 / N;            // y values per pass-1/2 tile
     static constexpr int KSTEPS = N / 16;         // K = 16 steps of one contraction
     static constexpr int KG = N / 8;              // core-matrix groups along K
-    static constexpr int NWG = N / 8;             // epilogue warpgroups (8 output columns each)
-    static constexpr int EPI_WARPS = 4 * NWG;
+    static constexpr int TW = T / 2;              // tiles per epilogue warpgroup
+    static constexpr int EPI_WARPS = 8;           // warpgroup w = warp / 4 owns tiles t = w (mod 2)
     static constexpr int THREADS = 32 * EPI_WARPS + 32;
     static constexpr int ISSUER = EPI_WARPS;      // warp index of the MMA warp
     // filter block of one (r, pair), K-major B operands: row n, column k at
-    // (n/8) FB_SBO + (k/8) FB_LBO + (n%8) 16 + (k%8) 2
+    // (n/8) FB_SBO + (k/8) FB_LBO + (n%8) 16 + (k%8) 2. B1 rows: +hi, -hi, +lo, -lo (n each);
+    // B2 and B3, per sign: hi, lo (n each)
     static constexpr uint32_t FB_LBO = 128, FB_SBO = 16 * N;
     static constexpr uint32_t B1_BYTES = 4 * N2 * 2, B23_BYTES = 2 * N2 * 2;
     static constexpr uint32_t OFF_B1 = 0, OFF_B2 = B1_BYTES, OFF_B3 = B1_BYTES + 2 * B23_BYTES;
@@ -64,9 +72,10 @@ struct Geo {
     // padded m-group and tile strides spread one warp's 16-byte stores over all bank groups.
     static constexpr uint32_t A3_SBO = 144, A3_TS = 16 * 144 + 16, A3_LBO = T * A3_TS;
     static constexpr uint32_t A3_BYTES = KG * A3_LBO;
-    // TMEM columns: three accumulator slots of 4 N columns, then f (N/2 columns per tile)
-    static constexpr uint32_t SLOT = 4 * N;
-    static constexpr uint32_t C_F = 3 * SLOT, F_COLS = T * (N / 2);
+    // TMEM columns: pass-1 slots 0, 1 (2 N columns: + then -), pass-2/3 slots 2, 3 (4 N columns:
+    // +hi, +lo, -hi, -lo), then f (N/2 columns per tile); slots 0 and 2 belong to warpgroup 0
+    static constexpr uint32_t C_S0 = 0, C_S1 = 2 * N, C_S2 = 4 * N, C_S3 = 8 * N;
+    static constexpr uint32_t C_F = 12 * N, F_COLS = T * (N / 2);
     static constexpr uint32_t C_USED = C_F + F_COLS;
     static constexpr uint32_t TMEM_COLS = C_USED <= 32 ? 32 : C_USED <= 64 ? 64 : C_USED <= 128 ? 128
                                           : C_USED <= 256 ? 256 : 512;
@@ -76,6 +85,8 @@ struct Geo {
     static constexpr uint32_t S_F = (S_A3 + 2 * A3_BYTES + 127) / 128 * 128;
     static constexpr uint32_t S_TOTAL = S_F + 2 * F_BLOCK;
     static_assert(S_TOTAL + 512 <= 232448, "shared-memory budget");
+    static_assert(A3_TS % 16 == 0 && A2_BYTES % 16 == 0 && A3_BYTES % 16 == 0 && F_BLOCK % 16 == 0 &&
+                  S_A3 % 16 == 0 && S_F % 16 == 0, "descriptor offsets are multiples of 16 bytes");
 };
 
 template <bool BF>
@@ -90,7 +101,7 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {   // a -> low half
 }
 
 struct Bars {
-    uint64_t full[3], freeb[3];        // TMEM slots: MMA completion -> epilogue, epilogue drained -> MMA
+    uint64_t full[4], freeb[4];        // TMEM slots: MMA completion -> epilogue, epilogue drained -> MMA
     uint64_t a2_full[2], a2_free[2];   // pass-2 operand tiles: epilogue -> MMA, MMA completion -> epilogue
     uint64_t a3_full, a3_free;         // pass-3 operands (both signs)
     uint64_t filt[2], fdone[2];        // filter buffers: copy landed; all MMAs of the pair using it done
@@ -142,17 +153,17 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
     // ---- set-up: barriers, first filter copies, TMEM (MMA warp); max |f| (epilogue warps) -----
     if (issuer) {
         if (lane == 0) {
-            for (int i = 0; i < 3; ++i) {
+            for (int i = 0; i < 4; ++i) {
                 tc::mbar_init(&bars.full[i], 1);
-                tc::mbar_init(&bars.freeb[i], G::EPI_WARPS);
+                tc::mbar_init(&bars.freeb[i], 128);
             }
             for (int i = 0; i < 2; ++i) {
-                tc::mbar_init(&bars.a2_full[i], G::EPI_WARPS);
+                tc::mbar_init(&bars.a2_full[i], 128);
                 tc::mbar_init(&bars.a2_free[i], 1);
                 tc::mbar_init(&bars.filt[i], 1);
                 tc::mbar_init(&bars.fdone[i], 1);
             }
-            tc::mbar_init(&bars.a3_full, G::EPI_WARPS);
+            tc::mbar_init(&bars.a3_full, 32 * G::EPI_WARPS);
             tc::mbar_init(&bars.a3_free, 1);
             tc::mbar_init(&bars.drain, 1);
             tc::fence_mbar_init();
@@ -181,15 +192,17 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
         float mx = s_red[0];
 #pragma unroll
         for (int i = 1; i < G::EPI_WARPS; ++i) mx = fmaxf(mx, s_red[i]);
-        if (mx > 0.f && isfinite(mx)) sf = exp2f(fminf(60.f, fmaxf(-60.f, floorf(log2f(512.f / mx)))));
+        if (mx > 0.f && isfinite(mx)) sf = exp2f(fminf(60.f, fmaxf(-60.f, floorf(log2f(2.f / mx)))));
     }
     const float eps = exp2f(-(float)(BF ? kLoShiftBF16 : kLoShiftF16));
-    const float out_scale = BF ? 1.f : 1.f / (sf * sf);
+    // fp16: max |f sf| in (1, 2]; pass 1 multiplies by 2^8 (its filters), which stays in the
+    // stored intermediates and is removed, squared, from the products
+    const float out_scale = BF ? 1.f : exp2f(-2.f * kP1ShiftF16) / (sf * sf);
 
     // ---- f -> TMEM as the pass-1 A operand: tile t, lane l = yl N + z holds f[0..N)[t ZT + yl][z] --
     if (!issuer) {
         const int q = warp & 3, w = warp >> 2, l = 32 * q + lane, yl = l / N, z = l % N;
-        for (int t = w; t < G::T; t += G::NWG) {
+        for (int t = w; t < G::T; t += 2) {
             const float* src = fb + (size_t)(t * G::ZT + yl) * N + z;
             uint32_t v[N / 2];
 #pragma unroll
@@ -209,7 +222,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
         // ================================ MMA warp (converged) ================================
         // per-slot / per-buffer state as bit masks (bit i = slot or buffer i), kept in registers
         uint32_t used = 0, ph_free = 0, ph_a2full = 0, ph_a3full = 0, ph_fdone = 0;
-        constexpr uint32_t id1 = tc::idesc_f16(BF, false, false, 4 * N, 128);
+        constexpr uint32_t id1 = tc::idesc_f16(BF, false, false, 2 * N, 128);
         constexpr uint32_t id23 = tc::idesc_f16(BF, true, false, 2 * N, 128);
 #define DGFS_WAITW(bar, ph)                                             \
     do {                                                                \
@@ -224,22 +237,35 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
         used |= 1u << (s);                                              \
         tc::tc_fence_after();                                           \
     } while (0)
+        // descriptors: constant stride parts + (shared address >> 4); every offset below is a
+        // compile-time constant or one multiply-add, so the issue loop stays short
+        constexpr uint64_t dF = tc::sdesc_base(G::FB_LBO, G::FB_SBO);
+        constexpr uint64_t dA2 = tc::sdesc_base(G::A2_LBO, G::A2_SBO);
+        constexpr uint64_t dA3 = tc::sdesc_base(G::A3_LBO, G::A3_SBO);
+        const uint32_t sb16 = sb >> 4;
         for (int p = 0; p < npairs; ++p) {
             const int fbuf = p & 1;
             DGFS_WAITW(&bars.filt[fbuf], (uint32_t)((fbuf ? waited1 : waited0) & 1));
             if (fbuf) ++waited1;
             else ++waited0;
             tc::tc_fence_after();
-            const uint32_t fsm = sb + G::S_F + fbuf * G::F_BLOCK;
-            // front: pass 1 of tile t (slot 0) and pass 2 of tile t - 1 (slot 1 + (t - 1) % 2)
+            const uint32_t f16 = sb16 + (G::S_F + fbuf * G::F_BLOCK) / 16;   // filter block of this pair
+            // front: pass 1 of tile t (slot t % 2) and pass 2 of tile t - 1 (slot 2 + (t - 1) % 2)
             for (int t = 0; t <= G::T; ++t) {
                 if (t < G::T) {
-                    DGFS_ACQUIRE(0);
+                    const int s1 = t & 1;
+                    DGFS_ACQUIRE(s1);
+                    const uint32_t d = tmem + s1 * G::C_S1;
+                    const uint32_t fa = tmem + G::C_F + t * (N / 2);
 #pragma unroll
-                    for (int ks = 0; ks < G::KSTEPS; ++ks)
-                        tc::mma_ts_warp(tmem, tmem + G::C_F + t * (N / 2) + 8 * ks,
-                                        tc::sdesc(fsm + G::OFF_B1 + ks * 2 * G::FB_LBO, G::FB_LBO, G::FB_SBO), id1, ks);
-                    tc::mma_commit_warp(&bars.full[0]);
+                    for (int ks = 0; ks < G::KSTEPS; ++ks) {   // hi rows [0, 2n), lo rows [2n, 4n) of B1
+                        tc::mma_ts_warp(d, fa + 8 * ks, tc::sdesc_at(dF, f16 + (G::OFF_B1 + ks * 2 * G::FB_LBO) / 16),
+                                        id1, ks);
+                        tc::mma_ts_warp(d, fa + 8 * ks,
+                                        tc::sdesc_at(dF, f16 + (G::OFF_B1 + (2 * N / 8) * G::FB_SBO + ks * 2 * G::FB_LBO) / 16),
+                                        id1, 1);
+                    }
+                    tc::mma_commit_warp(&bars.full[s1]);
                     // the other filter buffer (pair p - 1, whose MMAs are complete by now) takes pair p + 1
                     if (t == 0 && p >= 1 && p + 1 < npairs) {
                         const int nb = (p + 1) & 1;
@@ -256,40 +282,40 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                     }
                 }
                 if (t >= 1) {
-                    const int a = (t - 1) & 1, s = 1 + a;
+                    const int a = (t - 1) & 1, s = 2 + a;
                     DGFS_WAITW(&bars.a2_full[a], (ph_a2full >> a) & 1u);
                     ph_a2full ^= 1u << a;
                     DGFS_ACQUIRE(s);
+                    const uint32_t d = tmem + (a ? G::C_S3 : G::C_S2);
+                    const uint32_t a16 = sb16 + G::S_A2 / 16 + a * (2 * G::A2_BYTES / 16);
 #pragma unroll
                     for (int g = 0; g < 2; ++g)
 #pragma unroll
                         for (int ks = 0; ks < G::KSTEPS; ++ks)
-                            tc::mma_ss_warp(tmem + s * G::SLOT + g * 2 * N,
-                                            tc::sdesc(sb + G::S_A2 + (a * 2 + g) * G::A2_BYTES + ks * 2 * G::A2_LBO,
-                                                      G::A2_LBO, G::A2_SBO),
-                                            tc::sdesc(fsm + G::OFF_B2 + g * G::B23_BYTES + ks * 2 * G::FB_LBO, G::FB_LBO,
-                                                      G::FB_SBO),
+                            tc::mma_ss_warp(d + g * 2 * N,
+                                            tc::sdesc_at(dA2, a16 + (g * G::A2_BYTES + ks * 2 * G::A2_LBO) / 16),
+                                            tc::sdesc_at(dF, f16 + (G::OFF_B2 + g * G::B23_BYTES + ks * 2 * G::FB_LBO) / 16),
                                             id23, ks);
                     tc::mma_commit_warp(&bars.full[s]);
                     tc::mma_commit_warp(&bars.a2_free[a]);
                 }
             }
-            // back: pass 3 of tile u into slot 2 (u even) or 0 (u odd)
+            // back: pass 3 of tile u into slot 2 + u % 2
             DGFS_WAITW(&bars.a3_full, ph_a3full);
             ph_a3full ^= 1;
             tc::tc_fence_after();
             for (int u = 0; u < G::T; ++u) {
-                const int s = (u & 1) ? 0 : 2;
+                const int s = 2 + (u & 1);
                 DGFS_ACQUIRE(s);
+                const uint32_t d = tmem + ((u & 1) ? G::C_S3 : G::C_S2);
+                const uint32_t a16 = sb16 + G::S_A3 / 16 + u * (G::A3_TS / 16);
 #pragma unroll
                 for (int g = 0; g < 2; ++g)
 #pragma unroll
                     for (int ks = 0; ks < G::KSTEPS; ++ks)
-                        tc::mma_ss_warp(tmem + s * G::SLOT + g * 2 * N,
-                                        tc::sdesc(sb + G::S_A3 + g * G::A3_BYTES + u * G::A3_TS + ks * 2 * G::A3_LBO,
-                                                  G::A3_LBO, G::A3_SBO),
-                                        tc::sdesc(fsm + G::OFF_B3 + g * G::B23_BYTES + ks * 2 * G::FB_LBO, G::FB_LBO,
-                                                  G::FB_SBO),
+                        tc::mma_ss_warp(d + g * 2 * N,
+                                        tc::sdesc_at(dA3, a16 + (g * G::A3_BYTES + ks * 2 * G::A3_LBO) / 16),
+                                        tc::sdesc_at(dF, f16 + (G::OFF_B3 + g * G::B23_BYTES + ks * 2 * G::FB_LBO) / 16),
                                         id23, ks);
                 tc::mma_commit_warp(&bars.full[s]);
             }
@@ -301,112 +327,122 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
     mma_done:;
     } else {
         // ============================== epilogue warpgroups ===================================
-        const int q = warp & 3, w = warp >> 2, c0 = 8 * w;
+        // warpgroup w owns tiles t = 2k + w (k < TW) of every pass; thread = TMEM lane l
+        const int q = warp & 3, w = warp >> 2;
         const int l = 32 * q + lane, yl = l / N, lz = l % N;   // tile row: (yl, z) in pass 1, (yl, x') in pass 2
         const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
-        // store offsets: A2 unit (rows yl N + c0 .. +8, k = z = lz); A3 unit (rows lz N + c0 .. +8)
-        const uint32_t a2_off = ((uint32_t)(yl * N + c0) >> 3) * G::A2_SBO + (lz >> 3) * G::A2_LBO + (lz & 7) * 16;
-        const int mg3 = (lz * N + c0) >> 3;
-        const uint32_t a3_off = (mg3 >> 4) * G::A3_TS + (mg3 & 15) * G::A3_SBO;
-        uint32_t ph_full = 0, ph_a2free = 0, a2_used = 0, ph_a3free = 0;   // bit masks, as in the MMA warp
-        float acc[G::T][8];
+        const uint32_t tP1 = trow + G::C_S0 + w * G::C_S1;        // pass-1 slot: + at 0, - at N
+        const uint32_t tB = trow + (w ? G::C_S3 : G::C_S2);       // pass-2/3 slot: +hi, +lo, -hi, -lo
+        // shared-memory stores (one 16-byte unit = 8 consecutive rows of one k): A2 rows yl N + x',
+        // k = z = lz; A3 rows x' N + z' with x' = lz, k = y
+        const uint32_t a2_row = sb + G::S_A2 + w * 2 * G::A2_BYTES + ((uint32_t)(yl * N) >> 3) * G::A2_SBO +
+                                (lz >> 3) * G::A2_LBO + (lz & 7) * 16;
+        const int mg3 = (lz * N) >> 3;
+        uint32_t ph_full = 0, ph_a2free = 0, ph_a3free = 0;   // phase bits of this warpgroup's barriers
+        float acc[G::TW][N];
 #pragma unroll
-        for (int u = 0; u < G::T; ++u)
+        for (int k = 0; k < G::TW; ++k)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[u][j] = 0.f;
+            for (int j = 0; j < N; ++j) acc[k][j] = 0.f;
 #define DGFS_WAITE(bar, ph)                                             \
     do {                                                                \
         if (!tc::warp_wait((bar), (ph), abort)) goto epi_done;          \
     } while (0)
         for (int p = 0; p < npairs; ++p) {
-            for (int t = 0; t <= G::T; ++t) {
-                if (t < G::T) {
-                    // pass-1 tile t -> pass-2 operands of both signs
-                    DGFS_WAITE(&bars.full[0], ph_full & 1u);
+            for (int k = 0; k <= G::TW; ++k) {
+                if (k < G::TW) {
+                    // pass-1 tile t = 2k + w -> the pass-2 operands of both signs (A2 buffer w)
+                    if (p > 0 || k > 0) {   // P2 of this warpgroup's previous tile has read A2[w]
+                        DGFS_WAITE(&bars.a2_free[w], ph_a2free);
+                        ph_a2free ^= 1;
+                    }
+                    DGFS_WAITE(&bars.full[w], ph_full & 1u);
                     ph_full ^= 1u;
                     tc::tc_fence_after();
-                    uint32_t up[4], um[4];
-                    {
-                        float v[8];
-                        load_combined<N>(trow + c0, eps, v);
-                        pack8<BF>(v, up);
-                        load_combined<N>(trow + 2 * N + c0, eps, v);
-                        pack8<BF>(v, um);
-                    }
-                    tc::tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&bars.freeb[0]);
-                    const int a = t & 1;
-                    if (a2_used & (1u << a)) {
-                        DGFS_WAITE(&bars.a2_free[a], (ph_a2free >> a) & 1u);
-                        ph_a2free ^= 1u << a;
-                    }
-                    a2_used |= 1u << a;
-                    const uint32_t dst = sb + G::S_A2 + a * 2 * G::A2_BYTES + a2_off;
-                    tc::st_shared_v4(dst, up[0], up[1], up[2], up[3]);
-                    tc::st_shared_v4(dst + G::A2_BYTES, um[0], um[1], um[2], um[3]);
+#pragma unroll
+                    for (int g = 0; g < 2; ++g)
+#pragma unroll
+                        for (int c = 0; c < N / 8; ++c) {   // 8 columns x' = 8c .. 8c + 7
+                            float v[8];
+                            tc::tmem_ld8(tP1 + g * N + 8 * c, v);
+                            tc::tmem_wait_ld();
+                            if (g == 1 && c == N / 8 - 1) {
+                                tc::tc_fence_before();
+                                tc::mbar_arrive(&bars.freeb[w]);
+                            }
+                            uint32_t u[4];
+                            pack8<BF>(v, u);
+                            tc::st_shared_v4(a2_row + g * G::A2_BYTES + c * G::A2_SBO, u[0], u[1], u[2], u[3]);
+                        }
                     tc::fence_proxy_async();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&bars.a2_full[a]);
+                    tc::mbar_arrive(&bars.a2_full[w]);
                 }
-                if (t >= 1) {
-                    // pass-2 tile t - 1 -> rows of the pass-3 operands of both signs
-                    const int tt = t - 1, s = 1 + (tt & 1);
-                    DGFS_WAITE(&bars.full[s], (ph_full >> s) & 1u);
-                    ph_full ^= 1u << s;
-                    tc::tc_fence_after();
-                    uint32_t up[4], um[4];
-                    {
-                        float v[8];
-                        load_combined<N>(trow + s * G::SLOT + c0, eps, v);
-                        pack8<BF>(v, up);
-                        load_combined<N>(trow + s * G::SLOT + 2 * N + c0, eps, v);
-                        pack8<BF>(v, um);
-                    }
-                    tc::tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&bars.freeb[s]);
-                    if (tt == 0 && p > 0) {   // the previous pair's pass 3 has read the operands
+                if (k >= 1) {
+                    // pass-2 tile t = 2(k - 1) + w -> rows of the pass-3 operands of both signs
+                    const int t = 2 * (k - 1) + w, y = t * G::ZT + yl;
+                    if (k == 1 && p > 0) {   // the previous pair's pass 3 has read the operands
                         DGFS_WAITE(&bars.a3_free, ph_a3free);
                         ph_a3free ^= 1;
                     }
-                    const int y = tt * G::ZT + yl;
-                    const uint32_t dst = sb + G::S_A3 + a3_off + (y >> 3) * G::A3_LBO + (y & 7) * 16;
-                    tc::st_shared_v4(dst, up[0], up[1], up[2], up[3]);
-                    tc::st_shared_v4(dst + G::A3_BYTES, um[0], um[1], um[2], um[3]);
-                    if (tt == G::T - 1) {
+                    DGFS_WAITE(&bars.full[2 + w], (ph_full >> 1) & 1u);
+                    ph_full ^= 2u;
+                    tc::tc_fence_after();
+                    const uint32_t ky = (y >> 3) * G::A3_LBO + (y & 7) * 16;
+#pragma unroll
+                    for (int g = 0; g < 2; ++g)
+#pragma unroll
+                        for (int c = 0; c < N / 8; ++c) {   // 8 columns z' = 8c .. 8c + 7
+                            float v[8];
+                            load_combined<N>(tB + g * 2 * N + 8 * c, eps, v);
+                            if (g == 1 && c == N / 8 - 1) {
+                                tc::tc_fence_before();
+                                tc::mbar_arrive(&bars.freeb[2 + w]);
+                            }
+                            uint32_t u[4];
+                            pack8<BF>(v, u);
+                            const int mg = mg3 + c;
+                            tc::st_shared_v4(sb + G::S_A3 + g * G::A3_BYTES + (mg >> 4) * G::A3_TS + (mg & 15) * G::A3_SBO + ky,
+                                             u[0], u[1], u[2], u[3]);
+                        }
+                    if (k == G::TW) {
                         tc::fence_proxy_async();
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&bars.a3_full);
+                        tc::mbar_arrive(&bars.a3_full);
                     }
                 }
             }
-            // pass-3 tiles: products of the two translates
+            // pass-3 tiles u = 2k + w: products of the two translates
 #pragma unroll
-            for (int u = 0; u < G::T; ++u) {
-                const int s = (u & 1) ? 0 : 2;
-                DGFS_WAITE(&bars.full[s], (ph_full >> s) & 1u);
-                ph_full ^= 1u << s;
+            for (int k = 0; k < G::TW; ++k) {
+                DGFS_WAITE(&bars.full[2 + w], (ph_full >> 1) & 1u);
+                ph_full ^= 2u;
                 tc::tc_fence_after();
-                float vp[8], vm[8];
-                load_combined<N>(trow + s * G::SLOT + c0, eps, vp);
-                load_combined<N>(trow + s * G::SLOT + 2 * N + c0, eps, vm);
-                tc::tc_fence_before();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&bars.freeb[s]);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[u][j] = fmaf(vp[j], vm[j], acc[u][j]);
+                for (int c = 0; c < N / 4; ++c) {   // 4 columns y' = 4c .. 4c + 3
+                    float hp[4], lp[4], hm[4], lm[4];
+                    tc::tmem_ld4(tB + 4 * c, hp);
+                    tc::tmem_ld4(tB + N + 4 * c, lp);
+                    tc::tmem_ld4(tB + 2 * N + 4 * c, hm);
+                    tc::tmem_ld4(tB + 3 * N + 4 * c, lm);
+                    tc::tmem_wait_ld();
+                    if (c == N / 4 - 1) {
+                        tc::tc_fence_before();
+                        tc::mbar_arrive(&bars.freeb[2 + w]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        acc[k][4 * c + j] = fmaf(fmaf(lp[j], eps, hp[j]), fmaf(lm[j], eps, hm[j]), acc[k][4 * c + j]);
+                }
             }
         }
 #undef DGFS_WAITE
-        if (!*abort) {   // P[node][r][x'][y'][z'], row m3 = x' N + z' of tile u, column y' = c0 + j
+        if (!*abort) {   // P[node][r][x'][y'][z'], row m3 = x' N + z' of tile u = 2k + w, column y'
             float* dst = P + ((size_t)node * Nrho + r) * n3;
 #pragma unroll
-            for (int u = 0; u < G::T; ++u) {
-                const int m3 = u * 128 + l, xp = m3 / N, zp = m3 % N;
-                float* o = dst + (size_t)xp * G::N2 + (size_t)c0 * N + zp;
+            for (int k = 0; k < G::TW; ++k) {
+                const int m3 = (2 * k + w) * 128 + l, xp = m3 / N, zp = m3 % N;
+                float* o = dst + (size_t)xp * G::N2 + zp;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) o[(size_t)j * N] = acc[u][j] * out_scale;
+                for (int j = 0; j < N; ++j) o[(size_t)j * N] = acc[k][j] * out_scale;
             }
         }
     epi_done:;
@@ -486,6 +522,7 @@ size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>&
     const int N = hp.N, np = hp.npairs, Nr = hp.Nrho;
     const bool bf = prec == DGFS_PREC_BF16S;
     const double lo_scale = std::ldexp(1.0, bf ? kLoShiftBF16 : kLoShiftF16);
+    const double p1_scale = bf ? 1.0 : std::ldexp(1.0, kP1ShiftF16);
     const size_t n2b = (size_t)N * N * 2;            // bytes of one N x N 16-bit matrix
     const size_t b1 = 4 * n2b, b23 = 2 * n2b, block = b1 + 4 * b23;
     blob.assign((size_t)Nr * np * block, 0);
@@ -494,11 +531,11 @@ size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>&
     auto put = [&](unsigned char* base, int n, int k, uint16_t bits) {
         std::memcpy(base + (n / 8) * sbo + (k / 8) * lbo + (n % 8) * 16 + (k % 8) * 2, &bits, 2);
     };
-    // hi + 2^-e lo split of v, both rounded to the operand type
-    auto split = [&](double v, uint16_t& hi, uint16_t& lo) {
+    // v = hi + lo / ls, both parts rounded to the operand type
+    auto split = [&](double v, double ls, uint16_t& hi, uint16_t& lo) {
         hi = bf ? to_bf16_bits(v) : to_half_bits(v);
         const double hv = bf ? bf16_bits_value(hi) : half_bits_value(hi);
-        lo = bf ? to_bf16_bits((v - hv) * lo_scale) : to_half_bits((v - hv) * lo_scale);
+        lo = bf ? to_bf16_bits((v - hv) * ls) : to_half_bits((v - hv) * ls);
     };
     for (int r = 0; r < Nr; ++r)
         for (int p = 0; p < np; ++p) {
@@ -514,15 +551,16 @@ size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>&
                 for (int i = 0; i < N; ++i)
                     for (int j = 0; j < N; ++j) {
                         uint16_t hi, lo;
-                        // pass 1 (x, axis 0): parts (+hi, +lo, -hi, -lo); the + filter carries 2 w_p
-                        split(F(0, g, i, j) * (g == 0 ? w2 : 1.0), hi, lo);
-                        put(blk, (2 * g) * N + i, j, hi);
-                        put(blk, (2 * g + 1) * N + i, j, lo);
-                        // pass 2 (z, axis 2) and pass 3 (y, axis 1): parts (hi, lo) per sign
-                        split(F(2, g, i, j), hi, lo);
+                        // pass 1 (x, axis 0): rows +hi, -hi, +lo, -lo, both parts times p1_scale
+                        // (accumulated in one accumulator); the + filter carries 2 w_p
+                        split(F(0, g, i, j) * (g == 0 ? w2 : 1.0) * p1_scale, 1.0, hi, lo);
+                        put(blk, g * N + i, j, hi);
+                        put(blk, (2 + g) * N + i, j, lo);
+                        // pass 2 (z, axis 2) and pass 3 (y, axis 1): rows hi, lo per sign
+                        split(F(2, g, i, j), lo_scale, hi, lo);
                         put(blk + b1 + g * b23, i, j, hi);
                         put(blk + b1 + g * b23, N + i, j, lo);
-                        split(F(1, g, i, j), hi, lo);
+                        split(F(1, g, i, j), lo_scale, hi, lo);
                         put(blk + b1 + 2 * b23 + g * b23, i, j, hi);
                         put(blk + b1 + 2 * b23 + g * b23, N + i, j, lo);
                     }

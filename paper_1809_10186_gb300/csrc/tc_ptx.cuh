@@ -23,6 +23,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     return d;
 }
 
+// The same descriptor split for cheap issue: the constant part (strides, version) with a zero
+// address field, to which the caller adds (byte address >> 4) as a 32-bit offset. Shared-memory
+// addresses stay below 256 KB, so the 14-bit address field never carries into the LBO field.
+__host__ __device__ constexpr uint64_t sdesc_base(uint32_t lbo, uint32_t sbo) {
+    return ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ uint64_t sdesc_at(uint64_t base, uint32_t addr16) { return base + addr16; }
+
 // Instruction descriptor of tcgen05.mma.kind::f16: FP32 accumulator, A/B fp16 (0) or bf16 (1),
 // major-ness of A and B (0 = K-major, 1 = MN-major), N >> 3, M >> 4.
 __host__ __device__ constexpr uint32_t idesc_f16(bool bf16, bool a_mn, bool b_mn, int N, int M) {
@@ -128,6 +136,14 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(taddr) : "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // 32 consecutive 32-bit TMEM columns of this thread's lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     float a[16], b[16];
@@ -189,11 +205,22 @@ __device__ __forceinline__ void mma_commit_warp(uint64_t* bar) {
                  ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Bounded wait by every lane of a warp with a warp-uniform outcome: false (and *abort raised by
-// whichever lane gave up) unless every lane saw the phase complete.
+// Bounded wait by every lane of a warp. Every branch depends only on warp votes, so the loop
+// never diverges (divergent branches around the .sync.aligned tcgen05 instructions cost far more
+// than the wait itself). False, with *abort raised, on timeout or when another role aborted.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
-    const bool ok = mbar_wait_or_abort(bar, parity, abort);
-    return __all_sync(0xffffffffu, ok);
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < (1u << 20); ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (__all_sync(0xffffffffu, done != 0)) return true;
+        if ((it & 63u) == 63u && __any_sync(0xffffffffu, *abort != 0)) return false;
+    }
+    *abort = 1;
+    return false;
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t saddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
