@@ -196,51 +196,72 @@ cudaError_t fft3(Cplx<T>* X, const Cplx<T>* W, int64_t count, bool forward, T sc
 
 // ---- projections and multipliers ----------------------------------------------------------
 
+// two consecutive values from an even index (8- or 16-byte aligned), and two complex values with
+// zero imaginary parts stored as one 16-byte (float) or two 16-byte (double) stores
+__device__ __forceinline__ void load_pair(const float* p, float& a, float& b) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void load_pair(const double* p, double& a, double& b) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void store_real_pair(Cplx<float>* x, float a, float b) {
+    *reinterpret_cast<float4*>(x) = make_float4(a, 0.f, b, 0.f);
+}
+__device__ __forceinline__ void store_real_pair(Cplx<double>* x, double a, double b) {
+    reinterpret_cast<double2*>(x)[0] = make_double2(a, 0.0);
+    reinterpret_cast<double2*>(x)[1] = make_double2(b, 0.0);
+}
+
 // X[node][s][j] = sum_r C[s][r] P[node][r][j],  C[s][r] = Vr[s][r] w_r rho_r(node).
-// Each thread owns 4 consecutive j and accumulates 8 outputs s at a time from register-held
-// P values, with the coefficients broadcast from shared memory (stored [r][s]).
-template <typename T>
-__global__ void k_project(const T* __restrict__ P, const T* __restrict__ Vr,
-                          const double* __restrict__ cr, const double* __restrict__ wr,
-                          NodeParams np, int Nrho, int rank, int64_t n3, Cplx<T>* __restrict__ X,
-                          int xfields) {
+// Memory-bound: P is read once. Each thread owns 2 consecutive j and accumulates SG outputs s in
+// registers (one pass when rank <= SG), with the coefficients broadcast from shared memory
+// (stored [r][s], rows padded to a multiple of SG).
+template <typename T, int SG>
+__global__ void __launch_bounds__(256) k_project(const T* __restrict__ P, const T* __restrict__ Vr,
+                                                 const double* __restrict__ cr, const double* __restrict__ wr,
+                                                 NodeParams np, int Nrho, int rank, int64_t n3,
+                                                 Cplx<T>* __restrict__ X, int xfields) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    T* CT = reinterpret_cast<T*>(sm_raw);                 // [Nrho][rank8]
-    const int rank8 = (rank + 7) & ~7;
+    T* CT = reinterpret_cast<T*>(sm_raw);                 // [Nrho][rpad]
+    T* wrho = CT + Nrho * ((rank + SG - 1) / SG * SG);    // [Nrho]: w_r rho_r of this node
+    const int rpad = (rank + SG - 1) / SG * SG;
     const int64_t node = blockIdx.y;
     const double gam = np.gamma ? np.gamma[node] : np.gamma0;
     const double bb = np.b ? np.b[node] : np.b0;
-    for (int e = threadIdx.x; e < Nrho * rank8; e += blockDim.x) {
-        const int r = e / rank8, sidx = e % rank8;
-        CT[e] = sidx < rank ? Vr[sidx * Nrho + r] * (T)wr[r] * radial_rho<T>(bb, gam, cr[r], np.dlog) : T(0);
+    // one FP64 power per radial point (FP64 is slow on this part), then the coefficient table
+    for (int r = threadIdx.x; r < Nrho; r += blockDim.x) wrho[r] = (T)wr[r] * radial_rho<T>(bb, gam, cr[r], np.dlog);
+    __syncthreads();
+    for (int e = threadIdx.x; e < Nrho * rpad; e += blockDim.x) {
+        const int r = e / rpad, sidx = e % rpad;
+        CT[e] = sidx < rank ? Vr[sidx * Nrho + r] * wrho[r] : T(0);
     }
     __syncthreads();
-    const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
     if (j0 >= n3) return;
     const T* Pn = P + node * Nrho * n3 + j0;
     Cplx<T>* Xn = X + node * (int64_t)xfields * n3 + j0;
-    for (int s0 = 0; s0 < rank; s0 += 8) {
-        T acc[8][4];
+    for (int s0 = 0; s0 < rank; s0 += SG) {
+        T acc[SG][2];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[i][v] = T(0);
+        for (int i = 0; i < SG; ++i) acc[i][0] = acc[i][1] = T(0);
+#pragma unroll 4
         for (int r = 0; r < Nrho; ++r) {
-            T pv[4];
+            T p0, p1;
+            load_pair(Pn + (int64_t)r * n3, p0, p1);
+            const T* c = CT + r * rpad + s0;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) pv[v] = Pn[(int64_t)r * n3 + v];
-            const T* c = CT + r * rank8 + s0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[i][v] = fma(c[i], pv[v], acc[i][v]);
+            for (int i = 0; i < SG; ++i) {
+                acc[i][0] = fma(c[i], p0, acc[i][0]);
+                acc[i][1] = fma(c[i], p1, acc[i][1]);
+            }
         }
-        const int ns = rank - s0 < 8 ? rank - s0 : 8;
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            if (i < ns)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) Xn[(int64_t)(s0 + i) * n3 + v] = Cplx<T>{acc[i][v], T(0)};
+        for (int i = 0; i < SG; ++i)
+            if (s0 + i < rank) store_real_pair(Xn + (int64_t)(s0 + i) * n3, acc[i][0], acc[i][1]);
     }
 }
 
@@ -339,13 +360,13 @@ __global__ void k_expand_radial(const Cplx<T>* __restrict__ X, int xfields, cons
     extern __shared__ __align__(16) unsigned char sm_raw[];
     T* C = reinterpret_cast<T*>(sm_raw);        // [rank][Nrho]
     T* Xt = C + rank * Nrho;                     // [rank][blockDim]
+    T* wrho = Xt + rank * blockDim.x;            // [Nrho]: w_r rho_r of this node
     const int64_t node = blockIdx.y;
     const double gam = np.gamma ? np.gamma[node] : np.gamma0;
     const double bb = np.b ? np.b[node] : np.b0;
-    for (int e = threadIdx.x; e < rank * Nrho; e += blockDim.x) {
-        const int r = e % Nrho;
-        C[e] = Vr[e] * (T)wr[r] * radial_rho<T>(bb, gam, cr[r], np.dlog);
-    }
+    for (int r = threadIdx.x; r < Nrho; r += blockDim.x) wrho[r] = (T)wr[r] * radial_rho<T>(bb, gam, cr[r], np.dlog);
+    __syncthreads();
+    for (int e = threadIdx.x; e < rank * Nrho; e += blockDim.x) C[e] = Vr[e] * wrho[e % Nrho];
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const Cplx<T>* Xn = X + node * (int64_t)xfields * n3;
     for (int s = 0; s < rank; ++s) Xt[s * blockDim.x + threadIdx.x] = j < n3 ? Xn[s * n3 + j].x : T(0);
@@ -425,11 +446,18 @@ template <typename T>
 cudaError_t launch_project(const DevTables<T>& t, const T* P, NodeParams np, int64_t nodes,
                            Cplx<T>* X, int xfields, cudaStream_t s) {
     if (nodes <= 0) return cudaSuccess;
-    const int64_t n3 = (int64_t)t.N * t.N * t.N;      // a multiple of 4 for every supported N
-    const int bs = 128;
-    const size_t sm = sizeof(T) * (size_t)(t.Nrho * ((t.rank + 7) & ~7));
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_project<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_project<T><<<dim3(blocks_for(n3 / 4, bs), (unsigned)nodes), bs, sm, s>>>(P, t.Vr, t.cr, t.wr, np, t.Nrho, t.rank, n3, X, xfields);
+    const int64_t n3 = (int64_t)t.N * t.N * t.N;      // even for every supported N
+    const int bs = 256;
+    const dim3 grid(blocks_for(n3 / 2, bs), (unsigned)nodes);
+    auto go = [&](auto kern, int sg) {
+        const size_t sm = sizeof(T) * (size_t)t.Nrho * (size_t)((t.rank + sg - 1) / sg * sg + 1);
+        if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        kern<<<grid, bs, sm, s>>>(P, t.Vr, t.cr, t.wr, np, t.Nrho, t.rank, n3, X, xfields);
+    };
+    if (t.rank <= 8) go(k_project<T, 8>, 8);
+    else if (t.rank <= 16) go(k_project<T, 16>, 16);
+    else if (t.rank <= 24) go(k_project<T, 24>, 24);
+    else go(k_project<T, 32>, 32);
     return cudaGetLastError();
 }
 
@@ -476,7 +504,7 @@ cudaError_t launch_expand_radial(const DevTables<T>& t, const Cplx<T>* X, int xf
     if (nodes <= 0) return cudaSuccess;
     const int64_t n3 = (int64_t)t.N * t.N * t.N;
     const int bs = 128;
-    const size_t sm = sizeof(T) * (size_t)(t.rank * t.Nrho + t.rank * bs);
+    const size_t sm = sizeof(T) * (size_t)(t.rank * t.Nrho + t.rank * bs + t.Nrho);
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_expand_radial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_expand_radial<T><<<dim3(blocks_for(n3, bs), (unsigned)nodes), bs, sm, s>>>(X, xfields, t.Vr, t.cr, t.wr, np, t.Nrho, t.rank, n3, U);
     return cudaGetLastError();
