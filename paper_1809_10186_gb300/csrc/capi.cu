@@ -210,7 +210,7 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
     cudaError_t e;
     if (op == Op::Vjp) {
         // g holds u. 1) K_r u for every r:  DFT(u) -> Uk[s] u^ -> IDFT -> sum_s Vr w_r rho_r
-        e = launch_load_field<T>(t.N, g, nullptr, offs, nodes, X, xf, rank, s);
+        e = launch_load_field<T>(t.N, g, nullptr, offs, nodes, X, xf, rank, 0, s);
         if (!e) e = launch_dft3<T>(t, X + (size_t)0, nodes * xf, true, s);
         if (!e) e = launch_multiply_uk<T>(t, X, xf, rank, nodes, s);
         if (!e) e = launch_dft3<T>(t, X, nodes * xf, false, s);
@@ -227,8 +227,8 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
         e = launch_vjp_products(t, f, P, nodes, S, G, s);
         if (e) return cuda_fail(e, "vjp: translate-product kernel");
         // 3) loss: K_L f + i K_L (u f)
-        e = launch_load_field<T>(t.N, f, nullptr, offs, nodes, X, xf, 0, s);
-        if (!e) e = launch_load_field<T>(t.N, f, g, offs, nodes, X, xf, 1, s);
+        e = launch_load_field<T>(t.N, f, nullptr, offs, nodes, X, xf, 0, 0, s);
+        if (!e) e = launch_load_field<T>(t.N, f, g, offs, nodes, X, xf, 1, 0, s);
         if (!e) e = launch_dft3<T>(t, X, nodes * xf, true, s);
         if (!e) e = launch_loss_pair<T>(t, X, xf, np, nodes, 0, 1, Y, 2, s);
         if (!e) e = launch_dft3<T>(t, Y, nodes * 2, false, s);
@@ -256,19 +256,21 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
         cudaEventRecord(p->ev[2 * p->prof_timed + 1], s);
         p->prof_timed += 1;
     }
-    e = launch_project<T>(t, P, np, nodes, X, xf, s);
+    // real fields packed two per complex slot: the rank projected fields, then the loss
+    // operand(s): Q(f,g) -> field rank = g;  JVP -> field rank = v, field rank + 1 = f
+    const int nfields = rank + (op == Op::Jvp ? 2 : 1), xs = (nfields + 1) / 2;
+    e = launch_project<T>(t, P, np, nodes, X, xs, s);
     if (e) return cuda_fail(e, "radial projection");
-    // loss operands: Q(f,g) -> g in slot rank;  JVP -> v in slot rank, f in slot rank+1
     const T* loss0 = (op == Op::Collide || op == Op::Dgamma) ? f : g;
-    e = launch_load_field<T>(t.N, loss0, nullptr, offs, nodes, X, xf, rank, s);
-    if (!e && op == Op::Jvp) e = launch_load_field<T>(t.N, f, nullptr, offs, nodes, X, xf, rank + 1, s);
+    e = launch_load_field<T>(t.N, loss0, nullptr, offs, nodes, X, xs, rank / 2, rank % 2, s);
+    if (!e && op == Op::Jvp) e = launch_load_field<T>(t.N, f, nullptr, offs, nodes, X, xs, (rank + 1) / 2, (rank + 1) % 2, s);
     if (e) return cuda_fail(e, "loss operand");
-    // forward DFT of the rank projected fields and the loss operand(s)
-    e = launch_dft3<T>(t, X, nodes * xf, true, s);
+    // forward DFT of the packed slots
+    e = launch_dft3<T>(t, X, nodes * xs, true, s);
     if (e) return cuda_fail(e, "forward DFT");
     const T scale = op == Op::Jvp ? T(2) : T(1);
     const int yf = op == Op::Jvp ? 3 : 2;
-    e = launch_combine<T>(t, X, xf, np, nodes, scale, rank, op == Op::Jvp ? rank + 1 : -1, Y, yf, s);
+    e = launch_combine<T>(t, X, xs, np, nodes, scale, rank, op == Op::Jvp ? rank + 1 : -1, Y, yf, s);
     if (!e) e = launch_dft3<T>(t, Y, nodes * yf, false, s);
     if (e) return cuda_fail(e, "Fourier combine / inverse DFT");
     // Q = gain - f (K_L g)   (JVP: 2 gain(f,v) - f K_L v - v K_L f)
@@ -672,10 +674,11 @@ dgfs_status noalloc_run(dgfs_plan_s* p, const T* f, T* Q, int64_t B, unsigned ch
                                     reinterpret_cast<float*>(P), p->d_flags, s);
     else
         e = launch_gain_products(t, f, nullptr, nullptr, B, P, s);
-    if (!e) e = launch_project<T>(t, P, np, B, X, xf, s);
-    if (!e) e = launch_load_field<T>(t.N, f, nullptr, nullptr, B, X, xf, t.rank, s);
-    if (!e) e = launch_dft3<T>(t, X, B * xf, true, s);
-    if (!e) e = launch_combine<T>(t, X, xf, np, B, T(1), t.rank, -1, Y, 2, s);
+    const int xs = (t.rank + 2) / 2;   // rank projected fields and f, packed two per slot
+    if (!e) e = launch_project<T>(t, P, np, B, X, xs, s);
+    if (!e) e = launch_load_field<T>(t.N, f, nullptr, nullptr, B, X, xs, t.rank / 2, t.rank % 2, s);
+    if (!e) e = launch_dft3<T>(t, X, B * xs, true, s);
+    if (!e) e = launch_combine<T>(t, X, xs, np, B, T(1), t.rank, -1, Y, 2, s);
     if (!e) e = launch_dft3<T>(t, Y, B * 2, false, s);
     if (!e) e = launch_finalize<T>(t.N, t.Nrho, Y, 2, f, nullptr, nullptr, nullptr, B, 0, Q, p->d_flags, s);
     if (e) return cuda_fail(e, "dgfs_collide_noalloc");

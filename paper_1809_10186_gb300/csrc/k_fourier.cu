@@ -208,23 +208,24 @@ __device__ __forceinline__ void load_pair(const double* p, double& a, double& b)
     a = v.x;
     b = v.y;
 }
-__device__ __forceinline__ void store_real_pair(Cplx<float>* x, float a, float b) {
-    *reinterpret_cast<float4*>(x) = make_float4(a, 0.f, b, 0.f);
+// x[0] = {a0, b0}, x[1] = {a1, b1}: one 16-byte (float) or two 16-byte (double) stores
+__device__ __forceinline__ void store_cplx_pair(Cplx<float>* x, float a0, float b0, float a1, float b1) {
+    *reinterpret_cast<float4*>(x) = make_float4(a0, b0, a1, b1);
 }
-__device__ __forceinline__ void store_real_pair(Cplx<double>* x, double a, double b) {
-    reinterpret_cast<double2*>(x)[0] = make_double2(a, 0.0);
-    reinterpret_cast<double2*>(x)[1] = make_double2(b, 0.0);
+__device__ __forceinline__ void store_cplx_pair(Cplx<double>* x, double a0, double b0, double a1, double b1) {
+    reinterpret_cast<double2*>(x)[0] = make_double2(a0, b0);
+    reinterpret_cast<double2*>(x)[1] = make_double2(a1, b1);
 }
 
-// X[node][s][j] = sum_r C[s][r] P[node][r][j],  C[s][r] = Vr[s][r] w_r rho_r(node).
-// Memory-bound: P is read once. Each thread owns 2 consecutive j and accumulates SG outputs s in
+// field s = sum_r C[s][r] P[node][r][j],  C[s][r] = Vr[s][r] w_r rho_r(node), stored packed: fields
+// 2m and 2m + 1 are the real and imaginary parts of slot m. Memory-bound: P is read once. Each thread owns 2 consecutive j and accumulates SG outputs s in
 // registers (one pass when rank <= SG), with the coefficients broadcast from shared memory
 // (stored [r][s], rows padded to a multiple of SG).
 template <typename T, int SG>
 __global__ void __launch_bounds__(256) k_project(const T* __restrict__ P, const T* __restrict__ Vr,
                                                  const double* __restrict__ cr, const double* __restrict__ wr,
                                                  NodeParams np, int Nrho, int rank, int64_t n3,
-                                                 Cplx<T>* __restrict__ X, int xfields) {
+                                                 Cplx<T>* __restrict__ X, int xslots) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     T* CT = reinterpret_cast<T*>(sm_raw);                 // [Nrho][rpad]
     T* wrho = CT + Nrho * ((rank + SG - 1) / SG * SG);    // [Nrho]: w_r rho_r of this node
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(256) k_project(const T* __restrict__ P, const 
     const int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
     if (j0 >= n3) return;
     const T* Pn = P + node * Nrho * n3 + j0;
-    Cplx<T>* Xn = X + node * (int64_t)xfields * n3 + j0;
+    Cplx<T>* Xn = X + node * (int64_t)xslots * n3 + j0;
     for (int s0 = 0; s0 < rank; s0 += SG) {
         T acc[SG][2];
 #pragma unroll
@@ -260,29 +261,35 @@ __global__ void __launch_bounds__(256) k_project(const T* __restrict__ P, const 
             }
         }
 #pragma unroll
-        for (int i = 0; i < SG; ++i)
-            if (s0 + i < rank) store_real_pair(Xn + (int64_t)(s0 + i) * n3, acc[i][0], acc[i][1]);
+        for (int i = 0; i < SG; i += 2)   // s0 is even: fields s0 + i, s0 + i + 1 share slot (s0 + i) / 2
+            if (s0 + i < rank) {
+                const bool two = s0 + i + 1 < rank;
+                store_cplx_pair(Xn + (int64_t)((s0 + i) / 2) * n3, acc[i][0], two ? acc[i + 1][0] : T(0), acc[i][1],
+                                two ? acc[i + 1][1] : T(0));
+            }
     }
 }
 
 template <typename T>
 __global__ void k_load_field(int64_t n3, const T* __restrict__ a, const T* __restrict__ b,
                              const int64_t* __restrict__ offs, Cplx<T>* __restrict__ X, int xfields,
-                             int slot) {
+                             int slot, int part) {
     const int64_t node = blockIdx.y;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n3) return;
     const int64_t base = offs ? offs[node] : node * n3;
     T v = a[base + j];
     if (b) v *= b[base + j];
-    X[(node * xfields + slot) * n3 + j] = Cplx<T>{v, T(0)};
+    Cplx<T>& x = X[(node * xfields + slot) * n3 + j];
+    if (part == 0) x = Cplx<T>{v, T(0)};
+    else x.y = v;
 }
 
 template <typename T>
-__global__ void k_combine(const Cplx<T>* __restrict__ X, int xfields, const T* __restrict__ Uk,
+__global__ void k_combine(const Cplx<T>* __restrict__ X, int xslots, const T* __restrict__ Uk,
                           const T* __restrict__ Lr, const T* __restrict__ GL0, const T* __restrict__ GLd,
-                          const double* __restrict__ cr, NodeParams np, int Nrho, int rank, int64_t n3,
-                          T scale, int ls0, int ls1, Cplx<T>* __restrict__ Y, int yfields) {
+                          const double* __restrict__ cr, NodeParams np, int N, int Nrho, int rank, int64_t n3,
+                          T scale, int lf0, int lf1, Cplx<T>* __restrict__ Y, int yfields) {
     __shared__ double rho[64];
     const int64_t node = blockIdx.y;
     const bool per_node = np.gamma || np.b;
@@ -293,26 +300,41 @@ __global__ void k_combine(const Cplx<T>* __restrict__ X, int xfields, const T* _
     __syncthreads();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n3) return;
-    const Cplx<T>* Xn = X + node * (int64_t)xfields * n3;
+    // index of -k (each axis index q -> (N - q) mod N in the standard DFT ordering)
+    const int kz = (int)(k % N), ky = (int)((k / N) % N), kx = (int)(k / ((int64_t)N * N));
+    const int64_t km = ((int64_t)((N - kx) % N) * N + (N - ky) % N) * N + (N - kz) % N;
+    const Cplx<T>* Xn = X + node * (int64_t)xslots * n3;
+    const int nfields = (lf1 >= 0 ? lf1 : lf0) + 1;
     T gr = 0, gi = 0;
-    for (int s = 0; s < rank; ++s) {
-        const T u = Uk[s * n3 + k];
-        const Cplx<T> v = Xn[s * n3 + k];
-        gr = fma(u, v.x, gr);
-        gi = fma(u, v.y, gi);
+    Cplx<T> l0{T(0), T(0)}, l1{T(0), T(0)};
+    for (int m = 0; 2 * m < nfields; ++m) {
+        const Cplx<T> z = Xn[m * n3 + k], w = Xn[m * n3 + km];
+        // spectra of the real fields 2m and 2m + 1 packed in slot m
+        const Cplx<T> fa{(z.x + w.x) * T(0.5), (z.y - w.y) * T(0.5)};
+        const Cplx<T> fb{(z.y + w.y) * T(0.5), (w.x - z.x) * T(0.5)};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int fi = 2 * m + h;
+            const Cplx<T> v = h ? fb : fa;
+            if (fi < rank) {
+                const T u = Uk[fi * n3 + k];
+                gr = fma(u, v.x, gr);
+                gi = fma(u, v.y, gi);
+            } else if (fi == lf0) {
+                l0 = v;
+            } else if (fi == lf1) {
+                l1 = v;
+            }
+        }
     }
     const T GL = loss_multiplier<T>(GL0, GLd, Lr, rho, per_node, np.dlog, Nrho, n3, k);
-    // the gain and each loss convolution get their own field: packing two real results of
-    // very different size into one complex transform would leak the rounding of the larger
-    // one (K_L g ~ n everywhere) into the smaller one (the gain, tiny in the tails)
+    // the gain and each loss convolution get their own inverse transform: packing two real
+    // results of very different size into one complex transform would leak the rounding of the
+    // larger one (K_L g ~ n everywhere) into the smaller one (the gain, tiny in the tails)
     Cplx<T>* Yn = Y + node * (int64_t)yfields * n3;
     Yn[k] = Cplx<T>{scale * gr, scale * gi};
-    const Cplx<T> l0 = Xn[ls0 * n3 + k];
     Yn[n3 + k] = Cplx<T>{GL * l0.x, GL * l0.y};
-    if (ls1 >= 0) {
-        const Cplx<T> l1 = Xn[ls1 * n3 + k];
-        Yn[2 * n3 + k] = Cplx<T>{GL * l1.x, GL * l1.y};
-    }
+    if (lf1 >= 0) Yn[2 * n3 + k] = Cplx<T>{GL * l1.x, GL * l1.y};
 }
 
 template <typename T>
@@ -463,20 +485,20 @@ cudaError_t launch_project(const DevTables<T>& t, const T* P, NodeParams np, int
 
 template <typename T>
 cudaError_t launch_load_field(int N, const T* a, const T* b, const int64_t* offs, int64_t nodes,
-                              Cplx<T>* X, int xfields, int slot, cudaStream_t s) {
+                              Cplx<T>* X, int xfields, int slot, int part, cudaStream_t s) {
     if (nodes <= 0) return cudaSuccess;
     const int64_t n3 = (int64_t)N * N * N;
-    k_load_field<T><<<dim3(blocks_for(n3, 256), (unsigned)nodes), 256, 0, s>>>(n3, a, b, offs, X, xfields, slot);
+    k_load_field<T><<<dim3(blocks_for(n3, 256), (unsigned)nodes), 256, 0, s>>>(n3, a, b, offs, X, xfields, slot, part);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_combine(const DevTables<T>& t, const Cplx<T>* X, int xfields, NodeParams np,
-                           int64_t nodes, T scale, int ls0, int ls1, Cplx<T>* Y, int yfields,
+cudaError_t launch_combine(const DevTables<T>& t, const Cplx<T>* X, int xslots, NodeParams np,
+                           int64_t nodes, T scale, int lf0, int lf1, Cplx<T>* Y, int yfields,
                            cudaStream_t s) {
     if (nodes <= 0) return cudaSuccess;
     const int64_t n3 = (int64_t)t.N * t.N * t.N;
-    k_combine<T><<<dim3(blocks_for(n3, 256), (unsigned)nodes), 256, 0, s>>>(X, xfields, t.Uk, t.Lr, t.GL0, t.GLd, t.cr, np, t.Nrho, t.rank, n3, scale, ls0, ls1, Y, yfields);
+    k_combine<T><<<dim3(blocks_for(n3, 256), (unsigned)nodes), 256, 0, s>>>(X, xslots, t.Uk, t.Lr, t.GL0, t.GLd, t.cr, np, t.N, t.Nrho, t.rank, n3, scale, lf0, lf1, Y, yfields);
     return cudaGetLastError();
 }
 
@@ -525,7 +547,7 @@ cudaError_t launch_finalize(int N, int Nrho, const Cplx<T>* Y, int yfields, cons
     template cudaError_t launch_project<T>(const DevTables<T>&, const T*, NodeParams, int64_t,        \
                                            Cplx<T>*, int, cudaStream_t);                              \
     template cudaError_t launch_load_field<T>(int, const T*, const T*, const int64_t*, int64_t,       \
-                                              Cplx<T>*, int, int, cudaStream_t);                      \
+                                              Cplx<T>*, int, int, int, cudaStream_t);                 \
     template cudaError_t launch_combine<T>(const DevTables<T>&, const Cplx<T>*, int, NodeParams,      \
                                            int64_t, T, int, int, Cplx<T>*, int, cudaStream_t);        \
     template cudaError_t launch_loss_pair<T>(const DevTables<T>&, const Cplx<T>*, int, NodeParams,    \

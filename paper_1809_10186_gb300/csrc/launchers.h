@@ -50,28 +50,34 @@ cudaError_t launch_vjp_products(const DevTables<double>& t, const double* f, con
 template <typename T>
 struct Cplx { T x, y; };
 
-// X[node][s] (complex) = sum_r Vr[s][r] w_r rho_r(node) P[node][r]  for s < rank.
+// Packed real fields: field i of a node lives in the real (i even) or imaginary (i odd) part of
+// complex slot i / 2, so one complex transform carries two real fields.
+// Projected field s (s < rank) = sum_r Vr[s][r] w_r rho_r(node) P[node][r], packed into
+// X[node][xslots]; with odd rank the imaginary part of the last slot is left zero.
 template <typename T>
 cudaError_t launch_project(const DevTables<T>& t, const T* P, NodeParams np, int64_t nodes,
-                           Cplx<T>* X, int xfields, cudaStream_t s);
+                           Cplx<T>* X, int xslots, cudaStream_t s);
 
-// X[node][slot] = a (real -> complex) for an input field a (offs as above) or a*b product.
+// Field a (offs as above) or the product a*b into X[node][slot]: part 0 writes {v, 0}, part 1
+// writes only the imaginary part (the real part keeps the field written there before).
 template <typename T>
 cudaError_t launch_load_field(int N, const T* a, const T* b, const int64_t* offs, int64_t nodes,
-                              Cplx<T>* X, int xfields, int slot, cudaStream_t s);
+                              Cplx<T>* X, int xfields, int slot, int part, cudaStream_t s);
 
 // In-place 3-D DFT of `count` complex fields of N^3 (forward: scale 1/N^3, sign -1).
 template <typename T>
 cudaError_t launch_dft3(const DevTables<T>& t, Cplx<T>* X, int64_t count, bool forward,
                         cudaStream_t s);
 
-// Y[node][0] = scale * sum_s Uk[s] X[node][s];  Y[node][1] = GL X[node][loss_slot0];
-// if loss_slot1 >= 0: Y[node][2] = GL X[node][loss_slot1]. GL = sum_r rho_r(node) Lr[r]: the
+// X holds the forward DFTs of packed real fields (see launch_project); field i's spectrum is
+// recovered from slot m = i / 2 as (Z_k + conj Z_-k) / 2 (i even) or (Z_k - conj Z_-k) / 2i.
+// Y[node][0] = scale * sum_s Uk[s] Xhat_s;  Y[node][1] = GL Xhat_{loss_field0};
+// if loss_field1 >= 0: Y[node][2] = GL Xhat_{loss_field1}. GL = sum_r rho_r(node) Lr[r]: the
 // plan's FP64-built table when no per-node parameters are given, else summed in FP64 (the
 // radial sum cancels strongly at large |k|, so it is never accumulated in FP32).
 template <typename T>
-cudaError_t launch_combine(const DevTables<T>& t, const Cplx<T>* X, int xfields, NodeParams np,
-                           int64_t nodes, T scale, int loss_slot0, int loss_slot1, Cplx<T>* Y,
+cudaError_t launch_combine(const DevTables<T>& t, const Cplx<T>* X, int xslots, NodeParams np,
+                           int64_t nodes, T scale, int loss_field0, int loss_field1, Cplx<T>* Y,
                            int yfields, cudaStream_t s);
 
 // U[node][r] = w_r rho_r(node) sum_s Vr[s][r] Re X[node][s]   (after an inverse DFT)
