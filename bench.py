@@ -172,6 +172,13 @@ def fft_algorithmic_flops_per_node(N, Nrho, npairs):
     return Nrho * npairs * (5.0 * N ** 3 * math.log2(N ** 3) + 20.0 * N ** 3)
 
 
+# DRAM bytes (read + write) per node of one translate-product launch at N = 32, N_rho = 32, M = 38,
+# from the ncu capture summarised in profiles/ (None for configurations without a capture of the
+# current kernel version).
+TRAFFIC_PER_NODE = {("f16s", 32, 32, 38): 269.24e6 / 69, ("bf16s", 32, 32, 38): None,
+                    ("fp32", 32, 32, 38): None}
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -296,7 +303,8 @@ def main():
         roof = {"bound": "tensor", "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"
                 if peaks.get("bf16_tflops_sustained") else "fallback 1.7 PFLOP/s sustained"}
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                 "traffic": None, "kernel": "translate-product",
+                 "traffic": (TRAFFIC_PER_NODE.get((prec, N, Nr, 2 * npairs)) or 0) * nodes_per_launch or None,
+                 "traffic_unit": "bytes per launch", "kernel": "translate-product",
                  "kernel_share": prof["gain_ms"] / ms if ms else None,
                  "flops_per_node": flops_node, "nodes_per_launch": nodes_per_launch,
                  "fft_algorithmic_tflops": fft_algorithmic_flops_per_node(N, Nr, npairs) * value / world / 1e12})
