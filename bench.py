@@ -190,9 +190,10 @@ def _peaks():
 
 def run_reference(a):
     import numpy as np  # noqa: F401
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    from paper_1809_10186_gb300.multirank import rank_env
+    env = rank_env()
+    world = env.world
+    if env.rank != 0:   # rank 0 alone runs the oracle; the other ranks exit without work
         return 0
     from paper_1809_10186_gb300 import workloads as W
     cfg = W.CONFIGS[WORKLOAD]
@@ -234,10 +235,10 @@ def main():
     import numpy as np
     import torch
     from paper_1809_10186_gb300 import binding, workloads as W
+    from paper_1809_10186_gb300.multirank import job_throughput, max_over_ranks, rank_env, rank_seed
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    env = rank_env()
+    world, rank, local = env.world, env.rank, env.local
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -249,7 +250,7 @@ def main():
     N, L, M, Nr = cfg["N"], cfg["L"], cfg["M"], cfg["Nrho"]
     B = a.nodes or cfg["B"]
     prec = a.prec
-    F, _ = W.two_maxwellian(B, N, L, cfg["seed"] + rank, dtype=np.float32)
+    F, _ = W.two_maxwellian(B, N, L, rank_seed(cfg["seed"], rank), dtype=np.float32)
     f = torch.from_numpy(F).cuda()
     q = torch.empty_like(f)
     plan = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=M, N_rho=Nr, svd_tol=cfg["svd_tol"], precision=prec)
@@ -277,16 +278,12 @@ def main():
         prof = p.profile_end()
         clocks = sampler.stop()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")   # the slowest rank's time
         p.stream_status()
         return ms, prof, clocks
 
     ms, prof, clocks = timed(plan, a.steps, a.warmup)
-    value = world * B * a.steps / (ms / 1e3)
+    value = job_throughput(world, B, a.steps, ms / 1e3)
 
     # roofline of the dominant kernel (translate-product), from the library's own events
     per_launch_ms = prof["gain_ms"] / max(1, prof["gain_timed"])
@@ -335,12 +332,8 @@ def main():
         for _ in range(ke):
             plan.collide_host(fh, qh)
         barrier()
-        dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        line["e2e"] = {"value": world * B * ke / dt, "unit": "node-evals/s",
+        dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        line["e2e"] = {"value": job_throughput(world, B, ke, dt), "unit": "node-evals/s",
                        "h2d_bytes_per_step": fh.numel() * 4, "d2h_bytes_per_step": qh.numel() * 4}
 
     # the other forms on the same nodes: the plain FP32 GPU form and the other 16-bit mode
@@ -354,7 +347,7 @@ def main():
             ko = max(1, a.steps // 2)
             mso, profo, _ = timed(po, ko, 1)
             outputs[other] = q.clone()
-            line["compare"][other] = {"value": world * B * ko / (mso / 1e3), "unit": "node-evals/s",
+            line["compare"][other] = {"value": job_throughput(world, B, ko, mso / 1e3), "unit": "node-evals/s",
                                       "translate_kernel_ms_per_node": profo["gain_ms"] / max(1, profo["nodes"])}
             po.close()
         plan.collide(f, out=q)
