@@ -17,7 +17,10 @@
 // shared-memory A operand once, and the epilogue combines hi + 2^-e lo in FP32. The + sign's x
 // filter carries the factor 2 w_p, so the products need no further weighting.
 //
-// One CTA per (radial point, node): two epilogue warpgroups and one MMA warp. Warpgroup w owns the
+// One CTA per (radial point, node): two epilogue warpgroups and a third warpgroup holding the MMA
+// warp (its other three warps only balance the register file: after set-up the third warpgroup
+// gives registers back and the epilogue warpgroups take them, 224 per thread, so that an epilogue
+// step loads a whole tile row from TMEM behind one wait). Warpgroup w owns the
 // tiles t = w (mod 2) of every pass (all n columns, one TMEM lane per thread), so the two
 // warpgroups form two independent pipelines whose MMA <-> epilogue hand-offs overlap. Each
 // warpgroup has its own TMEM slots: one for pass 1 (2n columns) and one shared by passes 2 and 3
@@ -57,8 +60,12 @@ struct Geo {
     static constexpr int KG = N / 8;              // core-matrix groups along K
     static constexpr int TW = T / 2;              // tiles per epilogue warpgroup
     static constexpr int EPI_WARPS = 8;           // warpgroup w = warp / 4 owns tiles t = w (mod 2)
-    static constexpr int THREADS = 32 * EPI_WARPS + 32;
+    static constexpr int THREADS = 32 * EPI_WARPS + 128;   // + a warpgroup holding the MMA warp
     static constexpr int ISSUER = EPI_WARPS;      // warp index of the MMA warp
+    // registers per thread: 168 at launch (65536 / 384, rounded down to a multiple of 8), then
+    // 224 for the epilogue warpgroups and 56 for the third: 256 * 224 + 128 * 56 = 384 * 168
+    static constexpr uint32_t REG_LAUNCH = 168, REG_EPI = 224, REG_MMA = 56;
+    static_assert(256 * REG_EPI + 128 * REG_MMA <= 384 * REG_LAUNCH, "register reallocation exceeds the pool");
     // filter block of one (r, pair), K-major B operands: row n, column k at
     // (n/8) FB_SBO + (k/8) FB_LBO + (n%8) 16 + (k%8) 2. B1 rows: +hi, -hi, +lo, -lo (n each);
     // B2 and B3, per sign: hi, lo (n each)
@@ -107,18 +114,6 @@ struct Bars {
     uint64_t filt[2], fdone[2];        // filter buffers: copy landed; all MMAs of the pair using it done
     uint64_t drain;
 };
-
-// 8 columns of this thread's lane of the hi and lo parts (at c and c + N), combined as
-// hi + eps lo in FP32; one sign at a time keeps 16 loaded values live next to the accumulators.
-template <int N>
-__device__ __forceinline__ void load_combined(uint32_t taddr, float eps, float (&v)[8]) {
-    float hi[8], lo[8];
-    tc::tmem_ld8(taddr, hi);
-    tc::tmem_ld8(taddr + N, lo);
-    tc::tmem_wait_ld();
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = fmaf(lo[j], eps, hi[j]);
-}
 
 template <bool BF>
 __device__ __forceinline__ void pack8(const float (&v)[8], uint32_t (&u)[4]) {
@@ -175,7 +170,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
         }
         __syncwarp();
         tc::tmem_alloc(&s_tmem, G::TMEM_COLS);
-    } else if (!BF) {
+    } else if (!BF && warp < G::EPI_WARPS) {
         float mx = 0.f;
         for (int e = tid; e < n3; e += 32 * G::EPI_WARPS) mx = fmaxf(mx, fabsf(__ldg(fb + e)));
 #pragma unroll
@@ -200,7 +195,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
     const float out_scale = BF ? 1.f : exp2f(-2.f * kP1ShiftF16) / (sf * sf);
 
     // ---- f -> TMEM as the pass-1 A operand: tile t, lane l = yl N + z holds f[0..N)[t ZT + yl][z] --
-    if (!issuer) {
+    if (warp < G::EPI_WARPS) {
         const int q = warp & 3, w = warp >> 2, l = 32 * q + lane, yl = l / N, z = l % N;
         for (int t = w; t < G::T; t += 2) {
             const float* src = fb + (size_t)(t * G::ZT + yl) * N + z;
@@ -217,8 +212,9 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-
-    if (issuer) {
+    if (warp >= G::EPI_WARPS) {
+      tc::setmaxnreg_dec<G::REG_MMA>();   // every warp of the third warpgroup
+      if (issuer) {
         // ================================ MMA warp (converged) ================================
         // per-slot / per-buffer state as bit masks (bit i = slot or buffer i), kept in registers
         uint32_t used = 0, ph_free = 0, ph_a2full = 0, ph_a3full = 0, ph_fdone = 0;
@@ -325,7 +321,9 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
 #undef DGFS_ACQUIRE
 #undef DGFS_WAITW
     mma_done:;
+      }
     } else {
+        tc::setmaxnreg_inc<G::REG_EPI>();
         // ============================== epilogue warpgroups ===================================
         // warpgroup w owns tiles t = 2k + w (k < TW) of every pass; thread = TMEM lane l
         const int q = warp & 3, w = warp >> 2;
@@ -359,21 +357,25 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                     DGFS_WAITE(&bars.full[w], ph_full & 1u);
                     ph_full ^= 1u;
                     tc::tc_fence_after();
+                    {
+                        float v[2][N];   // the thread's row of the tile, both signs, behind one wait
 #pragma unroll
-                    for (int g = 0; g < 2; ++g)
+                        for (int g = 0; g < 2; ++g)
 #pragma unroll
-                        for (int c = 0; c < N / 8; ++c) {   // 8 columns x' = 8c .. 8c + 7
-                            float v[8];
-                            tc::tmem_ld8(tP1 + g * N + 8 * c, v);
-                            tc::tmem_wait_ld();
-                            if (g == 1 && c == N / 8 - 1) {
-                                tc::tc_fence_before();
-                                tc::mbar_arrive(&bars.freeb[w]);
+                            for (int c = 0; c < N / 16; ++c)
+                                tc::tmem_ld16(tP1 + g * N + 16 * c, *reinterpret_cast<float(*)[16]>(&v[g][16 * c]));
+                        tc::tmem_wait_ld();
+                        tc::tc_fence_before();
+                        tc::mbar_arrive(&bars.freeb[w]);
+#pragma unroll
+                        for (int g = 0; g < 2; ++g)
+#pragma unroll
+                            for (int c = 0; c < N / 8; ++c) {   // 8 columns x' = 8c .. 8c + 7
+                                uint32_t u[4];
+                                pack8<BF>(*reinterpret_cast<const float(*)[8]>(&v[g][8 * c]), u);
+                                tc::st_shared_v4(a2_row + g * G::A2_BYTES + c * G::A2_SBO, u[0], u[1], u[2], u[3]);
                             }
-                            uint32_t u[4];
-                            pack8<BF>(v, u);
-                            tc::st_shared_v4(a2_row + g * G::A2_BYTES + c * G::A2_SBO, u[0], u[1], u[2], u[3]);
-                        }
+                    }
                     tc::fence_proxy_async();
                     tc::mbar_arrive(&bars.a2_full[w]);
                 }
@@ -389,21 +391,30 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                     tc::tc_fence_after();
                     const uint32_t ky = (y >> 3) * G::A3_LBO + (y & 7) * 16;
 #pragma unroll
-                    for (int g = 0; g < 2; ++g)
+                    for (int g = 0; g < 2; ++g) {   // one sign: hi and lo of the row behind one wait
+                        float hi[N], lo[N];
+#pragma unroll
+                        for (int c = 0; c < N / 16; ++c) {
+                            tc::tmem_ld16(tB + g * 2 * N + 16 * c, *reinterpret_cast<float(*)[16]>(&hi[16 * c]));
+                            tc::tmem_ld16(tB + g * 2 * N + N + 16 * c, *reinterpret_cast<float(*)[16]>(&lo[16 * c]));
+                        }
+                        tc::tmem_wait_ld();
+                        if (g == 1) {
+                            tc::tc_fence_before();
+                            tc::mbar_arrive(&bars.freeb[2 + w]);
+                        }
 #pragma unroll
                         for (int c = 0; c < N / 8; ++c) {   // 8 columns z' = 8c .. 8c + 7
                             float v[8];
-                            load_combined<N>(tB + g * 2 * N + 8 * c, eps, v);
-                            if (g == 1 && c == N / 8 - 1) {
-                                tc::tc_fence_before();
-                                tc::mbar_arrive(&bars.freeb[2 + w]);
-                            }
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) v[j] = fmaf(lo[8 * c + j], eps, hi[8 * c + j]);
                             uint32_t u[4];
                             pack8<BF>(v, u);
                             const int mg = mg3 + c;
                             tc::st_shared_v4(sb + G::S_A3 + g * G::A3_BYTES + (mg >> 4) * G::A3_TS + (mg & 15) * G::A3_SBO + ky,
                                              u[0], u[1], u[2], u[3]);
                         }
+                    }
                     if (k == G::TW) {
                         tc::fence_proxy_async();
                         tc::mbar_arrive(&bars.a3_full);
@@ -417,20 +428,20 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                 ph_full ^= 2u;
                 tc::tc_fence_after();
 #pragma unroll
-                for (int c = 0; c < N / 4; ++c) {   // 4 columns y' = 4c .. 4c + 3
-                    float hp[4], lp[4], hm[4], lm[4];
-                    tc::tmem_ld4(tB + 4 * c, hp);
-                    tc::tmem_ld4(tB + N + 4 * c, lp);
-                    tc::tmem_ld4(tB + 2 * N + 4 * c, hm);
-                    tc::tmem_ld4(tB + 3 * N + 4 * c, lm);
+                for (int c = 0; c < N / 16; ++c) {   // 16 columns y' = 16c .. 16c + 15 behind one wait
+                    float hp[16], lp[16], hm[16], lm[16];
+                    tc::tmem_ld16(tB + 16 * c, hp);
+                    tc::tmem_ld16(tB + N + 16 * c, lp);
+                    tc::tmem_ld16(tB + 2 * N + 16 * c, hm);
+                    tc::tmem_ld16(tB + 3 * N + 16 * c, lm);
                     tc::tmem_wait_ld();
-                    if (c == N / 4 - 1) {
+                    if (c == N / 16 - 1) {
                         tc::tc_fence_before();
                         tc::mbar_arrive(&bars.freeb[2 + w]);
                     }
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        acc[k][4 * c + j] = fmaf(fmaf(lp[j], eps, hp[j]), fmaf(lm[j], eps, hm[j]), acc[k][4 * c + j]);
+                    for (int j = 0; j < 16; ++j)
+                        acc[k][16 * c + j] = fmaf(fmaf(lp[j], eps, hp[j]), fmaf(lm[j], eps, hm[j]), acc[k][16 * c + j]);
                 }
             }
         }

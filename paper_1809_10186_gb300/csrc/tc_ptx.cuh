@@ -171,6 +171,13 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// Register reallocation between warpgroups (every warp of the warpgroup executes it). The block's
+// register pool is fixed at launch: the increments must not exceed what the decrements release.
+template <uint32_t R>
+__device__ __forceinline__ void setmaxnreg_inc() { asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(R)); }
+template <uint32_t R>
+__device__ __forceinline__ void setmaxnreg_dec() { asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(R)); }
+
 // True in exactly one lane of a converged warp (the lowest lane, the same lane every call).
 __device__ __forceinline__ bool elect_one() {
     uint32_t e;
