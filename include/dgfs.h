@@ -150,6 +150,25 @@ dgfs_status dgfs_collide_ragged(const dgfs_plan_t* plans, int nplans, const int3
                                 const double* node_b, int64_t B, const void* f, void* Q,
                                 void* stream);
 
+/* A ragged schedule: the node layout of dgfs_collide_ragged (plan per node, offsets, per-node
+   gamma and b) prepared once, for a mesh whose layout does not change between calls (a DG mesh
+   over time steps). dgfs_ragged_create validates the layout exactly as dgfs_collide_ragged does,
+   groups the nodes by plan and copies the per-class offsets, gamma and b to device memory the
+   schedule owns (it allocates; the call is synchronous). dgfs_ragged_collide then computes
+   Q(f,f) for every node with stream-ordered kernel launches only, no host staging, so a whole
+   mixed-N batch can be captured in one CUDA graph. The plans must outlive the schedule; calls
+   through one schedule (or its plans) must not run concurrently on different streams.
+   The paper has no counterpart (its element-local parallelism, Sec. 3, is the reason nodes are
+   independent). Arguments as dgfs_collide_ragged; node_plan, node_offset, node_gamma, node_b
+   are HOST arrays, read during the create call only. */
+typedef struct dgfs_ragged_s* dgfs_ragged_t;
+dgfs_status dgfs_ragged_create(const dgfs_plan_t* plans, int nplans, const int32_t* node_plan,
+                               const int64_t* node_offset, const double* node_gamma,
+                               const double* node_b, int64_t B, dgfs_ragged_t* out);
+dgfs_status dgfs_ragged_collide(dgfs_ragged_t ragged, const void* f, void* Q, void* stream);
+/* Releases the schedule's device arrays (synchronises the device first). NULL is a no-op. */
+dgfs_status dgfs_ragged_destroy(dgfs_ragged_t ragged);
+
 /* dgfs_collide with HOST buffers: copies f to the device, computes, copies Q back and
    synchronises the stream before returning. f_host/Q_host may be pageable or pinned. */
 dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host, int64_t B,

@@ -59,6 +59,11 @@ _SIGNATURES = {
     "dgfs_collide_ragged": [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_double), _I64, _P, _P, _P],
+    "dgfs_ragged_create": [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double), _I64, ctypes.POINTER(_P)],
+    "dgfs_ragged_collide": [_P, _P, _P, _P],
+    "dgfs_ragged_destroy": [_P],
     "dgfs_collide_host": [_P, _P, _P, _I64, _P],
     "dgfs_collide_noalloc": [_P, _P, _P, _I64, _P],
     "dgfs_stream_status": [_P, _P],
@@ -268,6 +273,51 @@ def collide_ragged(plans, node_plan, node_offset, f_packed, node_gamma=None, nod
                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
           "dgfs_collide_ragged")
     return out
+
+
+class RaggedSchedule:
+    """A mixed-N node layout prepared once (dgfs_ragged_create): per-class node arrays live on the
+    device, so collide() issues kernel launches only and can be captured in a CUDA graph."""
+
+    def __init__(self, plans, node_plan, node_offset, node_gamma=None, node_b=None):
+        import numpy as np
+        node_plan = np.ascontiguousarray(node_plan, dtype=np.int32)
+        node_offset = np.ascontiguousarray(node_offset, dtype=np.int64)
+        self.plans = list(plans)   # the plans must outlive the schedule
+        handles = (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
+        gptr = bptr = None
+        if node_gamma is not None:
+            node_gamma = np.ascontiguousarray(node_gamma, dtype=np.float64)
+            gptr = node_gamma.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if node_b is not None:
+            node_b = np.ascontiguousarray(node_b, dtype=np.float64)
+            bptr = node_b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        h = ctypes.c_void_p()
+        check(lib().dgfs_ragged_create(handles, len(plans), node_plan.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       node_offset.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), gptr, bptr,
+                                       ctypes.c_int64(node_plan.shape[0]), ctypes.byref(h)),
+              "dgfs_ragged_create")
+        self.handle = h
+
+    def collide(self, f_packed, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(f_packed)
+        check(lib().dgfs_ragged_collide(self.handle, ctypes.c_void_p(f_packed.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+              "dgfs_ragged_collide")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().dgfs_ragged_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _autograd_function():

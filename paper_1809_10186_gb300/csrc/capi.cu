@@ -462,29 +462,38 @@ dgfs_status dgfs_collide_dgamma(dgfs_plan_t plan, const void* f, void* dQdg, int
     return compute(plan, Op::Dgamma, f, nullptr, dQdg, B, stream, false);
 }
 
+// Validation shared by the ragged entry points (host arrays).
+static dgfs_status check_ragged(const dgfs_plan_t* plans, int nplans, const int32_t* node_plan,
+                                const int64_t* node_offset, int64_t B) {
+    if (!plans || nplans <= 0) return fail(DGFS_ERR_INVALID_ARG, "no plans");
+    for (int i = 0; i < nplans; ++i)
+        if (!check_plan(plans[i])) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    for (int i = 1; i < nplans; ++i) {
+        if ((plans[i]->prec == DGFS_PREC_FP64) != (plans[0]->prec == DGFS_PREC_FP64))
+            return fail(DGFS_ERR_INVALID_ARG, "ragged plans must share the element type");
+        if (plans[i]->device != plans[0]->device) return fail(DGFS_ERR_INVALID_ARG, "ragged plans must share the device");
+    }
+    if (B < 0) return fail(DGFS_ERR_INVALID_ARG, "B must be >= 0");
+    if (B == 0) return DGFS_OK;
+    if (!node_plan || !node_offset) return fail(DGFS_ERR_INVALID_ARG, "NULL argument");
+    for (int64_t i = 0; i < B; ++i) {
+        if (node_plan[i] < 0 || node_plan[i] >= nplans) return fail(DGFS_ERR_INVALID_ARG, "node_plan out of range");
+        if (node_offset[i] < 0) return fail(DGFS_ERR_INVALID_ARG, "negative node_offset");
+        if ((node_offset[i] * (int64_t)elem_size(plans[node_plan[i]]->prec)) % 16)
+            return fail(DGFS_ERR_INVALID_ARG, "node offsets must keep 16-byte alignment");
+    }
+    return DGFS_OK;
+}
+
 dgfs_status dgfs_collide_ragged(const dgfs_plan_t* plans, int nplans, const int32_t* node_plan,
                                 const int64_t* node_offset, const double* node_gamma,
                                 const double* node_b, int64_t B, const void* f, void* Q,
                                 void* stream) {
-    if (!plans || nplans <= 0) return fail(DGFS_ERR_INVALID_ARG, "no plans");
-    for (int i = 0; i < nplans; ++i)
-        if (!check_plan(plans[i])) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
-    for (int i = 1; i < nplans; ++i)
-        if ((plans[i]->prec == DGFS_PREC_FP64) != (plans[0]->prec == DGFS_PREC_FP64))
-            return fail(DGFS_ERR_INVALID_ARG, "ragged plans must share the element type");
-    if (B < 0) return fail(DGFS_ERR_INVALID_ARG, "B must be >= 0");
-    if (B == 0) return DGFS_OK;
-    if (!node_plan || !node_offset || !f || !Q) return fail(DGFS_ERR_INVALID_ARG, "NULL argument");
+    const dgfs_status chk = check_ragged(plans, nplans, node_plan, node_offset, B);
+    if (chk != DGFS_OK || B == 0) return chk;
+    if (!f || !Q) return fail(DGFS_ERR_INVALID_ARG, "NULL argument");
     if (!aligned16(f) || !aligned16(Q)) return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
     if (f == Q) return fail(DGFS_ERR_INVALID_ARG, "output aliases the input");
-    for (int64_t i = 0; i < B; ++i) {
-        if (node_plan[i] < 0 || node_plan[i] >= nplans) return fail(DGFS_ERR_INVALID_ARG, "node_plan out of range");
-        if (node_offset[i] < 0) return fail(DGFS_ERR_INVALID_ARG, "negative node_offset");
-        const int N = plans[node_plan[i]]->hp.N;
-        if ((node_offset[i] * (int64_t)elem_size(plans[node_plan[i]]->prec)) % 16)
-            return fail(DGFS_ERR_INVALID_ARG, "node offsets must keep 16-byte alignment");
-        (void)N;
-    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     for (int pi = 0; pi < nplans; ++pi) {
         dgfs_plan_s* p = plans[pi];
@@ -520,6 +529,121 @@ dgfs_status dgfs_collide_ragged(const dgfs_plan_t* plans, int nplans, const int3
         }
         // the host vectors are staged by the copies above before they return (pageable source)
     }
+    return DGFS_OK;
+}
+
+// ---- ragged schedule: per-class node arrays resident on the device ----------------------------
+
+constexpr uint64_t kRaggedMagic = 0x4447465352414747ull;   // "DGFSRAGG"
+
+struct dgfs_ragged_s {
+    uint64_t magic = kRaggedMagic;
+    std::vector<dgfs_plan_t> plans;
+    std::vector<int64_t> count;        // nodes per plan class
+    std::vector<size_t> base;          // first index of the class in the device arrays
+    int device = 0;
+    void* d_mem = nullptr;             // [B] offsets (int64), [B] gamma, [B] b (double), by class
+};
+
+static bool check_ragged_handle(dgfs_ragged_t r) { return r && r->magic == kRaggedMagic; }
+
+dgfs_status dgfs_ragged_create(const dgfs_plan_t* plans, int nplans, const int32_t* node_plan,
+                               const int64_t* node_offset, const double* node_gamma,
+                               const double* node_b, int64_t B, dgfs_ragged_t* out) {
+    if (!out) return fail(DGFS_ERR_INVALID_ARG, "NULL output handle");
+    *out = nullptr;
+    const dgfs_status chk = check_ragged(plans, nplans, node_plan, node_offset, B);
+    if (chk != DGFS_OK) return chk;
+    auto r = std::make_unique<dgfs_ragged_s>();
+    r->plans.assign(plans, plans + nplans);
+    r->device = plans[0]->device;
+    r->count.assign(nplans, 0);
+    r->base.assign(nplans, 0);
+    for (int64_t i = 0; i < B; ++i) r->count[node_plan[i]]++;
+    for (int c = 1; c < nplans; ++c) r->base[c] = r->base[c - 1] + (size_t)r->count[c - 1];
+    std::vector<int64_t> offs((size_t)B);
+    std::vector<double> gam((size_t)B), bb((size_t)B);
+    std::vector<size_t> fill(r->base);
+    for (int64_t i = 0; i < B; ++i) {
+        const int c = node_plan[i];
+        const size_t k = fill[c]++;
+        offs[k] = node_offset[i];
+        gam[k] = node_gamma ? node_gamma[i] : plans[c]->hp.gamma;
+        bb[k] = node_b ? node_b[i] : plans[c]->hp.b;
+    }
+    if (B > 0) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        DGFS_CUDA(cudaSetDevice(r->device), "cudaSetDevice");
+        const size_t bytes = (size_t)B * (sizeof(int64_t) + 2 * sizeof(double));
+        cudaError_t e = cudaMalloc(&r->d_mem, bytes);
+        if (e != cudaSuccess) {
+            cudaSetDevice(cur);
+            return fail(DGFS_ERR_OOM, "ragged schedule: cudaMalloc failed");
+        }
+        unsigned char* m = static_cast<unsigned char*>(r->d_mem);
+        e = cudaMemcpy(m, offs.data(), (size_t)B * sizeof(int64_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(m + (size_t)B * sizeof(int64_t), gam.data(), (size_t)B * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(m + (size_t)B * (sizeof(int64_t) + sizeof(double)), bb.data(), (size_t)B * sizeof(double),
+                           cudaMemcpyHostToDevice);
+        cudaSetDevice(cur);
+        if (e != cudaSuccess) {
+            cudaFree(r->d_mem);
+            return cuda_fail(e, "ragged schedule: upload");
+        }
+    }
+    *out = r.release();
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_ragged_collide(dgfs_ragged_t r, const void* f, void* Q, void* stream) {
+    if (!check_ragged_handle(r)) return fail(DGFS_ERR_STATE, "invalid or destroyed ragged schedule");
+    int64_t B = 0;
+    for (int64_t c : r->count) B += c;
+    if (B == 0) return DGFS_OK;
+    if (!f || !Q) return fail(DGFS_ERR_INVALID_ARG, "NULL argument");
+    if (!aligned16(f) || !aligned16(Q)) return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
+    if (f == Q) return fail(DGFS_ERR_INVALID_ARG, "output aliases the input");
+    for (dgfs_plan_t p : r->plans)
+        if (!check_plan(p)) return fail(DGFS_ERR_STATE, "a plan of the ragged schedule was destroyed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char* m = static_cast<unsigned char*>(r->d_mem);
+    const int64_t* d_offs = reinterpret_cast<const int64_t*>(m);
+    const double* d_gam = reinterpret_cast<const double*>(m + (size_t)B * sizeof(int64_t));
+    const double* d_b = d_gam + B;
+    for (size_t c = 0; c < r->plans.size(); ++c) {
+        dgfs_plan_s* p = r->plans[c];
+        if (r->count[c] == 0) continue;
+        std::lock_guard<std::mutex> lock(p->host_mu);
+        DGFS_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+        for (int64_t n0 = 0; n0 < r->count[c]; n0 += p->chunk) {
+            const int64_t nn = std::min<int64_t>(p->chunk, r->count[c] - n0);
+            const size_t k = r->base[c] + (size_t)n0;
+            NodeParams np{d_gam + k, d_b + k, p->hp.gamma, p->hp.b, 0};
+            const dgfs_status st = p->prec == DGFS_PREC_FP64
+                ? run_chunk<double>(p, Op::Collide, static_cast<const double*>(f), nullptr, static_cast<double*>(Q),
+                                    d_offs + k, np, nn, s)
+                : run_chunk<float>(p, Op::Collide, static_cast<const float*>(f), nullptr, static_cast<float*>(Q),
+                                   d_offs + k, np, nn, s);
+            if (st != DGFS_OK) return st;
+        }
+    }
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_ragged_destroy(dgfs_ragged_t r) {
+    if (!r) return DGFS_OK;
+    if (!check_ragged_handle(r)) return fail(DGFS_ERR_STATE, "invalid or destroyed ragged schedule");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(r->device);
+    cudaDeviceSynchronize();
+    cudaFree(r->d_mem);
+    cudaSetDevice(cur);
+    r->magic = 0;
+    delete r;
     return DGFS_OK;
 }
 

@@ -263,6 +263,64 @@ def test_ragged_mixed_grids():
     assert worst < TOL["fp32"]
 
 
+def _ragged_case(B, Ns, split, seed, L):
+    omegas = (0.5, 0.74, 0.81)
+    node_N, node_omega = W.ragged_layout(B, Ns, split, omegas, seed)
+    offs = np.zeros(B, np.int64)
+    tot = 0
+    for i in range(B):
+        offs[i] = tot
+        tot += int(node_N[i]) ** 3
+    packed = np.zeros(tot, np.float32)
+    for i in range(B):
+        n = int(node_N[i])
+        packed[offs[i]:offs[i] + n ** 3] = W.near_equilibrium(1, n, L, seed + i, dtype=np.float32)[0].ravel()
+    gam = 2 * (1 - node_omega)
+    bb = np.array([O.b_vhs(w) for w in node_omega])
+    return node_N, offs, packed, gam, bb
+
+
+@pytest.mark.parametrize("prec,Ns", [("fp32", (16, 24, 32)), ("f16s", (16, 32))])
+def test_ragged_schedule_equals_call_and_replays_in_a_graph(prec, Ns):
+    """dgfs_ragged_create/collide: device-resident layout, identical to dgfs_collide_ragged, and a
+    CUDA-graph capture of a whole mixed-N batch replays to the same result on new inputs."""
+    L, M, B = 9.0, 26, 40
+    split = tuple([1.0 / len(Ns)] * len(Ns))
+    node_N, offs, packed, gam, bb = _ragged_case(B, Ns, split, 4242, L)
+    plans = [binding.Plan(N=n, L=L, M=M, N_rho=n, precision=prec) for n in Ns]
+    cls = [list(Ns).index(int(n)) for n in node_N]
+    fp = torch.from_numpy(packed).cuda()
+    ref = binding.collide_ragged(plans, cls, offs, fp, node_gamma=gam, node_b=bb)
+    sched = binding.RaggedSchedule(plans, cls, offs, node_gamma=gam, node_b=bb)
+    q = sched.collide(fp)
+    torch.cuda.synchronize()
+    for p in plans:
+        p.stream_status()
+    assert torch.equal(q, ref)
+    # capture the whole mixed-N batch once, replay on another input
+    x = fp.clone()
+    y = torch.empty_like(fp)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        sched.collide(x, out=y, stream=s)   # warm-up outside the capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        sched.collide(x, out=y, stream=s)
+    _, _, packed2, _, _ = _ragged_case(B, Ns, split, 777, L)
+    x.copy_(torch.from_numpy(packed2).cuda())
+    g.replay()
+    torch.cuda.synchronize()
+    direct = sched.collide(torch.from_numpy(packed2).cuda())
+    torch.cuda.synchronize()
+    for p in plans:
+        p.stream_status()
+    assert torch.equal(y, direct)
+    sched.close()
+
+
 # ---- structural properties and the C ABI's contract ----------------------------------------------
 
 def test_chunking_batch_order_and_determinism():
