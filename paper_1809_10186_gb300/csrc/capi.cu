@@ -117,6 +117,8 @@ void fill_tables(dgfs_plan_s* p, std::vector<unsigned char>& blob, DevTables<T>&
     const size_t o_cr = take(h.cr.size() * sizeof(double));
     const size_t o_wr = take(h.wr.size() * sizeof(double));
     const size_t o_Uk = take(h.Uk.size() * sizeof(T));
+    const int nq2 = 3 * (N / 2) * (N / 2) + 1;
+    const size_t o_Uq = take((size_t)h.rank * nq2 * sizeof(T));
     const size_t o_Vr = take(h.Vr.size() * sizeof(T));
     const size_t o_Lr = take(h.Lr.size() * sizeof(T));
     const size_t o_GL0 = take(n3 * sizeof(T));
@@ -136,6 +138,16 @@ void fill_tables(dgfs_plan_s* p, std::vector<unsigned char>& blob, DevTables<T>&
     putd(o_cr, h.cr);
     putd(o_wr, h.wr);
     put(o_Uk, h.Uk);
+    {
+        // the radial kernel factors depend on |k|^2 only: a compact copy indexed by it
+        T* d = reinterpret_cast<T*>(blob.data() + o_Uq);
+        auto sk = [N](int q) { return q < N / 2 ? q : q - N; };
+        for (size_t i = 0; i < n3; ++i) {
+            const int kx = sk((int)(i / ((size_t)N * N))), ky = sk((int)((i / N) % N)), kz = sk((int)(i % N));
+            const int q2 = kx * kx + ky * ky + kz * kz;
+            for (int s = 0; s < h.rank; ++s) d[(size_t)s * nq2 + q2] = (T)h.Uk[(size_t)s * n3 + i];
+        }
+    }
     put(o_Vr, h.Vr);
     put(o_Lr, h.Lr);
     {
@@ -172,6 +184,7 @@ void fill_tables(dgfs_plan_s* p, std::vector<unsigned char>& blob, DevTables<T>&
     t.cr = reinterpret_cast<const double*>(o_cr);
     t.wr = reinterpret_cast<const double*>(o_wr);
     t.Uk = reinterpret_cast<const T*>(o_Uk);
+    t.Uq = reinterpret_cast<const T*>(o_Uq);
     t.Vr = reinterpret_cast<const T*>(o_Vr);
     t.Lr = reinterpret_cast<const T*>(o_Lr);
     t.GL0 = reinterpret_cast<const T*>(o_GL0);
@@ -185,7 +198,7 @@ void rebase(DevTables<T>& t, void* base) {
         using P = std::remove_reference_t<decltype(ptr)>;
         ptr = reinterpret_cast<P>(static_cast<unsigned char*>(base) + reinterpret_cast<uintptr_t>(ptr));
     };
-    fix(t.filt); fix(t.wsig); fix(t.cr); fix(t.wr); fix(t.Uk); fix(t.Vr); fix(t.Lr); fix(t.GL0); fix(t.GLd);
+    fix(t.filt); fix(t.wsig); fix(t.cr); fix(t.wr); fix(t.Uk); fix(t.Uq); fix(t.Vr); fix(t.Lr); fix(t.GL0); fix(t.GLd);
     fix(t.dftw);
 }
 
@@ -239,7 +252,8 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
     // gain products: Q(f,f) and dQ/dgamma use (f, f); Q(f,g) uses (f, g); JVP uses (f, v)
     const T* gg = (op == Op::Collide || op == Op::Dgamma) ? nullptr : g;
     if (p->prof) {
-        p->prof_launches += 11 + (op == Op::Jvp ? 1 : 0) + tc_extra_launches(p->prec);
+        p->prof_launches += (spectral_supported(tables<T>(p)) ? 4 : 11 + (op == Op::Jvp ? 1 : 0)) +
+                            tc_extra_launches(p->prec);
         p->prof_gain += 1;
         p->prof_nodes += nodes;
         if (p->prof_timed < (int64_t)p->ev.size() / 2) cudaEventRecord(p->ev[2 * p->prof_timed], s);
@@ -258,6 +272,14 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
     }
     // real fields packed two per complex slot: the rank projected fields, then the loss
     // operand(s): Q(f,g) -> field rank = g;  JVP -> field rank = v, field rank + 1 = f
+    if (spectral_supported(t)) {   // the fused three-launch Fourier stage
+        const T* la = (op == Op::Collide || op == Op::Dgamma) ? f : g;
+        e = launch_spectral<T>(t, P, np, nodes, la, op == Op::Jvp ? f : nullptr, offs,
+                               op == Op::Jvp ? T(2) : T(1), X, Y, f, op == Op::Jvp ? g : nullptr, out,
+                               p->d_flags, s);
+        if (e) return cuda_fail(e, "Fourier stage");
+        return DGFS_OK;
+    }
     const int nfields = rank + (op == Op::Jvp ? 2 : 1), xs = (nfields + 1) / 2;
     e = launch_project<T>(t, P, np, nodes, X, xs, s);
     if (e) return cuda_fail(e, "radial projection");
@@ -798,6 +820,11 @@ dgfs_status noalloc_run(dgfs_plan_s* p, const T* f, T* Q, int64_t B, unsigned ch
                                     reinterpret_cast<float*>(P), p->d_flags, s);
     else
         e = launch_gain_products(t, f, nullptr, nullptr, B, P, s);
+    if (!e && spectral_supported(t)) {   // the fused Fourier stage, as in dgfs_collide
+        e = launch_spectral<T>(t, P, np, B, f, nullptr, nullptr, T(1), X, Y, f, nullptr, Q, p->d_flags, s);
+        if (e) return cuda_fail(e, "dgfs_collide_noalloc");
+        return DGFS_OK;
+    }
     const int xs = (t.rank + 2) / 2;   // rank projected fields and f, packed two per slot
     if (!e) e = launch_project<T>(t, P, np, B, X, xs, s);
     if (!e) e = launch_load_field<T>(t.N, f, nullptr, nullptr, B, X, xs, t.rank / 2, t.rank % 2, s);

@@ -16,6 +16,7 @@ struct DevTables {
     const double* cr;   // [Nrho]
     const double* wr;   // [Nrho]
     const T* Uk;        // [rank][N^3]  DFT index order
+    const T* Uq;        // [rank][3 (N/2)^2 + 1]: Uk[s](k) = Uq[s][|k|^2] (signed lattice index)
     const T* Vr;        // [rank][Nrho]
     const T* Lr;        // [Nrho][N^3]  DFT index order
     const T* GL0;       // [N^3] sum_r rho_r(gamma, b) Lr[r]: loss multiplier of the plan's kernel
@@ -102,5 +103,18 @@ template <typename T>
 cudaError_t launch_finalize(int N, int Nrho, const Cplx<T>* Y, int yfields, const T* a,
                             const T* c, const T* G, const int64_t* offs, int64_t nodes, int mode,
                             T* out, int* flags, cudaStream_t s);
+
+// ---- fused Fourier stage (k_spectral.cu) ----------------------------------------------
+// The whole Fourier side of a non-adjoint call in three launches for N = 8, 16 (float, double)
+// and N = 32 (float), rank <= 32, Nrho <= 64: projection of P, loss operands la (field rank)
+// and lb (field rank + 1, or nullptr), forward DFT, combine with gain scale `gain_scale`,
+// inverse DFT and out = Re gain - fa Re(K_L la) - (fc ? fc Re(K_L lb) : 0). Same workspace
+// X [nodes][(rank + nloss + 1) / 2][N^3] and Y [nodes][2 or 3][N^3] as the separate kernels.
+template <typename T>
+bool spectral_supported(const DevTables<T>& t);
+template <typename T>
+cudaError_t launch_spectral(const DevTables<T>& t, const T* P, NodeParams np, int64_t nodes, const T* la,
+                            const T* lb, const int64_t* offs, T gain_scale, Cplx<T>* X, Cplx<T>* Y,
+                            const T* fa, const T* fc, T* out, int* flags, cudaStream_t s);
 
 }  // namespace dgfs
