@@ -175,7 +175,7 @@ def fft_algorithmic_flops_per_node(N, Nrho, npairs):
 # DRAM bytes (read + write) per node of one translate-product launch at N = 32, N_rho = 32, M = 38,
 # from the ncu capture summarised in profiles/ (None for configurations without a capture of the
 # current kernel version).
-TRAFFIC_PER_NODE = {("f16s", 32, 32, 38): 269.24e6 / 69, ("bf16s", 32, 32, 38): None,
+TRAFFIC_PER_NODE = {("f16s", 32, 32, 38): 232.73e6 / 64, ("bf16s", 32, 32, 38): None,
                     ("fp32", 32, 32, 38): None}
 
 
@@ -317,7 +317,10 @@ def main():
                        "nodes_per_gpu": B, "N": N, "M": M, "N_rho": Nr,
                        "svd_rank": plan.info["svd_rank_used"], "precision": prec,
                        "chunk_nodes": plan.info["chunk_nodes"],
-                       "l2": "inputs (%d MB) larger than L2 (129 MB)" % (f.numel() * 4 >> 20),
+                       "l2": "no flush: inputs %d MB (%s L2, 129 MB); each chunk writes and re-reads %d MB "
+                             "of translate products" % (f.numel() * 4 >> 20,
+                                                        "larger than" if f.numel() * 4 > 129 << 20 else "within",
+                                                        plan.info["chunk_nodes"] * Nr * N ** 3 * 4 >> 20),
                        "parallelism": "dp%d" % world},
             "gpu_launches": prof["launches"], "clocks": clocks, "roofline": roof}
 

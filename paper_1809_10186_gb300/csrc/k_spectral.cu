@@ -31,6 +31,7 @@ struct SpecGeo {
     static constexpr int T1 = N == 8 ? 64 : 256;                // k_spec_xz: V points per thread
     static constexpr int V = N2 / T1;
     static constexpr int SL = N == 32 ? 5 : 8;                  // slots (2 SL fields) per k_spec_xz CTA
+    static constexpr int RB = 16;                               // radial points of P in flight per thread
     static constexpr int T2 = 256;                             // k_spec_y
     static constexpr int GS = T2 / (2 * N);                    // slots per group: one y line per thread
     static constexpr int PT = (2 * N2 + T2 - 1) / T2;          // points per thread in k_spec_y
@@ -67,6 +68,19 @@ __device__ __forceinline__ void cp_async_cplx(Cplx<T>* dst, const Cplx<T>* src) 
         asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
+// V consecutive values (V * sizeof(T) = 4, 8 or 16 bytes, both addresses aligned to it)
+template <typename T, int V>
+__device__ __forceinline__ void cp_async_v(T* dst, const T* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    constexpr int B = V * (int)sizeof(T);
+    if constexpr (B == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(B) : "memory");
+}
 
 // One line of N complex values in shared memory (element k at base[k * stride]) transformed in
 // place in registers, times `scale`.
@@ -97,6 +111,8 @@ k_spec_xz(const T* __restrict__ P, const T* __restrict__ Vr, const double* __res
     Cplx<T>* tw = F + G::SL * G::PLANE;                         // [N]
     T* CT = reinterpret_cast<T*>(tw + N);                       // [Nrho][FG]
     T* wrho = CT + Nrho * FG;                                   // [Nrho]
+    T* ring = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(wrho + Nrho) + 15) & ~uintptr_t(15));
+                                                                // [RB][T1 V]: asynchronous copies of P
     const int g = blockIdx.x % groups, y = blockIdx.x / groups, t = threadIdx.x;
     const int s0 = g * G::SL, ns = xs - s0 < G::SL ? xs - s0 : G::SL, f0 = 2 * s0;
     const int64_t node = blockIdx.y, n3 = (int64_t)N * G::N2;
@@ -119,17 +135,30 @@ k_spec_xz(const T* __restrict__ P, const T* __restrict__ Vr, const double* __res
         for (int v = 0; v < G::V; ++v)
 #pragma unroll
             for (int i = 0; i < FG; ++i) acc[v][i] = T(0);
+        // each thread streams its own V values of P_r through a ring of RB asynchronous copies
+        // (one commit group per r), so RB radial points are in flight without holding registers
         const T* Pn = P + node * Nrho * n3 + j0;
-#pragma unroll 8
+        T* mine = ring + t * G::V;
+        auto issue = [&](int r) {
+            if (r < Nrho) cp_async_v<T, G::V>(mine + (r % G::RB) * (G::T1 * G::V), Pn + (int64_t)r * n3);
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int r = 0; r < G::RB; ++r) issue(r);
+#pragma unroll 4
         for (int r = 0; r < Nrho; ++r) {
+            cp_async_wait_group<G::RB - 1>();   // the copy of P_r has landed
             T p[G::V];
-            load_v<T, G::V>(Pn + (int64_t)r * n3, p);
+#pragma unroll
+            for (int v = 0; v < G::V; ++v) p[v] = mine[(r % G::RB) * (G::T1 * G::V) + v];
             const T* c = CT + r * FG;
 #pragma unroll
             for (int i = 0; i < FG; ++i)
 #pragma unroll
                 for (int v = 0; v < G::V; ++v) acc[v][i] = fma(c[i], p[v], acc[v][i]);
+            issue(r + G::RB);   // after the FMAs that consumed the slot's values
         }
+        cp_async_wait_all();
 #pragma unroll
         for (int i = 0; i < FG; i += 2)
             if (i / 2 < ns)
@@ -332,7 +361,8 @@ cudaError_t spectral_n(const DevTables<T>& t, const T* P, NodeParams np, int64_t
     cudaError_t e;
     {
         const int groups = (xs + G::SL - 1) / G::SL;
-        const size_t sm = sizeof(Cplx<T>) * ((size_t)G::SL * G::PLANE + N) + sizeof(T) * (size_t)t.Nrho * (2 * G::SL + 1);
+        const size_t sm = sizeof(Cplx<T>) * ((size_t)G::SL * G::PLANE + N) +
+                          sizeof(T) * ((size_t)t.Nrho * (2 * G::SL + 1) + (size_t)G::RB * G::T1 * G::V) + 16;
         e = cudaFuncSetAttribute(k_spec_xz<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         k_spec_xz<T, N><<<dim3(groups * N, nn), G::T1, sm, s>>>(P, t.Vr, t.cr, t.wr, np, t.Nrho, t.rank, la, lb, offs,
