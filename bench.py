@@ -44,6 +44,8 @@ def _args():
     ap.add_argument("--prec", default="f16s", choices=["fp32", "f16s", "bf16s"],
                     help="f16s: tensor-core translates, fp16 data + split fp16 filters (default)")
     ap.add_argument("--nodes", type=int, default=None, help="nodes per GPU (default 2048)")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="nodes per internal chunk (plan max_batch); 0: the whole per-GPU batch in one chunk")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
@@ -253,7 +255,8 @@ def main():
     F, _ = W.two_maxwellian(B, N, L, rank_seed(cfg["seed"], rank), dtype=np.float32)
     f = torch.from_numpy(F).cuda()
     q = torch.empty_like(f)
-    plan = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=M, N_rho=Nr, svd_tol=cfg["svd_tol"], precision=prec)
+    plan = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=M, N_rho=Nr, svd_tol=cfg["svd_tol"], precision=prec,
+                        max_batch=a.chunk if a.chunk > 0 else B)
     npairs = plan.info["n_pairs"]
 
     def barrier():
@@ -317,6 +320,7 @@ def main():
                        "nodes_per_gpu": B, "N": N, "M": M, "N_rho": Nr,
                        "svd_rank": plan.info["svd_rank_used"], "precision": prec,
                        "chunk_nodes": plan.info["chunk_nodes"],
+                       "workspace_gb": round(plan.info["workspace_bytes"] / 2 ** 30, 2),
                        "l2": "no flush: inputs %d MB (%s L2, 129 MB); each chunk writes and re-reads %d MB "
                              "of translate products" % (f.numel() * 4 >> 20,
                                                         "larger than" if f.numel() * 4 > 129 << 20 else "within",

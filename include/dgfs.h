@@ -89,8 +89,9 @@ typedef struct {
     int svd_rank;              /* > 0: fixed rank of the radial kernel (overrides svd_tol)      */
     int precision;             /* dgfs_precision                                               */
     int loss_mode;             /* dgfs_loss_mode                                               */
-    int64_t max_batch;         /* nodes processed per internal chunk (workspace sizing); <= 0:
-                                  chosen by the library. Compute calls accept any B >= 0.     */
+    int64_t max_batch;         /* nodes processed per internal chunk (sizes the workspace:
+                                  about 22 MB per node at N = 32, rank 19); <= 0: chosen by the library
+                                  (about 1.5 GB of workspace). Compute calls accept any B >= 0. */
 } dgfs_plan_desc;
 
 typedef struct {
@@ -170,7 +171,11 @@ dgfs_status dgfs_ragged_collide(dgfs_ragged_t ragged, const void* f, void* Q, vo
 dgfs_status dgfs_ragged_destroy(dgfs_ragged_t ragged);
 
 /* dgfs_collide with HOST buffers: copies f to the device, computes, copies Q back and
-   synchronises the stream before returning. f_host/Q_host may be pageable or pinned. */
+   synchronises before returning. f_host/Q_host may be pageable or pinned (pinned lets the
+   copies overlap the compute). The batch is split into at least four sub-batches that fit the
+   plan's staging buffers; the copies run on two copy streams owned by the plan, so the
+   host-to-device copy of one sub-batch and the device-to-host copy of the previous one overlap
+   the compute on `stream`. */
 dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host, int64_t B,
                               void* stream);
 

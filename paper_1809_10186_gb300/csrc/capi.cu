@@ -68,6 +68,9 @@ struct dgfs_plan_s {
     size_t off_P = 0, off_G = 0, off_S = 0, off_X = 0, off_Y = 0, off_io = 0, off_node = 0;
     int xfields = 0;
     std::mutex host_mu;      // serialises host-side staging of per-node arrays
+    // host-buffer entry point: copy streams and the events that pipeline copies with compute
+    cudaStream_t cs_h2d = nullptr, cs_d2h = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_h2d[2] = {}, ev_comp[2] = {}, ev_d2h[2] = {};
     // profiling session
     bool prof = false;
     std::vector<cudaEvent_t> ev;   // pairs
@@ -83,6 +86,18 @@ size_t elem_size(int prec) { return prec == DGFS_PREC_FP64 ? 8 : 4; }
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 bool check_plan(dgfs_plan_t p) { return p && p->magic == kMagic; }
+
+void destroy_io(dgfs_plan_s* p) {
+    for (cudaEvent_t* ev : {&p->ev_start, &p->ev_h2d[0], &p->ev_h2d[1], &p->ev_comp[0], &p->ev_comp[1], &p->ev_d2h[0],
+                            &p->ev_d2h[1]})
+        if (*ev) {
+            cudaEventDestroy(*ev);
+            *ev = nullptr;
+        }
+    if (p->cs_h2d) cudaStreamDestroy(p->cs_h2d);
+    if (p->cs_d2h) cudaStreamDestroy(p->cs_d2h);
+    p->cs_h2d = p->cs_d2h = nullptr;
+}
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -385,9 +400,9 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
         probe.prec = p->prec;
         workspace_layout(&probe, 1);
         const size_t per_node = probe.ws_bytes;
-        int64_t C = (int64_t)((size_t)1536 << 20) / (int64_t)per_node;
+        int64_t C = (int64_t)((size_t)4096 << 20) / (int64_t)per_node;   // about 4 GB of workspace
         C = std::max<int64_t>(1, std::min<int64_t>(C, 4096));
-        if (desc->max_batch > 0) C = std::min<int64_t>(C, desc->max_batch);
+        if (desc->max_batch > 0) C = std::min<int64_t>(desc->max_batch, (int64_t)1 << 20);   // the caller's choice
         p->chunk = C;
     }
     workspace_layout(p.get(), p->chunk);
@@ -416,6 +431,18 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
         if (p->d_flags) cudaFree(p->d_flags);
         return cuda_fail(e, "plan upload");
     }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cs_h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cs_d2h, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&p->ev_start, &p->ev_h2d[0], &p->ev_h2d[1], &p->ev_comp[0], &p->ev_comp[1], &p->ev_d2h[0],
+                            &p->ev_d2h[1]})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        destroy_io(p.get());
+        cudaFree(p->d_tables);
+        cudaFree(p->d_ws);
+        cudaFree(p->d_flags);
+        return cuda_fail(e, "plan streams and events");
+    }
     if (p->prec == DGFS_PREC_FP64) rebase(p->td, p->d_tables);
     else rebase(p->tf, p->d_tables);
     if (tc_bytes) rebase_tc_tables(p->tc, static_cast<unsigned char*>(p->d_tables) + p->table_bytes);
@@ -435,6 +462,7 @@ dgfs_status dgfs_plan_destroy(dgfs_plan_t plan) {
     cudaFree(plan->d_ws);
     cudaFree(plan->d_flags);
     for (auto& e : plan->ev) cudaEventDestroy(e);
+    destroy_io(plan);
     cudaSetDevice(cur);
     plan->magic = 0;
     delete plan;
@@ -679,13 +707,29 @@ dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host
     DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
     const size_t es = elem_size(plan->prec);
     const int64_t n3 = (int64_t)plan->hp.N * plan->hp.N * plan->hp.N;
-    unsigned char* fin = ws(plan, plan->off_io);
-    unsigned char* qout = fin + (size_t)plan->chunk * n3 * es;
-    for (int64_t n0 = 0; n0 < B; n0 += plan->chunk) {
-        const int64_t nn = std::min<int64_t>(plan->chunk, B - n0);
+    // The staging area (2 chunk fields) holds nbuf buffers of S nodes in and S nodes out. Sub-batch i
+    // uses buffer i % nbuf: its host-to-device copy (copy stream 1) overlaps the compute of sub-batch
+    // i - 1 (stream s), and the device-to-host copy of sub-batch i - 1 (copy stream 2) overlaps the
+    // compute of sub-batch i. A buffer is refilled once the compute that read it has finished, and
+    // its output half is rewritten once the copy that read it has finished.
+    const int nbuf = plan->chunk >= 2 ? 2 : 1;
+    const int64_t S = std::min<int64_t>(plan->chunk / nbuf, std::max<int64_t>(1, (B + 3) / 4));
+    DGFS_CUDA(cudaEventRecord(plan->ev_start, s), "event record");   // earlier work on s that used the plan
+    DGFS_CUDA(cudaStreamWaitEvent(plan->cs_h2d, plan->ev_start, 0), "stream wait");
+    DGFS_CUDA(cudaStreamWaitEvent(plan->cs_d2h, plan->ev_start, 0), "stream wait");
+    int64_t i = 0;
+    for (int64_t n0 = 0; n0 < B; n0 += S, ++i) {
+        const int b = (int)(i % nbuf);
+        unsigned char* fin = ws(plan, plan->off_io) + (size_t)b * 2 * S * n3 * es;
+        unsigned char* qout = fin + (size_t)S * n3 * es;
+        const int64_t nn = std::min<int64_t>(S, B - n0);
         const size_t bytes = (size_t)nn * n3 * es;
+        if (i >= nbuf) DGFS_CUDA(cudaStreamWaitEvent(plan->cs_h2d, plan->ev_comp[b], 0), "stream wait");
         DGFS_CUDA(cudaMemcpyAsync(fin, static_cast<const unsigned char*>(f_host) + (size_t)n0 * n3 * es, bytes,
-                                  cudaMemcpyHostToDevice, s), "host to device");
+                                  cudaMemcpyHostToDevice, plan->cs_h2d), "host to device");
+        DGFS_CUDA(cudaEventRecord(plan->ev_h2d[b], plan->cs_h2d), "event record");
+        DGFS_CUDA(cudaStreamWaitEvent(s, plan->ev_h2d[b], 0), "stream wait");
+        if (i >= nbuf) DGFS_CUDA(cudaStreamWaitEvent(s, plan->ev_d2h[b], 0), "stream wait");
         dgfs_status st = plan->prec == DGFS_PREC_FP64
             ? run_chunk<double>(plan, Op::Collide, reinterpret_cast<const double*>(fin), nullptr,
                                 reinterpret_cast<double*>(qout), nullptr,
@@ -694,9 +738,13 @@ dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host
                                reinterpret_cast<float*>(qout), nullptr,
                                NodeParams{nullptr, nullptr, plan->hp.gamma, plan->hp.b, 0}, nn, s);
         if (st != DGFS_OK) return st;
+        DGFS_CUDA(cudaEventRecord(plan->ev_comp[b], s), "event record");
+        DGFS_CUDA(cudaStreamWaitEvent(plan->cs_d2h, plan->ev_comp[b], 0), "stream wait");
         DGFS_CUDA(cudaMemcpyAsync(static_cast<unsigned char*>(Q_host) + (size_t)n0 * n3 * es, qout, bytes,
-                                  cudaMemcpyDeviceToHost, s), "device to host");
+                                  cudaMemcpyDeviceToHost, plan->cs_d2h), "device to host");
+        DGFS_CUDA(cudaEventRecord(plan->ev_d2h[b], plan->cs_d2h), "event record");
     }
+    DGFS_CUDA(cudaStreamSynchronize(plan->cs_d2h), "stream synchronise");
     DGFS_CUDA(cudaStreamSynchronize(s), "stream synchronise");
     return DGFS_OK;
 }

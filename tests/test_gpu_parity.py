@@ -337,14 +337,22 @@ def test_chunking_batch_order_and_determinism():
     assert torch.equal(a[perm], p1.collide(f[perm].contiguous()))
 
 
-def test_host_buffer_entry_point_matches_device():
+@pytest.mark.parametrize("max_batch,B,pinned", [(1, 3, True), (2, 5, True), (7, 5, False), (0, 9, True)])
+def test_host_buffer_entry_point_matches_device(max_batch, B, pinned):
+    """The host-buffer call pipelines its copies over sub-batches (one staging buffer when the
+    plan's chunk is one node, two otherwise); every node's result equals the device call's, on
+    two consecutive calls (the second reuses the staging buffers while the first's are fresh)."""
     N, L = 16, 5.0
-    F, _ = W.two_maxwellian(5, N, L, 12, dtype=np.float32)
-    plan = binding.Plan(N=N, L=L, gamma=0.38, M=12, N_rho=N, precision="fp32", max_batch=2)
-    fh = torch.from_numpy(F).pin_memory()
-    qh = torch.empty_like(fh).pin_memory()
-    plan.collide_host(fh, qh)
-    assert torch.equal(qh, plan.collide(fh.cuda()).cpu())
+    plan = binding.Plan(N=N, L=L, gamma=0.38, M=12, N_rho=N, precision="fp32", max_batch=max_batch)
+    for call in range(2):
+        F, _ = W.two_maxwellian(B, N, L, 12 + call, dtype=np.float32)
+        fh = torch.from_numpy(F)
+        qh = torch.empty_like(fh)
+        if pinned:
+            fh, qh = fh.pin_memory(), qh.pin_memory()
+        plan.collide_host(fh, qh)
+        assert torch.equal(qh, plan.collide(fh.cuda()).cpu()), (max_batch, B, call)
+    plan.close()
 
 
 def test_empty_batch_and_argument_errors():
