@@ -48,7 +48,8 @@ __device__ __forceinline__ constexpr int bitrev(int i) {
 }
 
 // One radix-2 stage of butterfly span LEN, then the next stage. LEN is a template parameter so
-// that every loop has a compile-time trip count and the line stays in registers.
+// that every loop has a compile-time trip count and the line stays in registers; the twiddles
+// 1 and -+i (known once the loops are unrolled) take no multiplication.
 template <typename T, int N, int LEN>
 __device__ __forceinline__ void fft_stage(Cplx<T> (&a)[N], const Cplx<T>* __restrict__ tw, bool forward) {
     constexpr int half = LEN / 2, step = N / LEN;
@@ -56,10 +57,17 @@ __device__ __forceinline__ void fft_stage(Cplx<T> (&a)[N], const Cplx<T>* __rest
     for (int i = 0; i < N; i += LEN)
 #pragma unroll
         for (int j = 0; j < half; ++j) {
-            const Cplx<T> w = tw[j * step];
-            const T wi = forward ? w.y : -w.y;
             const Cplx<T> u = a[i + j], v0 = a[i + j + half];
-            const Cplx<T> v{v0.x * w.x - v0.y * wi, v0.x * wi + v0.y * w.x};
+            Cplx<T> v;
+            if (j == 0) {                      // twiddle 1
+                v = v0;
+            } else if (4 * j * step == N) {    // twiddle -i (forward) or +i (inverse)
+                v = forward ? Cplx<T>{v0.y, -v0.x} : Cplx<T>{-v0.y, v0.x};
+            } else {
+                const Cplx<T> w = tw[j * step];
+                const T wi = forward ? w.y : -w.y;
+                v = Cplx<T>{v0.x * w.x - v0.y * wi, v0.x * wi + v0.y * w.x};
+            }
             a[i + j] = Cplx<T>{u.x + v.x, u.y + v.y};
             a[i + j + half] = Cplx<T>{u.x - v.x, u.y - v.y};
         }
