@@ -17,17 +17,17 @@
 // shared-memory A operand once, and the epilogue combines hi + 2^-e lo in FP32. The + sign's x
 // filter carries the factor 2 w_p, so the products need no further weighting.
 //
-// One CTA per (radial point, node): two epilogue warpgroups and a third warpgroup holding two MMA
-// warps, one per epilogue warpgroup (its other two warps only balance the register file: after
-// set-up the third warpgroup gives registers back and the epilogue warpgroups take them, 216 per
-// thread, so that an epilogue step loads a whole tile row from TMEM behind one wait). Warpgroup w
-// owns the tiles t = w (mod 2) of every pass (all n columns, one TMEM lane per thread), and MMA
-// warp w issues exactly that warpgroup's MMAs, so the two warpgroups form two independent
-// pipelines whose MMA <-> epilogue hand-offs overlap and neither MMA warp waits on the other
-// pipeline's hand-offs. Each warpgroup has its own TMEM slots: one for pass 1 (2n columns) and
-// one shared by passes 2 and 3 (4n columns). Both signs' pass-3 operands (full fields) stay in
-// shared memory until the products are formed; the barriers shared by both pipelines (pass-3
-// operand released, filter buffer done, final drain) take one commit from each MMA warp. All hand-offs
+// One CTA per (radial point, node): two epilogue warpgroups and a third warpgroup of four MMA
+// warps (after set-up the third warpgroup gives registers back and the epilogue warpgroups take
+// them, 216 per thread, so that an epilogue step loads a whole tile row from TMEM behind one
+// wait). Warpgroup w owns the tiles t = w (mod 2) of every pass (all n columns, one TMEM lane per
+// thread); its pass-1 groups are issued by one MMA warp and its pass-2/3 groups by another, so
+// the two warpgroups form two independent pipelines whose MMA <-> epilogue hand-offs overlap,
+// and no MMA warp waits on hand-offs that do not gate its own groups. Each warpgroup has its own
+// TMEM slots: one for pass 1 (2n columns) and one shared by passes 2 and 3 (4n columns). Both
+// signs' pass-3 operands (full fields) stay in shared memory until the products are formed; the
+// barriers shared by the MMA warps (pass-3 operand released, filter buffer done, final drain)
+// take one commit from each warp that uses the resource. All hand-offs
 // are mbarriers; every lane of the epilogue warps arrives and every wait loop branches on warp
 // votes only, so no branch diverges around the .sync.aligned tcgen05 instructions. Every wait is
 // bounded: on timeout the CTA raises flag bit 0, every role stops, the MMAs and copies in flight
@@ -123,18 +123,11 @@ __device__ __forceinline__ void pack8(const float (&v)[8], uint32_t (&u)[4]) {
     for (int j = 0; j < 4; ++j) u[j] = pack2<BF>(v[2 * j], v[2 * j + 1]);
 }
 
-// The loop of MMA warp ISSUER + w: the groups of epilogue warpgroup w (tiles t = w mod 2) of every
-// pass, with w a template parameter so that every slot, barrier and operand offset is a constant.
-// Warp ISSUER (w = 0) also refills the filter buffers. Returns early when a wait gave up (abort).
-template <int N, bool BF, int w>
-__device__ __forceinline__ void mma_warp_loop(Bars& bars, unsigned char* smem, uint32_t sb, uint32_t tmem,
-                                              const unsigned char* fglob, int npairs, volatile int* abort,
-                                              int& copies0, int& copies1, int& waited0, int& waited1) {
-    using G = Geo<N>;
-    // per-slot / per-buffer state as bit masks (bit i = slot or buffer i), kept in registers
-    uint32_t used = 0, ph_free = 0, ph_a2full = 0, ph_a3full = 0, ph_fdone = 0;
-    constexpr uint32_t id1 = tc::idesc_f16(BF, false, false, 2 * N, 128);
-    constexpr uint32_t id23 = tc::idesc_f16(BF, true, false, 2 * N, 128);
+// The MMA warps. Warpgroup w's groups are issued by two warps: mma_p1_loop<w> (pass 1 of its
+// tiles; warp w = 0 also refills the filter buffers) and mma_p23_loop<w> (passes 2 and 3), so a
+// pass-1 group is issued as soon as its TMEM slot is drained, independently of the pass-2 chain.
+// w is a template parameter: every slot, barrier and operand offset is a constant. Each returns
+// early when a wait gave up (abort).
 #define DGFS_WAITW(bar, ph)                                             \
     do {                                                                \
         if (!tc::warp_wait((bar), (ph), abort)) return;                 \
@@ -148,11 +141,15 @@ __device__ __forceinline__ void mma_warp_loop(Bars& bars, unsigned char* smem, u
         used |= 1u << (s);                                              \
         tc::tc_fence_after();                                           \
     } while (0)
-    // descriptors: constant stride parts + (shared address >> 4); every offset below is a
-    // compile-time constant or one multiply-add, so the issue loop stays short
+
+template <int N, bool BF, int w>
+__device__ __forceinline__ void mma_p1_loop(Bars& bars, unsigned char* smem, uint32_t sb, uint32_t tmem,
+                                            const unsigned char* fglob, int npairs, volatile int* abort,
+                                            int& copies0, int& copies1, int& waited0, int& waited1) {
+    using G = Geo<N>;
+    uint32_t used = 0, ph_free = 0, ph_fdone = 0;   // bit masks (bit i = slot or buffer i)
+    constexpr uint32_t id1 = tc::idesc_f16(BF, false, false, 2 * N, 128);
     constexpr uint64_t dF = tc::sdesc_base(G::FB_LBO, G::FB_SBO);
-    constexpr uint64_t dA2 = tc::sdesc_base(G::A2_LBO, G::A2_SBO);
-    constexpr uint64_t dA3 = tc::sdesc_base(G::A3_LBO, G::A3_SBO);
     const uint32_t sb16 = sb >> 4;
     for (int p = 0; p < npairs; ++p) {
         const int fbuf = p & 1;
@@ -163,62 +160,75 @@ __device__ __forceinline__ void mma_warp_loop(Bars& bars, unsigned char* smem, u
         }
         tc::tc_fence_after();
         const uint32_t f16 = sb16 + (G::S_F + fbuf * G::F_BLOCK) / 16;   // filter block of this pair
-        // front: pass 1 of tile 2k + w (slot w) and pass 2 of tile 2(k - 1) + w (slot 2 + w)
-        for (int k = 0; k <= G::TW; ++k) {
-            if (k < G::TW) {
-                const int t = 2 * k + w;
-                DGFS_ACQUIRE(w);
-                const uint32_t d = tmem + w * G::C_S1;
-                const uint32_t fa = tmem + G::C_F + t * (N / 2);
+        for (int k = 0; k < G::TW; ++k) {   // pass 1 of tile 2k + w into slot w
+            const int t = 2 * k + w;
+            DGFS_ACQUIRE(w);
+            const uint32_t d = tmem + w * G::C_S1;
+            const uint32_t fa = tmem + G::C_F + t * (N / 2);
 #pragma unroll
-                for (int ks = 0; ks < G::KSTEPS; ++ks) {   // hi rows [0, 2n), lo rows [2n, 4n) of B1
-                    tc::mma_ts_warp(d, fa + 8 * ks, tc::sdesc_at(dF, f16 + (G::OFF_B1 + ks * 2 * G::FB_LBO) / 16),
-                                    id1, ks);
-                    tc::mma_ts_warp(d, fa + 8 * ks,
-                                    tc::sdesc_at(dF, f16 + (G::OFF_B1 + (2 * N / 8) * G::FB_SBO + ks * 2 * G::FB_LBO) / 16),
-                                    id1, 1);
-                }
-                tc::mma_commit_warp(&bars.full[w]);
-                // the other filter buffer (pair p - 1, whose MMAs are complete by now) takes pair p + 1
-                if (w == 0 && k == 0 && p >= 1 && p + 1 < npairs) {   // first MMA warp only
-                    const int nb = (p + 1) & 1;
-                    DGFS_WAITW(&bars.fdone[nb], (ph_fdone >> nb) & 1u);
-                    ph_fdone ^= 1u << nb;
-                    if (tc::elect_one()) {
-                        tc::mbar_expect_tx(&bars.filt[nb], G::F_BLOCK);
-                        tc::bulk_g2s(smem + G::S_F + nb * G::F_BLOCK, fglob + (size_t)(p + 1) * G::F_BLOCK,
-                                     G::F_BLOCK, &bars.filt[nb]);
-                    }
-                    __syncwarp();
-                    if (nb) ++copies1;
-                    else ++copies0;
-                }
+            for (int ks = 0; ks < G::KSTEPS; ++ks) {   // hi rows [0, 2n), lo rows [2n, 4n) of B1
+                tc::mma_ts_warp(d, fa + 8 * ks, tc::sdesc_at(dF, f16 + (G::OFF_B1 + ks * 2 * G::FB_LBO) / 16), id1, ks);
+                tc::mma_ts_warp(d, fa + 8 * ks,
+                                tc::sdesc_at(dF, f16 + (G::OFF_B1 + (2 * N / 8) * G::FB_SBO + ks * 2 * G::FB_LBO) / 16),
+                                id1, 1);
             }
-            if (k >= 1) {
-                const int s = 2 + w;
-                DGFS_WAITW(&bars.a2_full[w], ph_a2full & 1u);
-                ph_a2full ^= 1u;
-                DGFS_ACQUIRE(s);
-                const uint32_t d = tmem + (w ? G::C_S3 : G::C_S2);
-                const uint32_t a16 = sb16 + G::S_A2 / 16 + w * (2 * G::A2_BYTES / 16);
-#pragma unroll
-                for (int g = 0; g < 2; ++g)
-#pragma unroll
-                    for (int ks = 0; ks < G::KSTEPS; ++ks)
-                        tc::mma_ss_warp(d + g * 2 * N,
-                                        tc::sdesc_at(dA2, a16 + (g * G::A2_BYTES + ks * 2 * G::A2_LBO) / 16),
-                                        tc::sdesc_at(dF, f16 + (G::OFF_B2 + g * G::B23_BYTES + ks * 2 * G::FB_LBO) / 16),
-                                        id23, ks);
-                tc::mma_commit_warp(&bars.full[s]);
-                tc::mma_commit_warp(&bars.a2_free[w]);
+            tc::mma_commit_warp(&bars.full[w]);
+            // the other filter buffer (pair p - 1, whose MMAs are complete by now) takes pair p + 1
+            if (w == 0 && k == 0 && p >= 1 && p + 1 < npairs) {
+                const int nb = (p + 1) & 1;
+                DGFS_WAITW(&bars.fdone[nb], (ph_fdone >> nb) & 1u);
+                ph_fdone ^= 1u << nb;
+                if (tc::elect_one()) {
+                    tc::mbar_expect_tx(&bars.filt[nb], G::F_BLOCK);
+                    tc::bulk_g2s(smem + G::S_F + nb * G::F_BLOCK, fglob + (size_t)(p + 1) * G::F_BLOCK, G::F_BLOCK,
+                                 &bars.filt[nb]);
+                }
+                __syncwarp();
+                if (nb) ++copies1;
+                else ++copies0;
             }
         }
-        // back: pass 3 of tile u = 2k + w into slot 2 + w
+        tc::mma_commit_warp(&bars.fdone[fbuf]);
+    }
+}
+
+template <int N, bool BF, int w>
+__device__ __forceinline__ void mma_p23_loop(Bars& bars, uint32_t sb, uint32_t tmem, int npairs, volatile int* abort) {
+    using G = Geo<N>;
+    uint32_t used = 0, ph_free = 0, ph_a2full = 0, ph_a3full = 0;
+    constexpr uint32_t id23 = tc::idesc_f16(BF, true, false, 2 * N, 128);
+    constexpr uint64_t dF = tc::sdesc_base(G::FB_LBO, G::FB_SBO);
+    constexpr uint64_t dA2 = tc::sdesc_base(G::A2_LBO, G::A2_SBO);
+    constexpr uint64_t dA3 = tc::sdesc_base(G::A3_LBO, G::A3_SBO);
+    const uint32_t sb16 = sb >> 4;
+    constexpr int s = 2 + w;
+    for (int p = 0; p < npairs; ++p) {
+        const int fbuf = p & 1;
+        DGFS_WAITW(&bars.filt[fbuf], (uint32_t)((p >> 1) & 1));
+        tc::tc_fence_after();
+        const uint32_t f16 = sb16 + (G::S_F + fbuf * G::F_BLOCK) / 16;
+        for (int k = 0; k < G::TW; ++k) {   // pass 2 of tile 2k + w into slot 2 + w
+            DGFS_WAITW(&bars.a2_full[w], ph_a2full & 1u);
+            ph_a2full ^= 1u;
+            DGFS_ACQUIRE(s);
+            const uint32_t d = tmem + (w ? G::C_S3 : G::C_S2);
+            const uint32_t a16 = sb16 + G::S_A2 / 16 + w * (2 * G::A2_BYTES / 16);
+#pragma unroll
+            for (int g = 0; g < 2; ++g)
+#pragma unroll
+                for (int ks = 0; ks < G::KSTEPS; ++ks)
+                    tc::mma_ss_warp(d + g * 2 * N, tc::sdesc_at(dA2, a16 + (g * G::A2_BYTES + ks * 2 * G::A2_LBO) / 16),
+                                    tc::sdesc_at(dF, f16 + (G::OFF_B2 + g * G::B23_BYTES + ks * 2 * G::FB_LBO) / 16),
+                                    id23, ks);
+            tc::mma_commit_warp(&bars.full[s]);
+            tc::mma_commit_warp(&bars.a2_free[w]);
+        }
+        // pass 3 of tile u = 2k + w into slot 2 + w, once every pass-2 tile is in shared memory
         DGFS_WAITW(&bars.a3_full, ph_a3full);
         ph_a3full ^= 1;
         tc::tc_fence_after();
         for (int k = 0; k < G::TW; ++k) {
-            const int u = 2 * k + w, s = 2 + w;
+            const int u = 2 * k + w;
             DGFS_ACQUIRE(s);
             const uint32_t d = tmem + (w ? G::C_S3 : G::C_S2);
             const uint32_t a16 = sb16 + G::S_A3 / 16 + u * (G::A3_TS / 16);
@@ -226,8 +236,7 @@ __device__ __forceinline__ void mma_warp_loop(Bars& bars, unsigned char* smem, u
             for (int g = 0; g < 2; ++g)
 #pragma unroll
                 for (int ks = 0; ks < G::KSTEPS; ++ks)
-                    tc::mma_ss_warp(d + g * 2 * N,
-                                    tc::sdesc_at(dA3, a16 + (g * G::A3_BYTES + ks * 2 * G::A3_LBO) / 16),
+                    tc::mma_ss_warp(d + g * 2 * N, tc::sdesc_at(dA3, a16 + (g * G::A3_BYTES + ks * 2 * G::A3_LBO) / 16),
                                     tc::sdesc_at(dF, f16 + (G::OFF_B3 + g * G::B23_BYTES + ks * 2 * G::FB_LBO) / 16),
                                     id23, ks);
             tc::mma_commit_warp(&bars.full[s]);
@@ -235,9 +244,9 @@ __device__ __forceinline__ void mma_warp_loop(Bars& bars, unsigned char* smem, u
         tc::mma_commit_warp(&bars.a3_free);
         tc::mma_commit_warp(&bars.fdone[fbuf]);
     }
+}
 #undef DGFS_ACQUIRE
 #undef DGFS_WAITW
-}
 
 template <int N, bool BF>
 __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
@@ -274,11 +283,11 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                 tc::mbar_init(&bars.a2_full[i], 128);
                 tc::mbar_init(&bars.a2_free[i], 1);
                 tc::mbar_init(&bars.filt[i], 1);
-                tc::mbar_init(&bars.fdone[i], 2);
+                tc::mbar_init(&bars.fdone[i], 4);   // one commit from each MMA warp
             }
             tc::mbar_init(&bars.a3_full, 32 * G::EPI_WARPS);
-            tc::mbar_init(&bars.a3_free, 2);   // one commit from each MMA warp
-            tc::mbar_init(&bars.drain, 2);
+            tc::mbar_init(&bars.a3_free, 2);   // one commit from each pass-2/3 MMA warp
+            tc::mbar_init(&bars.drain, 4);
             tc::fence_mbar_init();
             s_abort = 0;
             for (int p = 0; p < 2 && p < npairs; ++p) {
@@ -332,14 +341,17 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
     tc::tc_fence_after();
     if (warp >= G::EPI_WARPS) {
       tc::setmaxnreg_dec<G::REG_MMA>();   // every warp of the third warpgroup
-      if (warp == G::ISSUER) {
-        // ============================ MMA warps (converged) ===================================
-        // one per epilogue warpgroup, so that the two pipelines never wait on each other's
-        // hand-offs; each commit tracks only the issuing warp's MMAs
-        mma_warp_loop<N, BF, 0>(bars, smem, sb, tmem, fglob, npairs, abort, copies0, copies1, waited0, waited1);
-      } else if (warp == G::ISSUER + 1) {
-        mma_warp_loop<N, BF, 1>(bars, smem, sb, tmem, fglob, npairs, abort, copies0, copies1, waited0, waited1);
-      }
+      // ============================ MMA warps (converged) =====================================
+      // warps ISSUER + w: pass 1 of warpgroup w; warps ISSUER + 2 + w: passes 2 and 3; each
+      // commit tracks only the issuing warp's MMAs
+      if (warp == G::ISSUER)
+        mma_p1_loop<N, BF, 0>(bars, smem, sb, tmem, fglob, npairs, abort, copies0, copies1, waited0, waited1);
+      else if (warp == G::ISSUER + 1)
+        mma_p1_loop<N, BF, 1>(bars, smem, sb, tmem, fglob, npairs, abort, copies0, copies1, waited0, waited1);
+      else if (warp == G::ISSUER + 2)
+        mma_p23_loop<N, BF, 0>(bars, sb, tmem, npairs, abort);
+      else
+        mma_p23_loop<N, BF, 1>(bars, sb, tmem, npairs, abort);
     } else {
         tc::setmaxnreg_inc<G::REG_EPI>();
         // ============================== epilogue warpgroups ===================================
@@ -480,7 +492,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
     // ---- drain: no MMA or copy of this CTA may be in flight when TMEM is freed -----------
     tc::tc_fence_before();
     __syncthreads();
-    if (warp == G::ISSUER || warp == G::ISSUER + 1) {
+    if (warp >= G::ISSUER) {
         if (tc::elect_one()) tc::mma_commit(&bars.drain);   // the lane that issued the warp's MMAs
         __syncwarp();
     }
