@@ -20,13 +20,14 @@
 // One CTA per (radial point, node): two epilogue warpgroups and a third warpgroup of four MMA
 // warps (after set-up the third warpgroup gives registers back and the epilogue warpgroups take
 // them, 216 per thread, so that an epilogue step loads a whole tile row from TMEM behind one
-// wait). Warpgroup w owns the tiles t = w (mod 2) of every pass (all n columns, one TMEM lane per
-// thread); its pass-1 groups are issued by one MMA warp and its pass-2/3 groups by another, so
-// the two warpgroups form two independent pipelines whose MMA <-> epilogue hand-offs overlap,
-// and no MMA warp waits on hand-offs that do not gate its own groups. Each warpgroup has its own
-// TMEM slots: one for pass 1 (2n columns) and one shared by passes 2 and 3 (4n columns). Both
-// signs' pass-3 operands (full fields) stay in shared memory until the products are formed; the
-// barriers shared by the MMA warps (pass-3 operand released, filter buffer done, final drain)
+// wait). The front of a sphere pair (passes 1 and 2 of every tile) is a producer/consumer chain:
+// the pass-1 MMA warp fills two pass-1 TMEM slots, epilogue warpgroup 0 turns each pass-1 result
+// into pass-2 operands in two shared-memory buffers, the pass-2 MMA warp fills two pass-2/3 TMEM
+// slots, and epilogue warpgroup 1 writes each pass-2 result into the pass-3 operands (both signs'
+// full fields, in shared memory); every ring is two deep, so consecutive tiles overlap. The back
+// (pass 3) starts once every pass-2 tile is stored: pass-3 MMA warp b fills slot b with the tiles
+// u = b (mod 2), and epilogue warpgroup b forms their products (one TMEM lane per thread).
+// Barriers shared by several MMA warps (filter buffer done, final drain, pass-3 operands released)
 // take one commit from each warp that uses the resource. All hand-offs
 // are mbarriers; every lane of the epilogue warps arrives and every wait loop branches on warp
 // votes only, so no branch diverges around the .sync.aligned tcgen05 instructions. Every wait is
@@ -61,9 +62,9 @@ struct Geo {
     static constexpr int KSTEPS = N / 16;         // K = 16 steps of one contraction
     static constexpr int KG = N / 8;              // core-matrix groups along K
     static constexpr int TW = T / 2;              // tiles per epilogue warpgroup
-    static constexpr int EPI_WARPS = 8;           // warpgroup w = warp / 4 owns tiles t = w (mod 2)
+    static constexpr int EPI_WARPS = 8;           // epilogue warpgroups 0 and 1 (warp / 4)
     static constexpr int THREADS = 32 * EPI_WARPS + 128;   // + a warpgroup holding the MMA warp
-    static constexpr int ISSUER = EPI_WARPS;      // warp index of the MMA warp
+    static constexpr int ISSUER = EPI_WARPS;      // first MMA warp (pass 1); then pass 2, pass 3 of slots 0, 1
     // registers per thread: 168 at launch (65536 / 384, rounded down to a multiple of 8), then
     // 216 for the epilogue warpgroups and 72 for the third: 256 * 216 + 128 * 72 = 384 * 168
     static constexpr uint32_t REG_LAUNCH = 168, REG_EPI = 216, REG_MMA = 72;
@@ -110,8 +111,12 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {   // a -> low half
 }
 
 struct Bars {
-    uint64_t full[4], freeb[4];        // TMEM slots: MMA completion -> epilogue, epilogue drained -> MMA
-    uint64_t a2_full[2], a2_free[2];   // pass-2 operand tiles: epilogue -> MMA, MMA completion -> epilogue
+    // TMEM slot rings (index = tile % 2): MMA completion -> epilogue, epilogue drained -> MMA
+    uint64_t full1[2], free1[2];       // pass-1 slots (pass-1 epilogue, warpgroup 0)
+    uint64_t full2[2], free2[2];       // pass-2/3 slots used by pass 2 (pass-2 epilogue, warpgroup 1)
+    uint64_t full3[2], free3[2];       // pass-2/3 slots used by pass 3 (warpgroup = slot)
+    uint64_t free3x[2];                // last pass-3 drain of a slot in a pair (next pair's pass 2 may start)
+    uint64_t a2_full[2], a2_free[2];   // pass-2 operand ring: epilogue -> MMA, MMA completion -> epilogue
     uint64_t a3_full, a3_free;         // pass-3 operands (both signs)
     uint64_t filt[2], fdone[2];        // filter buffers: copy landed; all MMAs of the pair using it done
     uint64_t drain;
@@ -123,26 +128,18 @@ __device__ __forceinline__ void pack8(const float (&v)[8], uint32_t (&u)[4]) {
     for (int j = 0; j < 4; ++j) u[j] = pack2<BF>(v[2 * j], v[2 * j + 1]);
 }
 
-// The MMA warps. Warpgroup w's groups are issued by two warps: mma_p1_loop<w> (pass 1 of its
-// tiles; warp w = 0 also refills the filter buffers) and mma_p23_loop<w> (passes 2 and 3), so a
-// pass-1 group is issued as soon as its TMEM slot is drained, independently of the pass-2 chain.
-// w is a template parameter: every slot, barrier and operand offset is a constant. Each returns
-// early when a wait gave up (abort).
+// The MMA warps (four, converged). Pass 1 of every tile (mma_p1_loop; it also refills the filter
+// buffers), pass 2 of every tile (mma_p2_loop) and pass 3 of the tiles of warpgroup b
+// (mma_p3_loop<b>) are issued by separate warps, so a group is issued as soon as its own inputs
+// and slot are ready. Each commit tracks only the issuing warp's MMAs. Every barrier below is
+// waited by one warp, phase after phase, except a3_full (one completion per pair, waited by both
+// pass-3 warps). Each loop returns early when a wait gave up (abort).
 #define DGFS_WAITW(bar, ph)                                             \
     do {                                                                \
         if (!tc::warp_wait((bar), (ph), abort)) return;                 \
     } while (0)
-#define DGFS_ACQUIRE(s)                                                 \
-    do {                                                                \
-        if (used & (1u << (s))) {                                       \
-            DGFS_WAITW(&bars.freeb[s], (ph_free >> (s)) & 1u);          \
-            ph_free ^= 1u << (s);                                       \
-        }                                                               \
-        used |= 1u << (s);                                              \
-        tc::tc_fence_after();                                           \
-    } while (0)
 
-template <int N, bool BF, int w>
+template <int N, bool BF>
 __device__ __forceinline__ void mma_p1_loop(Bars& bars, unsigned char* smem, uint32_t sb, uint32_t tmem,
                                             const unsigned char* fglob, int npairs, volatile int* abort,
                                             int& copies0, int& copies1, int& waited0, int& waited1) {
@@ -154,16 +151,19 @@ __device__ __forceinline__ void mma_p1_loop(Bars& bars, unsigned char* smem, uin
     for (int p = 0; p < npairs; ++p) {
         const int fbuf = p & 1;
         DGFS_WAITW(&bars.filt[fbuf], (uint32_t)((p >> 1) & 1));
-        if constexpr (w == 0) {
-            if (fbuf) ++waited1;
-            else ++waited0;
-        }
+        if (fbuf) ++waited1;
+        else ++waited0;
         tc::tc_fence_after();
         const uint32_t f16 = sb16 + (G::S_F + fbuf * G::F_BLOCK) / 16;   // filter block of this pair
-        for (int k = 0; k < G::TW; ++k) {   // pass 1 of tile 2k + w into slot w
-            const int t = 2 * k + w;
-            DGFS_ACQUIRE(w);
-            const uint32_t d = tmem + w * G::C_S1;
+        for (int t = 0; t < G::T; ++t) {   // pass 1 of tile t into pass-1 slot t % 2
+            const int b = t & 1;
+            if (used & (1u << b)) {
+                DGFS_WAITW(&bars.free1[b], (ph_free >> b) & 1u);
+                ph_free ^= 1u << b;
+            }
+            used |= 1u << b;
+            tc::tc_fence_after();
+            const uint32_t d = tmem + b * G::C_S1;
             const uint32_t fa = tmem + G::C_F + t * (N / 2);
 #pragma unroll
             for (int ks = 0; ks < G::KSTEPS; ++ks) {   // hi rows [0, 2n), lo rows [2n, 4n) of B1
@@ -172,9 +172,9 @@ __device__ __forceinline__ void mma_p1_loop(Bars& bars, unsigned char* smem, uin
                                 tc::sdesc_at(dF, f16 + (G::OFF_B1 + (2 * N / 8) * G::FB_SBO + ks * 2 * G::FB_LBO) / 16),
                                 id1, 1);
             }
-            tc::mma_commit_warp(&bars.full[w]);
+            tc::mma_commit_warp(&bars.full1[b]);
             // the other filter buffer (pair p - 1, whose MMAs are complete by now) takes pair p + 1
-            if (w == 0 && k == 0 && p >= 1 && p + 1 < npairs) {
+            if (t == 0 && p >= 1 && p + 1 < npairs) {
                 const int nb = (p + 1) & 1;
                 DGFS_WAITW(&bars.fdone[nb], (ph_fdone >> nb) & 1u);
                 ph_fdone ^= 1u << nb;
@@ -192,27 +192,37 @@ __device__ __forceinline__ void mma_p1_loop(Bars& bars, unsigned char* smem, uin
     }
 }
 
-template <int N, bool BF, int w>
-__device__ __forceinline__ void mma_p23_loop(Bars& bars, uint32_t sb, uint32_t tmem, int npairs, volatile int* abort) {
+// Pass 2 of tile t reads pass-2 operand buffer t % 2 and writes pass-2/3 slot t % 2. Slot b is
+// reused within a pair after the pass-2 epilogue drained it (free2, completions 0..2 of the pair's
+// four); the pair's first use waits for the previous pair's last pass-3 drain (free3x).
+template <int N, bool BF>
+__device__ __forceinline__ void mma_p2_loop(Bars& bars, uint32_t sb, uint32_t tmem, int npairs, volatile int* abort) {
     using G = Geo<N>;
-    uint32_t used = 0, ph_free = 0, ph_a2full = 0, ph_a3full = 0;
+    uint32_t ph_a2 = 0, ph_x = 0;
     constexpr uint32_t id23 = tc::idesc_f16(BF, true, false, 2 * N, 128);
     constexpr uint64_t dF = tc::sdesc_base(G::FB_LBO, G::FB_SBO);
     constexpr uint64_t dA2 = tc::sdesc_base(G::A2_LBO, G::A2_SBO);
-    constexpr uint64_t dA3 = tc::sdesc_base(G::A3_LBO, G::A3_SBO);
     const uint32_t sb16 = sb >> 4;
-    constexpr int s = 2 + w;
     for (int p = 0; p < npairs; ++p) {
         const int fbuf = p & 1;
         DGFS_WAITW(&bars.filt[fbuf], (uint32_t)((p >> 1) & 1));
         tc::tc_fence_after();
         const uint32_t f16 = sb16 + (G::S_F + fbuf * G::F_BLOCK) / 16;
-        for (int k = 0; k < G::TW; ++k) {   // pass 2 of tile 2k + w into slot 2 + w
-            DGFS_WAITW(&bars.a2_full[w], ph_a2full & 1u);
-            ph_a2full ^= 1u;
-            DGFS_ACQUIRE(s);
-            const uint32_t d = tmem + (w ? G::C_S3 : G::C_S2);
-            const uint32_t a16 = sb16 + G::S_A2 / 16 + w * (2 * G::A2_BYTES / 16);
+        for (int t = 0; t < G::T; ++t) {
+            const int b = t & 1, j = t >> 1;   // j-th use of slot b in this pair
+            DGFS_WAITW(&bars.a2_full[b], (ph_a2 >> b) & 1u);
+            ph_a2 ^= 1u << b;
+            if (j == 0) {
+                if (p > 0) {
+                    DGFS_WAITW(&bars.free3x[b], (ph_x >> b) & 1u);
+                    ph_x ^= 1u << b;
+                }
+            } else {
+                DGFS_WAITW(&bars.free2[b], (uint32_t)((j - 1) & 1));   // four completions per pair
+            }
+            tc::tc_fence_after();
+            const uint32_t d = tmem + (b ? G::C_S3 : G::C_S2);
+            const uint32_t a16 = sb16 + G::S_A2 / 16 + b * (2 * G::A2_BYTES / 16);
 #pragma unroll
             for (int g = 0; g < 2; ++g)
 #pragma unroll
@@ -220,17 +230,38 @@ __device__ __forceinline__ void mma_p23_loop(Bars& bars, uint32_t sb, uint32_t t
                     tc::mma_ss_warp(d + g * 2 * N, tc::sdesc_at(dA2, a16 + (g * G::A2_BYTES + ks * 2 * G::A2_LBO) / 16),
                                     tc::sdesc_at(dF, f16 + (G::OFF_B2 + g * G::B23_BYTES + ks * 2 * G::FB_LBO) / 16),
                                     id23, ks);
-            tc::mma_commit_warp(&bars.full[s]);
-            tc::mma_commit_warp(&bars.a2_free[w]);
+            tc::mma_commit_warp(&bars.full2[b]);
+            tc::mma_commit_warp(&bars.a2_free[b]);
         }
-        // pass 3 of tile u = 2k + w into slot 2 + w, once every pass-2 tile is in shared memory
+        tc::mma_commit_warp(&bars.fdone[fbuf]);
+    }
+}
+
+// Pass 3 of the tiles u = 2k + b into slot b once every pass-2 tile is in shared memory (a3_full
+// also orders every pass-2 drain of the slot before these MMAs); reuse within the pair waits
+// for the warpgroup's drains (free3, completions 0..2 of the pair's four).
+template <int N, bool BF, int b>
+__device__ __forceinline__ void mma_p3_loop(Bars& bars, uint32_t sb, uint32_t tmem, int npairs, volatile int* abort) {
+    using G = Geo<N>;
+    uint32_t ph_a3full = 0;
+    constexpr uint32_t id23 = tc::idesc_f16(BF, true, false, 2 * N, 128);
+    constexpr uint64_t dF = tc::sdesc_base(G::FB_LBO, G::FB_SBO);
+    constexpr uint64_t dA3 = tc::sdesc_base(G::A3_LBO, G::A3_SBO);
+    const uint32_t sb16 = sb >> 4;
+    for (int p = 0; p < npairs; ++p) {
+        const int fbuf = p & 1;
+        DGFS_WAITW(&bars.filt[fbuf], (uint32_t)((p >> 1) & 1));
+        const uint32_t f16 = sb16 + (G::S_F + fbuf * G::F_BLOCK) / 16;
         DGFS_WAITW(&bars.a3_full, ph_a3full);
         ph_a3full ^= 1;
         tc::tc_fence_after();
         for (int k = 0; k < G::TW; ++k) {
-            const int u = 2 * k + w;
-            DGFS_ACQUIRE(s);
-            const uint32_t d = tmem + (w ? G::C_S3 : G::C_S2);
+            const int u = 2 * k + b;
+            if (k > 0) {
+                DGFS_WAITW(&bars.free3[b], (uint32_t)((k - 1) & 1));   // four completions per pair
+                tc::tc_fence_after();
+            }
+            const uint32_t d = tmem + (b ? G::C_S3 : G::C_S2);
             const uint32_t a16 = sb16 + G::S_A3 / 16 + u * (G::A3_TS / 16);
 #pragma unroll
             for (int g = 0; g < 2; ++g)
@@ -239,13 +270,12 @@ __device__ __forceinline__ void mma_p23_loop(Bars& bars, uint32_t sb, uint32_t t
                     tc::mma_ss_warp(d + g * 2 * N, tc::sdesc_at(dA3, a16 + (g * G::A3_BYTES + ks * 2 * G::A3_LBO) / 16),
                                     tc::sdesc_at(dF, f16 + (G::OFF_B3 + g * G::B23_BYTES + ks * 2 * G::FB_LBO) / 16),
                                     id23, ks);
-            tc::mma_commit_warp(&bars.full[s]);
+            tc::mma_commit_warp(&bars.full3[b]);
         }
         tc::mma_commit_warp(&bars.a3_free);
         tc::mma_commit_warp(&bars.fdone[fbuf]);
     }
 }
-#undef DGFS_ACQUIRE
 #undef DGFS_WAITW
 
 template <int N, bool BF>
@@ -275,18 +305,21 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
     // ---- set-up: barriers, first filter copies, TMEM (MMA warp); max |f| (epilogue warps) -----
     if (issuer) {
         if (lane == 0) {
-            for (int i = 0; i < 4; ++i) {
-                tc::mbar_init(&bars.full[i], 1);
-                tc::mbar_init(&bars.freeb[i], 128);
-            }
             for (int i = 0; i < 2; ++i) {
+                tc::mbar_init(&bars.full1[i], 1);
+                tc::mbar_init(&bars.free1[i], 128);
+                tc::mbar_init(&bars.full2[i], 1);
+                tc::mbar_init(&bars.free2[i], 128);
+                tc::mbar_init(&bars.full3[i], 1);
+                tc::mbar_init(&bars.free3[i], 128);
+                tc::mbar_init(&bars.free3x[i], 128);
                 tc::mbar_init(&bars.a2_full[i], 128);
                 tc::mbar_init(&bars.a2_free[i], 1);
                 tc::mbar_init(&bars.filt[i], 1);
                 tc::mbar_init(&bars.fdone[i], 4);   // one commit from each MMA warp
             }
-            tc::mbar_init(&bars.a3_full, 32 * G::EPI_WARPS);
-            tc::mbar_init(&bars.a3_free, 2);   // one commit from each pass-2/3 MMA warp
+            tc::mbar_init(&bars.a3_full, 128);     // the pass-2 epilogue warpgroup
+            tc::mbar_init(&bars.a3_free, 2);       // the two pass-3 MMA warps
             tc::mbar_init(&bars.drain, 4);
             tc::fence_mbar_init();
             s_abort = 0;
@@ -342,31 +375,29 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
     if (warp >= G::EPI_WARPS) {
       tc::setmaxnreg_dec<G::REG_MMA>();   // every warp of the third warpgroup
       // ============================ MMA warps (converged) =====================================
-      // warps ISSUER + w: pass 1 of warpgroup w; warps ISSUER + 2 + w: passes 2 and 3; each
-      // commit tracks only the issuing warp's MMAs
       if (warp == G::ISSUER)
-        mma_p1_loop<N, BF, 0>(bars, smem, sb, tmem, fglob, npairs, abort, copies0, copies1, waited0, waited1);
+        mma_p1_loop<N, BF>(bars, smem, sb, tmem, fglob, npairs, abort, copies0, copies1, waited0, waited1);
       else if (warp == G::ISSUER + 1)
-        mma_p1_loop<N, BF, 1>(bars, smem, sb, tmem, fglob, npairs, abort, copies0, copies1, waited0, waited1);
+        mma_p2_loop<N, BF>(bars, sb, tmem, npairs, abort);
       else if (warp == G::ISSUER + 2)
-        mma_p23_loop<N, BF, 0>(bars, sb, tmem, npairs, abort);
+        mma_p3_loop<N, BF, 0>(bars, sb, tmem, npairs, abort);
       else
-        mma_p23_loop<N, BF, 1>(bars, sb, tmem, npairs, abort);
+        mma_p3_loop<N, BF, 1>(bars, sb, tmem, npairs, abort);
     } else {
         tc::setmaxnreg_inc<G::REG_EPI>();
         // ============================== epilogue warpgroups ===================================
-        // warpgroup w owns tiles t = 2k + w (k < TW) of every pass; thread = TMEM lane l
+        // front (passes 1 and 2, every tile): warpgroup 0 turns each pass-1 result into the pass-2
+        // operands, warpgroup 1 each pass-2 result into rows of the pass-3 operands, so the two
+        // steps of consecutive tiles overlap; back (pass 3): warpgroup w forms the products of the
+        // tiles u = 2k + w. Thread = TMEM lane l.
         const int q = warp & 3, w = warp >> 2;
         const int l = 32 * q + lane, yl = l / N, lz = l % N;   // tile row: (yl, z) in pass 1, (yl, x') in pass 2
         const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
-        const uint32_t tP1 = trow + G::C_S0 + w * G::C_S1;        // pass-1 slot: + at 0, - at N
-        const uint32_t tB = trow + (w ? G::C_S3 : G::C_S2);       // pass-2/3 slot: +hi, +lo, -hi, -lo
         // shared-memory stores (one 16-byte unit = 8 consecutive rows of one k): A2 rows yl N + x',
         // k = z = lz; A3 rows x' N + z' with x' = lz, k = y
-        const uint32_t a2_row = sb + G::S_A2 + w * 2 * G::A2_BYTES + ((uint32_t)(yl * N) >> 3) * G::A2_SBO +
-                                (lz >> 3) * G::A2_LBO + (lz & 7) * 16;
+        const uint32_t a2_row = sb + G::S_A2 + ((uint32_t)(yl * N) >> 3) * G::A2_SBO + (lz >> 3) * G::A2_LBO + (lz & 7) * 16;
         const int mg3 = (lz * N) >> 3;
-        uint32_t ph_full = 0, ph_a2free = 0, ph_a3free = 0;   // phase bits of this warpgroup's barriers
+        uint32_t ph_f = 0, ph_a2free = 0, ph_a3free = 0, ph_f3 = 0;   // phase bits (bit b = ring slot b)
         float acc[G::TW][N];
 #pragma unroll
         for (int k = 0; k < G::TW; ++k)
@@ -377,48 +408,49 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
         if (!tc::warp_wait((bar), (ph), abort)) goto epi_done;          \
     } while (0)
         for (int p = 0; p < npairs; ++p) {
-            for (int k = 0; k <= G::TW; ++k) {
-                if (k < G::TW) {
-                    // pass-1 tile t = 2k + w -> the pass-2 operands of both signs (A2 buffer w)
-                    if (p > 0 || k > 0) {   // P2 of this warpgroup's previous tile has read A2[w]
-                        DGFS_WAITE(&bars.a2_free[w], ph_a2free);
-                        ph_a2free ^= 1;
+            if (w == 0) {
+                for (int t = 0; t < G::T; ++t) {   // pass-1 tile t (slot t % 2) -> pass-2 operands (buffer t % 2)
+                    const int b = t & 1;
+                    if (p > 0 || t >= 2) {   // pass 2 of tile t - 2 has read buffer b
+                        DGFS_WAITE(&bars.a2_free[b], (ph_a2free >> b) & 1u);
+                        ph_a2free ^= 1u << b;
                     }
-                    DGFS_WAITE(&bars.full[w], ph_full & 1u);
-                    ph_full ^= 1u;
+                    DGFS_WAITE(&bars.full1[b], (ph_f >> b) & 1u);
+                    ph_f ^= 1u << b;
                     tc::tc_fence_after();
-                    {
-                        float v[2][N];   // the thread's row of the tile, both signs, behind one wait
+                    float v[2][N];   // the thread's row of the tile, both signs, behind one wait
+                    const uint32_t tP1 = trow + G::C_S0 + b * G::C_S1;   // + at 0, - at N
 #pragma unroll
-                        for (int g = 0; g < 2; ++g)
+                    for (int g = 0; g < 2; ++g)
 #pragma unroll
-                            for (int c = 0; c < N / 16; ++c)
-                                tc::tmem_ld16(tP1 + g * N + 16 * c, *reinterpret_cast<float(*)[16]>(&v[g][16 * c]));
-                        tc::tmem_wait_ld();
-                        tc::tc_fence_before();
-                        tc::mbar_arrive(&bars.freeb[w]);
+                        for (int c = 0; c < N / 16; ++c)
+                            tc::tmem_ld16(tP1 + g * N + 16 * c, *reinterpret_cast<float(*)[16]>(&v[g][16 * c]));
+                    tc::tmem_wait_ld();
+                    tc::tc_fence_before();
+                    tc::mbar_arrive(&bars.free1[b]);
+                    const uint32_t a2b = a2_row + b * 2 * G::A2_BYTES;
 #pragma unroll
-                        for (int g = 0; g < 2; ++g)
+                    for (int g = 0; g < 2; ++g)
 #pragma unroll
-                            for (int c = 0; c < N / 8; ++c) {   // 8 columns x' = 8c .. 8c + 7
-                                uint32_t u[4];
-                                pack8<BF>(*reinterpret_cast<const float(*)[8]>(&v[g][8 * c]), u);
-                                tc::st_shared_v4(a2_row + g * G::A2_BYTES + c * G::A2_SBO, u[0], u[1], u[2], u[3]);
-                            }
-                    }
+                        for (int c = 0; c < N / 8; ++c) {   // 8 columns x' = 8c .. 8c + 7
+                            uint32_t u[4];
+                            pack8<BF>(*reinterpret_cast<const float(*)[8]>(&v[g][8 * c]), u);
+                            tc::st_shared_v4(a2b + g * G::A2_BYTES + c * G::A2_SBO, u[0], u[1], u[2], u[3]);
+                        }
                     tc::fence_proxy_async();
-                    tc::mbar_arrive(&bars.a2_full[w]);
+                    tc::mbar_arrive(&bars.a2_full[b]);
                 }
-                if (k >= 1) {
-                    // pass-2 tile t = 2(k - 1) + w -> rows of the pass-3 operands of both signs
-                    const int t = 2 * (k - 1) + w, y = t * G::ZT + yl;
-                    if (k == 1 && p > 0) {   // the previous pair's pass 3 has read the operands
+            } else {
+                for (int t = 0; t < G::T; ++t) {   // pass-2 tile t (slot t % 2) -> rows of the pass-3 operands
+                    const int b = t & 1, y = t * G::ZT + yl;
+                    if (t == 0 && p > 0) {   // the previous pair's pass 3 has read the operands
                         DGFS_WAITE(&bars.a3_free, ph_a3free);
                         ph_a3free ^= 1;
                     }
-                    DGFS_WAITE(&bars.full[2 + w], (ph_full >> 1) & 1u);
-                    ph_full ^= 2u;
+                    DGFS_WAITE(&bars.full2[b], (ph_f >> b) & 1u);
+                    ph_f ^= 1u << b;
                     tc::tc_fence_after();
+                    const uint32_t tB = trow + (b ? G::C_S3 : G::C_S2);   // +hi, +lo, -hi, -lo
                     const uint32_t ky = (y >> 3) * G::A3_LBO + (y & 7) * 16;
 #pragma unroll
                     for (int g = 0; g < 2; ++g) {   // one sign: hi and lo of the row behind one wait
@@ -431,7 +463,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                         tc::tmem_wait_ld();
                         if (g == 1) {
                             tc::tc_fence_before();
-                            tc::mbar_arrive(&bars.freeb[2 + w]);
+                            tc::mbar_arrive(&bars.free2[b]);
                         }
 #pragma unroll
                         for (int c = 0; c < N / 8; ++c) {   // 8 columns z' = 8c .. 8c + 7
@@ -445,17 +477,16 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                                              u[0], u[1], u[2], u[3]);
                         }
                     }
-                    if (k == G::TW) {
-                        tc::fence_proxy_async();
-                        tc::mbar_arrive(&bars.a3_full);
-                    }
                 }
+                tc::fence_proxy_async();
+                tc::mbar_arrive(&bars.a3_full);
             }
-            // pass-3 tiles u = 2k + w: products of the two translates
+            // pass-3 tiles u = 2k + w (slot w): products of the two translates
+            const uint32_t tB = trow + (w ? G::C_S3 : G::C_S2);
 #pragma unroll
             for (int k = 0; k < G::TW; ++k) {
-                DGFS_WAITE(&bars.full[2 + w], (ph_full >> 1) & 1u);
-                ph_full ^= 2u;
+                DGFS_WAITE(&bars.full3[w], ph_f3);
+                ph_f3 ^= 1u;
                 tc::tc_fence_after();
 #pragma unroll
                 for (int c = 0; c < N / 16; ++c) {   // 16 columns y' = 16c .. 16c + 15 behind one wait
@@ -467,7 +498,8 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                     tc::tmem_wait_ld();
                     if (c == N / 16 - 1) {
                         tc::tc_fence_before();
-                        tc::mbar_arrive(&bars.freeb[2 + w]);
+                        tc::mbar_arrive(&bars.free3[w]);
+                        if (k == G::TW - 1) tc::mbar_arrive(&bars.free3x[w]);
                     }
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
