@@ -177,7 +177,7 @@ def fft_algorithmic_flops_per_node(N, Nrho, npairs):
 # DRAM bytes (read + write) per node of one translate-product launch at N = 32, N_rho = 32, M = 38,
 # from the ncu capture of a 512-node launch summarised in profiles/ (None for configurations
 # without a capture of the current kernel version).
-TRAFFIC_PER_NODE = {("f16s", 32, 32, 38): 2180.37e6 / 512, ("bf16s", 32, 32, 38): None,
+TRAFFIC_PER_NODE = {("f16s", 32, 32, 38): 2175.90e6 / 512, ("bf16s", 32, 32, 38): None,
                     ("fp32", 32, 32, 38): None}
 
 
