@@ -405,6 +405,37 @@ def test_tensor_core_collide(prec, N, kind):
         assert e_loss < TOL[prec]
 
 
+@pytest.mark.parametrize("N,rule", [(16, 6), (16, 26), (16, 38), (32, 6), (32, "one_pair"), (32, "two_pairs")])
+def test_tensor_core_sphere_rules(N, rule):
+    """1, 2, 3, 13 and 19 antipodal pairs through the tensor-core kernel (the filter double buffer
+    with one or both halves in use and with refills; the rings' phase counts per pair at both
+    grid sizes), and rotated user rules with no zero components, against the oracle with the
+    same rule."""
+    L, gamma = 6.0, 0.52
+    if isinstance(rule, int):
+        kw, okw = {"M": rule}, {"M": rule}
+    else:
+        rng = np.random.default_rng(7)
+        n = 1 if rule == "one_pair" else 2
+        v = rng.normal(size=(n, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        w = np.full(n, 2.0 * np.pi / n)   # weight of each point; the full sphere sums to 4 pi
+        kw = {"sphere": np.column_stack([v, w])}
+        okw = {"sphere": (np.concatenate([v, -v]), np.concatenate([w, w]))}
+    F = _as_input(W.two_maxwellian(2, N, L, 900 + N)[0], "fp32")
+    plan = binding.Plan(N=N, L=L, gamma=gamma, N_rho=N, precision="f16s", **kw)
+    q = plan.collide(_dev(F, "fp32")).double().cpu().numpy()
+    plan.stream_status()
+    op = O.OraclePlan(N, L, gamma=gamma, Nrho=N, nyquist="sym", **okw)
+    assert plan.info["n_pairs"] == len(op.sigma)
+    for i in range(2):
+        ref = O.fast_Q(op, F[i])
+        e_loss, e_q = _errors(q[i], ref, np.real(O.loss_Q(op, F[i], F[i])))
+        print("f16s N=%d rule %s node %d err/|Q-| %.3g err/|Q| %.3g" % (N, rule, i, e_loss, e_q))
+        assert e_loss < TOL["f16s"]
+    plan.close()
+
+
 @pytest.mark.parametrize("prec", ["f16s", "bf16s"])
 def test_tensor_core_vhs_n32_full_batch_sampled(prec):
     """The primary workload's launch (2048 nodes, N = 32, M = 38, SVD 1e-8) on tensor cores."""
