@@ -195,6 +195,14 @@ dgfs_status dgfs_collide_noalloc(dgfs_plan_t plan, const void* f, void* Q, int64
    plan (DGFS_ERR_TIMEOUT, DGFS_ERR_NUMERIC), then clear them. */
 dgfs_status dgfs_stream_status(dgfs_plan_t plan, void* stream);
 
+/* Test hook of the failure detection (the paper has no counterpart). mode 1: in the next
+   compute call of a tensor-core plan, the first CTA of the translate-product kernel withholds
+   the signal that its pass-3 operands are complete, as a lost hand-off would. Its bounded
+   waits then give up, every role of that CTA stops, the MMAs in flight are drained, TMEM is
+   freed, its P_r is not written and flag TIMEOUT is raised; the other CTAs and later calls are
+   unaffected. mode 0 clears the injection. Other plans and precisions ignore it. */
+dgfs_status dgfs_debug_inject(dgfs_plan_t plan, int mode);
+
 /* Profiling of one plan: between begin and end the library counts its kernel launches and
    brackets every launch of the translate-product kernel (the dominant kernel) with CUDA
    events on the call's stream. end synchronises those events and reports the totals.

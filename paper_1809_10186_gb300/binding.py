@@ -67,6 +67,7 @@ _SIGNATURES = {
     "dgfs_collide_host": [_P, _P, _P, _I64, _P],
     "dgfs_collide_noalloc": [_P, _P, _P, _I64, _P],
     "dgfs_stream_status": [_P, _P],
+    "dgfs_debug_inject": [_P, ctypes.c_int],
     "dgfs_profile_begin": [_P],
     "dgfs_profile_end": [_P, ctypes.POINTER(dgfs_profile_t)],
     "dgfs_last_error_message": [],
@@ -246,6 +247,11 @@ class Plan:
 
     def stream_status(self, stream=None):
         check(lib().dgfs_stream_status(self.handle, _stream_ptr(stream)), "dgfs_stream_status")
+
+    def debug_inject(self, mode=1):
+        """Failure-detection test hook: mode 1 makes the next tensor-core launch lose one
+        hand-off signal in its first CTA (see dgfs_debug_inject)."""
+        check(lib().dgfs_debug_inject(self.handle, int(mode)), "dgfs_debug_inject")
 
 
 def collide_ragged(plans, node_plan, node_offset, f_packed, node_gamma=None, node_b=None,

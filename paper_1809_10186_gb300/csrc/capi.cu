@@ -68,6 +68,7 @@ struct dgfs_plan_s {
     size_t off_P = 0, off_G = 0, off_S = 0, off_X = 0, off_Y = 0, off_io = 0, off_node = 0;
     int xfields = 0;
     std::mutex host_mu;      // serialises host-side staging of per-node arrays
+    int fault = 0;           // failure-test injection for the next tensor-core launch (dgfs_debug_inject)
     // host-buffer entry point: copy streams and the events that pipeline copies with compute
     cudaStream_t cs_h2d = nullptr, cs_d2h = nullptr;
     cudaEvent_t ev_start = nullptr, ev_h2d[2] = {}, ev_comp[2] = {}, ev_d2h[2] = {};
@@ -276,7 +277,8 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
     if (is_tc(p->prec) && std::is_same<T, float>::value && gg == nullptr) {
         e = launch_tc_gain_products(p->tc, p->prec, reinterpret_cast<const float*>(f),
                                     reinterpret_cast<const float*>(gg), offs, nodes,
-                                    reinterpret_cast<float*>(P), p->d_flags, s);
+                                    reinterpret_cast<float*>(P), p->d_flags, s, p->fault);
+        p->fault = 0;
     } else {
         e = launch_gain_products(t, f, gg, offs, nodes, P, s);
     }
@@ -778,6 +780,13 @@ dgfs_status dgfs_profile_end(dgfs_plan_t plan, dgfs_profile_t* out) {
     out->gain_ms = ms;
     out->nodes = plan->prof_nodes;
     plan->prof = false;
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_debug_inject(dgfs_plan_t plan, int mode) {
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    if (mode != 0 && mode != 1) return fail(DGFS_ERR_INVALID_ARG, "unknown injection mode");
+    plan->fault = mode;
     return DGFS_OK;
 }
 

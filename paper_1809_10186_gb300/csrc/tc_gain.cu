@@ -281,7 +281,7 @@ __device__ __forceinline__ void mma_p3_loop(Bars& bars, uint32_t sb, uint32_t tm
 template <int N, bool BF>
 __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
 k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const unsigned char* __restrict__ filt,
-          int npairs, int Nrho, float* __restrict__ P, int* __restrict__ flags) {
+          int npairs, int Nrho, float* __restrict__ P, int* __restrict__ flags, int fault) {
     using G = Geo<N>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) Bars bars;
@@ -479,7 +479,8 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                     }
                 }
                 tc::fence_proxy_async();
-                tc::mbar_arrive(&bars.a3_full);
+                // failure test: the first CTA withholds the signal for its first pair
+                if (!(fault == 1 && p == 0 && blockIdx.x == 0 && blockIdx.y == 0)) tc::mbar_arrive(&bars.a3_full);
             }
             // pass-3 tiles u = 2k + w (slot w): products of the two translates
             const uint32_t tB = trow + (w ? G::C_S3 : G::C_S2);
@@ -547,7 +548,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
 
 template <int N, bool BF>
 cudaError_t launch_n(const TcTables& t, const float* f, const int64_t* offs, int64_t nodes, float* P,
-                     int* flags, cudaStream_t s) {
+                     int* flags, cudaStream_t s, int fault) {
     using G = Geo<N>;
     auto kern = k_tc_gain<N, BF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::S_TOTAL);
@@ -557,7 +558,7 @@ cudaError_t launch_n(const TcTables& t, const float* f, const int64_t* offs, int
         const int64_t nn = nodes - n0 < 65535 ? nodes - n0 : 65535;
         kern<<<dim3(t.Nrho, (unsigned)nn), G::THREADS, G::S_TOTAL, s>>>(
             f + (offs ? 0 : n0 * n3), offs ? offs + n0 : nullptr, static_cast<const unsigned char*>(t.mats),
-            t.npairs, t.Nrho, P + n0 * t.Nrho * n3, flags);
+            t.npairs, t.Nrho, P + n0 * t.Nrho * n3, flags, n0 == 0 ? fault : 0);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -654,13 +655,15 @@ void rebase_tc_tables(TcTables& t, void* base) {
 
 cudaError_t launch_tc_gain_products(const TcTables& t, int prec, const float* f, const float* g,
                                     const int64_t* offs, int64_t nodes, float* P, int* flags,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, int fault) {
     if (g) return cudaErrorNotSupported;
     if (nodes <= 0) return cudaSuccess;
     const bool bf = prec == DGFS_PREC_BF16S;
     switch (t.N) {
-        case 16: return bf ? launch_n<16, true>(t, f, offs, nodes, P, flags, s) : launch_n<16, false>(t, f, offs, nodes, P, flags, s);
-        case 32: return bf ? launch_n<32, true>(t, f, offs, nodes, P, flags, s) : launch_n<32, false>(t, f, offs, nodes, P, flags, s);
+        case 16: return bf ? launch_n<16, true>(t, f, offs, nodes, P, flags, s, fault)
+                           : launch_n<16, false>(t, f, offs, nodes, P, flags, s, fault);
+        case 32: return bf ? launch_n<32, true>(t, f, offs, nodes, P, flags, s, fault)
+                           : launch_n<32, false>(t, f, offs, nodes, P, flags, s, fault);
         default: return cudaErrorInvalidValue;
     }
 }

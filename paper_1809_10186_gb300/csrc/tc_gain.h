@@ -20,8 +20,9 @@ bool tc_supported(int N);
 int tc_extra_launches(int prec);   // launches the tensor-core path adds per chunk (beyond one)
 size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>& blob, TcTables& t);
 void rebase_tc_tables(TcTables& t, void* base);
+// fault: 0, or 1 = the first CTA withholds its pass-3-operands-complete signal (failure test)
 cudaError_t launch_tc_gain_products(const TcTables& t, int prec, const float* f, const float* g,
                                     const int64_t* offs, int64_t nodes, float* P, int* flags,
-                                    cudaStream_t s);
+                                    cudaStream_t s, int fault = 0);
 
 }  // namespace dgfs

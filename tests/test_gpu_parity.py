@@ -455,6 +455,31 @@ def test_tensor_core_chunking_and_determinism():
     assert torch.equal(a, p2.collide(f))
 
 
+def test_lost_hand_off_times_out_and_the_plan_recovers():
+    """Failure detection without a GPU fault: the first CTA of the tensor-core kernel withholds
+    one hand-off signal (host-injected), its bounded waits give up, the CTA drains and frees its
+    resources, the call reports DGFS_ERR_TIMEOUT through dgfs_stream_status, and the next call
+    on the same plan returns the normal result."""
+    import time
+    N, L = 32, 7.0
+    F, _ = W.two_maxwellian(3, N, L, 55, dtype=np.float32)
+    f = _dev(F, "fp32")
+    plan = binding.Plan(N=N, L=L, gamma=0.52, M=6, N_rho=N, precision="f16s")
+    ref = plan.collide(f)
+    plan.stream_status()
+    plan.debug_inject(1)
+    t0 = time.time()
+    plan.collide(f)
+    with pytest.raises(binding.DGFSError) as err:
+        plan.stream_status()
+    print("injected lost signal: %s after %.2f s" % (err.value, time.time() - t0))
+    assert "TIMEOUT" in str(err.value)
+    again = plan.collide(f)
+    plan.stream_status()
+    assert torch.equal(again, ref)
+    plan.close()
+
+
 @pytest.mark.parametrize("prec", ["fp32", "f16s"])
 def test_cuda_graph_capture_equals_eager(prec):
     """dgfs_collide enqueues kernels only, so a captured call replays to the eager result."""
