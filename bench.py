@@ -49,6 +49,9 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--dg", action="store_true",
+                    help="measure the DG element collision term (Sec. 3.4, SVD variant) on the 1-D slab "
+                         "workload instead of the headline (prints its own line)")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -228,12 +231,60 @@ def run_reference(a):
 
 # ---- our arm -----------------------------------------------------------------------------------
 
+def run_dg(a):
+    """DG element collision term of the slab workload: 16 elements x K = 3 Gauss-Lobatto nodes,
+    N = 24, omega = 0.81, M = 12, FP32; C[e][m] = sum_r Q(f_r, g_r) (every R_m = 3 at svd_tol 0)."""
+    import numpy as np
+    import torch
+    from paper_1809_10186_gb300 import binding, workloads as W
+    torch.cuda.set_device(0)
+    cfg = W.CONFIGS["slab_n24"]
+    N, L, K = cfg["N"], cfg["L"], 3
+    E = cfg["B"] // K
+    F, _ = W.two_maxwellian(E * K, N, L, cfg["seed"], dtype=np.float32)
+    f = torch.from_numpy(F.reshape(E, K, N, N, N)).cuda()
+    plan = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=cfg["M"], N_rho=cfg["Nrho"], precision="fp32",
+                        max_batch=E * K * K)
+    _, _, H = binding.host_dg_tensor(K)
+    dg = binding.DGElement(plan, H, max_elements=E)
+    c = torch.empty_like(f)
+    for _ in range(a.warmup):
+        dg.collide(f, out=c)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    plan.profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        dg.collide(f, out=c)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = plan.profile_end()
+    clocks = sampler.stop()
+    plan.stream_status()
+    ms = e0.elapsed_time(e1) / a.steps
+    line = {"metric": "DG element collision terms/s, 1-D slab (16 elements x 3 nodes, N=24, omega=0.81, M=12)",
+            "value": E / (ms / 1e3), "unit": "elements/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "bilinear_Q_per_s": E * dg.total_rank / (ms / 1e3),
+            "config": {"workload": "slab_n24 DG element term, SVD variant", "elements": E, "K": K,
+                       "ranks": dg.ranks, "N": N, "M": cfg["M"], "N_rho": cfg["Nrho"]},
+            "gpu_launches": prof["launches"], "clocks": clocks}
+    print(json.dumps(line))
+    dg.close()
+    plan.close()
+    return 0
+
+
 def main():
     a = _args()
     if a.oracle_worker:
         return 0
     if a.impl == "reference":
         return run_reference(a)
+    if a.dg:
+        return run_dg(a)
     import numpy as np
     import torch
     from paper_1809_10186_gb300 import binding, workloads as W

@@ -195,6 +195,34 @@ dgfs_status dgfs_collide_noalloc(dgfs_plan_t plan, const void* f, void* Q, int64
    plan (DGFS_ERR_TIMEOUT, DGFS_ERR_NUMERIC), then clear them. */
 dgfs_status dgfs_stream_status(dgfs_plan_t plan, void* stream);
 
+/* ---- DG element collision term (Sec. 3.4) ---------------------------------------------
+   In the weak form (eq. eq_weakForm) the collision term of test function m in an element is
+     C[m] = sum_{l1, l2} H[m][l1][l2] Q(F[l1], F[l2])                               (eq. HH)
+   with H[m][l1][l2] = int phi_m phi_l1 phi_l2 (eq. eq_stiffMatrix3) and F[l] the element's K
+   nodal distribution functions. dgfs_dg evaluates it in the paper's SVD variant (eqs.
+   eq_coln_derivation_SVD_3/4): each K x K slice H[m] = sum_r U[l1][r] V[r][l2] (singular values
+   in V), C[m] = sum_r Q(f_r, g_r), f_r = sum_l U[l][r] F[l], g_r = sum_l V[r][l] F[l]: R_m <= K
+   bilinear collisions per m instead of K^2. The 1/Kn factor is left to the caller. */
+typedef struct dgfs_dg_s* dgfs_dg_t;
+/* H: host [K][K][K] (read during the call), 2 <= K <= 16. svd_tol: singular values of H[m] at
+   or below svd_tol times its largest are dropped (0: keep those above 1e-14 of the largest).
+   max_elements: elements per internal pass (sizes the device workspace: 3 R max_elements N^3
+   values, R = sum_m R_m); calls accept any E. The plan must outlive the object. */
+dgfs_status dgfs_dg_create(dgfs_plan_t plan, int K, const double* H, double svd_tol, int64_t max_elements,
+                           dgfs_dg_t* out);
+/* ranks: host [K] or NULL (R_m of every m); total: host or NULL (R). */
+dgfs_status dgfs_dg_info(dgfs_dg_t dg, int* ranks, int* total);
+/* F, C: device [E][K][N^3] in the plan's element type (float; double for FP64 plans), 16-byte
+   aligned, not aliased; C[e][m] as above. Stream-ordered; no allocation. The bilinear Q runs on
+   the plan's CUDA-core path in its precision (FP32 for the 16-bit plans). */
+dgfs_status dgfs_dg_collide(dgfs_dg_t dg, const void* F, void* C, int64_t E, void* stream);
+/* Synchronises the device and frees the workspace. NULL is a no-op. */
+dgfs_status dgfs_dg_destroy(dgfs_dg_t dg);
+/* Host only: the 1-D nodal basis of the paper's slab cases: the K Gauss-Lobatto points of the
+   reference element [-1, 1] (nodes[K]), its mass matrix M[m][l] (eq. eq_massMatrix, [K][K]) and
+   H[m][l1][l2] ([K][K][K]), by Gauss-Legendre quadrature exact for the polynomial integrands. */
+dgfs_status dgfs_host_dg_tensor(int K, double* nodes, double* M, double* H);
+
 /* Test hook of the failure detection (the paper has no counterpart). mode 1: in the next
    compute call of a tensor-core plan, the first CTA of the translate-product kernel withholds
    the signal that its pass-3 operands are complete, as a lost hand-off would. Its bounded

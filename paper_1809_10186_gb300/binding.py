@@ -77,6 +77,13 @@ _SIGNATURES = {
                              ctypes.POINTER(ctypes.c_double)],
     "dgfs_host_translate_filter": [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(ctypes.c_double)],
+    "dgfs_dg_create": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_double, _I64,
+                       ctypes.POINTER(_P)],
+    "dgfs_dg_info": [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "dgfs_dg_collide": [_P, _P, _P, _I64, _P],
+    "dgfs_dg_destroy": [_P],
+    "dgfs_host_dg_tensor": [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double)],
 }
 
 _lib = None
@@ -317,6 +324,54 @@ class RaggedSchedule:
     def close(self):
         if getattr(self, "handle", None):
             lib().dgfs_ragged_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def host_dg_tensor(K):
+    """Gauss-Lobatto nodes, mass matrix and H[m][l1][l2] of the 1-D nodal DG basis (host only)."""
+    import numpy as np
+    nodes, M, H = np.zeros(K), np.zeros((K, K)), np.zeros((K, K, K))
+    dp = ctypes.POINTER(ctypes.c_double)
+    check(lib().dgfs_host_dg_tensor(int(K), nodes.ctypes.data_as(dp), M.ctypes.data_as(dp), H.ctypes.data_as(dp)),
+          "dgfs_host_dg_tensor")
+    return nodes, M, H
+
+
+class DGElement:
+    """The DG element collision term in the SVD variant (dgfs_dg_*): collide(F) maps the nodal
+    distribution functions F [E, K, N, N, N] of E elements to C[e, m] = sum H[m, l1, l2] Q(F_l1, F_l2)."""
+
+    def __init__(self, plan, H, svd_tol=0.0, max_elements=64):
+        import numpy as np
+        H = np.ascontiguousarray(H, dtype=np.float64)
+        self.K = H.shape[0]
+        self.plan = plan   # the plan must outlive this object
+        h = ctypes.c_void_p()
+        check(lib().dgfs_dg_create(plan.handle, self.K, H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   float(svd_tol), ctypes.c_int64(max_elements), ctypes.byref(h)), "dgfs_dg_create")
+        self.handle = h
+        ranks = (ctypes.c_int * self.K)()
+        total = ctypes.c_int()
+        check(lib().dgfs_dg_info(h, ranks, ctypes.byref(total)), "dgfs_dg_info")
+        self.ranks, self.total_rank = list(ranks), total.value
+
+    def collide(self, F, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(F)
+        check(lib().dgfs_dg_collide(self.handle, ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                    ctypes.c_int64(F.shape[0]), _stream_ptr(stream)), "dgfs_dg_collide")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().dgfs_dg_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -699,6 +699,180 @@ dgfs_status dgfs_ragged_destroy(dgfs_ragged_t r) {
     return DGFS_OK;
 }
 
+// ---- DG element collision (Sec. 3.4, SVD variant) -------------------------------------------
+
+constexpr uint64_t kDgMagic = 0x444746534447454cull;   // "DGFSDGEL"
+
+}  // extern "C"
+
+struct dgfs_dg_s {
+    uint64_t magic = kDgMagic;
+    dgfs_plan_s* plan = nullptr;
+    int K = 0, R = 0, device = 0;
+    int64_t emax = 0;
+    std::vector<int> ranks;
+    void* d_mem = nullptr;   // A [R][K] | B [R][K] | rs [K + 1] | f | g | Q ([emax][R][N^3] each)
+    size_t off_A = 0, off_B = 0, off_rs = 0, off_f = 0, off_g = 0, off_Q = 0;
+};
+
+namespace {
+
+bool check_dg(dgfs_dg_t d) { return d && d->magic == kDgMagic; }
+
+template <typename T>
+dgfs_status dg_run(dgfs_dg_s* d, const T* F, T* C, int64_t E, cudaStream_t s) {
+    dgfs_plan_s* p = d->plan;
+    const int64_t n3 = (int64_t)p->hp.N * p->hp.N * p->hp.N;
+    unsigned char* base = static_cast<unsigned char*>(d->d_mem);
+    const T* A = reinterpret_cast<const T*>(base + d->off_A);
+    const T* B = reinterpret_cast<const T*>(base + d->off_B);
+    const int* rs = reinterpret_cast<const int*>(base + d->off_rs);
+    T* f = reinterpret_cast<T*>(base + d->off_f);
+    T* g = reinterpret_cast<T*>(base + d->off_g);
+    T* Q = reinterpret_cast<T*>(base + d->off_Q);
+    for (int64_t e0 = 0; e0 < E; e0 += d->emax) {
+        const int64_t ne = std::min<int64_t>(d->emax, E - e0);
+        const T* Fe = F + e0 * d->K * n3;
+        T* Ce = C + e0 * d->K * n3;
+        if (d->R > 0) {
+            cudaError_t e = launch_dg_combine<T>(Fe, A, B, d->K, d->R, n3, ne, f, g, s);
+            if (e) return cuda_fail(e, "DG combination");
+            const dgfs_status st = run<T>(p, Op::Collide2, f, g, Q, ne * d->R, s);
+            if (st != DGFS_OK) return st;
+        }
+        cudaError_t e = launch_dg_accumulate<T>(Q, rs, d->K, d->R, n3, ne, Ce, s);
+        if (e) return cuda_fail(e, "DG accumulation");
+        if (p->prof) p->prof_launches += d->R > 0 ? 2 : 1;
+    }
+    return DGFS_OK;
+}
+
+template <typename T>
+void put_coeffs(std::vector<unsigned char>& blob, size_t off, const std::vector<double>& v) {
+    T* d = reinterpret_cast<T*>(blob.data() + off);
+    for (size_t i = 0; i < v.size(); ++i) d[i] = (T)v[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+dgfs_status dgfs_dg_create(dgfs_plan_t plan, int K, const double* H, double svd_tol, int64_t max_elements,
+                           dgfs_dg_t* out) {
+    if (!out) return fail(DGFS_ERR_INVALID_ARG, "NULL output");
+    *out = nullptr;
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    if (K < 2 || K > 16) return fail(DGFS_ERR_INVALID_ARG, "K must be in [2, 16]");
+    if (!H) return fail(DGFS_ERR_INVALID_ARG, "NULL H");
+    if (!(svd_tol >= 0.0) || svd_tol >= 1.0) return fail(DGFS_ERR_INVALID_ARG, "svd_tol must be in [0, 1)");
+    if (max_elements < 1 || max_elements > 65535) return fail(DGFS_ERR_INVALID_ARG, "max_elements must be in [1, 65535]");
+    std::unique_ptr<dgfs_dg_s> d(new (std::nothrow) dgfs_dg_s);
+    if (!d) return fail(DGFS_ERR_OOM, "host allocation failed");
+    d->plan = plan;
+    d->K = K;
+    d->emax = max_elements;
+    d->device = plan->device;
+    // SVD of every slice H[m] (column-major K x K): H[m] = U diag(sv) V^T; row r of the
+    // f coefficients is column r of U, row r of the g coefficients is sv[r] times column r of V
+    std::vector<double> A, B;
+    std::vector<int> rs(1, 0);
+    for (int m = 0; m < K; ++m) {
+        std::vector<double> Hm((size_t)K * K), sv, U, V;
+        for (int a = 0; a < K; ++a)
+            for (int b = 0; b < K; ++b) Hm[(size_t)b * K + a] = H[((size_t)m * K + a) * K + b];
+        svd_small(K, K, Hm, sv, U, V);
+        const double thr = (svd_tol > 0 ? svd_tol : 1e-14) * sv[0];
+        int Rm = 0;
+        for (int r = 0; r < K; ++r) {
+            if (!(sv[r] > thr)) continue;
+            for (int l = 0; l < K; ++l) {
+                A.push_back(U[(size_t)r * K + l]);
+                B.push_back(sv[r] * V[(size_t)r * K + l]);
+            }
+            ++Rm;
+        }
+        d->ranks.push_back(Rm);
+        rs.push_back(rs.back() + Rm);
+    }
+    d->R = rs.back();
+    const size_t es = elem_size(plan->prec);
+    const size_t n3 = (size_t)plan->hp.N * plan->hp.N * plan->hp.N;
+    size_t off = 0;
+    auto take = [&](size_t b) { const size_t o = off; off = align_up(off + b, 256); return o; };
+    d->off_A = take(A.size() * es + es);
+    d->off_B = take(B.size() * es + es);
+    d->off_rs = take(rs.size() * sizeof(int));
+    d->off_f = take((size_t)max_elements * d->R * n3 * es);
+    d->off_g = take((size_t)max_elements * d->R * n3 * es);
+    d->off_Q = take((size_t)max_elements * d->R * n3 * es);
+    std::vector<unsigned char> blob(d->off_f, 0);
+    if (plan->prec == DGFS_PREC_FP64) {
+        put_coeffs<double>(blob, d->off_A, A);
+        put_coeffs<double>(blob, d->off_B, B);
+    } else {
+        put_coeffs<float>(blob, d->off_A, A);
+        put_coeffs<float>(blob, d->off_B, B);
+    }
+    std::memcpy(blob.data() + d->off_rs, rs.data(), rs.size() * sizeof(int));
+    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    cudaError_t e = cudaMalloc(&d->d_mem, off);
+    if (e != cudaSuccess) return fail(DGFS_ERR_OOM, std::string("DG workspace: ") + cudaGetErrorString(e));
+    e = cudaMemcpy(d->d_mem, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d->d_mem);
+        return cuda_fail(e, "DG coefficients upload");
+    }
+    *out = d.release();
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_dg_info(dgfs_dg_t dg, int* ranks, int* total) {
+    if (!check_dg(dg)) return fail(DGFS_ERR_STATE, "invalid or destroyed DG operator");
+    if (ranks)
+        for (int m = 0; m < dg->K; ++m) ranks[m] = dg->ranks[m];
+    if (total) *total = dg->R;
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_dg_collide(dgfs_dg_t dg, const void* F, void* C, int64_t E, void* stream) {
+    if (!check_dg(dg)) return fail(DGFS_ERR_STATE, "invalid or destroyed DG operator");
+    if (!check_plan(dg->plan)) return fail(DGFS_ERR_STATE, "the DG operator's plan was destroyed");
+    if (E < 0) return fail(DGFS_ERR_INVALID_ARG, "E must be >= 0");
+    if (E == 0) return DGFS_OK;
+    if (!F || !C) return fail(DGFS_ERR_INVALID_ARG, "NULL field pointer");
+    if (!aligned16(F) || !aligned16(C)) return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
+    if (F == C) return fail(DGFS_ERR_INVALID_ARG, "output aliases the input");
+    DGFS_CUDA(cudaSetDevice(dg->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return dg->plan->prec == DGFS_PREC_FP64
+               ? dg_run<double>(dg, static_cast<const double*>(F), static_cast<double*>(C), E, s)
+               : dg_run<float>(dg, static_cast<const float*>(F), static_cast<float*>(C), E, s);
+}
+
+dgfs_status dgfs_dg_destroy(dgfs_dg_t dg) {
+    if (!dg) return DGFS_OK;
+    if (!check_dg(dg)) return fail(DGFS_ERR_STATE, "invalid or destroyed DG operator");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(dg->device);
+    cudaDeviceSynchronize();
+    cudaFree(dg->d_mem);
+    cudaSetDevice(cur);
+    dg->magic = 0;
+    delete dg;
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_host_dg_tensor(int K, double* nodes, double* M, double* H) {
+    if (!nodes || !M || !H) return fail(DGFS_ERR_INVALID_ARG, "NULL output");
+    std::vector<double> x, m, h;
+    if (!dg_tensor_1d(K, x, m, h)) return fail(DGFS_ERR_INVALID_ARG, "K must be in [2, 16]");
+    std::memcpy(nodes, x.data(), x.size() * sizeof(double));
+    std::memcpy(M, m.data(), m.size() * sizeof(double));
+    std::memcpy(H, h.data(), h.size() * sizeof(double));
+    return DGFS_OK;
+}
+
 dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host, int64_t B,
                               void* stream) {
     if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");

@@ -104,6 +104,16 @@ cudaError_t launch_finalize(int N, int Nrho, const Cplx<T>* Y, int yfields, cons
                             const T* c, const T* G, const int64_t* offs, int64_t nodes, int mode,
                             T* out, int* flags, cudaStream_t s);
 
+// ---- DG element collision, SVD variant (k_dg.cu) ---------------------------------------
+// f[e][r] = sum_l A[r][l] F[e][l], g[e][r] = sum_l B[r][l] F[e][l]   (F [E][K][n3], K <= 16)
+template <typename T>
+cudaError_t launch_dg_combine(const T* F, const T* A, const T* B, int K, int R, int64_t n3, int64_t E, T* f, T* g,
+                              cudaStream_t s);
+// C[e][m] = sum_{r = rs[m]}^{rs[m+1]-1} Q[e][r]   (rs: device [K + 1])
+template <typename T>
+cudaError_t launch_dg_accumulate(const T* Q, const int* rs, int K, int R, int64_t n3, int64_t E, T* C,
+                                 cudaStream_t s);
+
 // ---- fused Fourier stage (k_spectral.cu) ----------------------------------------------
 // The whole Fourier side of a non-adjoint call in three launches for N = 8, 16 (float, double)
 // and N = 32 (float), rank <= 32, Nrho <= 64: projection of P, loss operands la (field rank)

@@ -251,7 +251,73 @@ void jacobi_svd(int m, int n, std::vector<double> A, std::vector<double>& sv,
 
 inline int signed_k(int q, int N) { return q < N / 2 ? q : q - N; }
 
+// P_n(x) and P'_n(x) by the three-term recurrence (|x| < 1 for the derivative formula)
+void legendre_pd(int n, double x, double& p, double& dp) {
+    double p0 = 1.0, p1 = x;
+    if (n == 0) {
+        p = 1.0;
+        dp = 0.0;
+        return;
+    }
+    for (int k = 1; k < n; ++k) {
+        const double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    p = p1;
+    dp = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
 }  // namespace
+
+void svd_small(int m, int n, const std::vector<double>& A, std::vector<double>& sv, std::vector<double>& U,
+               std::vector<double>& V) {
+    jacobi_svd(m, n, A, sv, U, V);
+}
+
+bool dg_tensor_1d(int K, std::vector<double>& nodes, std::vector<double>& M, std::vector<double>& H) {
+    if (K < 2 || K > 16) return false;
+    // Gauss-Lobatto points: -1, the roots of P'_{K-1} (Newton from the Chebyshev-Lobatto points,
+    // with P''_n = (2 x P'_n - n (n + 1) P_n) / (1 - x^2) from Legendre's equation), 1
+    const int n = K - 1;
+    nodes.assign(K, 0.0);
+    nodes[0] = -1.0;
+    nodes[K - 1] = 1.0;
+    for (int j = 1; j < K - 1; ++j) {
+        double x = -std::cos(kPi * j / n);
+        for (int it = 0; it < 100; ++it) {
+            double p, dp;
+            legendre_pd(n, x, p, dp);
+            const double d2p = (2.0 * x * dp - n * (n + 1.0) * p) / (1.0 - x * x);
+            const double dx = dp / d2p;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16) break;
+        }
+        nodes[j] = x;
+    }
+    // Lagrange basis at Gauss-Legendre points exact for the degree 3 (K - 1) integrands
+    std::vector<double> xq, wq;
+    gauss_legendre(3 * K / 2 + 1, -1.0, 1.0, xq, wq);
+    const int nq = (int)xq.size();
+    std::vector<double> phi((size_t)K * nq);
+    for (int l = 0; l < K; ++l)
+        for (int q = 0; q < nq; ++q) {
+            double v = 1.0;
+            for (int j = 0; j < K; ++j)
+                if (j != l) v *= (xq[q] - nodes[j]) / (nodes[l] - nodes[j]);
+            phi[(size_t)l * nq + q] = v;
+        }
+    M.assign((size_t)K * K, 0.0);
+    H.assign((size_t)K * K * K, 0.0);
+    for (int m = 0; m < K; ++m)
+        for (int a = 0; a < K; ++a)
+            for (int q = 0; q < nq; ++q) {
+                const double pm = phi[(size_t)m * nq + q] * phi[(size_t)a * nq + q] * wq[q];
+                M[(size_t)m * K + a] += pm;
+                for (int b = 0; b < K; ++b) H[((size_t)m * K + a) * K + b] += pm * phi[(size_t)b * nq + q];
+            }
+    return true;
+}
 
 // ---- plan --------------------------------------------------------------------------------
 

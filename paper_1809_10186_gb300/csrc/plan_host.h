@@ -39,6 +39,16 @@ bool sphere_pairs(int M, std::vector<double>& sig, std::vector<double>& w);
 // Circulant filter a[N] of the translate by t (multiplier e^{i pi k t / L}, Nyquist cos).
 void translate_filter(int N, double L, double t, double* a);
 
+// Dense SVD A = U diag(sv) V^T of a column-major m x n matrix (m >= n), one-sided Jacobi; sv
+// descending, U m x n and V n x n column-major.
+void svd_small(int m, int n, const std::vector<double>& A, std::vector<double>& sv, std::vector<double>& U,
+               std::vector<double>& V);
+
+// 1-D nodal DG basis (Sec. 3.4): K Gauss-Lobatto points of [-1, 1], mass matrix M[m][l] and
+// H[m][l1][l2] = int phi_m phi_l1 phi_l2 (eqs. eq_massMatrix, eq_stiffMatrix3). False for K
+// outside [2, 16].
+bool dg_tensor_1d(int K, std::vector<double>& nodes, std::vector<double>& M, std::vector<double>& H);
+
 double default_b(double gamma);
 double default_R(double L);
 

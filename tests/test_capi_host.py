@@ -97,3 +97,22 @@ def test_null_and_destroyed_plans_rejected(lib):
     assert lib.dgfs_collide(None, None, None, 1, None) == 7
     assert lib.dgfs_plan_destroy(None) == 0
     assert lib.dgfs_plan_create(None, None) == 1
+
+
+@pytest.mark.parametrize("K", [2, 3, 4, 6, 9])
+def test_dg_tensor_matches_oracle(lib, K):
+    """Gauss-Lobatto nodes, mass matrix and H of the C library against the oracle's own
+    construction (Sec. 3.4, eqs. eq_massMatrix and eq_stiffMatrix3)."""
+    from oracle import dg as D
+    nodes, M, H = binding.host_dg_tensor(K)
+    on, oM, oH = D.dg_tensors(K)
+    np.testing.assert_allclose(nodes, on, atol=1e-14)
+    np.testing.assert_allclose(M, oM, atol=1e-14)
+    np.testing.assert_allclose(H, oH, atol=1e-14)
+
+
+def test_dg_tensor_rejects_bad_K(lib):
+    d = ctypes.POINTER(ctypes.c_double)
+    buf = np.zeros(20 * 20 * 20)
+    for K in (1, 17):
+        assert lib.dgfs_host_dg_tensor(K, buf.ctypes.data_as(d), buf.ctypes.data_as(d), buf.ctypes.data_as(d)) == 1
