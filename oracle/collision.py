@@ -448,3 +448,21 @@ def ssp_rk2(plan: OraclePlan, f, dt, steps):
         v1 = f + dt * fast_Q(plan, f)
         f = 0.5 * f + 0.5 * v1 + 0.5 * dt * fast_Q(plan, v1)
     return f
+
+
+def ssp_rk3(plan: OraclePlan, f, dt, steps):
+    """Space-homogeneous df/dt = Q(f,f) with the 3rd-order SSP Runge-Kutta scheme (eq. SSPRK3)."""
+    f = np.asarray(f, float).copy()
+    for _ in range(steps):
+        v1 = f + dt * fast_Q(plan, f)
+        v2 = 0.75 * f + 0.25 * v1 + 0.25 * dt * fast_Q(plan, v1)
+        f = f / 3.0 + 2.0 / 3.0 * v2 + 2.0 / 3.0 * dt * fast_Q(plan, v2)
+    return f
+
+
+def entropy(plan: OraclePlan, f):
+    """Boltzmann's H = int f ln f dc over the points where f > 0 (mid-point rule); the collision
+    operator does not increase it (H-theorem)."""
+    f = np.asarray(f, float)
+    pos = f > 0
+    return float((f[pos] * np.log(f[pos])).sum() * plan.dc ** 3)

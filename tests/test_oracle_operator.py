@@ -87,6 +87,41 @@ def test_bkw_ssp_rk2_time_stepping():
     assert err < 0.2 * 2.42e-5 * 1.5 + 1e-7
 
 
+def test_bkw_ssp_rk3_time_stepping_and_temporal_orders():
+    """Eq. SSPRK3 follows the BKW closed form like eq. SSPRK2, and the two schemes converge in dt
+    at orders 3 and 2 (self-convergence against dt/8: the spatial error is the same in every run)."""
+    plan = _bkw_plan(16, 16, nyquist="sym")
+    c2 = O.grid_c2(plan)
+    f0 = O.bkw_f(c2, 5.5)
+    f3 = O.ssp_rk3(plan, f0, 0.01, 20)
+    f2 = O.ssp_rk2(plan, f0, 0.01, 20)
+    ref_err = np.abs(f2 - O.bkw_f(c2, 5.7)).max()
+    assert np.abs(f3 - O.bkw_f(c2, 5.7)).max() < 1.05 * ref_err + 1e-9
+    T, dts = 2.0, (0.5, 0.25)
+    for scheme, order in ((O.ssp_rk2, 2), (O.ssp_rk3, 3)):
+        fine = scheme(plan, f0, 0.0625, int(T / 0.0625))
+        e = [np.abs(scheme(plan, f0, dt, int(T / dt)) - fine).max() for dt in dts]
+        rate = np.log2(e[0] / e[1])
+        assert abs(rate - order) < 0.35, (order, e, rate)
+
+
+def test_entropy_of_a_maxwellian_and_H_theorem():
+    """H of n (pi T)^{-3/2} e^{-|c-u|^2/T} is n [ln(n (pi T)^{-3/2}) - 3/2]; under the collision
+    operator H does not increase along an SSP-RK2 run from a two-Maxwellian mixture."""
+    plan = O.OraclePlan(16, 6.0, gamma=0.38, M=12, Nrho=16, nyquist="sym")
+    cx, cy, cz = np.meshgrid(plan.c, plan.c, plan.c, indexing="ij")
+    n, T, u = 1.3, 0.9, np.array([0.2, -0.1, 0.05])
+    fm = n * (np.pi * T) ** -1.5 * np.exp(-((cx - u[0]) ** 2 + (cy - u[1]) ** 2 + (cz - u[2]) ** 2) / T)
+    # mid-point rule on the 16-point grid: spectrally accurate, 2e-6 here
+    assert O.entropy(plan, fm) == pytest.approx(n * (np.log(n * (np.pi * T) ** -1.5) - 1.5), rel=1e-5)
+    f = fm + 0.7 * (np.pi * 0.6) ** -1.5 * np.exp(-((cx + 1.0) ** 2 + cy ** 2 + cz ** 2) / 0.6)
+    hs = [O.entropy(plan, f)]
+    for _ in range(4):
+        f = O.ssp_rk2(plan, f, 0.05, 1)
+        hs.append(O.entropy(plan, f))
+    assert all(b < a for a, b in zip(hs, hs[1:])), hs
+
+
 # ---- direct Galerkin sum versus the fast form -------------------------------------------
 
 @pytest.mark.parametrize("N,M,loss", [(4, 6, "paper"), (6, 12, "paper"), (8, 12, "paper"),
