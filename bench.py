@@ -52,6 +52,9 @@ def _args():
     ap.add_argument("--dg", action="store_true",
                     help="measure the DG element collision term (Sec. 3.4, SVD variant) on the 1-D slab "
                          "workload instead of the headline (prints its own line)")
+    ap.add_argument("--rk", type=int, default=0, choices=[0, 2, 3],
+                    help="measure SSP-RK2/3 time steps (dgfs_ssprk) of the headline workload instead "
+                         "(prints its own line)")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -277,6 +280,44 @@ def run_dg(a):
     return 0
 
 
+def run_rk(a):
+    """Space-homogeneous SSP-RK steps (eqs. SSPRK2/3) of the headline workload's 2048 nodes: each
+    step is `order` collision evaluations plus the stage kernels, all through dgfs_ssprk."""
+    import numpy as np
+    import torch
+    from paper_1809_10186_gb300 import binding, workloads as W
+    torch.cuda.set_device(0)
+    cfg = W.CONFIGS[WORKLOAD]
+    N, L, B = cfg["N"], cfg["L"], a.nodes or cfg["B"]
+    F, _ = W.two_maxwellian(B, N, L, cfg["seed"], dtype=np.float32)
+    f = torch.from_numpy(F).cuda()
+    plan = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=cfg["M"], N_rho=cfg["Nrho"], svd_tol=cfg["svd_tol"],
+                        precision=a.prec, max_batch=B)
+    plan.ssprk(f, 0.01, a.warmup, order=a.rk)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    plan.profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.ssprk(f, 0.01, a.steps, order=a.rk)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = plan.profile_end()
+    clocks = sampler.stop()
+    plan.stream_status()
+    ms = e0.elapsed_time(e1) / a.steps
+    mom = plan.moments(f).cpu().numpy()
+    line = {"metric": "SSP-RK%d node-steps/s, space-homogeneous, N=32 VHS" % a.rk, "value": B / (ms / 1e3),
+            "unit": "node-steps/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": a.prec, "data": "synthetic",
+            "config": {"workload": "%s: %d nodes, dt = 0.01" % (WORKLOAD, B), "order": a.rk},
+            "mass_after": float(mom[:, 0].mean()), "gpu_launches": prof["launches"], "clocks": clocks}
+    print(json.dumps(line))
+    plan.close()
+    return 0
+
+
 def main():
     a = _args()
     if a.oracle_worker:
@@ -285,6 +326,8 @@ def main():
         return run_reference(a)
     if a.dg:
         return run_dg(a)
+    if a.rk:
+        return run_rk(a)
     import numpy as np
     import torch
     from paper_1809_10186_gb300 import binding, workloads as W

@@ -195,6 +195,20 @@ dgfs_status dgfs_collide_noalloc(dgfs_plan_t plan, const void* f, void* Q, int64
    plan (DGFS_ERR_TIMEOUT, DGFS_ERR_NUMERIC), then clear them. */
 dgfs_status dgfs_stream_status(dgfs_plan_t plan, void* stream);
 
+/* ---- space-homogeneous time stepping and moments (Secs. 3.3, 3.5) ---------------------
+   dgfs_ssprk advances df/dt = scale Q(f, f) (scale: e.g. 1/Kn) by nsteps steps of dt with the
+   2nd- or 3rd-order SSP Runge-Kutta scheme (eqs. SSPRK2, SSPRK3), in place: f device [B][N^3] in
+   the plan's element type. Every stage is a dgfs_collide evaluation plus one elementwise
+   combination kernel; the stage fields live in the plan's workspace. Stream-ordered, no
+   allocation; non-finite values raise DGFS_ERR_NUMERIC in dgfs_stream_status. */
+dgfs_status dgfs_ssprk(dgfs_plan_t plan, int order, void* f, int64_t B, double dt, double scale, int nsteps,
+                       void* stream);
+/* Mid-point-rule moments of every node (eq. moments1) and Boltzmann's H: out device [B][15]
+   doubles: n, u_x, u_y, u_z, T, P_xx, P_yy, P_zz, P_xy, P_xz, P_yz, q_x, q_y, q_z, H, with
+   T = 2/(3n) int f |c-u|^2, P = 2 int f (c-u)(c-u), q = int f (c-u)|c-u|^2, H = int f ln f over
+   the points where f > 0; accumulated in FP64. */
+dgfs_status dgfs_moments(dgfs_plan_t plan, const void* f, double* out, int64_t B, void* stream);
+
 /* ---- DG element collision term (Sec. 3.4) ---------------------------------------------
    In the weak form (eq. eq_weakForm) the collision term of test function m in an element is
      C[m] = sum_{l1, l2} H[m][l1][l2] Q(F[l1], F[l2])                               (eq. HH)

@@ -77,6 +77,8 @@ _SIGNATURES = {
                              ctypes.POINTER(ctypes.c_double)],
     "dgfs_host_translate_filter": [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(ctypes.c_double)],
+    "dgfs_ssprk": [_P, ctypes.c_int, _P, _I64, ctypes.c_double, ctypes.c_double, ctypes.c_int, _P],
+    "dgfs_moments": [_P, _P, _P, _I64, _P],
     "dgfs_dg_create": [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_double, _I64,
                        ctypes.POINTER(_P)],
     "dgfs_dg_info": [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
@@ -254,6 +256,22 @@ class Plan:
 
     def stream_status(self, stream=None):
         check(lib().dgfs_stream_status(self.handle, _stream_ptr(stream)), "dgfs_stream_status")
+
+    def ssprk(self, f, dt, steps, order=2, scale=1.0, stream=None):
+        """Advances df/dt = scale Q(f, f) in place by `steps` SSP-RK steps (dgfs_ssprk)."""
+        check(lib().dgfs_ssprk(self.handle, int(order), ctypes.c_void_p(f.data_ptr()), ctypes.c_int64(f.shape[0]),
+                               float(dt), float(scale), int(steps), _stream_ptr(stream)), "dgfs_ssprk")
+        return f
+
+    MOMENT_NAMES = ("n", "ux", "uy", "uz", "T", "Pxx", "Pyy", "Pzz", "Pxy", "Pxz", "Pyz", "qx", "qy", "qz", "H")
+
+    def moments(self, f, stream=None):
+        """[B, 15] float64 device tensor: n, u, T, P, q and H of every node (dgfs_moments)."""
+        import torch
+        out = torch.empty(f.shape[0], 15, dtype=torch.float64, device=f.device)
+        check(lib().dgfs_moments(self.handle, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_int64(f.shape[0]), _stream_ptr(stream)), "dgfs_moments")
+        return out
 
     def debug_inject(self, mode=1):
         """Failure-detection test hook: mode 1 makes the next tensor-core launch lose one

@@ -699,6 +699,86 @@ dgfs_status dgfs_ragged_destroy(dgfs_ragged_t r) {
     return DGFS_OK;
 }
 
+// ---- space-homogeneous SSP-RK time stepping and moments (Secs. 3.3, 3.5) ----------------------
+
+}  // extern "C"
+
+namespace {
+
+// Stages (eqs. SSPRK2, SSPRK3) with L(u) = scale Q(u, u) evaluated by run_chunk into q:
+//   v1 = u + dt L(u)
+//   RK2: u <- 1/2 u + 1/2 v1 + 1/2 dt L(v1)
+//   RK3: v2 = 3/4 u + 1/4 v1 + 1/4 dt L(v1);  u <- 1/3 u + 2/3 v2 + 2/3 dt L(v2)
+template <typename T>
+dgfs_status ssprk_run(dgfs_plan_s* p, int order, T* f, int64_t B, double dt, double scale, int nsteps,
+                      cudaStream_t s) {
+    const int64_t n3 = (int64_t)p->hp.N * p->hp.N * p->hp.N;
+    T* stage = reinterpret_cast<T*>(ws(p, p->off_io));   // the staging area holds 2 chunks of fields
+    T* q = stage + p->chunk * n3;
+    const NodeParams np{nullptr, nullptr, p->hp.gamma, p->hp.b, 0};
+    const double h = dt * scale;
+    for (int64_t n0 = 0; n0 < B; n0 += p->chunk) {
+        const int64_t nn = std::min<int64_t>(p->chunk, B - n0), n = nn * n3;
+        T* u = f + n0 * n3;
+        for (int it = 0; it < nsteps; ++it) {
+            dgfs_status st = run_chunk<T>(p, Op::Collide, u, nullptr, q, nullptr, np, nn, s);
+            if (st != DGFS_OK) return st;
+            cudaError_t e = launch_rk_combine<T>(n, 1.0, u, 0.0, nullptr, h, q, stage, p->d_flags, s);
+            if (e) return cuda_fail(e, "SSP-RK stage");
+            st = run_chunk<T>(p, Op::Collide, stage, nullptr, q, nullptr, np, nn, s);
+            if (st != DGFS_OK) return st;
+            if (order == 2) {
+                e = launch_rk_combine<T>(n, 0.5, u, 0.5, stage, 0.5 * h, q, u, p->d_flags, s);
+            } else {
+                e = launch_rk_combine<T>(n, 0.75, u, 0.25, stage, 0.25 * h, q, stage, p->d_flags, s);
+                if (!e) {
+                    st = run_chunk<T>(p, Op::Collide, stage, nullptr, q, nullptr, np, nn, s);
+                    if (st != DGFS_OK) return st;
+                    e = launch_rk_combine<T>(n, 1.0 / 3.0, u, 2.0 / 3.0, stage, 2.0 / 3.0 * h, q, u, p->d_flags, s);
+                }
+            }
+            if (e) return cuda_fail(e, "SSP-RK stage");
+            if (p->prof) p->prof_launches += order;
+        }
+    }
+    return DGFS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dgfs_status dgfs_ssprk(dgfs_plan_t plan, int order, void* f, int64_t B, double dt, double scale, int nsteps,
+                       void* stream) {
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    if (order != 2 && order != 3) return fail(DGFS_ERR_INVALID_ARG, "order must be 2 or 3");
+    if (B < 0 || nsteps < 0) return fail(DGFS_ERR_INVALID_ARG, "B and nsteps must be >= 0");
+    if (!std::isfinite(dt) || !std::isfinite(scale)) return fail(DGFS_ERR_INVALID_ARG, "dt and scale must be finite");
+    if (B == 0 || nsteps == 0) return DGFS_OK;
+    if (!f) return fail(DGFS_ERR_INVALID_ARG, "NULL field pointer");
+    if (!aligned16(f)) return fail(DGFS_ERR_INVALID_ARG, "field pointer must be 16-byte aligned");
+    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return plan->prec == DGFS_PREC_FP64
+               ? ssprk_run<double>(plan, order, static_cast<double*>(f), B, dt, scale, nsteps, s)
+               : ssprk_run<float>(plan, order, static_cast<float*>(f), B, dt, scale, nsteps, s);
+}
+
+dgfs_status dgfs_moments(dgfs_plan_t plan, const void* f, double* out, int64_t B, void* stream) {
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    if (B < 0) return fail(DGFS_ERR_INVALID_ARG, "B must be >= 0");
+    if (B == 0) return DGFS_OK;
+    if (!f || !out) return fail(DGFS_ERR_INVALID_ARG, "NULL pointer");
+    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const cudaError_t e = plan->prec == DGFS_PREC_FP64
+                              ? launch_moments<double>(static_cast<const double*>(f), plan->hp.N, plan->hp.L, B, out, s)
+                              : launch_moments<float>(static_cast<const float*>(f), plan->hp.N, plan->hp.L, B, out, s);
+    if (e) return cuda_fail(e, "moments");
+    if (plan->prof) plan->prof_launches += 1;
+    return DGFS_OK;
+}
+
 // ---- DG element collision (Sec. 3.4, SVD variant) -------------------------------------------
 
 constexpr uint64_t kDgMagic = 0x444746534447454cull;   // "DGFSDGEL"

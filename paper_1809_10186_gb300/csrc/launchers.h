@@ -114,6 +114,15 @@ template <typename T>
 cudaError_t launch_dg_accumulate(const T* Q, const int* rs, int K, int R, int64_t n3, int64_t E, T* C,
                                  cudaStream_t s);
 
+// ---- time stepping and moments (k_time.cu) --------------------------------------------
+// out = a u + b v + c q over n values (v may be nullptr); non-finite results raise flag bit 1
+template <typename T>
+cudaError_t launch_rk_combine(int64_t n, double a, const T* u, double b, const T* v, double c, const T* q, T* out,
+                              int* flags, cudaStream_t s);
+// out [B][15] (FP64): n, u[3], T, P[xx, yy, zz, xy, xz, yz], q[3], H = int f ln f (f > 0)
+template <typename T>
+cudaError_t launch_moments(const T* f, int N, double L, int64_t B, double* out, cudaStream_t s);
+
 // ---- fused Fourier stage (k_spectral.cu) ----------------------------------------------
 // The whole Fourier side of a non-adjoint call in three launches for N = 8, 16 (float, double)
 // and N = 32 (float), rank <= 32, Nrho <= 64: projection of P, loss operands la (field rank)

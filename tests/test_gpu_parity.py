@@ -118,11 +118,10 @@ def test_bkw_single_node_fp64():
         c2 = O.grid_c2(op)
         print("R=%.4f err/|Q-| %.3g err/|Q| %.3g  |Q-Q_bkw|_inf %.3g" % (R, e_loss, e_q, np.abs(q - O.bkw_Q(c2, 5.5)).max()))
         assert e_q < 1e-10
-        # 20 SSP-RK2 steps (eq. SSPRK2), the stage arithmetic on the device
+        # 20 SSP-RK2 steps (eq. SSPRK2) by the library's own stepper (dgfs_ssprk)
         f = _dev(f0[None], "fp64")
-        for _ in range(20):
-            v1 = f + 0.01 * plan.collide(f)
-            f = 0.5 * f + 0.5 * v1 + 0.005 * plan.collide(v1)
+        plan.ssprk(f, 0.01, 20, order=2)
+        plan.stream_status()
         fo = O.ssp_rk2(op, f0, 0.01, 20)
         assert np.abs(f.cpu().numpy()[0] - fo).max() < 1e-13
         print("  after 20 steps |f - f_bkw(5.7)|_inf = %.3g" % np.abs(fo - O.bkw_f(c2, 5.7)).max())
@@ -133,6 +132,64 @@ def test_bkw_single_node_fp64():
     q8 = plan8.collide(_dev(f8[None], "fp64")).cpu().numpy()[0]
     d8 = O.direct_Q(op8, f8)
     assert np.linalg.norm(q8 - d8) / np.linalg.norm(d8) < 1e-8
+
+
+@pytest.mark.parametrize("prec,order", [("fp64", 2), ("fp64", 3), ("fp32", 3)])
+def test_ssprk_matches_oracle_and_follows_bkw(prec, order):
+    """dgfs_ssprk (eqs. SSPRK2, SSPRK3) on a batch of BKW data against the oracle's schemes, with
+    a scale factor (1/Kn) and more nodes than one internal chunk."""
+    cfg = W.CONFIGS["bkw_n16"]
+    N, L = cfg["N"], cfg["L"]
+    f0 = W.bkw(N, L, 5.5)
+    plan = binding.Plan(N=N, L=L, gamma=0.0, b=cfg["b"], R=cfg["R"], M=cfg["M"], N_rho=cfg["Nrho"], precision=prec,
+                        max_batch=2)
+    op = O.OraclePlan(N, L, gamma=0.0, b=cfg["b"], R=cfg["R"], M=cfg["M"], Nrho=cfg["Nrho"], nyquist="sym")
+    scale, dt, steps = 0.5, 0.02, 10      # df/dt = 0.5 Q: the BKW datum at t0 + 0.5 * 0.2
+    F0 = np.stack([f0] * 3)
+    f = _dev(_as_input(F0, prec), prec)
+    plan.ssprk(f, dt, steps, order=order, scale=scale)
+    plan.stream_status()
+    scheme = O.ssp_rk2 if order == 2 else O.ssp_rk3
+    ref = scheme(op, _as_input(f0, prec), dt * scale, steps)   # scale folds into the step
+    got = f.double().cpu().numpy()
+    err = np.abs(got - ref[None]).max() / np.abs(ref).max()
+    print(prec, "RK%d" % order, "rel max err vs oracle %.3g, |f - f_bkw|_inf %.3g" % (
+        err, np.abs(ref - O.bkw_f(O.grid_c2(op), 5.6)).max()))
+    assert err < (1e-12 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_moments_and_entropy_match_oracle(prec):
+    N, L = 16, 6.0
+    F, _ = W.two_maxwellian(4, N, L, 808)
+    F = _as_input(F, prec)
+    plan = binding.Plan(N=N, L=L, gamma=0.38, M=12, N_rho=N, precision=prec)
+    mom = plan.moments(_dev(F, prec)).cpu().numpy()
+    op = O.OraclePlan(N, L, gamma=0.38, M=12, Nrho=N, nyquist="sym")
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    for i in range(4):
+        m = O.moments(op, F[i])
+        ref = [m["n"], *m["u"], m["T"], m["P"][0, 0], m["P"][1, 1], m["P"][2, 2], m["P"][0, 1], m["P"][0, 2],
+               m["P"][1, 2], *m["q"], O.entropy(op, F[i])]
+        np.testing.assert_allclose(mom[i], ref, rtol=tol, atol=tol * max(1.0, abs(m["n"])))
+
+
+def test_entropy_decreases_along_device_steps():
+    """H-theorem along dgfs_ssprk: a two-Maxwellian mixture relaxes, H decreases, mass, momentum
+    and energy stay (loss in the paper's form conserves them to the spectral error)."""
+    N, L = 16, 6.0
+    F, _ = W.two_maxwellian(2, N, L, 909)
+    plan = binding.Plan(N=N, L=L, gamma=0.38, M=12, N_rho=N, precision="fp64")
+    f = _dev(F, "fp64")
+    hist = [plan.moments(f).cpu().numpy()]
+    for _ in range(4):
+        plan.ssprk(f, 0.05, 2, order=3)
+        hist.append(plan.moments(f).cpu().numpy())
+    plan.stream_status()
+    H = np.array([h[:, 14] for h in hist])
+    assert (np.diff(H, axis=0) < 0).all(), H
+    n = np.array([h[:, 0] for h in hist])
+    assert np.abs(n / n[0] - 1).max() < 1e-3
 
 
 def test_slab_n24_fp32_all_nodes():
