@@ -3,7 +3,8 @@
  *
  * The library evaluates the collision operator Q(f,g) of the Boltzmann equation
  * (arXiv:1809.10186, eq. eq_dim_Q_full, in the relative-velocity form eq. apndx_Q)
- * for the VHS kernel B = b |c - c_*|^gamma (eq. B_gen with alpha = 1) with the fast
+ * for the VHS kernel B = b |c - c_*|^gamma (eq. B_gen with alpha = 1), or the VSS kernel
+ * B = b |c - c_*|^gamma (1 + cos chi)^(alpha - 1) (alpha in (1, 2]), with the fast
  * spectral method of the paper's Appendix (eqs. realGG, lowrank1, apndx_fs_Glm_Qk):
  * a batch of B independent distribution functions, each sampled on the uniform
  * cell-centred velocity grid c_j = -L + (j + 1/2) 2L/N of Sec. 3.3, goes in; Q at the
@@ -92,6 +93,15 @@ typedef struct {
     int64_t max_batch;         /* nodes processed per internal chunk (sizes the workspace:
                                   about 22 MB per node at N = 32, rank 19); <= 0: chosen by the library
                                   (about 1.5 GB of workspace). Compute calls accept any B >= 0. */
+    double alpha;              /* VSS scattering parameter of eq. B_gen, in [1, 2]; 0 or 1: VHS.
+                                  alpha != 1 keeps the sphere point in the kernel factor
+                                  F(k, c_r, sigma) of eq. realGG, so the gain takes one transform
+                                  per radial AND sphere point (the paper's O(M N^4 log N) cost).
+                                  Supported with DGFS_PREC_FP64 and DGFS_PREC_FP32, svd_tol = 0 and
+                                  svd_rank = 0, by dgfs_collide, dgfs_collide2, dgfs_collide_jvp,
+                                  dgfs_collide_host, dgfs_ssprk and the DG element calls; the
+                                  others return DGFS_ERR_UNSUPPORTED. b <= 0 selects
+                                  alpha / (2^{2-omega+alpha} Gamma(5/2-omega) pi) (Sec. 2.2).  */
 } dgfs_plan_desc;
 
 typedef struct {
@@ -100,6 +110,7 @@ typedef struct {
     int64_t chunk_nodes;       /* nodes per internal chunk                                     */
     size_t workspace_bytes;    /* device workspace owned by the plan                           */
     size_t table_bytes;        /* device tables owned by the plan                              */
+    double alpha;              /* VSS scattering parameter (1: VHS)                            */
 } dgfs_plan_info_t;
 
 /* Fill a descriptor with defaults (N=32, L=7, gamma=0, b=default, M=38, N_rho=N, FP32). */
@@ -276,6 +287,19 @@ dgfs_status dgfs_host_quadrature(const dgfs_plan_desc* desc, double* c_r, double
    sum_j' a[(j - j') mod N] f_j', the grid restriction of the trigonometric interpolant
    shifted by t (multiplier e^{i pi k t / L}, Nyquist: cos(pi N t / 2L)). */
 dgfs_status dgfs_host_translate_filter(int N, double L, double t, double* a);
+
+/* The plan builder's VSS kernel factor F(k, c_r, sigma) of eq. realGG for B = b c_r^gamma
+   (1 + cos chi)^(alpha - 1) (Funk-Hecke series of its Legendre expansion), at n points given
+   by k_abs[i] = |k| (lattice units), mu[i] = sigma.k / |k| and c_r[i]; host arrays, F[i] out.
+   b <= 0 selects the default constant of dgfs_plan_desc. No GPU needed. */
+dgfs_status dgfs_host_vss_factor(double L, double gamma, double b, double alpha, int n,
+                                 const double* k_abs, const double* mu, const double* c_r, double* F);
+
+/* The FP64 tables a VSS plan (desc->alpha != 1) would upload, built on the host: A [N_rho][n_pairs]
+   [N^3] = w_r w_p F(k, c_r, sigma_p) and the loss weight GL [N^3], both in DFT index order (index
+   q of an axis is the lattice index q for q < N/2, q - N otherwise). Host arrays sized by the caller
+   (n_pairs as returned by dgfs_host_quadrature); either may be NULL. No GPU needed. */
+dgfs_status dgfs_host_vss_tables(const dgfs_plan_desc* desc, double* A, double* GL);
 
 #ifdef __cplusplus
 }

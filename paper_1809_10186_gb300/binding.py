@@ -27,7 +27,7 @@ class dgfs_plan_desc(ctypes.Structure):
                 ("sphere_xyzw", ctypes.POINTER(ctypes.c_double)), ("N_rho", ctypes.c_int),
                 ("svd_tol", ctypes.c_double), ("svd_rank", ctypes.c_int),
                 ("precision", ctypes.c_int), ("loss_mode", ctypes.c_int),
-                ("max_batch", ctypes.c_int64)]
+                ("max_batch", ctypes.c_int64), ("alpha", ctypes.c_double)]
 
 
 class dgfs_plan_info_t(ctypes.Structure):
@@ -36,7 +36,7 @@ class dgfs_plan_info_t(ctypes.Structure):
                 ("loss_mode", ctypes.c_int), ("L", ctypes.c_double), ("R", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("b", ctypes.c_double),
                 ("chunk_nodes", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t),
-                ("table_bytes", ctypes.c_size_t)]
+                ("table_bytes", ctypes.c_size_t), ("alpha", ctypes.c_double)]
 
 
 class dgfs_profile_t(ctypes.Structure):
@@ -86,6 +86,11 @@ _SIGNATURES = {
     "dgfs_dg_destroy": [_P],
     "dgfs_host_dg_tensor": [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_double)],
+    "dgfs_host_vss_tables": [ctypes.POINTER(dgfs_plan_desc), ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double)],
+    "dgfs_host_vss_factor": [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
 }
 
 _lib = None
@@ -120,7 +125,7 @@ def check(status, where):
 
 
 def make_desc(N=32, L=7.0, gamma=0.0, b=0.0, R=0.0, M=38, N_rho=0, svd_tol=0.0, svd_rank=0,
-              precision="fp32", loss="paper", max_batch=0, sphere=None):
+              precision="fp32", loss="paper", max_batch=0, sphere=None, alpha=0.0):
     d = dgfs_plan_desc()
     check(lib().dgfs_plan_desc_init(ctypes.byref(d)), "dgfs_plan_desc_init")
     d.N, d.L, d.gamma, d.b, d.R, d.M = int(N), float(L), float(gamma), float(b or 0.0), float(R or 0.0), int(M)
@@ -128,6 +133,7 @@ def make_desc(N=32, L=7.0, gamma=0.0, b=0.0, R=0.0, M=38, N_rho=0, svd_tol=0.0, 
     d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     d.loss_mode = LOSS_MODES[loss] if isinstance(loss, str) else int(loss)
     d.max_batch = int(max_batch)
+    d.alpha = float(alpha or 0.0)
     keep = None
     if sphere is not None:
         import numpy as np
@@ -161,6 +167,31 @@ def host_translate_filter(N, L, t):
                                            a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
           "dgfs_host_translate_filter")
     return a
+
+
+def host_vss_factor(L, gamma, alpha, k_abs, mu, c_r, b=0.0):
+    """The plan builder's F(k, c_r, sigma) of the VSS kernel at the given points (host, no GPU)."""
+    import numpy as np
+    k_abs, mu, c_r = np.broadcast_arrays(*(np.ascontiguousarray(x, dtype=np.float64) for x in (k_abs, mu, c_r)))
+    k_abs, mu, c_r = (np.ascontiguousarray(x).ravel() for x in (k_abs, mu, c_r))
+    out = np.zeros(len(k_abs))
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    check(lib().dgfs_host_vss_factor(float(L), float(gamma), float(b), float(alpha), len(out), dp(k_abs), dp(mu),
+                                     dp(c_r), dp(out)), "dgfs_host_vss_factor")
+    return out
+
+
+def host_vss_tables(**kw):
+    """(A [N_rho, n_pairs, N, N, N], GL [N, N, N]) of a VSS plan, built on the host, DFT index order."""
+    import numpy as np
+    _, _, sig, _, _ = host_quadrature(**kw)
+    d, keep = make_desc(**kw)
+    N, nr = d.N, (d.N_rho if d.N_rho > 0 else d.N)
+    A = np.zeros((nr, sig.shape[0], N, N, N))
+    GL = np.zeros((N, N, N))
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    check(lib().dgfs_host_vss_tables(ctypes.byref(d), dp(A), dp(GL)), "dgfs_host_vss_tables")
+    return A, GL
 
 
 def _stream_ptr(stream=None):

@@ -22,7 +22,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]
-SOURCES = ["plan_host.cpp", "capi.cu", "k_gain_f32.cu", "k_gain_f64.cu", "k_fourier.cu", "k_spectral.cu", "k_dg.cu", "k_time.cu", "tc_gain.cu"]
+SOURCES = ["plan_host.cpp", "capi.cu", "k_gain_f32.cu", "k_gain_f64.cu", "k_fourier.cu", "k_spectral.cu", "k_dg.cu", "k_time.cu", "k_vss.cu", "tc_gain.cu"]
 
 
 def _nvcc():
@@ -67,7 +67,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
         for _, log in results:
             sys.stderr.write(log)
     if not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcudart"]
+        cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcudart", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

@@ -8,7 +8,8 @@
 //   3. forward DFTs of X_s and the loss operand
 //   4. the Fourier combine                     sum_s Uk[s] X^_s + i G_loss g^
 //   5. one inverse DFT and the finalisation    Q = Re - f Im
-// on the caller's stream; nothing is allocated after dgfs_plan_create.
+// on the caller's stream; nothing is allocated after dgfs_plan_create. Plans of the VSS kernel
+// (alpha != 1) take the per-sphere-point path of k_vss.cu instead (vss_chunk below).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -66,6 +67,10 @@ struct dgfs_plan_s {
     TcTables tc{};           // tensor-core translate tables (16-bit precisions only)
     // workspace carve (byte offsets into d_ws)
     size_t off_P = 0, off_G = 0, off_S = 0, off_X = 0, off_Y = 0, off_io = 0, off_node = 0;
+    // VSS kernel: nodes per transform batch, its workspace region and the device tables
+    int64_t vchunk = 0;
+    size_t off_V = 0, vss_bytes = 0;
+    void* d_vss = nullptr;   // A [Nrho][npairs][N^3] (T) | GL [N^3] (T) | mu [Nrho][npairs][3][N] (complex T)
     int xfields = 0;
     std::mutex host_mu;      // serialises host-side staging of per-node arrays
     int fault = 0;           // failure-test injection for the next tensor-core launch (dgfs_debug_inject)
@@ -102,14 +107,30 @@ void destroy_io(dgfs_plan_s* p) {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Per-node workspace bytes (all operations share one layout).
+// Bytes of the VSS path per node of a transform batch: the operand spectra (2), the translate
+// spectra (2 sets x npairs), the packed products ((npairs + 1) / 2) and the output spectra (3).
+size_t vss_node_bytes(const HostPlan& h, int prec) {
+    const size_t n3 = (size_t)h.N * h.N * h.N;
+    return 2 * elem_size(prec) * n3 * (2 + 2 * (size_t)h.npairs + (size_t)(h.npairs + 1) / 2 + 3);
+}
+
+// Per-node workspace bytes (all operations share one layout). VSS plans use only the staging
+// area and their own region (off_V, vchunk nodes).
 void workspace_layout(dgfs_plan_s* p, int64_t C) {
     const size_t es = elem_size(p->prec);
     const size_t n3 = (size_t)p->hp.N * p->hp.N * p->hp.N;
-    const size_t Nr = p->hp.Nrho;
+    const size_t Nr = p->hp.aniso ? 0 : p->hp.Nrho;
     p->xfields = p->hp.rank + 2;
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 256); return o; };
+    if (p->hp.aniso) {
+        p->off_V = take((size_t)p->vchunk * vss_node_bytes(p->hp, p->prec));
+        p->off_P = p->off_G = p->off_S = p->off_X = p->off_Y = p->off_V;
+        p->off_io = take(C * 2 * n3 * es);
+        p->off_node = take(C * (sizeof(int64_t) + 2 * sizeof(double)));
+        p->ws_bytes = off;
+        return;
+    }
     p->off_P = take(C * Nr * n3 * es);                 // P_r (also K_r u for the VJP)
     p->off_G = take(C * Nr * n3 * es);                 // VJP per-radial outputs
     p->off_S = take(C * Nr * 2 * n3 * es);             // VJP scratch
@@ -208,6 +229,19 @@ void fill_tables(dgfs_plan_s* p, std::vector<unsigned char>& blob, DevTables<T>&
     t.dftw = reinterpret_cast<const T*>(o_W);
 }
 
+// VSS tables in the compute type: A = w_r w_p F(k, c_r, sigma_p), the loss weight, the multipliers.
+template <typename T>
+void fill_vss_tables(const HostPlan& h, std::vector<unsigned char>& blob) {
+    const size_t n3 = (size_t)h.N * h.N * h.N;
+    blob.assign((h.Fa.size() + h.GLa.size() + h.mu.size()) * sizeof(T), 0);
+    T* d = reinterpret_cast<T*>(blob.data());
+    for (size_t i = 0; i < h.Fa.size(); ++i) d[i] = (T)h.Fa[i];
+    d += h.Fa.size();
+    for (size_t i = 0; i < n3; ++i) d[i] = (T)h.GLa[i];
+    d += n3;
+    for (size_t i = 0; i < h.mu.size(); ++i) d[i] = (T)h.mu[i];
+}
+
 template <typename T>
 void rebase(DevTables<T>& t, void* base) {
     auto fix = [&](auto& ptr) {
@@ -226,10 +260,64 @@ unsigned char* ws(dgfs_plan_s* p, size_t off) { return static_cast<unsigned char
 
 enum class Op { Collide, Collide2, Jvp, Dgamma, Vjp };
 
+// The VSS kernel (alpha != 1): gain^ = scale sum_r sum_p A_rp DFT(products of the translates by
+// +-s_rp), one transform per radial and sphere point (k_vss.cu), in batches of vchunk nodes;
+// loss and finalisation as for VHS: out = Re gain - a Re(GL * b) [- b Re(GL * a) for the JVP].
+template <typename T>
+dgfs_status vss_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, const int64_t* offs, int64_t nodes,
+                      cudaStream_t s) {
+    if (op == Op::Vjp || op == Op::Dgamma)
+        return fail(DGFS_ERR_UNSUPPORTED, "the VSS kernel (alpha != 1) supports Q(f,f), Q(f,g) and the JVP");
+    if (offs) return fail(DGFS_ERR_UNSUPPORTED, "the VSS kernel (alpha != 1) takes no node offsets");
+    const DevTables<T>& t = tables<T>(p);
+    const int N = t.N, np = t.npairs, Nr = t.Nrho, nw = (np + 1) / 2;
+    const int64_t n3 = (int64_t)N * N * N, C = p->vchunk;
+    const bool two = op != Op::Collide;
+    const int sets = two ? 2 : 1, yf = op == Op::Jvp ? 3 : 2;
+    const T scale = op == Op::Jvp ? T(2) : T(1);
+    const T* a = f;
+    const T* b = two ? g : f;
+    Cplx<T>* Fh = reinterpret_cast<Cplx<T>*>(ws(p, p->off_V));
+    Cplx<T>* Gh = Fh + C * n3;
+    Cplx<T>* Z = Gh + C * n3;
+    Cplx<T>* W = Z + C * 2 * np * n3;
+    Cplx<T>* Y = W + C * nw * n3;
+    const T* A = static_cast<const T*>(p->d_vss);
+    const T* GL = A + (size_t)Nr * np * n3;
+    const Cplx<T>* mu = reinterpret_cast<const Cplx<T>*>(GL + n3);
+    for (int64_t n0 = 0; n0 < nodes; n0 += C) {
+        const int64_t nn = std::min<int64_t>(C, nodes - n0);
+        cudaError_t e = launch_load_field<T>(N, a + n0 * n3, nullptr, nullptr, nn, Fh, 1, 0, 0, s);
+        if (!e) e = launch_dft3<T>(t, Fh, nn, true, s);
+        if (!e && two) e = launch_load_field<T>(N, b + n0 * n3, nullptr, nullptr, nn, Gh, 1, 0, 0, s);
+        if (!e && two) e = launch_dft3<T>(t, Gh, nn, true, s);
+        if (!e) e = launch_vss_loss_init<T>(Fh, two ? Gh : Fh, GL, N, nn, Y, yf, s);
+        if (e) return cuda_fail(e, "VSS operand transforms");
+        for (int r = 0; r < Nr && !e; ++r) {
+            e = launch_vss_spectra<T>(Fh, two ? Gh : nullptr, mu + (size_t)r * np * 3 * N, N, np, sets, nn, Z, s);
+            if (!e) e = launch_dft3<T>(t, Z, nn * sets * np, false, s);
+            if (!e) e = launch_vss_product<T>(Z, N, np, sets, nn, W, s);
+            if (!e) e = launch_dft3<T>(t, W, nn * nw, true, s);
+            if (!e) e = launch_vss_accumulate<T>(W, A + (size_t)r * np * n3, N, np, nn, scale, Y, yf, s);
+        }
+        if (e) return cuda_fail(e, "VSS gain");
+        e = launch_dft3<T>(t, Y, nn * yf, false, s);
+        if (!e) e = launch_finalize<T>(N, Nr, Y, yf, a + n0 * n3, op == Op::Jvp ? b + n0 * n3 : nullptr, nullptr,
+                                       nullptr, nn, 0, out + n0 * n3, p->d_flags, s);
+        if (e) return cuda_fail(e, "VSS loss and finalisation");
+        if (p->prof) {
+            p->prof_launches += (two ? 8 : 4) + 1 + (int64_t)Nr * 9 + 4;
+            p->prof_nodes += nn;
+        }
+    }
+    return DGFS_OK;
+}
+
 // One chunk of nodes through the whole pipeline. a/b/f_loss are chunk-base pointers.
 template <typename T>
 dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, const int64_t* offs,
                       NodeParams np, int64_t nodes, cudaStream_t s) {
+    if (p->hp.aniso) return vss_chunk<T>(p, op, f, g, out, offs, nodes, s);
     const DevTables<T>& t = tables<T>(p);
     const int xf = p->xfields;
     T* P = reinterpret_cast<T*>(ws(p, p->off_P));
@@ -374,6 +462,7 @@ dgfs_status dgfs_plan_desc_init(dgfs_plan_desc* d) {
     d->precision = DGFS_PREC_FP32;
     d->loss_mode = DGFS_LOSS_PAPER;
     d->max_batch = 0;
+    d->alpha = 0.0;
     return DGFS_OK;
 }
 
@@ -392,6 +481,8 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
         return fail(DGFS_ERR_UNSUPPORTED, "FP64 plans support N <= 24");
     if (is_tc(p->prec) && !tc_supported(p->hp.N))
         return fail(DGFS_ERR_UNSUPPORTED, "tensor-core precisions support N = 16 and 32");
+    if (p->hp.aniso && is_tc(p->prec))
+        return fail(DGFS_ERR_UNSUPPORTED, "the VSS kernel (alpha != 1) runs in FP64 or FP32");
     DGFS_CUDA(cudaGetDevice(&p->device), "cudaGetDevice");
     // chunk: about 1.5 GB of workspace
     {
@@ -399,13 +490,22 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
         probe.hp.N = p->hp.N;
         probe.hp.Nrho = p->hp.Nrho;
         probe.hp.rank = p->hp.rank;
+        probe.hp.npairs = p->hp.npairs;
+        probe.hp.aniso = p->hp.aniso;
         probe.prec = p->prec;
+        probe.vchunk = 0;
         workspace_layout(&probe, 1);
         const size_t per_node = probe.ws_bytes;
         int64_t C = (int64_t)((size_t)4096 << 20) / (int64_t)per_node;   // about 4 GB of workspace
         C = std::max<int64_t>(1, std::min<int64_t>(C, 4096));
         if (desc->max_batch > 0) C = std::min<int64_t>(desc->max_batch, (int64_t)1 << 20);   // the caller's choice
         p->chunk = C;
+        if (p->hp.aniso) {
+            // transform batches of about 64 MB of translate spectra and products, which stay in L2
+            const size_t n3 = (size_t)p->hp.N * p->hp.N * p->hp.N;
+            const size_t zw = 2 * elem_size(p->prec) * n3 * (2 * (size_t)p->hp.npairs + (p->hp.npairs + 1) / 2);
+            p->vchunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(C, (int64_t)(((size_t)64 << 20) / zw)), 65535));
+        }
     }
     workspace_layout(p.get(), p->chunk);
     std::vector<unsigned char> blob;
@@ -414,11 +514,31 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
     std::vector<unsigned char> tcblob;
     size_t tc_bytes = 0;
     if (is_tc(p->prec)) tc_bytes = build_tc_tables(p->hp, p->prec, tcblob, p->tc);
+    if (p->hp.aniso) {
+        std::vector<unsigned char> vblob;
+        if (p->prec == DGFS_PREC_FP64) fill_vss_tables<double>(p->hp, vblob);
+        else fill_vss_tables<float>(p->hp, vblob);
+        cudaError_t ev = cudaMalloc(&p->d_vss, vblob.size());
+        if (ev != cudaSuccess) return fail(DGFS_ERR_OOM, std::string("VSS tables: ") + cudaGetErrorString(ev));
+        ev = cudaMemcpy(p->d_vss, vblob.data(), vblob.size(), cudaMemcpyHostToDevice);
+        if (ev != cudaSuccess) {
+            cudaFree(p->d_vss);
+            return cuda_fail(ev, "VSS table upload");
+        }
+        p->vss_bytes = vblob.size();
+        // the FP64 host copies are no longer needed
+        std::vector<double>().swap(p->hp.Fa);
+        std::vector<double>().swap(p->hp.mu);
+    }
     cudaError_t e = cudaMalloc(&p->d_tables, p->table_bytes + tc_bytes);
-    if (e != cudaSuccess) return fail(DGFS_ERR_OOM, std::string("device tables: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        if (p->d_vss) cudaFree(p->d_vss);
+        return fail(DGFS_ERR_OOM, std::string("device tables: ") + cudaGetErrorString(e));
+    }
     e = cudaMalloc(&p->d_ws, p->ws_bytes);
     if (e != cudaSuccess) {
         cudaFree(p->d_tables);
+        if (p->d_vss) cudaFree(p->d_vss);
         return fail(DGFS_ERR_OOM, std::string("device workspace: ") + cudaGetErrorString(e));
     }
     e = cudaMalloc(&p->d_flags, 64);
@@ -431,6 +551,7 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
         cudaFree(p->d_tables);
         cudaFree(p->d_ws);
         if (p->d_flags) cudaFree(p->d_flags);
+        if (p->d_vss) cudaFree(p->d_vss);
         return cuda_fail(e, "plan upload");
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cs_h2d, cudaStreamNonBlocking);
@@ -443,12 +564,13 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
         cudaFree(p->d_tables);
         cudaFree(p->d_ws);
         cudaFree(p->d_flags);
+        if (p->d_vss) cudaFree(p->d_vss);
         return cuda_fail(e, "plan streams and events");
     }
     if (p->prec == DGFS_PREC_FP64) rebase(p->td, p->d_tables);
     else rebase(p->tf, p->d_tables);
     if (tc_bytes) rebase_tc_tables(p->tc, static_cast<unsigned char*>(p->d_tables) + p->table_bytes);
-    p->table_bytes += tc_bytes;
+    p->table_bytes += tc_bytes + p->vss_bytes;
     *plan_out = p.release();
     return DGFS_OK;
 }
@@ -463,6 +585,7 @@ dgfs_status dgfs_plan_destroy(dgfs_plan_t plan) {
     cudaFree(plan->d_tables);
     cudaFree(plan->d_ws);
     cudaFree(plan->d_flags);
+    if (plan->d_vss) cudaFree(plan->d_vss);
     for (auto& e : plan->ev) cudaEventDestroy(e);
     destroy_io(plan);
     cudaSetDevice(cur);
@@ -488,6 +611,7 @@ dgfs_status dgfs_plan_info(dgfs_plan_t plan, dgfs_plan_info_t* info) {
     info->chunk_nodes = plan->chunk;
     info->workspace_bytes = plan->ws_bytes;
     info->table_bytes = plan->table_bytes;
+    info->alpha = h.alpha;
     return DGFS_OK;
 }
 
@@ -518,8 +642,10 @@ dgfs_status dgfs_collide_dgamma(dgfs_plan_t plan, const void* f, void* dQdg, int
 static dgfs_status check_ragged(const dgfs_plan_t* plans, int nplans, const int32_t* node_plan,
                                 const int64_t* node_offset, int64_t B) {
     if (!plans || nplans <= 0) return fail(DGFS_ERR_INVALID_ARG, "no plans");
-    for (int i = 0; i < nplans; ++i)
+    for (int i = 0; i < nplans; ++i) {
         if (!check_plan(plans[i])) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+        if (plans[i]->hp.aniso) return fail(DGFS_ERR_UNSUPPORTED, "ragged batches of VSS plans (alpha != 1)");
+    }
     for (int i = 1; i < nplans; ++i) {
         if ((plans[i]->prec == DGFS_PREC_FP64) != (plans[0]->prec == DGFS_PREC_FP64))
             return fail(DGFS_ERR_INVALID_ARG, "ragged plans must share the element type");
@@ -1086,6 +1212,32 @@ dgfs_status dgfs_host_translate_filter(int N, double L, double t, double* a) {
     return DGFS_OK;
 }
 
+dgfs_status dgfs_host_vss_tables(const dgfs_plan_desc* desc, double* A, double* GL) {
+    if (!desc) return fail(DGFS_ERR_INVALID_ARG, "NULL descriptor");
+    HostPlan hp;
+    std::string err;
+    const dgfs_status st = build_host_plan(*desc, hp, err);
+    if (st != DGFS_OK) return fail(st, err);
+    if (!hp.aniso) return fail(DGFS_ERR_INVALID_ARG, "not a VSS descriptor (alpha must differ from 0 and 1)");
+    if (A) std::memcpy(A, hp.Fa.data(), hp.Fa.size() * sizeof(double));
+    if (GL) std::memcpy(GL, hp.GLa.data(), hp.GLa.size() * sizeof(double));
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_host_vss_factor(double L, double gamma, double b, double alpha, int n, const double* k_abs,
+                                 const double* mu, const double* c_r, double* F) {
+    if (!(L > 0) || !std::isfinite(gamma) || !(alpha >= 1.0 && alpha <= 2.0) || n < 0 || !std::isfinite(b))
+        return fail(DGFS_ERR_INVALID_ARG, "bad VSS factor arguments");
+    if (n > 0 && (!k_abs || !mu || !c_r || !F)) return fail(DGFS_ERR_INVALID_ARG, "NULL argument");
+    const double bb = b > 0 ? b : default_b_vss(gamma, alpha);
+    for (int i = 0; i < n; ++i) {
+        if (!(k_abs[i] >= 0) || !(c_r[i] >= 0) || !(std::fabs(mu[i]) <= 1.0))
+            return fail(DGFS_ERR_INVALID_ARG, "k_abs, c_r >= 0 and |mu| <= 1 required");
+        F[i] = vss_F(bb, gamma, alpha, L, k_abs[i], mu[i], c_r[i]);
+    }
+    return DGFS_OK;
+}
+
 }  // extern "C"
 
 // ---- Q(f,f) with its scratch in a fixed device array (no device allocation) --------------
@@ -1156,6 +1308,7 @@ extern "C" dgfs_status dgfs_collide_noalloc(dgfs_plan_t plan, const void* f, voi
     if (!f || !Q) return fail(DGFS_ERR_INVALID_ARG, "NULL field pointer");
     if (!aligned16(f) || !aligned16(Q)) return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
     if (f == Q) return fail(DGFS_ERR_INVALID_ARG, "output aliases the input");
+    if (plan->hp.aniso) return fail(DGFS_ERR_UNSUPPORTED, "dgfs_collide_noalloc of a VSS plan (alpha != 1)");
     const size_t per_node = noalloc_node_bytes(plan);
     const int64_t capacity = (int64_t)(kNoAllocScratchBytes / per_node);
     if (B > capacity) {

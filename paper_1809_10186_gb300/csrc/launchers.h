@@ -104,6 +104,25 @@ cudaError_t launch_finalize(int N, int Nrho, const Cplx<T>* Y, int yfields, cons
                             const T* c, const T* G, const int64_t* offs, int64_t nodes, int mode,
                             T* out, int* flags, cudaStream_t s);
 
+// ---- VSS kernel gain (k_vss.cu) -----------------------------------------------------------
+// Z[n][set][p] = mu_s Fh[n] + i conj(mu_s) Gh[n]  (set 0),  conj(mu_s) Fh[n] + i mu_s Gh[n]  (set 1,
+// sets == 2); Gh == nullptr means Gh = Fh. mu_r: [npairs][3][N] complex per-axis multipliers of +s_rp.
+template <typename T>
+cudaError_t launch_vss_spectra(const Cplx<T>* Fh, const Cplx<T>* Gh, const Cplx<T>* mu_r, int N, int npairs,
+                               int sets, int64_t nodes, Cplx<T>* Z, cudaStream_t s);
+// W[n][j] = P_2j + i P_2j+1 with P_p = sum over sets of Re Z Im Z (twice Re Z0 Im Z0 when sets == 1)
+template <typename T>
+cudaError_t launch_vss_product(const Cplx<T>* Z, int N, int npairs, int sets, int64_t nodes, Cplx<T>* W,
+                               cudaStream_t s);
+// Y[n][0] += scale sum_p A_r[p] P^_p, P^_p separated from the packed spectra W by Hermitian symmetry
+template <typename T>
+cudaError_t launch_vss_accumulate(const Cplx<T>* W, const T* A_r, int N, int npairs, int64_t nodes, T scale,
+                                  Cplx<T>* Y, int yfields, cudaStream_t s);
+// Y[n][0] = 0, Y[n][1] = GL Bh[n], Y[n][2] = GL Ah[n] (yfields == 3)
+template <typename T>
+cudaError_t launch_vss_loss_init(const Cplx<T>* Ah, const Cplx<T>* Bh, const T* GL, int N, int64_t nodes,
+                                 Cplx<T>* Y, int yfields, cudaStream_t s);
+
 // ---- DG element collision, SVD variant (k_dg.cu) ---------------------------------------
 // f[e][r] = sum_l A[r][l] F[e][l], g[e][r] = sum_l B[r][l] F[e][l]   (F [E][K][n3], K <= 16)
 template <typename T>

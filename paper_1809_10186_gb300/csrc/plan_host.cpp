@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <numeric>
+#include <thread>
 
 namespace dgfs {
 
@@ -17,6 +18,12 @@ double default_b(double gamma) {
 }
 
 double default_R(double L) { return 4.0 * L / (3.0 + std::sqrt(2.0)); }  // Appendix
+
+double default_b_vss(double gamma, double alpha) {
+    // nondimensional VSS constant alpha / (2^{2-omega+alpha} Gamma(5/2-omega) pi) (Sec. 2.2)
+    const double omega = 1.0 - 0.5 * gamma;
+    return alpha / (std::pow(2.0, 2.0 - omega + alpha) * std::tgamma(2.5 - omega) * kPi);
+}
 
 void gauss_legendre(int n, double a, double b, std::vector<double>& x, std::vector<double>& w) {
     x.assign(n, 0.0);
@@ -319,6 +326,174 @@ bool dg_tensor_1d(int K, std::vector<double>& nodes, std::vector<double>& M, std
     return true;
 }
 
+// ---- VSS kernel factor (alpha != 1) ---------------------------------------------------------
+//
+// With B = b c_r^gamma (1 + cos chi)^beta, beta = alpha - 1 (eq. B_gen), the factor of eq. realGG,
+// F(k, c_r, sigma) = 2 c_r^2 int_{S2+} B_sym(c_r, sigma.e) cos(pi c_r k.e / 2L) de, is evaluated
+// through the Legendre expansion of the angular factor and the Funk-Hecke formula
+// int_S2 P_l(sigma.e) e^{i a khat.e} de = 4 pi i^l j_l(a) P_l(sigma.khat): only even l survive
+// the symmetrisation and the cosine, and
+//   F = 2 pi b c_r^{gamma+2} sum_{l even} (2l+1) c_l (-1)^{l/2} j_l(a) P_l(mu),
+//   a = pi c_r |k| / 2L, mu = sigma.khat, c_l = int_{-1}^{1} (1 + t)^beta P_l(t) dt.
+// The Legendre moments follow c_0 = 2^{beta+1}/(beta+1), c_{l+1} = c_l (beta - l)/(beta + l + 2)
+// (the ratio of the Beta-function closed form); j_l(a) decays faster than geometrically once l > a,
+// so the series stops at l = a + 40.
+
+namespace {
+
+// j_0..j_lmax(a), a >= 0: backward recurrence j_{l-1} = (2l+1)/a j_l - j_{l+1} from far above
+// max(lmax, a), normalised with sum_l (2l+1) j_l(a)^2 = 1 and signed by the closed form of j_0 or j_1.
+void sph_bessel(int lmax, double a, std::vector<double>& j) {
+    j.assign((size_t)lmax + 1, 0.0);
+    if (a < 1e-8) {          // j_l(a) = O(a^l): only j_0 = 1 matters to double precision for even l
+        j[0] = 1.0;
+        return;
+    }
+    const double hi = std::max((double)lmax, a);
+    const int top = (int)hi + 40 + (int)std::sqrt(40.0 * hi);
+    std::vector<double> v((size_t)top + 2, 0.0);
+    v[top] = 1e-300;
+    for (int l = top; l >= 1; --l) {
+        v[l - 1] = (2.0 * l + 1.0) / a * v[l] - v[l + 1];
+        if (std::fabs(v[l - 1]) > 1e200)
+            for (int m = l - 1; m <= top; ++m) v[m] *= 1e-200;
+    }
+    double vmax = 0.0;
+    for (int l = 0; l <= top; ++l) vmax = std::max(vmax, std::fabs(v[l]));
+    double sum = 0.0;
+    for (int l = 0; l <= top; ++l) sum += (2.0 * l + 1.0) * (v[l] / vmax) * (v[l] / vmax);
+    double scale = 1.0 / (vmax * std::sqrt(sum));
+    const double j0 = std::sin(a) / a, j1 = std::sin(a) / (a * a) - std::cos(a) / a;
+    if (std::fabs(j0) >= std::fabs(j1) ? ((j0 < 0) != (v[0] < 0)) : ((j1 < 0) != (v[1] < 0))) scale = -scale;
+    for (int l = 0; l <= lmax; ++l) j[l] = v[l] * scale;
+}
+
+// Series coefficients g_l = (2l+1) c_l (-1)^{l/2} j_l(a) for even l (0 for odd l), l <= lmax.
+void vss_series(double beta, double a, std::vector<double>& g) {
+    const int lmax = 2 * (((int)a + 41) / 2);
+    std::vector<double> j;
+    sph_bessel(lmax, a, j);
+    g.assign((size_t)lmax + 1, 0.0);
+    double c = std::pow(2.0, beta + 1.0) / (beta + 1.0);
+    for (int l = 0; l <= lmax; ++l) {
+        if (l % 2 == 0) g[l] = (2.0 * l + 1.0) * c * ((l / 2) % 2 ? -1.0 : 1.0) * j[l];
+        c *= (beta - l) / (beta + l + 2.0);
+    }
+}
+
+// sum_l g_l P_l(mu) by the three-term recurrence (l + 1) P_{l+1} = (2l + 1) mu P_l - l P_{l-1}
+double legendre_sum(const std::vector<double>& g, double mu) {
+    double pm = 1.0, pc = mu, s = g[0];
+    for (size_t l = 1; l < g.size(); ++l) {
+        if (g[l] != 0.0) s += g[l] * pc;
+        const double pn = ((2.0 * l + 1.0) * mu * pc - (double)l * pm) / (double)(l + 1);
+        pm = pc;
+        pc = pn;
+    }
+    return s;
+}
+
+}  // namespace
+
+double vss_F(double b, double gamma, double alpha, double L, double k_abs, double mu, double c_r) {
+    std::vector<double> g;
+    vss_series(alpha - 1.0, kPi * c_r * k_abs / (2.0 * L), g);
+    return 2.0 * kPi * b * std::pow(c_r, gamma + 2.0) * legendre_sum(g, std::max(-1.0, std::min(1.0, mu)));
+}
+
+namespace {
+
+// Gain factors Fa[r][q][i] = w_r w_q F(k_i, c_r, sigma_q), the VSS loss weight and the per-axis
+// translate multipliers; one worker thread per group of radial points.
+void build_vss_tables(HostPlan& p) {
+    const int N = p.N, Nr = p.Nrho, np = p.npairs;
+    const size_t n3 = (size_t)N * N * N;
+    const double beta = p.alpha - 1.0;
+    std::vector<int> kv(3 * n3);
+    std::vector<int> q2(n3);
+    for (size_t i = 0; i < n3; ++i) {
+        kv[3 * i] = signed_k((int)(i / ((size_t)N * N)), N);
+        kv[3 * i + 1] = signed_k((int)((i / N) % N), N);
+        kv[3 * i + 2] = signed_k((int)(i % N), N);
+        q2[i] = kv[3 * i] * kv[3 * i] + kv[3 * i + 1] * kv[3 * i + 1] + kv[3 * i + 2] * kv[3 * i + 2];
+    }
+    const int qmax = 3 * (N / 2) * (N / 2);
+    p.Fa.assign((size_t)Nr * np * n3, 0.0);
+    std::vector<double> lossr((size_t)Nr * n3, 0.0);
+    auto work = [&](int r) {
+        const double pref = 2.0 * kPi * p.b * std::pow(p.cr[r], p.gamma + 2.0);
+        std::vector<std::vector<double>> gq(qmax + 1), gq2(qmax + 1);
+        for (size_t i = 0; i < n3; ++i)
+            if (gq[q2[i]].empty()) {
+                const double kk = std::sqrt((double)q2[i]);
+                vss_series(beta, kPi * p.cr[r] * kk / (2.0 * p.L), gq[q2[i]]);
+                if (p.loss_mode == DGFS_LOSS_PAPER) vss_series(beta, kPi * p.cr[r] * kk / p.L, gq2[q2[i]]);
+            }
+        for (int q = 0; q < np; ++q) {
+            const double* sg = &p.sig[3 * q];
+            double* out = &p.Fa[((size_t)r * np + q) * n3];
+            for (size_t i = 0; i < n3; ++i) {
+                // F is even in k (even Legendre degrees only): one evaluation serves k and -k when -k
+                // is on the lattice (no Nyquist component); the DFT mirror index of a Nyquist mode is
+                // a different lattice vector and gets its own evaluation
+                const size_t im = ((size_t)((N - (int)(i / ((size_t)N * N))) % N) * N + (N - (int)((i / N) % N)) % N) * N +
+                                  (N - (int)(i % N)) % N;
+                const bool pair = kv[3 * im] == -kv[3 * i] && kv[3 * im + 1] == -kv[3 * i + 1] &&
+                                  kv[3 * im + 2] == -kv[3 * i + 2];
+                if (pair && im < i) continue;
+                const double kk = std::sqrt((double)q2[i]);
+                const double mu = kk > 0 ? (kv[3 * i] * sg[0] + kv[3 * i + 1] * sg[1] + kv[3 * i + 2] * sg[2]) / kk : 0.0;
+                out[i] = p.wr[r] * p.wsig[q] * pref * legendre_sum(gq[q2[i]], mu);
+                if (pair) out[im] = out[i];
+                if (p.loss_mode == DGFS_LOSS_PAPER) {   // eq. lowrank1 at l = m: F(2m, c_r, sigma_q)
+                    const double l0 = 2.0 * p.wr[r] * p.wsig[q] * pref * legendre_sum(gq2[q2[i]], mu);
+                    lossr[(size_t)r * n3 + i] += l0;
+                    if (pair && im != i) lossr[(size_t)r * n3 + im] += l0;
+                }
+            }
+        }
+    };
+    const int nt = std::max(1, std::min<int>(Nr, (int)std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t)
+        pool.emplace_back([&, t] {
+            for (int r = t; r < Nr; r += nt) work(r);
+        });
+    for (auto& th : pool) th.join();
+    p.GLa.assign(n3, 0.0);
+    if (p.loss_mode == DGFS_LOSS_PAPER) {
+        for (int r = 0; r < Nr; ++r)
+            for (size_t i = 0; i < n3; ++i) p.GLa[i] += lossr[(size_t)r * n3 + i];
+    } else {
+        // G(-m, m) = 2 sum_r w_r F(0, c_r) sum_q w_q cos(...): Lr carries w_r sum_q w_q [mu_s^2 + mu_-s^2],
+        // and F(0, c_r) = 2 pi b c_r^{gamma+2} c_0 is isotropic
+        const double c0 = std::pow(2.0, beta + 1.0) / (beta + 1.0);
+        for (int r = 0; r < Nr; ++r) {
+            const double F0 = 2.0 * kPi * p.b * std::pow(p.cr[r], p.gamma + 2.0) * c0;
+            for (size_t i = 0; i < n3; ++i) p.GLa[i] += F0 * p.Lr[(size_t)r * n3 + i];
+        }
+    }
+    // per-axis multipliers of the translate by +s_rp: e^{i pi k t / L}, Nyquist cos(pi N t / 2L)
+    p.mu.assign((size_t)Nr * np * 3 * N * 2, 0.0);
+    for (int r = 0; r < Nr; ++r)
+        for (int q = 0; q < np; ++q)
+            for (int a = 0; a < 3; ++a) {
+                const double t = 0.5 * p.cr[r] * p.sig[3 * q + a];
+                double* m = &p.mu[(((size_t)r * np + q) * 3 + a) * N * 2];
+                for (int kq = 0; kq < N; ++kq) {
+                    const int k = signed_k(kq, N);
+                    if (k == -N / 2) {
+                        m[2 * kq] = std::cos(kPi * N * t / (2.0 * p.L));
+                    } else {
+                        m[2 * kq] = std::cos(kPi * k * t / p.L);
+                        m[2 * kq + 1] = std::sin(kPi * k * t / p.L);
+                    }
+                }
+            }
+}
+
+}  // namespace
+
 // ---- plan --------------------------------------------------------------------------------
 
 static bool supported_N(int N) { return N == 8 || N == 12 || N == 16 || N == 24 || N == 32; }
@@ -337,7 +512,10 @@ dgfs_status build_quadrature(const dgfs_plan_desc& d, HostPlan& p, std::string& 
     p.L = d.L;
     p.gamma = d.gamma;
     p.R = d.R > 0 ? d.R : default_R(d.L);
-    p.b = d.b > 0 ? d.b : default_b(d.gamma);
+    p.alpha = (d.alpha == 0.0) ? 1.0 : d.alpha;
+    if (!(p.alpha >= 1.0 && p.alpha <= 2.0)) { err = "alpha must lie in [1, 2] (0: VHS)"; return DGFS_ERR_INVALID_ARG; }
+    p.aniso = p.alpha != 1.0;
+    p.b = d.b > 0 ? d.b : (p.aniso ? default_b_vss(d.gamma, p.alpha) : default_b(d.gamma));
     p.Nrho = d.N_rho > 0 ? d.N_rho : d.N;
     p.loss_mode = d.loss_mode;
     if (p.Nrho > 64) { err = "N_rho must be <= 64"; return DGFS_ERR_INVALID_ARG; }
@@ -495,6 +673,13 @@ dgfs_status build_host_plan(const dgfs_plan_desc& d, HostPlan& p, std::string& e
                 }
             }
         }
+    }
+    if (p.aniso) {
+        if (d.svd_tol > 0 || d.svd_rank > 0) {
+            err = "the VSS kernel factor is not compressed: svd_tol and svd_rank must be 0";
+            return DGFS_ERR_UNSUPPORTED;
+        }
+        build_vss_tables(p);
     }
     return DGFS_OK;
 }

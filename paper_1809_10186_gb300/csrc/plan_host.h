@@ -27,7 +27,17 @@ struct HostPlan {
     std::vector<double> Vr;              // [rank][Nrho]
     // loss: G_loss(k) = sum_r rho_r(gamma, b) * Lr[r][k]
     std::vector<double> Lr;              // [Nrho][N^3] in DFT index order
+    // VSS kernel (alpha != 1, eq. B_gen): the kernel factor depends on the sphere point
+    double alpha = 1.0;
+    bool aniso = false;
+    std::vector<double> Fa;              // [Nrho][npairs][N^3] w_r w_p F(k, c_r, sigma_p), DFT index order
+    std::vector<double> GLa;             // [N^3] loss weight G(m, m) of the VSS kernel
+    std::vector<double> mu;              // [Nrho][npairs][3][N][2] per-axis multipliers of +s_rp
 };
+
+// F(k, c_r, sigma) of eq. realGG for the VSS kernel b c_r^gamma (1 + cos chi)^(alpha - 1), as the
+// Funk-Hecke series of its Legendre expansion; k_abs = |k|, mu = sigma.k / |k|.
+double vss_F(double b, double gamma, double alpha, double L, double k_abs, double mu, double c_r);
 
 // Gauss-Legendre rule on [a, b] by Newton iteration on the Legendre recurrence.
 void gauss_legendre(int n, double a, double b, std::vector<double>& x, std::vector<double>& w);
@@ -50,6 +60,7 @@ void svd_small(int m, int n, const std::vector<double>& A, std::vector<double>& 
 bool dg_tensor_1d(int K, std::vector<double>& nodes, std::vector<double>& M, std::vector<double>& H);
 
 double default_b(double gamma);
+double default_b_vss(double gamma, double alpha);
 double default_R(double L);
 
 // Validates the descriptor and fills the plan. On failure returns a status and a message.

@@ -125,6 +125,10 @@ CONFIGS = {
     # differentiation: 512 nodes, N = 32, omega = 0.81, FP32
     "grad_n32": dict(N=32, L=7.0, Nrho=32, M=38, gamma=omega_to_gamma(0.81), B=512,
                      prec="fp32", seed=SEED_BASE + 5),
+    # VSS kernel (eq. B_gen, alpha != 1): argon's VSS parameters omega = 0.81, alpha = 1.40,
+    # 256 nodes, N = 32, M = 38, FP32 (one transform per radial and sphere point)
+    "vss_n32": dict(N=32, L=7.0, Nrho=32, M=38, gamma=omega_to_gamma(0.81), alpha=1.40, B=256,
+                    prec="fp32", seed=SEED_BASE + 6),
 }
 
 

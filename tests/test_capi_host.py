@@ -116,3 +116,51 @@ def test_dg_tensor_rejects_bad_K(lib):
     buf = np.zeros(20 * 20 * 20)
     for K in (1, 17):
         assert lib.dgfs_host_dg_tensor(K, buf.ctypes.data_as(d), buf.ctypes.data_as(d), buf.ctypes.data_as(d)) == 1
+
+
+# ---- VSS kernel (alpha != 1): the plan builder's tables against the oracle --------------------
+
+@pytest.mark.parametrize("alpha", [1.0, 1.3, 1.5, 2.0])
+def test_vss_factor_matches_oracle_quadrature(lib, alpha):
+    """The library evaluates F(k, c_r, sigma) of eq. realGG as a Funk-Hecke series; the oracle by
+    Gauss-Jacobi and Bessel quadrature about sigma."""
+    from oracle import vss as V
+    rng = np.random.default_rng(5)
+    k = np.concatenate([[0.0, 1.0, 3.0], rng.uniform(0, 56, 60)])
+    mu = rng.uniform(-1, 1, len(k))
+    cr = rng.uniform(0, 6.6, len(k))
+    got = binding.host_vss_factor(7.0, 0.38, alpha, k, mu, cr)
+    b = V.b_vss(1 - 0.19, alpha)
+    ref = np.array([V.F_vss(b, 0.38, alpha, 7.0, np.array([a]), np.array([m]), c)[0] for a, m, c in zip(k, mu, cr)])
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("N,loss,alpha", [(8, "paper", 1.5), (8, "conservative", 1.3), (12, "paper", 1.8)])
+def test_vss_tables_match_oracle(lib, N, loss, alpha):
+    """A = w_r w_p F(k, c_r, sigma_p) on the lattice (Nyquist modes at their own signed index) and
+    the loss weight; the library's sphere pairs are matched to the oracle's up to order and sign."""
+    from oracle import vss as V
+    kw = dict(N=N, L=4.0, gamma=0.5, alpha=alpha, M=12, N_rho=6, loss=loss)
+    A, GL = binding.host_vss_tables(**kw)
+    _, _, sig, _, _ = binding.host_quadrature(**kw)
+    pl = V.VSSPlan(N, 4.0, gamma=0.5, alpha=alpha, M=12, Nrho=6, nyquist="sym", loss=loss)
+    Ao = np.fft.ifftshift(pl.A * pl.wsig[None, :, None, None, None], axes=(2, 3, 4))
+    for p in range(sig.shape[0]):
+        q = int(np.argmax(np.abs(pl.sigma @ sig[p, :3])))
+        assert abs(abs(pl.sigma[q] @ sig[p, :3]) - 1) < 1e-12
+        assert np.abs(A[:, p] - Ao[:, q]).max() < 1e-12 * np.abs(Ao).max()
+    assert np.abs(GL - np.fft.ifftshift(pl.Gloss)).max() < 1e-12 * np.abs(pl.Gloss).max()
+
+
+def test_vss_descriptors_rejected(lib):
+    with pytest.raises(binding.DGFSError):
+        binding.host_vss_tables(N=8, L=4.0, alpha=2.5, M=12)
+    with pytest.raises(binding.DGFSError):
+        binding.host_vss_tables(N=8, L=4.0, alpha=1.5, M=12, svd_tol=1e-3)
+    with pytest.raises(binding.DGFSError):
+        binding.host_vss_tables(N=8, L=4.0, alpha=1.0, M=12)
+    with pytest.raises(binding.DGFSError):
+        binding.host_vss_factor(4.0, 0.0, 1.5, [1.0], [1.5], [1.0])
+    _, _, _, _, b = binding.host_quadrature(N=8, L=4.0, M=12, gamma=0.5, alpha=1.5)
+    from oracle import vss as V
+    assert b == pytest.approx(V.b_vss(0.75, 1.5), rel=1e-14)
