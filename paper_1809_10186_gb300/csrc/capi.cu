@@ -69,6 +69,7 @@ struct dgfs_plan_s {
     size_t off_P = 0, off_G = 0, off_S = 0, off_X = 0, off_Y = 0, off_io = 0, off_node = 0;
     // VSS kernel: nodes per transform batch, its workspace region and the device tables
     int64_t vchunk = 0;
+    bool vss_planes = false;   // fused plane/line kernels, plane-major fields and tables
     size_t off_V = 0, vss_bytes = 0;
     void* d_vss = nullptr;   // A [Nrho][npairs][N^3] (T) | GL [N^3] (T) | mu [Nrho][npairs][3][N] (complex T)
     int xfields = 0;
@@ -229,15 +230,23 @@ void fill_tables(dgfs_plan_s* p, std::vector<unsigned char>& blob, DevTables<T>&
     t.dftw = reinterpret_cast<const T*>(o_W);
 }
 
-// VSS tables in the compute type: A = w_r w_p F(k, c_r, sigma_p), the loss weight, the multipliers.
+// VSS tables in the compute type: A = w_r w_p F(k, c_r, sigma_p), the loss weight, the multipliers;
+// A and the loss weight plane-major ([kz][kx][ky]) for the fused kernels.
 template <typename T>
-void fill_vss_tables(const HostPlan& h, std::vector<unsigned char>& blob) {
-    const size_t n3 = (size_t)h.N * h.N * h.N;
+void fill_vss_tables(const HostPlan& h, bool planes, std::vector<unsigned char>& blob) {
+    const int N = h.N;
+    const size_t n3 = (size_t)N * N * N;
     blob.assign((h.Fa.size() + h.GLa.size() + h.mu.size()) * sizeof(T), 0);
     T* d = reinterpret_cast<T*>(blob.data());
-    for (size_t i = 0; i < h.Fa.size(); ++i) d[i] = (T)h.Fa[i];
+    auto dst = [&](size_t i) {   // standard index (kx N + ky) N + kz -> stored index
+        if (!planes) return i;
+        const size_t kx = i / ((size_t)N * N), ky = (i / N) % N, kz = i % N;
+        return (kz * N + kx) * N + ky;
+    };
+    for (size_t f = 0; f < h.Fa.size() / n3; ++f)
+        for (size_t i = 0; i < n3; ++i) d[f * n3 + dst(i)] = (T)h.Fa[f * n3 + i];
     d += h.Fa.size();
-    for (size_t i = 0; i < n3; ++i) d[i] = (T)h.GLa[i];
+    for (size_t i = 0; i < n3; ++i) d[dst(i)] = (T)h.GLa[i];
     d += n3;
     for (size_t i = 0; i < h.mu.size(); ++i) d[i] = (T)h.mu[i];
 }
@@ -285,7 +294,34 @@ dgfs_status vss_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
     const T* A = static_cast<const T*>(p->d_vss);
     const T* GL = A + (size_t)Nr * np * n3;
     const Cplx<T>* mu = reinterpret_cast<const Cplx<T>*>(GL + n3);
-    for (int64_t n0 = 0; n0 < nodes; n0 += C) {
+    const Cplx<T>* dftw = reinterpret_cast<const Cplx<T>*>(t.dftw);
+    for (int64_t n0 = 0; n0 < nodes && p->vss_planes; n0 += C) {
+        // fused kernels, plane-major fields
+        const int64_t nn = std::min<int64_t>(C, nodes - n0);
+        cudaError_t e = launch_vss_load_t<T>(a + n0 * n3, N, nn, Fh, s);
+        if (!e) e = launch_dft3<T>(t, Fh, nn, true, s);
+        if (!e && two) e = launch_vss_load_t<T>(b + n0 * n3, N, nn, Gh, s);
+        if (!e && two) e = launch_dft3<T>(t, Gh, nn, true, s);
+        if (!e) e = launch_vss_loss_init<T>(Fh, two ? Gh : Fh, GL, N, nn, Y, yf, s);
+        if (e) return cuda_fail(e, "VSS operand transforms");
+        for (int r = 0; r < Nr && !e; ++r) {
+            e = launch_vss_inverse_planes<T>(Fh, two ? Gh : nullptr, mu + (size_t)r * np * 3 * N, dftw, N, np, sets, nn,
+                                             Z, s);
+            if (!e) e = launch_vss_lines<T>(Z, dftw, N, np, sets, nn, W, s);
+            if (!e) e = launch_vss_forward_planes<T>(dftw, N, nw, nn, W, s);
+            if (!e) e = launch_vss_accumulate<T>(W, A + (size_t)r * np * n3, N, np, nn, scale, Y, yf, s);
+        }
+        if (e) return cuda_fail(e, "VSS gain");
+        e = launch_dft3<T>(t, Y, nn * yf, false, s);
+        if (!e) e = launch_vss_finalize_t<T>(Y, yf, a + n0 * n3, op == Op::Jvp ? b + n0 * n3 : nullptr, N, nn,
+                                             out + n0 * n3, p->d_flags, s);
+        if (e) return cuda_fail(e, "VSS loss and finalisation");
+        if (p->prof) {
+            p->prof_launches += (two ? 8 : 4) + 1 + (int64_t)Nr * 4 + 4;
+            p->prof_nodes += nn;
+        }
+    }
+    for (int64_t n0 = 0; n0 < nodes && !p->vss_planes; n0 += C) {
         const int64_t nn = std::min<int64_t>(C, nodes - n0);
         cudaError_t e = launch_load_field<T>(N, a + n0 * n3, nullptr, nullptr, nn, Fh, 1, 0, 0, s);
         if (!e) e = launch_dft3<T>(t, Fh, nn, true, s);
@@ -501,10 +537,10 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
         if (desc->max_batch > 0) C = std::min<int64_t>(desc->max_batch, (int64_t)1 << 20);   // the caller's choice
         p->chunk = C;
         if (p->hp.aniso) {
-            // transform batches of about 64 MB of translate spectra and products, which stay in L2
+            // transform batches of about 512 MB of translate spectra and products (enough CTAs per launch)
             const size_t n3 = (size_t)p->hp.N * p->hp.N * p->hp.N;
             const size_t zw = 2 * elem_size(p->prec) * n3 * (2 * (size_t)p->hp.npairs + (p->hp.npairs + 1) / 2);
-            p->vchunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(C, (int64_t)(((size_t)64 << 20) / zw)), 65535));
+            p->vchunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(C, (int64_t)(((size_t)512 << 20) / zw)), 65535));
         }
     }
     workspace_layout(p.get(), p->chunk);
@@ -516,8 +552,9 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
     if (is_tc(p->prec)) tc_bytes = build_tc_tables(p->hp, p->prec, tcblob, p->tc);
     if (p->hp.aniso) {
         std::vector<unsigned char> vblob;
-        if (p->prec == DGFS_PREC_FP64) fill_vss_tables<double>(p->hp, vblob);
-        else fill_vss_tables<float>(p->hp, vblob);
+        p->vss_planes = vss_fused_supported(p->hp.N, p->prec == DGFS_PREC_FP64);
+        if (p->prec == DGFS_PREC_FP64) fill_vss_tables<double>(p->hp, p->vss_planes, vblob);
+        else fill_vss_tables<float>(p->hp, p->vss_planes, vblob);
         cudaError_t ev = cudaMalloc(&p->d_vss, vblob.size());
         if (ev != cudaSuccess) return fail(DGFS_ERR_OOM, std::string("VSS tables: ") + cudaGetErrorString(ev));
         ev = cudaMemcpy(p->d_vss, vblob.data(), vblob.size(), cudaMemcpyHostToDevice);

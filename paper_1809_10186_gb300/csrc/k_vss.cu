@@ -17,8 +17,19 @@
 //   forward DFT
 //   k_vss_accumulate  Y[n][0](k) += scale sum_p A_rp(k) P^_p(k)
 // All four are elementwise streams over N^3 points; the transforms dominate.
+//
+// For N = 8, 16, 32 the transforms are fused with the elementwise steps, with every field stored
+// plane-major ([kz][kx][ky], the z axis outermost) so that a plane of fixed kz is contiguous:
+//   k_vss_planes<INV>   per (node, field, KZ planes): translate spectra formed on load, inverse
+//                       transforms along x and y in shared memory                  -> Z
+//   k_vss_lines         per (node, sphere-point pair, (x, y) line): inverse transform along z,
+//                       the two products, packing, forward transform along z        -> W
+//   k_vss_planes<FWD>   forward transforms along x and y of the packed spectra, in place
+//   k_vss_accumulate    as above (the mirror -k is taken per axis, so any axis order works)
+// which moves a third of the bytes of the separate passes. N = 12, 24 keep the separate passes.
 #include <cstdint>
 
+#include "fourier_dev.cuh"
 #include "launchers.h"
 
 namespace dgfs {
@@ -127,9 +138,229 @@ __global__ void __launch_bounds__(256) k_vss_loss_init(const Cplx<T>* __restrict
     }
 }
 
+// ---- fused plane / line kernels (power-of-two N) ---------------------------------------------
+
+using fdev::bitrev;
+using fdev::fft_line;
+
+template <typename T, int N>
+struct PlaneGeo {
+    static constexpr int KZ = (N * N <= 128) ? N : 128 / N;   // planes per CTA (4 at N = 32, 8 at N = 16)
+    static constexpr int NT = KZ * N;                          // one line per thread per pass
+    static constexpr int P = N + 1;                            // padded row (complex elements)
+    static constexpr size_t smem = (size_t)KZ * N * P * sizeof(Cplx<T>);
+};
+
+// INV: field f = set * npairs + p of node n; planes kz0 .. kz0 + KZ - 1 of the translate spectra
+// (set 0: mu f^ + i conj(mu) g^, set 1: the same with conj(mu) for mu), then inverse transforms
+// along x and y; output Z[n][f] plane-major. !INV: forward transforms (scale 1/N each) along x and y
+// of X[n][f] in place. grid (N / KZ, fields, nodes). The x lines are read straight from global
+// memory (consecutive threads take consecutive ky: coalesced), the y lines go through shared memory.
+template <typename T, int N, bool INV>
+__global__ void __launch_bounds__(PlaneGeo<T, N>::NT)
+    k_vss_planes(const Cplx<T>* __restrict__ Fh, const Cplx<T>* __restrict__ Gh, const Cplx<T>* __restrict__ mu_r,
+                 const Cplx<T>* __restrict__ dftw, int npairs, Cplx<T>* __restrict__ X) {
+    using G = PlaneGeo<T, N>;
+    constexpr int KZ = G::KZ, NT = G::NT, P = G::P;
+    constexpr int64_t n2 = (int64_t)N * N, n3 = n2 * N;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    Cplx<T>* S = reinterpret_cast<Cplx<T>*>(sm_raw);   // [KZ][N][P]
+    __shared__ Cplx<T> tw[N];
+    __shared__ Cplx<T> m[3 * N];
+    const int tid = threadIdx.x, kz0 = blockIdx.x * KZ, f = blockIdx.y, nf = gridDim.y;
+    const int64_t n = blockIdx.z;
+    const int pl = tid / N, ln = tid % N;
+    if (tid < N) tw[tid] = dftw[N + tid];
+    Cplx<T>* Xf = X + (n * nf + f) * n3 + (int64_t)kz0 * n2;
+    Cplx<T> v[N];
+    if constexpr (INV) {
+        const int p = f % npairs;
+        const T sgn = f < npairs ? T(1) : T(-1);   // set 1 takes conj(mu) where set 0 takes mu
+        for (int i = tid; i < 3 * N; i += NT) m[i] = mu_r[(int64_t)p * 3 * N + i];
+        __syncthreads();
+        const Cplx<T>* Fp = Fh + n * n3 + (int64_t)(kz0 + pl) * n2 + ln;
+        const Cplx<T>* Gp = (Gh ? Gh : Fh) + n * n3 + (int64_t)(kz0 + pl) * n2 + ln;
+        const Cplx<T> my = m[N + ln], mz = m[2 * N + kz0 + pl];
+        const Cplx<T> myz{my.x * mz.x - my.y * mz.y, my.x * mz.y + my.y * mz.x};
+#pragma unroll
+        for (int kx = 0; kx < N; ++kx) {
+            const Cplx<T> mx = m[kx];
+            const T a = mx.x * myz.x - mx.y * myz.y, b = sgn * (mx.x * myz.y + mx.y * myz.x);
+            const Cplx<T> fv = Fp[kx * N], gv = Gp[kx * N];
+            v[bitrev<N>(kx)] = Cplx<T>{a * fv.x - b * fv.y - a * gv.y + b * gv.x, a * fv.y + b * fv.x + a * gv.x + b * gv.y};
+        }
+    } else {
+        __syncthreads();
+#pragma unroll
+        for (int x = 0; x < N; ++x) v[bitrev<N>(x)] = Xf[(int64_t)pl * n2 + x * N + ln];
+    }
+    const T sc = INV ? T(1) : T(1) / T(N);
+    // x lines (fixed ky = ln)
+    fft_line<T, N>(v, tw, !INV);
+#pragma unroll
+    for (int k = 0; k < N; ++k) S[(pl * N + k) * P + ln] = Cplx<T>{v[k].x * sc, v[k].y * sc};
+    __syncthreads();
+    // y lines (fixed x = ln)
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[bitrev<N>(k)] = S[(pl * N + ln) * P + k];
+    fft_line<T, N>(v, tw, !INV);
+#pragma unroll
+    for (int k = 0; k < N; ++k) S[(pl * N + ln) * P + k] = Cplx<T>{v[k].x * sc, v[k].y * sc};
+    __syncthreads();
+    for (int e = tid; e < KZ * N * N; e += NT) {
+        const int q = e / (N * N), x = (e / N) % N, y = e % N;
+        Xf[e] = S[(q * N + x) * P + y];
+    }
+}
+
+// z-line (x, y) of node n and sphere-point pair j: inverse transform of the translate lines of
+// points 2j and 2j + 1 (both sets), products, packing P_2j + i P_2j+1, forward transform (1/N).
+// grid (ceil(N^2 / 128), (npairs + 1) / 2, nodes); Z, W plane-major.
+template <typename T, int N>
+__device__ __forceinline__ void vss_line_products(const Cplx<T>* __restrict__ Z, int64_t stride, int sets,
+                                                  int64_t set_stride, const Cplx<T>* tw, T (&P)[N]) {
+    Cplx<T> v[N];
+    for (int s = 0; s < sets; ++s) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[bitrev<N>(k)] = Z[s * set_stride + k * stride];
+        fft_line<T, N>(v, tw, false);
+#pragma unroll
+        for (int k = 0; k < N; ++k) P[k] = fma(v[k].x, v[k].y, P[k]);
+    }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(128) k_vss_lines(const Cplx<T>* __restrict__ Z, const Cplx<T>* __restrict__ dftw,
+                                                   int npairs, int sets, Cplx<T>* __restrict__ W) {
+    constexpr int64_t n2 = (int64_t)N * N, n3 = n2 * N;
+    __shared__ Cplx<T> tw[N];
+    if (threadIdx.x < N) tw[threadIdx.x] = dftw[N + threadIdx.x];
+    __syncthreads();
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n2) return;
+    const int j = blockIdx.y, nw = gridDim.y;
+    const int64_t n = blockIdx.z;
+    const int64_t set_stride = (int64_t)npairs * n3;
+    T P0[N], P1[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) P0[k] = P1[k] = T(0);
+    vss_line_products<T, N>(Z + ((n * sets) * npairs + 2 * j) * n3 + l, n2, sets, set_stride, tw, P0);
+    if (2 * j + 1 < npairs)
+        vss_line_products<T, N>(Z + ((n * sets) * npairs + 2 * j + 1) * n3 + l, n2, sets, set_stride, tw, P1);
+    const T two = sets == 1 ? T(2) : T(1), sc = two / T(N);
+    Cplx<T> v[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[bitrev<N>(k)] = Cplx<T>{P0[k], P1[k]};
+    fft_line<T, N>(v, tw, true);
+    Cplx<T>* w = W + (n * nw + j) * n3 + l;
+#pragma unroll
+    for (int k = 0; k < N; ++k) w[k * n2] = Cplx<T>{v[k].x * sc, v[k].y * sc};
+}
+
+// X[n][z][x][y] = {f[n][x][y][z], 0}: a real field into a plane-major complex field
+template <typename T>
+__global__ void __launch_bounds__(256) k_vss_load_t(const T* __restrict__ f, int N, int64_t n3, Cplx<T>* __restrict__ X) {
+    const int64_t n = blockIdx.y;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // plane-major index
+    if (e >= n3) return;
+    const int64_t n2 = (int64_t)N * N;
+    const int z = (int)(e / n2), x = (int)((e / N) % N), y = (int)(e % N);
+    X[n * n3 + e] = Cplx<T>{f[n * n3 + ((int64_t)x * N + y) * N + z], T(0)};
+}
+
+// out[n][x][y][z] = Re Y0 - a Re Y1 - (c ? c Re Y2 : 0), Y plane-major [n][yfields][z][x][y]
+template <typename T>
+__global__ void __launch_bounds__(256) k_vss_finalize_t(const Cplx<T>* __restrict__ Y, int yfields, const T* __restrict__ a,
+                                                        const T* __restrict__ c, int N, int64_t n3, T* __restrict__ out,
+                                                        int* __restrict__ flags) {
+    const int64_t n = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // standard index
+    if (i >= n3) return;
+    const int64_t n2 = (int64_t)N * N;
+    const int x = (int)(i / n2), y = (int)((i / N) % N), z = (int)(i % N);
+    const int64_t e = ((int64_t)z * N + x) * N + y;
+    const Cplx<T>* Yn = Y + n * yfields * n3;
+    T v = Yn[e].x - a[n * n3 + i] * Yn[n3 + e].x;
+    if (c) v -= c[n * n3 + i] * Yn[2 * n3 + e].x;
+    if (!isfinite(v)) atomicOr(flags, 2);
+    out[n * n3 + i] = v;
+}
+
 inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
 
+template <typename T, int N, bool INV>
+cudaError_t planes_launch(const Cplx<T>* Fh, const Cplx<T>* Gh, const Cplx<T>* mu_r, const Cplx<T>* dftw, int npairs,
+                          int fields, int64_t nodes, Cplx<T>* X, cudaStream_t s) {
+    using G = PlaneGeo<T, N>;
+    auto kern = k_vss_planes<T, N, INV>;
+    if (G::smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<dim3(N / G::KZ, (unsigned)fields, (unsigned)nodes), G::NT, G::smem, s>>>(Fh, Gh, mu_r, dftw, npairs, X);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+bool vss_fused_supported(int N, bool fp64) { return N == 8 || N == 16 || (N == 32 && !fp64); }
+
+template <typename T>
+cudaError_t launch_vss_load_t(const T* f, int N, int64_t nodes, Cplx<T>* X, cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    if (nodes > 65535) return cudaErrorInvalidValue;
+    const int64_t n3 = (int64_t)N * N * N;
+    k_vss_load_t<T><<<dim3(nblk(n3), (unsigned)nodes), 256, 0, s>>>(f, N, n3, X);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_vss_inverse_planes(const Cplx<T>* Fh, const Cplx<T>* Gh, const Cplx<T>* mu_r, const Cplx<T>* dftw,
+                                      int N, int npairs, int sets, int64_t nodes, Cplx<T>* Z, cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    if (nodes > 65535) return cudaErrorInvalidValue;
+    const int fields = sets * npairs;
+    if (N == 8) return planes_launch<T, 8, true>(Fh, Gh, mu_r, dftw, npairs, fields, nodes, Z, s);
+    if (N == 16) return planes_launch<T, 16, true>(Fh, Gh, mu_r, dftw, npairs, fields, nodes, Z, s);
+    if constexpr (sizeof(T) == 4)
+        if (N == 32) return planes_launch<T, 32, true>(Fh, Gh, mu_r, dftw, npairs, fields, nodes, Z, s);
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_vss_lines(const Cplx<T>* Z, const Cplx<T>* dftw, int N, int npairs, int sets, int64_t nodes,
+                             Cplx<T>* W, cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    if (nodes > 65535) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((N * N + 127) / 128), (unsigned)((npairs + 1) / 2), (unsigned)nodes);
+    if (N == 8) k_vss_lines<T, 8><<<grid, 128, 0, s>>>(Z, dftw, npairs, sets, W);
+    else if (N == 16) k_vss_lines<T, 16><<<grid, 128, 0, s>>>(Z, dftw, npairs, sets, W);
+    else if (sizeof(T) == 4 && N == 32) k_vss_lines<T, sizeof(T) == 4 ? 32 : 16><<<grid, 128, 0, s>>>(Z, dftw, npairs, sets, W);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_vss_forward_planes(const Cplx<T>* dftw, int N, int fields, int64_t nodes, Cplx<T>* W,
+                                      cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    if (nodes > 65535) return cudaErrorInvalidValue;
+    if (N == 8) return planes_launch<T, 8, false>(nullptr, nullptr, nullptr, dftw, 0, fields, nodes, W, s);
+    if (N == 16) return planes_launch<T, 16, false>(nullptr, nullptr, nullptr, dftw, 0, fields, nodes, W, s);
+    if constexpr (sizeof(T) == 4)
+        if (N == 32) return planes_launch<T, 32, false>(nullptr, nullptr, nullptr, dftw, 0, fields, nodes, W, s);
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_vss_finalize_t(const Cplx<T>* Y, int yfields, const T* a, const T* c, int N, int64_t nodes, T* out,
+                                  int* flags, cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    if (nodes > 65535) return cudaErrorInvalidValue;
+    const int64_t n3 = (int64_t)N * N * N;
+    k_vss_finalize_t<T><<<dim3(nblk(n3), (unsigned)nodes), 256, 0, s>>>(Y, yfields, a, c, N, n3, out, flags);
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_vss_spectra(const Cplx<T>* Fh, const Cplx<T>* Gh, const Cplx<T>* mu_r, int N, int npairs,
@@ -180,7 +411,16 @@ cudaError_t launch_vss_loss_init(const Cplx<T>* Ah, const Cplx<T>* Bh, const T* 
     template cudaError_t launch_vss_accumulate<T>(const Cplx<T>*, const T*, int, int, int64_t, T, Cplx<T>*, int, \
                                                   cudaStream_t);                                                  \
     template cudaError_t launch_vss_loss_init<T>(const Cplx<T>*, const Cplx<T>*, const T*, int, int64_t,         \
-                                                 Cplx<T>*, int, cudaStream_t);
+                                                 Cplx<T>*, int, cudaStream_t);                                    \
+    template cudaError_t launch_vss_load_t<T>(const T*, int, int64_t, Cplx<T>*, cudaStream_t);                    \
+    template cudaError_t launch_vss_inverse_planes<T>(const Cplx<T>*, const Cplx<T>*, const Cplx<T>*,            \
+                                                      const Cplx<T>*, int, int, int, int64_t, Cplx<T>*,           \
+                                                      cudaStream_t);                                              \
+    template cudaError_t launch_vss_lines<T>(const Cplx<T>*, const Cplx<T>*, int, int, int, int64_t, Cplx<T>*,   \
+                                             cudaStream_t);                                                       \
+    template cudaError_t launch_vss_forward_planes<T>(const Cplx<T>*, int, int, int64_t, Cplx<T>*, cudaStream_t); \
+    template cudaError_t launch_vss_finalize_t<T>(const Cplx<T>*, int, const T*, const T*, int, int64_t, T*,     \
+                                                  int*, cudaStream_t);
 DGFS_VSS_INST(float)
 DGFS_VSS_INST(double)
 #undef DGFS_VSS_INST

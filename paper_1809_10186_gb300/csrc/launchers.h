@@ -123,6 +123,28 @@ template <typename T>
 cudaError_t launch_vss_loss_init(const Cplx<T>* Ah, const Cplx<T>* Bh, const T* GL, int N, int64_t nodes,
                                  Cplx<T>* Y, int yfields, cudaStream_t s);
 
+// Fused path (N = 8, 16 and, in FP32, 32), every field plane-major [kz][kx][ky]:
+bool vss_fused_supported(int N, bool fp64);
+// X[n] = {f[n], 0} transposed to plane-major (then transformed with launch_dft3)
+template <typename T>
+cudaError_t launch_vss_load_t(const T* f, int N, int64_t nodes, Cplx<T>* X, cudaStream_t s);
+// Z[n][set][p] = inverse x, y transforms of the translate spectra of launch_vss_spectra
+template <typename T>
+cudaError_t launch_vss_inverse_planes(const Cplx<T>* Fh, const Cplx<T>* Gh, const Cplx<T>* mu_r, const Cplx<T>* dftw,
+                                      int N, int npairs, int sets, int64_t nodes, Cplx<T>* Z, cudaStream_t s);
+// W[n][j] = forward z transform of P_2j + i P_2j+1 after the inverse z transform of the Z lines
+template <typename T>
+cudaError_t launch_vss_lines(const Cplx<T>* Z, const Cplx<T>* dftw, int N, int npairs, int sets, int64_t nodes,
+                             Cplx<T>* W, cudaStream_t s);
+// forward y, x transforms of W[n][0 .. fields) in place
+template <typename T>
+cudaError_t launch_vss_forward_planes(const Cplx<T>* dftw, int N, int fields, int64_t nodes, Cplx<T>* W,
+                                      cudaStream_t s);
+// out (standard layout) = Re Y0 - a Re Y1 - (c ? c Re Y2 : 0), Y plane-major
+template <typename T>
+cudaError_t launch_vss_finalize_t(const Cplx<T>* Y, int yfields, const T* a, const T* c, int N, int64_t nodes, T* out,
+                                  int* flags, cudaStream_t s);
+
 // ---- DG element collision, SVD variant (k_dg.cu) ---------------------------------------
 // f[e][r] = sum_l A[r][l] F[e][l], g[e][r] = sum_l B[r][l] F[e][l]   (F [E][K][n3], K <= 16)
 template <typename T>

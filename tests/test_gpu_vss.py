@@ -43,7 +43,8 @@ def _err(got, ref, f, g, op):
 
 
 @pytest.mark.parametrize("prec,N,M,Nrho,loss", [("fp64", 8, 12, 8, "paper"), ("fp64", 16, 26, 8, "conservative"),
-                                                ("fp32", 8, 26, 8, "paper"), ("fp32", 16, 12, 16, "paper")])
+                                                ("fp32", 8, 26, 8, "paper"), ("fp32", 16, 12, 16, "paper"),
+                                                ("fp64", 12, 12, 6, "paper"), ("fp32", 12, 6, 6, "conservative")])
 def test_vss_collide_matches_oracle(prec, N, M, Nrho, loss):
     L, gamma, alpha = 3.5, 0.52, 1.6
     F = _as_input(W.rough(3, N, 300 + N), prec)
