@@ -52,6 +52,8 @@ def _args():
     ap.add_argument("--dg", action="store_true",
                     help="measure the DG element collision term (Sec. 3.4, SVD variant) on the 1-D slab "
                          "workload instead of the headline (prints its own line)")
+    ap.add_argument("--vss", action="store_true",
+                    help="VSS kernel (alpha = 1.40, argon) on 256 nodes of N = 32, FP32, instead of the headline")
     ap.add_argument("--rk", type=int, default=0, choices=[0, 2, 3],
                     help="measure SSP-RK2/3 time steps (dgfs_ssprk) of the headline workload instead "
                          "(prints its own line)")
@@ -318,6 +320,64 @@ def run_rk(a):
     return 0
 
 
+def vss_flops_per_node(N, Nrho, npairs):
+    """Radix-2 count of the VSS gain per node: per radial and sphere point one complex 3-D inverse
+    transform (both translates) and half a forward one (two sphere points per transform), plus
+    ~20 flops per point of phases, products, Hermitian separation and accumulation."""
+    return Nrho * npairs * (7.5 * N ** 3 * math.log2(N ** 3) + 20.0 * N ** 3)
+
+
+def run_vss(a):
+    """Q(f, f) for the VSS kernel (eq. B_gen, alpha != 1) on the vss_n32 workload, FP32."""
+    import numpy as np
+    import torch
+    from paper_1809_10186_gb300 import binding, workloads as W
+    torch.cuda.set_device(0)
+    cfg = W.CONFIGS["vss_n32"]
+    N, L, B = cfg["N"], cfg["L"], a.nodes or cfg["B"]
+    F, _ = W.two_maxwellian(B, N, L, cfg["seed"], dtype=np.float32)
+    f = torch.from_numpy(F).cuda()
+    q = torch.empty_like(f)
+    plan = binding.Plan(N=N, L=L, gamma=cfg["gamma"], alpha=cfg["alpha"], M=cfg["M"], N_rho=cfg["Nrho"],
+                        precision="fp32", max_batch=B)
+    npairs = plan.info["n_pairs"]
+    for _ in range(a.warmup):
+        plan.collide(f, out=q)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    plan.profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        plan.collide(f, out=q)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = plan.profile_end()
+    clocks = sampler.stop()
+    plan.stream_status()
+    ms = e0.elapsed_time(e1) / a.steps
+    value = B / (ms / 1e3)
+    flops = vss_flops_per_node(N, cfg["Nrho"], npairs)
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    line = {"metric": "Q(f,f) node-evals/s at N=32 VSS (alpha=1.40, omega=0.81), FP32", "value": value,
+            "unit": "node-evals/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "vss_n32: %d two-Maxwellian nodes, N=32 on [-7,7]^3, N_rho=32, M=38" % B,
+                       "alpha": cfg["alpha"], "N": N, "M": cfg["M"], "N_rho": cfg["Nrho"],
+                       "chunk_nodes": plan.info["chunk_nodes"],
+                       "workspace_gb": round(plan.info["workspace_bytes"] / 2 ** 30, 2),
+                       "l2": "no flush: translate spectra of a transform batch exceed L2"},
+            "roofline": {"bound": "alu", "scope": "whole VSS step (transforms and elementwise kernels)",
+                         "achieved": flops * value / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops * value / 1e12 / peak, "traffic": None, "flops_per_node": flops,
+                         "peak_source": "152 SMs x 128 FP32 FMA lanes x 2 flops x 2070 MHz"},
+            "gpu_launches": prof["launches"], "clocks": clocks}
+    print(json.dumps(line))
+    plan.close()
+    return 0
+
+
 def main():
     a = _args()
     if a.oracle_worker:
@@ -328,6 +388,8 @@ def main():
         return run_dg(a)
     if a.rk:
         return run_rk(a)
+    if a.vss:
+        return run_vss(a)
     import numpy as np
     import torch
     from paper_1809_10186_gb300 import binding, workloads as W
