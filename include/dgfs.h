@@ -181,6 +181,33 @@ dgfs_status dgfs_ragged_collide(dgfs_ragged_t ragged, const void* f, void* Q, vo
 /* Releases the schedule's device arrays (synchronises the device first). NULL is a no-op. */
 dgfs_status dgfs_ragged_destroy(dgfs_ragged_t ragged);
 
+/* ---- 1-D DGFS solver (Sec. 3: eq. eq_weakForm, the upwind flux eq. eq_numericalFlux_upwind,
+   the fully diffuse wall condition of Sec. 3.6, eqs. SSPRK2/SSPRK3) ------------------------------
+   A slab x in [edges[0], edges[I]] of I elements, K Gauss-Lobatto nodes each (nodal DG basis), walls
+   at both ends. F: device [I][K][N^3] (element-major, the plan's element type), node l of element i
+   at x = (edges[i] + edges[i+1])/2 + (edges[i+1] - edges[i])/2 * xi_l. The right-hand side is
+     dF/dt = (2/h_i) M^{-1} (c_1 S F - Fl) + (1/Kn) M^{-1} sum_{l1,l2} H Q(F_l1, F_l2)
+   with S[m][l] = int phi_l phi_m' and M, H on [-1, 1], the upwind flux Fl (interior value where
+   c_1 n >= 0, neighbour or wall value otherwise) and, at a wall with velocity u_w (u_w,x = 0) and
+   temperature T_w, the incoming value n_w exp(-|c - u_w|^2 / T_w), n_w balancing the outgoing
+   mass flux of the wall node. The collision term is the DG element term of dgfs_dg_collide (the
+   SVD variant at svd_tol) with the plan's kernel (VHS or VSS). Kn = +infinity: collisionless.
+   wall_left, wall_right: host arrays {u_x, u_y, u_z, T_w} in the units of the velocity grid.
+   dgfs_slab_create and dgfs_slab_set_walls synchronise the device; the other calls are
+   stream-ordered. A slab must not be used concurrently on several streams, nor its plan. */
+typedef struct dgfs_slab_s* dgfs_slab_t;
+dgfs_status dgfs_slab_create(dgfs_plan_t plan, int K, int I, const double* edges, double Kn,
+                             const double* wall_left, const double* wall_right, double svd_tol,
+                             dgfs_slab_t* out);
+dgfs_status dgfs_slab_set_walls(dgfs_slab_t slab, const double* wall_left, const double* wall_right);
+/* dFdt = the right-hand side at F (both device [I][K][N^3], distinct). */
+dgfs_status dgfs_slab_rhs(dgfs_slab_t slab, const void* F, void* dFdt, void* stream);
+/* nsteps SSP-RK steps (order 2 or 3) of size dt, in place on F. */
+dgfs_status dgfs_slab_ssprk(dgfs_slab_t slab, int order, void* F, double dt, int nsteps, void* stream);
+dgfs_status dgfs_slab_destroy(dgfs_slab_t slab);
+/* Host: S [K][K] (eq. eq_stiffMatrix1 on [-1, 1]) and the inverse mass matrix [K][K]; either NULL. */
+dgfs_status dgfs_host_dg_stiffness(int K, double* S, double* Minv);
+
 /* dgfs_collide with HOST buffers: copies f to the device, computes, copies Q back and
    synchronises before returning. f_host/Q_host may be pageable or pinned (pinned lets the
    copies overlap the compute). The batch is split into at least four sub-batches that fit the

@@ -86,6 +86,14 @@ _SIGNATURES = {
     "dgfs_dg_destroy": [_P],
     "dgfs_host_dg_tensor": [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_double)],
+    "dgfs_slab_create": [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                         ctypes.POINTER(_P)],
+    "dgfs_slab_set_walls": [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "dgfs_slab_rhs": [_P, _P, _P, _P],
+    "dgfs_slab_ssprk": [_P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_int, _P],
+    "dgfs_slab_destroy": [_P],
+    "dgfs_host_dg_stiffness": [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "dgfs_host_vss_tables": [ctypes.POINTER(dgfs_plan_desc), ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double)],
     "dgfs_host_vss_factor": [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -421,6 +429,61 @@ class DGElement:
     def close(self):
         if getattr(self, "handle", None):
             lib().dgfs_dg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def host_dg_stiffness(K):
+    """(S, M^-1) of the K-node Gauss-Lobatto basis on [-1, 1] (S[m][l] = int phi_l phi_m')."""
+    import numpy as np
+    S, Mi = np.zeros((K, K)), np.zeros((K, K))
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    check(lib().dgfs_host_dg_stiffness(int(K), dp(S), dp(Mi)), "dgfs_host_dg_stiffness")
+    return S, Mi
+
+
+class Slab:
+    """The 1-D DGFS solver (dgfs_slab_*): I elements of K nodes between two diffuse walls.
+    F: CUDA tensor [I, K, N, N, N] of the plan's dtype. walls: (u_x, u_y, u_z, T_w), u_x = 0."""
+
+    def __init__(self, plan, K, edges, Kn, wall_left, wall_right, svd_tol=0.0):
+        import numpy as np
+        edges = np.ascontiguousarray(edges, dtype=np.float64)
+        self.K, self.I, self.plan = int(K), len(edges) - 1, plan   # the plan must outlive the slab
+        wl, wr = (np.ascontiguousarray(w, dtype=np.float64) for w in (wall_left, wall_right))
+        dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        h = ctypes.c_void_p()
+        check(lib().dgfs_slab_create(plan.handle, self.K, self.I, dp(edges), float(Kn), dp(wl), dp(wr),
+                                     float(svd_tol), ctypes.byref(h)), "dgfs_slab_create")
+        self.handle = h
+
+    def set_walls(self, wall_left, wall_right):
+        import numpy as np
+        wl, wr = (np.ascontiguousarray(w, dtype=np.float64) for w in (wall_left, wall_right))
+        dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        check(lib().dgfs_slab_set_walls(self.handle, dp(wl), dp(wr)), "dgfs_slab_set_walls")
+
+    def rhs(self, F, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(F)
+        check(lib().dgfs_slab_rhs(self.handle, ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                  _stream_ptr(stream)), "dgfs_slab_rhs")
+        return out
+
+    def ssprk(self, F, dt, steps, order=2, stream=None):
+        check(lib().dgfs_slab_ssprk(self.handle, int(order), ctypes.c_void_p(F.data_ptr()), float(dt), int(steps),
+                                    _stream_ptr(stream)), "dgfs_slab_ssprk")
+        return F
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().dgfs_slab_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

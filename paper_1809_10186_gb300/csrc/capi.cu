@@ -1116,6 +1116,227 @@ dgfs_status dgfs_host_dg_tensor(int K, double* nodes, double* M, double* H) {
     return DGFS_OK;
 }
 
+}  // extern "C"
+
+// ---- 1-D DGFS solver: DG transport, diffuse walls, element collision, SSP-RK (Sec. 3) ----------
+
+constexpr uint64_t kSlabMagic = 0x4447465353424c53ull;   // "DGFSSLBS"
+
+struct dgfs_slab_s {
+    uint64_t magic = kSlabMagic;
+    dgfs_plan_s* plan = nullptr;
+    dgfs_dg_s* dg = nullptr;   // the element collision term (nullptr: collisionless, Kn = inf)
+    int K = 0, I = 0, device = 0;
+    double invKn = 0.0;
+    SlabMatrices mats{};
+    void* d_mem = nullptr;     // fw [2][N^3] | num [2] | 2/h [I] | C | stage | q ([I][K][N^3] each)
+    size_t off_fw = 0, off_num = 0, off_h = 0, off_C = 0, off_stage = 0, off_q = 0;
+};
+
+namespace {
+
+bool check_slab(dgfs_slab_t s) { return s && s->magic == kSlabMagic; }
+
+// Wall Maxwellians f_w = exp(-|c - u_w|^2 / T_w) in the compute type and the FP64 denominators
+// sum over the incoming velocities of |c_1| f_w (left wall: c_1 > 0, right wall: c_1 < 0).
+dgfs_status slab_walls(dgfs_slab_s* sl, const double* wl, const double* wr) {
+    if (!wl || !wr) return fail(DGFS_ERR_INVALID_ARG, "NULL wall state");
+    const double* w[2] = {wl, wr};
+    for (int k = 0; k < 2; ++k) {
+        for (int a = 0; a < 4; ++a)
+            if (!std::isfinite(w[k][a])) return fail(DGFS_ERR_INVALID_ARG, "non-finite wall state");
+        if (w[k][0] != 0.0) return fail(DGFS_ERR_INVALID_ARG, "walls move parallel to themselves: u_x must be 0");
+        if (!(w[k][3] > 0.0)) return fail(DGFS_ERR_INVALID_ARG, "wall temperature must be positive");
+    }
+    const HostPlan& h = sl->plan->hp;
+    const int N = h.N;
+    const size_t n3 = (size_t)N * N * N, es = elem_size(sl->plan->prec);
+    const double dc = 2.0 * h.L / N;
+    std::vector<unsigned char> blob(2 * n3 * es);
+    for (int k = 0; k < 2; ++k) {
+        double den = 0.0;
+        for (size_t j = 0; j < n3; ++j) {
+            const double c[3] = {-h.L + ((double)(j / ((size_t)N * N)) + 0.5) * dc,
+                                 -h.L + ((double)((j / N) % N) + 0.5) * dc, -h.L + ((double)(j % N) + 0.5) * dc};
+            const double d2 = (c[0] - w[k][0]) * (c[0] - w[k][0]) + (c[1] - w[k][1]) * (c[1] - w[k][1]) +
+                              (c[2] - w[k][2]) * (c[2] - w[k][2]);
+            const double fw = std::exp(-d2 / w[k][3]);
+            if (k == 0 ? c[0] > 0.0 : c[0] < 0.0) den += std::fabs(c[0]) * fw;
+            if (es == 8) reinterpret_cast<double*>(blob.data())[k * n3 + j] = fw;
+            else reinterpret_cast<float*>(blob.data())[k * n3 + j] = (float)fw;
+        }
+        if (!(den > 0.0)) return fail(DGFS_ERR_INVALID_ARG, "wall Maxwellian vanishes on the velocity grid");
+        sl->mats.den[k] = den;
+    }
+    DGFS_CUDA(cudaSetDevice(sl->device), "cudaSetDevice");
+    DGFS_CUDA(cudaDeviceSynchronize(), "synchronise before the wall update");
+    DGFS_CUDA(cudaMemcpy(static_cast<unsigned char*>(sl->d_mem) + sl->off_fw, blob.data(), blob.size(),
+                         cudaMemcpyHostToDevice), "wall tables upload");
+    return DGFS_OK;
+}
+
+template <typename T>
+dgfs_status slab_rhs(dgfs_slab_s* sl, const T* F, T* out, cudaStream_t s) {
+    dgfs_plan_s* p = sl->plan;
+    unsigned char* base = static_cast<unsigned char*>(sl->d_mem);
+    T* C = reinterpret_cast<T*>(base + sl->off_C);
+    if (sl->dg) {
+        const dgfs_status st = dg_run<T>(sl->dg, F, C, sl->I, s);
+        if (st != DGFS_OK) return st;
+    }
+    double* num = reinterpret_cast<double*>(base + sl->off_num);
+    cudaError_t e = launch_slab_wall<T>(F, p->hp.N, sl->I, sl->K, p->hp.L, num, s);
+    if (!e) e = launch_slab_rhs<T>(F, sl->dg ? C : nullptr, reinterpret_cast<const T*>(base + sl->off_fw), num,
+                                   sl->mats, reinterpret_cast<const double*>(base + sl->off_h), sl->invKn, p->hp.N,
+                                   sl->I, p->hp.L, out, s);
+    if (e) return cuda_fail(e, "slab transport");
+    if (p->prof) p->prof_launches += 2;
+    return DGFS_OK;
+}
+
+// SSP-RK2 / RK3 (eqs. SSPRK2, SSPRK3) of dF/dt = rhs(F), in place, stages in the slab's buffers
+template <typename T>
+dgfs_status slab_ssprk(dgfs_slab_s* sl, int order, T* F, double dt, int nsteps, cudaStream_t s) {
+    unsigned char* base = static_cast<unsigned char*>(sl->d_mem);
+    T* stage = reinterpret_cast<T*>(base + sl->off_stage);
+    T* q = reinterpret_cast<T*>(base + sl->off_q);
+    const int64_t n = (int64_t)sl->I * sl->K * sl->plan->hp.N * sl->plan->hp.N * sl->plan->hp.N;
+    int* flags = sl->plan->d_flags;
+    for (int it = 0; it < nsteps; ++it) {
+        dgfs_status st = slab_rhs<T>(sl, F, q, s);
+        if (st != DGFS_OK) return st;
+        cudaError_t e = launch_rk_combine<T>(n, 1.0, F, 0.0, nullptr, dt, q, stage, flags, s);
+        if (e) return cuda_fail(e, "slab SSP-RK stage");
+        st = slab_rhs<T>(sl, stage, q, s);
+        if (st != DGFS_OK) return st;
+        if (order == 2) {
+            e = launch_rk_combine<T>(n, 0.5, F, 0.5, stage, 0.5 * dt, q, F, flags, s);
+        } else {
+            e = launch_rk_combine<T>(n, 0.75, F, 0.25, stage, 0.25 * dt, q, stage, flags, s);
+            if (!e) {
+                st = slab_rhs<T>(sl, stage, q, s);
+                if (st != DGFS_OK) return st;
+                e = launch_rk_combine<T>(n, 1.0 / 3.0, F, 2.0 / 3.0, stage, 2.0 / 3.0 * dt, q, F, flags, s);
+            }
+        }
+        if (e) return cuda_fail(e, "slab SSP-RK stage");
+        if (sl->plan->prof) sl->plan->prof_launches += order;
+    }
+    return DGFS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dgfs_status dgfs_slab_create(dgfs_plan_t plan, int K, int I, const double* edges, double Kn, const double* wall_left,
+                             const double* wall_right, double svd_tol, dgfs_slab_t* out) {
+    if (!out) return fail(DGFS_ERR_INVALID_ARG, "NULL output");
+    *out = nullptr;
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    if (K < 2 || K > 8) return fail(DGFS_ERR_INVALID_ARG, "K must be in [2, 8]");
+    if (I < 1 || I > 65535) return fail(DGFS_ERR_INVALID_ARG, "I must be in [1, 65535]");
+    if (!edges) return fail(DGFS_ERR_INVALID_ARG, "NULL edges");
+    for (int i = 0; i < I; ++i)
+        if (!std::isfinite(edges[i]) || !std::isfinite(edges[i + 1]) || !(edges[i + 1] > edges[i]))
+            return fail(DGFS_ERR_INVALID_ARG, "edges must be finite and strictly increasing");
+    if (!(Kn > 0.0)) return fail(DGFS_ERR_INVALID_ARG, "Kn must be positive (infinity: collisionless)");
+    std::unique_ptr<dgfs_slab_s> sl(new (std::nothrow) dgfs_slab_s);
+    if (!sl) return fail(DGFS_ERR_OOM, "host allocation failed");
+    sl->plan = plan;
+    sl->K = K;
+    sl->I = I;
+    sl->device = plan->device;
+    sl->invKn = std::isfinite(Kn) ? 1.0 / Kn : 0.0;
+    sl->mats.K = K;
+    std::vector<double> S, Minv, nodes, M, H;
+    if (!dg_stiffness_1d(K, S, Minv) || !dg_tensor_1d(K, nodes, M, H)) return fail(DGFS_ERR_INVALID_ARG, "bad K");
+    std::copy(S.begin(), S.end(), sl->mats.S);
+    std::copy(Minv.begin(), Minv.end(), sl->mats.Minv);
+    const size_t es = elem_size(plan->prec);
+    const size_t n3 = (size_t)plan->hp.N * plan->hp.N * plan->hp.N;
+    size_t off = 0;
+    auto take = [&](size_t b) { const size_t o = off; off = align_up(off + b, 256); return o; };
+    sl->off_fw = take(2 * n3 * es);
+    sl->off_num = take(2 * sizeof(double));
+    sl->off_h = take((size_t)I * sizeof(double));
+    sl->off_C = take((size_t)I * K * n3 * es);
+    sl->off_stage = take((size_t)I * K * n3 * es);
+    sl->off_q = take((size_t)I * K * n3 * es);
+    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    cudaError_t e = cudaMalloc(&sl->d_mem, off);
+    if (e != cudaSuccess) return fail(DGFS_ERR_OOM, std::string("slab workspace: ") + cudaGetErrorString(e));
+    std::vector<double> h2(I);
+    for (int i = 0; i < I; ++i) h2[i] = 2.0 / (edges[i + 1] - edges[i]);
+    e = cudaMemcpy(static_cast<unsigned char*>(sl->d_mem) + sl->off_h, h2.data(), I * sizeof(double),
+                   cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(sl->d_mem);
+        return cuda_fail(e, "slab upload");
+    }
+    dgfs_status st = slab_walls(sl.get(), wall_left, wall_right);
+    if (st == DGFS_OK && std::isfinite(Kn)) st = dgfs_dg_create(plan, K, H.data(), svd_tol, I, &sl->dg);
+    if (st != DGFS_OK) {
+        cudaFree(sl->d_mem);
+        return st;
+    }
+    *out = sl.release();
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_slab_set_walls(dgfs_slab_t slab, const double* wall_left, const double* wall_right) {
+    if (!check_slab(slab)) return fail(DGFS_ERR_STATE, "invalid or destroyed slab");
+    return slab_walls(slab, wall_left, wall_right);
+}
+
+dgfs_status dgfs_slab_rhs(dgfs_slab_t slab, const void* F, void* dFdt, void* stream) {
+    if (!check_slab(slab)) return fail(DGFS_ERR_STATE, "invalid or destroyed slab");
+    if (!F || !dFdt) return fail(DGFS_ERR_INVALID_ARG, "NULL field pointer");
+    if (!aligned16(F) || !aligned16(dFdt)) return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
+    if (F == dFdt) return fail(DGFS_ERR_INVALID_ARG, "output aliases the input");
+    DGFS_CUDA(cudaSetDevice(slab->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return slab->plan->prec == DGFS_PREC_FP64
+               ? slab_rhs<double>(slab, static_cast<const double*>(F), static_cast<double*>(dFdt), s)
+               : slab_rhs<float>(slab, static_cast<const float*>(F), static_cast<float*>(dFdt), s);
+}
+
+dgfs_status dgfs_slab_ssprk(dgfs_slab_t slab, int order, void* F, double dt, int nsteps, void* stream) {
+    if (!check_slab(slab)) return fail(DGFS_ERR_STATE, "invalid or destroyed slab");
+    if (order != 2 && order != 3) return fail(DGFS_ERR_INVALID_ARG, "order must be 2 or 3");
+    if (nsteps < 0 || !std::isfinite(dt)) return fail(DGFS_ERR_INVALID_ARG, "nsteps >= 0 and finite dt required");
+    if (nsteps == 0) return DGFS_OK;
+    if (!F) return fail(DGFS_ERR_INVALID_ARG, "NULL field pointer");
+    if (!aligned16(F)) return fail(DGFS_ERR_INVALID_ARG, "field pointer must be 16-byte aligned");
+    DGFS_CUDA(cudaSetDevice(slab->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return slab->plan->prec == DGFS_PREC_FP64 ? slab_ssprk<double>(slab, order, static_cast<double*>(F), dt, nsteps, s)
+                                              : slab_ssprk<float>(slab, order, static_cast<float*>(F), dt, nsteps, s);
+}
+
+dgfs_status dgfs_slab_destroy(dgfs_slab_t slab) {
+    if (!slab) return DGFS_OK;
+    if (!check_slab(slab)) return fail(DGFS_ERR_STATE, "invalid or destroyed slab");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(slab->device);
+    cudaDeviceSynchronize();
+    if (slab->dg) dgfs_dg_destroy(slab->dg);
+    cudaFree(slab->d_mem);
+    cudaSetDevice(cur);
+    slab->magic = 0;
+    delete slab;
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_host_dg_stiffness(int K, double* S, double* Minv) {
+    std::vector<double> s, mi;
+    if (!dg_stiffness_1d(K, s, mi)) return fail(DGFS_ERR_INVALID_ARG, "K must be in [2, 16]");
+    if (S) std::memcpy(S, s.data(), s.size() * sizeof(double));
+    if (Minv) std::memcpy(Minv, mi.data(), mi.size() * sizeof(double));
+    return DGFS_OK;
+}
+
 dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host, int64_t B,
                               void* stream) {
     if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");

@@ -155,6 +155,21 @@ template <typename T>
 cudaError_t launch_dg_accumulate(const T* Q, const int* rs, int K, int R, int64_t n3, int64_t E, T* C,
                                  cudaStream_t s);
 
+// ---- 1-D DGFS transport (k_slab.cu) ------------------------------------------------------
+struct SlabMatrices {
+    int K;                 // nodes per element, 2..8
+    double S[64];          // [K][K] stiffness S[m][l] = int phi_l phi_m' (reference element)
+    double Minv[64];       // [K][K] inverse reference mass matrix
+    double den[2];         // wall denominators: sum over incoming c of |c_1| f_w (left, right)
+};
+// num[0], num[1] = sum over outgoing c of |c_1| f at the left / right wall node (FP64)
+template <typename T>
+cudaError_t launch_slab_wall(const T* F, int N, int I, int K, double L, double* num, cudaStream_t s);
+// out = (2/h_i) M^{-1} (c_1 S F - Fl) + invKn M^{-1} C (C may be nullptr); fw [2][N^3] wall Maxwellians
+template <typename T>
+cudaError_t launch_slab_rhs(const T* F, const T* C, const T* fw, const double* num, const SlabMatrices& mats,
+                            const double* hinv2, double invKn, int N, int I, double L, T* out, cudaStream_t s);
+
 // ---- time stepping and moments (k_time.cu) --------------------------------------------
 // out = a u + b v + c q over n values (v may be nullptr); non-finite results raise flag bit 1
 template <typename T>

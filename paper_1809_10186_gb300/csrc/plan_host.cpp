@@ -326,6 +326,59 @@ bool dg_tensor_1d(int K, std::vector<double>& nodes, std::vector<double>& M, std
     return true;
 }
 
+bool dg_stiffness_1d(int K, std::vector<double>& S, std::vector<double>& Minv) {
+    std::vector<double> nodes, M, H;
+    if (!dg_tensor_1d(K, nodes, M, H)) return false;
+    // S[m][l] = int phi_l phi_m' on the reference element, phi_m' by the product rule of the
+    // Lagrange formula; Gauss-Legendre with K points is exact for the degree 2K - 3 integrand
+    std::vector<double> xq, wq;
+    gauss_legendre(K, -1.0, 1.0, xq, wq);
+    S.assign((size_t)K * K, 0.0);
+    for (int q = 0; q < K; ++q) {
+        std::vector<double> phi(K, 1.0), dphi(K, 0.0);
+        for (int l = 0; l < K; ++l)
+            for (int j = 0; j < K; ++j)
+                if (j != l) phi[l] *= (xq[q] - nodes[j]) / (nodes[l] - nodes[j]);
+        for (int m = 0; m < K; ++m)
+            for (int j = 0; j < K; ++j) {
+                if (j == m) continue;
+                double t = 1.0 / (nodes[m] - nodes[j]);
+                for (int k = 0; k < K; ++k)
+                    if (k != m && k != j) t *= (xq[q] - nodes[k]) / (nodes[m] - nodes[k]);
+                dphi[m] += t;
+            }
+        for (int m = 0; m < K; ++m)
+            for (int l = 0; l < K; ++l) S[(size_t)m * K + l] += wq[q] * phi[l] * dphi[m];
+    }
+    // M^{-1} by Gauss-Jordan elimination with partial pivoting (M is symmetric positive definite)
+    std::vector<double> A = M;
+    Minv.assign((size_t)K * K, 0.0);
+    for (int i = 0; i < K; ++i) Minv[(size_t)i * K + i] = 1.0;
+    for (int c = 0; c < K; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < K; ++r)
+            if (std::fabs(A[(size_t)r * K + c]) > std::fabs(A[(size_t)piv * K + c])) piv = r;
+        for (int k = 0; k < K; ++k) {
+            std::swap(A[(size_t)c * K + k], A[(size_t)piv * K + k]);
+            std::swap(Minv[(size_t)c * K + k], Minv[(size_t)piv * K + k]);
+        }
+        const double d = A[(size_t)c * K + c];
+        for (int k = 0; k < K; ++k) {
+            A[(size_t)c * K + k] /= d;
+            Minv[(size_t)c * K + k] /= d;
+        }
+        for (int r = 0; r < K; ++r) {
+            if (r == c) continue;
+            const double f = A[(size_t)r * K + c];
+            for (int k = 0; k < K; ++k) {
+                A[(size_t)r * K + k] -= f * A[(size_t)c * K + k];
+                Minv[(size_t)r * K + k] -= f * Minv[(size_t)c * K + k];
+            }
+        }
+    }
+    return true;
+}
+
 // ---- VSS kernel factor (alpha != 1) ---------------------------------------------------------
 //
 // With B = b c_r^gamma (1 + cos chi)^beta, beta = alpha - 1 (eq. B_gen), the factor of eq. realGG,

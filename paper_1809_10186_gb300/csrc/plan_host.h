@@ -59,6 +59,10 @@ void svd_small(int m, int n, const std::vector<double>& A, std::vector<double>& 
 // outside [2, 16].
 bool dg_tensor_1d(int K, std::vector<double>& nodes, std::vector<double>& M, std::vector<double>& H);
 
+// Stiffness matrix S[m][l] = int phi_l dphi_m/dxi (eq. eq_stiffMatrix1 on [-1, 1]) and the inverse
+// mass matrix of the same basis. False for K outside [2, 16].
+bool dg_stiffness_1d(int K, std::vector<double>& S, std::vector<double>& Minv);
+
 double default_b(double gamma);
 double default_b_vss(double gamma, double alpha);
 double default_R(double L);

@@ -164,3 +164,14 @@ def test_vss_descriptors_rejected(lib):
     _, _, _, _, b = binding.host_quadrature(N=8, L=4.0, M=12, gamma=0.5, alpha=1.5)
     from oracle import vss as V
     assert b == pytest.approx(V.b_vss(0.75, 1.5), rel=1e-14)
+
+
+@pytest.mark.parametrize("K", [2, 3, 4, 6])
+def test_dg_stiffness_matches_oracle(lib, K):
+    from oracle import slab as SL
+    from oracle.dg import dg_tensors
+    S, Minv = binding.host_dg_stiffness(K)
+    np.testing.assert_allclose(S, SL.stiffness(K), atol=1e-13)
+    np.testing.assert_allclose(Minv, np.linalg.inv(dg_tensors(K)[1]), rtol=1e-11, atol=1e-11)
+    with pytest.raises(binding.DGFSError):
+        binding.host_dg_stiffness(1)
