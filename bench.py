@@ -54,6 +54,10 @@ def _args():
                          "workload instead of the headline (prints its own line)")
     ap.add_argument("--vss", action="store_true",
                     help="VSS kernel (alpha = 1.40, argon) on 256 nodes of N = 32, FP32, instead of the headline")
+    ap.add_argument("--slab", action="store_true",
+                    help="1-D DGFS Fourier heat transfer (10 elements x 3 nodes, N = 24) SSP-RK2 steps")
+    ap.add_argument("--slab-profile", type=int, default=0,
+                    help="with --slab: run this many more steps and report the temperature profile")
     ap.add_argument("--rk", type=int, default=0, choices=[0, 2, 3],
                     help="measure SSP-RK2/3 time steps (dgfs_ssprk) of the headline workload instead "
                          "(prints its own line)")
@@ -378,6 +382,60 @@ def run_vss(a):
     return 0
 
 
+def run_slab(a):
+    """SSP-RK2 steps of the 1-D DGFS solver on the Fourier heat-transfer setup: every step is two
+    right-hand sides, each the DG element collision term of the 10 elements (90 bilinear Q at N = 24)
+    plus the transport kernels, and the stage combinations."""
+    import numpy as np
+    import torch
+    from paper_1809_10186_gb300 import binding, workloads as W
+    torch.cuda.set_device(0)
+    cfg = W.CONFIGS["fourier_slab"]
+    N, L, K, I = cfg["N"], cfg["L"], cfg["K"], cfg["I"]
+    edges = np.linspace(0.0, 1.0, I + 1)
+    plan = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=cfg["M"], N_rho=cfg["Nrho"], precision=cfg["prec"],
+                        max_batch=I * K * K)
+    slab = binding.Slab(plan, K, edges, cfg["Kn"], (0, 0, 0, cfg["T_left"]), (0, 0, 0, cfg["T_right"]))
+    c = W.velocity_grid(N, L)
+    cx, cy, cz = np.meshgrid(c, c, c, indexing="ij")
+    f0 = (np.pi ** -1.5 * np.exp(-(cx ** 2 + cy ** 2 + cz ** 2))).astype(np.float32)
+    F = torch.from_numpy(np.broadcast_to(f0, (I, K, N, N, N)).copy()).cuda()
+    slab.ssprk(F, cfg["dt"], a.warmup)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    plan.profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    slab.ssprk(F, cfg["dt"], a.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = plan.profile_end()
+    clocks = sampler.stop()
+    plan.stream_status()
+    ms = e0.elapsed_time(e1) / a.steps
+    line = {"metric": "1-D DGFS SSP-RK2 steps/s, Fourier heat transfer (10 elements x 3 nodes, N=24, M=12)",
+            "value": 1e3 / ms, "unit": "steps/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "phase_space_updates_per_s": I * K * N ** 3 / (ms / 1e3),
+            "config": {"workload": "fourier_slab: walls %.4f / %.4f, Kn %.4f, dt %g" % (
+                cfg["T_left"], cfg["T_right"], cfg["Kn"], cfg["dt"]), "I": I, "K": K, "N": N, "M": cfg["M"]},
+            "gpu_launches": prof["launches"], "clocks": clocks}
+    if a.slab_profile:
+        slab.ssprk(F, cfg["dt"], a.slab_profile)
+        mom = plan.moments(F.reshape(I * K, N, N, N)).cpu().numpy()
+        xs = (0.5 * (edges[:-1, None] + edges[1:, None]) + 0.5 * np.diff(edges)[:, None]
+              * np.array([-1.0, 0.0, 1.0])[None, :]).ravel()
+        line["temperature_profile"] = {"t": cfg["dt"] * (a.warmup + a.steps + a.slab_profile),
+                                       "x": [round(float(x), 4) for x in xs],
+                                       "T_kelvin": [round(float(t) * 273.0, 2) for t in mom[:, 4]],
+                                       "n": [round(float(v), 5) for v in mom[:, 0]]}
+    print(json.dumps(line))
+    slab.close()
+    plan.close()
+    return 0
+
+
 def main():
     a = _args()
     if a.oracle_worker:
@@ -390,6 +448,8 @@ def main():
         return run_rk(a)
     if a.vss:
         return run_vss(a)
+    if a.slab:
+        return run_slab(a)
     import numpy as np
     import torch
     from paper_1809_10186_gb300 import binding, workloads as W

@@ -125,6 +125,11 @@ CONFIGS = {
     # differentiation: 512 nodes, N = 32, omega = 0.81, FP32
     "grad_n32": dict(N=32, L=7.0, Nrho=32, M=38, gamma=omega_to_gamma(0.81), B=512,
                      prec="fp32", seed=SEED_BASE + 5),
+    # 1-D Fourier heat transfer (Sec. 4.4 setup): argon, Maxwell molecules (omega = 1), walls at
+    # 263 K and 283 K (T_ref = 273 K) at rest, Kn (Cercignani) = 1.582, i.e. Kn (eq. Kn) = 1.582 * 2 / pi;
+    # 10 elements of K = 3 Gauss-Lobatto nodes, N = 24 on [-5.09, 5.09]^3, M = 12 (6 on the half sphere)
+    "fourier_slab": dict(N=24, L=5.09, Nrho=24, M=12, gamma=0.0, K=3, I=10, Kn=1.582 * 2.0 / math.pi,
+                         T_left=263.0 / 273.0, T_right=283.0 / 273.0, dt=0.002, prec="fp32"),
     # VSS kernel (eq. B_gen, alpha != 1): argon's VSS parameters omega = 0.81, alpha = 1.40,
     # 256 nodes, N = 32, M = 38, FP32 (one transform per radial and sphere point)
     "vss_n32": dict(N=32, L=7.0, Nrho=32, M=38, gamma=omega_to_gamma(0.81), alpha=1.40, B=256,
