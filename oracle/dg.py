@@ -92,3 +92,23 @@ def element_collision_svd(plan, H: np.ndarray, F: np.ndarray, svd_tol: float = 0
             gr = np.tensordot(Vs[m][r], F, axes=1)
             C[m] += fast_Q(plan, fr, gr)
     return C
+
+
+def element_collision_sym(plan, H: np.ndarray, F: np.ndarray, svd_tol: float = 0.0) -> np.ndarray:
+    """Eq. eq_coln_derivation_SVD_4 for symmetric slices H[m] (the nodal basis gives them): the
+    eigen-decomposition H[m] = sum_r lambda_r u_r u_r^T is an SVD with singular values |lambda_r|
+    and V[r] = sign(lambda_r) |lambda_r| u_r^T, and Q is bilinear, so
+    C[m] = sum_r sign(lambda_r) Q(f_r, f_r),  f_r = sqrt|lambda_r| sum_l u_r[l] F_l,
+    truncated like the SVD (|lambda_r| above svd_tol times the largest)."""
+    F = np.asarray(F, dtype=np.float64)
+    C = np.zeros_like(F)
+    for m in range(H.shape[0]):
+        lam, U = np.linalg.eigh(H[m])
+        top = np.abs(lam).max()
+        for r in range(len(lam)):
+            if abs(lam[r]) <= (svd_tol * top if svd_tol > 0 else 1e-14 * top):
+                continue
+            fr = np.sqrt(abs(lam[r])) * np.tensordot(U[:, r], F, axes=1)
+            C[m] += np.sign(lam[r]) * fast_Q(plan, fr)
+    return C
+

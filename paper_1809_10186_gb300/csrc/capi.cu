@@ -10,6 +10,7 @@
 //   5. one inverse DFT and the finalisation    Q = Re - f Im
 // on the caller's stream; nothing is allocated after dgfs_plan_create. Plans of the VSS kernel
 // (alpha != 1) take the per-sphere-point path of k_vss.cu instead (vss_chunk below).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -957,9 +958,10 @@ struct dgfs_dg_s {
     dgfs_plan_s* plan = nullptr;
     int K = 0, R = 0, device = 0;
     int64_t emax = 0;
+    bool sym = false;        // every H[m] symmetric: terms s_r Q(f_r, f_r) (see k_dg.cu)
     std::vector<int> ranks;
-    void* d_mem = nullptr;   // A [R][K] | B [R][K] | rs [K + 1] | f | g | Q ([emax][R][N^3] each)
-    size_t off_A = 0, off_B = 0, off_rs = 0, off_f = 0, off_g = 0, off_Q = 0;
+    void* d_mem = nullptr;   // A [R][K] | B [R][K] | sgn [R] | rs [K + 1] | f | g | Q ([emax][R][N^3] each)
+    size_t off_A = 0, off_B = 0, off_sgn = 0, off_rs = 0, off_f = 0, off_g = 0, off_Q = 0;
 };
 
 namespace {
@@ -972,7 +974,8 @@ dgfs_status dg_run(dgfs_dg_s* d, const T* F, T* C, int64_t E, cudaStream_t s) {
     const int64_t n3 = (int64_t)p->hp.N * p->hp.N * p->hp.N;
     unsigned char* base = static_cast<unsigned char*>(d->d_mem);
     const T* A = reinterpret_cast<const T*>(base + d->off_A);
-    const T* B = reinterpret_cast<const T*>(base + d->off_B);
+    const T* B = d->sym ? nullptr : reinterpret_cast<const T*>(base + d->off_B);
+    const T* sgn = d->sym ? reinterpret_cast<const T*>(base + d->off_sgn) : nullptr;
     const int* rs = reinterpret_cast<const int*>(base + d->off_rs);
     T* f = reinterpret_cast<T*>(base + d->off_f);
     T* g = reinterpret_cast<T*>(base + d->off_g);
@@ -984,10 +987,11 @@ dgfs_status dg_run(dgfs_dg_s* d, const T* F, T* C, int64_t E, cudaStream_t s) {
         if (d->R > 0) {
             cudaError_t e = launch_dg_combine<T>(Fe, A, B, d->K, d->R, n3, ne, f, g, s);
             if (e) return cuda_fail(e, "DG combination");
-            const dgfs_status st = run<T>(p, Op::Collide2, f, g, Q, ne * d->R, s);
+            const dgfs_status st = d->sym ? run<T>(p, Op::Collide, f, nullptr, Q, ne * d->R, s)
+                                          : run<T>(p, Op::Collide2, f, g, Q, ne * d->R, s);
             if (st != DGFS_OK) return st;
         }
-        cudaError_t e = launch_dg_accumulate<T>(Q, rs, d->K, d->R, n3, ne, Ce, s);
+        cudaError_t e = launch_dg_accumulate<T>(Q, rs, sgn, d->K, d->R, n3, ne, Ce, s);
         if (e) return cuda_fail(e, "DG accumulation");
         if (p->prof) p->prof_launches += d->R > 0 ? 2 : 1;
     }
@@ -1020,10 +1024,42 @@ dgfs_status dgfs_dg_create(dgfs_plan_t plan, int K, const double* H, double svd_
     d->emax = max_elements;
     d->device = plan->device;
     // SVD of every slice H[m] (column-major K x K): H[m] = U diag(sv) V^T; row r of the
-    // f coefficients is column r of U, row r of the g coefficients is sv[r] times column r of V
-    std::vector<double> A, B;
+    // f coefficients is column r of U, row r of the g coefficients is sv[r] times column r of V.
+    // Symmetric slices (the nodal basis always gives them): the eigen-decomposition
+    // H[m] = sum_r lambda_r u_r u_r^T is such an SVD with f_r = sqrt|lambda_r| u_r . F and
+    // g_r = sign(lambda_r) f_r, so every term is sign(lambda_r) Q(f_r, f_r)
+    std::vector<double> A, B, sg;
     std::vector<int> rs(1, 0);
-    for (int m = 0; m < K; ++m) {
+    bool sym = true;
+    for (size_t m = 0; m < (size_t)K && sym; ++m)
+        for (int a = 0; a < K && sym; ++a)
+            for (int b = 0; b < a; ++b) {
+                const double x = H[(m * K + a) * K + b], y = H[(m * K + b) * K + a];
+                if (std::fabs(x - y) > 1e-13 * (std::fabs(x) + std::fabs(y)) + 1e-300) {
+                    sym = false;
+                    break;
+                }
+            }
+    d->sym = sym;
+    for (int m = 0; m < K && sym; ++m) {
+        std::vector<double> Hm(H + (size_t)m * K * K, H + (size_t)(m + 1) * K * K), w, V;
+        sym_eig_small(K, Hm, w, V);
+        std::vector<int> order(K);
+        for (int r = 0; r < K; ++r) order[r] = r;
+        std::sort(order.begin(), order.end(), [&](int x, int y) { return std::fabs(w[x]) > std::fabs(w[y]); });
+        const double thr = (svd_tol > 0 ? svd_tol : 1e-14) * std::fabs(w[order[0]]);
+        int Rm = 0;
+        for (int r : order) {
+            if (!(std::fabs(w[r]) > thr)) continue;
+            const double sc = std::sqrt(std::fabs(w[r]));
+            for (int l = 0; l < K; ++l) A.push_back(sc * V[(size_t)l * K + r]);
+            sg.push_back(w[r] > 0 ? 1.0 : -1.0);
+            ++Rm;
+        }
+        d->ranks.push_back(Rm);
+        rs.push_back(rs.back() + Rm);
+    }
+    for (int m = 0; m < K && !sym; ++m) {
         std::vector<double> Hm((size_t)K * K), sv, U, V;
         for (int a = 0; a < K; ++a)
             for (int b = 0; b < K; ++b) Hm[(size_t)b * K + a] = H[((size_t)m * K + a) * K + b];
@@ -1048,17 +1084,20 @@ dgfs_status dgfs_dg_create(dgfs_plan_t plan, int K, const double* H, double svd_
     auto take = [&](size_t b) { const size_t o = off; off = align_up(off + b, 256); return o; };
     d->off_A = take(A.size() * es + es);
     d->off_B = take(B.size() * es + es);
+    d->off_sgn = take(sg.size() * es + es);
     d->off_rs = take(rs.size() * sizeof(int));
     d->off_f = take((size_t)max_elements * d->R * n3 * es);
-    d->off_g = take((size_t)max_elements * d->R * n3 * es);
+    d->off_g = take(sym ? 0 : (size_t)max_elements * d->R * n3 * es);
     d->off_Q = take((size_t)max_elements * d->R * n3 * es);
     std::vector<unsigned char> blob(d->off_f, 0);
     if (plan->prec == DGFS_PREC_FP64) {
         put_coeffs<double>(blob, d->off_A, A);
         put_coeffs<double>(blob, d->off_B, B);
+        put_coeffs<double>(blob, d->off_sgn, sg);
     } else {
         put_coeffs<float>(blob, d->off_A, A);
         put_coeffs<float>(blob, d->off_B, B);
+        put_coeffs<float>(blob, d->off_sgn, sg);
     }
     std::memcpy(blob.data() + d->off_rs, rs.data(), rs.size() * sizeof(int));
     DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");

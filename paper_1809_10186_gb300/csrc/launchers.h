@@ -146,13 +146,14 @@ cudaError_t launch_vss_finalize_t(const Cplx<T>* Y, int yfields, const T* a, con
                                   int* flags, cudaStream_t s);
 
 // ---- DG element collision, SVD variant (k_dg.cu) ---------------------------------------
-// f[e][r] = sum_l A[r][l] F[e][l], g[e][r] = sum_l B[r][l] F[e][l]   (F [E][K][n3], K <= 16)
+// f[e][r] = sum_l A[r][l] F[e][l], g[e][r] = sum_l B[r][l] F[e][l]   (F [E][K][n3], K <= 16; B == nullptr:
+// f only)
 template <typename T>
 cudaError_t launch_dg_combine(const T* F, const T* A, const T* B, int K, int R, int64_t n3, int64_t E, T* f, T* g,
                               cudaStream_t s);
-// C[e][m] = sum_{r = rs[m]}^{rs[m+1]-1} Q[e][r]   (rs: device [K + 1])
+// C[e][m] = sum_{r = rs[m]}^{rs[m+1]-1} sgn[r] Q[e][r]   (rs: device [K + 1]; sgn: device [R] or nullptr)
 template <typename T>
-cudaError_t launch_dg_accumulate(const T* Q, const int* rs, int K, int R, int64_t n3, int64_t E, T* C,
+cudaError_t launch_dg_accumulate(const T* Q, const int* rs, const T* sgn, int K, int R, int64_t n3, int64_t E, T* C,
                                  cudaStream_t s);
 
 // ---- 1-D DGFS transport (k_slab.cu) ------------------------------------------------------

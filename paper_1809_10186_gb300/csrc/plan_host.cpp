@@ -326,6 +326,46 @@ bool dg_tensor_1d(int K, std::vector<double>& nodes, std::vector<double>& M, std
     return true;
 }
 
+void sym_eig_small(int n, std::vector<double> A, std::vector<double>& w, std::vector<double>& V) {
+    // cyclic Jacobi: rotations in the (p, q) planes zero A[p][q] in turn until the off-diagonal
+    // part vanishes; V accumulates the rotations (row-major, column k = eigenvector k)
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
+    double norm2 = 0.0;
+    for (double x : A) norm2 += x * x;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += a(p, q) * a(p, q);
+        if (!(off > 1e-32 * norm2)) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                if (a(p, q) == 0.0) continue;
+                const double theta = (a(q, q) - a(p, p)) / (2.0 * a(p, q));
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) {   // A <- A J (columns p, q)
+                    const double kp = a(k, p), kq = a(k, q);
+                    a(k, p) = c * kp - sn * kq;
+                    a(k, q) = sn * kp + c * kq;
+                }
+                for (int k = 0; k < n; ++k) {   // A <- J^T A (rows p, q)
+                    const double pk = a(p, k), qk = a(q, k);
+                    a(p, k) = c * pk - sn * qk;
+                    a(q, k) = sn * pk + c * qk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double kp = V[(size_t)k * n + p], kq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = c * kp - sn * kq;
+                    V[(size_t)k * n + q] = sn * kp + c * kq;
+                }
+            }
+    }
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) w[i] = a(i, i);
+}
+
 bool dg_stiffness_1d(int K, std::vector<double>& S, std::vector<double>& Minv) {
     std::vector<double> nodes, M, H;
     if (!dg_tensor_1d(K, nodes, M, H)) return false;

@@ -59,6 +59,10 @@ void svd_small(int m, int n, const std::vector<double>& A, std::vector<double>& 
 // outside [2, 16].
 bool dg_tensor_1d(int K, std::vector<double>& nodes, std::vector<double>& M, std::vector<double>& H);
 
+// Eigen-decomposition of a symmetric n x n matrix (row-major) by cyclic Jacobi rotations:
+// A = V diag(w) V^T, V row-major with column k the k-th eigenvector (unsorted).
+void sym_eig_small(int n, std::vector<double> A, std::vector<double>& w, std::vector<double>& V);
+
 // Stiffness matrix S[m][l] = int phi_l dphi_m/dxi (eq. eq_stiffMatrix1 on [-1, 1]) and the inverse
 // mass matrix of the same basis. False for K outside [2, 16].
 bool dg_stiffness_1d(int K, std::vector<double>& S, std::vector<double>& Minv);

@@ -79,3 +79,18 @@ def test_svd_truncation_drops_small_singular_values_only():
         err = np.linalg.norm(u @ v - H[m], 2)
         dropped = s[s <= 0.3 * s[0]]
         assert err <= (dropped.max() if len(dropped) else 0.0) + 1e-14
+
+
+@pytest.mark.parametrize("K,tol", [(2, 0.0), (3, 0.0), (3, 0.3)])
+def test_symmetric_slices_eigen_form_equals_svd_variant(K, tol):
+    """Every H[m] is symmetric, so its eigen-decomposition is an SVD: the signed sum of quadratic
+    terms Q(f_r, f_r) equals eq. eq_coln_derivation_SVD_4 (and eq. HH without truncation)."""
+    plan = O.OraclePlan(8, 4.0, gamma=0.38, M=12, Nrho=8, nyquist="sym")
+    _, _, H = D.dg_tensors(K)
+    F = _element_inputs(K, 8, 4.0, 31 + K)
+    sym = D.element_collision_sym(plan, H, F, tol)
+    svd = D.element_collision_svd(plan, H, F, tol)
+    assert np.linalg.norm(sym - svd) <= 1e-12 * np.linalg.norm(svd)
+    if tol == 0.0:
+        direct = D.element_collision_direct(plan, H, F)
+        assert np.linalg.norm(sym - direct) <= 1e-12 * np.linalg.norm(direct)
