@@ -167,12 +167,17 @@ class ClockSampler:
 # ---- roofline bookkeeping ----------------------------------------------------------------------
 
 def translate_flops_per_node(N, Nrho, npairs, prec):
-    """Flops the chosen formulation executes in the translate-product kernel, per node.
+    """Flops the chosen formulation executes in the translate-product step, per node.
 
-    Per (radial point, pair): two 3-D translates, each three dense N x N circulant passes over
-    N^2 lines (2 N^4 flops per pass), then the product and weighted accumulation (3 N^3).
-    The 16-bit modes split every filter into hi + lo parts: two products per contraction.
+    Tensor-core modes: per (radial point, pair) two 3-D translates, each three dense N x N
+    circulant passes over N^2 lines (2 N^4 flops per pass), every filter split into hi + lo parts
+    (two products per contraction), then the product and weighted accumulation (3 N^3).
+    FP32 / FP64 (N = 8, 16, 32): translates in Fourier space, one complex 3-D inverse transform per
+    (radial point, pair) (radix-2: 5 N^3 log2 N^3) giving both translates, plus ~17 flops per
+    point of phases, product and accumulation.
     """
+    if prec in ("fp32", "fp64") and N in (8, 16, 32):
+        return Nrho * npairs * (5.0 * N ** 3 * math.log2(N ** 3) + 17.0 * N ** 3)
     mma = 12.0 * N ** 4
     elem = 3.0 * N ** 3
     mult = {"fp32": 1, "fp64": 1, "f16s": 2, "bf16s": 2}[prec]

@@ -217,7 +217,9 @@ dgfs_status dgfs_host_dg_stiffness(int K, double* S, double* Minv);
 dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host, int64_t B,
                               void* stream);
 
-/* Q(f,f) exactly as dgfs_collide computes it, for callers that must not allocate device
+/* Q(f,f) as dgfs_collide computes it (the same kernels, except that FP32/FP64 plans form the
+   translate products with the dense circulant kernel where dgfs_collide takes them in Fourier
+   space: equal to rounding), for callers that must not allocate device
    memory when they run (for example code whose device memory is fully reserved up front, or
    that may not pay the device synchronisation an allocation can cause). The paper has no
    counterpart to this call. Its intermediate fields live in one fixed 64 MiB device array

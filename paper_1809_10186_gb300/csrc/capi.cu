@@ -71,6 +71,11 @@ struct dgfs_plan_s {
     // VSS kernel: nodes per transform batch, its workspace region and the device tables
     int64_t vchunk = 0;
     bool vss_planes = false;   // fused plane/line kernels, plane-major fields and tables
+    // VHS translate products in Fourier space (FP32/FP64, N = 8, 16, 32): nodes per transform batch
+    bool fftx = false;
+    int64_t xchunk = 0;
+    size_t off_Xt = 0;
+    const void* d_mu = nullptr;   // [Nrho][npairs][3][N] complex multipliers (inside d_vss)
     size_t off_V = 0, vss_bytes = 0;
     void* d_vss = nullptr;   // A [Nrho][npairs][N^3] (T) | GL [N^3] (T) | mu [Nrho][npairs][3][N] (complex T)
     int xfields = 0;
@@ -140,6 +145,8 @@ void workspace_layout(dgfs_plan_s* p, int64_t C) {
     p->off_Y = take(C * 3 * n3 * 2 * es);
     p->off_io = take(C * 2 * n3 * es);                 // host-buffer staging (f in, Q out)
     p->off_node = take(C * (sizeof(int64_t) + 2 * sizeof(double)));
+    // operand spectra and translate spectra of a batch of the Fourier-space translate products
+    p->off_Xt = take((size_t)p->xchunk * (2 + 2 * (size_t)p->hp.npairs) * n3 * 2 * es);
     p->ws_bytes = off;
 }
 
@@ -353,6 +360,37 @@ dgfs_status vss_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
     return DGFS_OK;
 }
 
+// P[node][r] = sum_p w_p [(T_s f)(T_-s g) + (T_-s f)(T_s g)] with the translates taken in Fourier
+// space (k_vss.cu: one complex inverse transform gives T_s f + i T_-s g), in batches of xchunk nodes;
+// the same P as the dense circulant passes of launch_gain_products at a fifth of the arithmetic.
+template <typename T>
+cudaError_t fft_gain_products(dgfs_plan_s* p, const T* f, const T* g, int64_t nodes, T* P, cudaStream_t s) {
+    const DevTables<T>& t = tables<T>(p);
+    const int N = t.N, np = t.npairs, Nr = t.Nrho, sets = g ? 2 : 1;
+    const int64_t n3 = (int64_t)N * N * N, C = p->xchunk;
+    Cplx<T>* Fh = reinterpret_cast<Cplx<T>*>(ws(p, p->off_Xt));
+    Cplx<T>* Gh = Fh + C * n3;
+    Cplx<T>* Z = Gh + C * n3;
+    const Cplx<T>* mu = static_cast<const Cplx<T>*>(p->d_mu);
+    const Cplx<T>* dftw = reinterpret_cast<const Cplx<T>*>(t.dftw);
+    for (int64_t n0 = 0; n0 < nodes; n0 += C) {
+        const int64_t nn = std::min<int64_t>(C, nodes - n0);
+        cudaError_t e = launch_vss_load_t<T>(f + n0 * n3, N, nn, Fh, s);
+        if (!e) e = launch_dft3<T>(t, Fh, nn, true, s);
+        if (!e && g) e = launch_vss_load_t<T>(g + n0 * n3, N, nn, Gh, s);
+        if (!e && g) e = launch_dft3<T>(t, Gh, nn, true, s);
+        for (int r = 0; r < Nr && !e; ++r) {
+            e = launch_vss_inverse_planes<T>(Fh, g ? Gh : nullptr, mu + (size_t)r * np * 3 * N, dftw, N, np, sets, nn,
+                                             Z, s);
+            if (!e) e = launch_vss_lines_sum<T>(Z, dftw, t.wsig, N, np, sets, nn, (int64_t)Nr * n3,
+                                                P + n0 * Nr * n3 + (int64_t)r * n3, s);
+        }
+        if (e) return e;
+        if (p->prof) p->prof_launches += (g ? 8 : 4) + 2 * (int64_t)Nr;
+    }
+    return cudaSuccess;
+}
+
 // One chunk of nodes through the whole pipeline. a/b/f_loss are chunk-base pointers.
 template <typename T>
 dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, const int64_t* offs,
@@ -407,6 +445,8 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
                                     reinterpret_cast<const float*>(gg), offs, nodes,
                                     reinterpret_cast<float*>(P), p->d_flags, s, p->fault);
         p->fault = 0;
+    } else if (p->fftx && !offs) {
+        e = fft_gain_products<T>(p, f, gg, nodes, P, s);
     } else {
         e = launch_gain_products(t, f, gg, offs, nodes, P, s);
     }
@@ -548,6 +588,14 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
             p->vchunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(C, (int64_t)(((size_t)1536 << 20) / zw)), 65535));
         }
     }
+    p->fftx = !is_tc(p->prec) && !p->hp.aniso && vss_fused_supported(p->hp.N, p->prec == DGFS_PREC_FP64);
+    if (p->fftx) {
+        // transform batches of about 1.5 GB of operand and translate spectra
+        const size_t n3 = (size_t)p->hp.N * p->hp.N * p->hp.N;
+        const size_t per = (2 + 2 * (size_t)p->hp.npairs) * n3 * 2 * elem_size(p->prec);
+        p->xchunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(p->chunk, (int64_t)(((size_t)1536 << 20) / per)),
+                                                           65535));
+    }
     workspace_layout(p.get(), p->chunk);
     std::vector<unsigned char> blob;
     if (p->prec == DGFS_PREC_FP64) fill_tables<double>(p.get(), blob, p->td, p->table_bytes);
@@ -568,9 +616,26 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
             return cuda_fail(ev, "VSS table upload");
         }
         p->vss_bytes = vblob.size();
+        p->d_mu = static_cast<unsigned char*>(p->d_vss) + (p->hp.Fa.size() + p->hp.GLa.size()) * elem_size(p->prec);
         // the FP64 host copies are no longer needed
         std::vector<double>().swap(p->hp.Fa);
         std::vector<double>().swap(p->hp.mu);
+    } else if (p->fftx) {
+        const size_t es = elem_size(p->prec);
+        std::vector<unsigned char> mblob(p->hp.mu.size() * es);
+        for (size_t i = 0; i < p->hp.mu.size(); ++i) {
+            if (es == 8) reinterpret_cast<double*>(mblob.data())[i] = p->hp.mu[i];
+            else reinterpret_cast<float*>(mblob.data())[i] = (float)p->hp.mu[i];
+        }
+        cudaError_t ev = cudaMalloc(&p->d_vss, mblob.size());
+        if (ev != cudaSuccess) return fail(DGFS_ERR_OOM, std::string("translate multipliers: ") + cudaGetErrorString(ev));
+        ev = cudaMemcpy(p->d_vss, mblob.data(), mblob.size(), cudaMemcpyHostToDevice);
+        if (ev != cudaSuccess) {
+            cudaFree(p->d_vss);
+            return cuda_fail(ev, "translate multiplier upload");
+        }
+        p->vss_bytes = mblob.size();
+        p->d_mu = p->d_vss;
     }
     cudaError_t e = cudaMalloc(&p->d_tables, p->table_bytes + tc_bytes);
     if (e != cudaSuccess) {

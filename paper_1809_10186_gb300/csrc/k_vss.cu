@@ -257,6 +257,48 @@ __global__ void __launch_bounds__(128) k_vss_lines(const Cplx<T>* __restrict__ Z
     for (int k = 0; k < N; ++k) w[k * n2] = Cplx<T>{v[k].x * sc, v[k].y * sc};
 }
 
+// VHS radial products in Fourier space (the isotropic kernel needs no per-point transform): for
+// z-line (x, y) of node n, the inverse z transforms of every sphere point's translate lines give
+//   P_r(x, y, z) = sum_p w_p [(T_s f)(T_-s g) + (T_-s f)(T_s g)]     (2 w_p (T_s f)(T_-s f) for g = f)
+// summed in registers; P_r is written in the standard layout [x][y][z] through shared memory.
+// grid (N^2 / 128, nodes); Z plane-major [n][set][p][kz][x][y]; P_r = P + n stride + r N^3.
+template <typename T, int N>
+__global__ void __launch_bounds__(128) k_vss_lines_sum(const Cplx<T>* __restrict__ Z, const Cplx<T>* __restrict__ dftw,
+                                                       const T* __restrict__ wsig, int npairs, int sets,
+                                                       int64_t node_stride, T* __restrict__ P) {
+    constexpr int64_t n2 = (int64_t)N * N, n3 = n2 * N;
+    constexpr int LINES = 128;
+    __shared__ Cplx<T> tw[N];
+    __shared__ T tile[LINES * (N + 1)];
+    if (threadIdx.x < N) tw[threadIdx.x] = dftw[N + threadIdx.x];
+    __syncthreads();
+    const int64_t l0 = (int64_t)blockIdx.x * LINES, l = l0 + threadIdx.x;   // N^2 is a multiple of 64
+    const int64_t n = blockIdx.y;
+    T acc[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) acc[k] = T(0);
+    Cplx<T> v[N];
+    if (l < n2) {
+        for (int p = 0; p < npairs; ++p) {
+            const T w = wsig[p] * (sets == 1 ? T(2) : T(1));
+            for (int s = 0; s < sets; ++s) {
+                const Cplx<T>* z = Z + ((n * sets + s) * npairs + p) * n3 + l;
+#pragma unroll
+                for (int k = 0; k < N; ++k) v[bitrev<N>(k)] = z[k * n2];
+                fft_line<T, N>(v, tw, false);
+#pragma unroll
+                for (int k = 0; k < N; ++k) acc[k] = fma(w * v[k].x, v[k].y, acc[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) tile[threadIdx.x * (N + 1) + k] = acc[k];
+    }
+    __syncthreads();
+    const int nl = (int)((n2 - l0) < LINES ? (n2 - l0) : LINES);
+    T* out = P + n * node_stride + l0 * N;
+    for (int e = threadIdx.x; e < nl * N; e += LINES) out[e] = tile[(e / N) * (N + 1) + e % N];
+}
+
 // X[n][z][x][y] = {f[n][x][y][z], 0}: a real field into a plane-major complex field
 template <typename T>
 __global__ void __launch_bounds__(256) k_vss_load_t(const T* __restrict__ f, int N, int64_t n3, Cplx<T>* __restrict__ X) {
@@ -353,6 +395,20 @@ cudaError_t launch_vss_forward_planes(const Cplx<T>* dftw, int N, int fields, in
 }
 
 template <typename T>
+cudaError_t launch_vss_lines_sum(const Cplx<T>* Z, const Cplx<T>* dftw, const T* wsig, int N, int npairs, int sets,
+                                 int64_t nodes, int64_t node_stride, T* P, cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    if (nodes > 65535) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((N * N + 127) / 128), (unsigned)nodes);
+    if (N == 8) k_vss_lines_sum<T, 8><<<grid, 128, 0, s>>>(Z, dftw, wsig, npairs, sets, node_stride, P);
+    else if (N == 16) k_vss_lines_sum<T, 16><<<grid, 128, 0, s>>>(Z, dftw, wsig, npairs, sets, node_stride, P);
+    else if (sizeof(T) == 4 && N == 32)
+        k_vss_lines_sum<T, sizeof(T) == 4 ? 32 : 16><<<grid, 128, 0, s>>>(Z, dftw, wsig, npairs, sets, node_stride, P);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_vss_finalize_t(const Cplx<T>* Y, int yfields, const T* a, const T* c, int N, int64_t nodes, T* out,
                                   int* flags, cudaStream_t s) {
     if (nodes <= 0) return cudaSuccess;
@@ -420,7 +476,9 @@ cudaError_t launch_vss_loss_init(const Cplx<T>* Ah, const Cplx<T>* Bh, const T* 
                                              cudaStream_t);                                                       \
     template cudaError_t launch_vss_forward_planes<T>(const Cplx<T>*, int, int, int64_t, Cplx<T>*, cudaStream_t); \
     template cudaError_t launch_vss_finalize_t<T>(const Cplx<T>*, int, const T*, const T*, int, int64_t, T*,     \
-                                                  int*, cudaStream_t);
+                                                  int*, cudaStream_t);                                            \
+    template cudaError_t launch_vss_lines_sum<T>(const Cplx<T>*, const Cplx<T>*, const T*, int, int, int, int64_t, \
+                                                 int64_t, T*, cudaStream_t);
 DGFS_VSS_INST(float)
 DGFS_VSS_INST(double)
 #undef DGFS_VSS_INST

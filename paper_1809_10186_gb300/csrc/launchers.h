@@ -140,6 +140,10 @@ cudaError_t launch_vss_lines(const Cplx<T>* Z, const Cplx<T>* dftw, int N, int n
 template <typename T>
 cudaError_t launch_vss_forward_planes(const Cplx<T>* dftw, int N, int fields, int64_t nodes, Cplx<T>* W,
                                       cudaStream_t s);
+// VHS: P[n][r] (standard layout, node stride node_stride) = sum_p w_p (products of the translate lines of Z)
+template <typename T>
+cudaError_t launch_vss_lines_sum(const Cplx<T>* Z, const Cplx<T>* dftw, const T* wsig, int N, int npairs, int sets,
+                                 int64_t nodes, int64_t node_stride, T* P, cudaStream_t s);
 // out (standard layout) = Re Y0 - a Re Y1 - (c ? c Re Y2 : 0), Y plane-major
 template <typename T>
 cudaError_t launch_vss_finalize_t(const Cplx<T>* Y, int yfields, const T* a, const T* c, int N, int64_t nodes, T* out,

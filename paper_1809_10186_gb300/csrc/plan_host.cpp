@@ -566,7 +566,11 @@ void build_vss_tables(HostPlan& p) {
             for (size_t i = 0; i < n3; ++i) p.GLa[i] += F0 * p.Lr[(size_t)r * n3 + i];
         }
     }
-    // per-axis multipliers of the translate by +s_rp: e^{i pi k t / L}, Nyquist cos(pi N t / 2L)
+}
+
+// per-axis multipliers of the translate by +s_rp: e^{i pi k t / L}, Nyquist cos(pi N t / 2L)
+void build_translate_multipliers(HostPlan& p) {
+    const int N = p.N, Nr = p.Nrho, np = p.npairs;
     p.mu.assign((size_t)Nr * np * 3 * N * 2, 0.0);
     for (int r = 0; r < Nr; ++r)
         for (int q = 0; q < np; ++q)
@@ -767,6 +771,7 @@ dgfs_status build_host_plan(const dgfs_plan_desc& d, HostPlan& p, std::string& e
             }
         }
     }
+    build_translate_multipliers(p);
     if (p.aniso) {
         if (d.svd_tol > 0 || d.svd_rank > 0) {
             err = "the VSS kernel factor is not compressed: svd_tol and svd_rank must be 0";

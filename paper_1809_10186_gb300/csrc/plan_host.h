@@ -32,7 +32,7 @@ struct HostPlan {
     bool aniso = false;
     std::vector<double> Fa;              // [Nrho][npairs][N^3] w_r w_p F(k, c_r, sigma_p), DFT index order
     std::vector<double> GLa;             // [N^3] loss weight G(m, m) of the VSS kernel
-    std::vector<double> mu;              // [Nrho][npairs][3][N][2] per-axis multipliers of +s_rp
+    std::vector<double> mu;              // [Nrho][npairs][3][N][2] per-axis multipliers of +s_rp (every plan)
 };
 
 // F(k, c_r, sigma) of eq. realGG for the VSS kernel b c_r^gamma (1 + cos chi)^(alpha - 1), as the

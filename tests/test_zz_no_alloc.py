@@ -2,9 +2,11 @@
 
 Some callers cannot allocate device memory when they run (their memory is reserved up front,
 or they must not pay the synchronisation an allocation can cause). dgfs_collide_noalloc serves
-them: it runs the same kernels as dgfs_collide but keeps its scratch in the library's fixed
-64 MiB device array. These tests call it through the C ABI, twice in a row (the array keeps the
-previous call's contents), and compare each result with dgfs_collide's on the same input.
+them: it evaluates the same operator as dgfs_collide but keeps its scratch in the library's fixed
+64 MiB device array (with the dense circulant translate kernel for FP32/FP64 plans, where
+dgfs_collide takes the translates in Fourier space). These tests call it through the C ABI, twice
+in a row (the array keeps the previous call's contents), and compare each result with
+dgfs_collide's on the same input.
 """
 import ctypes
 
@@ -16,7 +18,9 @@ from paper_1809_10186_gb300 import binding, workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-5   # the FP32 parity tolerance of the other GPU tests (relative L2)
+# relative L2 against dgfs_collide's result: the same kernels for F16S; for FP32 two translate
+# methods, each within 1e-5 of the loss term of the FP64 oracle (Q itself is a few % of the loss)
+TOL = {"fp32": 1e-4, "f16s": 1e-5, "fp64": 1e-10}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -48,7 +52,8 @@ def test_noalloc_matches_collide_twice(N, L, M, prec, B):
         torch.cuda.synchronize()
         plan.stream_status()
         rel = (torch.linalg.norm(q - ref) / torch.linalg.norm(ref)).item()
-        assert rel < TOL, (call, rel)
+        print(prec, N, call, "rel %.3g" % rel)
+        assert rel < TOL[prec], (call, rel)
 
 
 def test_noalloc_rejects_batches_beyond_the_fixed_array():
