@@ -306,8 +306,7 @@ dgfs_status vss_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
     const T* GL = A + (size_t)Nr * np * n3;
     const Cplx<T>* mu = reinterpret_cast<const Cplx<T>*>(GL + n3);
     const Cplx<T>* dftw = reinterpret_cast<const Cplx<T>*>(t.dftw);
-    for (int64_t n0 = 0; n0 < nodes && p->vss_planes; n0 += C) {
-        // fused kernels, plane-major fields
+    for (int64_t n0 = 0; n0 < nodes; n0 += C) {
         const int64_t nn = std::min<int64_t>(C, nodes - n0);
         cudaError_t e = launch_vss_load_t<T>(a + n0 * n3, N, nn, Fh, s);
         if (!e) e = launch_dft3<T>(t, Fh, nn, true, s);
@@ -329,31 +328,6 @@ dgfs_status vss_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
         if (e) return cuda_fail(e, "VSS loss and finalisation");
         if (p->prof) {
             p->prof_launches += (two ? 8 : 4) + 1 + (int64_t)Nr * 4 + 4;
-            p->prof_nodes += nn;
-        }
-    }
-    for (int64_t n0 = 0; n0 < nodes && !p->vss_planes; n0 += C) {
-        const int64_t nn = std::min<int64_t>(C, nodes - n0);
-        cudaError_t e = launch_load_field<T>(N, a + n0 * n3, nullptr, nullptr, nn, Fh, 1, 0, 0, s);
-        if (!e) e = launch_dft3<T>(t, Fh, nn, true, s);
-        if (!e && two) e = launch_load_field<T>(N, b + n0 * n3, nullptr, nullptr, nn, Gh, 1, 0, 0, s);
-        if (!e && two) e = launch_dft3<T>(t, Gh, nn, true, s);
-        if (!e) e = launch_vss_loss_init<T>(Fh, two ? Gh : Fh, GL, N, nn, Y, yf, s);
-        if (e) return cuda_fail(e, "VSS operand transforms");
-        for (int r = 0; r < Nr && !e; ++r) {
-            e = launch_vss_spectra<T>(Fh, two ? Gh : nullptr, mu + (size_t)r * np * 3 * N, N, np, sets, nn, Z, s);
-            if (!e) e = launch_dft3<T>(t, Z, nn * sets * np, false, s);
-            if (!e) e = launch_vss_product<T>(Z, N, np, sets, nn, W, s);
-            if (!e) e = launch_dft3<T>(t, W, nn * nw, true, s);
-            if (!e) e = launch_vss_accumulate<T>(W, A + (size_t)r * np * n3, N, np, nn, scale, Y, yf, s);
-        }
-        if (e) return cuda_fail(e, "VSS gain");
-        e = launch_dft3<T>(t, Y, nn * yf, false, s);
-        if (!e) e = launch_finalize<T>(N, Nr, Y, yf, a + n0 * n3, op == Op::Jvp ? b + n0 * n3 : nullptr, nullptr,
-                                       nullptr, nn, 0, out + n0 * n3, p->d_flags, s);
-        if (e) return cuda_fail(e, "VSS loss and finalisation");
-        if (p->prof) {
-            p->prof_launches += (two ? 8 : 4) + 1 + (int64_t)Nr * 9 + 4;
             p->prof_nodes += nn;
         }
     }

@@ -80,5 +80,70 @@ __device__ __forceinline__ void fft_line(Cplx<T> (&a)[N], const Cplx<T>* __restr
     fft_stage<T, N, 2>(a, tw, forward);
 }
 
+// ---- N = 3 * 2^m (12, 24): one radix-3 stage over three radix-2 transforms of length N/3 ------
+//
+// Decimation in time by 3: x[3m + j] (j = 0, 1, 2) are transformed with length S = N/3 and
+// X[k] = Y_0[k mod S] + w^k Y_1[k mod S] + w^2k Y_2[k mod S], w = e^{-+2 pi i / N}. Element k of a
+// line is loaded into slot line_slot<N>(k): bit-reversed for a power of two, block j = k mod 3 and
+// the bit-reversed position of k / 3 inside it otherwise. line_fft leaves the result in natural
+// order in both cases; tw is row 1 of the N-point DFT table.
+
+template <int N>
+__device__ __forceinline__ constexpr int line_slot(int k) {
+    if constexpr ((N & (N - 1)) == 0) return bitrev<N>(k);
+    else return (k % 3) * (N / 3) + bitrev<N / 3>(k / 3);
+}
+
+// radix-2 stages of a length-S transform held in a[OFF .. OFF + S); its twiddle w_S^q is
+// tw[q N / S] of the N-row
+template <typename T, int NA, int OFF, int S, int LEN>
+__device__ __forceinline__ void fft_stage_sub(Cplx<T> (&a)[NA], const Cplx<T>* __restrict__ tw, bool forward) {
+    constexpr int half = LEN / 2, step = S / LEN, tstride = NA / S;
+#pragma unroll
+    for (int i = 0; i < S; i += LEN)
+#pragma unroll
+        for (int j = 0; j < half; ++j) {
+            const Cplx<T> u = a[OFF + i + j], v0 = a[OFF + i + j + half];
+            Cplx<T> v;
+            if (j == 0) {
+                v = v0;
+            } else if (4 * j * step == S) {
+                v = forward ? Cplx<T>{v0.y, -v0.x} : Cplx<T>{-v0.y, v0.x};
+            } else {
+                const Cplx<T> w = tw[j * step * tstride];
+                const T wi = forward ? w.y : -w.y;
+                v = Cplx<T>{v0.x * w.x - v0.y * wi, v0.x * wi + v0.y * w.x};
+            }
+            a[OFF + i + j] = Cplx<T>{u.x + v.x, u.y + v.y};
+            a[OFF + i + j + half] = Cplx<T>{u.x - v.x, u.y - v.y};
+        }
+    if constexpr (LEN < S) fft_stage_sub<T, NA, OFF, S, 2 * LEN>(a, tw, forward);
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void line_fft(Cplx<T> (&a)[N], const Cplx<T>* __restrict__ tw, bool forward) {
+    if constexpr ((N & (N - 1)) == 0) {
+        fft_stage<T, N, 2>(a, tw, forward);
+    } else {
+        static_assert(N % 3 == 0 && ((N / 3) & (N / 3 - 1)) == 0, "N must be a power of two or 3 times one");
+        constexpr int S = N / 3;
+        fft_stage_sub<T, N, 0, S, 2>(a, tw, forward);
+        fft_stage_sub<T, N, S, S, 2>(a, tw, forward);
+        fft_stage_sub<T, N, 2 * S, S, 2>(a, tw, forward);
+        Cplx<T> b[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const int q = k % S;
+            const Cplx<T> y0 = a[q], y1 = a[S + q], y2 = a[2 * S + q];
+            const Cplx<T> w1 = tw[k], w2 = tw[(2 * k) % N];
+            const T s1 = forward ? w1.y : -w1.y, s2 = forward ? w2.y : -w2.y;
+            b[k] = Cplx<T>{y0.x + (y1.x * w1.x - y1.y * s1) + (y2.x * w2.x - y2.y * s2),
+                           y0.y + (y1.x * s1 + y1.y * w1.x) + (y2.x * s2 + y2.y * w2.x)};
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) a[k] = b[k];
+    }
+}
+
 }  // namespace fdev
 }  // namespace dgfs

@@ -6,9 +6,10 @@
 // kernel mode G(m,m). With the radial kernel compressed as sinc(pi c_r |k| / 2L) ~=
 // sum_s Uk[s](k) Vr[s][r], the gain needs only `rank` forward transforms:
 //   gain^_k = sum_s Uk[s](k) DFT( sum_r Vr[s][r] w_r rho_r P_r )_k.
-// Transforms are dense separable DFTs of the standard grid ordering; every multiplier is
-// diagonal, so the half-cell phase of the cell-centred grid cancels between the forward
-// and inverse transforms and the signed lattice index k = q (q < N/2) or q - N is used.
+// Transforms are separable DFTs of the standard grid ordering, one register-resident FFT line per
+// thread and axis (radix 2, plus one radix-3 stage for N = 12, 24); every multiplier is diagonal,
+// so the half-cell phase of the cell-centred grid cancels between the forward and inverse
+// transforms and the signed lattice index k = q (q < N/2) or q - N is used.
 #include <cmath>
 #include <cstdint>
 
@@ -21,67 +22,7 @@ namespace {
 
 using namespace fdev;
 
-// ---- dense DFT passes -----------------------------------------------------------------
-
-// Strided axis: data viewed as [outer][N][inner], tile [N][TI] of one outer index.
-template <typename T, int TI>
-__global__ void k_dft_strided(Cplx<T>* __restrict__ X, const Cplx<T>* __restrict__ W, int N,
-                              int64_t inner, int64_t tiles_per_outer, int forward, T scale) {
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    Cplx<T>* Ws = reinterpret_cast<Cplx<T>*>(sm_raw);        // [N][N]
-    Cplx<T>* tile = Ws + N * N;                                // [N][TI]
-    const int64_t o = blockIdx.x / tiles_per_outer;
-    const int64_t i0 = (blockIdx.x % tiles_per_outer) * TI;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int nth = blockDim.x * blockDim.y, t = ty * blockDim.x + tx;
-    for (int e = t; e < N * N; e += nth) Ws[e] = W[e];
-    Cplx<T>* base = X + o * (int64_t)N * inner;
-    const bool live = (i0 + tx) < inner;
-    for (int j = ty; j < N; j += blockDim.y)
-        if (live) tile[j * TI + tx] = base[(int64_t)j * inner + i0 + tx];
-    __syncthreads();
-    if (!live) return;
-    for (int q = ty; q < N; q += blockDim.y) {
-        T re = 0, im = 0;
-        for (int j = 0; j < N; ++j) {
-            const Cplx<T> w = Ws[q * N + j];
-            const T wi = forward ? w.y : -w.y;
-            const Cplx<T> v = tile[j * TI + tx];
-            re = fma(w.x, v.x, fma(-wi, v.y, re));
-            im = fma(w.x, v.y, fma(wi, v.x, im));
-        }
-        base[(int64_t)q * inner + i0 + tx] = Cplx<T>{re * scale, im * scale};
-    }
-}
-
-// Contiguous axis: TL lines of N consecutive values per CTA (padded tile against bank conflicts).
-template <typename T, int TL>
-__global__ void k_dft_contig(Cplx<T>* __restrict__ X, const Cplx<T>* __restrict__ W, int N,
-                             int64_t lines, int forward, T scale) {
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    Cplx<T>* Ws = reinterpret_cast<Cplx<T>*>(sm_raw);        // [N][N]
-    Cplx<T>* tile = Ws + N * N;                                // [TL][N+1]
-    const int64_t l0 = (int64_t)blockIdx.x * TL;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int nth = blockDim.x * blockDim.y, t = ty * blockDim.x + tx;
-    for (int e = t; e < N * N; e += nth) Ws[e] = W[e];
-    const int64_t nl = (lines - l0) < TL ? (lines - l0) : TL;
-    Cplx<T>* base = X + l0 * N;
-    for (int e = t; e < nl * N; e += nth) tile[(e / N) * (N + 1) + e % N] = base[e];
-    __syncthreads();
-    if (tx >= nl) return;
-    for (int q = ty; q < N; q += blockDim.y) {
-        T re = 0, im = 0;
-        for (int j = 0; j < N; ++j) {
-            const Cplx<T> w = Ws[q * N + j];
-            const T wi = forward ? w.y : -w.y;
-            const Cplx<T> v = tile[tx * (N + 1) + j];
-            re = fma(w.x, v.x, fma(-wi, v.y, re));
-            im = fma(w.x, v.y, fma(wi, v.x, im));
-        }
-        base[(int64_t)tx * N + q] = Cplx<T>{re * scale, im * scale};
-    }
-}
+// ---- radix-2 / radix-3 FFT passes -------------------------------------------------------
 
 // Strided axes: line l of the field group starts at base(l) and has stride S; consecutive
 // threads take consecutive lines whose elements are adjacent in memory (coalesced).
@@ -99,8 +40,8 @@ k_fft_strided(Cplx<T>* __restrict__ X, const Cplx<T>* __restrict__ W, int64_t li
     Cplx<T>* base = X + o * (int64_t)N * stride + i;
     Cplx<T> a[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) a[bitrev<N>(k)] = base[(int64_t)k * stride];
-    fft_line<T, N>(a, tw, forward != 0);
+    for (int k = 0; k < N; ++k) a[line_slot<N>(k)] = base[(int64_t)k * stride];
+    line_fft<T, N>(a, tw, forward != 0);
 #pragma unroll
     for (int k = 0; k < N; ++k) base[(int64_t)k * stride] = Cplx<T>{a[k].x * scale, a[k].y * scale};
 }
@@ -120,8 +61,8 @@ k_fft_contig(Cplx<T>* __restrict__ X, const Cplx<T>* __restrict__ W, int64_t lin
     if (threadIdx.x < nl) {
         Cplx<T> a[N];
 #pragma unroll
-        for (int k = 0; k < N; ++k) a[bitrev<N>(k)] = tile[threadIdx.x * (N + 1) + k];
-        fft_line<T, N>(a, tw, forward != 0);
+        for (int k = 0; k < N; ++k) a[line_slot<N>(k)] = tile[threadIdx.x * (N + 1) + k];
+        line_fft<T, N>(a, tw, forward != 0);
 #pragma unroll
         for (int k = 0; k < N; ++k) tile[threadIdx.x * (N + 1) + k] = Cplx<T>{a[k].x * scale, a[k].y * scale};
     }
@@ -385,29 +326,12 @@ cudaError_t launch_dft3(const DevTables<T>& t, Cplx<T>* X, int64_t count, bool f
     const T scale = forward ? T(1) / T(N) : T(1);
     const Cplx<T>* W = reinterpret_cast<const Cplx<T>*>(t.dftw);
     if (N == 8) return fft3<T, 8>(X, W, count, forward, scale, s);
+    if (N == 12) return fft3<T, 12>(X, W, count, forward, scale, s);
     if (N == 16) return fft3<T, 16>(X, W, count, forward, scale, s);
+    if (N == 24) return fft3<T, 24>(X, W, count, forward, scale, s);
     if constexpr (sizeof(T) == 4)                       // FP64 plans stop at N = 24
         if (N == 32) return fft3<T, 32>(X, W, count, forward, scale, s);
-    constexpr int TI = 32;
-    const size_t sm_s = sizeof(Cplx<T>) * (size_t)(N * N + N * TI);
-    // axis x: [count][N][N^2]
-    {
-        const int64_t tiles = (n2 + TI - 1) / TI;
-        k_dft_strided<T, TI><<<(unsigned)(count * tiles), dim3(TI, 8), sm_s, s>>>(X, W, N, n2, tiles, forward, scale);
-    }
-    // axis y: [count*N][N][N]
-    {
-        const int64_t tiles = ((int64_t)N + TI - 1) / TI;
-        k_dft_strided<T, TI><<<(unsigned)(count * N * tiles), dim3(TI, 8), sm_s, s>>>(X, W, N, N, tiles, forward, scale);
-    }
-    // axis z: count*N^2 contiguous lines
-    {
-        constexpr int TL = 32;
-        const int64_t lines = count * n2;
-        const size_t sm_c = sizeof(Cplx<T>) * (size_t)(N * N + TL * (N + 1));
-        k_dft_contig<T, TL><<<blocks_for(lines, TL), dim3(TL, 8), sm_c, s>>>(X, W, N, lines, forward, scale);
-    }
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>

@@ -9,24 +9,20 @@
 // field is real (symmetric Nyquist convention), one complex inverse transform carries two of them:
 //   IDFT(mu_s f^ + i mu_-s g^) = T_s f + i T_-s g,   IDFT(mu_-s f^ + i mu_s g^) = T_-s f + i T_s g,
 // and the real products of two sphere points share one forward transform (real and imaginary
-// parts), separated in Fourier space by Hermitian symmetry. Per radial point r, over a chunk of
-// nodes and all sphere points:
-//   k_vss_spectra     Z[n][set][p] = the two multiplied spectra above (set 1 only for f != g)
-//   inverse DFT       (k_fourier.cu)
-//   k_vss_product     W[n][j] = P_2j + i P_2j+1,  P_p = Re Z0 Im Z0 + Re Z1 Im Z1  (2 Re Z0 Im Z0 for f = g)
-//   forward DFT
-//   k_vss_accumulate  Y[n][0](k) += scale sum_p A_rp(k) P^_p(k)
-// All four are elementwise streams over N^3 points; the transforms dominate.
-//
-// For N = 8, 16, 32 the transforms are fused with the elementwise steps, with every field stored
-// plane-major ([kz][kx][ky], the z axis outermost) so that a plane of fixed kz is contiguous:
-//   k_vss_planes<INV>   per (node, field, KZ planes): translate spectra formed on load, inverse
-//                       transforms along x and y in shared memory                  -> Z
+// parts), separated in Fourier space by Hermitian symmetry. Per radial point r, over a batch of
+// nodes and all sphere points, with every field stored plane-major ([kz][kx][ky], the z axis
+// outermost, so that a plane of fixed kz is contiguous):
+//   k_vss_planes<INV>   per (node, field, KZ planes): translate spectra formed while the x lines
+//                       load, inverse transforms along x and y                         -> Z
 //   k_vss_lines         per (node, sphere-point pair, (x, y) line): inverse transform along z,
-//                       the two products, packing, forward transform along z        -> W
+//                       the products P_p = Re Z0 Im Z0 + Re Z1 Im Z1 (2 Re Z0 Im Z0 for f = g),
+//                       packing P_2j + i P_2j+1, forward transform along z             -> W
 //   k_vss_planes<FWD>   forward transforms along x and y of the packed spectra, in place
-//   k_vss_accumulate    as above (the mirror -k is taken per axis, so any axis order works)
-// which moves a third of the bytes of the separate passes. N = 12, 24 keep the separate passes.
+//   k_vss_accumulate    Y[n][0](k) += scale sum_p A_rp(k) P^_p(k) (the mirror -k is taken per
+//                       axis, so any axis order works)
+// The VHS path uses the same plane kernel and k_vss_lines_sum, which sums the products over the
+// sphere in registers. Lines are transformed in registers: radix 2 for N = 8, 16, 32, one radix-3
+// stage over three radix-2 transforms for N = 12, 24 (fourier_dev.cuh).
 #include <cstdint>
 
 #include "fourier_dev.cuh"
@@ -35,60 +31,6 @@
 namespace dgfs {
 
 namespace {
-
-template <typename T>
-__device__ __forceinline__ Cplx<T> cmul(Cplx<T> a, Cplx<T> b) {
-    return Cplx<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
-}
-
-// grid (ceil(n3 / 256), npairs, nodes); mu_r: [npairs][3][N] complex multipliers of +s_rp
-template <typename T>
-__global__ void __launch_bounds__(256) k_vss_spectra(const Cplx<T>* __restrict__ Fh, const Cplx<T>* __restrict__ Gh,
-                                                     const Cplx<T>* __restrict__ mu_r, int N, int npairs, int sets,
-                                                     int64_t n3, Cplx<T>* __restrict__ Z) {
-    __shared__ Cplx<T> m[3 * 64];
-    const int p = blockIdx.y;
-    const int64_t n = blockIdx.z;
-    for (int i = threadIdx.x; i < 3 * N; i += blockDim.x) m[i] = mu_r[(int64_t)p * 3 * N + i];
-    __syncthreads();
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n3) return;
-    const int kx = (int)(j / ((int64_t)N * N)), ky = (int)((j / N) % N), kz = (int)(j % N);
-    const Cplx<T> mu = cmul(cmul(m[kx], m[N + ky]), m[2 * N + kz]);   // mu_s(k); mu_-s = conj
-    const Cplx<T> f = Fh[n * n3 + j];
-    const Cplx<T> g = Gh ? Gh[n * n3 + j] : f;
-    const T a = mu.x, b = mu.y;
-    // set 0: mu f + i conj(mu) g
-    Z[((n * sets) * npairs + p) * n3 + j] =
-        Cplx<T>{a * f.x - b * f.y - a * g.y + b * g.x, a * f.y + b * f.x + a * g.x + b * g.y};
-    if (sets == 2)   // set 1: conj(mu) f + i mu g
-        Z[((n * sets + 1) * npairs + p) * n3 + j] =
-            Cplx<T>{a * f.x + b * f.y - a * g.y - b * g.x, a * f.y - b * f.x + a * g.x - b * g.y};
-}
-
-// grid (ceil(n3 / 256), (npairs + 1) / 2, nodes)
-template <typename T>
-__global__ void __launch_bounds__(256) k_vss_product(const Cplx<T>* __restrict__ Z, int npairs, int sets, int64_t n3,
-                                                     Cplx<T>* __restrict__ W) {
-    const int jw = blockIdx.y, nw = gridDim.y;
-    const int64_t n = blockIdx.z;
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n3) return;
-    T P[2] = {T(0), T(0)};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int p = 2 * jw + h;
-        if (p >= npairs) break;
-        const Cplx<T> z0 = Z[((n * sets) * npairs + p) * n3 + j];
-        if (sets == 2) {
-            const Cplx<T> z1 = Z[((n * sets + 1) * npairs + p) * n3 + j];
-            P[h] = z0.x * z0.y + z1.x * z1.y;
-        } else {
-            P[h] = T(2) * z0.x * z0.y;
-        }
-    }
-    W[(n * nw + jw) * n3 + j] = Cplx<T>{P[0], P[1]};
-}
 
 // grid (ceil(n3 / 256), nodes); A_r: [npairs][n3] real, W: [nodes][(npairs + 1) / 2][n3]
 template <typename T>
@@ -140,12 +82,20 @@ __global__ void __launch_bounds__(256) k_vss_loss_init(const Cplx<T>* __restrict
 
 // ---- fused plane / line kernels (power-of-two N) ---------------------------------------------
 
-using fdev::bitrev;
-using fdev::fft_line;
+using fdev::line_fft;
+using fdev::line_slot;
+
+// the largest divisor of N with KZ N <= 128 threads
+constexpr int planes_per_cta(int N) {
+    int kz = 1;
+    for (int d = 1; d <= N; ++d)
+        if (N % d == 0 && d * N <= 128) kz = d;
+    return kz;
+}
 
 template <typename T, int N>
 struct PlaneGeo {
-    static constexpr int KZ = (N * N <= 128) ? N : 128 / N;   // planes per CTA (4 at N = 32, 8 at N = 16)
+    static constexpr int KZ = planes_per_cta(N);               // planes per CTA (4 at N = 32 and 24, 8 at 16)
     static constexpr int NT = KZ * N;                          // one line per thread per pass
     static constexpr int P = N + 1;                            // padded row (complex elements)
     static constexpr size_t smem = (size_t)KZ * N * P * sizeof(Cplx<T>);
@@ -187,23 +137,23 @@ __global__ void __launch_bounds__(PlaneGeo<T, N>::NT)
             const Cplx<T> mx = m[kx];
             const T a = mx.x * myz.x - mx.y * myz.y, b = sgn * (mx.x * myz.y + mx.y * myz.x);
             const Cplx<T> fv = Fp[kx * N], gv = Gp[kx * N];
-            v[bitrev<N>(kx)] = Cplx<T>{a * fv.x - b * fv.y - a * gv.y + b * gv.x, a * fv.y + b * fv.x + a * gv.x + b * gv.y};
+            v[line_slot<N>(kx)] = Cplx<T>{a * fv.x - b * fv.y - a * gv.y + b * gv.x, a * fv.y + b * fv.x + a * gv.x + b * gv.y};
         }
     } else {
         __syncthreads();
 #pragma unroll
-        for (int x = 0; x < N; ++x) v[bitrev<N>(x)] = Xf[(int64_t)pl * n2 + x * N + ln];
+        for (int x = 0; x < N; ++x) v[line_slot<N>(x)] = Xf[(int64_t)pl * n2 + x * N + ln];
     }
     const T sc = INV ? T(1) : T(1) / T(N);
     // x lines (fixed ky = ln)
-    fft_line<T, N>(v, tw, !INV);
+    line_fft<T, N>(v, tw, !INV);
 #pragma unroll
     for (int k = 0; k < N; ++k) S[(pl * N + k) * P + ln] = Cplx<T>{v[k].x * sc, v[k].y * sc};
     __syncthreads();
     // y lines (fixed x = ln)
 #pragma unroll
-    for (int k = 0; k < N; ++k) v[bitrev<N>(k)] = S[(pl * N + ln) * P + k];
-    fft_line<T, N>(v, tw, !INV);
+    for (int k = 0; k < N; ++k) v[line_slot<N>(k)] = S[(pl * N + ln) * P + k];
+    line_fft<T, N>(v, tw, !INV);
 #pragma unroll
     for (int k = 0; k < N; ++k) S[(pl * N + ln) * P + k] = Cplx<T>{v[k].x * sc, v[k].y * sc};
     __syncthreads();
@@ -222,8 +172,8 @@ __device__ __forceinline__ void vss_line_products(const Cplx<T>* __restrict__ Z,
     Cplx<T> v[N];
     for (int s = 0; s < sets; ++s) {
 #pragma unroll
-        for (int k = 0; k < N; ++k) v[bitrev<N>(k)] = Z[s * set_stride + k * stride];
-        fft_line<T, N>(v, tw, false);
+        for (int k = 0; k < N; ++k) v[line_slot<N>(k)] = Z[s * set_stride + k * stride];
+        line_fft<T, N>(v, tw, false);
 #pragma unroll
         for (int k = 0; k < N; ++k) P[k] = fma(v[k].x, v[k].y, P[k]);
     }
@@ -250,8 +200,8 @@ __global__ void __launch_bounds__(128) k_vss_lines(const Cplx<T>* __restrict__ Z
     const T two = sets == 1 ? T(2) : T(1), sc = two / T(N);
     Cplx<T> v[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) v[bitrev<N>(k)] = Cplx<T>{P0[k], P1[k]};
-    fft_line<T, N>(v, tw, true);
+    for (int k = 0; k < N; ++k) v[line_slot<N>(k)] = Cplx<T>{P0[k], P1[k]};
+    line_fft<T, N>(v, tw, true);
     Cplx<T>* w = W + (n * nw + j) * n3 + l;
 #pragma unroll
     for (int k = 0; k < N; ++k) w[k * n2] = Cplx<T>{v[k].x * sc, v[k].y * sc};
@@ -272,7 +222,7 @@ __global__ void __launch_bounds__(128) k_vss_lines_sum(const Cplx<T>* __restrict
     __shared__ T tile[LINES * (N + 1)];
     if (threadIdx.x < N) tw[threadIdx.x] = dftw[N + threadIdx.x];
     __syncthreads();
-    const int64_t l0 = (int64_t)blockIdx.x * LINES, l = l0 + threadIdx.x;   // N^2 is a multiple of 64
+    const int64_t l0 = (int64_t)blockIdx.x * LINES, l = l0 + threadIdx.x;
     const int64_t n = blockIdx.y;
     T acc[N];
 #pragma unroll
@@ -284,8 +234,8 @@ __global__ void __launch_bounds__(128) k_vss_lines_sum(const Cplx<T>* __restrict
             for (int s = 0; s < sets; ++s) {
                 const Cplx<T>* z = Z + ((n * sets + s) * npairs + p) * n3 + l;
 #pragma unroll
-                for (int k = 0; k < N; ++k) v[bitrev<N>(k)] = z[k * n2];
-                fft_line<T, N>(v, tw, false);
+                for (int k = 0; k < N; ++k) v[line_slot<N>(k)] = z[k * n2];
+                line_fft<T, N>(v, tw, false);
 #pragma unroll
                 for (int k = 0; k < N; ++k) acc[k] = fma(w * v[k].x, v[k].y, acc[k]);
             }
@@ -345,7 +295,7 @@ cudaError_t planes_launch(const Cplx<T>* Fh, const Cplx<T>* Gh, const Cplx<T>* m
 
 }  // namespace
 
-bool vss_fused_supported(int N, bool fp64) { return N == 8 || N == 16 || (N == 32 && !fp64); }
+bool vss_fused_supported(int N, bool fp64) { return N == 8 || N == 12 || N == 16 || N == 24 || (N == 32 && !fp64); }
 
 template <typename T>
 cudaError_t launch_vss_load_t(const T* f, int N, int64_t nodes, Cplx<T>* X, cudaStream_t s) {
@@ -363,7 +313,9 @@ cudaError_t launch_vss_inverse_planes(const Cplx<T>* Fh, const Cplx<T>* Gh, cons
     if (nodes > 65535) return cudaErrorInvalidValue;
     const int fields = sets * npairs;
     if (N == 8) return planes_launch<T, 8, true>(Fh, Gh, mu_r, dftw, npairs, fields, nodes, Z, s);
+    if (N == 12) return planes_launch<T, 12, true>(Fh, Gh, mu_r, dftw, npairs, fields, nodes, Z, s);
     if (N == 16) return planes_launch<T, 16, true>(Fh, Gh, mu_r, dftw, npairs, fields, nodes, Z, s);
+    if (N == 24) return planes_launch<T, 24, true>(Fh, Gh, mu_r, dftw, npairs, fields, nodes, Z, s);
     if constexpr (sizeof(T) == 4)
         if (N == 32) return planes_launch<T, 32, true>(Fh, Gh, mu_r, dftw, npairs, fields, nodes, Z, s);
     return cudaErrorInvalidValue;
@@ -376,7 +328,9 @@ cudaError_t launch_vss_lines(const Cplx<T>* Z, const Cplx<T>* dftw, int N, int n
     if (nodes > 65535) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)((N * N + 127) / 128), (unsigned)((npairs + 1) / 2), (unsigned)nodes);
     if (N == 8) k_vss_lines<T, 8><<<grid, 128, 0, s>>>(Z, dftw, npairs, sets, W);
+    else if (N == 12) k_vss_lines<T, 12><<<grid, 128, 0, s>>>(Z, dftw, npairs, sets, W);
     else if (N == 16) k_vss_lines<T, 16><<<grid, 128, 0, s>>>(Z, dftw, npairs, sets, W);
+    else if (N == 24) k_vss_lines<T, 24><<<grid, 128, 0, s>>>(Z, dftw, npairs, sets, W);
     else if (sizeof(T) == 4 && N == 32) k_vss_lines<T, sizeof(T) == 4 ? 32 : 16><<<grid, 128, 0, s>>>(Z, dftw, npairs, sets, W);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -388,7 +342,9 @@ cudaError_t launch_vss_forward_planes(const Cplx<T>* dftw, int N, int fields, in
     if (nodes <= 0) return cudaSuccess;
     if (nodes > 65535) return cudaErrorInvalidValue;
     if (N == 8) return planes_launch<T, 8, false>(nullptr, nullptr, nullptr, dftw, 0, fields, nodes, W, s);
+    if (N == 12) return planes_launch<T, 12, false>(nullptr, nullptr, nullptr, dftw, 0, fields, nodes, W, s);
     if (N == 16) return planes_launch<T, 16, false>(nullptr, nullptr, nullptr, dftw, 0, fields, nodes, W, s);
+    if (N == 24) return planes_launch<T, 24, false>(nullptr, nullptr, nullptr, dftw, 0, fields, nodes, W, s);
     if constexpr (sizeof(T) == 4)
         if (N == 32) return planes_launch<T, 32, false>(nullptr, nullptr, nullptr, dftw, 0, fields, nodes, W, s);
     return cudaErrorInvalidValue;
@@ -401,7 +357,9 @@ cudaError_t launch_vss_lines_sum(const Cplx<T>* Z, const Cplx<T>* dftw, const T*
     if (nodes > 65535) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)((N * N + 127) / 128), (unsigned)nodes);
     if (N == 8) k_vss_lines_sum<T, 8><<<grid, 128, 0, s>>>(Z, dftw, wsig, npairs, sets, node_stride, P);
+    else if (N == 12) k_vss_lines_sum<T, 12><<<grid, 128, 0, s>>>(Z, dftw, wsig, npairs, sets, node_stride, P);
     else if (N == 16) k_vss_lines_sum<T, 16><<<grid, 128, 0, s>>>(Z, dftw, wsig, npairs, sets, node_stride, P);
+    else if (N == 24) k_vss_lines_sum<T, 24><<<grid, 128, 0, s>>>(Z, dftw, wsig, npairs, sets, node_stride, P);
     else if (sizeof(T) == 4 && N == 32)
         k_vss_lines_sum<T, sizeof(T) == 4 ? 32 : 16><<<grid, 128, 0, s>>>(Z, dftw, wsig, npairs, sets, node_stride, P);
     else return cudaErrorInvalidValue;
@@ -415,28 +373,6 @@ cudaError_t launch_vss_finalize_t(const Cplx<T>* Y, int yfields, const T* a, con
     if (nodes > 65535) return cudaErrorInvalidValue;
     const int64_t n3 = (int64_t)N * N * N;
     k_vss_finalize_t<T><<<dim3(nblk(n3), (unsigned)nodes), 256, 0, s>>>(Y, yfields, a, c, N, n3, out, flags);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_vss_spectra(const Cplx<T>* Fh, const Cplx<T>* Gh, const Cplx<T>* mu_r, int N, int npairs,
-                               int sets, int64_t nodes, Cplx<T>* Z, cudaStream_t s) {
-    if (nodes <= 0) return cudaSuccess;
-    if (N > 64 || nodes > 65535 || npairs > 65535) return cudaErrorInvalidValue;
-    const int64_t n3 = (int64_t)N * N * N;
-    k_vss_spectra<T><<<dim3(nblk(n3), (unsigned)npairs, (unsigned)nodes), 256, 0, s>>>(Fh, Gh, mu_r, N, npairs, sets,
-                                                                                       n3, Z);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_vss_product(const Cplx<T>* Z, int N, int npairs, int sets, int64_t nodes, Cplx<T>* W,
-                               cudaStream_t s) {
-    if (nodes <= 0) return cudaSuccess;
-    if (nodes > 65535) return cudaErrorInvalidValue;
-    const int64_t n3 = (int64_t)N * N * N;
-    k_vss_product<T><<<dim3(nblk(n3), (unsigned)((npairs + 1) / 2), (unsigned)nodes), 256, 0, s>>>(Z, npairs, sets,
-                                                                                                   n3, W);
     return cudaGetLastError();
 }
 
@@ -461,9 +397,6 @@ cudaError_t launch_vss_loss_init(const Cplx<T>* Ah, const Cplx<T>* Bh, const T* 
 }
 
 #define DGFS_VSS_INST(T)                                                                                          \
-    template cudaError_t launch_vss_spectra<T>(const Cplx<T>*, const Cplx<T>*, const Cplx<T>*, int, int, int,    \
-                                               int64_t, Cplx<T>*, cudaStream_t);                                  \
-    template cudaError_t launch_vss_product<T>(const Cplx<T>*, int, int, int, int64_t, Cplx<T>*, cudaStream_t);  \
     template cudaError_t launch_vss_accumulate<T>(const Cplx<T>*, const T*, int, int, int64_t, T, Cplx<T>*, int, \
                                                   cudaStream_t);                                                  \
     template cudaError_t launch_vss_loss_init<T>(const Cplx<T>*, const Cplx<T>*, const T*, int, int64_t,         \

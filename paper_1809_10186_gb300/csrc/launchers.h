@@ -104,16 +104,10 @@ cudaError_t launch_finalize(int N, int Nrho, const Cplx<T>* Y, int yfields, cons
                             const T* c, const T* G, const int64_t* offs, int64_t nodes, int mode,
                             T* out, int* flags, cudaStream_t s);
 
-// ---- VSS kernel gain (k_vss.cu) -----------------------------------------------------------
-// Z[n][set][p] = mu_s Fh[n] + i conj(mu_s) Gh[n]  (set 0),  conj(mu_s) Fh[n] + i mu_s Gh[n]  (set 1,
-// sets == 2); Gh == nullptr means Gh = Fh. mu_r: [npairs][3][N] complex per-axis multipliers of +s_rp.
-template <typename T>
-cudaError_t launch_vss_spectra(const Cplx<T>* Fh, const Cplx<T>* Gh, const Cplx<T>* mu_r, int N, int npairs,
-                               int sets, int64_t nodes, Cplx<T>* Z, cudaStream_t s);
-// W[n][j] = P_2j + i P_2j+1 with P_p = sum over sets of Re Z Im Z (twice Re Z0 Im Z0 when sets == 1)
-template <typename T>
-cudaError_t launch_vss_product(const Cplx<T>* Z, int N, int npairs, int sets, int64_t nodes, Cplx<T>* W,
-                               cudaStream_t s);
+// ---- VSS kernel gain and Fourier-space translates (k_vss.cu) ------------------------------
+// Every field plane-major [kz][kx][ky]. Translate spectra of sphere point p (mu_r: [npairs][3][N]
+// complex per-axis multipliers of +s_rp): set 0 = mu_s Fh + i conj(mu_s) Gh, set 1 (f != g) =
+// conj(mu_s) Fh + i mu_s Gh; Gh == nullptr means Gh = Fh.
 // Y[n][0] += scale sum_p A_r[p] P^_p, P^_p separated from the packed spectra W by Hermitian symmetry
 template <typename T>
 cudaError_t launch_vss_accumulate(const Cplx<T>* W, const T* A_r, int N, int npairs, int64_t nodes, T scale,
@@ -123,12 +117,12 @@ template <typename T>
 cudaError_t launch_vss_loss_init(const Cplx<T>* Ah, const Cplx<T>* Bh, const T* GL, int N, int64_t nodes,
                                  Cplx<T>* Y, int yfields, cudaStream_t s);
 
-// Fused path (N = 8, 16 and, in FP32, 32), every field plane-major [kz][kx][ky]:
+// N = 8, 12, 16, 24 and, in FP32, 32
 bool vss_fused_supported(int N, bool fp64);
 // X[n] = {f[n], 0} transposed to plane-major (then transformed with launch_dft3)
 template <typename T>
 cudaError_t launch_vss_load_t(const T* f, int N, int64_t nodes, Cplx<T>* X, cudaStream_t s);
-// Z[n][set][p] = inverse x, y transforms of the translate spectra of launch_vss_spectra
+// Z[n][set][p] = inverse x, y transforms of the translate spectra
 template <typename T>
 cudaError_t launch_vss_inverse_planes(const Cplx<T>* Fh, const Cplx<T>* Gh, const Cplx<T>* mu_r, const Cplx<T>* dftw,
                                       int N, int npairs, int sets, int64_t nodes, Cplx<T>* Z, cudaStream_t s);
