@@ -308,9 +308,9 @@ dgfs_status vss_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
     const Cplx<T>* dftw = reinterpret_cast<const Cplx<T>*>(t.dftw);
     for (int64_t n0 = 0; n0 < nodes; n0 += C) {
         const int64_t nn = std::min<int64_t>(C, nodes - n0);
-        cudaError_t e = launch_vss_load_t<T>(a + n0 * n3, N, nn, Fh, s);
+        cudaError_t e = launch_vss_load_t<T>(a + n0 * n3, nullptr, N, nn, Fh, s);
         if (!e) e = launch_dft3<T>(t, Fh, nn, true, s);
-        if (!e && two) e = launch_vss_load_t<T>(b + n0 * n3, N, nn, Gh, s);
+        if (!e && two) e = launch_vss_load_t<T>(b + n0 * n3, nullptr, N, nn, Gh, s);
         if (!e && two) e = launch_dft3<T>(t, Gh, nn, true, s);
         if (!e) e = launch_vss_loss_init<T>(Fh, two ? Gh : Fh, GL, N, nn, Y, yf, s);
         if (e) return cuda_fail(e, "VSS operand transforms");
@@ -338,7 +338,8 @@ dgfs_status vss_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
 // space (k_vss.cu: one complex inverse transform gives T_s f + i T_-s g), in batches of xchunk nodes;
 // the same P as the dense circulant passes of launch_gain_products at a fifth of the arithmetic.
 template <typename T>
-cudaError_t fft_gain_products(dgfs_plan_s* p, const T* f, const T* g, int64_t nodes, T* P, cudaStream_t s) {
+cudaError_t fft_gain_products(dgfs_plan_s* p, const T* f, const T* g, const int64_t* offs, int64_t nodes, T* P,
+                              cudaStream_t s) {
     const DevTables<T>& t = tables<T>(p);
     const int N = t.N, np = t.npairs, Nr = t.Nrho, sets = g ? 2 : 1;
     const int64_t n3 = (int64_t)N * N * N, C = p->xchunk;
@@ -349,9 +350,11 @@ cudaError_t fft_gain_products(dgfs_plan_s* p, const T* f, const T* g, int64_t no
     const Cplx<T>* dftw = reinterpret_cast<const Cplx<T>*>(t.dftw);
     for (int64_t n0 = 0; n0 < nodes; n0 += C) {
         const int64_t nn = std::min<int64_t>(C, nodes - n0);
-        cudaError_t e = launch_vss_load_t<T>(f + n0 * n3, N, nn, Fh, s);
+        cudaError_t e = offs ? launch_vss_load_t<T>(f, offs + n0, N, nn, Fh, s)
+                             : launch_vss_load_t<T>(f + n0 * n3, nullptr, N, nn, Fh, s);
         if (!e) e = launch_dft3<T>(t, Fh, nn, true, s);
-        if (!e && g) e = launch_vss_load_t<T>(g + n0 * n3, N, nn, Gh, s);
+        if (!e && g) e = offs ? launch_vss_load_t<T>(g, offs + n0, N, nn, Gh, s)
+                              : launch_vss_load_t<T>(g + n0 * n3, nullptr, N, nn, Gh, s);
         if (!e && g) e = launch_dft3<T>(t, Gh, nn, true, s);
         for (int r = 0; r < Nr && !e; ++r) {
             e = launch_vss_inverse_planes<T>(Fh, g ? Gh : nullptr, mu + (size_t)r * np * 3 * N, dftw, N, np, sets, nn,
@@ -419,8 +422,8 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
                                     reinterpret_cast<const float*>(gg), offs, nodes,
                                     reinterpret_cast<float*>(P), p->d_flags, s, p->fault);
         p->fault = 0;
-    } else if (p->fftx && !offs) {
-        e = fft_gain_products<T>(p, f, gg, nodes, P, s);
+    } else if (p->fftx) {
+        e = fft_gain_products<T>(p, f, gg, offs, nodes, P, s);
     } else {
         e = launch_gain_products(t, f, gg, offs, nodes, P, s);
     }

@@ -249,15 +249,18 @@ __global__ void __launch_bounds__(128) k_vss_lines_sum(const Cplx<T>* __restrict
     for (int e = threadIdx.x; e < nl * N; e += LINES) out[e] = tile[(e / N) * (N + 1) + e % N];
 }
 
-// X[n][z][x][y] = {f[n][x][y][z], 0}: a real field into a plane-major complex field
+// X[n][z][x][y] = {f[n][x][y][z], 0}: a real field into a plane-major complex field; node n of f
+// starts at offs[n] (offs == nullptr: n N^3)
 template <typename T>
-__global__ void __launch_bounds__(256) k_vss_load_t(const T* __restrict__ f, int N, int64_t n3, Cplx<T>* __restrict__ X) {
+__global__ void __launch_bounds__(256) k_vss_load_t(const T* __restrict__ f, const int64_t* __restrict__ offs, int N,
+                                                    int64_t n3, Cplx<T>* __restrict__ X) {
     const int64_t n = blockIdx.y;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // plane-major index
     if (e >= n3) return;
     const int64_t n2 = (int64_t)N * N;
     const int z = (int)(e / n2), x = (int)((e / N) % N), y = (int)(e % N);
-    X[n * n3 + e] = Cplx<T>{f[n * n3 + ((int64_t)x * N + y) * N + z], T(0)};
+    const int64_t base = offs ? offs[n] : n * n3;
+    X[n * n3 + e] = Cplx<T>{f[base + ((int64_t)x * N + y) * N + z], T(0)};
 }
 
 // out[n][x][y][z] = Re Y0 - a Re Y1 - (c ? c Re Y2 : 0), Y plane-major [n][yfields][z][x][y]
@@ -298,11 +301,11 @@ cudaError_t planes_launch(const Cplx<T>* Fh, const Cplx<T>* Gh, const Cplx<T>* m
 bool vss_fused_supported(int N, bool fp64) { return N == 8 || N == 12 || N == 16 || N == 24 || (N == 32 && !fp64); }
 
 template <typename T>
-cudaError_t launch_vss_load_t(const T* f, int N, int64_t nodes, Cplx<T>* X, cudaStream_t s) {
+cudaError_t launch_vss_load_t(const T* f, const int64_t* offs, int N, int64_t nodes, Cplx<T>* X, cudaStream_t s) {
     if (nodes <= 0) return cudaSuccess;
     if (nodes > 65535) return cudaErrorInvalidValue;
     const int64_t n3 = (int64_t)N * N * N;
-    k_vss_load_t<T><<<dim3(nblk(n3), (unsigned)nodes), 256, 0, s>>>(f, N, n3, X);
+    k_vss_load_t<T><<<dim3(nblk(n3), (unsigned)nodes), 256, 0, s>>>(f, offs, N, n3, X);
     return cudaGetLastError();
 }
 
@@ -401,7 +404,7 @@ cudaError_t launch_vss_loss_init(const Cplx<T>* Ah, const Cplx<T>* Bh, const T* 
                                                   cudaStream_t);                                                  \
     template cudaError_t launch_vss_loss_init<T>(const Cplx<T>*, const Cplx<T>*, const T*, int, int64_t,         \
                                                  Cplx<T>*, int, cudaStream_t);                                    \
-    template cudaError_t launch_vss_load_t<T>(const T*, int, int64_t, Cplx<T>*, cudaStream_t);                    \
+    template cudaError_t launch_vss_load_t<T>(const T*, const int64_t*, int, int64_t, Cplx<T>*, cudaStream_t);                    \
     template cudaError_t launch_vss_inverse_planes<T>(const Cplx<T>*, const Cplx<T>*, const Cplx<T>*,            \
                                                       const Cplx<T>*, int, int, int, int64_t, Cplx<T>*,           \
                                                       cudaStream_t);                                              \

@@ -119,9 +119,10 @@ cudaError_t launch_vss_loss_init(const Cplx<T>* Ah, const Cplx<T>* Bh, const T* 
 
 // N = 8, 12, 16, 24 and, in FP32, 32
 bool vss_fused_supported(int N, bool fp64);
-// X[n] = {f[n], 0} transposed to plane-major (then transformed with launch_dft3)
+// X[n] = {f[n], 0} transposed to plane-major (then transformed with launch_dft3); node n of f at
+// offs[n] (device, or nullptr: n N^3)
 template <typename T>
-cudaError_t launch_vss_load_t(const T* f, int N, int64_t nodes, Cplx<T>* X, cudaStream_t s);
+cudaError_t launch_vss_load_t(const T* f, const int64_t* offs, int N, int64_t nodes, Cplx<T>* X, cudaStream_t s);
 // Z[n][set][p] = inverse x, y transforms of the translate spectra
 template <typename T>
 cudaError_t launch_vss_inverse_planes(const Cplx<T>* Fh, const Cplx<T>* Gh, const Cplx<T>* mu_r, const Cplx<T>* dftw,
