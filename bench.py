@@ -54,6 +54,8 @@ def _args():
                          "workload instead of the headline (prints its own line)")
     ap.add_argument("--vss", action="store_true",
                     help="VSS kernel (alpha = 1.40, argon) on 256 nodes of N = 32, FP32, instead of the headline")
+    ap.add_argument("--ragged", action="store_true",
+                    help="cavity_ragged: 9216 nodes of mixed N (16/24/32) through one graph-captured ragged schedule")
     ap.add_argument("--slab", action="store_true",
                     help="1-D DGFS Fourier heat transfer (10 elements x 3 nodes, N = 24) SSP-RK2 steps")
     ap.add_argument("--slab-profile", type=int, default=0,
@@ -388,6 +390,72 @@ def run_vss(a):
     return 0
 
 
+def run_ragged(a):
+    """The ragged cavity mesh: 9216 near-equilibrium nodes, N in {16, 24, 32} (40/40/20 %), per-node
+    VHS omega in {0.5, 0.74, 0.81}, M = 26; one plan per N (the --prec mode where the tensor cores
+    support the grid, FP32 otherwise), all classes in one dgfs_ragged schedule captured as one CUDA
+    graph and replayed."""
+    import numpy as np
+    import torch
+    from paper_1809_10186_gb300 import binding, workloads as W
+    torch.cuda.set_device(0)
+    cfg = W.CONFIGS["cavity_ragged"]
+    Ns, L, M, B = cfg["Ns"], cfg["L"], cfg["M"], cfg["B"]
+    node_N, node_omega = W.ragged_layout(B, Ns, cfg["split"], cfg["omegas"], cfg["seed"])
+    offs = np.zeros(B, np.int64)
+    offs[1:] = np.cumsum(node_N.astype(np.int64) ** 3)[:-1]
+    packed = np.empty(int(offs[-1] + int(node_N[-1]) ** 3), np.float32)
+    for n in Ns:
+        idx = np.nonzero(node_N == n)[0]
+        fields = W.near_equilibrium(len(idx), n, L, cfg["seed"] + n, dtype=np.float32)
+        for j, i in enumerate(idx):
+            packed[offs[i]:offs[i] + n ** 3] = fields[j].ravel()
+    gam = 2.0 * (1.0 - node_omega)
+    bb = 1.0 / (2.0 ** (3.0 - node_omega) * np.array([math.gamma(2.5 - w) for w in node_omega]) * math.pi)
+    precs = {n: (a.prec if (a.prec in ("fp32",) or n in (16, 32)) else "fp32") for n in Ns}
+    plans = [binding.Plan(N=n, L=L, M=M, N_rho=n, precision=precs[n]) for n in Ns]
+    cls = [list(Ns).index(int(n)) for n in node_N]
+    sched = binding.RaggedSchedule(plans, cls, offs, node_gamma=gam, node_b=bb)
+    x = torch.from_numpy(packed).cuda()
+    y = torch.empty_like(x)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        for _ in range(max(1, a.warmup)):
+            sched.collide(x, out=y, stream=st)
+    torch.cuda.current_stream().wait_stream(st)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        sched.collide(x, out=y, stream=st)
+    g.replay()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    for p in plans:
+        p.stream_status()
+    ms = e0.elapsed_time(e1) / a.steps
+    line = {"metric": "ragged Q(f,f) node-evals/s, cavity mesh 9216 nodes, N in {16,24,32}, one CUDA graph",
+            "value": B / (ms / 1e3), "unit": "node-evals/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "dtype": ",".join("N=%d:%s" % (n, precs[n]) for n in Ns),
+            "data": "synthetic",
+            "config": {"workload": "cavity_ragged: %d nodes, split %s, omegas %s, M=%d, N_rho=N" % (
+                B, cfg["split"], cfg["omegas"], M), "nodes_per_N": {int(n): int(np.sum(node_N == n)) for n in Ns}},
+            "clocks": clocks}
+    print(json.dumps(line))
+    sched.close()
+    for p in plans:
+        p.close()
+    return 0
+
+
 def run_slab(a):
     """SSP-RK2 steps of the 1-D DGFS solver on the Fourier heat-transfer setup: every step is two
     right-hand sides, each the DG element collision term of the 10 elements (90 bilinear Q at N = 24)
@@ -456,6 +524,8 @@ def main():
         return run_vss(a)
     if a.slab:
         return run_slab(a)
+    if a.ragged:
+        return run_ragged(a)
     import numpy as np
     import torch
     from paper_1809_10186_gb300 import binding, workloads as W
