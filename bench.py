@@ -54,6 +54,8 @@ def _args():
                          "workload instead of the headline (prints its own line)")
     ap.add_argument("--vss", action="store_true",
                     help="VSS kernel (alpha = 1.40, argon) on 256 nodes of N = 32, FP32, instead of the headline")
+    ap.add_argument("--grad", action="store_true",
+                    help="grad_n32: JVP, VJP and dQ/dgamma throughput on 512 nodes of N = 32, FP32")
     ap.add_argument("--ragged", action="store_true",
                     help="cavity_ragged: 9216 nodes of mixed N (16/24/32) through one graph-captured ragged schedule")
     ap.add_argument("--slab", action="store_true",
@@ -390,6 +392,50 @@ def run_vss(a):
     return 0
 
 
+def run_grad(a):
+    """Tangent and adjoint of Q(f, f) on the grad_n32 workload (512 two-Maxwellian nodes, N = 32,
+    omega = 0.81, M = 38, FP32): node-evals/s of dgfs_collide_jvp, dgfs_collide_vjp and
+    dgfs_collide_dgamma, each timed over `steps` calls."""
+    import numpy as np
+    import torch
+    from paper_1809_10186_gb300 import binding, workloads as W
+    torch.cuda.set_device(0)
+    cfg = W.CONFIGS["grad_n32"]
+    N, L, B = cfg["N"], cfg["L"], cfg["B"]
+    F, _ = W.two_maxwellian(B, N, L, cfg["seed"], dtype=np.float32)
+    D = W.directions(B, N, cfg["seed"] + 1, dtype=np.float32)
+    f, v = torch.from_numpy(F).cuda(), torch.from_numpy(D).cuda()
+    out = torch.empty_like(f)
+    plan = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=cfg["M"], N_rho=cfg["Nrho"], precision="fp32", max_batch=B)
+    calls = {"jvp": lambda: plan.collide_jvp(f, v, out=out), "vjp": lambda: plan.collide_vjp(f, v, out=out),
+             "dgamma": lambda: plan.collide_dgamma(f, out=out), "collide": lambda: plan.collide(f, out=out)}
+    res = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    for name, call in calls.items():
+        for _ in range(a.warmup):
+            call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.steps):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = B / (e0.elapsed_time(e1) / a.steps / 1e3)
+    clocks = sampler.stop()
+    plan.stream_status()
+    line = {"metric": "VJP node-evals/s (dQ(f,f)/df transposed), N=32 VHS omega=0.81, M=38, FP32", "value": res["vjp"],
+            "unit": "node-evals/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "grad_n32: %d nodes, unit-norm Gaussian directions" % B, "N": N, "M": cfg["M"],
+                       "N_rho": cfg["Nrho"]},
+            "jvp": res["jvp"], "vjp": res["vjp"], "dgamma": res["dgamma"], "collide": res["collide"], "clocks": clocks}
+    print(json.dumps(line))
+    plan.close()
+    return 0
+
+
 def run_ragged(a):
     """The ragged cavity mesh: 9216 near-equilibrium nodes, N in {16, 24, 32} (40/40/20 %), per-node
     VHS omega in {0.5, 0.74, 0.81}, M = 26; one plan per N (the --prec mode where the tensor cores
@@ -526,6 +572,8 @@ def main():
         return run_slab(a)
     if a.ragged:
         return run_ragged(a)
+    if a.grad:
+        return run_grad(a)
     import numpy as np
     import torch
     from paper_1809_10186_gb300 import binding, workloads as W

@@ -368,6 +368,40 @@ cudaError_t fft_gain_products(dgfs_plan_s* p, const T* f, const T* g, const int6
     return cudaSuccess;
 }
 
+// Adjoint gain sum_r G_r (G_r = sum_p 2 w_p [T_-s(U_r T_-s f) + T_s(U_r T_s f)], U[node][r] = K_r u)
+// with the translates and back-translates in Fourier space (k_vss.cu), in batches of xchunk nodes:
+// Gsum [nodes][N^3], standard layout.
+template <typename T>
+cudaError_t fft_vjp_products(dgfs_plan_s* p, const T* f, const T* U, int64_t nodes, T* Gsum, cudaStream_t s) {
+    const DevTables<T>& t = tables<T>(p);
+    const int N = t.N, np = t.npairs, Nr = t.Nrho;
+    const int64_t n3 = (int64_t)N * N * N, C = p->xchunk;
+    Cplx<T>* Fh = reinterpret_cast<Cplx<T>*>(ws(p, p->off_Xt));
+    Cplx<T>* Gh = Fh + C * n3;
+    Cplx<T>* Z = Gh + C * n3;
+    Cplx<T>* W = Z + C * np * n3;
+    const Cplx<T>* mu = static_cast<const Cplx<T>*>(p->d_mu);
+    const Cplx<T>* dftw = reinterpret_cast<const Cplx<T>*>(t.dftw);
+    for (int64_t n0 = 0; n0 < nodes; n0 += C) {
+        const int64_t nn = std::min<int64_t>(C, nodes - n0);
+        cudaError_t e = launch_vss_load_t<T>(f + n0 * n3, nullptr, N, nn, Fh, s);
+        if (!e) e = launch_dft3<T>(t, Fh, nn, true, s);
+        if (!e) e = cudaMemsetAsync(Gh, 0, (size_t)nn * n3 * sizeof(Cplx<T>), s);
+        for (int r = 0; r < Nr && !e; ++r) {
+            const Cplx<T>* mu_r = mu + (size_t)r * np * 3 * N;
+            e = launch_vss_inverse_planes<T>(Fh, nullptr, mu_r, dftw, N, np, 1, nn, Z, s);
+            if (!e) e = launch_vjp_lines<T>(Z, U + n0 * Nr * n3 + (int64_t)r * n3, (int64_t)Nr * n3, dftw, N, np, nn, W, s);
+            if (!e) e = launch_vss_forward_planes<T>(dftw, N, np, nn, W, s);
+            if (!e) e = launch_vjp_accumulate<T>(W, mu_r, t.wsig, N, np, nn, Gh, s);
+        }
+        if (!e) e = launch_dft3<T>(t, Gh, nn, false, s);
+        if (!e) e = launch_vjp_real_t<T>(Gh, N, nn, Gsum + n0 * n3, s);
+        if (e) return e;
+        if (p->prof) p->prof_launches += 4 + 4 * (int64_t)Nr + 4;
+    }
+    return cudaSuccess;
+}
+
 // One chunk of nodes through the whole pipeline. a/b/f_loss are chunk-base pointers.
 template <typename T>
 dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, const int64_t* offs,
@@ -393,10 +427,10 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
         T* S = reinterpret_cast<T*>(ws(p, p->off_S));
         if (offs) return fail(DGFS_ERR_UNSUPPORTED, "vjp with node offsets");
         if (p->prof) {
-            p->prof_launches += 20;
+            p->prof_launches += p->fftx ? 0 : 20;
             p->prof_nodes += nodes;
         }
-        e = launch_vjp_products(t, f, P, nodes, S, G, s);
+        e = p->fftx ? fft_vjp_products<T>(p, f, P, nodes, G, s) : launch_vjp_products(t, f, P, nodes, S, G, s);
         if (e) return cuda_fail(e, "vjp: translate-product kernel");
         // 3) loss: K_L f + i K_L (u f)
         e = launch_load_field<T>(t.N, f, nullptr, offs, nodes, X, xf, 0, 0, s);
@@ -404,7 +438,9 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
         if (!e) e = launch_dft3<T>(t, X, nodes * xf, true, s);
         if (!e) e = launch_loss_pair<T>(t, X, xf, np, nodes, 0, 1, Y, 2, s);
         if (!e) e = launch_dft3<T>(t, Y, nodes * 2, false, s);
-        if (!e) e = launch_finalize<T>(t.N, t.Nrho, Y, 2, g, nullptr, G, offs, nodes, 1, out, p->d_flags, s);
+        // the Fourier-space adjoint leaves the radial sum in G (one field per node)
+        if (!e) e = launch_finalize<T>(t.N, p->fftx ? 1 : t.Nrho, Y, 2, g, nullptr, G, offs, nodes, 1, out, p->d_flags,
+                                       s);
         if (e) return cuda_fail(e, "vjp: loss and finalisation");
         return DGFS_OK;
     }

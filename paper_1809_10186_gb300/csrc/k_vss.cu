@@ -249,6 +249,96 @@ __global__ void __launch_bounds__(128) k_vss_lines_sum(const Cplx<T>* __restrict
     for (int e = threadIdx.x; e < nl * N; e += LINES) out[e] = tile[(e / N) * (N + 1) + e % N];
 }
 
+// Adjoint (VJP) gain in Fourier space, per radial point r:
+//   G_r = sum_p 2 w_p [T_-s(U_r T_-s f) + T_s(U_r T_s f)],   U_r = K_r u,
+// with a + i b = IDFT(mu_s f^ + i mu_-s f^) = T_s f + i T_-s f (k_vss_planes<INV>, one set). The two
+// products share one forward transform, W = DFT(U_r b + i U_r a), and the back-translates are
+// phase multiplies: G^ += 2 w_p [conj(mu_s) (W(k) + conj W(-k)) / 2 + mu_s (W(k) - conj W(-k)) / 2i].
+// k_vjp_lines: per (x, y) line, the U_r line (standard layout, staged through shared memory) times
+// the inverse z transform of every sphere point's line, packed and transformed forward along z.
+// grid (ceil(N^2 / 128), nodes); Z [n][p] and W [n][p] plane-major; U_r = U + n node_stride.
+template <typename T, int N>
+__global__ void __launch_bounds__(128) k_vjp_lines(const Cplx<T>* __restrict__ Z, const T* __restrict__ U,
+                                                   int64_t node_stride, const Cplx<T>* __restrict__ dftw, int npairs,
+                                                   Cplx<T>* __restrict__ W) {
+    constexpr int64_t n2 = (int64_t)N * N, n3 = n2 * N;
+    constexpr int LINES = 128;
+    __shared__ Cplx<T> tw[N];
+    __shared__ T tile[LINES * (N + 1)];
+    const int64_t n = blockIdx.y, l0 = (int64_t)blockIdx.x * LINES, l = l0 + threadIdx.x;
+    const int nl = (int)((n2 - l0) < LINES ? (n2 - l0) : LINES);
+    if (threadIdx.x < N) tw[threadIdx.x] = dftw[N + threadIdx.x];
+    const T* Un = U + n * node_stride + l0 * N;
+    for (int e = threadIdx.x; e < nl * N; e += LINES) tile[(e / N) * (N + 1) + e % N] = Un[e];
+    __syncthreads();
+    if (l >= n2) return;
+    T u[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) u[k] = tile[threadIdx.x * (N + 1) + k];
+    const T sc = T(1) / T(N);
+    Cplx<T> v[N];
+    for (int p = 0; p < npairs; ++p) {
+        const Cplx<T>* z = Z + (n * npairs + p) * n3 + l;
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[line_slot<N>(k)] = z[k * n2];
+        line_fft<T, N>(v, tw, false);
+        Cplx<T> w[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) w[line_slot<N>(k)] = Cplx<T>{u[k] * v[k].y, u[k] * v[k].x};   // U b + i U a
+        line_fft<T, N>(w, tw, true);
+        Cplx<T>* o = W + (n * npairs + p) * n3 + l;
+#pragma unroll
+        for (int k = 0; k < N; ++k) o[k * n2] = Cplx<T>{w[k].x * sc, w[k].y * sc};
+    }
+}
+
+// G^[n](k) += sum_p 2 w_p [conj(mu_s) P1^ + mu_s P2^],  P1^ = (W + conj W(-k)) / 2,
+// P2^ = (W - conj W(-k)) / 2i; mu_r: [npairs][3][N] per-axis multipliers; plane-major index.
+// grid (ceil(n3 / 256), nodes); dynamic shared memory: npairs 3 N complex
+template <typename T>
+__global__ void __launch_bounds__(256) k_vjp_accumulate(const Cplx<T>* __restrict__ W, const Cplx<T>* __restrict__ mu_r,
+                                                        const T* __restrict__ wsig, int N, int npairs, int64_t n3,
+                                                        Cplx<T>* __restrict__ Gh) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    Cplx<T>* m = reinterpret_cast<Cplx<T>*>(sm_raw);
+    for (int i = threadIdx.x; i < npairs * 3 * N; i += blockDim.x) m[i] = mu_r[i];
+    __syncthreads();
+    const int64_t n = blockIdx.y;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n3) return;
+    const int kz = (int)(e / ((int64_t)N * N)), kx = (int)((e / N) % N), ky = (int)(e % N);
+    const int64_t em = ((int64_t)((N - kz) % N) * N + (N - kx) % N) * N + (N - ky) % N;
+    T re = 0, im = 0;
+    for (int p = 0; p < npairs; ++p) {
+        const Cplx<T>* mp = m + p * 3 * N;
+        const Cplx<T> a = mp[kx], b = mp[N + ky], c = mp[2 * N + kz];
+        const Cplx<T> ab{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+        const Cplx<T> mu{ab.x * c.x - ab.y * c.y, ab.x * c.y + ab.y * c.x};
+        const Cplx<T> w = W[(n * npairs + p) * n3 + e], wm = W[(n * npairs + p) * n3 + em];
+        const Cplx<T> p1{T(0.5) * (w.x + wm.x), T(0.5) * (w.y - wm.y)};
+        const Cplx<T> p2{T(0.5) * (w.y + wm.y), T(-0.5) * (w.x - wm.x)};
+        const T two_w = T(2) * wsig[p];
+        // conj(mu) p1 + mu p2
+        re = fma(two_w, (mu.x * p1.x + mu.y * p1.y) + (mu.x * p2.x - mu.y * p2.y), re);
+        im = fma(two_w, (mu.x * p1.y - mu.y * p1.x) + (mu.x * p2.y + mu.y * p2.x), im);
+    }
+    Cplx<T>& g = Gh[n * n3 + e];
+    g.x += re;
+    g.y += im;
+}
+
+// out[n][x][y][z] = Re Gt[n][z][x][y]
+template <typename T>
+__global__ void __launch_bounds__(256) k_vjp_real_t(const Cplx<T>* __restrict__ Gt, int N, int64_t n3,
+                                                    T* __restrict__ out) {
+    const int64_t n = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    const int64_t n2 = (int64_t)N * N;
+    const int x = (int)(i / n2), y = (int)((i / N) % N), z = (int)(i % N);
+    out[n * n3 + i] = Gt[n * n3 + ((int64_t)z * N + x) * N + y].x;
+}
+
 // X[n][z][x][y] = {f[n][x][y][z], 0}: a real field into a plane-major complex field; node n of f
 // starts at offs[n] (offs == nullptr: n N^3)
 template <typename T>
@@ -370,6 +460,47 @@ cudaError_t launch_vss_lines_sum(const Cplx<T>* Z, const Cplx<T>* dftw, const T*
 }
 
 template <typename T>
+cudaError_t launch_vjp_lines(const Cplx<T>* Z, const T* U, int64_t node_stride, const Cplx<T>* dftw, int N,
+                             int npairs, int64_t nodes, Cplx<T>* W, cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    if (nodes > 65535) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((N * N + 127) / 128), (unsigned)nodes);
+    if (N == 8) k_vjp_lines<T, 8><<<grid, 128, 0, s>>>(Z, U, node_stride, dftw, npairs, W);
+    else if (N == 12) k_vjp_lines<T, 12><<<grid, 128, 0, s>>>(Z, U, node_stride, dftw, npairs, W);
+    else if (N == 16) k_vjp_lines<T, 16><<<grid, 128, 0, s>>>(Z, U, node_stride, dftw, npairs, W);
+    else if (N == 24) k_vjp_lines<T, 24><<<grid, 128, 0, s>>>(Z, U, node_stride, dftw, npairs, W);
+    else if (sizeof(T) == 4 && N == 32)
+        k_vjp_lines<T, sizeof(T) == 4 ? 32 : 16><<<grid, 128, 0, s>>>(Z, U, node_stride, dftw, npairs, W);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_vjp_accumulate(const Cplx<T>* W, const Cplx<T>* mu_r, const T* wsig, int N, int npairs,
+                                  int64_t nodes, Cplx<T>* Gh, cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    if (nodes > 65535) return cudaErrorInvalidValue;
+    const int64_t n3 = (int64_t)N * N * N;
+    const size_t sm = (size_t)npairs * 3 * N * sizeof(Cplx<T>);
+    if (sm > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_vjp_accumulate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    k_vjp_accumulate<T><<<dim3(nblk(n3), (unsigned)nodes), 256, sm, s>>>(W, mu_r, wsig, N, npairs, n3, Gh);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_vjp_real_t(const Cplx<T>* Gt, int N, int64_t nodes, T* out, cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    if (nodes > 65535) return cudaErrorInvalidValue;
+    const int64_t n3 = (int64_t)N * N * N;
+    k_vjp_real_t<T><<<dim3(nblk(n3), (unsigned)nodes), 256, 0, s>>>(Gt, N, n3, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_vss_finalize_t(const Cplx<T>* Y, int yfields, const T* a, const T* c, int N, int64_t nodes, T* out,
                                   int* flags, cudaStream_t s) {
     if (nodes <= 0) return cudaSuccess;
@@ -413,6 +544,11 @@ cudaError_t launch_vss_loss_init(const Cplx<T>* Ah, const Cplx<T>* Bh, const T* 
     template cudaError_t launch_vss_forward_planes<T>(const Cplx<T>*, int, int, int64_t, Cplx<T>*, cudaStream_t); \
     template cudaError_t launch_vss_finalize_t<T>(const Cplx<T>*, int, const T*, const T*, int, int64_t, T*,     \
                                                   int*, cudaStream_t);                                            \
+    template cudaError_t launch_vjp_lines<T>(const Cplx<T>*, const T*, int64_t, const Cplx<T>*, int, int, int64_t, \
+                                             Cplx<T>*, cudaStream_t);                                             \
+    template cudaError_t launch_vjp_accumulate<T>(const Cplx<T>*, const Cplx<T>*, const T*, int, int, int64_t,     \
+                                                  Cplx<T>*, cudaStream_t);                                        \
+    template cudaError_t launch_vjp_real_t<T>(const Cplx<T>*, int, int64_t, T*, cudaStream_t);                    \
     template cudaError_t launch_vss_lines_sum<T>(const Cplx<T>*, const Cplx<T>*, const T*, int, int, int, int64_t, \
                                                  int64_t, T*, cudaStream_t);
 DGFS_VSS_INST(float)

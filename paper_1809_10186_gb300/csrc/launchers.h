@@ -139,6 +139,17 @@ cudaError_t launch_vss_forward_planes(const Cplx<T>* dftw, int N, int fields, in
 template <typename T>
 cudaError_t launch_vss_lines_sum(const Cplx<T>* Z, const Cplx<T>* dftw, const T* wsig, int N, int npairs, int sets,
                                  int64_t nodes, int64_t node_stride, T* P, cudaStream_t s);
+// adjoint gain in Fourier space (see k_vss.cu): W[n][p] = DFT_z(U_r b + i U_r a) of the translate lines,
+// G^[n] += sum_p 2 w_p [conj(mu_s) P1^ + mu_s P2^], and the real part of the transformed-back G^ in the
+// standard layout
+template <typename T>
+cudaError_t launch_vjp_lines(const Cplx<T>* Z, const T* U, int64_t node_stride, const Cplx<T>* dftw, int N,
+                             int npairs, int64_t nodes, Cplx<T>* W, cudaStream_t s);
+template <typename T>
+cudaError_t launch_vjp_accumulate(const Cplx<T>* W, const Cplx<T>* mu_r, const T* wsig, int N, int npairs,
+                                  int64_t nodes, Cplx<T>* Gh, cudaStream_t s);
+template <typename T>
+cudaError_t launch_vjp_real_t(const Cplx<T>* Gt, int N, int64_t nodes, T* out, cudaStream_t s);
 // out (standard layout) = Re Y0 - a Re Y1 - (c ? c Re Y2 : 0), Y plane-major
 template <typename T>
 cudaError_t launch_vss_finalize_t(const Cplx<T>* Y, int yfields, const T* a, const T* c, int N, int64_t nodes, T* out,
