@@ -3,7 +3,9 @@
 // A plan owns: the FP64 host plan (plan_host.cpp), the device tables rounded to the compute
 // type, one device workspace sized for a chunk of nodes, and a device flag word. Every
 // compute call loops over node chunks and enqueues, per chunk,
-//   1. the translate-product kernel            P_r = sum_p w_p [(T_s f)(T_-s g) + (T_-s f)(T_s g)]
+//   1. the translate products                  P_r = sum_p w_p [(T_s f)(T_-s g) + (T_-s f)(T_s g)]
+//      (tensor cores for F16S/BF16S, tc_gain.cu; Fourier-space translates for FP32/FP64, k_vss.cu;
+//      the dense circulant kernel, k_gain_simt.cuh, for the allocation-free call)
 //   2. the radial projection                   X_s = sum_r Vr[s][r] w_r rho_r P_r
 //   3. forward DFTs of X_s and the loss operand
 //   4. the Fourier combine                     sum_s Uk[s] X^_s + i G_loss g^
