@@ -4,8 +4,9 @@
 // type, one device workspace sized for a chunk of nodes, and a device flag word. Every
 // compute call loops over node chunks and enqueues, per chunk,
 //   1. the translate products                  P_r = sum_p w_p [(T_s f)(T_-s g) + (T_-s f)(T_s g)]
-//      (tensor cores for F16S/BF16S, tc_gain.cu; Fourier-space translates for FP32/FP64, k_vss.cu;
-//      the dense circulant kernel, k_gain_simt.cuh, for the allocation-free call)
+//      (tensor cores for Q(f, f) of F16S/BF16S plans, tc_gain.cu; Fourier-space translates for every
+//      other call, k_vss.cu; the dense circulant kernel, k_gain_simt.cuh, for the allocation-free
+//      call of FP32/FP64 plans)
 //   2. the radial projection                   X_s = sum_r Vr[s][r] w_r rho_r P_r
 //   3. forward DFTs of X_s and the loss operand
 //   4. the Fourier combine                     sum_s Uk[s] X^_s + i G_loss g^
@@ -603,7 +604,9 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
             p->vchunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(C, (int64_t)(((size_t)1536 << 20) / zw)), 65535));
         }
     }
-    p->fftx = !is_tc(p->prec) && !p->hp.aniso && vss_fused_supported(p->hp.N, p->prec == DGFS_PREC_FP64);
+    // tensor-core plans keep their kernel for Q(f, f) and dQ/dgamma; their bilinear calls (Q(f, g),
+    // the JVP) and the VJP take the Fourier-space translates in FP32 like the FP32 plans
+    p->fftx = !p->hp.aniso && vss_fused_supported(p->hp.N, p->prec == DGFS_PREC_FP64);
     if (p->fftx) {
         // transform batches of about 1.5 GB of operand and translate spectra
         const size_t n3 = (size_t)p->hp.N * p->hp.N * p->hp.N;

@@ -1,7 +1,7 @@
 // CUDA-core (FP32 / FP64) kernels of the gain's translate-product-accumulate step as dense
-// circulant passes. The library's FP32/FP64 calls take their translates in Fourier space
-// (k_vss.cu, a fifth of the arithmetic); these kernels serve the allocation-free call and the
-// adjoint of the tensor-core precisions.
+// circulant passes. The library's CUDA-core calls take their translates in Fourier space
+// (k_vss.cu, a fifth of the arithmetic); these kernels serve the allocation-free call of FP32/FP64
+// plans.
 //
 // For every node and radial Gauss-Legendre point c_r this computes
 //   P_r = sum_{pairs p} w_p [ (T_s f)(T_{-s} g) + (T_{-s} f)(T_s g) ],   s = c_r sigma_p / 2,

@@ -104,6 +104,30 @@ def test_vjp_small(prec):
         assert np.linalg.norm(gf[i] - ref) / np.linalg.norm(ref) < 10 * TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["f16s", "bf16s"])
+def test_tensor_core_plans_bilinear_and_adjoint_calls(prec):
+    """Tensor-core plans run Q(f, f) and dQ/dgamma on the tensor cores and their bilinear calls
+    (Q(f, g), the JVP) and the VJP through the FP32 Fourier-space translates: FP32 accuracy there."""
+    N, L, gamma, M = 16, 5.0, 0.38, 12
+    F, G = _as_input(W.rough(2, N, 27), "fp32"), _as_input(W.rough(2, N, 28) - 0.5, "fp32")
+    plan = binding.Plan(N=N, L=L, gamma=gamma, M=M, N_rho=8, precision=prec)
+    op = O.OraclePlan(N, L, gamma=gamma, M=M, Nrho=8, nyquist="sym")
+    f, g = _dev(F, "fp32"), _dev(G, "fp32")
+    q2 = plan.collide2(f, g).double().cpu().numpy()
+    jv = plan.collide_jvp(f, g).double().cpu().numpy()
+    gf = plan.collide_vjp(f, g).double().cpu().numpy()
+    qq = plan.collide(f).double().cpu().numpy()
+    plan.stream_status()
+    for i in range(2):
+        scale = np.linalg.norm(np.real(O.loss_Q(op, F[i], G[i])))
+        assert np.linalg.norm(q2[i] - O.fast_Q(op, F[i], G[i])) / scale < TOL["fp32"]
+        assert np.linalg.norm(jv[i] - O.jvp(op, F[i], G[i])) / scale < TOL["fp32"]
+        ref = O.vjp(op, F[i], G[i])
+        assert np.linalg.norm(gf[i] - ref) / np.linalg.norm(ref) < 10 * TOL["fp32"]
+        e, _ = _errors(qq[i], O.fast_Q(op, F[i]), np.real(O.loss_Q(op, F[i], F[i])))
+        assert e < TOL[prec]
+
+
 # ---- the workload configurations -------------------------------------------------------------
 
 def test_bkw_single_node_fp64():
