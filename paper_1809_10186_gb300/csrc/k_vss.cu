@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(PlaneGeo<T, N>::NT)
         for (int kx = 0; kx < N; ++kx) {
             const Cplx<T> mx = m[kx];
             const T a = mx.x * myz.x - mx.y * myz.y, b = sgn * (mx.x * myz.y + mx.y * myz.x);
-            const Cplx<T> fv = Fp[kx * N], gv = Gp[kx * N];
+            const Cplx<T> fv = Fp[kx * N];
+            const Cplx<T> gv = Gh ? Gp[kx * N] : fv;   // g = f: one load
             v[line_slot<N>(kx)] = Cplx<T>{a * fv.x - b * fv.y - a * gv.y + b * gv.x, a * fv.y + b * fv.x + a * gv.x + b * gv.y};
         }
     } else {
