@@ -161,3 +161,18 @@ def test_slab_unsteady_walls_match_oracle():
     plan.stream_status()
     G = ref.ssp_rk2(G, dt, 2)
     assert np.linalg.norm(f.cpu().numpy() - G) / np.linalg.norm(G) < 1e-12
+
+
+def test_slab_single_element_between_walls():
+    """I = 1: both faces of the only element are walls."""
+    N, L, K = 8, 4.0, 4
+    edges = [0.0, 1.0]
+    wl, wr = (0.0, 0.2, 0.0, 0.9), (0.0, -0.1, 0.0, 1.2)
+    plan = binding.Plan(N=N, L=L, gamma=0.2, M=12, N_rho=6, precision="fp64")
+    slab = binding.Slab(plan, K, edges, 0.6, wl, wr)
+    op = O.OraclePlan(N, L, gamma=0.2, M=12, Nrho=6, nyquist="sym")
+    F = _state(op, 1, K, 61, "fp64")
+    got = slab.rhs(_dev(F, "fp64")).cpu().numpy()
+    plan.stream_status()
+    ref = SL.SlabOracle(op, K, edges, 0.6, wl, wr, svd_tol=0.0).rhs(F)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < TOL["fp64"]

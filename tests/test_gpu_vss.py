@@ -175,3 +175,14 @@ def test_vss_unsupported_calls_are_rejected():
     q = plan.collide(f)
     plan.stream_status()
     assert torch.isfinite(q).all()
+
+
+def test_vss_empty_batch_and_single_node():
+    plan = binding.Plan(N=8, L=3.0, alpha=1.7, M=6, N_rho=4, precision="fp64")
+    empty = torch.empty(0, 8, 8, 8, dtype=torch.float64, device="cuda")
+    assert plan.collide(empty).shape == (0, 8, 8, 8)
+    F = _as_input(W.rough(1, 8, 71), "fp64")
+    q = plan.collide(_dev(F, "fp64")).cpu().numpy()
+    plan.stream_status()
+    op = V.VSSPlan(8, 3.0, gamma=0.0, alpha=1.7, M=6, Nrho=4, nyquist="sym")
+    assert _err(q[0], V.fast_Q_vss(op, F[0]), F[0], F[0], op) < TOL["fp64"]
