@@ -91,7 +91,8 @@ typedef struct {
     int precision;             /* dgfs_precision                                               */
     int loss_mode;             /* dgfs_loss_mode                                               */
     int64_t max_batch;         /* nodes processed per internal chunk (sizes the workspace:
-                                  about 22 MB per node at N = 32, rank 19); <= 0: chosen by the library
+                                  about 11 MB per node at N = 32, rank 19, plus up to 1.5 GB of
+                                  transform batches); <= 0: chosen by the library
                                   (about 1.5 GB of workspace). Compute calls accept any B >= 0. */
     double alpha;              /* VSS scattering parameter of eq. B_gen, in [1, 2]; 0 or 1: VHS.
                                   alpha != 1 keeps the sphere point in the kernel factor

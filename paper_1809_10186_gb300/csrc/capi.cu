@@ -70,7 +70,7 @@ struct dgfs_plan_s {
     DevTables<double> td{};
     TcTables tc{};           // tensor-core translate tables (16-bit precisions only)
     // workspace carve (byte offsets into d_ws)
-    size_t off_P = 0, off_G = 0, off_S = 0, off_X = 0, off_Y = 0, off_io = 0, off_node = 0;
+    size_t off_P = 0, off_G = 0, off_X = 0, off_Y = 0, off_io = 0, off_node = 0;
     // VSS kernel: nodes per transform batch, its workspace region and the device tables
     int64_t vchunk = 0;
     bool vss_planes = false;   // fused plane/line kernels, plane-major fields and tables
@@ -135,15 +135,14 @@ void workspace_layout(dgfs_plan_s* p, int64_t C) {
     auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 256); return o; };
     if (p->hp.aniso) {
         p->off_V = take((size_t)p->vchunk * vss_node_bytes(p->hp, p->prec));
-        p->off_P = p->off_G = p->off_S = p->off_X = p->off_Y = p->off_V;
+        p->off_P = p->off_G = p->off_X = p->off_Y = p->off_V;
         p->off_io = take(C * 2 * n3 * es);
         p->off_node = take(C * (sizeof(int64_t) + 2 * sizeof(double)));
         p->ws_bytes = off;
         return;
     }
     p->off_P = take(C * Nr * n3 * es);                 // P_r (also K_r u for the VJP)
-    p->off_G = take(C * Nr * n3 * es);                 // VJP per-radial outputs
-    p->off_S = take(C * Nr * 2 * n3 * es);             // VJP scratch
+    p->off_G = take(C * n3 * es);                      // VJP: the gain's radial sum
     p->off_X = take(C * (size_t)p->xfields * n3 * 2 * es);
     p->off_Y = take(C * 3 * n3 * 2 * es);
     p->off_io = take(C * 2 * n3 * es);                 // host-buffer staging (f in, Q out)
@@ -425,16 +424,13 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
         if (!e) e = launch_dft3<T>(t, X, nodes * xf, false, s);
         if (!e) e = launch_expand_radial<T>(t, X, xf, np, nodes, P, s);
         if (e) return cuda_fail(e, "vjp: radial multipliers");
-        // 2) adjoint translate-product
+        // 2) adjoint translate-products, summed over r, with the translates in Fourier space
         T* G = reinterpret_cast<T*>(ws(p, p->off_G));
-        T* S = reinterpret_cast<T*>(ws(p, p->off_S));
         if (offs) return fail(DGFS_ERR_UNSUPPORTED, "vjp with node offsets");
-        if (p->prof) {
-            p->prof_launches += p->fftx ? 0 : 20;
-            p->prof_nodes += nodes;
-        }
-        e = p->fftx ? fft_vjp_products<T>(p, f, P, nodes, G, s) : launch_vjp_products(t, f, P, nodes, S, G, s);
-        if (e) return cuda_fail(e, "vjp: translate-product kernel");
+        if (!p->fftx) return fail(DGFS_ERR_UNSUPPORTED, "vjp: no Fourier-space translates for this plan");
+        if (p->prof) p->prof_nodes += nodes;
+        e = fft_vjp_products<T>(p, f, P, nodes, G, s);
+        if (e) return cuda_fail(e, "vjp: translate-product kernels");
         // 3) loss: K_L f + i K_L (u f)
         e = launch_load_field<T>(t.N, f, nullptr, offs, nodes, X, xf, 0, 0, s);
         if (!e) e = launch_load_field<T>(t.N, f, g, offs, nodes, X, xf, 1, 0, s);
@@ -442,8 +438,7 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
         if (!e) e = launch_loss_pair<T>(t, X, xf, np, nodes, 0, 1, Y, 2, s);
         if (!e) e = launch_dft3<T>(t, Y, nodes * 2, false, s);
         // the Fourier-space adjoint leaves the radial sum in G (one field per node)
-        if (!e) e = launch_finalize<T>(t.N, p->fftx ? 1 : t.Nrho, Y, 2, g, nullptr, G, offs, nodes, 1, out, p->d_flags,
-                                       s);
+        if (!e) e = launch_finalize<T>(t.N, 1, Y, 2, g, nullptr, G, offs, nodes, 1, out, p->d_flags, s);
         if (e) return cuda_fail(e, "vjp: loss and finalisation");
         return DGFS_OK;
     }

@@ -23,16 +23,5 @@ cudaError_t launch_gain_products(const DevTables<float>& t, const float* f, cons
     return g ? dispatch_gp<2>(t, f, g, offs, nodes, P, s) : dispatch_gp<1>(t, f, nullptr, offs, nodes, P, s);
 }
 
-cudaError_t launch_vjp_products(const DevTables<float>& t, const float* f, const float* U, int64_t nodes,
-                                     float* scratch, float* out, cudaStream_t s) {
-    if (nodes <= 0) return cudaSuccess;
-    switch (t.N) {
-        case 8: return simt::launch_vjp_n<8, float>(t, f, U, nodes, scratch, out, s);
-        case 16: return simt::launch_vjp_n<16, float>(t, f, U, nodes, scratch, out, s);
-        case 24: return simt::launch_vjp_n<24, float>(t, f, U, nodes, scratch, out, s);
-        case 32: return simt::launch_vjp_n<32, float>(t, f, U, nodes, scratch, out, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
 
 }  // namespace dgfs

@@ -22,15 +22,5 @@ cudaError_t launch_gain_products(const DevTables<double>& t, const double* f, co
     return g ? dispatch_gp<2>(t, f, g, offs, nodes, P, s) : dispatch_gp<1>(t, f, nullptr, offs, nodes, P, s);
 }
 
-cudaError_t launch_vjp_products(const DevTables<double>& t, const double* f, const double* U, int64_t nodes,
-                                     double* scratch, double* out, cudaStream_t s) {
-    if (nodes <= 0) return cudaSuccess;
-    switch (t.N) {
-        case 8: return simt::launch_vjp_n<8, double>(t, f, U, nodes, scratch, out, s);
-        case 16: return simt::launch_vjp_n<16, double>(t, f, U, nodes, scratch, out, s);
-        case 24: return simt::launch_vjp_n<24, double>(t, f, U, nodes, scratch, out, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
 
 }  // namespace dgfs

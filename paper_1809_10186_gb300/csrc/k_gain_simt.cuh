@@ -210,146 +210,5 @@ cudaError_t launch_gp(const DevTables<T>& t, const T* f, const T* g, const int64
     return cudaSuccess;
 }
 
-// ---- adjoint of the translate-product step (VJP) ---------------------------------------
-//
-// out_r = sum_pairs 2 w_p [ T_s(U_r . T_s f) + T_{-s}(U_r . T_{-s} f) ], U_r = K_r u.
-// One CTA per (radial point, node). Per pair: phase A writes Y_+- = U_r . T_{+-s} f to the
-// CTA's scratch; phase B translates Y_+ by +s and Y_- by -s and adds them into out_r.
-// Each element of scratch and out_r is owned by exactly one thread per phase.
-template <int N, typename T>
-__device__ __forceinline__ void xpass_two(const T* __restrict__ srcP, const T* __restrict__ srcM,
-                                          const T* __restrict__ XF, int x0, T* __restrict__ Zb,
-                                          int tid) {
-    constexpr int XC = Cfg<N, T>::XC;
-    constexpr int N2 = N * N;
-    constexpr int ZV = N / XC;
-    constexpr int ZG = N / ZV;
-    const int py = tid / ZG, pz0 = (tid % ZG) * ZV;
-#pragma unroll
-    for (int sg = 0; sg < 2; ++sg) {
-        const T* src = (sg == 0 ? srcP : srcM) + py * N + pz0;
-        T za[XC][ZV];
-#pragma unroll
-        for (int l = 0; l < XC; ++l)
-#pragma unroll
-            for (int v = 0; v < ZV; ++v) za[l][v] = T(0);
-#pragma unroll 2
-        for (int x = 0; x < N; ++x) {
-            T val[ZV];
-#pragma unroll
-            for (int v = 0; v < ZV; ++v) val[v] = src[(size_t)x * N2 + v];
-#pragma unroll
-            for (int l = 0; l < XC; ++l) {
-                const T a = XF[sg * N2 + x * N + x0 + l];
-#pragma unroll
-                for (int v = 0; v < ZV; ++v) za[l][v] = fma(a, val[v], za[l][v]);
-            }
-        }
-#pragma unroll
-        for (int l = 0; l < XC; ++l)
-#pragma unroll
-            for (int v = 0; v < ZV; ++v) Zb[((sg * XC + l) * N + py) * N + pz0 + v] = za[l][v];
-    }
-}
-
-template <int N, typename T>
-__global__ void __launch_bounds__(Cfg<N, T>::XC * N)
-k_vjp_products(const T* __restrict__ f, const T* __restrict__ U, const T* __restrict__ filt,
-               const T* __restrict__ wsig, int npairs, int Nrho, T* __restrict__ scratch,
-               T* __restrict__ out) {
-    constexpr int XC = Cfg<N, T>::XC;
-    constexpr int NT = XC * N;
-    constexpr int N2 = N * N;
-    constexpr int64_t N3 = (int64_t)N * N2;
-    const int r = blockIdx.x;
-    const int64_t node = blockIdx.y;
-    const T* fb = f + node * N3;
-    const T* Ur = U + (node * Nrho + r) * N3;
-    T* Yp = scratch + ((node * Nrho + r) * 2) * N3;
-    T* Ym = Yp + N3;
-    T* Or = out + (node * Nrho + r) * N3;
-
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* XF = reinterpret_cast<T*>(smem_raw);   // [2][N][N]: XF[sg][x][x'] = A_sg[x'][x]
-    T* YM = XF + 2 * N2;                       // [2][N][N]: YM[sg][y][y'] = A_sg[y'][y]
-    T* ZM = YM + 2 * N2;                       // [2][N][N]: ZM[sg][z'][z] = A_sg[z'][z]
-    T* Zb = ZM + 2 * N2;                       // [2][XC][N][N]
-
-    const int tid = threadIdx.x;
-    const int xl = tid / N, yp = tid % N;
-    for (int64_t e = tid; e < N3; e += NT) Or[e] = T(0);
-
-    for (int p = 0; p < npairs; ++p) {
-        const T* fl = filt + ((size_t)r * npairs + p) * 3 * N;
-        __syncthreads();
-        for (int e = tid; e < N2; e += NT) {
-            const int i = e / N, j = e % N;
-            const int dij = (i - j + N) % N, dji = (j - i + N) % N;
-            XF[j * N + i] = fl[dij];
-            XF[N2 + j * N + i] = fl[dji];
-            YM[j * N + i] = fl[N + dij];
-            YM[N2 + j * N + i] = fl[N + dji];
-            ZM[i * N + j] = fl[2 * N + dij];
-            ZM[N2 + i * N + j] = fl[2 * N + dji];
-        }
-        __syncthreads();
-        const T w2 = T(2) * wsig[p];
-        // phase A: Y_+- = U_r . T_{+-s} f
-        for (int x0 = 0; x0 < N; x0 += XC) {
-            xpass_two<N, T>(fb, fb, XF, x0, Zb, tid);
-            __syncthreads();
-            const size_t row = (size_t)(x0 + xl) * N2 + (size_t)yp * N;
-#pragma unroll
-            for (int sg = 0; sg < 2; ++sg) {
-                T Y[N];
-                ypass<N, T>(Zb + (size_t)(sg * XC + xl) * N2, YM + sg * N2, yp, Y);
-                T* dst = (sg == 0 ? Yp : Ym) + row;
-#pragma unroll
-                for (int z = 0; z < N; ++z) dst[z] = Ur[row + z] * zdot<N, T>(ZM + sg * N2 + z * N, Y);
-            }
-            __syncthreads();
-        }
-        // phase B: out_r += 2 w_p (T_s Y_+ + T_{-s} Y_-)
-        for (int x0 = 0; x0 < N; x0 += XC) {
-            xpass_two<N, T>(Yp, Ym, XF, x0, Zb, tid);
-            __syncthreads();
-            const size_t row = (size_t)(x0 + xl) * N2 + (size_t)yp * N;
-            T acc[N];
-#pragma unroll
-            for (int z = 0; z < N; ++z) acc[z] = T(0);
-#pragma unroll
-            for (int sg = 0; sg < 2; ++sg) {
-                T Y[N];
-                ypass<N, T>(Zb + (size_t)(sg * XC + xl) * N2, YM + sg * N2, yp, Y);
-#pragma unroll
-                for (int z = 0; z < N; ++z) acc[z] += zdot<N, T>(ZM + sg * N2 + z * N, Y);
-            }
-#pragma unroll
-            for (int z = 0; z < N; ++z) Or[row + z] = fma(w2, acc[z], Or[row + z]);
-            __syncthreads();
-        }
-    }
-}
-
-template <int N, typename T>
-cudaError_t launch_vjp_n(const DevTables<T>& t, const T* f, const T* U, int64_t nodes, T* scratch,
-                         T* out, cudaStream_t s) {
-    constexpr int XC = Cfg<N, T>::XC;
-    constexpr size_t sm = sizeof(T) * (size_t)(6 * N * N + 2 * XC * N * N);
-    auto kern = k_vjp_products<N, T>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    for (int64_t n0 = 0; n0 < nodes; n0 += 65535) {
-        const int64_t nn = nodes - n0 < 65535 ? nodes - n0 : 65535;
-        const int64_t n3 = (int64_t)N * N * N;
-        kern<<<dim3(t.Nrho, (unsigned)nn), XC * N, sm, s>>>(f + n0 * n3, U + n0 * t.Nrho * n3, t.filt, t.wsig,
-                                                           t.npairs, t.Nrho, scratch + n0 * t.Nrho * 2 * n3,
-                                                           out + n0 * t.Nrho * n3);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
 }  // namespace simt
 }  // namespace dgfs

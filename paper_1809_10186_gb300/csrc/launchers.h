@@ -40,13 +40,6 @@ cudaError_t launch_gain_products(const DevTables<float>& t, const float* f, cons
 cudaError_t launch_gain_products(const DevTables<double>& t, const double* f, const double* g,
                                  const int64_t* offs, int64_t nodes, double* P, cudaStream_t s);
 
-// VJP gain part: out[node][r][N^3] = sum_pairs 2 w_p [T_-s(U_r T_-s f) + T_s(U_r T_s f)],
-// with U[node][r][N^3] = K_r u given; scratch: [nodes][Nrho][2][N^3].
-cudaError_t launch_vjp_products(const DevTables<float>& t, const float* f, const float* U,
-                                int64_t nodes, float* scratch, float* out, cudaStream_t s);
-cudaError_t launch_vjp_products(const DevTables<double>& t, const double* f, const double* U,
-                                int64_t nodes, double* scratch, double* out, cudaStream_t s);
-
 // ---- Fourier-side kernels -------------------------------------------------------------
 template <typename T>
 struct Cplx { T x, y; };
