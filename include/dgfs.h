@@ -57,7 +57,8 @@ typedef enum {
 } dgfs_status;
 
 typedef enum {
-    DGFS_PREC_FP64 = 0,   /* CUDA-core FP64 everywhere (reference-accuracy mode; N <= 24)          */
+    DGFS_PREC_FP64 = 0,   /* CUDA-core FP64 everywhere (reference-accuracy mode; the VSS kernel
+                             and dgfs_collide_noalloc up to N = 24)                                  */
     DGFS_PREC_FP32 = 1,   /* CUDA-core FP32 everywhere                                              */
     DGFS_PREC_F16S = 2,   /* translates on tcgen05 tensor cores: fp16 data operands with a per-node
                              power-of-two scale, every filter split into fp16 hi + lo parts (two

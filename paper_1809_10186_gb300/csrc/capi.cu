@@ -568,8 +568,8 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
     dgfs_status st = build_host_plan(*desc, p->hp, err);
     if (st != DGFS_OK) return fail(st, err);
     p->prec = desc->precision;
-    if (p->prec == DGFS_PREC_FP64 && p->hp.N > 24)
-        return fail(DGFS_ERR_UNSUPPORTED, "FP64 plans support N <= 24");
+    if (p->hp.aniso && !vss_fused_supported(p->hp.N, p->prec == DGFS_PREC_FP64))
+        return fail(DGFS_ERR_UNSUPPORTED, "the VSS kernel supports N <= 24 in FP64");
     if (is_tc(p->prec) && !tc_supported(p->hp.N))
         return fail(DGFS_ERR_UNSUPPORTED, "tensor-core precisions support N = 16 and 32");
     if (p->hp.aniso && is_tc(p->prec))
@@ -601,7 +601,7 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
     }
     // tensor-core plans keep their kernel for Q(f, f) and dQ/dgamma; their bilinear calls (Q(f, g),
     // the JVP) and the VJP take the Fourier-space translates in FP32 like the FP32 plans
-    p->fftx = !p->hp.aniso && vss_fused_supported(p->hp.N, p->prec == DGFS_PREC_FP64);
+    p->fftx = !p->hp.aniso && fft_translate_supported(p->hp.N);
     if (p->fftx) {
         // transform batches of about 1.5 GB of operand and translate spectra
         const size_t n3 = (size_t)p->hp.N * p->hp.N * p->hp.N;
@@ -1688,6 +1688,8 @@ extern "C" dgfs_status dgfs_collide_noalloc(dgfs_plan_t plan, const void* f, voi
     if (!aligned16(f) || !aligned16(Q)) return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
     if (f == Q) return fail(DGFS_ERR_INVALID_ARG, "output aliases the input");
     if (plan->hp.aniso) return fail(DGFS_ERR_UNSUPPORTED, "dgfs_collide_noalloc of a VSS plan (alpha != 1)");
+    if (plan->prec == DGFS_PREC_FP64 && plan->hp.N > 24)
+        return fail(DGFS_ERR_UNSUPPORTED, "dgfs_collide_noalloc of an FP64 plan supports N <= 24");
     const size_t per_node = noalloc_node_bytes(plan);
     const int64_t capacity = (int64_t)(kNoAllocScratchBytes / per_node);
     if (B > capacity) {

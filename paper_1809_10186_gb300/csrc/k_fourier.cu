@@ -329,8 +329,7 @@ cudaError_t launch_dft3(const DevTables<T>& t, Cplx<T>* X, int64_t count, bool f
     if (N == 12) return fft3<T, 12>(X, W, count, forward, scale, s);
     if (N == 16) return fft3<T, 16>(X, W, count, forward, scale, s);
     if (N == 24) return fft3<T, 24>(X, W, count, forward, scale, s);
-    if constexpr (sizeof(T) == 4)                       // FP64 plans stop at N = 24
-        if (N == 32) return fft3<T, 32>(X, W, count, forward, scale, s);
+    if (N == 32) return fft3<T, 32>(X, W, count, forward, scale, s);
     return cudaErrorInvalidValue;
 }
 

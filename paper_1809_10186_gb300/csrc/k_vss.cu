@@ -391,6 +391,8 @@ cudaError_t planes_launch(const Cplx<T>* Fh, const Cplx<T>* Gh, const Cplx<T>* m
 
 bool vss_fused_supported(int N, bool fp64) { return N == 8 || N == 12 || N == 16 || N == 24 || (N == 32 && !fp64); }
 
+bool fft_translate_supported(int N) { return N == 8 || N == 12 || N == 16 || N == 24 || N == 32; }
+
 template <typename T>
 cudaError_t launch_vss_load_t(const T* f, const int64_t* offs, int N, int64_t nodes, Cplx<T>* X, cudaStream_t s) {
     if (nodes <= 0) return cudaSuccess;
@@ -410,8 +412,7 @@ cudaError_t launch_vss_inverse_planes(const Cplx<T>* Fh, const Cplx<T>* Gh, cons
     if (N == 12) return planes_launch<T, 12, true>(Fh, Gh, mu_r, dftw, npairs, fields, nodes, Z, s);
     if (N == 16) return planes_launch<T, 16, true>(Fh, Gh, mu_r, dftw, npairs, fields, nodes, Z, s);
     if (N == 24) return planes_launch<T, 24, true>(Fh, Gh, mu_r, dftw, npairs, fields, nodes, Z, s);
-    if constexpr (sizeof(T) == 4)
-        if (N == 32) return planes_launch<T, 32, true>(Fh, Gh, mu_r, dftw, npairs, fields, nodes, Z, s);
+    if (N == 32) return planes_launch<T, 32, true>(Fh, Gh, mu_r, dftw, npairs, fields, nodes, Z, s);
     return cudaErrorInvalidValue;
 }
 
@@ -439,8 +440,7 @@ cudaError_t launch_vss_forward_planes(const Cplx<T>* dftw, int N, int fields, in
     if (N == 12) return planes_launch<T, 12, false>(nullptr, nullptr, nullptr, dftw, 0, fields, nodes, W, s);
     if (N == 16) return planes_launch<T, 16, false>(nullptr, nullptr, nullptr, dftw, 0, fields, nodes, W, s);
     if (N == 24) return planes_launch<T, 24, false>(nullptr, nullptr, nullptr, dftw, 0, fields, nodes, W, s);
-    if constexpr (sizeof(T) == 4)
-        if (N == 32) return planes_launch<T, 32, false>(nullptr, nullptr, nullptr, dftw, 0, fields, nodes, W, s);
+    if (N == 32) return planes_launch<T, 32, false>(nullptr, nullptr, nullptr, dftw, 0, fields, nodes, W, s);
     return cudaErrorInvalidValue;
 }
 
@@ -454,8 +454,7 @@ cudaError_t launch_vss_lines_sum(const Cplx<T>* Z, const Cplx<T>* dftw, const T*
     else if (N == 12) k_vss_lines_sum<T, 12><<<grid, 128, 0, s>>>(Z, dftw, wsig, npairs, sets, node_stride, P);
     else if (N == 16) k_vss_lines_sum<T, 16><<<grid, 128, 0, s>>>(Z, dftw, wsig, npairs, sets, node_stride, P);
     else if (N == 24) k_vss_lines_sum<T, 24><<<grid, 128, 0, s>>>(Z, dftw, wsig, npairs, sets, node_stride, P);
-    else if (sizeof(T) == 4 && N == 32)
-        k_vss_lines_sum<T, sizeof(T) == 4 ? 32 : 16><<<grid, 128, 0, s>>>(Z, dftw, wsig, npairs, sets, node_stride, P);
+    else if (N == 32) k_vss_lines_sum<T, 32><<<grid, 128, 0, s>>>(Z, dftw, wsig, npairs, sets, node_stride, P);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -470,8 +469,7 @@ cudaError_t launch_vjp_lines(const Cplx<T>* Z, const T* U, int64_t node_stride, 
     else if (N == 12) k_vjp_lines<T, 12><<<grid, 128, 0, s>>>(Z, U, node_stride, dftw, npairs, W);
     else if (N == 16) k_vjp_lines<T, 16><<<grid, 128, 0, s>>>(Z, U, node_stride, dftw, npairs, W);
     else if (N == 24) k_vjp_lines<T, 24><<<grid, 128, 0, s>>>(Z, U, node_stride, dftw, npairs, W);
-    else if (sizeof(T) == 4 && N == 32)
-        k_vjp_lines<T, sizeof(T) == 4 ? 32 : 16><<<grid, 128, 0, s>>>(Z, U, node_stride, dftw, npairs, W);
+    else if (N == 32) k_vjp_lines<T, 32><<<grid, 128, 0, s>>>(Z, U, node_stride, dftw, npairs, W);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

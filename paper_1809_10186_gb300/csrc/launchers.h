@@ -110,8 +110,9 @@ template <typename T>
 cudaError_t launch_vss_loss_init(const Cplx<T>* Ah, const Cplx<T>* Bh, const T* GL, int N, int64_t nodes,
                                  Cplx<T>* Y, int yfields, cudaStream_t s);
 
-// N = 8, 12, 16, 24 and, in FP32, 32
+// the VSS kernels: N = 8, 12, 16, 24 and, in FP32, 32; the VHS translates, the adjoint: every N
 bool vss_fused_supported(int N, bool fp64);
+bool fft_translate_supported(int N);
 // X[n] = {f[n], 0} transposed to plane-major (then transformed with launch_dft3); node n of f at
 // offs[n] (device, or nullptr: n N^3)
 template <typename T>
