@@ -482,8 +482,8 @@ def test_empty_batch_and_argument_errors():
     assert L_.dgfs_collide(plan.handle, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(f.data_ptr()), 1, s) == 1
     # negative batch
     assert L_.dgfs_collide(plan.handle, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(out.data_ptr()), -1, s) == 1
-    with pytest.raises(binding.DGFSError):
-        binding.Plan(N=32, L=7.0, M=38, precision="fp64")       # FP64 is limited to N <= 24
+    with pytest.raises(binding.DGFSError):                       # FP64 VSS is limited to N <= 24
+        binding.Plan(N=32, L=7.0, M=38, alpha=1.4, precision="fp64")
 
 
 def test_autograd_function():

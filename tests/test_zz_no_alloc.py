@@ -64,3 +64,12 @@ def test_noalloc_rejects_batches_beyond_the_fixed_array():
     assert st == 1
     msg = binding.lib().dgfs_last_error_message().decode()
     assert "exceeds" in msg and "fixed" in msg
+
+
+def test_noalloc_rejects_fp64_beyond_n24():
+    """FP64 plans at N = 32 run through dgfs_collide, not the fixed-scratch call."""
+    plan = binding.Plan(N=32, L=7.0, gamma=0.52, M=38, N_rho=8, precision="fp64")
+    f = torch.zeros(1, 32, 32, 32, dtype=torch.float64, device="cuda")
+    st, _ = _noalloc(plan, f)
+    assert st == 2
+    assert "N <= 24" in binding.lib().dgfs_last_error_message().decode()
