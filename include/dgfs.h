@@ -76,7 +76,8 @@ typedef enum {
 } dgfs_loss_mode;
 
 typedef struct {
-    int N;                     /* grid points per velocity axis: 8, 16, 24 or 32                */
+    int N;                     /* grid points per velocity axis: 8, 12, 16, 24 or 32 (tensor-core
+                                  precisions: 16 or 32)                                       */
     double L;                  /* velocity domain [-L, L]^3 (Sec. 3.3), L > 0                   */
     double R;                  /* ball radius of the c_r integral; <= 0: 4L/(3+sqrt 2) (Appendix) */
     double gamma;              /* VHS exponent 2(1 - omega) of |c - c_*| (eq. B_gen)            */
