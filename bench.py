@@ -46,6 +46,9 @@ def _args():
     ap.add_argument("--nodes", type=int, default=None, help="nodes per GPU (default 2048)")
     ap.add_argument("--chunk", type=int, default=0,
                     help="nodes per internal chunk (plan max_batch); 0: the whole per-GPU batch in one chunk")
+    ap.add_argument("--sphere", type=int, default=0, choices=[0, 6, 12, 26, 38],
+                    help="sphere rule size M of the headline leg (0: the workload's 38); smaller rules "
+                         "give the translate kernel's fixed cost per CTA by a fit over M")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
@@ -198,7 +201,7 @@ def fft_algorithmic_flops_per_node(N, Nrho, npairs):
 # DRAM bytes (read + write) per node of one translate-product launch at N = 32, N_rho = 32, M = 38,
 # from the ncu capture of a 512-node launch summarised in profiles/ (None for configurations
 # without a capture of the current kernel version).
-TRAFFIC_PER_NODE = {("f16s", 32, 32, 38): 2175.90e6 / 512, ("bf16s", 32, 32, 38): None,
+TRAFFIC_PER_NODE = {("f16s", 32, 32, 38): 2184.94e6 / 512, ("bf16s", 32, 32, 38): 2184.69e6 / 512,
                     ("fp32", 32, 32, 38): None}
 
 
@@ -589,7 +592,7 @@ def main():
     binding.lib()
 
     cfg = W.CONFIGS[WORKLOAD]
-    N, L, M, Nr = cfg["N"], cfg["L"], cfg["M"], cfg["Nrho"]
+    N, L, M, Nr = cfg["N"], cfg["L"], a.sphere or cfg["M"], cfg["Nrho"]
     B = a.nodes or cfg["B"]
     prec = a.prec
     F, _ = W.two_maxwellian(B, N, L, rank_seed(cfg["seed"], rank), dtype=np.float32)
@@ -646,7 +649,7 @@ def main():
                  "traffic": (TRAFFIC_PER_NODE.get((prec, N, Nr, 2 * npairs)) or 0) * nodes_per_launch or None,
                  "traffic_unit": "bytes per launch", "kernel": "translate-product",
                  "kernel_share": prof["gain_ms"] / ms if ms else None,
-                 "flops_per_node": flops_node, "nodes_per_launch": nodes_per_launch,
+                 "flops_per_node": flops_node, "nodes_per_launch": nodes_per_launch, "launch_ms": per_launch_ms,
                  "fft_algorithmic_tflops": fft_algorithmic_flops_per_node(N, Nr, npairs) * value / world / 1e12})
 
     line = {"metric": METRIC, "value": value, "unit": "node-evals/s", "n_gpus": world,
@@ -656,7 +659,7 @@ def main():
                       "bf16s": "bf16 operands (filters hi+lo), f32 accumulate"}[prec],
             "data": "synthetic",
             "config": {"workload": "%s: %d two-Maxwellian nodes/GPU, N=32 on [-7,7]^3, omega=0.74, "
-                                   "N_rho=32, M=38, SVD 1e-8" % (WORKLOAD, B),
+                                   "N_rho=32, M=%d, SVD 1e-8" % (WORKLOAD, B, M),
                        "nodes_per_gpu": B, "N": N, "M": M, "N_rho": Nr,
                        "svd_rank": plan.info["svd_rank_used"], "precision": prec,
                        "chunk_nodes": plan.info["chunk_nodes"],
@@ -701,7 +704,7 @@ def main():
         torch.cuda.synchronize()
 
     # CPU baseline: the oracle on a bounded sample of the same nodes (rank 0, N = 1 only)
-    if world == 1 and not a.no_cpu:
+    if world == 1 and not a.no_cpu and M == cfg["M"]:   # the oracle sample uses the workload's rule
         plan.collide(f, out=q)
         torch.cuda.synchronize()
         cores = os.cpu_count() or 1

@@ -17,7 +17,7 @@
 // shared-memory A operand once, and the epilogue combines hi + 2^-e lo in FP32. The + sign's x
 // filter carries the factor 2 w_p, so the products need no further weighting.
 //
-// One CTA per (radial point, node): two epilogue warpgroups and a third warpgroup of four MMA
+// One CTA per (node, rpc consecutive radial points): two epilogue warpgroups and a third warpgroup of four MMA
 // warps (after set-up the third warpgroup gives registers back and the epilogue warpgroups take
 // them, 216 per thread, so that an epilogue step loads a whole tile row from TMEM behind one
 // wait). The front of a sphere pair (passes 1 and 2 of every tile) is a producer/consumer chain:
@@ -32,7 +32,7 @@
 // are mbarriers; every lane of the epilogue warps arrives and every wait loop branches on warp
 // votes only, so no branch diverges around the .sync.aligned tcgen05 instructions. Every wait is
 // bounded: on timeout the CTA raises flag bit 0, every role stops, the MMAs and copies in flight
-// are drained (bounded), TMEM is freed and P is not written.
+// are drained (bounded), TMEM is freed and no further P_r is written (the flag marks P invalid).
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -281,7 +281,7 @@ __device__ __forceinline__ void mma_p3_loop(Bars& bars, uint32_t sb, uint32_t tm
 template <int N, bool BF>
 __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
 k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const unsigned char* __restrict__ filt,
-          int npairs, int Nrho, float* __restrict__ P, int* __restrict__ flags, int fault) {
+          int npairs, int Nrho, int rpc, float* __restrict__ P, int* __restrict__ flags, int fault) {
     using G = Geo<N>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) Bars bars;
@@ -292,15 +292,18 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool issuer = warp == G::ISSUER;
-    const int r = blockIdx.x;
+    // radial points r0 .. r0 + rpc - 1 of the node, one after the other: their filter blocks are
+    // consecutive, so the CTA runs one sequence of nseq (radial point, pair) steps and the set-up
+    // (barriers, TMEM, max |f|, f in TMEM) is paid once per rpc radial points
+    const int r0 = blockIdx.x * rpc, nseq = npairs * rpc;
     const int64_t node = blockIdx.y;
     constexpr int64_t n3 = (int64_t)N * N * N;
     const float* fb = f + (offs ? offs[node] : node * n3);
     const uint32_t sb = tc::smem_u32(smem);
-    const unsigned char* fglob = filt + (size_t)r * npairs * G::F_BLOCK;
+    const unsigned char* fglob = filt + (size_t)r0 * npairs * G::F_BLOCK;
 
     // filter copies issued and waited per buffer 0 / 1 (used by the MMA warp and the drain)
-    int copies0 = npairs > 0 ? 1 : 0, copies1 = npairs > 1 ? 1 : 0, waited0 = 0, waited1 = 0;
+    int copies0 = nseq > 0 ? 1 : 0, copies1 = nseq > 1 ? 1 : 0, waited0 = 0, waited1 = 0;
 
     // ---- set-up: barriers, first filter copies, TMEM (MMA warp); max |f| (epilogue warps) -----
     if (issuer) {
@@ -323,7 +326,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
             tc::mbar_init(&bars.drain, 4);
             tc::fence_mbar_init();
             s_abort = 0;
-            for (int p = 0; p < 2 && p < npairs; ++p) {
+            for (int p = 0; p < 2 && p < nseq; ++p) {
                 tc::mbar_expect_tx(&bars.filt[p], G::F_BLOCK);
                 tc::bulk_g2s(smem + G::S_F + p * G::F_BLOCK, fglob + (size_t)p * G::F_BLOCK, G::F_BLOCK, &bars.filt[p]);
             }
@@ -331,8 +334,17 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
         __syncwarp();
         tc::tmem_alloc(&s_tmem, G::TMEM_COLS);
     } else if (!BF && warp < G::EPI_WARPS) {
-        float mx = 0.f;
-        for (int e = tid; e < n3; e += 32 * G::EPI_WARPS) mx = fmaxf(mx, fabsf(__ldg(fb + e)));
+        // max |f| of the node; the unrolled loads and eight independent maxima keep the thread's
+        // loads in flight together (a loop carried through one maximum costs a memory round trip
+        // per element: about a tenth of the kernel at N = 32)
+        constexpr int STRIDE = 32 * G::EPI_WARPS, PER = (int)(n3 / STRIDE);
+        static_assert(n3 % STRIDE == 0 && PER % 8 == 0, "scan split");
+        float m8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) m8[j] = 0.f;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) m8[i & 7] = fmaxf(m8[i & 7], fabsf(__ldg(fb + tid + i * STRIDE)));
+        float mx = fmaxf(fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3])), fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7])));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) s_red[warp] = mx;
@@ -357,15 +369,27 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
     // ---- f -> TMEM as the pass-1 A operand: tile t, lane l = yl N + z holds f[0..N)[t ZT + yl][z] --
     if (warp < G::EPI_WARPS) {
         const int q = warp & 3, w = warp >> 2, l = 32 * q + lane, yl = l / N, z = l % N;
-        for (int t = w; t < G::T; t += 2) {
-            const float* src = fb + (size_t)(t * G::ZT + yl) * N + z;
-            uint32_t v[N / 2];
+        // tiles t = 2k + w, two at a time: both tiles' loads precede the TMEM stores (whose memory
+        // clobber would otherwise keep the next tile's loads behind them)
+        constexpr int TB = G::TW >= 2 ? 2 : 1;
+        static_assert(G::TW % TB == 0, "tile batches");
+#pragma unroll 1
+        for (int k0 = 0; k0 < G::TW; k0 += TB) {
+            uint32_t v[TB][N / 2];
 #pragma unroll
-            for (int c = 0; c < N / 2; ++c)
-                v[c] = pack2<BF>(__ldg(src + (size_t)(2 * c) * G::N2) * sf, __ldg(src + (size_t)(2 * c + 1) * G::N2) * sf);
-            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + G::C_F + t * (N / 2);
-            if constexpr (N == 32) tc::tmem_st16(ta, v);
-            else tc::tmem_st8(ta, v);
+            for (int b = 0; b < TB; ++b) {
+                const float* src = fb + (size_t)((2 * (k0 + b) + w) * G::ZT + yl) * N + z;
+#pragma unroll
+                for (int c = 0; c < N / 2; ++c)
+                    v[b][c] = pack2<BF>(__ldg(src + (size_t)(2 * c) * G::N2) * sf,
+                                        __ldg(src + (size_t)(2 * c + 1) * G::N2) * sf);
+            }
+#pragma unroll
+            for (int b = 0; b < TB; ++b) {
+                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + G::C_F + (2 * (k0 + b) + w) * (N / 2);
+                if constexpr (N == 32) tc::tmem_st16(ta, v[b]);
+                else tc::tmem_st8(ta, v[b]);
+            }
         }
         tc::tmem_wait_st();
     }
@@ -376,13 +400,13 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
       tc::setmaxnreg_dec<G::REG_MMA>();   // every warp of the third warpgroup
       // ============================ MMA warps (converged) =====================================
       if (warp == G::ISSUER)
-        mma_p1_loop<N, BF>(bars, smem, sb, tmem, fglob, npairs, abort, copies0, copies1, waited0, waited1);
+        mma_p1_loop<N, BF>(bars, smem, sb, tmem, fglob, nseq, abort, copies0, copies1, waited0, waited1);
       else if (warp == G::ISSUER + 1)
-        mma_p2_loop<N, BF>(bars, sb, tmem, npairs, abort);
+        mma_p2_loop<N, BF>(bars, sb, tmem, nseq, abort);
       else if (warp == G::ISSUER + 2)
-        mma_p3_loop<N, BF, 0>(bars, sb, tmem, npairs, abort);
+        mma_p3_loop<N, BF, 0>(bars, sb, tmem, nseq, abort);
       else
-        mma_p3_loop<N, BF, 1>(bars, sb, tmem, npairs, abort);
+        mma_p3_loop<N, BF, 1>(bars, sb, tmem, nseq, abort);
     } else {
         tc::setmaxnreg_inc<G::REG_EPI>();
         // ============================== epilogue warpgroups ===================================
@@ -407,7 +431,9 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
     do {                                                                \
         if (!tc::warp_wait((bar), (ph), abort)) goto epi_done;          \
     } while (0)
-        for (int p = 0; p < npairs; ++p) {
+        for (int rr = 0; rr < rpc; ++rr) {
+          for (int pp = 0; pp < npairs; ++pp) {
+            const int p = rr * npairs + pp;   // step of the CTA's (radial point, pair) sequence
             if (w == 0) {
                 for (int t = 0; t < G::T; ++t) {   // pass-1 tile t (slot t % 2) -> pass-2 operands (buffer t % 2)
                     const int b = t & 1;
@@ -507,18 +533,24 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                         acc[k][16 * c + j] = fmaf(fmaf(lp[j], eps, hp[j]), fmaf(lm[j], eps, hm[j]), acc[k][16 * c + j]);
                 }
             }
+          }
+          // radial point r0 + rr done: P_r out, sums cleared
+          if (!*abort) {   // P[node][r][x'][y'][z'], row m3 = x' N + z' of tile u = 2k + w, column y'
+              float* dst = P + ((size_t)node * Nrho + r0 + rr) * n3;
+#pragma unroll
+              for (int k = 0; k < G::TW; ++k) {
+                  const int m3 = (2 * k + w) * 128 + l, xp = m3 / N, zp = m3 % N;
+                  float* o = dst + (size_t)xp * G::N2 + zp;
+#pragma unroll
+                  for (int j = 0; j < N; ++j) o[(size_t)j * N] = acc[k][j] * out_scale;
+              }
+          }
+#pragma unroll
+          for (int k = 0; k < G::TW; ++k)
+#pragma unroll
+              for (int j = 0; j < N; ++j) acc[k][j] = 0.f;
         }
 #undef DGFS_WAITE
-        if (!*abort) {   // P[node][r][x'][y'][z'], row m3 = x' N + z' of tile u = 2k + w, column y'
-            float* dst = P + ((size_t)node * Nrho + r) * n3;
-#pragma unroll
-            for (int k = 0; k < G::TW; ++k) {
-                const int m3 = (2 * k + w) * 128 + l, xp = m3 / N, zp = m3 % N;
-                float* o = dst + (size_t)xp * G::N2 + zp;
-#pragma unroll
-                for (int j = 0; j < N; ++j) o[(size_t)j * N] = acc[k][j] * out_scale;
-            }
-        }
     epi_done:;
     }
 
@@ -554,11 +586,17 @@ cudaError_t launch_n(const TcTables& t, const float* f, const int64_t* offs, int
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::S_TOTAL);
     if (e != cudaSuccess) return e;
     const int64_t n3 = (int64_t)N * N * N;
+    // two radial points per CTA halve the per-CTA set-up when the grid still fills the GPU many
+    // times over (one CTA per SM); small batches keep one radial point per CTA
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int rpc = (t.Nrho % 2 == 0 && (int64_t)(t.Nrho / 2) * nodes >= 16 * (int64_t)sms) ? 2 : 1;
     for (int64_t n0 = 0; n0 < nodes; n0 += 65535) {
         const int64_t nn = nodes - n0 < 65535 ? nodes - n0 : 65535;
-        kern<<<dim3(t.Nrho, (unsigned)nn), G::THREADS, G::S_TOTAL, s>>>(
+        kern<<<dim3(t.Nrho / rpc, (unsigned)nn), G::THREADS, G::S_TOTAL, s>>>(
             f + (offs ? 0 : n0 * n3), offs ? offs + n0 : nullptr, static_cast<const unsigned char*>(t.mats),
-            t.npairs, t.Nrho, P + n0 * t.Nrho * n3, flags, n0 == 0 ? fault : 0);
+            t.npairs, t.Nrho, rpc, P + n0 * t.Nrho * n3, flags, n0 == 0 ? fault : 0);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

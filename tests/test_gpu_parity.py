@@ -568,6 +568,29 @@ def test_tensor_core_chunking_and_determinism():
     assert torch.equal(a, p2.collide(f))
 
 
+@pytest.mark.parametrize("prec,rule", [("f16s", 6), ("f16s", 38), ("bf16s", 38), ("f16s", "one_pair")])
+def test_tensor_core_two_radial_points_per_cta_equal_one(prec, rule):
+    """Batches that fill the GPU many times over run two radial points per CTA (one set-up for
+    both: the pair sequence continues into the next radial point's filters); small chunks run one
+    radial point per CTA. The two schedules perform the same arithmetic per radial point, so the
+    results are identical, including for a single sphere pair (two steps per CTA, no refill)."""
+    N, L = 32, 7.0
+    if isinstance(rule, int):
+        kw = {"M": rule}
+    else:
+        kw = {"sphere": np.array([[0.36, 0.48, 0.8, 2.0 * np.pi]])}
+    F, _ = W.two_maxwellian(200, N, L, 91, dtype=np.float32)
+    f = _dev(F, "fp32")
+    big = binding.Plan(N=N, L=L, gamma=0.52, N_rho=N, precision=prec, max_batch=200, **kw)    # 3200 CTAs of 2
+    small = binding.Plan(N=N, L=L, gamma=0.52, N_rho=N, precision=prec, max_batch=8, **kw)    # 256 CTAs of 1
+    a, b = big.collide(f), small.collide(f)
+    big.stream_status()
+    small.stream_status()
+    assert torch.equal(a, b)
+    big.close()
+    small.close()
+
+
 def test_lost_hand_off_times_out_and_the_plan_recovers():
     """Failure detection without a GPU fault: the first CTA of the tensor-core kernel withholds
     one hand-off signal (host-injected), its bounded waits give up, the CTA drains and frees its
