@@ -586,12 +586,14 @@ cudaError_t launch_n(const TcTables& t, const float* f, const int64_t* offs, int
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::S_TOTAL);
     if (e != cudaSuccess) return e;
     const int64_t n3 = (int64_t)N * N * N;
-    // two radial points per CTA halve the per-CTA set-up when the grid still fills the GPU many
-    // times over (one CTA per SM); small batches keep one radial point per CTA
+    // several radial points per CTA share its set-up: the most of 4, 2, 1 that divides N_rho while
+    // the grid still fills the GPU at least 16 times over (one CTA per SM); small batches keep one
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const int rpc = (t.Nrho % 2 == 0 && (int64_t)(t.Nrho / 2) * nodes >= 16 * (int64_t)sms) ? 2 : 1;
+    int rpc = 1;
+    for (int c = 4; c > 1 && rpc == 1; c /= 2)
+        if (t.Nrho % c == 0 && (int64_t)(t.Nrho / c) * nodes >= 16 * (int64_t)sms) rpc = c;
     for (int64_t n0 = 0; n0 < nodes; n0 += 65535) {
         const int64_t nn = nodes - n0 < 65535 ? nodes - n0 : 65535;
         kern<<<dim3(t.Nrho / rpc, (unsigned)nn), G::THREADS, G::S_TOTAL, s>>>(

@@ -568,21 +568,23 @@ def test_tensor_core_chunking_and_determinism():
     assert torch.equal(a, p2.collide(f))
 
 
-@pytest.mark.parametrize("prec,rule", [("f16s", 6), ("f16s", 38), ("bf16s", 38), ("f16s", "one_pair")])
-def test_tensor_core_two_radial_points_per_cta_equal_one(prec, rule):
-    """Batches that fill the GPU many times over run two radial points per CTA (one set-up for
-    both: the pair sequence continues into the next radial point's filters); small chunks run one
-    radial point per CTA. The two schedules perform the same arithmetic per radial point, so the
-    results are identical, including for a single sphere pair (two steps per CTA, no refill)."""
+@pytest.mark.parametrize("prec,rule,B", [("f16s", 6, 200), ("f16s", 38, 200), ("bf16s", 38, 200),
+                                         ("f16s", "one_pair", 200), ("f16s", 38, 400), ("f16s", "one_pair", 400)])
+def test_tensor_core_radial_points_per_cta_equal_one(prec, rule, B):
+    """Batches that fill the GPU many times over run several radial points per CTA (one set-up for
+    all: the pair sequence continues into the next radial point's filters): two at 200 nodes of
+    N_rho = 32, four at 400; small chunks run one radial point per CTA. The schedules perform the
+    same arithmetic per radial point, so the results are identical, including for a single sphere
+    pair (two or four steps per CTA)."""
     N, L = 32, 7.0
     if isinstance(rule, int):
         kw = {"M": rule}
     else:
         kw = {"sphere": np.array([[0.36, 0.48, 0.8, 2.0 * np.pi]])}
-    F, _ = W.two_maxwellian(200, N, L, 91, dtype=np.float32)
+    F, _ = W.two_maxwellian(B, N, L, 91, dtype=np.float32)
     f = _dev(F, "fp32")
-    big = binding.Plan(N=N, L=L, gamma=0.52, N_rho=N, precision=prec, max_batch=200, **kw)    # 3200 CTAs of 2
-    small = binding.Plan(N=N, L=L, gamma=0.52, N_rho=N, precision=prec, max_batch=8, **kw)    # 256 CTAs of 1
+    big = binding.Plan(N=N, L=L, gamma=0.52, N_rho=N, precision=prec, max_batch=B, **kw)   # 3200 CTAs of 2 or 4
+    small = binding.Plan(N=N, L=L, gamma=0.52, N_rho=N, precision=prec, max_batch=8, **kw)  # 256 CTAs of 1
     a, b = big.collide(f), small.collide(f)
     big.stream_status()
     small.stream_status()
