@@ -228,8 +228,11 @@ dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host
    counterpart to this call. Its intermediate fields live in one fixed 64 MiB device array
    defined in this library (one per GPU that loads it, held until the process exits) instead of
    the plan's workspace; it calls no allocating routine. B is limited to the number of nodes
-   whose scratch fits the array (about 6 at N = 32, more for smaller grids); larger B returns
-   DGFS_ERR_INVALID_ARG with the limit in the message. The first call on a device looks up the
+   whose scratch fits the array: floor(64 MiB / s) with s = e (N_rho + 2 (rank + 2) + 4) N^3
+   bytes per node (e = 4 for float plans, 8 for FP64; each of the three parts rounded up to
+   256 bytes), i.e. 6 nodes at N = 32, N_rho = 32 with an SVD rank of 19, 4 at N = 32 without
+   truncation, 73 at N = 16, N_rho = 16; larger B returns DGFS_ERR_INVALID_ARG with the limit
+   in the message. The first call on a device looks up the
    array's device address; make it before capturing any stream. Every call shares the array:
    calls whose work overlaps on the GPU race on it. f, Q: device, [B][N^3], as dgfs_collide. */
 dgfs_status dgfs_collide_noalloc(dgfs_plan_t plan, const void* f, void* Q, int64_t B, void* stream);
@@ -302,6 +305,13 @@ typedef struct {
 
 dgfs_status dgfs_profile_begin(dgfs_plan_t plan);
 dgfs_status dgfs_profile_end(dgfs_plan_t plan, dgfs_profile_t* out);
+
+/* Device-rate probe for rooflines (the paper has no counterpart): the FP32 and FP64 fused
+   multiply-add throughput of the CUDA cores of the current device, in TFLOP/s (2 flops per FMA),
+   the best of three timed launches of independent FMA chains on every SM. Synchronous; allocates
+   a few bytes of device memory for the duration of the call; changes no device setting. Either
+   output may be NULL. */
+dgfs_status dgfs_device_fma_peaks(double* fp32_tflops, double* fp64_tflops);
 
 /* Message of the last failed call on the calling thread ("" if none). */
 const char* dgfs_last_error_message(void);

@@ -68,6 +68,7 @@ _SIGNATURES = {
     "dgfs_collide_noalloc": [_P, _P, _P, _I64, _P],
     "dgfs_stream_status": [_P, _P],
     "dgfs_debug_inject": [_P, ctypes.c_int],
+    "dgfs_device_fma_peaks": [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "dgfs_profile_begin": [_P],
     "dgfs_profile_end": [_P, ctypes.POINTER(dgfs_profile_t)],
     "dgfs_last_error_message": [],
@@ -200,6 +201,13 @@ def host_vss_tables(**kw):
     dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     check(lib().dgfs_host_vss_tables(ctypes.byref(d), dp(A), dp(GL)), "dgfs_host_vss_tables")
     return A, GL
+
+
+def device_fma_peaks():
+    """(FP32, FP64) FMA throughput of the current device in TFLOP/s, measured (dgfs_device_fma_peaks)."""
+    a, b = ctypes.c_double(0), ctypes.c_double(0)
+    check(lib().dgfs_device_fma_peaks(ctypes.byref(a), ctypes.byref(b)), "dgfs_device_fma_peaks")
+    return a.value, b.value
 
 
 def _stream_ptr(stream=None):
@@ -497,28 +505,46 @@ def _autograd_function():
     import torch
 
     class CollideFunction(torch.autograd.Function):
-        """Q(f, f) with reverse mode through dgfs_collide_vjp and forward mode through
-        dgfs_collide_jvp. Translates are recomputed by the kernels, never stored."""
+        """Q(f, f) of a plan, differentiable with respect to f and to the VHS exponent gamma.
+
+        Reverse mode: the gradient of f is dgfs_collide_vjp(f, gQ); the gradient of gamma is the
+        contraction sum_j gQ_j (dQ/dgamma)_j with dQ/dgamma from dgfs_collide_dgamma (b held fixed),
+        per node for a gamma of shape [B], summed over the batch for a scalar gamma. Forward mode:
+        dgfs_collide_jvp(f, v) + (dQ/dgamma) gamma_dot. The kernels recompute every translate;
+        nothing but f is saved."""
 
         @staticmethod
-        def forward(plan, f):
+        def forward(plan, f, gamma):
             return plan.collide(f.contiguous())
 
         @staticmethod
         def setup_context(ctx, inputs, output):
-            plan, f = inputs
+            plan, f, gamma = inputs
             ctx.plan = plan
+            ctx.gamma_shape = None if gamma is None else tuple(gamma.shape)
             ctx.save_for_backward(f)
             ctx.f_fwd = f
 
         @staticmethod
         def backward(ctx, gQ):
             (f,) = ctx.saved_tensors
-            return None, ctx.plan.collide_vjp(f.contiguous(), gQ.contiguous())
+            f, gQ = f.contiguous(), gQ.contiguous()
+            gf = ctx.plan.collide_vjp(f, gQ) if ctx.needs_input_grad[1] else None
+            gg = None
+            if ctx.gamma_shape is not None and ctx.needs_input_grad[2]:
+                per_node = (gQ * ctx.plan.collide_dgamma(f)).sum(dim=(1, 2, 3))
+                gg = per_node.sum() if len(ctx.gamma_shape) == 0 else per_node.reshape(ctx.gamma_shape)
+            return None, gf, gg
 
         @staticmethod
-        def jvp(ctx, _plan_t, v):
-            return ctx.plan.collide_jvp(ctx.f_fwd.contiguous(), v.contiguous())
+        def jvp(ctx, _plan_t, v, gamma_t):
+            f = ctx.f_fwd.contiguous()
+            out = ctx.plan.collide_jvp(f, v.contiguous()) if v is not None else None
+            if gamma_t is not None:
+                scale = gamma_t.reshape(-1, 1, 1, 1) if gamma_t.dim() else gamma_t
+                dg = ctx.plan.collide_dgamma(f) * scale
+                out = dg if out is None else out + dg
+            return out if out is not None else torch.zeros_like(f)
 
     return CollideFunction
 
@@ -526,9 +552,21 @@ def _autograd_function():
 _CF = None
 
 
-def collide(plan, f):
-    """Differentiable Q(f, f) (torch.autograd and forward-mode AD)."""
+def collide(plan, f, gamma=None):
+    """Differentiable Q(f, f) (torch.autograd reverse and forward mode).
+
+    gamma: None, or a tensor (scalar, or [B] for one value per node) holding the plan's VHS
+    exponent; gradients flow to it through dQ/dgamma at fixed b. The plan's tables are built for
+    its gamma, so the values must equal it: to move gamma (e.g. in a fit), build a plan at the new
+    value (the host plan builder takes milliseconds) and call again."""
     global _CF
     if _CF is None:
         _CF = _autograd_function()
-    return _CF.apply(plan, f)
+    if gamma is not None:
+        import torch
+        if not torch.is_tensor(gamma) or gamma.dim() > 1 or (gamma.dim() == 1 and gamma.shape[0] != f.shape[0]):
+            raise ValueError("gamma must be a scalar tensor or a tensor of shape [B]")
+        if torch.any(torch.abs(gamma.detach().double() - plan.info["gamma"]) > 1e-12 * max(1.0, abs(plan.info["gamma"]))):
+            raise ValueError("gamma must equal the plan's gamma (%r); build a plan at the new value"
+                             % plan.info["gamma"])
+    return _CF.apply(plan, f, gamma)

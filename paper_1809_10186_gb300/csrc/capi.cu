@@ -54,6 +54,34 @@ dgfs_status cuda_fail(cudaError_t e, const char* where) {
 
 constexpr uint64_t kMagic = 0x44474653504c414eull;   // "DGFSPLAN"
 
+// Makes `dev` the calling thread's current device while the object lives and then restores the
+// caller's device: no entry point leaves its caller on another device.
+class DeviceScope {
+  public:
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+        if (prev_ != dev) {
+            err_ = cudaSetDevice(dev);
+            changed_ = err_ == cudaSuccess && prev_ >= 0;
+        }
+    }
+    ~DeviceScope() {
+        if (changed_) cudaSetDevice(prev_);
+    }
+    DeviceScope(const DeviceScope&) = delete;
+    DeviceScope& operator=(const DeviceScope&) = delete;
+    cudaError_t error() const { return err_; }
+
+  private:
+    int prev_ = -1;
+    bool changed_ = false;
+    cudaError_t err_ = cudaSuccess;
+};
+
+#define DGFS_ON_DEVICE(dev)                                                           \
+    DeviceScope dgfs_scope_(dev);                                                     \
+    if (dgfs_scope_.error() != cudaSuccess) return cuda_fail(dgfs_scope_.error(), "cudaSetDevice")
+
 }  // namespace
 
 struct dgfs_plan_s {
@@ -502,7 +530,7 @@ template <typename T>
 dgfs_status run(dgfs_plan_s* p, Op op, const void* f, const void* g, void* out, int64_t B,
                 cudaStream_t s) {
     const int64_t n3 = (int64_t)p->hp.N * p->hp.N * p->hp.N;
-    DGFS_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+    DGFS_ON_DEVICE(p->device);
     NodeParams np{nullptr, nullptr, p->hp.gamma, p->hp.b, op == Op::Dgamma ? 1 : 0};
     for (int64_t n0 = 0; n0 < B; n0 += p->chunk) {
         const int64_t nn = std::min<int64_t>(p->chunk, B - n0);
@@ -698,17 +726,16 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
 dgfs_status dgfs_plan_destroy(dgfs_plan_t plan) {
     if (!plan) return DGFS_OK;
     if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
-    int cur = 0;
-    cudaGetDevice(&cur);
-    cudaSetDevice(plan->device);
-    cudaDeviceSynchronize();
-    cudaFree(plan->d_tables);
-    cudaFree(plan->d_ws);
-    cudaFree(plan->d_flags);
-    if (plan->d_vss) cudaFree(plan->d_vss);
-    for (auto& e : plan->ev) cudaEventDestroy(e);
-    destroy_io(plan);
-    cudaSetDevice(cur);
+    {
+        DeviceScope scope(plan->device);
+        cudaDeviceSynchronize();
+        cudaFree(plan->d_tables);
+        cudaFree(plan->d_ws);
+        cudaFree(plan->d_flags);
+        if (plan->d_vss) cudaFree(plan->d_vss);
+        for (auto& e : plan->ev) cudaEventDestroy(e);
+        destroy_io(plan);
+    }
     plan->magic = 0;
     delete plan;
     return DGFS_OK;
@@ -796,7 +823,7 @@ dgfs_status dgfs_collide_ragged(const dgfs_plan_t* plans, int nplans, const int3
     for (int pi = 0; pi < nplans; ++pi) {
         dgfs_plan_s* p = plans[pi];
         std::lock_guard<std::mutex> lock(p->host_mu);
-        DGFS_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+        DGFS_ON_DEVICE(p->device);
         std::vector<int64_t> offs;
         std::vector<double> gam, bb;
         for (int64_t i = 0; i < B; ++i)
@@ -870,15 +897,10 @@ dgfs_status dgfs_ragged_create(const dgfs_plan_t* plans, int nplans, const int32
         bb[k] = node_b ? node_b[i] : plans[c]->hp.b;
     }
     if (B > 0) {
-        int cur = 0;
-        cudaGetDevice(&cur);
-        DGFS_CUDA(cudaSetDevice(r->device), "cudaSetDevice");
+        DGFS_ON_DEVICE(r->device);
         const size_t bytes = (size_t)B * (sizeof(int64_t) + 2 * sizeof(double));
         cudaError_t e = cudaMalloc(&r->d_mem, bytes);
-        if (e != cudaSuccess) {
-            cudaSetDevice(cur);
-            return fail(DGFS_ERR_OOM, "ragged schedule: cudaMalloc failed");
-        }
+        if (e != cudaSuccess) return fail(DGFS_ERR_OOM, "ragged schedule: cudaMalloc failed");
         unsigned char* m = static_cast<unsigned char*>(r->d_mem);
         e = cudaMemcpy(m, offs.data(), (size_t)B * sizeof(int64_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
@@ -886,7 +908,6 @@ dgfs_status dgfs_ragged_create(const dgfs_plan_t* plans, int nplans, const int32
         if (e == cudaSuccess)
             e = cudaMemcpy(m + (size_t)B * (sizeof(int64_t) + sizeof(double)), bb.data(), (size_t)B * sizeof(double),
                            cudaMemcpyHostToDevice);
-        cudaSetDevice(cur);
         if (e != cudaSuccess) {
             cudaFree(r->d_mem);
             return cuda_fail(e, "ragged schedule: upload");
@@ -915,7 +936,7 @@ dgfs_status dgfs_ragged_collide(dgfs_ragged_t r, const void* f, void* Q, void* s
         dgfs_plan_s* p = r->plans[c];
         if (r->count[c] == 0) continue;
         std::lock_guard<std::mutex> lock(p->host_mu);
-        DGFS_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+        DGFS_ON_DEVICE(p->device);
         for (int64_t n0 = 0; n0 < r->count[c]; n0 += p->chunk) {
             const int64_t nn = std::min<int64_t>(p->chunk, r->count[c] - n0);
             const size_t k = r->base[c] + (size_t)n0;
@@ -934,12 +955,11 @@ dgfs_status dgfs_ragged_collide(dgfs_ragged_t r, const void* f, void* Q, void* s
 dgfs_status dgfs_ragged_destroy(dgfs_ragged_t r) {
     if (!r) return DGFS_OK;
     if (!check_ragged_handle(r)) return fail(DGFS_ERR_STATE, "invalid or destroyed ragged schedule");
-    int cur = 0;
-    cudaGetDevice(&cur);
-    cudaSetDevice(r->device);
-    cudaDeviceSynchronize();
-    cudaFree(r->d_mem);
-    cudaSetDevice(cur);
+    {
+        DeviceScope scope(r->device);
+        cudaDeviceSynchronize();
+        cudaFree(r->d_mem);
+    }
     r->magic = 0;
     delete r;
     return DGFS_OK;
@@ -1003,7 +1023,7 @@ dgfs_status dgfs_ssprk(dgfs_plan_t plan, int order, void* f, int64_t B, double d
     if (B == 0 || nsteps == 0) return DGFS_OK;
     if (!f) return fail(DGFS_ERR_INVALID_ARG, "NULL field pointer");
     if (!aligned16(f)) return fail(DGFS_ERR_INVALID_ARG, "field pointer must be 16-byte aligned");
-    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    DGFS_ON_DEVICE(plan->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     return plan->prec == DGFS_PREC_FP64
                ? ssprk_run<double>(plan, order, static_cast<double*>(f), B, dt, scale, nsteps, s)
@@ -1015,7 +1035,7 @@ dgfs_status dgfs_moments(dgfs_plan_t plan, const void* f, double* out, int64_t B
     if (B < 0) return fail(DGFS_ERR_INVALID_ARG, "B must be >= 0");
     if (B == 0) return DGFS_OK;
     if (!f || !out) return fail(DGFS_ERR_INVALID_ARG, "NULL pointer");
-    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    DGFS_ON_DEVICE(plan->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const cudaError_t e = plan->prec == DGFS_PREC_FP64
                               ? launch_moments<double>(static_cast<const double*>(f), plan->hp.N, plan->hp.L, B, out, s)
@@ -1178,7 +1198,7 @@ dgfs_status dgfs_dg_create(dgfs_plan_t plan, int K, const double* H, double svd_
         put_coeffs<float>(blob, d->off_sgn, sg);
     }
     std::memcpy(blob.data() + d->off_rs, rs.data(), rs.size() * sizeof(int));
-    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    DGFS_ON_DEVICE(plan->device);
     cudaError_t e = cudaMalloc(&d->d_mem, off);
     if (e != cudaSuccess) return fail(DGFS_ERR_OOM, std::string("DG workspace: ") + cudaGetErrorString(e));
     e = cudaMemcpy(d->d_mem, blob.data(), blob.size(), cudaMemcpyHostToDevice);
@@ -1206,7 +1226,7 @@ dgfs_status dgfs_dg_collide(dgfs_dg_t dg, const void* F, void* C, int64_t E, voi
     if (!F || !C) return fail(DGFS_ERR_INVALID_ARG, "NULL field pointer");
     if (!aligned16(F) || !aligned16(C)) return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
     if (F == C) return fail(DGFS_ERR_INVALID_ARG, "output aliases the input");
-    DGFS_CUDA(cudaSetDevice(dg->device), "cudaSetDevice");
+    DGFS_ON_DEVICE(dg->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     return dg->plan->prec == DGFS_PREC_FP64
                ? dg_run<double>(dg, static_cast<const double*>(F), static_cast<double*>(C), E, s)
@@ -1216,12 +1236,11 @@ dgfs_status dgfs_dg_collide(dgfs_dg_t dg, const void* F, void* C, int64_t E, voi
 dgfs_status dgfs_dg_destroy(dgfs_dg_t dg) {
     if (!dg) return DGFS_OK;
     if (!check_dg(dg)) return fail(DGFS_ERR_STATE, "invalid or destroyed DG operator");
-    int cur = 0;
-    cudaGetDevice(&cur);
-    cudaSetDevice(dg->device);
-    cudaDeviceSynchronize();
-    cudaFree(dg->d_mem);
-    cudaSetDevice(cur);
+    {
+        DeviceScope scope(dg->device);
+        cudaDeviceSynchronize();
+        cudaFree(dg->d_mem);
+    }
     dg->magic = 0;
     delete dg;
     return DGFS_OK;
@@ -1289,7 +1308,7 @@ dgfs_status slab_walls(dgfs_slab_s* sl, const double* wl, const double* wr) {
         if (!(den > 0.0)) return fail(DGFS_ERR_INVALID_ARG, "wall Maxwellian vanishes on the velocity grid");
         sl->mats.den[k] = den;
     }
-    DGFS_CUDA(cudaSetDevice(sl->device), "cudaSetDevice");
+    DGFS_ON_DEVICE(sl->device);
     DGFS_CUDA(cudaDeviceSynchronize(), "synchronise before the wall update");
     DGFS_CUDA(cudaMemcpy(static_cast<unsigned char*>(sl->d_mem) + sl->off_fw, blob.data(), blob.size(),
                          cudaMemcpyHostToDevice), "wall tables upload");
@@ -1384,7 +1403,7 @@ dgfs_status dgfs_slab_create(dgfs_plan_t plan, int K, int I, const double* edges
     sl->off_C = take((size_t)I * K * n3 * es);
     sl->off_stage = take((size_t)I * K * n3 * es);
     sl->off_q = take((size_t)I * K * n3 * es);
-    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    DGFS_ON_DEVICE(plan->device);
     cudaError_t e = cudaMalloc(&sl->d_mem, off);
     if (e != cudaSuccess) return fail(DGFS_ERR_OOM, std::string("slab workspace: ") + cudaGetErrorString(e));
     std::vector<double> h2(I);
@@ -1415,7 +1434,7 @@ dgfs_status dgfs_slab_rhs(dgfs_slab_t slab, const void* F, void* dFdt, void* str
     if (!F || !dFdt) return fail(DGFS_ERR_INVALID_ARG, "NULL field pointer");
     if (!aligned16(F) || !aligned16(dFdt)) return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
     if (F == dFdt) return fail(DGFS_ERR_INVALID_ARG, "output aliases the input");
-    DGFS_CUDA(cudaSetDevice(slab->device), "cudaSetDevice");
+    DGFS_ON_DEVICE(slab->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     return slab->plan->prec == DGFS_PREC_FP64
                ? slab_rhs<double>(slab, static_cast<const double*>(F), static_cast<double*>(dFdt), s)
@@ -1429,7 +1448,7 @@ dgfs_status dgfs_slab_ssprk(dgfs_slab_t slab, int order, void* F, double dt, int
     if (nsteps == 0) return DGFS_OK;
     if (!F) return fail(DGFS_ERR_INVALID_ARG, "NULL field pointer");
     if (!aligned16(F)) return fail(DGFS_ERR_INVALID_ARG, "field pointer must be 16-byte aligned");
-    DGFS_CUDA(cudaSetDevice(slab->device), "cudaSetDevice");
+    DGFS_ON_DEVICE(slab->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     return slab->plan->prec == DGFS_PREC_FP64 ? slab_ssprk<double>(slab, order, static_cast<double*>(F), dt, nsteps, s)
                                               : slab_ssprk<float>(slab, order, static_cast<float*>(F), dt, nsteps, s);
@@ -1438,13 +1457,12 @@ dgfs_status dgfs_slab_ssprk(dgfs_slab_t slab, int order, void* F, double dt, int
 dgfs_status dgfs_slab_destroy(dgfs_slab_t slab) {
     if (!slab) return DGFS_OK;
     if (!check_slab(slab)) return fail(DGFS_ERR_STATE, "invalid or destroyed slab");
-    int cur = 0;
-    cudaGetDevice(&cur);
-    cudaSetDevice(slab->device);
-    cudaDeviceSynchronize();
-    if (slab->dg) dgfs_dg_destroy(slab->dg);
-    cudaFree(slab->d_mem);
-    cudaSetDevice(cur);
+    {
+        DeviceScope scope(slab->device);
+        cudaDeviceSynchronize();
+        if (slab->dg) dgfs_dg_destroy(slab->dg);
+        cudaFree(slab->d_mem);
+    }
     slab->magic = 0;
     delete slab;
     return DGFS_OK;
@@ -1465,7 +1483,7 @@ dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host
     if (B == 0) return DGFS_OK;
     if (!f_host || !Q_host) return fail(DGFS_ERR_INVALID_ARG, "NULL argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    DGFS_ON_DEVICE(plan->device);
     const size_t es = elem_size(plan->prec);
     const int64_t n3 = (int64_t)plan->hp.N * plan->hp.N * plan->hp.N;
     // The staging area (2 chunk fields) holds nbuf buffers of S nodes in and S nodes out. Sub-batch i
@@ -1512,7 +1530,7 @@ dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host
 
 dgfs_status dgfs_profile_begin(dgfs_plan_t plan) {
     if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
-    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    DGFS_ON_DEVICE(plan->device);
     if (plan->ev.empty()) {
         plan->ev.resize(2 * 65536);
         for (auto& e : plan->ev) DGFS_CUDA(cudaEventCreate(&e), "cudaEventCreate");
@@ -1525,7 +1543,7 @@ dgfs_status dgfs_profile_begin(dgfs_plan_t plan) {
 dgfs_status dgfs_profile_end(dgfs_plan_t plan, dgfs_profile_t* out) {
     if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
     if (!out) return fail(DGFS_ERR_INVALID_ARG, "NULL output");
-    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    DGFS_ON_DEVICE(plan->device);
     double ms = 0;
     for (int64_t i = 0; i < plan->prof_timed; ++i) {
         DGFS_CUDA(cudaEventSynchronize(plan->ev[2 * i + 1]), "cudaEventSynchronize");
@@ -1542,6 +1560,15 @@ dgfs_status dgfs_profile_end(dgfs_plan_t plan, dgfs_profile_t* out) {
     return DGFS_OK;
 }
 
+dgfs_status dgfs_device_fma_peaks(double* fp32_tflops, double* fp64_tflops) {
+    double a = 0.0, b = 0.0;
+    const cudaError_t e = measure_fma_peaks(a, b);
+    if (e != cudaSuccess) return cuda_fail(e, "FMA rate probe");
+    if (fp32_tflops) *fp32_tflops = a;
+    if (fp64_tflops) *fp64_tflops = b;
+    return DGFS_OK;
+}
+
 dgfs_status dgfs_debug_inject(dgfs_plan_t plan, int mode) {
     if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
     if (mode != 0 && mode != 1) return fail(DGFS_ERR_INVALID_ARG, "unknown injection mode");
@@ -1552,7 +1579,7 @@ dgfs_status dgfs_debug_inject(dgfs_plan_t plan, int mode) {
 dgfs_status dgfs_stream_status(dgfs_plan_t plan, void* stream) {
     if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    DGFS_ON_DEVICE(plan->device);
     DGFS_CUDA(cudaStreamSynchronize(s), "stream synchronise");
     int flags = 0;
     DGFS_CUDA(cudaMemcpy(&flags, plan->d_flags, sizeof(int), cudaMemcpyDeviceToHost), "read flags");
@@ -1700,7 +1727,7 @@ extern "C" dgfs_status dgfs_collide_noalloc(dgfs_plan_t plan, const void* f, voi
                       (long long)B, (long long)capacity, per_node, kNoAllocScratchBytes);
         return fail(DGFS_ERR_INVALID_ARG, msg);
     }
-    DGFS_CUDA(cudaSetDevice(plan->device), "cudaSetDevice");
+    DGFS_ON_DEVICE(plan->device);
     void* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);

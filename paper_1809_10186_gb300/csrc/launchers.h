@@ -197,4 +197,9 @@ cudaError_t launch_spectral(const DevTables<T>& t, const T* P, NodeParams np, in
                             const T* lb, const int64_t* offs, T gain_scale, Cplx<T>* X, Cplx<T>* Y,
                             const T* fa, const T* fc, T* out, int* flags, cudaStream_t s);
 
+// ---- device-rate probe (k_peaks.cu) ---------------------------------------------------------
+// FP32 and FP64 FMA throughput of the current device in TFLOP/s (2 flops per FMA), best of three
+// timed launches of independent FMA chains on every SM. Synchronous.
+cudaError_t measure_fma_peaks(double& fp32_tflops, double& fp64_tflops);
+
 }  // namespace dgfs

@@ -1,10 +1,17 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Error measure: relative L2 error of Q against the oracle, normalised by the oracle's loss
-term ||Q-|| (the magnitude of the quantities the kernels add up; gain and loss nearly cancel,
-so ||Q|| can be a few percent of it). The error normalised by ||Q|| is printed as well.
-Tolerances per precision (derived in the design notes from the unit round-off and the
-length of the sums): FP64 1e-10, FP32 1e-5, F16S 1e-3, BF16S 3e-3.
+Error measure: the relative L2 error of a batch, ||Q_gpu - Q_oracle|| / ||Q_oracle|| with all
+checked nodes taken as one vector, and the same error normalised by the oracle's loss term ||Q-||
+(the magnitude of what the kernels add up: gain and loss cancel to ||Q|| = 0.7-14 % of ||Q-|| on
+the two-Maxwellian workloads). Both are asserted against the tolerance of the precision; the
+largest per-node values of both are printed. Per node, ||Q||-normalised FP32 errors cannot reach
+1e-5 at the nodes nearest equilibrium: an FP32 Fourier stage alone (exact translates) gives
+4.7e-5 there (tests/test_precision_floor.py), so the per-node figure is reported, not asserted.
+
+Tolerances (batch, by ||Q|| and by ||Q-||): FP64 1e-10; FP32 1e-5; F16S 1e-3; BF16S 1e-2 by ||Q||
+and 1e-3 by ||Q-|| (bf16's 8-bit significand rounds the three stored intermediates of every
+translate: about 5e-3 by ||Q|| at the N = 32 workload, so BF16S does not meet the 1e-3 of the
+BF16-split tolerance; the split-data mode does).
 """
 import math
 
@@ -15,12 +22,13 @@ import torch
 import oracle as O
 from paper_1809_10186_gb300 import binding, workloads as W
 
+from oracle_refs import batch_errors, references, sample_nodes
+
 pytestmark = pytest.mark.gpu
 
-# 16-bit modes: data operands rounded to 16 bits between passes. fp16 (11-bit significand,
-# unit round-off 2^-11): observed <= 2e-4; bf16 (8-bit significand, 2^-8): observed <= 1.1e-3,
-# i.e. about 8x more, as the significands predict.
-TOL = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-3, "bf16s": 3e-3}
+TOL_Q = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-3, "bf16s": 1e-2}
+TOL_L = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-3, "bf16s": 1e-3}
+TOL = TOL_L
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -47,6 +55,16 @@ def _errors(got, ref, loss):
     return d / np.linalg.norm(loss), d / np.linalg.norm(ref)
 
 
+def _check(prec, got, ref, loss, label, tol_q=None, tol_l=None):
+    """Assert the batch errors of Q (lists of per-node arrays) by ||Q|| and by ||Q-||."""
+    e = batch_errors(got, ref, loss)
+    print("%s %s: batch err/|Q| %.3g err/|Q-| %.3g; worst node err/|Q| %.3g err/|Q-| %.3g" % (
+        label, prec, e["batch_q"], e["batch_loss"], e["node_q"], e["node_loss"]))
+    assert e["batch_q"] < (tol_q or TOL_Q[prec]), e
+    assert e["batch_loss"] < (tol_l or TOL_L[prec]), e
+    return e
+
+
 def _oplan(N, L, gamma, M, Nrho, **kw):
     return O.OraclePlan(N, L, gamma=gamma, M=M, Nrho=Nrho, nyquist="sym", **kw)
 
@@ -65,11 +83,8 @@ def test_collide_rough_small(prec, N):
     q = plan.collide(_dev(F, prec)).double().cpu().numpy()
     plan.stream_status()
     op = _oplan(N, L, gamma, M, Nr)
-    for i in range(3):
-        ref = O.fast_Q(op, F[i])
-        e_loss, e_q = _errors(q[i], ref, np.real(O.loss_Q(op, F[i], F[i])))
-        print(prec, N, i, "err/|Q-| %.3g  err/|Q| %.3g" % (e_loss, e_q))
-        assert e_loss < TOL[prec]
+    refs = [O.fast_Q(op, F[i]) for i in range(3)]
+    _check(prec, list(q), refs, [np.real(O.loss_Q(op, F[i], F[i])) for i in range(3)], "rough N=%d" % N)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -83,12 +98,13 @@ def test_collide2_jvp_dgamma_small(prec):
     jv = plan.collide_jvp(f, g).double().cpu().numpy()
     dg = plan.collide_dgamma(f).double().cpu().numpy()
     plan.stream_status()
-    for i in range(2):
-        scale = np.linalg.norm(np.real(O.loss_Q(op, F[i], G[i])))
-        assert np.linalg.norm(q2[i] - O.fast_Q(op, F[i], G[i])) / scale < TOL[prec]
-        assert np.linalg.norm(jv[i] - O.jvp(op, F[i], G[i])) / scale < TOL[prec]
-        ref = O.dQ_dgamma(op, F[i])
-        assert np.linalg.norm(dg[i] - ref) / np.linalg.norm(ref) < 10 * TOL[prec]
+    loss = [np.real(O.loss_Q(op, F[i], G[i])) for i in range(2)]
+    _check(prec, list(q2), [O.fast_Q(op, F[i], G[i]) for i in range(2)], loss, "Q(f,g)")
+    jloss = [np.real(O.loss_Q(op, F[i], G[i]) + O.loss_Q(op, G[i], F[i])) for i in range(2)]
+    _check(prec, list(jv), [O.jvp(op, F[i], G[i]) for i in range(2)], jloss, "JVP")
+    dop = O.dgamma_plan(op)
+    _check(prec, list(dg), [O.dQ_dgamma(op, F[i]) for i in range(2)],
+           [np.real(O.loss_Q(dop, F[i], F[i])) for i in range(2)], "dQ/dgamma")
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -99,9 +115,9 @@ def test_vjp_small(prec):
     op = O.OraclePlan(N, L, gamma=gamma, M=M, Nrho=6, nyquist="sym")
     gf = plan.collide_vjp(_dev(F, prec), _dev(U, prec)).double().cpu().numpy()
     plan.stream_status()
-    for i in range(2):
-        ref = O.vjp(op, F[i], U[i])
-        assert np.linalg.norm(gf[i] - ref) / np.linalg.norm(ref) < 10 * TOL[prec]
+    e = batch_errors(list(gf), [O.vjp(op, F[i], U[i]) for i in range(2)])
+    print("VJP", prec, e)
+    assert e["batch_q"] < TOL_Q[prec]
 
 
 @pytest.mark.parametrize("prec", ["f16s", "bf16s"])
@@ -118,14 +134,14 @@ def test_tensor_core_plans_bilinear_and_adjoint_calls(prec):
     gf = plan.collide_vjp(f, g).double().cpu().numpy()
     qq = plan.collide(f).double().cpu().numpy()
     plan.stream_status()
-    for i in range(2):
-        scale = np.linalg.norm(np.real(O.loss_Q(op, F[i], G[i])))
-        assert np.linalg.norm(q2[i] - O.fast_Q(op, F[i], G[i])) / scale < TOL["fp32"]
-        assert np.linalg.norm(jv[i] - O.jvp(op, F[i], G[i])) / scale < TOL["fp32"]
-        ref = O.vjp(op, F[i], G[i])
-        assert np.linalg.norm(gf[i] - ref) / np.linalg.norm(ref) < 10 * TOL["fp32"]
-        e, _ = _errors(qq[i], O.fast_Q(op, F[i]), np.real(O.loss_Q(op, F[i], F[i])))
-        assert e < TOL[prec]
+    loss = [np.real(O.loss_Q(op, F[i], G[i])) for i in range(2)]
+    _check("fp32", list(q2), [O.fast_Q(op, F[i], G[i]) for i in range(2)], loss, "Q(f,g) of a %s plan" % prec)
+    jloss = [np.real(O.loss_Q(op, F[i], G[i]) + O.loss_Q(op, G[i], F[i])) for i in range(2)]
+    _check("fp32", list(jv), [O.jvp(op, F[i], G[i]) for i in range(2)], jloss, "JVP of a %s plan" % prec)
+    e = batch_errors(list(gf), [O.vjp(op, F[i], G[i]) for i in range(2)])
+    assert e["batch_q"] < TOL_Q["fp32"], e
+    _check(prec, list(qq), [O.fast_Q(op, F[i]) for i in range(2)],
+           [np.real(O.loss_Q(op, F[i], F[i])) for i in range(2)], "Q(f,f)")
 
 
 # ---- the workload configurations -------------------------------------------------------------
@@ -257,15 +273,15 @@ def test_slab_n24_fp32_all_nodes():
     q = plan.collide(_dev(F, "fp32")).double().cpu().numpy()
     plan.stream_status()
     op = _oplan(N, L, cfg["gamma"], cfg["M"], cfg["Nrho"])
-    worst = (0, 0)
-    for i in range(B):
-        e = _errors(q[i], O.fast_Q(op, F[i]), np.real(O.loss_Q(op, F[i], F[i])))
-        worst = max(worst, e)
-    print("slab N=24 FP32 worst err/|Q-| %.3g err/|Q| %.3g" % worst)
-    assert worst[0] < TOL["fp32"]
+    _check("fp32", list(q), [O.fast_Q(op, F[i]) for i in range(B)],
+           [np.real(O.loss_Q(op, F[i], F[i])) for i in range(B)], "slab N=24, all %d nodes" % B)
 
 
-def _vhs32(cfg_name, prec, nodes_checked):
+N32_NODES = 24   # nodes of the 2048-node launch checked against the oracle
+
+
+def _vhs32(cfg_name, prec, nodes_checked=N32_NODES):
+    """The whole 2048-node launch on the device; batch errors on `nodes_checked` sampled nodes."""
     cfg = W.CONFIGS[cfg_name]
     N, L, B = cfg["N"], cfg["L"], cfg["B"]
     F, _ = W.two_maxwellian(B, N, L, cfg["seed"], dtype=np.float32)
@@ -273,24 +289,17 @@ def _vhs32(cfg_name, prec, nodes_checked):
                         svd_tol=cfg.get("svd_tol", 0.0), precision=prec)
     q = plan.collide(_dev(F, prec)).double().cpu().numpy()
     plan.stream_status()
-    op = _oplan(N, L, cfg["gamma"], cfg["M"], cfg["Nrho"], svd_rank=plan.info["svd_rank_used"]
-                if cfg.get("svd_tol") else 0)
-    rng = np.random.default_rng(5)
-    idx = sorted(set([0, B - 1] + list(rng.choice(B, nodes_checked - 2, replace=False))))
-    worst = (0, 0)
-    for i in idx:
-        Fi = F[i].astype(np.float64)
-        worst = max(worst, _errors(q[i], O.fast_Q(op, Fi), np.real(O.loss_Q(op, Fi, Fi))))
-    # every node: finite, and mass of Q small against the loss mass
     assert np.isfinite(q).all()
-    return worst, plan
+    idx = sample_nodes(B, nodes_checked)
+    refs = references("Q", cfg_name, idx, plan.info["svd_rank_used"] if cfg.get("svd_tol") else 0)
+    e = _check(prec, [q[i] for i in idx], [refs[i]["Q"] for i in idx], [refs[i]["loss"] for i in idx],
+               "N=32 %d-node launch, %d nodes checked (rank %d)" % (B, len(idx), plan.info["svd_rank_used"]))
+    return e, plan
 
 
 def test_vhs_n32_full_batch_fp32_sampled():
     """The primary workload's launch (2048 nodes, N = 32, M = 38, SVD at 1e-8) in FP32."""
-    worst, plan = _vhs32("vhs_n32", "fp32", 4)
-    print("N=32 FP32 rank %d worst err/|Q-| %.3g err/|Q| %.3g" % (plan.info["svd_rank_used"], *worst))
-    assert worst[0] < TOL["fp32"]
+    _vhs32("vhs_n32", "fp32")
 
 
 def test_derivatives_n32_fp32():
@@ -305,17 +314,19 @@ def test_derivatives_n32_fp32():
     gf = plan.collide_vjp(f, u).double().cpu().numpy()
     dg = plan.collide_dgamma(f).double().cpu().numpy()
     plan.stream_status()
-    op = _oplan(N, L, cfg["gamma"], cfg["M"], cfg["Nrho"])
-    for i in (0, B - 1):
-        Fi, Vi, Ui = (x[i].astype(np.float64) for x in (F, V, U))
-        for got, ref, name in ((jv[i], O.jvp(op, Fi, Vi), "jvp"), (gf[i], O.vjp(op, Fi, Ui), "vjp"),
-                               (dg[i], O.dQ_dgamma(op, Fi), "dgamma")):
-            e = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-            print("N=32", name, "node", i, "rel err %.3g" % e)
-            assert e < 1e-4
-        # dot-product identity on the device results
-        lhs, rhs = float(np.sum(Ui * jv[i])), float(np.sum(gf[i] * Vi))
-        assert abs(lhs - rhs) < 1e-4 * abs(lhs)
+    idx = sample_nodes(B, 16)
+    refs = references("grad", "grad_n32", idx)
+    for name, got, lossname in (("jvp", jv, "jvp_loss"), ("vjp", gf, None), ("dgamma", dg, "dgamma_loss")):
+        e = batch_errors([got[i] for i in idx], [refs[i][name] for i in idx],
+                         [refs[i][lossname] for i in idx] if lossname else None)
+        print("N=32 FP32 %s on %d nodes: %s" % (name, len(idx), e))
+        assert e["batch_q"] < TOL_Q["fp32"], (name, e)
+        if lossname:
+            assert e["batch_loss"] < TOL_L["fp32"], (name, e)
+    # dot-product identity on the device results, every checked node
+    for i in idx:
+        lhs, rhs = float(np.dot(U[i].ravel(), jv[i].ravel())), float(np.dot(gf[i].ravel(), V[i].ravel()))
+        assert abs(lhs - rhs) < 1e-5 * abs(lhs), (i, lhs, rhs)
 
 
 def test_jvp_central_difference_fp64():
@@ -499,6 +510,48 @@ def test_autograd_function():
     assert np.linalg.norm(g[0].cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-10
 
 
+def test_autograd_gamma_gradient():
+    """gamma as a differentiable input of binding.collide: reverse mode with a scalar gamma and with
+    one gamma per node, and forward mode, against the oracle's dQ/dgamma contracted with the upstream
+    gradient and against central differences of the device Q in gamma (b held fixed), FP64."""
+    N, L, g0, M = 16, 5.0, 0.38, 12
+    plan = binding.Plan(N=N, L=L, gamma=g0, M=M, N_rho=N, precision="fp64")
+    b = plan.info["b"]
+    F, _ = W.two_maxwellian(2, N, L, 31)
+    Ug = W.directions(2, N, 32)
+    u = _dev(Ug, "fp64")
+    op = O.OraclePlan(N, L, gamma=g0, b=b, M=M, Nrho=N, nyquist="sym")
+    per_node = np.array([np.sum(Ug[i] * O.dQ_dgamma(op, F[i])) for i in range(2)])
+    # scalar gamma, together with the gradient of f
+    f = _dev(F, "fp64").requires_grad_(True)
+    gam = torch.tensor(g0, dtype=torch.float64, device="cuda", requires_grad=True)
+    gg, gf = torch.autograd.grad((binding.collide(plan, f, gam) * u).sum(), (gam, f))
+    assert abs(gg.item() - per_node.sum()) < 1e-10 * abs(per_node.sum())
+    assert np.linalg.norm(gf[0].cpu().numpy() - O.vjp(op, F[0], Ug[0])) < 1e-10 * np.linalg.norm(gf[0].cpu().numpy())
+    # central differences of the device Q in gamma
+    h = 1e-4
+    pp = binding.Plan(N=N, L=L, gamma=g0 + h, b=b, M=M, N_rho=N, precision="fp64")
+    pm = binding.Plan(N=N, L=L, gamma=g0 - h, b=b, M=M, N_rho=N, precision="fp64")
+    fd = (((pp.collide(f.detach()) - pm.collide(f.detach())) * u).sum() / (2 * h)).item()
+    assert abs(gg.item() - fd) < 1e-6 * abs(fd)
+    # one gamma per node
+    gvec = torch.full((2,), g0, dtype=torch.float64, device="cuda", requires_grad=True)
+    (gv,) = torch.autograd.grad((binding.collide(plan, f, gvec) * u).sum(), (gvec,))
+    np.testing.assert_allclose(gv.cpu().numpy(), per_node, rtol=1e-10)
+    # forward mode: tangent of Q along gamma_dot = 1 is dQ/dgamma
+    import torch.autograd.forward_ad as fwAD
+    with fwAD.dual_level():
+        gd = fwAD.make_dual(gam.detach(), torch.ones((), dtype=torch.float64, device="cuda"))
+        qd = binding.collide(plan, f.detach(), gd)
+        tangent = fwAD.unpack_dual(qd).tangent
+    for i in range(2):
+        ref = O.dQ_dgamma(op, F[i])
+        assert np.linalg.norm(tangent[i].cpu().numpy() - ref) < 1e-10 * np.linalg.norm(ref)
+    # a gamma that differs from the plan's is refused
+    with pytest.raises(ValueError):
+        binding.collide(plan, f, torch.tensor(g0 + 0.1, dtype=torch.float64, device="cuda"))
+
+
 # ---- tensor-core (tcgen05) translates ---------------------------------------------------------
 
 @pytest.mark.parametrize("prec", ["f16s", "bf16s"])
@@ -511,11 +564,8 @@ def test_tensor_core_collide(prec, N, kind):
     q = plan.collide(_dev(F, "fp32")).double().cpu().numpy()
     plan.stream_status()
     op = _oplan(N, L, gamma, M, N)
-    for i in range(3):
-        ref = O.fast_Q(op, F[i])
-        e_loss, e_q = _errors(q[i], ref, np.real(O.loss_Q(op, F[i], F[i])))
-        print(prec, N, kind, i, "err/|Q-| %.3g  err/|Q| %.3g" % (e_loss, e_q))
-        assert e_loss < TOL[prec]
+    _check(prec, list(q), [O.fast_Q(op, F[i]) for i in range(3)],
+           [np.real(O.loss_Q(op, F[i], F[i])) for i in range(3)], "tensor cores N=%d %s" % (N, kind))
 
 
 @pytest.mark.parametrize("N,rule", [(16, 6), (16, 26), (16, 38), (32, 6), (32, "one_pair"), (32, "two_pairs")])
@@ -541,20 +591,15 @@ def test_tensor_core_sphere_rules(N, rule):
     plan.stream_status()
     op = O.OraclePlan(N, L, gamma=gamma, Nrho=N, nyquist="sym", **okw)
     assert plan.info["n_pairs"] == len(op.sigma)
-    for i in range(2):
-        ref = O.fast_Q(op, F[i])
-        e_loss, e_q = _errors(q[i], ref, np.real(O.loss_Q(op, F[i], F[i])))
-        print("f16s N=%d rule %s node %d err/|Q-| %.3g err/|Q| %.3g" % (N, rule, i, e_loss, e_q))
-        assert e_loss < TOL["f16s"]
+    _check("f16s", list(q), [O.fast_Q(op, F[i]) for i in range(2)],
+           [np.real(O.loss_Q(op, F[i], F[i])) for i in range(2)], "N=%d rule %s" % (N, rule))
     plan.close()
 
 
 @pytest.mark.parametrize("prec", ["f16s", "bf16s"])
 def test_tensor_core_vhs_n32_full_batch_sampled(prec):
     """The primary workload's launch (2048 nodes, N = 32, M = 38, SVD 1e-8) on tensor cores."""
-    worst, plan = _vhs32("vhs_n32", prec, 4)
-    print("N=32", prec, "rank %d worst err/|Q-| %.3g err/|Q| %.3g" % (plan.info["svd_rank_used"], *worst))
-    assert worst[0] < TOL[prec]
+    _vhs32("vhs_n32", prec)
 
 
 def test_tensor_core_chunking_and_determinism():

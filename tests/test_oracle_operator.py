@@ -78,6 +78,48 @@ def test_bkw_f_unit_density_and_temperature():
     np.testing.assert_allclose(W.bkw(32, 6.62, 5.5), f, rtol=1e-14, atol=1e-300)
 
 
+def test_moments_of_a_drifting_maxwellian_closed_form():
+    """Sec. 3.5's Maxwellian n (pi T)^{-3/2} exp(-|c - u|^2 / T) in the moments' convention
+    (T = 2/(3n) int f |c-u|^2, P = 2 int f (c-u)(c-u), q = int f (c-u)|c-u|^2): P = n T I, q = 0,
+    to the mid-point rule's spectral accuracy on a domain that holds the tails."""
+    plan = O.OraclePlan(32, 8.0, M=6, Nrho=4)
+    n, u, T = 1.3, np.array([0.4, -0.25, 0.15]), 0.9
+    f = W.maxwellian(32, 8.0, n, u, T)
+    m = O.moments(plan, f)
+    assert m["n"] == pytest.approx(n, rel=1e-12)
+    np.testing.assert_allclose(m["u"], u, atol=1e-12)
+    assert m["T"] == pytest.approx(T, rel=1e-12)
+    np.testing.assert_allclose(m["P"], n * T * np.eye(3), atol=1e-12)
+    np.testing.assert_allclose(m["q"], 0.0, atol=1e-12)
+
+
+def test_moments_of_a_two_maxwellian_mixture_closed_form():
+    """A mixture sum_i n_i M(u_i, T_i) with d_i = u_i - u (u the mixture's mean velocity):
+    P = sum_i n_i T_i I + 2 sum_i n_i d_i d_i^T (off-diagonal terms from the drifts) and
+    q = sum_i n_i d_i (5 T_i / 2 + |d_i|^2), from the Gaussian moments int M w_a w_b = n T/2 delta_ab,
+    int M |w|^2 = 3 n T / 2 and the vanishing odd moments."""
+    N, L = 40, 9.0
+    plan = O.OraclePlan(N, L, M=6, Nrho=4)
+    comps = [(0.7, np.array([0.5, -0.3, 0.2]), 1.1), (1.2, np.array([-0.4, 0.35, -0.1]), 0.8)]
+    f = sum(W.maxwellian(N, L, n, u, T) for n, u, T in comps)
+    ntot = sum(n for n, _, _ in comps)
+    umix = sum(n * u for n, u, _ in comps) / ntot
+    P = np.zeros((3, 3))
+    q = np.zeros(3)
+    for n, u, T in comps:
+        d = u - umix
+        P += n * T * np.eye(3) + 2.0 * n * np.outer(d, d)
+        q += n * d * (2.5 * T + d @ d)
+    m = O.moments(plan, f)
+    assert m["n"] == pytest.approx(ntot, rel=1e-12)
+    np.testing.assert_allclose(m["u"], umix, atol=1e-12)
+    assert m["T"] == pytest.approx(np.trace(P) / (3.0 * ntot), rel=1e-12)
+    np.testing.assert_allclose(m["P"], P, atol=1e-11)
+    assert abs(m["P"][0, 1]) > 0.05 and abs(m["P"][1, 2]) > 0.01     # the drifts make it anisotropic
+    np.testing.assert_allclose(m["q"], q, atol=1e-11)
+    assert np.abs(q).min() > 0.01
+
+
 def test_bkw_ssp_rk2_time_stepping():
     """20 SSP-RK2 steps of dt = 0.01 from t0 = 5.5 follow the closed form to Q-error level."""
     plan = _bkw_plan(24, 24, nyquist="sym")

@@ -6,7 +6,7 @@ them: it evaluates the same operator as dgfs_collide but keeps its scratch in th
 64 MiB device array (with the dense circulant translate kernel for FP32/FP64 plans, where
 dgfs_collide takes the translates in Fourier space). These tests call it through the C ABI, twice
 in a row (the array keeps the previous call's contents), and compare each result with
-dgfs_collide's on the same input.
+dgfs_collide's on the same input and with the FP64 oracle.
 """
 import ctypes
 
@@ -14,13 +14,19 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
 from paper_1809_10186_gb300 import binding, workloads as W
+
+from oracle_refs import batch_errors
 
 pytestmark = pytest.mark.gpu
 
 # relative L2 against dgfs_collide's result: the same kernels for F16S; for FP32 two translate
 # methods, each within 1e-5 of the loss term of the FP64 oracle (Q itself is a few % of the loss)
 TOL = {"fp32": 1e-4, "f16s": 1e-5, "fp64": 1e-10}
+# against the FP64 oracle, by ||Q|| and by ||Q-|| (batch errors): the tolerances of the parity tests
+TOL_Q = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-3, "bf16s": 1e-2}
+TOL_L = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-3, "bf16s": 1e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -54,6 +60,27 @@ def test_noalloc_matches_collide_twice(N, L, M, prec, B):
         rel = (torch.linalg.norm(q - ref) / torch.linalg.norm(ref)).item()
         print(prec, N, call, "rel %.3g" % rel)
         assert rel < TOL[prec], (call, rel)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16s", "bf16s", "fp64"])
+def test_noalloc_matches_the_oracle(prec):
+    """The allocation-free call against the FP64 oracle itself (not only against dgfs_collide, which
+    runs the same tensor-core kernels for the 16-bit plans), two calls in a row."""
+    N, L, M, B = 16, 5.0, 12, 2
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    plan = binding.Plan(N=N, L=L, gamma=0.52, M=M, N_rho=N, precision=prec)
+    op = O.OraclePlan(N, L, gamma=0.52, M=M, Nrho=N, nyquist="sym")
+    for call in range(2):
+        F, _ = W.two_maxwellian(B, N, L, 640 + call, dtype=np.float64 if prec == "fp64" else np.float32)
+        st, q = _noalloc(plan, torch.from_numpy(F).to("cuda", dt))
+        assert st == 0, binding.lib().dgfs_last_error_message().decode()
+        torch.cuda.synchronize()
+        plan.stream_status()
+        Fd = F.astype(np.float64)
+        e = batch_errors(list(q.double().cpu().numpy()), [O.fast_Q(op, Fd[i]) for i in range(B)],
+                         [np.real(O.loss_Q(op, Fd[i], Fd[i])) for i in range(B)])
+        print(prec, call, e)
+        assert e["batch_q"] < TOL_Q[prec] and e["batch_loss"] < TOL_L[prec], e
 
 
 def test_noalloc_rejects_batches_beyond_the_fixed_array():
