@@ -32,8 +32,13 @@ METRIC = "Q(f,f) node-evals/s at N=32 VHS, % roofline, mixed-prec vs FP32 at sta
 WORKLOAD = "vhs_n32"
 # Tolerances of the relative L2 error against the FP64 oracle, over the sampled nodes as one
 # vector, normalised by ||Q|| and by the loss term ||Q-||.
-TOL_Q = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-3, "bf16s": 1e-2}
-TOL_L = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-3, "bf16s": 1e-3}
+TOL_Q = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-2, "bf16s": 5e-2, "f16x3": 1e-5, "bf16x3": 1e-3}
+TOL_L = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-3, "bf16s": 3e-3, "f16x3": 1e-5, "bf16x3": 1e-4}
+MODES = ("fp32", "f16s", "bf16s", "f16x3", "bf16x3")
+DTYPES = {"fp32": "f32", "fp64": "f64", "f16s": "f16 data, f16 hi+lo filters, f32 accumulate",
+          "bf16s": "bf16 data, bf16 hi+lo filters, f32 accumulate",
+          "f16x3": "f16 hi+lo data and filters (3 products), f32 accumulate",
+          "bf16x3": "bf16 hi+lo data and filters (3 products), f32 accumulate"}
 
 
 def _args():
@@ -42,8 +47,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="f16s", choices=["fp32", "f16s", "bf16s"],
-                    help="f16s: tensor-core translates, fp16 data + split fp16 filters (default)")
+    ap.add_argument("--prec", default="f16s", choices=["fp32", "f16s", "bf16s", "f16x3", "bf16x3"],
+                    help="f16s: tensor-core translates, fp16 data + split fp16 filters; f16x3 / bf16x3: data and "
+                         "filters split (three products)")
     ap.add_argument("--nodes", type=int, default=None, help="nodes per GPU (default 2048)")
     ap.add_argument("--chunk", type=int, default=0,
                     help="nodes per internal chunk (plan max_batch); 0: the whole per-GPU batch in one chunk")
@@ -179,7 +185,8 @@ def translate_flops_per_node(N, Nrho, npairs, prec):
 
     Tensor-core modes: per (radial point, pair) two 3-D translates, each three dense N x N
     circulant passes over N^2 lines (2 N^4 flops per pass), every filter split into hi + lo parts
-    (two products per contraction), then the product and weighted accumulation (3 N^3).
+    (two products per contraction; three, hi hi + hi lo + lo hi, when the data are split too), then
+    the product and weighted accumulation (3 N^3).
     FP32 / FP64 (N = 8, 16, 32): translates in Fourier space, one complex 3-D inverse transform per
     (radial point, pair) (radix-2: 5 N^3 log2 N^3) giving both translates, plus ~17 flops per
     point of phases, product and accumulation.
@@ -188,7 +195,7 @@ def translate_flops_per_node(N, Nrho, npairs, prec):
         return Nrho * npairs * (5.0 * N ** 3 * math.log2(N ** 3) + 17.0 * N ** 3)
     mma = 12.0 * N ** 4
     elem = 3.0 * N ** 3
-    mult = {"fp32": 1, "fp64": 1, "f16s": 2, "bf16s": 2}[prec]
+    mult = {"fp32": 1, "fp64": 1, "f16s": 2, "bf16s": 2, "f16x3": 3, "bf16x3": 3}[prec]
     return Nrho * npairs * (mult * mma + elem)
 
 
@@ -755,8 +762,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "node-evals/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "fp64": "f64", "f16s": "f16 operands (filters hi+lo), f32 accumulate",
-                      "bf16s": "bf16 operands (filters hi+lo), f32 accumulate"}[prec],
+            "dtype": DTYPES[prec],
             "data": "synthetic",
             "config": {"workload": "%s: %d two-Maxwellian nodes/GPU, N=32 on [-7,7]^3, omega=0.74, "
                                    "N_rho=32, M=%d, SVD 1e-8" % (WORKLOAD, B, M),
@@ -791,7 +797,7 @@ def main():
     values = {prec: value}
     if not a.no_compare:
         line["compare"] = {}
-        for other in ("fp32", "f16s", "bf16s"):
+        for other in MODES:
             if other == prec:
                 continue
             po = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=M, N_rho=Nr, svd_tol=cfg["svd_tol"], precision=other)

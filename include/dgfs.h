@@ -63,7 +63,14 @@ typedef enum {
     DGFS_PREC_F16S = 2,   /* translates on tcgen05 tensor cores: fp16 data operands with a per-node
                              power-of-two scale, every filter split into fp16 hi + lo parts (two
                              products), FP32 accumulation in tensor memory; FP32 elsewhere. N = 16, 32 */
-    DGFS_PREC_BF16S = 3   /* as F16S with bf16 operands (no scaling)                                 */
+    DGFS_PREC_BF16S = 3,  /* as F16S with bf16 operands (no scaling)                                 */
+    DGFS_PREC_F16X3 = 4,  /* translates on tcgen05 tensor cores with every data operand AND every
+                             filter split into an fp16 hi part and a lo part times 2^11: three
+                             products per contraction (hi hi, hi lo, lo hi), FP32 accumulation, so
+                             the translates carry about FP32 accuracy; two CTAs of a thread-block
+                             cluster per node and radial block, one per translate sign. FP32
+                             elsewhere. N = 16, 32                                                   */
+    DGFS_PREC_BF16X3 = 5  /* as F16X3 with bf16 hi and lo parts (lo times 2^8): 16 significand bits */
 } dgfs_precision;
 
 typedef enum {

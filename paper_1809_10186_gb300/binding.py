@@ -15,7 +15,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libdgfs.so")
 
-PRECISIONS = {"fp64": 0, "fp32": 1, "f16s": 2, "bf16s": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1, "f16s": 2, "bf16s": 3, "f16x3": 4, "bf16x3": 5}
 LOSS_MODES = {"paper": 0, "conservative": 1}
 STATUS = {0: "DGFS_OK", 1: "DGFS_ERR_INVALID_ARG", 2: "DGFS_ERR_UNSUPPORTED", 3: "DGFS_ERR_OOM",
           4: "DGFS_ERR_CUDA", 5: "DGFS_ERR_TIMEOUT", 6: "DGFS_ERR_NUMERIC", 7: "DGFS_ERR_STATE"}

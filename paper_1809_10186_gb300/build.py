@@ -22,7 +22,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]
-SOURCES = ["plan_host.cpp", "capi.cu", "k_gain_f32.cu", "k_gain_f64.cu", "k_fourier.cu", "k_spectral.cu", "k_dg.cu", "k_time.cu", "k_vss.cu", "k_slab.cu", "tc_gain.cu", "k_peaks.cu"]
+SOURCES = ["plan_host.cpp", "capi.cu", "k_gain_f32.cu", "k_gain_f64.cu", "k_fourier.cu", "k_spectral.cu", "k_dg.cu", "k_time.cu", "k_vss.cu", "k_slab.cu", "tc_gain.cu", "tc_gain3.cu", "k_peaks.cu"]
 
 
 def _nvcc():

@@ -123,7 +123,9 @@ struct dgfs_plan_s {
 
 namespace {
 
-bool is_tc(int prec) { return prec == DGFS_PREC_F16S || prec == DGFS_PREC_BF16S; }
+bool is_tc(int prec) {
+    return prec == DGFS_PREC_F16S || prec == DGFS_PREC_BF16S || prec == DGFS_PREC_F16X3 || prec == DGFS_PREC_BF16X3;
+}
 
 size_t elem_size(int prec) { return prec == DGFS_PREC_FP64 ? 8 : 4; }
 
@@ -588,7 +590,7 @@ dgfs_status dgfs_plan_desc_init(dgfs_plan_desc* d) {
 dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) {
     if (!desc || !plan_out) return fail(DGFS_ERR_INVALID_ARG, "NULL argument");
     *plan_out = nullptr;
-    if (desc->precision < DGFS_PREC_FP64 || desc->precision > DGFS_PREC_BF16S)
+    if (desc->precision < DGFS_PREC_FP64 || desc->precision > DGFS_PREC_BF16X3)
         return fail(DGFS_ERR_INVALID_ARG, "unknown precision");
     std::unique_ptr<dgfs_plan_s> p(new (std::nothrow) dgfs_plan_s);
     if (!p) return fail(DGFS_ERR_OOM, "host allocation failed");

@@ -636,6 +636,7 @@ bool tc_supported(int N) { return N == 16 || N == 32; }
 int tc_extra_launches(int) { return 0; }
 
 size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>& blob, TcTables& t) {
+    if (tc3_precision(prec)) return build_tc3_tables(hp, prec, blob, t);
     const int N = hp.N, np = hp.npairs, Nr = hp.Nrho;
     const bool bf = prec == DGFS_PREC_BF16S;
     const double lo_scale = std::ldexp(1.0, bf ? kLoShiftBF16 : kLoShiftF16);
@@ -698,6 +699,7 @@ cudaError_t launch_tc_gain_products(const TcTables& t, int prec, const float* f,
                                     cudaStream_t s, int fault) {
     if (g) return cudaErrorNotSupported;
     if (nodes <= 0) return cudaSuccess;
+    if (tc3_precision(prec)) return launch_tc3_gain_products(t, prec, f, offs, nodes, P, flags, s, fault);
     const bool bf = prec == DGFS_PREC_BF16S;
     switch (t.N) {
         case 16: return bf ? launch_n<16, true>(t, f, offs, nodes, P, flags, s, fault)

@@ -25,4 +25,11 @@ cudaError_t launch_tc_gain_products(const TcTables& t, int prec, const float* f,
                                     const int64_t* offs, int64_t nodes, float* P, int* flags,
                                     cudaStream_t s, int fault = 0);
 
+// The split-data precisions F16X3 and BF16X3 (tc_gain3.cu); build_tc_tables and
+// launch_tc_gain_products dispatch to these for them.
+bool tc3_precision(int prec);
+size_t build_tc3_tables(const HostPlan& hp, int prec, std::vector<unsigned char>& blob, TcTables& t);
+cudaError_t launch_tc3_gain_products(const TcTables& t, int prec, const float* f, const int64_t* offs, int64_t nodes,
+                                     float* P, int* flags, cudaStream_t s, int fault);
+
 }  // namespace dgfs

@@ -24,12 +24,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 }
 
 // The same descriptor split for cheap issue: the constant part (strides, version) with a zero
-// address field, to which the caller adds (byte address >> 4) as a 32-bit offset. Shared-memory
-// addresses stay below 256 KB, so the 14-bit address field never carries into the LBO field.
+// address field, to which the caller adds (byte address >> 4) as a 32-bit offset, masked to the
+// 14-bit field: the shared::cta addresses of a CTA in a thread-block cluster carry its rank in
+// the cluster above bit 23 (measured: 0x1000800 for rank 1 where rank 0 sees 0x800), which would
+// otherwise run into the LBO field; the offset within the CTA stays below 256 KB.
 __host__ __device__ constexpr uint64_t sdesc_base(uint32_t lbo, uint32_t sbo) {
     return ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
-__device__ __forceinline__ uint64_t sdesc_at(uint64_t base, uint32_t addr16) { return base + addr16; }
+__device__ __forceinline__ uint64_t sdesc_at(uint64_t base, uint32_t addr16) { return base + (addr16 & 0x3FFFu); }
 
 // Instruction descriptor of tcgen05.mma.kind::f16: FP32 accumulator, A/B fp16 (0) or bf16 (1),
 // major-ness of A and B (0 = K-major, 1 = MN-major), N >> 3, M >> 4.
@@ -232,6 +234,72 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
 
 __device__ __forceinline__ void st_shared_v4(uint32_t saddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(saddr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+// ---- thread-block clusters: distributed shared memory and cluster-scope barriers ---------------
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// The shared::cluster address of this CTA's shared-memory address `saddr` in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_peer(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+
+// Every thread of every CTA of the cluster (aligned: the whole CTA executes it): the memory
+// operations before the arrive are visible to the cluster after the wait.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// 16 bytes stored into another CTA's shared memory (shared::cluster address).
+__device__ __forceinline__ void st_cluster_v4(uint32_t caddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(caddr), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+// Arrive (count 1) on an mbarrier of another CTA (shared::cluster address), releasing this
+// thread's earlier memory operations at cluster scope.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+
+// As warp_wait, acquiring at cluster scope: for barriers that threads of another CTA arrive on.
+__device__ __forceinline__ bool warp_wait_cluster(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < (1u << 20); ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (__all_sync(0xffffffffu, done != 0)) return true;
+        if ((it & 63u) == 63u && __any_sync(0xffffffffu, *abort != 0)) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
+// Warp-collective commit (elected lane) whose arrive reaches the mbarrier at the same shared-memory
+// offset in every CTA of `mask` (bit r = cluster rank r): one completion signal for several CTAs.
+__device__ __forceinline__ void mma_commit_multicast_warp(uint64_t* bar, uint16_t mask) {
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+                 "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n\t}"
+                 ::"r"(smem_u32(bar)), "h"(mask) : "memory");
+}
+
+// Orders this thread's generic-proxy writes to shared memory anywhere in the cluster before later
+// async-proxy (tensor core) reads of it.
+__device__ __forceinline__ void fence_proxy_async_cluster() { asm volatile("fence.proxy.async.shared::cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void ld_shared_v4(uint32_t saddr, float (&v)[4]) {
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                 : "r"(saddr) : "memory");
 }
 
 }  // namespace tc
