@@ -27,9 +27,11 @@
 // read the other.
 //
 // Per CTA, as in tc_gain.cu: two epilogue warpgroups and a third warpgroup of four MMA warps
-// (pass 1, pass 2, pass 3 into slot 2, pass 3 into slot 3). Warpgroup 0 turns each pass-1 result
-// into the pass-2 operands, warpgroup 1 each pass-2 result into pass-3 operand rows; in the back,
-// warpgroup b forms the products of the pass-3 tiles in slot 2 + b. Every wait is bounded; on
+// (pass 1, pass 2, pass 3 into slot 2, pass 3 into slot 3). Epilogue warpgroup w works on sign w:
+// it turns the sign-w columns of each pass-1 result into the sign-w pass-2 operands and of each
+// pass-2 result into sign-w pass-3 operand rows, software-pipelined (the pass-1 epilogue of front
+// tile i, then the pass-2 epilogue of tile i - 1, whose MMAs ran meanwhile); in the back it forms
+// the products of the pass-3 tiles in slot 2 + w, accumulating P_r in registers. Every wait is bounded; on
 // timeout the CTA raises flag bit 0, every role stops at its next wait, the MMAs and copies in
 // flight are drained, TMEM is freed and no P_r is written; both CTAs meet at a final cluster barrier.
 #include <cmath>
@@ -113,9 +115,9 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
 }
 
 struct Bars3 {
-    uint64_t full1, free1;             // pass-1 slot: MMA -> warpgroup 0, warpgroup 0 -> MMA
-    uint64_t a2_full[2], a2_free[2];   // pass-2 operands of sign s: warpgroup 0 -> MMA, MMA completion -> warpgroup 0
-    uint64_t full2[2], free2[2];       // slots 2, 3 used by pass 2 (warpgroup 1 drains)
+    uint64_t full1, free1;             // pass-1 slot: MMA -> both warpgroups, both warpgroups -> MMA
+    uint64_t a2_full[2], a2_free[2];   // pass-2 operands of sign s: warpgroup s -> MMA, MMA completion -> warpgroup s
+    uint64_t full2[2], free2[2];       // slots 2, 3 used by pass 2 (both warpgroups drain, one sign each)
     uint64_t full3[2], free3[2];       // slots 2, 3 used by pass 3 (warpgroup b drains slot 2 + b)
     uint64_t free3x[2];                // last pass-3 drain of a slot in a pair
     uint64_t a3_full;                  // the 128 pass-2 epilogue threads (of both CTAs) that own rows here wrote them
@@ -245,7 +247,8 @@ __device__ __forceinline__ void mma3_p2_loop(Bars3& bars, uint32_t sb, uint32_t 
 }
 
 // Pass 3 of back tiles k = b, b + 2, ... (both signs) into slot 2 + b once the pass-3 operands of
-// both CTAs' epilogues are complete; its completion is signalled to both CTAs (multicast commit).
+// both CTAs' epilogues are complete (warpgroup b drains the slot); the release of the operands is
+// signalled to both CTAs (multicast commit).
 template <int N, bool BF, int b>
 __device__ __forceinline__ void mma3_p3_loop(Bars3& bars, uint32_t sb, uint32_t tmem, int nseq, volatile int* abort) {
     using G = Geo3<N>;
@@ -318,21 +321,21 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
     if (issuer) {
         if (lane == 0) {
             tc::mbar_init(&bars.full1, 1);
-            tc::mbar_init(&bars.free1, 128);
+            tc::mbar_init(&bars.free1, 256);      // both epilogue warpgroups (one sign each)
             for (int i = 0; i < 2; ++i) {
                 tc::mbar_init(&bars.a2_full[i], 128);
                 tc::mbar_init(&bars.a2_free[i], 1);
             }
             for (int i = 0; i < 2; ++i) {
                 tc::mbar_init(&bars.full2[i], 1);
-                tc::mbar_init(&bars.free2[i], 128);
+                tc::mbar_init(&bars.free2[i], 256);
                 tc::mbar_init(&bars.full3[i], 1);
                 tc::mbar_init(&bars.free3[i], 128);
                 tc::mbar_init(&bars.free3x[i], 128);
                 tc::mbar_init(&bars.filt[i], 1);
                 tc::mbar_init(&bars.fdone[i], 4);
             }
-            tc::mbar_init(&bars.a3_full, 128);   // the pass-2 epilogue threads of both CTAs whose rows are here
+            tc::mbar_init(&bars.a3_full, 256);   // the epilogue threads of both CTAs whose pass-3 rows are here
             tc::mbar_init(&bars.a3_free, 4);     // the pass-3 MMA warps of both CTAs
             tc::mbar_init(&bars.drain, 4);
             tc::fence_mbar_init();
@@ -411,19 +414,21 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
             mma3_p3_loop<N, BF, 1>(bars, sb, tmem, nseq, abort);
     } else {
         tc::setmaxnreg_inc<G::REG_EPI>();
+        // warpgroup w: the epilogues of sign w (w = 0: +s, 1: -s) and the back tiles k = w, w + 2, ...
         const int q = warp & 3, w = warp >> 2;
         const int l = 32 * q + lane, yl = l / N, lz = l % N;
         const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
-        // pass-2 operand row of this thread (pass-1 lane (yl, z = lz)): rows yl N + x', k = z
-        const uint32_t a2_row = sb + G::S_A2 + ((uint32_t)(yl * N) >> 3) * G::A2_SBO + (lz >> 3) * G::A2_LBO + (lz & 7) * 16;
-        // pass-3 operand rows of this thread (pass-2 lane (yl, x' = lz)): rows x' N + z' of the CTA that
-        // owns x' (its x'-tile (x' N) / 128), in that CTA's shared memory (shared::cluster addresses)
+        // pass-2 operand row of this thread (pass-1 lane (yl, z = lz)) in the sign-w region: rows yl N + x', k = z
+        const uint32_t a2_row = sb + G::S_A2 + w * 2 * G::A2_BYTES + ((uint32_t)(yl * N) >> 3) * G::A2_SBO +
+                                (lz >> 3) * G::A2_LBO + (lz & 7) * 16;
+        // pass-3 operand rows of this thread (pass-2 lane (yl, x' = lz)): rows x' N + z' in the CTA that owns
+        // x' (its x'-tile (x' N) / 128), sign-w region, as shared::cluster addresses
         const int owner = (lz * N) / (128 * G::TH), ul = (lz * N) / 128 - owner * G::TH;
-        const uint32_t a3_dst = tc::map_peer(sb + G::S_A3 + ul * G::A3_TS, (uint32_t)owner);
+        const uint32_t a3_dst = tc::map_peer(sb + G::S_A3 + w * 2 * G::A3_BYTES + ul * G::A3_TS, (uint32_t)owner);
         const int rg0 = ((lz * N) & 127) >> 3;   // row group of z' = 0 within the tile
         const bool remote = owner != (int)crank;   // this thread's pass-3 rows live in the peer
         const uint32_t a3full_owner = tc::map_peer(tc::smem_u32(&bars.a3_full), (uint32_t)owner);
-        uint32_t ph_f1 = 0, ph_a2free = 0, ph_a3free = 0, ph_f2 = 0, ph_f3 = 0;   // ph_a2free: bit s = sign s
+        uint32_t ph_f1 = 0, ph_a2free = 0, ph_a3free = 0, ph_f2 = 0, ph_f3 = 0;   // ph_f2: bit per slot
         int p1uses = 0;
         constexpr int NB = (G::TH + 1) / 2;   // back tiles of one warpgroup
         float acc[NB][N];
@@ -442,93 +447,84 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
         for (int rr = 0; rr < rpc; ++rr) {
           for (int pp = 0; pp < npairs; ++pp) {
             const int p = rr * npairs + pp;
-            if (w == 0) {
-                for (int i = 0; i < G::TH; ++i) {   // pass-1 result of front tile i -> pass-2 operands
+            // front, software-pipelined over the front tiles: pass-1 epilogue of tile s, then the pass-2
+            // epilogue of tile s - 1 (whose pass-2 MMAs ran meanwhile)
+            for (int st = 0; st <= G::TH; ++st) {
+                if (st < G::TH) {   // pass-1 result (sign w) of front tile st -> pass-2 operands
                     DGFS_WAITE(&bars.full1, ph_f1);
                     ph_f1 ^= 1u;
                     tc::tc_fence_after();
+                    float hv[N], lv[N];
 #pragma unroll
-                    for (int sg = 0; sg < 2; ++sg) {
-                        float hv[N], lv[N];
-#pragma unroll
-                        for (int c = 0; c < N / 16; ++c) {
-                            tc::tmem_ld16(trow + G::C_P1 + sg * N + 16 * c, *reinterpret_cast<float(*)[16]>(&hv[16 * c]));
-                            tc::tmem_ld16(trow + G::C_P1 + 2 * N + sg * N + 16 * c,
-                                          *reinterpret_cast<float(*)[16]>(&lv[16 * c]));
-                        }
-                        tc::tmem_wait_ld();
-                        if (sg == 1) {
-                            tc::tc_fence_before();
-                            tc::mbar_arrive(&bars.free1);
-                        }
-                        if (p1uses > 0) {   // pass 2 of the previous tile has read this sign's operands
-                            DGFS_WAITE(&bars.a2_free[sg], (ph_a2free >> sg) & 1u);
-                            ph_a2free ^= 1u << sg;
-                        }
-                        const uint32_t a2b = a2_row + sg * 2 * G::A2_BYTES;
-#pragma unroll
-                        for (int c = 0; c < N / 8; ++c) {   // 8 columns x' = 8c .. 8c + 7
-                            uint32_t uh[4], ulo[4];
-#pragma unroll
-                            for (int j = 0; j < 4; ++j)
-                                split2<BF>(fmaf(lv[8 * c + 2 * j], eps, hv[8 * c + 2 * j]),
-                                           fmaf(lv[8 * c + 2 * j + 1], eps, hv[8 * c + 2 * j + 1]), uh[j], ulo[j]);
-                            tc::st_shared_v4(a2b + c * G::A2_SBO, uh[0], uh[1], uh[2], uh[3]);
-                            tc::st_shared_v4(a2b + G::A2_BYTES + c * G::A2_SBO, ulo[0], ulo[1], ulo[2], ulo[3]);
-                        }
-                        tc::fence_proxy_async();
-                        tc::mbar_arrive(&bars.a2_full[sg]);
+                    for (int c = 0; c < N / 16; ++c) {
+                        tc::tmem_ld16(trow + G::C_P1 + w * N + 16 * c, *reinterpret_cast<float(*)[16]>(&hv[16 * c]));
+                        tc::tmem_ld16(trow + G::C_P1 + 2 * N + w * N + 16 * c, *reinterpret_cast<float(*)[16]>(&lv[16 * c]));
                     }
+                    tc::tmem_wait_ld();
+                    tc::tc_fence_before();
+                    tc::mbar_arrive(&bars.free1);
+                    if (p1uses > 0) {   // pass 2 of the previous tile has read this sign's operands
+                        DGFS_WAITE(&bars.a2_free[w], ph_a2free);
+                        ph_a2free ^= 1u;
+                    }
+#pragma unroll
+                    for (int c = 0; c < N / 8; ++c) {   // 8 columns x' = 8c .. 8c + 7
+                        uint32_t uh[4], ulo[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            split2<BF>(fmaf(lv[8 * c + 2 * j], eps, hv[8 * c + 2 * j]),
+                                       fmaf(lv[8 * c + 2 * j + 1], eps, hv[8 * c + 2 * j + 1]), uh[j], ulo[j]);
+                        tc::st_shared_v4(a2_row + c * G::A2_SBO, uh[0], uh[1], uh[2], uh[3]);
+                        tc::st_shared_v4(a2_row + G::A2_BYTES + c * G::A2_SBO, ulo[0], ulo[1], ulo[2], ulo[3]);
+                    }
+                    tc::fence_proxy_async();
+                    tc::mbar_arrive(&bars.a2_full[w]);
                     ++p1uses;
                 }
-            } else {
-                if (p > 0) {   // both CTAs' pass 3 of the previous pair has read the operands
-                    DGFS_WAITEC(&bars.a3_free, ph_a3free);
-                    ph_a3free ^= 1u;
-                }
-                for (int i = 0; i < G::TH; ++i) {   // pass-2 result of front tile i -> pass-3 operand rows
-                    const int b = i & 1, y = ((int)crank * G::TH + i) * G::ZT + yl;
+                if (st >= 1) {   // pass-2 result (sign w) of front tile i = st - 1 -> pass-3 operand rows
+                    const int i = st - 1, b = i & 1, y = ((int)crank * G::TH + i) * G::ZT + yl;
+                    if (i == 0 && p > 0) {   // both CTAs' pass 3 of the previous pair has read the operands
+                        DGFS_WAITEC(&bars.a3_free, ph_a3free);
+                        ph_a3free ^= 1u;
+                    }
                     DGFS_WAITE(&bars.full2[b], (ph_f2 >> b) & 1u);
                     ph_f2 ^= 1u << b;
                     tc::tc_fence_after();
-                    const uint32_t ts = trow + (b ? G::C_S3 : G::C_S2);
+                    const uint32_t ts = trow + (b ? G::C_S3 : G::C_S2) + w * 2 * N;
                     const uint32_t ky = (y >> 3) * G::A3_LBO + (y & 7) * 16;
 #pragma unroll
-                    for (int sg = 0; sg < 2; ++sg) {
-                        float hv[N], lv[N];
-#pragma unroll
-                        for (int c = 0; c < N / 16; ++c) {
-                            tc::tmem_ld16(ts + sg * 2 * N + 16 * c, *reinterpret_cast<float(*)[16]>(&hv[16 * c]));
-                            tc::tmem_ld16(ts + sg * 2 * N + N + 16 * c, *reinterpret_cast<float(*)[16]>(&lv[16 * c]));
-                        }
+                    for (int cc = 0; cc < N / 16; ++cc) {   // 16 columns z' behind one wait
+                        float hv[16], lv[16];
+                        tc::tmem_ld16(ts + 16 * cc, hv);
+                        tc::tmem_ld16(ts + N + 16 * cc, lv);
                         tc::tmem_wait_ld();
-                        if (sg == 1) {
+                        if (cc == N / 16 - 1) {
                             tc::tc_fence_before();
                             tc::mbar_arrive(&bars.free2[b]);
                         }
 #pragma unroll
-                        for (int c = 0; c < N / 8; ++c) {   // 8 columns z' = 8c .. 8c + 7: one row group
+                        for (int h = 0; h < 2; ++h) {   // 8 columns z' = 16 cc + 8 h ..: one row group
                             uint32_t uh[4], ulo[4];
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
-                                split2<BF>(fmaf(lv[8 * c + 2 * j], eps, hv[8 * c + 2 * j]),
-                                           fmaf(lv[8 * c + 2 * j + 1], eps, hv[8 * c + 2 * j + 1]), uh[j], ulo[j]);
-                            const uint32_t o = a3_dst + sg * 2 * G::A3_BYTES + (rg0 + c) * G::A3_SBO + ky;
+                                split2<BF>(fmaf(lv[8 * h + 2 * j], eps, hv[8 * h + 2 * j]),
+                                           fmaf(lv[8 * h + 2 * j + 1], eps, hv[8 * h + 2 * j + 1]), uh[j], ulo[j]);
+                            const uint32_t o = a3_dst + (rg0 + 2 * cc + h) * G::A3_SBO + ky;
                             tc::st_cluster_v4(o, uh[0], uh[1], uh[2], uh[3]);
                             tc::st_cluster_v4(o + G::A3_BYTES, ulo[0], ulo[1], ulo[2], ulo[3]);
                         }
                     }
                 }
-                // the rows of this pair are written: visible to the owner's tensor core (a thread writes
-                // rows of one CTA only, so it arrives on that CTA's barrier alone)
-                if (remote) tc::fence_proxy_async_cluster();
-                else tc::fence_proxy_async();
-                if (!(fault == 1 && p == 0 && blockIdx.x == 0 && blockIdx.y == 0)) {
-                    if (remote) tc::mbar_arrive_cluster(a3full_owner);
-                    else tc::mbar_arrive(&bars.a3_full);
-                }
             }
-            // back: pass-3 tiles k = w, w + 2, ... of slot 2 + w: products of the two translates
+            // this warpgroup's rows of the pair are written: visible to the owner's tensor core (a thread
+            // writes rows of one CTA only, so it arrives on that CTA's barrier alone)
+            if (remote) tc::fence_proxy_async_cluster();
+            else tc::fence_proxy_async();
+            if (!(fault == 1 && p == 0 && blockIdx.x == 0 && blockIdx.y == 0)) {
+                if (remote) tc::mbar_arrive_cluster(a3full_owner);
+                else tc::mbar_arrive(&bars.a3_full);
+            }
+            // back: pass-3 tiles k = w, w + 2, ... in slot 2 + w, products of the two translates
             const uint32_t tB = trow + (w ? G::C_S3 : G::C_S2);
 #pragma unroll
             for (int n = 0; n < NB; ++n) {
@@ -556,7 +552,7 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
                 }
             }
           }
-          // radial point r0 + rr done: P_r of this CTA's back tiles out, sums cleared
+          // radial point r0 + rr done: P_r of this warpgroup's back tiles out, sums cleared
           if (!*abort) {
               float* dst = P + ((size_t)node * Nrho + r0 + rr) * n3;
 #pragma unroll
