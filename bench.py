@@ -33,7 +33,7 @@ WORKLOAD = "vhs_n32"
 # Tolerances of the relative L2 error against the FP64 oracle, over the sampled nodes as one
 # vector, normalised by ||Q|| and by the loss term ||Q-||.
 TOL_Q = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-2, "bf16s": 5e-2, "f16x3": 1e-5, "bf16x3": 1e-3}
-TOL_L = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-3, "bf16s": 3e-3, "f16x3": 1e-5, "bf16x3": 1e-4}
+TOL_L = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-3, "bf16s": 5e-3, "f16x3": 1e-5, "bf16x3": 1e-4}
 MODES = ("fp32", "f16s", "bf16s", "f16x3", "bf16x3")
 DTYPES = {"fp32": "f32", "fp64": "f64", "f16s": "f16 data, f16 hi+lo filters, f32 accumulate",
           "bf16s": "bf16 data, bf16 hi+lo filters, f32 accumulate",
@@ -210,6 +210,7 @@ def fft_algorithmic_flops_per_node(N, Nrho, npairs):
 # from the ncu capture of a 512-node launch summarised in profiles/ (None for configurations
 # without a capture of the current kernel version).
 TRAFFIC_PER_NODE = {("f16s", 32, 32, 38): 2184.94e6 / 512, ("bf16s", 32, 32, 38): 2184.69e6 / 512,
+                    ("f16x3", 32, 32, 38): (106565888 + 2091562240) / 512,
                     ("fp32", 32, 32, 38): None}
 
 
@@ -521,6 +522,24 @@ def run_grad(a):
         e1.record()
         torch.cuda.synchronize()
         res[name] = B / (e0.elapsed_time(e1) / a.steps / 1e3)
+    # the JVP and Q(f, f) of tensor-core plans (translates on the tensor cores; the JVP by polarisation)
+    tc = {}
+    for prec in ("f16x3", "f16s"):
+        pt = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=cfg["M"], N_rho=cfg["Nrho"], precision=prec, max_batch=B)
+        tc[prec] = {}
+        for name, call in (("jvp", lambda: pt.collide_jvp(f, v, out=out)), ("collide", lambda: pt.collide(f, out=out))):
+            for _ in range(a.warmup):
+                call()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(a.steps):
+                call()
+            e1.record()
+            torch.cuda.synchronize()
+            tc[prec][name] = B / (e0.elapsed_time(e1) / a.steps / 1e3)
+        pt.stream_status()
+        pt.close()
     clocks = sampler.stop()
     plan.stream_status()
     line = {"metric": "VJP node-evals/s (dQ(f,f)/df transposed), N=32 VHS omega=0.81, M=38, FP32", "value": res["vjp"],
@@ -528,7 +547,8 @@ def run_grad(a):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "grad_n32: %d nodes, unit-norm Gaussian directions" % B, "N": N, "M": cfg["M"],
                        "N_rho": cfg["Nrho"]},
-            "jvp": res["jvp"], "vjp": res["vjp"], "dgamma": res["dgamma"], "collide": res["collide"], "clocks": clocks}
+            "jvp": res["jvp"], "vjp": res["vjp"], "dgamma": res["dgamma"], "collide": res["collide"],
+            "tensor_core_plans": tc, "clocks": clocks}
     print(json.dumps(line))
     plan.close()
     return 0

@@ -62,15 +62,23 @@ typedef enum {
     DGFS_PREC_FP32 = 1,   /* CUDA-core FP32 everywhere                                              */
     DGFS_PREC_F16S = 2,   /* translates on tcgen05 tensor cores: fp16 data operands with a per-node
                              power-of-two scale, every filter split into fp16 hi + lo parts (two
-                             products), FP32 accumulation in tensor memory; FP32 elsewhere. N = 16, 32 */
-    DGFS_PREC_BF16S = 3,  /* as F16S with bf16 operands (no scaling)                                 */
+                             products), FP32 accumulation in tensor memory; FP32 elsewhere. N = 16, 32.
+                             For every tensor-core precision, Q(f,f), Q(f,g), the JVP and dQ/dgamma
+                             take their translates on the tensor cores (the bilinear calls by
+                             polarisation: the translate-product sum is symmetric in f and g, so
+                             P(f,g) = [P(f + a g) - P(f - a g)] / 4a with a = |f|/|g| per node); the
+                             VJP runs on the FP32 CUDA-core translates. Accuracy (relative L2 of a
+                             batch against the FP64 oracle on the N = 32 two-Maxwellian workload):
+                             about 8e-4 of ||Q||, 5e-5 of the loss term ||Q-||                       */
+    DGFS_PREC_BF16S = 3,  /* as F16S with bf16 operands (no scaling): about 7e-3 of ||Q||           */
     DGFS_PREC_F16X3 = 4,  /* translates on tcgen05 tensor cores with every data operand AND every
                              filter split into an fp16 hi part and a lo part times 2^11: three
                              products per contraction (hi hi, hi lo, lo hi), FP32 accumulation, so
-                             the translates carry about FP32 accuracy; two CTAs of a thread-block
-                             cluster per node and radial block, one per translate sign. FP32
-                             elsewhere. N = 16, 32                                                   */
-    DGFS_PREC_BF16X3 = 5  /* as F16X3 with bf16 hi and lo parts (lo times 2^8): 16 significand bits */
+                             the translates carry about FP32 accuracy (8e-6 of ||Q||, 4e-7 of ||Q-||,
+                             as FP32); the two CTAs of a thread-block cluster share the field of one
+                             (node, radial points) item. FP32 elsewhere. N = 16, 32                  */
+    DGFS_PREC_BF16X3 = 5  /* as F16X3 with bf16 hi and lo parts (lo times 2^8), 16 significand
+                             bits: about 2e-5 of ||Q||, within 1e-3 of ||Q|| at every node          */
 } dgfs_precision;
 
 typedef enum {
@@ -280,8 +288,9 @@ dgfs_status dgfs_dg_create(dgfs_plan_t plan, int K, const double* H, double svd_
 /* ranks: host [K] or NULL (R_m of every m); total: host or NULL (R). */
 dgfs_status dgfs_dg_info(dgfs_dg_t dg, int* ranks, int* total);
 /* F, C: device [E][K][N^3] in the plan's element type (float; double for FP64 plans), 16-byte
-   aligned, not aliased; C[e][m] as above. Stream-ordered; no allocation. The bilinear Q runs on
-   the plan's CUDA-core path in its precision (FP32 for the 16-bit plans). */
+   aligned, not aliased; C[e][m] as above. Stream-ordered; no allocation. The collisions run as
+   dgfs_collide / dgfs_collide2 compute them in the plan's precision (on the tensor cores for the
+   tensor-core precisions). */
 dgfs_status dgfs_dg_collide(dgfs_dg_t dg, const void* F, void* C, int64_t E, void* stream);
 /* Synchronises the device and frees the workspace. NULL is a no-op. */
 dgfs_status dgfs_dg_destroy(dgfs_dg_t dg);

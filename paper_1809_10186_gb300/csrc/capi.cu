@@ -173,7 +173,9 @@ void workspace_layout(dgfs_plan_s* p, int64_t C) {
     }
     p->off_P = take(C * Nr * n3 * es);                 // P_r (also K_r u for the VJP)
     p->off_G = take(C * n3 * es);                      // VJP: the gain's radial sum
-    p->off_X = take(C * (size_t)p->xfields * n3 * 2 * es);
+    // X also holds, during the translate stage of a bilinear call of a tensor-core plan, the
+    // polarisation operands (2 fields per node) and their per-node factors
+    p->off_X = take(C * std::max<size_t>((size_t)p->xfields * n3 * 2 * es, 2 * n3 * es + 2 * sizeof(float)));
     p->off_Y = take(C * 3 * n3 * 2 * es);
     p->off_io = take(C * 2 * n3 * es);                 // host-buffer staging (f in, Q out)
     p->off_node = take(C * (sizeof(int64_t) + 2 * sizeof(double)));
@@ -486,6 +488,19 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
                                     reinterpret_cast<const float*>(gg), offs, nodes,
                                     reinterpret_cast<float*>(P), p->d_flags, s, p->fault);
         p->fault = 0;
+    } else if (is_tc(p->prec) && std::is_same<T, float>::value && offs == nullptr) {
+        // bilinear calls (Q(f, g), the JVP) on the tensor cores: the translate-product sum is symmetric in
+        // (f, g), so P(f, g) = [P(f + a g) - P(f - a g)] / (4 a), two quadratic launches; the operands u and
+        // the per-node factors live in the Fourier slots' workspace, which the Fourier stage fills only later
+        const int64_t n3 = (int64_t)t.N * t.N * t.N;
+        float* U = reinterpret_cast<float*>(X);
+        float* coef = U + 2 * nodes * n3;
+        e = launch_polar_prep(reinterpret_cast<const float*>(f), reinterpret_cast<const float*>(gg), n3, nodes, U, coef, s);
+        if (!e) e = launch_tc_gain_products(p->tc, p->prec, U, nullptr, nullptr, nodes, reinterpret_cast<float*>(P),
+                                            p->d_flags, s, 0, coef, 0);
+        if (!e) e = launch_tc_gain_products(p->tc, p->prec, U + nodes * n3, nullptr, nullptr, nodes,
+                                            reinterpret_cast<float*>(P), p->d_flags, s, 0, coef + nodes, 1);
+        if (p->prof) p->prof_launches += 2;
     } else if (p->fftx) {
         e = fft_gain_products<T>(p, f, gg, offs, nodes, P, s);
     } else {

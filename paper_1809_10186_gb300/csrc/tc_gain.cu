@@ -281,7 +281,8 @@ __device__ __forceinline__ void mma_p3_loop(Bars& bars, uint32_t sb, uint32_t tm
 template <int N, bool BF>
 __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
 k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const unsigned char* __restrict__ filt,
-          int npairs, int Nrho, int rpc, float* __restrict__ P, int* __restrict__ flags, int fault) {
+          int npairs, int Nrho, int rpc, float* __restrict__ P, int* __restrict__ flags, int fault,
+          const float* __restrict__ coef, int accum) {
     using G = Geo<N>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) Bars bars;
@@ -537,12 +538,16 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
           // radial point r0 + rr done: P_r out, sums cleared
           if (!*abort) {   // P[node][r][x'][y'][z'], row m3 = x' N + z' of tile u = 2k + w, column y'
               float* dst = P + ((size_t)node * Nrho + r0 + rr) * n3;
+              const float sc = out_scale * (coef ? coef[node] : 1.f);   // per-node factor (polarisation)
 #pragma unroll
               for (int k = 0; k < G::TW; ++k) {
                   const int m3 = (2 * k + w) * 128 + l, xp = m3 / N, zp = m3 % N;
                   float* o = dst + (size_t)xp * G::N2 + zp;
 #pragma unroll
-                  for (int j = 0; j < N; ++j) o[(size_t)j * N] = acc[k][j] * out_scale;
+                  for (int j = 0; j < N; ++j) {
+                      if (accum) o[(size_t)j * N] += acc[k][j] * sc;
+                      else o[(size_t)j * N] = acc[k][j] * sc;
+                  }
               }
           }
 #pragma unroll
@@ -580,7 +585,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
 
 template <int N, bool BF>
 cudaError_t launch_n(const TcTables& t, const float* f, const int64_t* offs, int64_t nodes, float* P,
-                     int* flags, cudaStream_t s, int fault) {
+                     int* flags, cudaStream_t s, int fault, const float* coef, int accum) {
     using G = Geo<N>;
     auto kern = k_tc_gain<N, BF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::S_TOTAL);
@@ -598,7 +603,8 @@ cudaError_t launch_n(const TcTables& t, const float* f, const int64_t* offs, int
         const int64_t nn = nodes - n0 < 65535 ? nodes - n0 : 65535;
         kern<<<dim3(t.Nrho / rpc, (unsigned)nn), G::THREADS, G::S_TOTAL, s>>>(
             f + (offs ? 0 : n0 * n3), offs ? offs + n0 : nullptr, static_cast<const unsigned char*>(t.mats),
-            t.npairs, t.Nrho, rpc, P + n0 * t.Nrho * n3, flags, n0 == 0 ? fault : 0);
+            t.npairs, t.Nrho, rpc, P + n0 * t.Nrho * n3, flags, n0 == 0 ? fault : 0, coef ? coef + n0 : nullptr,
+            accum);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -696,18 +702,79 @@ void rebase_tc_tables(TcTables& t, void* base) {
 
 cudaError_t launch_tc_gain_products(const TcTables& t, int prec, const float* f, const float* g,
                                     const int64_t* offs, int64_t nodes, float* P, int* flags,
-                                    cudaStream_t s, int fault) {
+                                    cudaStream_t s, int fault, const float* coef, int accumulate) {
     if (g) return cudaErrorNotSupported;
     if (nodes <= 0) return cudaSuccess;
-    if (tc3_precision(prec)) return launch_tc3_gain_products(t, prec, f, offs, nodes, P, flags, s, fault);
+    if (tc3_precision(prec))
+        return launch_tc3_gain_products(t, prec, f, offs, nodes, P, flags, s, fault, coef, accumulate);
     const bool bf = prec == DGFS_PREC_BF16S;
     switch (t.N) {
-        case 16: return bf ? launch_n<16, true>(t, f, offs, nodes, P, flags, s, fault)
-                           : launch_n<16, false>(t, f, offs, nodes, P, flags, s, fault);
-        case 32: return bf ? launch_n<32, true>(t, f, offs, nodes, P, flags, s, fault)
-                           : launch_n<32, false>(t, f, offs, nodes, P, flags, s, fault);
+        case 16: return bf ? launch_n<16, true>(t, f, offs, nodes, P, flags, s, fault, coef, accumulate)
+                           : launch_n<16, false>(t, f, offs, nodes, P, flags, s, fault, coef, accumulate);
+        case 32: return bf ? launch_n<32, true>(t, f, offs, nodes, P, flags, s, fault, coef, accumulate)
+                           : launch_n<32, false>(t, f, offs, nodes, P, flags, s, fault, coef, accumulate);
         default: return cudaErrorInvalidValue;
     }
+}
+
+namespace {
+
+// Operands of the polarisation of the symmetric translate-product sum, one CTA per node:
+// u[n] = f[n] + a_n g[n], u[nodes + n] = f[n] - a_n g[n] with a_n = |f_n| / |g_n| (1 when g_n = 0),
+// coef[n] = 1 / (4 a_n) and coef[nodes + n] = -1 / (4 a_n), so that
+// P(f, g) = coef[n] P(u[n]) + coef[nodes + n] P(u[nodes + n]).
+__global__ void __launch_bounds__(256) k_polar_prep(const float* __restrict__ f, const float* __restrict__ g, int64_t n3,
+                                                    int64_t nodes, float* __restrict__ u, float* __restrict__ coef) {
+    __shared__ double red[2][8];
+    __shared__ float s_a;
+    const int64_t n = blockIdx.x;
+    const float* fn = f + n * n3;
+    const float* gn = g + n * n3;
+    double sf = 0.0, sg = 0.0;
+    for (int64_t i = threadIdx.x; i < n3; i += blockDim.x) {
+        const double a = fn[i], b = gn[i];
+        sf += a * a;
+        sg += b * b;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sf += __shfl_xor_sync(0xffffffffu, sf, o);
+        sg += __shfl_xor_sync(0xffffffffu, sg, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = sf;
+        red[1][threadIdx.x >> 5] = sg;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tf = 0.0, tg = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            tf += red[0][i];
+            tg += red[1][i];
+        }
+        double a = (tg > 0.0 && tf > 0.0) ? sqrt(tf / tg) : 1.0;
+        s_a = (float)a;
+        coef[n] = (float)(0.25 / a);
+        coef[nodes + n] = (float)(-0.25 / a);
+    }
+    __syncthreads();
+    const float a = s_a;
+    float* up = u + n * n3;
+    float* um = u + (nodes + n) * n3;
+    for (int64_t i = threadIdx.x; i < n3; i += blockDim.x) {
+        const float x = fn[i], y = a * gn[i];
+        up[i] = x + y;
+        um[i] = x - y;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_polar_prep(const float* f, const float* g, int64_t n3, int64_t nodes, float* u, float* coef,
+                              cudaStream_t s) {
+    if (nodes <= 0) return cudaSuccess;
+    k_polar_prep<<<(unsigned)nodes, 256, 0, s>>>(f, g, n3, nodes, u, coef);
+    return cudaGetLastError();
 }
 
 }  // namespace dgfs

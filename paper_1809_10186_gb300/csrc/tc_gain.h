@@ -20,16 +20,24 @@ bool tc_supported(int N);
 int tc_extra_launches(int prec);   // launches the tensor-core path adds per chunk (beyond one)
 size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>& blob, TcTables& t);
 void rebase_tc_tables(TcTables& t, void* base);
-// fault: 0, or 1 = the first CTA withholds its pass-3-operands-complete signal (failure test)
+// fault: 0, or 1 = the first CTA withholds its pass-3-operands-complete signal (failure test).
+// coef (device [nodes] or nullptr): P_r of node n is written times coef[n]; accumulate: added to P
+// instead of overwriting it (the two halves of a polarisation).
 cudaError_t launch_tc_gain_products(const TcTables& t, int prec, const float* f, const float* g,
                                     const int64_t* offs, int64_t nodes, float* P, int* flags,
-                                    cudaStream_t s, int fault = 0);
+                                    cudaStream_t s, int fault = 0, const float* coef = nullptr, int accumulate = 0);
+
+// The operands of the bilinear translate-product sum by polarisation (it is symmetric in f, g):
+// u [2 nodes][n3] = f + a g, f - a g (a = |f| / |g| per node), coef [2 nodes] = +-1 / (4 a), so
+// P(f, g) = coef[n] P(u[n]) + coef[nodes + n] P(u[nodes + n]).
+cudaError_t launch_polar_prep(const float* f, const float* g, int64_t n3, int64_t nodes, float* u, float* coef,
+                              cudaStream_t s);
 
 // The split-data precisions F16X3 and BF16X3 (tc_gain3.cu); build_tc_tables and
 // launch_tc_gain_products dispatch to these for them.
 bool tc3_precision(int prec);
 size_t build_tc3_tables(const HostPlan& hp, int prec, std::vector<unsigned char>& blob, TcTables& t);
 cudaError_t launch_tc3_gain_products(const TcTables& t, int prec, const float* f, const int64_t* offs, int64_t nodes,
-                                     float* P, int* flags, cudaStream_t s, int fault);
+                                     float* P, int* flags, cudaStream_t s, int fault, const float* coef, int accumulate);
 
 }  // namespace dgfs

@@ -297,7 +297,8 @@ __device__ __forceinline__ void mma3_p3_loop(Bars3& bars, uint32_t sb, uint32_t 
 template <int N, bool BF>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo3<N>::THREADS, 1)
 k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const unsigned char* __restrict__ filt,
-           int npairs, int Nrho, int rpc, float* __restrict__ P, int* __restrict__ flags, int fault) {
+           int npairs, int Nrho, int rpc, float* __restrict__ P, int* __restrict__ flags, int fault,
+           const float* __restrict__ coef, int accum) {
     using G = Geo3<N>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) Bars3 bars;
@@ -555,6 +556,7 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
           // radial point r0 + rr done: P_r of this warpgroup's back tiles out, sums cleared
           if (!*abort) {
               float* dst = P + ((size_t)node * Nrho + r0 + rr) * n3;
+              const float sc = out_scale * (coef ? coef[node] : 1.f);   // per-node factor (polarisation)
 #pragma unroll
               for (int n = 0; n < NB; ++n) {
                   const int k = w + 2 * n;
@@ -562,7 +564,10 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
                   const int m3 = ((int)crank * G::TH + k) * 128 + l, xp = m3 / N, zp = m3 % N;
                   float* o = dst + (size_t)xp * G::N2 + zp;
 #pragma unroll
-                  for (int j = 0; j < N; ++j) o[(size_t)j * N] = acc[n][j] * out_scale;
+                  for (int j = 0; j < N; ++j) {
+                      if (accum) o[(size_t)j * N] += acc[n][j] * sc;
+                      else o[(size_t)j * N] = acc[n][j] * sc;
+                  }
               }
           }
 #pragma unroll
@@ -603,7 +608,7 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
 
 template <int N, bool BF>
 cudaError_t launch3_n(const TcTables& t, const float* f, const int64_t* offs, int64_t nodes, float* P, int* flags,
-                      cudaStream_t s, int fault) {
+                      cudaStream_t s, int fault, const float* coef, int accum) {
     using G = Geo3<N>;
     auto kern = k_tc3_gain<N, BF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::S_TOTAL);
@@ -621,7 +626,8 @@ cudaError_t launch3_n(const TcTables& t, const float* f, const int64_t* offs, in
         const int64_t nn = nodes - n0 < 65535 ? nodes - n0 : 65535;
         kern<<<dim3(2 * (t.Nrho / rpc), (unsigned)nn), G::THREADS, G::S_TOTAL, s>>>(
             f + (offs ? 0 : n0 * n3), offs ? offs + n0 : nullptr, static_cast<const unsigned char*>(t.mats),
-            t.npairs, t.Nrho, rpc, P + n0 * t.Nrho * n3, flags, n0 == 0 ? fault : 0);
+            t.npairs, t.Nrho, rpc, P + n0 * t.Nrho * n3, flags, n0 == 0 ? fault : 0, coef ? coef + n0 : nullptr,
+            accum);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -705,14 +711,14 @@ size_t build_tc3_tables(const HostPlan& hp, int prec, std::vector<unsigned char>
 }
 
 cudaError_t launch_tc3_gain_products(const TcTables& t, int prec, const float* f, const int64_t* offs, int64_t nodes,
-                                     float* P, int* flags, cudaStream_t s, int fault) {
+                                     float* P, int* flags, cudaStream_t s, int fault, const float* coef, int accumulate) {
     if (nodes <= 0) return cudaSuccess;
     const bool bf = prec == DGFS_PREC_BF16X3;
     switch (t.N) {
-        case 16: return bf ? launch3_n<16, true>(t, f, offs, nodes, P, flags, s, fault)
-                           : launch3_n<16, false>(t, f, offs, nodes, P, flags, s, fault);
-        case 32: return bf ? launch3_n<32, true>(t, f, offs, nodes, P, flags, s, fault)
-                           : launch3_n<32, false>(t, f, offs, nodes, P, flags, s, fault);
+        case 16: return bf ? launch3_n<16, true>(t, f, offs, nodes, P, flags, s, fault, coef, accumulate)
+                           : launch3_n<16, false>(t, f, offs, nodes, P, flags, s, fault, coef, accumulate);
+        case 32: return bf ? launch3_n<32, true>(t, f, offs, nodes, P, flags, s, fault, coef, accumulate)
+                           : launch3_n<32, false>(t, f, offs, nodes, P, flags, s, fault, coef, accumulate);
         default: return cudaErrorInvalidValue;
     }
 }
