@@ -11,7 +11,8 @@ largest per-node values of both are printed. Per node, ||Q||-normalised FP32 err
 Tolerances (batch, by ||Q|| and by ||Q-||): FP64 1e-10; FP32 1e-5. The modes with 16-bit data
 operands round the three stored intermediates of every translate to 11 (fp16) or 8 (bf16)
 significand bits: F16S reaches 7e-4 by ||Q|| on the N = 32 workload but 4e-3 on coarse N = 16
-grids, BF16S 7e-3 and 3e-2; their tolerances are 1e-2 / 5e-2 by ||Q|| and 1e-3 / 3e-3 by ||Q-||,
+grids, BF16S 7e-3 and 3e-2; their tolerances are 1e-2 / 5e-2 by ||Q|| and 1e-3 / 5e-3 by ||Q-||
+(the bilinear calls, polarised into two quadratic evaluations, double the bf16 rounding),
 and neither meets the 1e-3 of the BF16-split tolerance everywhere: the split-data modes do.
 F16X3 (fp16 hi + lo on data and filters, three products, FP32 accumulation) is held to the FP32
 tolerance 1e-5, BF16X3 to 1e-3 by ||Q|| and 1e-4 by ||Q-||.
