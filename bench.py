@@ -716,6 +716,8 @@ def main():
     plan = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=M, N_rho=Nr, svd_tol=cfg["svd_tol"], precision=prec,
                         max_batch=a.chunk if a.chunk > 0 else B)
     npairs = plan.info["n_pairs"]
+    # the autotuner picks radial points per CTA and nodes per chunk on this batch (outside the timed region)
+    tuning = {prec: plan.autotune(f)}
 
     def barrier():
         torch.cuda.synchronize()
@@ -795,7 +797,8 @@ def main():
                                                         "larger than" if f.numel() * 4 > 129 << 20 else "within",
                                                         plan.info["chunk_nodes"] * Nr * N ** 3 * 4 >> 20),
                        "parallelism": "dp%d" % world},
-            "gpu_launches": prof["launches"], "clocks": clocks, "roofline": roof, "peaks_measured": measured}
+            "gpu_launches": prof["launches"], "clocks": clocks, "roofline": roof, "peaks_measured": measured,
+            "tuning": tuning}
 
     # end to end through the host-buffer entry point (pinned host memory, copies inside)
     if not a.no_e2e:
@@ -820,7 +823,9 @@ def main():
         for other in MODES:
             if other == prec:
                 continue
-            po = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=M, N_rho=Nr, svd_tol=cfg["svd_tol"], precision=other)
+            po = binding.Plan(N=N, L=L, gamma=cfg["gamma"], M=M, N_rho=Nr, svd_tol=cfg["svd_tol"], precision=other,
+                              max_batch=a.chunk if a.chunk > 0 else B)
+            tuning[other] = po.autotune(f)
             ko = max(1, a.steps // 2)
             mso, profo, _ = timed(po, ko, 1)
             outputs[other] = q.clone()

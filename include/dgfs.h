@@ -322,6 +322,29 @@ typedef struct {
 dgfs_status dgfs_profile_begin(dgfs_plan_t plan);
 dgfs_status dgfs_profile_end(dgfs_plan_t plan, dgfs_profile_t* out);
 
+/* Autotuner (the paper has no counterpart): times dgfs_collide on the caller's batch f (device,
+   [B][N^3], the plan's element type; the first min(B, chunk) nodes are used) for every candidate
+   configuration - radial points per CTA of the tensor-core translate kernels (1, 2, 4, 8 where
+   they divide N_rho, or the batch-size rule) times nodes per internal chunk (the plan's chunk and
+   its halves) - with CUDA events on `stream`, keeps the fastest in the plan for its later compute
+   calls and caches it in the process by (N, sphere pairs, N_rho, SVD rank, precision, batch size
+   rounded down to a power of two): a later call for the same shape applies the cached choice
+   without timing (report->cached = 1). Results do not depend on the choice (each radial point's
+   arithmetic is the same in every configuration). Synchronous; not for use inside a stream
+   capture. The output goes to the plan's own staging buffer. VSS plans: DGFS_ERR_UNSUPPORTED. */
+typedef struct {
+    int rpc;                        /* radial points per CTA chosen (0 for plans without tensor cores) */
+    int64_t chunk_nodes;            /* nodes per chunk chosen                                          */
+    double ms_per_node_default;     /* time per node with the batch-size rule and the plan's chunk     */
+    double ms_per_node_tuned;       /* time per node with the choice                                   */
+    int candidates;                 /* configurations timed (0 when the choice came from the cache)    */
+    int cached;
+} dgfs_tune_report;
+dgfs_status dgfs_plan_autotune(dgfs_plan_t plan, const void* f, int64_t B, void* stream, dgfs_tune_report* report);
+/* Sets the configuration by hand: rpc dividing N_rho (0: the batch-size rule), chunk_nodes >= 0
+   (0: the plan's chunk). */
+dgfs_status dgfs_plan_set_tuning(dgfs_plan_t plan, int rpc, int64_t chunk_nodes);
+
 /* Device-rate probe for rooflines (the paper has no counterpart): the FP32 and FP64 fused
    multiply-add throughput of the CUDA cores of the current device, in TFLOP/s (2 flops per FMA),
    the best of three timed launches of independent FMA chains on every SM. Synchronous; allocates

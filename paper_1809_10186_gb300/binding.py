@@ -39,6 +39,11 @@ class dgfs_plan_info_t(ctypes.Structure):
                 ("table_bytes", ctypes.c_size_t), ("alpha", ctypes.c_double)]
 
 
+class dgfs_tune_report(ctypes.Structure):
+    _fields_ = [("rpc", ctypes.c_int), ("chunk_nodes", ctypes.c_int64), ("ms_per_node_default", ctypes.c_double),
+                ("ms_per_node_tuned", ctypes.c_double), ("candidates", ctypes.c_int), ("cached", ctypes.c_int)]
+
+
 class dgfs_profile_t(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("gain_launches", ctypes.c_int64),
                 ("gain_timed", ctypes.c_int64), ("gain_ms", ctypes.c_double), ("nodes", ctypes.c_int64)]
@@ -69,6 +74,8 @@ _SIGNATURES = {
     "dgfs_stream_status": [_P, _P],
     "dgfs_debug_inject": [_P, ctypes.c_int],
     "dgfs_device_fma_peaks": [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "dgfs_plan_autotune": [_P, _P, _I64, _P, ctypes.POINTER(dgfs_tune_report)],
+    "dgfs_plan_set_tuning": [_P, ctypes.c_int, _I64],
     "dgfs_profile_begin": [_P],
     "dgfs_profile_end": [_P, ctypes.POINTER(dgfs_profile_t)],
     "dgfs_last_error_message": [],
@@ -292,6 +299,18 @@ class Plan:
                                       ctypes.c_void_p(q_host.data_ptr()), ctypes.c_int64(B),
                                       _stream_ptr(stream)), "dgfs_collide_host")
         return q_host
+
+    def autotune(self, f, stream=None):
+        """Times the candidate configurations on f and keeps the fastest (dgfs_plan_autotune); returns
+        the report as a dict."""
+        self._check_field(f, "f")
+        rep = dgfs_tune_report()
+        check(lib().dgfs_plan_autotune(self.handle, ctypes.c_void_p(f.data_ptr()), ctypes.c_int64(f.shape[0]),
+                                       _stream_ptr(stream), ctypes.byref(rep)), "dgfs_plan_autotune")
+        return {k: getattr(rep, k) for k, _ in dgfs_tune_report._fields_}
+
+    def set_tuning(self, rpc=0, chunk_nodes=0):
+        check(lib().dgfs_plan_set_tuning(self.handle, int(rpc), ctypes.c_int64(chunk_nodes)), "dgfs_plan_set_tuning")
 
     def profile_begin(self):
         check(lib().dgfs_profile_begin(self.handle), "dgfs_profile_begin")

@@ -17,10 +17,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
@@ -90,6 +92,7 @@ struct dgfs_plan_s {
     int prec = DGFS_PREC_FP32;
     int device = 0;
     int64_t chunk = 1;
+    int64_t run_chunk = 0;   // nodes per chunk of the compute calls (autotuned); 0: chunk
     size_t ws_bytes = 0, table_bytes = 0;
     void* d_tables = nullptr;
     void* d_ws = nullptr;
@@ -549,8 +552,9 @@ dgfs_status run(dgfs_plan_s* p, Op op, const void* f, const void* g, void* out, 
     const int64_t n3 = (int64_t)p->hp.N * p->hp.N * p->hp.N;
     DGFS_ON_DEVICE(p->device);
     NodeParams np{nullptr, nullptr, p->hp.gamma, p->hp.b, op == Op::Dgamma ? 1 : 0};
-    for (int64_t n0 = 0; n0 < B; n0 += p->chunk) {
-        const int64_t nn = std::min<int64_t>(p->chunk, B - n0);
+    const int64_t C = p->run_chunk > 0 ? std::min<int64_t>(p->run_chunk, p->chunk) : p->chunk;
+    for (int64_t n0 = 0; n0 < B; n0 += C) {
+        const int64_t nn = std::min<int64_t>(C, B - n0);
         const T* fc = static_cast<const T*>(f) + n0 * n3;
         const T* gc = g ? static_cast<const T*>(g) + n0 * n3 : nullptr;
         T* oc = static_cast<T*>(out) + n0 * n3;
@@ -1574,6 +1578,145 @@ dgfs_status dgfs_profile_end(dgfs_plan_t plan, dgfs_profile_t* out) {
     out->gain_ms = ms;
     out->nodes = plan->prof_nodes;
     plan->prof = false;
+    return DGFS_OK;
+}
+
+// ---- autotuner: radial points per CTA of the tensor-core kernels and nodes per chunk ----------
+
+namespace {
+
+struct TuneKey {
+    int N, npairs, Nrho, rank, prec, bucket;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(N, npairs, Nrho, rank, prec, bucket) < std::tie(o.N, o.npairs, o.Nrho, o.rank, o.prec, o.bucket);
+    }
+};
+struct TuneVal {
+    int rpc;
+    int64_t chunk;
+    double ms_default, ms_tuned;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+
+int floor_log2(int64_t v) {
+    int b = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++b;
+    }
+    return b;
+}
+
+}  // namespace
+
+dgfs_status dgfs_plan_autotune(dgfs_plan_t plan, const void* f, int64_t B, void* stream, dgfs_tune_report* report) {
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    if (B < 1 || !f || !report) return fail(DGFS_ERR_INVALID_ARG, "autotune needs B >= 1, f and a report");
+    if (!aligned16(f)) return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
+    if (plan->hp.aniso) return fail(DGFS_ERR_UNSUPPORTED, "autotune of a VSS plan (alpha != 1)");
+    dgfs_plan_s* p = plan;
+    const int64_t nodes = std::min<int64_t>(B, p->chunk);
+    const TuneKey key{p->hp.N, p->hp.npairs, p->hp.Nrho, p->hp.rank, p->prec, floor_log2(nodes)};
+    std::memset(report, 0, sizeof *report);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {   // the same shape was tuned before in this process
+            p->tc.rpc = it->second.rpc;
+            p->run_chunk = it->second.chunk;
+            report->rpc = it->second.rpc;
+            report->chunk_nodes = it->second.chunk;
+            report->ms_per_node_default = it->second.ms_default;
+            report->ms_per_node_tuned = it->second.ms_tuned;
+            report->cached = 1;
+            return DGFS_OK;
+        }
+    }
+    DGFS_ON_DEVICE(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int sms = 0;
+    DGFS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device), "cudaDeviceGetAttribute");
+    const size_t n3 = (size_t)p->hp.N * p->hp.N * p->hp.N, es = elem_size(p->prec);
+    void* Q = ws(p, p->off_io) + (size_t)p->chunk * n3 * es;   // the output half of the host staging area
+    // candidates: radial points per CTA (tensor-core plans; 0 = the batch-size rule) x nodes per chunk
+    std::vector<int> rpcs{0};
+    if (is_tc(p->prec))
+        for (int c : {1, 2, 4, 8})
+            if (p->hp.Nrho % c == 0) rpcs.push_back(c);
+    std::vector<int64_t> chunks{nodes};
+    for (int64_t c = nodes / 2; c >= 1 && chunks.size() < 3; c /= 2) chunks.push_back(c);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DGFS_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+    cudaError_t e = cudaEventCreate(&e1);
+    const int saved_rpc = p->tc.rpc;
+    const int64_t saved_chunk = p->run_chunk;
+    double best = -1.0, ms_default = -1.0;
+    int best_rpc = 0, count = 0;
+    int64_t best_chunk = nodes;
+    for (int64_t ch : chunks)
+        for (int rp : rpcs) {
+            if (e != cudaSuccess) break;
+            p->tc.rpc = rp;
+            p->run_chunk = ch;
+            dgfs_status st = DGFS_OK;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && st == DGFS_OK; ++rep) {   // rep 0 warms up
+                if (rep == 1) e = cudaEventRecord(e0, s);
+                for (int k = 0; k < (rep ? 3 : 1) && st == DGFS_OK; ++k)
+                    st = p->prec == DGFS_PREC_FP64 ? run<double>(p, Op::Collide, f, nullptr, Q, nodes, s)
+                                                   : run<float>(p, Op::Collide, f, nullptr, Q, nodes, s);
+            }
+            if (st != DGFS_OK) {
+                p->tc.rpc = saved_rpc;
+                p->run_chunk = saved_chunk;
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return st;
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) break;
+            const double per = ms / 3.0 / (double)nodes;
+            ++count;
+            if (ch == nodes && rp == 0) ms_default = per;
+            if (best < 0 || per < best) {
+                best = per;
+                best_rpc = rp;
+                best_chunk = ch;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        p->tc.rpc = saved_rpc;
+        p->run_chunk = saved_chunk;
+        return cuda_fail(e, "autotune timing");
+    }
+    // record the resolved value of the batch-size rule, so that a cached choice means the same
+    if (best_rpc == 0 && is_tc(p->prec)) best_rpc = tc_resolve_rpc(p->tc, p->prec, best_chunk, sms);
+    p->tc.rpc = best_rpc;
+    p->run_chunk = best_chunk;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[key] = TuneVal{best_rpc, best_chunk, ms_default, best};
+    }
+    report->rpc = best_rpc;
+    report->chunk_nodes = best_chunk;
+    report->ms_per_node_default = ms_default;
+    report->ms_per_node_tuned = best;
+    report->candidates = count;
+    report->cached = 0;
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_plan_set_tuning(dgfs_plan_t plan, int rpc, int64_t chunk_nodes) {
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    if (rpc < 0 || (rpc > 0 && plan->hp.Nrho % rpc) || chunk_nodes < 0)
+        return fail(DGFS_ERR_INVALID_ARG, "rpc must divide N_rho (0: the batch-size rule); chunk_nodes >= 0");
+    plan->tc.rpc = rpc;
+    plan->run_chunk = chunk_nodes;
     return DGFS_OK;
 }
 

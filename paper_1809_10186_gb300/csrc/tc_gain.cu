@@ -591,14 +591,11 @@ cudaError_t launch_n(const TcTables& t, const float* f, const int64_t* offs, int
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::S_TOTAL);
     if (e != cudaSuccess) return e;
     const int64_t n3 = (int64_t)N * N * N;
-    // several radial points per CTA share its set-up: the most of 4, 2, 1 that divides N_rho while
-    // the grid still fills the GPU at least 16 times over (one CTA per SM); small batches keep one
+    // several radial points per CTA share its set-up (tc_resolve_rpc)
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    int rpc = 1;
-    for (int c = 4; c > 1 && rpc == 1; c /= 2)
-        if (t.Nrho % c == 0 && (int64_t)(t.Nrho / c) * nodes >= 16 * (int64_t)sms) rpc = c;
+    const int rpc = tc_resolve_rpc(t, BF ? DGFS_PREC_BF16S : DGFS_PREC_F16S, nodes, sms);
     for (int64_t n0 = 0; n0 < nodes; n0 += 65535) {
         const int64_t nn = nodes - n0 < 65535 ? nodes - n0 : 65535;
         kern<<<dim3(t.Nrho / rpc, (unsigned)nn), G::THREADS, G::S_TOTAL, s>>>(
@@ -638,6 +635,16 @@ double bf16_bits_value(uint16_t b) {
 }  // namespace
 
 bool tc_supported(int N) { return N == 16 || N == 32; }
+
+int tc_resolve_rpc(const TcTables& t, int prec, int64_t nodes, int sms) {
+    if (t.rpc > 0 && t.Nrho % t.rpc == 0) return t.rpc;
+    // CTAs per radial block: two (a cluster) for the split-data kernels
+    const int64_t per = tc3_precision(prec) ? 2 : 1;
+    int rpc = 1;
+    for (int c = 4; c > 1 && rpc == 1; c /= 2)
+        if (t.Nrho % c == 0 && per * (int64_t)(t.Nrho / c) * nodes >= 16 * (int64_t)sms) rpc = c;
+    return rpc;
+}
 
 int tc_extra_launches(int) { return 0; }
 

@@ -14,7 +14,13 @@ struct TcTables {
     int N = 0, Nrho = 0, npairs = 0;
     const void* mats = nullptr;     // per (r, pair, axis, sign) N x N operand tiles
     const float* wsig = nullptr;
+    int rpc = 0;                    // radial points per CTA (item): 0 = chosen from the batch (tc_resolve_rpc)
 };
+
+// Radial points per CTA (per CTA pair for the split-data kernels) of a launch over `nodes` nodes:
+// t.rpc when it divides N_rho, else the most of 4, 2, 1 that divides N_rho while the grid still fills
+// the GPU's `sms` SMs at least 16 times over.
+int tc_resolve_rpc(const TcTables& t, int prec, int64_t nodes, int sms);
 
 bool tc_supported(int N);
 int tc_extra_launches(int prec);   // launches the tensor-core path adds per chunk (beyond one)

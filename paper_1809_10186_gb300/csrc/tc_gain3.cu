@@ -617,11 +617,8 @@ cudaError_t launch3_n(const TcTables& t, const float* f, const int64_t* offs, in
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    // radial points per CTA pair: the most of 4, 2, 1 that divides N_rho while the grid (two CTAs
-    // per radial block) still fills the GPU at least 16 times over
-    int rpc = 1;
-    for (int c = 4; c > 1 && rpc == 1; c /= 2)
-        if (t.Nrho % c == 0 && (int64_t)(2 * t.Nrho / c) * nodes >= 16 * (int64_t)sms) rpc = c;
+    // radial points per CTA pair (tc_resolve_rpc: two CTAs per radial block)
+    const int rpc = tc_resolve_rpc(t, BF ? DGFS_PREC_BF16X3 : DGFS_PREC_F16X3, nodes, sms);
     for (int64_t n0 = 0; n0 < nodes; n0 += 65535) {
         const int64_t nn = nodes - n0 < 65535 ? nodes - n0 : 65535;
         kern<<<dim3(2 * (t.Nrho / rpc), (unsigned)nn), G::THREADS, G::S_TOTAL, s>>>(
