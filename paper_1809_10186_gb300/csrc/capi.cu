@@ -480,7 +480,7 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
     // gain products: Q(f,f) and dQ/dgamma use (f, f); Q(f,g) uses (f, g); JVP uses (f, v)
     const T* gg = (op == Op::Collide || op == Op::Dgamma) ? nullptr : g;
     if (p->prof) {
-        p->prof_launches += (spectral_supported(tables<T>(p)) ? 4 : 11 + (op == Op::Jvp ? 1 : 0)) +
+        p->prof_launches += (spectral_supported(tables<T>(p)) ? 5 : 11 + (op == Op::Jvp ? 1 : 0)) +
                             tc_extra_launches(p->prec);
         p->prof_gain += 1;
         p->prof_nodes += nodes;
