@@ -324,7 +324,8 @@ dgfs_status dgfs_profile_end(dgfs_plan_t plan, dgfs_profile_t* out);
 
 /* Autotuner (the paper has no counterpart): times dgfs_collide on the caller's batch f (device,
    [B][N^3], the plan's element type; the first min(B, chunk) nodes are used) for every candidate
-   configuration - radial points per CTA of the tensor-core translate kernels (1, 2, 4, 8 where
+   configuration - radial points per work item of the persistent tensor-core translate kernel (per
+   CTA pair of the split-data kernels; 1, 2, 4, 8 where
    they divide N_rho, or the batch-size rule) times nodes per internal chunk (the plan's chunk and
    its halves) - with CUDA events on `stream`, keeps the fastest in the plan for its later compute
    calls and caches it in the process by (N, sphere pairs, N_rho, SVD rank, precision, batch size
@@ -333,7 +334,7 @@ dgfs_status dgfs_profile_end(dgfs_plan_t plan, dgfs_profile_t* out);
    arithmetic is the same in every configuration). Synchronous; not for use inside a stream
    capture. The output goes to the plan's own staging buffer. VSS plans: DGFS_ERR_UNSUPPORTED. */
 typedef struct {
-    int rpc;                        /* radial points per CTA chosen (0 for plans without tensor cores) */
+    int rpc;                        /* radial points per item chosen (0 for plans without tensor cores) */
     int64_t chunk_nodes;            /* nodes per chunk chosen                                          */
     double ms_per_node_default;     /* time per node with the batch-size rule and the plan's chunk     */
     double ms_per_node_tuned;       /* time per node with the choice                                   */

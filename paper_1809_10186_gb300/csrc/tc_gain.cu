@@ -17,10 +17,14 @@
 // shared-memory A operand once, and the epilogue combines hi + 2^-e lo in FP32. The + sign's x
 // filter carries the factor 2 w_p, so the products need no further weighting.
 //
-// One CTA per (node, rpc consecutive radial points): two epilogue warpgroups and a third warpgroup of four MMA
-// warps (after set-up the third warpgroup gives registers back and the epilogue warpgroups take
-// them, 216 per thread, so that an epilogue step loads a whole tile row from TMEM behind one
-// wait). The front of a sphere pair (passes 1 and 2 of every tile) is a producer/consumer chain:
+// Persistent: one CTA per SM pulls work items (a node and rpc consecutive radial points) from a
+// queue counter in global memory until none are left; the pass-1 MMA warp claims them and hands
+// each one to the other warps through a ring in shared memory. Per item the epilogue warps scale f
+// and load it into TMEM (once the previous item's pass-1 MMAs are complete); the (radial point,
+// pair) steps of consecutive items form one pipelined sequence. Each CTA holds two epilogue
+// warpgroups and a third warpgroup of four MMA warps (after set-up the third warpgroup gives
+// registers back and the epilogue warpgroups take them, 216 per thread, so that an epilogue step
+// loads a whole tile row from TMEM behind one wait). The front of a sphere pair (passes 1 and 2 of every tile) is a producer/consumer chain:
 // the pass-1 MMA warp fills two pass-1 TMEM slots, epilogue warpgroup 0 turns each pass-1 result
 // into pass-2 operands in two shared-memory buffers, the pass-2 MMA warp fills two pass-2/3 TMEM
 // slots, and epilogue warpgroup 1 writes each pass-2 result into the pass-3 operands (both signs'
@@ -110,6 +114,20 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {   // a -> low half
     }
 }
 
+// Work items of the persistent kernel: item i = (node i / rblocks, radial points
+// r0 .. r0 + rpc - 1 with r0 = (i % rblocks) rpc), pulled from a queue counter in global memory.
+// The pass-1 MMA warp claims them and publishes each one in a ring in shared memory, which every
+// other warp reads in the same order.
+constexpr int kRing = 4;
+constexpr uint32_t kRingConsumers = 8 + 3;   // the eight epilogue warps, the pass-2 and pass-3 MMA warps
+
+struct Items {
+    int64_t n_items;   // nodes * rblocks
+    int rblocks;       // radial blocks per node (N_rho / rpc)
+    int rpc;           // radial points per item
+    int nseq;          // (radial point, pair) steps per item: rpc * npairs
+};
+
 struct Bars {
     // TMEM slot rings (index = tile % 2): MMA completion -> epilogue, epilogue drained -> MMA
     uint64_t full1[2], free1[2];       // pass-1 slots (pass-1 epilogue, warpgroup 0)
@@ -118,7 +136,10 @@ struct Bars {
     uint64_t free3x[2];                // last pass-3 drain of a slot in a pair (next pair's pass 2 may start)
     uint64_t a2_full[2], a2_free[2];   // pass-2 operand ring: epilogue -> MMA, MMA completion -> epilogue
     uint64_t a3_full, a3_free;         // pass-3 operands (both signs)
-    uint64_t filt[2], fdone[2];        // filter buffers: copy landed; all MMAs of the pair using it done
+    uint64_t filt[2], fdone[2];        // filter buffers: copy landed; all MMAs of the step using it done
+    uint64_t item_full[kRing], item_free[kRing];   // work-item ring: published; read by every consumer warp
+    uint64_t f_ready, f_free;          // f of the current item in TMEM; pass-1 MMAs of an item complete
+    uint64_t scan[2];                  // max |f| partial maxima of an item written (item % 2)
     uint64_t drain;
 };
 
@@ -128,185 +149,244 @@ __device__ __forceinline__ void pack8(const float (&v)[8], uint32_t (&u)[4]) {
     for (int j = 0; j < 4; ++j) u[j] = pack2<BF>(v[2 * j], v[2 * j + 1]);
 }
 
-// The MMA warps (four, converged). Pass 1 of every tile (mma_p1_loop; it also refills the filter
-// buffers), pass 2 of every tile (mma_p2_loop) and pass 3 of the tiles of warpgroup b
-// (mma_p3_loop<b>) are issued by separate warps, so a group is issued as soon as its own inputs
-// and slot are ready. Each commit tracks only the issuing warp's MMAs. Every barrier below is
-// waited by one warp, phase after phase, except a3_full (one completion per pair, waited by both
-// pass-3 warps). Each loop returns early when a wait gave up (abort).
+// The MMA warps (four, converged). Pass 1 of every tile (mma_p1_loop; it also claims the work items
+// and refills the filter buffers), pass 2 of every tile (mma_p2_loop) and pass 3 of the tiles of
+// warpgroup b (mma_p3_loop<b>) are issued by separate warps, so a group is issued as soon as its own
+// inputs and slot are ready. Each commit tracks only the issuing warp's MMAs. The (radial point,
+// pair) steps of consecutive items form one sequence; g counts them, and every phase below follows
+// g, not the item. Each loop returns early when a wait gave up (abort).
 #define DGFS_WAITW(bar, ph)                                             \
     do {                                                                \
         if (!tc::warp_wait((bar), (ph), abort)) return;                 \
     } while (0)
 
+// Item k of this CTA from the ring (every consumer warp, in order); -1 ends the sequence.
+__device__ __forceinline__ bool ring_take(Bars& bars, const volatile long long* s_item, int k, long long& item,
+                                          volatile int* abort) {
+    if (!tc::warp_wait(&bars.item_full[k % kRing], (uint32_t)((k / kRing) & 1), abort)) return false;
+    item = s_item[k % kRing];
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) tc::mbar_arrive(&bars.item_free[k % kRing]);
+    return true;
+}
+
+// The pass-1 warp claims this CTA's item k and publishes it (slot k % kRing, once its previous
+// item has been read by every consumer).
+__device__ __forceinline__ bool ring_claim(Bars& bars, volatile long long* s_item, int* queue, const Items& it, int k,
+                                           long long& item, volatile int* abort) {
+    if (k >= kRing && !tc::warp_wait(&bars.item_free[k % kRing], (uint32_t)((k / kRing - 1) & 1), abort)) return false;
+    long long v = -1;
+    if ((threadIdx.x & 31) == 0) {
+        const long long c = atomicAdd(queue, 1);
+        v = c < it.n_items ? c : -1;
+        s_item[k % kRing] = v;
+        tc::mbar_arrive(&bars.item_full[k % kRing]);
+    }
+    item = __shfl_sync(0xffffffffu, v, 0);
+    return true;
+}
+
+template <int N>
+__device__ __forceinline__ const unsigned char* item_filters(const unsigned char* filt, long long item, const Items& it,
+                                                             int npairs) {
+    return filt + (size_t)((item % it.rblocks) * it.rpc) * npairs * Geo<N>::F_BLOCK;
+}
+
 template <int N, bool BF>
 __device__ __forceinline__ void mma_p1_loop(Bars& bars, unsigned char* smem, uint32_t sb, uint32_t tmem,
-                                            const unsigned char* fglob, int npairs, volatile int* abort,
+                                            const unsigned char* filt, int npairs, const Items& it, long long first,
+                                            volatile long long* s_item, int* queue, volatile int* abort,
                                             int& copies0, int& copies1, int& waited0, int& waited1) {
     using G = Geo<N>;
     uint32_t used = 0, ph_free = 0, ph_fdone = 0;   // bit masks (bit i = slot or buffer i)
     constexpr uint32_t id1 = tc::idesc_f16(BF, false, false, 2 * N, 128);
     constexpr uint64_t dF = tc::sdesc_base(G::FB_LBO, G::FB_SBO);
     const uint32_t sb16 = sb >> 4;
-    for (int p = 0; p < npairs; ++p) {
-        const int fbuf = p & 1;
-        DGFS_WAITW(&bars.filt[fbuf], (uint32_t)((p >> 1) & 1));
-        if (fbuf) ++waited1;
-        else ++waited0;
-        tc::tc_fence_after();
-        const uint32_t f16 = sb16 + (G::S_F + fbuf * G::F_BLOCK) / 16;   // filter block of this pair
-        for (int t = 0; t < G::T; ++t) {   // pass 1 of tile t into pass-1 slot t % 2
-            const int b = t & 1;
-            if (used & (1u << b)) {
-                DGFS_WAITW(&bars.free1[b], (ph_free >> b) & 1u);
-                ph_free ^= 1u << b;
-            }
-            used |= 1u << b;
+    long long cur = first;
+    int64_t g = 0;
+    for (int k = 0; cur >= 0; ++k) {
+        // the next item is claimed now: its first filter block is copied during this item's last step
+        long long nxt = -1;
+        if (!ring_claim(bars, s_item, queue, it, k + 1, nxt, abort)) return;
+        const unsigned char* fcur = item_filters<N>(filt, cur, it, npairs);
+        const unsigned char* fnxt = nxt >= 0 ? item_filters<N>(filt, nxt, it, npairs) : nullptr;
+        DGFS_WAITW(&bars.f_ready, (uint32_t)(k & 1));   // f of this item is in TMEM
+        for (int s = 0; s < it.nseq; ++s, ++g) {
+            const int fbuf = (int)(g & 1);
+            DGFS_WAITW(&bars.filt[fbuf], (uint32_t)((g >> 1) & 1));
+            if (fbuf) ++waited1;
+            else ++waited0;
             tc::tc_fence_after();
-            const uint32_t d = tmem + b * G::C_S1;
-            const uint32_t fa = tmem + G::C_F + t * (N / 2);
-#pragma unroll
-            for (int ks = 0; ks < G::KSTEPS; ++ks) {   // hi rows [0, 2n), lo rows [2n, 4n) of B1
-                tc::mma_ts_warp(d, fa + 8 * ks, tc::sdesc_at(dF, f16 + (G::OFF_B1 + ks * 2 * G::FB_LBO) / 16), id1, ks);
-                tc::mma_ts_warp(d, fa + 8 * ks,
-                                tc::sdesc_at(dF, f16 + (G::OFF_B1 + (2 * N / 8) * G::FB_SBO + ks * 2 * G::FB_LBO) / 16),
-                                id1, 1);
-            }
-            tc::mma_commit_warp(&bars.full1[b]);
-            // the other filter buffer (pair p - 1, whose MMAs are complete by now) takes pair p + 1
-            if (t == 0 && p >= 1 && p + 1 < npairs) {
-                const int nb = (p + 1) & 1;
-                DGFS_WAITW(&bars.fdone[nb], (ph_fdone >> nb) & 1u);
-                ph_fdone ^= 1u << nb;
-                if (tc::elect_one()) {
-                    tc::mbar_expect_tx(&bars.filt[nb], G::F_BLOCK);
-                    tc::bulk_g2s(smem + G::S_F + nb * G::F_BLOCK, fglob + (size_t)(p + 1) * G::F_BLOCK, G::F_BLOCK,
-                                 &bars.filt[nb]);
+            const uint32_t f16 = sb16 + (G::S_F + fbuf * G::F_BLOCK) / 16;   // filter block of this step
+            for (int t = 0; t < G::T; ++t) {   // pass 1 of tile t into pass-1 slot t % 2
+                const int b = t & 1;
+                if (used & (1u << b)) {
+                    DGFS_WAITW(&bars.free1[b], (ph_free >> b) & 1u);
+                    ph_free ^= 1u << b;
                 }
-                __syncwarp();
-                if (nb) ++copies1;
-                else ++copies0;
+                used |= 1u << b;
+                tc::tc_fence_after();
+                const uint32_t d = tmem + b * G::C_S1;
+                const uint32_t fa = tmem + G::C_F + t * (N / 2);
+#pragma unroll
+                for (int ks = 0; ks < G::KSTEPS; ++ks) {   // hi rows [0, 2n), lo rows [2n, 4n) of B1
+                    tc::mma_ts_warp(d, fa + 8 * ks, tc::sdesc_at(dF, f16 + (G::OFF_B1 + ks * 2 * G::FB_LBO) / 16), id1, ks);
+                    tc::mma_ts_warp(d, fa + 8 * ks,
+                                    tc::sdesc_at(dF, f16 + (G::OFF_B1 + (2 * N / 8) * G::FB_SBO + ks * 2 * G::FB_LBO) / 16),
+                                    id1, 1);
+                }
+                tc::mma_commit_warp(&bars.full1[b]);
+                // the other filter buffer (step g - 1, whose MMAs are complete by now) takes step g + 1;
+                // the set-up copied steps 0 and 1, unless step 1 belongs to the next item (one-step items)
+                const unsigned char* src = s + 1 < it.nseq ? fcur + (size_t)(s + 1) * G::F_BLOCK : fnxt;
+                if (t == 0 && (g >= 1 || it.nseq == 1) && src) {
+                    const int nb = (int)((g + 1) & 1);
+                    if (g >= 1) {   // buffer nb held step g - 1
+                        DGFS_WAITW(&bars.fdone[nb], (ph_fdone >> nb) & 1u);
+                        ph_fdone ^= 1u << nb;
+                    }
+                    if (tc::elect_one()) {
+                        tc::mbar_expect_tx(&bars.filt[nb], G::F_BLOCK);
+                        tc::bulk_g2s(smem + G::S_F + nb * G::F_BLOCK, src, G::F_BLOCK, &bars.filt[nb]);
+                    }
+                    __syncwarp();
+                    if (nb) ++copies1;
+                    else ++copies0;
+                }
             }
+            tc::mma_commit_warp(&bars.fdone[fbuf]);
         }
-        tc::mma_commit_warp(&bars.fdone[fbuf]);
+        tc::mma_commit_warp(&bars.f_free);   // f of this item may be replaced once these MMAs complete
+        cur = nxt;
     }
 }
 
 // Pass 2 of tile t reads pass-2 operand buffer t % 2 and writes pass-2/3 slot t % 2. Slot b is
-// reused within a pair after the pass-2 epilogue drained it (free2, completions 0..2 of the pair's
-// four); the pair's first use waits for the previous pair's last pass-3 drain (free3x).
+// reused within a step after the pass-2 epilogue drained it (free2, completions 0..2 of the step's
+// four); the step's first use waits for the previous step's last pass-3 drain (free3x).
 template <int N, bool BF>
-__device__ __forceinline__ void mma_p2_loop(Bars& bars, uint32_t sb, uint32_t tmem, int npairs, volatile int* abort) {
+__device__ __forceinline__ void mma_p2_loop(Bars& bars, uint32_t sb, uint32_t tmem, const Items& it,
+                                            const volatile long long* s_item, volatile int* abort) {
     using G = Geo<N>;
     uint32_t ph_a2 = 0, ph_x = 0;
     constexpr uint32_t id23 = tc::idesc_f16(BF, true, false, 2 * N, 128);
     constexpr uint64_t dF = tc::sdesc_base(G::FB_LBO, G::FB_SBO);
     constexpr uint64_t dA2 = tc::sdesc_base(G::A2_LBO, G::A2_SBO);
     const uint32_t sb16 = sb >> 4;
-    for (int p = 0; p < npairs; ++p) {
-        const int fbuf = p & 1;
-        DGFS_WAITW(&bars.filt[fbuf], (uint32_t)((p >> 1) & 1));
-        tc::tc_fence_after();
-        const uint32_t f16 = sb16 + (G::S_F + fbuf * G::F_BLOCK) / 16;
-        for (int t = 0; t < G::T; ++t) {
-            const int b = t & 1, j = t >> 1;   // j-th use of slot b in this pair
-            DGFS_WAITW(&bars.a2_full[b], (ph_a2 >> b) & 1u);
-            ph_a2 ^= 1u << b;
-            if (j == 0) {
-                if (p > 0) {
-                    DGFS_WAITW(&bars.free3x[b], (ph_x >> b) & 1u);
-                    ph_x ^= 1u << b;
-                }
-            } else {
-                DGFS_WAITW(&bars.free2[b], (uint32_t)((j - 1) & 1));   // four completions per pair
-            }
+    int64_t g = 0;
+    for (int k = 0;; ++k) {
+        long long item;
+        if (!ring_take(bars, s_item, k, item, abort) || item < 0) return;
+        for (int s = 0; s < it.nseq; ++s, ++g) {
+            const int fbuf = (int)(g & 1);
+            DGFS_WAITW(&bars.filt[fbuf], (uint32_t)((g >> 1) & 1));
             tc::tc_fence_after();
-            const uint32_t d = tmem + (b ? G::C_S3 : G::C_S2);
-            const uint32_t a16 = sb16 + G::S_A2 / 16 + b * (2 * G::A2_BYTES / 16);
+            const uint32_t f16 = sb16 + (G::S_F + fbuf * G::F_BLOCK) / 16;
+            for (int t = 0; t < G::T; ++t) {
+                const int b = t & 1, j = t >> 1;   // j-th use of slot b in this step
+                DGFS_WAITW(&bars.a2_full[b], (ph_a2 >> b) & 1u);
+                ph_a2 ^= 1u << b;
+                if (j == 0) {
+                    if (g > 0) {
+                        DGFS_WAITW(&bars.free3x[b], (ph_x >> b) & 1u);
+                        ph_x ^= 1u << b;
+                    }
+                } else {
+                    DGFS_WAITW(&bars.free2[b], (uint32_t)((j - 1) & 1));   // four completions per step
+                }
+                tc::tc_fence_after();
+                const uint32_t d = tmem + (b ? G::C_S3 : G::C_S2);
+                const uint32_t a16 = sb16 + G::S_A2 / 16 + b * (2 * G::A2_BYTES / 16);
 #pragma unroll
-            for (int g = 0; g < 2; ++g)
+                for (int gs = 0; gs < 2; ++gs)
 #pragma unroll
-                for (int ks = 0; ks < G::KSTEPS; ++ks)
-                    tc::mma_ss_warp(d + g * 2 * N, tc::sdesc_at(dA2, a16 + (g * G::A2_BYTES + ks * 2 * G::A2_LBO) / 16),
-                                    tc::sdesc_at(dF, f16 + (G::OFF_B2 + g * G::B23_BYTES + ks * 2 * G::FB_LBO) / 16),
-                                    id23, ks);
-            tc::mma_commit_warp(&bars.full2[b]);
-            tc::mma_commit_warp(&bars.a2_free[b]);
+                    for (int ks = 0; ks < G::KSTEPS; ++ks)
+                        tc::mma_ss_warp(d + gs * 2 * N,
+                                        tc::sdesc_at(dA2, a16 + (gs * G::A2_BYTES + ks * 2 * G::A2_LBO) / 16),
+                                        tc::sdesc_at(dF, f16 + (G::OFF_B2 + gs * G::B23_BYTES + ks * 2 * G::FB_LBO) / 16),
+                                        id23, ks);
+                tc::mma_commit_warp(&bars.full2[b]);
+                tc::mma_commit_warp(&bars.a2_free[b]);
+            }
+            tc::mma_commit_warp(&bars.fdone[fbuf]);
         }
-        tc::mma_commit_warp(&bars.fdone[fbuf]);
     }
 }
 
 // Pass 3 of the tiles u = 2k + b into slot b once every pass-2 tile is in shared memory (a3_full
-// also orders every pass-2 drain of the slot before these MMAs); reuse within the pair waits
-// for the warpgroup's drains (free3, completions 0..2 of the pair's four).
+// also orders every pass-2 drain of the slot before these MMAs); reuse within the step waits
+// for the warpgroup's drains (free3, completions 0..2 of the step's four).
 template <int N, bool BF, int b>
-__device__ __forceinline__ void mma_p3_loop(Bars& bars, uint32_t sb, uint32_t tmem, int npairs, volatile int* abort) {
+__device__ __forceinline__ void mma_p3_loop(Bars& bars, uint32_t sb, uint32_t tmem, const Items& it,
+                                            const volatile long long* s_item, volatile int* abort) {
     using G = Geo<N>;
     uint32_t ph_a3full = 0;
     constexpr uint32_t id23 = tc::idesc_f16(BF, true, false, 2 * N, 128);
     constexpr uint64_t dF = tc::sdesc_base(G::FB_LBO, G::FB_SBO);
     constexpr uint64_t dA3 = tc::sdesc_base(G::A3_LBO, G::A3_SBO);
     const uint32_t sb16 = sb >> 4;
-    for (int p = 0; p < npairs; ++p) {
-        const int fbuf = p & 1;
-        DGFS_WAITW(&bars.filt[fbuf], (uint32_t)((p >> 1) & 1));
-        const uint32_t f16 = sb16 + (G::S_F + fbuf * G::F_BLOCK) / 16;
-        DGFS_WAITW(&bars.a3_full, ph_a3full);
-        ph_a3full ^= 1;
-        tc::tc_fence_after();
-        for (int k = 0; k < G::TW; ++k) {
-            const int u = 2 * k + b;
-            if (k > 0) {
-                DGFS_WAITW(&bars.free3[b], (uint32_t)((k - 1) & 1));   // four completions per pair
-                tc::tc_fence_after();
+    int64_t g = 0;
+    for (int ki = 0;; ++ki) {
+        long long item;
+        if (!ring_take(bars, s_item, ki, item, abort) || item < 0) return;
+        for (int s = 0; s < it.nseq; ++s, ++g) {
+            const int fbuf = (int)(g & 1);
+            DGFS_WAITW(&bars.filt[fbuf], (uint32_t)((g >> 1) & 1));
+            const uint32_t f16 = sb16 + (G::S_F + fbuf * G::F_BLOCK) / 16;
+            DGFS_WAITW(&bars.a3_full, ph_a3full);
+            ph_a3full ^= 1;
+            tc::tc_fence_after();
+            for (int k = 0; k < G::TW; ++k) {
+                const int u = 2 * k + b;
+                if (k > 0) {
+                    DGFS_WAITW(&bars.free3[b], (uint32_t)((k - 1) & 1));   // four completions per step
+                    tc::tc_fence_after();
+                }
+                const uint32_t d = tmem + (b ? G::C_S3 : G::C_S2);
+                const uint32_t a16 = sb16 + G::S_A3 / 16 + u * (G::A3_TS / 16);
+#pragma unroll
+                for (int gs = 0; gs < 2; ++gs)
+#pragma unroll
+                    for (int ks = 0; ks < G::KSTEPS; ++ks)
+                        tc::mma_ss_warp(d + gs * 2 * N,
+                                        tc::sdesc_at(dA3, a16 + (gs * G::A3_BYTES + ks * 2 * G::A3_LBO) / 16),
+                                        tc::sdesc_at(dF, f16 + (G::OFF_B3 + gs * G::B23_BYTES + ks * 2 * G::FB_LBO) / 16),
+                                        id23, ks);
+                tc::mma_commit_warp(&bars.full3[b]);
             }
-            const uint32_t d = tmem + (b ? G::C_S3 : G::C_S2);
-            const uint32_t a16 = sb16 + G::S_A3 / 16 + u * (G::A3_TS / 16);
-#pragma unroll
-            for (int g = 0; g < 2; ++g)
-#pragma unroll
-                for (int ks = 0; ks < G::KSTEPS; ++ks)
-                    tc::mma_ss_warp(d + g * 2 * N, tc::sdesc_at(dA3, a16 + (g * G::A3_BYTES + ks * 2 * G::A3_LBO) / 16),
-                                    tc::sdesc_at(dF, f16 + (G::OFF_B3 + g * G::B23_BYTES + ks * 2 * G::FB_LBO) / 16),
-                                    id23, ks);
-            tc::mma_commit_warp(&bars.full3[b]);
+            tc::mma_commit_warp(&bars.a3_free);
+            tc::mma_commit_warp(&bars.fdone[fbuf]);
         }
-        tc::mma_commit_warp(&bars.a3_free);
-        tc::mma_commit_warp(&bars.fdone[fbuf]);
     }
 }
 #undef DGFS_WAITW
 
+// Persistent: one CTA per SM pulls work items (node, block of rpc radial points) from the queue
+// counter queue[0] (zero at launch) until the items run out.
 template <int N, bool BF>
 __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
 k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const unsigned char* __restrict__ filt,
-          int npairs, int Nrho, int rpc, float* __restrict__ P, int* __restrict__ flags, int fault,
-          const float* __restrict__ coef, int accum) {
+          int npairs, int Nrho, Items it, int* __restrict__ queue, float* __restrict__ P, int* __restrict__ flags,
+          int fault, const float* __restrict__ coef, int accum) {
     using G = Geo<N>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) Bars bars;
     __shared__ uint32_t s_tmem;
-    __shared__ float s_red[G::EPI_WARPS];
+    __shared__ float s_red[2][G::EPI_WARPS];
     __shared__ int s_abort;
+    __shared__ long long s_item[kRing];
     volatile int* abort = &s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool issuer = warp == G::ISSUER;
-    // radial points r0 .. r0 + rpc - 1 of the node, one after the other: their filter blocks are
-    // consecutive, so the CTA runs one sequence of nseq (radial point, pair) steps and the set-up
-    // (barriers, TMEM, max |f|, f in TMEM) is paid once per rpc radial points
-    const int r0 = blockIdx.x * rpc, nseq = npairs * rpc;
-    const int64_t node = blockIdx.y;
     constexpr int64_t n3 = (int64_t)N * N * N;
-    const float* fb = f + (offs ? offs[node] : node * n3);
     const uint32_t sb = tc::smem_u32(smem);
-    const unsigned char* fglob = filt + (size_t)r0 * npairs * G::F_BLOCK;
 
     // filter copies issued and waited per buffer 0 / 1 (used by the MMA warp and the drain)
-    int copies0 = nseq > 0 ? 1 : 0, copies1 = nseq > 1 ? 1 : 0, waited0 = 0, waited1 = 0;
+    int copies0 = 0, copies1 = 0, waited0 = 0, waited1 = 0;
+    long long first = -1;
 
-    // ---- set-up: barriers, first filter copies, TMEM (MMA warp); max |f| (epilogue warps) -----
+    // ---- set-up: barriers, the first item and its first filter copies, TMEM (MMA warp) -----------
     if (issuer) {
         if (lane == 0) {
             for (int i = 0; i < 2; ++i) {
@@ -322,98 +402,60 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                 tc::mbar_init(&bars.filt[i], 1);
                 tc::mbar_init(&bars.fdone[i], 4);   // one commit from each MMA warp
             }
+            for (int i = 0; i < kRing; ++i) {
+                tc::mbar_init(&bars.item_full[i], 1);
+                tc::mbar_init(&bars.item_free[i], kRingConsumers);
+            }
+            tc::mbar_init(&bars.f_ready, 256);      // the epilogue warpgroups
+            tc::mbar_init(&bars.f_free, 1);
+            tc::mbar_init(&bars.scan[0], G::EPI_WARPS);
+            tc::mbar_init(&bars.scan[1], G::EPI_WARPS);
             tc::mbar_init(&bars.a3_full, 128);     // the pass-2 epilogue warpgroup
             tc::mbar_init(&bars.a3_free, 2);       // the two pass-3 MMA warps
             tc::mbar_init(&bars.drain, 4);
             tc::fence_mbar_init();
             s_abort = 0;
-            for (int p = 0; p < 2 && p < nseq; ++p) {
+        }
+        __syncwarp();
+        ring_claim(bars, s_item, queue, it, 0, first, abort);   // slot 0: no wait
+        if (lane == 0 && first >= 0) {
+            const unsigned char* f0 = item_filters<N>(filt, first, it, npairs);
+            for (int p = 0; p < 2 && p < it.nseq; ++p) {
                 tc::mbar_expect_tx(&bars.filt[p], G::F_BLOCK);
-                tc::bulk_g2s(smem + G::S_F + p * G::F_BLOCK, fglob + (size_t)p * G::F_BLOCK, G::F_BLOCK, &bars.filt[p]);
+                tc::bulk_g2s(smem + G::S_F + p * G::F_BLOCK, f0 + (size_t)p * G::F_BLOCK, G::F_BLOCK, &bars.filt[p]);
             }
         }
         __syncwarp();
+        if (first >= 0) {
+            copies0 = 1;
+            copies1 = it.nseq > 1 ? 1 : 0;
+        }
         tc::tmem_alloc(&s_tmem, G::TMEM_COLS);
-    } else if (!BF && warp < G::EPI_WARPS) {
-        // max |f| of the node; the unrolled loads and eight independent maxima keep the thread's
-        // loads in flight together (a loop carried through one maximum costs a memory round trip
-        // per element: about a tenth of the kernel at N = 32)
-        constexpr int STRIDE = 32 * G::EPI_WARPS, PER = (int)(n3 / STRIDE);
-        static_assert(n3 % STRIDE == 0 && PER % 8 == 0, "scan split");
-        float m8[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) m8[j] = 0.f;
-#pragma unroll
-        for (int i = 0; i < PER; ++i) m8[i & 7] = fmaxf(m8[i & 7], fabsf(__ldg(fb + tid + i * STRIDE)));
-        float mx = fmaxf(fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3])), fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7])));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) s_red[warp] = mx;
     }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    float sf = 1.f;
-    if (!BF) {
-        float mx = s_red[0];
-#pragma unroll
-        for (int i = 1; i < G::EPI_WARPS; ++i) mx = fmaxf(mx, s_red[i]);
-        if (mx > 0.f && isfinite(mx)) sf = exp2f(fminf(60.f, fmaxf(-60.f, floorf(log2f(2.f / mx)))));
-    }
-    const float eps = exp2f(-(float)(BF ? kLoShiftBF16 : kLoShiftF16));
-    // fp16: max |f sf| in (1, 2]; pass 1 multiplies by 2^8 (its filters), which stays in the
-    // stored intermediates and is removed, squared, from the products
-    const float out_scale = BF ? 1.f : exp2f(-2.f * kP1ShiftF16) / (sf * sf);
-
-    // ---- f -> TMEM as the pass-1 A operand: tile t, lane l = yl N + z holds f[0..N)[t ZT + yl][z] --
-    if (warp < G::EPI_WARPS) {
-        const int q = warp & 3, w = warp >> 2, l = 32 * q + lane, yl = l / N, z = l % N;
-        // tiles t = 2k + w, two at a time: both tiles' loads precede the TMEM stores (whose memory
-        // clobber would otherwise keep the next tile's loads behind them)
-        constexpr int TB = G::TW >= 2 ? 2 : 1;
-        static_assert(G::TW % TB == 0, "tile batches");
-#pragma unroll 1
-        for (int k0 = 0; k0 < G::TW; k0 += TB) {
-            uint32_t v[TB][N / 2];
-#pragma unroll
-            for (int b = 0; b < TB; ++b) {
-                const float* src = fb + (size_t)((2 * (k0 + b) + w) * G::ZT + yl) * N + z;
-#pragma unroll
-                for (int c = 0; c < N / 2; ++c)
-                    v[b][c] = pack2<BF>(__ldg(src + (size_t)(2 * c) * G::N2) * sf,
-                                        __ldg(src + (size_t)(2 * c + 1) * G::N2) * sf);
-            }
-#pragma unroll
-            for (int b = 0; b < TB; ++b) {
-                const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + G::C_F + (2 * (k0 + b) + w) * (N / 2);
-                if constexpr (N == 32) tc::tmem_st16(ta, v[b]);
-                else tc::tmem_st8(ta, v[b]);
-            }
-        }
-        tc::tmem_wait_st();
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::tc_fence_after();
     if (warp >= G::EPI_WARPS) {
       tc::setmaxnreg_dec<G::REG_MMA>();   // every warp of the third warpgroup
       // ============================ MMA warps (converged) =====================================
       if (warp == G::ISSUER)
-        mma_p1_loop<N, BF>(bars, smem, sb, tmem, fglob, nseq, abort, copies0, copies1, waited0, waited1);
+        mma_p1_loop<N, BF>(bars, smem, sb, tmem, filt, npairs, it, first, s_item, queue, abort, copies0, copies1,
+                           waited0, waited1);
       else if (warp == G::ISSUER + 1)
-        mma_p2_loop<N, BF>(bars, sb, tmem, nseq, abort);
+        mma_p2_loop<N, BF>(bars, sb, tmem, it, s_item, abort);
       else if (warp == G::ISSUER + 2)
-        mma_p3_loop<N, BF, 0>(bars, sb, tmem, nseq, abort);
+        mma_p3_loop<N, BF, 0>(bars, sb, tmem, it, s_item, abort);
       else
-        mma_p3_loop<N, BF, 1>(bars, sb, tmem, nseq, abort);
+        mma_p3_loop<N, BF, 1>(bars, sb, tmem, it, s_item, abort);
     } else {
         tc::setmaxnreg_inc<G::REG_EPI>();
         // ============================== epilogue warpgroups ===================================
-        // front (passes 1 and 2, every tile): warpgroup 0 turns each pass-1 result into the pass-2
-        // operands, warpgroup 1 each pass-2 result into rows of the pass-3 operands, so the two
-        // steps of consecutive tiles overlap; back (pass 3): warpgroup w forms the products of the
+        // per item: max |f| of its node (fp16 scale) and f into TMEM as the pass-1 A operand; then,
+        // per step, the front (passes 1 and 2, every tile): warpgroup 0 turns each pass-1 result into
+        // the pass-2 operands, warpgroup 1 each pass-2 result into rows of the pass-3 operands, so the
+        // two steps of consecutive tiles overlap; back (pass 3): warpgroup w forms the products of the
         // tiles u = 2k + w. Thread = TMEM lane l.
         const int q = warp & 3, w = warp >> 2;
         const int l = 32 * q + lane, yl = l / N, lz = l % N;   // tile row: (yl, z) in pass 1, (yl, x') in pass 2
@@ -423,6 +465,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
         const uint32_t a2_row = sb + G::S_A2 + ((uint32_t)(yl * N) >> 3) * G::A2_SBO + (lz >> 3) * G::A2_LBO + (lz & 7) * 16;
         const int mg3 = (lz * N) >> 3;
         uint32_t ph_f = 0, ph_a2free = 0, ph_a3free = 0, ph_f3 = 0;   // phase bits (bit b = ring slot b)
+        const float eps = exp2f(-(float)(BF ? kLoShiftBF16 : kLoShiftF16));
         float acc[G::TW][N];
 #pragma unroll
         for (int k = 0; k < G::TW; ++k)
@@ -432,13 +475,78 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
     do {                                                                \
         if (!tc::warp_wait((bar), (ph), abort)) goto epi_done;          \
     } while (0)
-        for (int rr = 0; rr < rpc; ++rr) {
-          for (int pp = 0; pp < npairs; ++pp) {
-            const int p = rr * npairs + pp;   // step of the CTA's (radial point, pair) sequence
+        int64_t g = 0;   // step of the CTA's (radial point, pair) sequence
+        for (int ki = 0;; ++ki) {
+          long long item;
+          if (!ring_take(bars, s_item, ki, item, abort) || item < 0) break;
+          const int64_t node = item / it.rblocks;
+          const int r0 = (int)(item % it.rblocks) * it.rpc;
+          const float* fb = f + (offs ? offs[node] : node * n3);
+          float sf = 1.f;
+          if (!BF) {
+              // max |f| of the node; the unrolled loads and eight independent maxima keep the thread's
+              // loads in flight together (a loop carried through one maximum costs a memory round trip
+              // per element: about a tenth of the kernel at N = 32)
+              constexpr int STRIDE = 32 * G::EPI_WARPS, PER = (int)(n3 / STRIDE);
+              static_assert(n3 % STRIDE == 0 && PER % 8 == 0, "scan split");
+              float m8[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) m8[j] = 0.f;
+#pragma unroll
+              for (int i = 0; i < PER; ++i) m8[i & 7] = fmaxf(m8[i & 7], fabsf(__ldg(fb + tid + i * STRIDE)));
+              float mx = fmaxf(fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3])), fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7])));
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+              if (lane == 0) {
+                  s_red[ki & 1][warp] = mx;
+                  tc::mbar_arrive(&bars.scan[ki & 1]);
+              }
+              DGFS_WAITE(&bars.scan[ki & 1], (uint32_t)((ki >> 1) & 1));   // every epilogue warp's maximum
+              mx = s_red[ki & 1][0];
+#pragma unroll
+              for (int i = 1; i < G::EPI_WARPS; ++i) mx = fmaxf(mx, s_red[ki & 1][i]);
+              if (mx > 0.f && isfinite(mx)) sf = exp2f(fminf(60.f, fmaxf(-60.f, floorf(log2f(2.f / mx)))));
+          }
+          // fp16: max |f sf| in (1, 2]; pass 1 multiplies by 2^8 (its filters), which stays in the
+          // stored intermediates and is removed, squared, from the products
+          const float out_scale = BF ? 1.f : exp2f(-2.f * kP1ShiftF16) / (sf * sf);
+          // ---- f -> TMEM as the pass-1 A operand once the previous item's pass-1 MMAs are complete:
+          // tile t, lane l = yl N + z holds f[0..N)[t ZT + yl][z]
+          if (ki > 0) DGFS_WAITE(&bars.f_free, (uint32_t)((ki - 1) & 1));
+          tc::tc_fence_after();
+          {
+              // tiles t = 2k + w, two at a time: both tiles' loads precede the TMEM stores (whose memory
+              // clobber would otherwise keep the next tile's loads behind them)
+              constexpr int TB = G::TW >= 2 ? 2 : 1;
+              static_assert(G::TW % TB == 0, "tile batches");
+#pragma unroll 1
+              for (int k0 = 0; k0 < G::TW; k0 += TB) {
+                  uint32_t v[TB][N / 2];
+#pragma unroll
+                  for (int bb = 0; bb < TB; ++bb) {
+                      const float* src = fb + (size_t)((2 * (k0 + bb) + w) * G::ZT + yl) * N + lz;
+#pragma unroll
+                      for (int c = 0; c < N / 2; ++c)
+                          v[bb][c] = pack2<BF>(__ldg(src + (size_t)(2 * c) * G::N2) * sf,
+                                               __ldg(src + (size_t)(2 * c + 1) * G::N2) * sf);
+                  }
+#pragma unroll
+                  for (int bb = 0; bb < TB; ++bb) {
+                      const uint32_t ta = trow + G::C_F + (2 * (k0 + bb) + w) * (N / 2);
+                      if constexpr (N == 32) tc::tmem_st16(ta, v[bb]);
+                      else tc::tmem_st8(ta, v[bb]);
+                  }
+              }
+              tc::tmem_wait_st();
+          }
+          tc::tc_fence_before();
+          tc::mbar_arrive(&bars.f_ready);
+          for (int rr = 0; rr < it.rpc; ++rr) {
+          for (int pp = 0; pp < npairs; ++pp, ++g) {
             if (w == 0) {
                 for (int t = 0; t < G::T; ++t) {   // pass-1 tile t (slot t % 2) -> pass-2 operands (buffer t % 2)
                     const int b = t & 1;
-                    if (p > 0 || t >= 2) {   // pass 2 of tile t - 2 has read buffer b
+                    if (g > 0 || t >= 2) {   // pass 2 of tile t - 2 has read buffer b
                         DGFS_WAITE(&bars.a2_free[b], (ph_a2free >> b) & 1u);
                         ph_a2free ^= 1u << b;
                     }
@@ -448,21 +556,21 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                     float v[2][N];   // the thread's row of the tile, both signs, behind one wait
                     const uint32_t tP1 = trow + G::C_S0 + b * G::C_S1;   // + at 0, - at N
 #pragma unroll
-                    for (int g = 0; g < 2; ++g)
+                    for (int gs = 0; gs < 2; ++gs)
 #pragma unroll
                         for (int c = 0; c < N / 16; ++c)
-                            tc::tmem_ld16(tP1 + g * N + 16 * c, *reinterpret_cast<float(*)[16]>(&v[g][16 * c]));
+                            tc::tmem_ld16(tP1 + gs * N + 16 * c, *reinterpret_cast<float(*)[16]>(&v[gs][16 * c]));
                     tc::tmem_wait_ld();
                     tc::tc_fence_before();
                     tc::mbar_arrive(&bars.free1[b]);
                     const uint32_t a2b = a2_row + b * 2 * G::A2_BYTES;
 #pragma unroll
-                    for (int g = 0; g < 2; ++g)
+                    for (int gs = 0; gs < 2; ++gs)
 #pragma unroll
                         for (int c = 0; c < N / 8; ++c) {   // 8 columns x' = 8c .. 8c + 7
                             uint32_t u[4];
-                            pack8<BF>(*reinterpret_cast<const float(*)[8]>(&v[g][8 * c]), u);
-                            tc::st_shared_v4(a2b + g * G::A2_BYTES + c * G::A2_SBO, u[0], u[1], u[2], u[3]);
+                            pack8<BF>(*reinterpret_cast<const float(*)[8]>(&v[gs][8 * c]), u);
+                            tc::st_shared_v4(a2b + gs * G::A2_BYTES + c * G::A2_SBO, u[0], u[1], u[2], u[3]);
                         }
                     tc::fence_proxy_async();
                     tc::mbar_arrive(&bars.a2_full[b]);
@@ -470,7 +578,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
             } else {
                 for (int t = 0; t < G::T; ++t) {   // pass-2 tile t (slot t % 2) -> rows of the pass-3 operands
                     const int b = t & 1, y = t * G::ZT + yl;
-                    if (t == 0 && p > 0) {   // the previous pair's pass 3 has read the operands
+                    if (t == 0 && g > 0) {   // the previous step's pass 3 has read the operands
                         DGFS_WAITE(&bars.a3_free, ph_a3free);
                         ph_a3free ^= 1;
                     }
@@ -480,15 +588,15 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                     const uint32_t tB = trow + (b ? G::C_S3 : G::C_S2);   // +hi, +lo, -hi, -lo
                     const uint32_t ky = (y >> 3) * G::A3_LBO + (y & 7) * 16;
 #pragma unroll
-                    for (int g = 0; g < 2; ++g) {   // one sign: hi and lo of the row behind one wait
+                    for (int gs = 0; gs < 2; ++gs) {   // one sign: hi and lo of the row behind one wait
                         float hi[N], lo[N];
 #pragma unroll
                         for (int c = 0; c < N / 16; ++c) {
-                            tc::tmem_ld16(tB + g * 2 * N + 16 * c, *reinterpret_cast<float(*)[16]>(&hi[16 * c]));
-                            tc::tmem_ld16(tB + g * 2 * N + N + 16 * c, *reinterpret_cast<float(*)[16]>(&lo[16 * c]));
+                            tc::tmem_ld16(tB + gs * 2 * N + 16 * c, *reinterpret_cast<float(*)[16]>(&hi[16 * c]));
+                            tc::tmem_ld16(tB + gs * 2 * N + N + 16 * c, *reinterpret_cast<float(*)[16]>(&lo[16 * c]));
                         }
                         tc::tmem_wait_ld();
-                        if (g == 1) {
+                        if (gs == 1) {
                             tc::tc_fence_before();
                             tc::mbar_arrive(&bars.free2[b]);
                         }
@@ -500,14 +608,14 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                             uint32_t u[4];
                             pack8<BF>(v, u);
                             const int mg = mg3 + c;
-                            tc::st_shared_v4(sb + G::S_A3 + g * G::A3_BYTES + (mg >> 4) * G::A3_TS + (mg & 15) * G::A3_SBO + ky,
+                            tc::st_shared_v4(sb + G::S_A3 + gs * G::A3_BYTES + (mg >> 4) * G::A3_TS + (mg & 15) * G::A3_SBO + ky,
                                              u[0], u[1], u[2], u[3]);
                         }
                     }
                 }
                 tc::fence_proxy_async();
-                // failure test: the first CTA withholds the signal for its first pair
-                if (!(fault == 1 && p == 0 && blockIdx.x == 0 && blockIdx.y == 0)) tc::mbar_arrive(&bars.a3_full);
+                // failure test: the first CTA withholds the signal for its first step
+                if (!(fault == 1 && g == 0 && blockIdx.x == 0)) tc::mbar_arrive(&bars.a3_full);
             }
             // pass-3 tiles u = 2k + w (slot w): products of the two translates
             const uint32_t tB = trow + (w ? G::C_S3 : G::C_S2);
@@ -554,6 +662,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
           for (int k = 0; k < G::TW; ++k)
 #pragma unroll
               for (int j = 0; j < N; ++j) acc[k][j] = 0.f;
+          }
         }
 #undef DGFS_WAITE
     epi_done:;
@@ -590,22 +699,22 @@ cudaError_t launch_n(const TcTables& t, const float* f, const int64_t* offs, int
     auto kern = k_tc_gain<N, BF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::S_TOTAL);
     if (e != cudaSuccess) return e;
-    const int64_t n3 = (int64_t)N * N * N;
-    // several radial points per CTA share its set-up (tc_resolve_rpc)
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const int rpc = tc_resolve_rpc(t, BF ? DGFS_PREC_BF16S : DGFS_PREC_F16S, nodes, sms);
-    for (int64_t n0 = 0; n0 < nodes; n0 += 65535) {
-        const int64_t nn = nodes - n0 < 65535 ? nodes - n0 : 65535;
-        kern<<<dim3(t.Nrho / rpc, (unsigned)nn), G::THREADS, G::S_TOTAL, s>>>(
-            f + (offs ? 0 : n0 * n3), offs ? offs + n0 : nullptr, static_cast<const unsigned char*>(t.mats),
-            t.npairs, t.Nrho, rpc, P + n0 * t.Nrho * n3, flags, n0 == 0 ? fault : 0, coef ? coef + n0 : nullptr,
-            accum);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    // radial points per item (tc_resolve_rpc); one CTA per SM pulls the items
+    Items it;
+    it.rpc = tc_resolve_rpc(t, BF ? DGFS_PREC_BF16S : DGFS_PREC_F16S, nodes, sms);
+    it.rblocks = t.Nrho / it.rpc;
+    it.nseq = it.rpc * t.npairs;
+    it.n_items = nodes * it.rblocks;
+    if (it.n_items > (int64_t)0x7FFFFFFF - 4096 || it.nseq < 1) return cudaErrorInvalidValue;
+    int* queue = flags + kQueueWord;
+    if ((e = cudaMemsetAsync(queue, 0, sizeof(int), s)) != cudaSuccess) return e;
+    const int64_t grid = it.n_items < sms ? it.n_items : sms;
+    kern<<<(unsigned)grid, G::THREADS, G::S_TOTAL, s>>>(f, offs, static_cast<const unsigned char*>(t.mats), t.npairs, t.Nrho,
+                                                        it, queue, P, flags, fault, coef, accum);
+    return cudaGetLastError();
 }
 
 // host-side rounding of a double to the 16-bit operand types

@@ -14,10 +14,11 @@ struct TcTables {
     int N = 0, Nrho = 0, npairs = 0;
     const void* mats = nullptr;     // per (r, pair, axis, sign) N x N operand tiles
     const float* wsig = nullptr;
-    int rpc = 0;                    // radial points per CTA (item): 0 = chosen from the batch (tc_resolve_rpc)
+    int rpc = 0;                    // radial points per work item: 0 = chosen from the batch (tc_resolve_rpc)
 };
 
-// Radial points per CTA (per CTA pair for the split-data kernels) of a launch over `nodes` nodes:
+// Radial points per work item of the persistent kernel (per CTA pair for the split-data kernels)
+// of a launch over `nodes` nodes:
 // t.rpc when it divides N_rho, else the most of 4, 2, 1 that divides N_rho while the grid still fills
 // the GPU's `sms` SMs at least 16 times over.
 int tc_resolve_rpc(const TcTables& t, int prec, int64_t nodes, int sms);
@@ -26,6 +27,10 @@ bool tc_supported(int N);
 int tc_extra_launches(int prec);   // launches the tensor-core path adds per chunk (beyond one)
 size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>& blob, TcTables& t);
 void rebase_tc_tables(TcTables& t, void* base);
+// Word of the plan's device flag array that counts the work items claimed by the persistent
+// translate kernel (set to zero on the stream before each launch).
+constexpr int kQueueWord = 4;
+
 // fault: 0, or 1 = the first CTA withholds its pass-3-operands-complete signal (failure test).
 // coef (device [nodes] or nullptr): P_r of node n is written times coef[n]; accumulate: added to P
 // instead of overwriting it (the two halves of a polarisation).
