@@ -199,6 +199,42 @@ def translate_flops_per_node(N, Nrho, npairs, prec):
     return Nrho * npairs * (mult * mma + elem)
 
 
+def shape_ceiling_fields(N, Nr, npairs, prec, measured, launch_ms, nodes, clocks):
+    """The kernel's cycles per (radial point, pair) step and SM (launch time at the sampled SM clock)
+    against mma_shape_ceiling: how close the kernel runs to what its MMA shapes allow."""
+    ceil, ctas = mma_shape_ceiling(N, prec, measured.get("mma_cycles", {}))
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz")
+    if not ceil or not mhz or not nodes:
+        return {}
+    kernel = launch_ms / 1e3 * mhz * 1e6 * measured["sms"] / (nodes * Nr * npairs * ctas)
+    return {"mma_shape_cycles_per_step": ceil, "kernel_cycles_per_step": kernel,
+            "frac_of_mma_shape_ceiling": ceil / kernel,
+            "mma_shape_basis": "cycles per (radial point, pair) step and SM that the kernel's own MMAs need back "
+                               "to back at the measured rates of their shapes (peaks_measured.mma_cycles), "
+                               "against the kernel's cycles per step at the sampled SM clock"}
+
+
+def mma_shape_ceiling(N, prec, mma):
+    """Cycles per (radial point, pair) step and SM that the translate kernel's own MMAs need when
+    issued back to back at the measured rates of their shapes (M = 128, K = 16), and the CTAs that
+    share one step. F16S / BF16S (one CTA per step, T = N^2 / 128 tiles, N / 16 K steps): pass 1 two
+    MMAs (hi, lo) of N = 2n per K step with A in TMEM, passes 2 and 3 one MMA of N = 2n per sign and
+    K step with A in shared memory. F16X3 / BF16X3 (a CTA pair per step, T / 2 tiles each): pass 1
+    one MMA of N = 4n and one of N = 2n (A in TMEM), passes 2 and 3 per sign one of N = 2n and one of
+    N = n (A in shared memory). None for the CUDA-core precisions or a missing shape."""
+    T, ks = N * N // 128, N // 16
+    try:
+        if prec in ("f16s", "bf16s"):
+            return T * ks * 2 * mma["tmem_n%d" % (2 * N)] + 2 * T * 2 * ks * mma["smem_n%d" % (2 * N)], 1
+        if prec in ("f16x3", "bf16x3"):
+            th = T // 2
+            return (th * ks * (mma["tmem_n%d" % (4 * N)] + mma["tmem_n%d" % (2 * N)]) +
+                    2 * th * 2 * ks * (mma["smem_n%d" % (2 * N)] + mma["smem_n%d" % N])), 2
+    except KeyError:
+        return None, None
+    return None, None
+
+
 def fft_algorithmic_flops_per_node(N, Nrho, npairs):
     """The method's work counted with radix-2 FFTs (one complex 3-D IDFT per pair gives both
     real translates; 5 N^3 log2 N^3 flops) plus ~20 flops per point per pair of phase,
@@ -209,7 +245,7 @@ def fft_algorithmic_flops_per_node(N, Nrho, npairs):
 # DRAM bytes (read + write) per node of one translate-product launch at N = 32, N_rho = 32, M = 38,
 # from the ncu capture of a 512-node launch summarised in profiles/ (None for configurations
 # without a capture of the current kernel version).
-TRAFFIC_PER_NODE = {("f16s", 32, 32, 38): 2184.94e6 / 512, ("bf16s", 32, 32, 38): 2184.69e6 / 512,
+TRAFFIC_PER_NODE = {("f16s", 32, 32, 38): (229120512 + 2087938048) / 512, ("bf16s", 32, 32, 38): None,
                     ("f16x3", 32, 32, 38): (106565888 + 2091562240) / 512,
                     ("fp32", 32, 32, 38): None}
 
@@ -255,12 +291,18 @@ def measure_peaks():
         del a, b
         return 2.0 * n ** 3 / (best / 1e3) / 1e12
 
+    # cycles per back-to-back tcgen05 MMA (M = 128, K = 16) of the shapes the translate kernels issue
+    mma = {"smem_n%d" % n: binding.device_mma_cycles(n, False) for n in (32, 64, 128, 256)}
+    mma.update({"tmem_n%d" % n: binding.device_mma_cycles(n, True) for n in (64, 128, 256)})
     out = {"sms": props.multi_processor_count,
            "l2_bytes": getattr(props, "L2_cache_size", None),
            "fp32_fma_tflops": fp32, "fp64_fma_tflops": fp64,
            "fp16_dense_tflops": mm(torch.float16), "bf16_dense_tflops": mm(torch.bfloat16),
            "tf32_dense_tflops": mm(torch.float32, tf32=True),
-           "how": "FMA chains on every SM (libdgfs probe); cuBLAS 8192^3 matmuls, best of 5 (burst)"}
+           "mma_cycles": mma,
+           "how": "FMA chains on every SM (libdgfs probe); cuBLAS 8192^3 matmuls, best of 5 (burst); "
+                  "cycles per back-to-back tcgen05.mma kind::f16, M = 128, K = 16, A from shared memory or "
+                  "TMEM (libdgfs probe, slowest SM)"}
     torch.cuda.empty_cache()
     return out
 
@@ -779,6 +821,7 @@ def main():
                  "traffic_unit": "bytes per launch", "kernel": "translate-product",
                  "kernel_share": prof["gain_ms"] / ms if ms else None,
                  "flops_per_node": flops_node, "nodes_per_launch": nodes_per_launch, "launch_ms": per_launch_ms,
+                 **shape_ceiling_fields(N, Nr, npairs, prec, measured, per_launch_ms, nodes_per_launch, clocks),
                  "fft_algorithmic_tflops": fft_algorithmic_flops_per_node(N, Nr, npairs) * value / world / 1e12})
 
     line = {"metric": METRIC, "value": value, "unit": "node-evals/s", "n_gpus": world,

@@ -353,6 +353,15 @@ dgfs_status dgfs_plan_set_tuning(dgfs_plan_t plan, int rpc, int64_t chunk_nodes)
    output may be NULL. */
 dgfs_status dgfs_device_fma_peaks(double* fp32_tflops, double* fp64_tflops);
 
+/* Tensor-core rate probe (the paper has no counterpart): SM clock cycles per tcgen05.mma.kind::f16
+   of the shape M = 128, K = 16, N = n (a multiple of 16 in [16, 256]) issued back to back into one
+   FP32 accumulator, on the slowest SM of the current device (one CTA per SM, 4096 MMAs, the second
+   of two launches). The A operand comes from shared memory (a_from_tmem = 0; MN-major, no swizzle,
+   as the translate kernels' pass-2/3 operands) or from tensor memory (1; as their pass-1 operand).
+   Sets the ceiling that the MMA shapes of a kernel allow: 2 * 128 * n * 16 flops per MMA over these
+   cycles. Synchronous; allocates a few bytes of device memory; changes no device setting. */
+dgfs_status dgfs_device_mma_cycles(int n, int a_from_tmem, double* cycles_per_mma);
+
 /* Message of the last failed call on the calling thread ("" if none). */
 const char* dgfs_last_error_message(void);
 

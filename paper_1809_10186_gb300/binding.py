@@ -74,6 +74,7 @@ _SIGNATURES = {
     "dgfs_stream_status": [_P, _P],
     "dgfs_debug_inject": [_P, ctypes.c_int],
     "dgfs_device_fma_peaks": [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "dgfs_device_mma_cycles": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
     "dgfs_plan_autotune": [_P, _P, _I64, _P, ctypes.POINTER(dgfs_tune_report)],
     "dgfs_plan_set_tuning": [_P, ctypes.c_int, _I64],
     "dgfs_profile_begin": [_P],
@@ -215,6 +216,13 @@ def device_fma_peaks():
     a, b = ctypes.c_double(0), ctypes.c_double(0)
     check(lib().dgfs_device_fma_peaks(ctypes.byref(a), ctypes.byref(b)), "dgfs_device_fma_peaks")
     return a.value, b.value
+
+
+def device_mma_cycles(n, a_from_tmem=False):
+    """SM cycles per back-to-back tcgen05 MMA of M = 128, K = 16, N = n (dgfs_device_mma_cycles)."""
+    c = ctypes.c_double(0)
+    check(lib().dgfs_device_mma_cycles(int(n), 1 if a_from_tmem else 0, ctypes.byref(c)), "dgfs_device_mma_cycles")
+    return c.value
 
 
 def _stream_ptr(stream=None):

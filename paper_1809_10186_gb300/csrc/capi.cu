@@ -1729,6 +1729,16 @@ dgfs_status dgfs_device_fma_peaks(double* fp32_tflops, double* fp64_tflops) {
     return DGFS_OK;
 }
 
+dgfs_status dgfs_device_mma_cycles(int n, int a_from_tmem, double* cycles_per_mma) {
+    if (!cycles_per_mma || n < 16 || n > 256 || n % 16 || (a_from_tmem != 0 && a_from_tmem != 1))
+        return fail(DGFS_ERR_INVALID_ARG, "n must be a multiple of 16 in [16, 256], a_from_tmem 0 or 1, output non-NULL");
+    double c = 0.0;
+    const cudaError_t e = measure_mma_cycles(n, a_from_tmem, c);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core rate probe");
+    *cycles_per_mma = c;
+    return DGFS_OK;
+}
+
 dgfs_status dgfs_debug_inject(dgfs_plan_t plan, int mode) {
     if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
     if (mode != 0 && mode != 1) return fail(DGFS_ERR_INVALID_ARG, "unknown injection mode");

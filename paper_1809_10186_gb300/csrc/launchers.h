@@ -201,5 +201,8 @@ cudaError_t launch_spectral(const DevTables<T>& t, const T* P, NodeParams np, in
 // FP32 and FP64 FMA throughput of the current device in TFLOP/s (2 flops per FMA), best of three
 // timed launches of independent FMA chains on every SM. Synchronous.
 cudaError_t measure_fma_peaks(double& fp32_tflops, double& fp64_tflops);
+// Cycles per back-to-back tcgen05.mma.kind::f16 (M = 128, K = 16, N = n) on the slowest SM; A from
+// shared memory (a_tmem = 0) or TMEM (1).
+cudaError_t measure_mma_cycles(int n, int a_tmem, double& cycles_per_mma);
 
 }  // namespace dgfs
