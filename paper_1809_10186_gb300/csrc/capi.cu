@@ -1639,7 +1639,7 @@ dgfs_status dgfs_plan_autotune(dgfs_plan_t plan, const void* f, int64_t B, void*
     DGFS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device), "cudaDeviceGetAttribute");
     const size_t n3 = (size_t)p->hp.N * p->hp.N * p->hp.N, es = elem_size(p->prec);
     void* Q = ws(p, p->off_io) + (size_t)p->chunk * n3 * es;   // the output half of the host staging area
-    // candidates: radial points per CTA (tensor-core plans; 0 = the batch-size rule) x nodes per chunk
+    // candidates: radial points per work item (tensor-core plans; 0 = the batch-size rule) x nodes per chunk
     std::vector<int> rpcs{0};
     if (is_tc(p->prec))
         for (int c : {1, 2, 4, 8})
@@ -1694,8 +1694,12 @@ dgfs_status dgfs_plan_autotune(dgfs_plan_t plan, const void* f, int64_t B, void*
         p->run_chunk = saved_chunk;
         return cuda_fail(e, "autotune timing");
     }
-    // record the resolved value of the batch-size rule, so that a cached choice means the same
-    if (best_rpc == 0 && is_tc(p->prec)) best_rpc = tc_resolve_rpc(p->tc, p->prec, best_chunk, sms);
+    // record the resolved value of the batch-size rule, so that a cached choice means the same (the
+    // rule reads the plan's rpc, which still holds the last candidate: clear it first)
+    if (best_rpc == 0 && is_tc(p->prec)) {
+        p->tc.rpc = 0;
+        best_rpc = tc_resolve_rpc(p->tc, p->prec, best_chunk, sms);
+    }
     p->tc.rpc = best_rpc;
     p->run_chunk = best_chunk;
     {

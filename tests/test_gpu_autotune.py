@@ -17,6 +17,17 @@ def built():
     torch.cuda.set_device(0)
 
 
+def _rule_rpc(prec, nodes, n_rho):
+    """The batch-size rule of the tensor-core launchers: the most of 4, 2, 1 radial points per item that
+    divides N_rho while the items (CTA pairs for the split-data kernels) fill the GPU 16 times over."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    per = 2 if prec in ("f16x3", "bf16x3") else 1
+    for c in (4, 2):
+        if n_rho % c == 0 and per * (n_rho // c) * nodes >= 16 * sms:
+            return c
+    return 1
+
+
 def _time(plan, f, q, reps=3):
     plan.collide(f, out=q)
     torch.cuda.synchronize()
@@ -53,6 +64,9 @@ def test_autotune_choice_is_never_slower_and_every_candidate_gives_the_same_resu
     if not rep["cached"]:
         assert rep["candidates"] == len(rpcs if prec != "fp32" else (0,)) * 3 or rep["candidates"] >= 3
     assert rep["ms_per_node_tuned"] <= rep["ms_per_node_default"] * 1.0001
+    if prec != "fp32" and rep["ms_per_node_tuned"] == rep["ms_per_node_default"]:
+        # the batch-size rule won: the report (and the plan) carry the rule's own value
+        assert rep["rpc"] == _rule_rpc(prec, B, 32), rep
     t_tuned = min(_time(plan, f, q) for _ in range(2))
     print("%s B=%d default %.3f ms, tuned %.3f ms (rpc %d, chunk %d)" % (prec, B, t_default, t_tuned, rep["rpc"],
                                                                          rep["chunk_nodes"]))
