@@ -62,7 +62,9 @@ typedef enum {
     DGFS_PREC_FP32 = 1,   /* CUDA-core FP32 everywhere                                              */
     DGFS_PREC_F16S = 2,   /* translates on tcgen05 tensor cores: fp16 data operands with a per-node
                              power-of-two scale, every filter split into fp16 hi + lo parts (two
-                             products), FP32 accumulation in tensor memory; FP32 elsewhere. N = 16, 32.
+                             products), FP32 accumulation in tensor memory; FP32 elsewhere. N = 16, 32,
+                             and 24 on the 32-point tiles (filters and data zero-padded: the exact
+                             24-point result at (32/24)^3 the work of a 24-point tiling).
                              For every tensor-core precision, Q(f,f), Q(f,g), the JVP and dQ/dgamma
                              take their translates on the tensor cores (the bilinear calls by
                              polarisation: the translate-product sum is symmetric in f and g, so
@@ -92,7 +94,7 @@ typedef enum {
 
 typedef struct {
     int N;                     /* grid points per velocity axis: 8, 12, 16, 24 or 32 (tensor-core
-                                  precisions: 16 or 32)                                       */
+                                  precisions: 16 or 32; F16S and BF16S also 24)               */
     double L;                  /* velocity domain [-L, L]^3 (Sec. 3.3), L > 0                   */
     double R;                  /* ball radius of the c_r integral; <= 0: 4L/(3+sqrt 2) (Appendix) */
     double gamma;              /* VHS exponent 2(1 - omega) of |c - c_*| (eq. B_gen)            */

@@ -619,8 +619,8 @@ dgfs_status dgfs_plan_create(const dgfs_plan_desc* desc, dgfs_plan_t* plan_out) 
     p->prec = desc->precision;
     if (p->hp.aniso && !vss_fused_supported(p->hp.N, p->prec == DGFS_PREC_FP64))
         return fail(DGFS_ERR_UNSUPPORTED, "the VSS kernel supports N <= 24 in FP64");
-    if (is_tc(p->prec) && !tc_supported(p->hp.N))
-        return fail(DGFS_ERR_UNSUPPORTED, "tensor-core precisions support N = 16 and 32");
+    if (is_tc(p->prec) && !tc_supported(p->hp.N, p->prec))
+        return fail(DGFS_ERR_UNSUPPORTED, "tensor-core precisions support N = 16 and 32 (F16S and BF16S also N = 24)");
     if (p->hp.aniso && is_tc(p->prec))
         return fail(DGFS_ERR_UNSUPPORTED, "the VSS kernel (alpha != 1) runs in FP64 or FP32");
     DGFS_CUDA(cudaGetDevice(&p->device), "cudaGetDevice");

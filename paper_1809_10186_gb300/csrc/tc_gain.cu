@@ -362,12 +362,13 @@ __device__ __forceinline__ void mma_p3_loop(Bars& bars, uint32_t sb, uint32_t tm
 #undef DGFS_WAITW
 
 // Persistent: one CTA per SM pulls work items (node, block of rpc radial points) from the queue
-// counter queue[0] (zero at launch) until the items run out.
-template <int N, bool BF>
+// counter queue[0] (zero at launch) until the items run out. PAD: f and P_r on an nsrc^3 grid,
+// nsrc < N (N = 24 on the 32-point tiles).
+template <int N, bool BF, bool PAD>
 __global__ void __launch_bounds__(Geo<N>::THREADS, 1)
 k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const unsigned char* __restrict__ filt,
-          int npairs, int Nrho, Items it, int* __restrict__ queue, float* __restrict__ P, int* __restrict__ flags,
-          int fault, const float* __restrict__ coef, int accum) {
+          int npairs, int Nrho, Items it, int nsrc, int* __restrict__ queue, float* __restrict__ P,
+          int* __restrict__ flags, int fault, const float* __restrict__ coef, int accum) {
     using G = Geo<N>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) Bars bars;
@@ -380,6 +381,11 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool issuer = warp == G::ISSUER;
     constexpr int64_t n3 = (int64_t)N * N * N;
+    // f and P_r live on an nsrc^3 grid: nsrc = N, or nsrc < N (N = 24 run on the 32-point tiles:
+    // the filters are zero outside the nsrc x nsrc block, f is read with zeros outside it and only
+    // the nsrc^3 block of P_r is written)
+    const int64_t n3s = PAD ? (int64_t)nsrc * nsrc * nsrc : n3;
+    constexpr bool padded = PAD;
     const uint32_t sb = tc::smem_u32(smem);
 
     // filter copies issued and waited per buffer 0 / 1 (used by the MMA warp and the drain)
@@ -481,7 +487,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
           if (!ring_take(bars, s_item, ki, item, abort) || item < 0) break;
           const int64_t node = item / it.rblocks;
           const int r0 = (int)(item % it.rblocks) * it.rpc;
-          const float* fb = f + (offs ? offs[node] : node * n3);
+          const float* fb = f + (offs ? offs[node] : node * n3s);
           float sf = 1.f;
           if (!BF) {
               // max |f| of the node; the unrolled loads and eight independent maxima keep the thread's
@@ -492,8 +498,15 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
               float m8[8];
 #pragma unroll
               for (int j = 0; j < 8; ++j) m8[j] = 0.f;
+              if constexpr (!padded) {
 #pragma unroll
-              for (int i = 0; i < PER; ++i) m8[i & 7] = fmaxf(m8[i & 7], fabsf(__ldg(fb + tid + i * STRIDE)));
+                  for (int i = 0; i < PER; ++i) m8[i & 7] = fmaxf(m8[i & 7], fabsf(__ldg(fb + tid + i * STRIDE)));
+              } else {
+                  for (int64_t i0 = tid; i0 < n3s; i0 += 8 * STRIDE)
+#pragma unroll
+                      for (int j = 0; j < 8; ++j)
+                          if (i0 + j * STRIDE < n3s) m8[j] = fmaxf(m8[j], fabsf(__ldg(fb + i0 + j * STRIDE)));
+              }
               float mx = fmaxf(fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3])), fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7])));
 #pragma unroll
               for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -524,11 +537,24 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                   uint32_t v[TB][N / 2];
 #pragma unroll
                   for (int bb = 0; bb < TB; ++bb) {
-                      const float* src = fb + (size_t)((2 * (k0 + bb) + w) * G::ZT + yl) * N + lz;
+                      const int y = (2 * (k0 + bb) + w) * G::ZT + yl;
+                      if constexpr (!padded) {
+                          const float* src = fb + (size_t)y * N + lz;
 #pragma unroll
-                      for (int c = 0; c < N / 2; ++c)
-                          v[bb][c] = pack2<BF>(__ldg(src + (size_t)(2 * c) * G::N2) * sf,
-                                               __ldg(src + (size_t)(2 * c + 1) * G::N2) * sf);
+                          for (int c = 0; c < N / 2; ++c)
+                              v[bb][c] = pack2<BF>(__ldg(src + (size_t)(2 * c) * G::N2) * sf,
+                                                   __ldg(src + (size_t)(2 * c + 1) * G::N2) * sf);
+                      } else {   // zeros outside the nsrc^3 block
+                          const bool in = y < nsrc && lz < nsrc;
+                          const float* src = fb + ((size_t)y * nsrc + lz);
+                          const size_t sx = (size_t)nsrc * nsrc;
+#pragma unroll
+                          for (int c = 0; c < N / 2; ++c) {
+                              const float a = in && 2 * c < nsrc ? __ldg(src + (size_t)(2 * c) * sx) * sf : 0.f;
+                              const float b = in && 2 * c + 1 < nsrc ? __ldg(src + (size_t)(2 * c + 1) * sx) * sf : 0.f;
+                              v[bb][c] = pack2<BF>(a, b);
+                          }
+                      }
                   }
 #pragma unroll
                   for (int bb = 0; bb < TB; ++bb) {
@@ -645,16 +671,26 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
           }
           // radial point r0 + rr done: P_r out, sums cleared
           if (!*abort) {   // P[node][r][x'][y'][z'], row m3 = x' N + z' of tile u = 2k + w, column y'
-              float* dst = P + ((size_t)node * Nrho + r0 + rr) * n3;
+              float* dst = P + ((size_t)node * Nrho + r0 + rr) * n3s;
               const float sc = out_scale * (coef ? coef[node] : 1.f);   // per-node factor (polarisation)
 #pragma unroll
               for (int k = 0; k < G::TW; ++k) {
                   const int m3 = (2 * k + w) * 128 + l, xp = m3 / N, zp = m3 % N;
-                  float* o = dst + (size_t)xp * G::N2 + zp;
+                  if constexpr (!padded) {
+                      float* o = dst + (size_t)xp * G::N2 + zp;
 #pragma unroll
-                  for (int j = 0; j < N; ++j) {
-                      if (accum) o[(size_t)j * N] += acc[k][j] * sc;
-                      else o[(size_t)j * N] = acc[k][j] * sc;
+                      for (int j = 0; j < N; ++j) {
+                          if (accum) o[(size_t)j * N] += acc[k][j] * sc;
+                          else o[(size_t)j * N] = acc[k][j] * sc;
+                      }
+                  } else if (xp < nsrc && zp < nsrc) {   // the nsrc^3 block only
+                      float* o = dst + (size_t)xp * nsrc * nsrc + zp;
+#pragma unroll
+                      for (int j = 0; j < N; ++j) {
+                          if (j >= nsrc) continue;
+                          if (accum) o[(size_t)j * nsrc] += acc[k][j] * sc;
+                          else o[(size_t)j * nsrc] = acc[k][j] * sc;
+                      }
                   }
               }
           }
@@ -696,7 +732,8 @@ template <int N, bool BF>
 cudaError_t launch_n(const TcTables& t, const float* f, const int64_t* offs, int64_t nodes, float* P,
                      int* flags, cudaStream_t s, int fault, const float* coef, int accum) {
     using G = Geo<N>;
-    auto kern = k_tc_gain<N, BF>;
+    const int nsrc = t.nsrc > 0 ? t.nsrc : N;
+    auto kern = nsrc == N ? k_tc_gain<N, BF, false> : k_tc_gain<N, BF, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::S_TOTAL);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
@@ -713,7 +750,7 @@ cudaError_t launch_n(const TcTables& t, const float* f, const int64_t* offs, int
     if ((e = cudaMemsetAsync(queue, 0, sizeof(int), s)) != cudaSuccess) return e;
     const int64_t grid = it.n_items < sms ? it.n_items : sms;
     kern<<<(unsigned)grid, G::THREADS, G::S_TOTAL, s>>>(f, offs, static_cast<const unsigned char*>(t.mats), t.npairs, t.Nrho,
-                                                        it, queue, P, flags, fault, coef, accum);
+                                                        it, nsrc, queue, P, flags, fault, coef, accum);
     return cudaGetLastError();
 }
 
@@ -743,7 +780,7 @@ double bf16_bits_value(uint16_t b) {
 
 }  // namespace
 
-bool tc_supported(int N) { return N == 16 || N == 32; }
+bool tc_supported(int N, int prec) { return N == 16 || N == 32 || (N == 24 && !tc3_precision(prec)); }
 
 int tc_resolve_rpc(const TcTables& t, int prec, int64_t nodes, int sms) {
     if (t.rpc > 0 && t.Nrho % t.rpc == 0) return t.rpc;
@@ -759,7 +796,10 @@ int tc_extra_launches(int) { return 0; }
 
 size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>& blob, TcTables& t) {
     if (tc3_precision(prec)) return build_tc3_tables(hp, prec, blob, t);
-    const int N = hp.N, np = hp.npairs, Nr = hp.Nrho;
+    // N = 24 runs on the 32-point tiles: its circulant filters fill the top-left 24 x 24 block of
+    // 32 x 32 matrices that are zero elsewhere, so every pass maps the zero-padded 24^3 field onto
+    // the zero-padded translate (the kernel reads and writes only the 24^3 block)
+    const int Nd = hp.N, N = Nd == 24 ? 32 : Nd, np = hp.npairs, Nr = hp.Nrho;
     const bool bf = prec == DGFS_PREC_BF16S;
     const double lo_scale = std::ldexp(1.0, bf ? kLoShiftBF16 : kLoShiftF16);
     const double p1_scale = bf ? 1.0 : std::ldexp(1.0, kP1ShiftF16);
@@ -782,9 +822,10 @@ size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>&
             unsigned char* blk = blob.data() + ((size_t)r * np + p) * block;
             // F_+[i][j] = a[(i - j) mod N] (translate by +s along the axis); F_- = F_+^T (T_-s = T_s^T)
             auto F = [&](int axis, int sign, int i, int j) {
-                const double* fl = &hp.filt[(((size_t)r * np + p) * 3 + axis) * N];
+                if (i >= Nd || j >= Nd) return 0.0;
+                const double* fl = &hp.filt[(((size_t)r * np + p) * 3 + axis) * Nd];
                 const int d = sign == 0 ? i - j : j - i;
-                return fl[((d % N) + N) % N];
+                return fl[((d % Nd) + Nd) % Nd];
             };
             const double w2 = 2.0 * hp.wsig[p];
             for (int g = 0; g < 2; ++g)
@@ -806,6 +847,7 @@ size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>&
                     }
         }
     t.N = N;
+    t.nsrc = Nd;
     t.Nrho = Nr;
     t.npairs = np;
     t.mats = reinterpret_cast<const void*>((uintptr_t)0);

@@ -11,7 +11,8 @@
 namespace dgfs {
 
 struct TcTables {
-    int N = 0, Nrho = 0, npairs = 0;
+    int N = 0, Nrho = 0, npairs = 0;   // N: points per axis of the tiles
+    int nsrc = 0;                   // points per axis of f and P_r (N, or 24 on 32-point tiles)
     const void* mats = nullptr;     // per (r, pair, axis, sign) N x N operand tiles
     const float* wsig = nullptr;
     int rpc = 0;                    // radial points per work item: 0 = chosen from the batch (tc_resolve_rpc)
@@ -23,7 +24,8 @@ struct TcTables {
 // the GPU's `sms` SMs at least 16 times over.
 int tc_resolve_rpc(const TcTables& t, int prec, int64_t nodes, int sms);
 
-bool tc_supported(int N);
+// N = 16, 32; N = 24 on the 32-point tiles for F16S / BF16S (zero-padded filters and data).
+bool tc_supported(int N, int prec);
 int tc_extra_launches(int prec);   // launches the tensor-core path adds per chunk (beyond one)
 size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>& blob, TcTables& t);
 void rebase_tc_tables(TcTables& t, void* base);
