@@ -364,6 +364,9 @@ dgfs_status dgfs_device_fma_peaks(double* fp32_tflops, double* fp64_tflops);
    cycles. Synchronous; allocates a few bytes of device memory; changes no device setting. */
 dgfs_status dgfs_device_mma_cycles(int n, int a_from_tmem, double* cycles_per_mma);
 
+/* The fingerprint of a plan (dgfs_host_plan_fingerprint of its descriptor). */
+dgfs_status dgfs_plan_fingerprint(dgfs_plan_t plan, uint64_t* fingerprint);
+
 /* Message of the last failed call on the calling thread ("" if none). */
 const char* dgfs_last_error_message(void);
 
@@ -375,6 +378,13 @@ const char* dgfs_last_error_message(void);
 dgfs_status dgfs_host_quadrature(const dgfs_plan_desc* desc, double* c_r, double* w_r,
                                  double* sigma_xyzw, int* n_pairs, double* R_used,
                                  double* b_used);
+
+/* Fingerprint of the plan a descriptor builds: a 64-bit FNV-1a hash of its precision, sizes,
+   scalars and every FP64 table of the host plan (quadrature, sphere rule, translate filters,
+   radial-kernel factors, loss weights, VSS factors), in a fixed order. Equal fingerprints mean the
+   same arithmetic; the tables come from the host's libm, so machines of different architecture can
+   give different fingerprints for one descriptor. No GPU needed. */
+dgfs_status dgfs_host_plan_fingerprint(const dgfs_plan_desc* desc, uint64_t* fingerprint);
 
 /* Circulant translate filter a[N] of the shift t along one axis: (T_t f)_j =
    sum_j' a[(j - j') mod N] f_j', the grid restriction of the trigonometric interpolant

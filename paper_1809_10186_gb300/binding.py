@@ -75,6 +75,8 @@ _SIGNATURES = {
     "dgfs_debug_inject": [_P, ctypes.c_int],
     "dgfs_device_fma_peaks": [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "dgfs_device_mma_cycles": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
+    "dgfs_plan_fingerprint": [_P, ctypes.POINTER(ctypes.c_uint64)],
+    "dgfs_host_plan_fingerprint": [ctypes.POINTER(dgfs_plan_desc), ctypes.POINTER(ctypes.c_uint64)],
     "dgfs_plan_autotune": [_P, _P, _I64, _P, ctypes.POINTER(dgfs_tune_report)],
     "dgfs_plan_set_tuning": [_P, ctypes.c_int, _I64],
     "dgfs_profile_begin": [_P],
@@ -211,6 +213,14 @@ def host_vss_tables(**kw):
     return A, GL
 
 
+def host_plan_fingerprint(**kw):
+    """64-bit fingerprint of the plan a descriptor builds (dgfs_host_plan_fingerprint; no GPU)."""
+    d, _keep = make_desc(**kw)
+    out = ctypes.c_uint64(0)
+    check(lib().dgfs_host_plan_fingerprint(ctypes.byref(d), ctypes.byref(out)), "dgfs_host_plan_fingerprint")
+    return out.value
+
+
 def device_fma_peaks():
     """(FP32, FP64) FMA throughput of the current device in TFLOP/s, measured (dgfs_device_fma_peaks)."""
     a, b = ctypes.c_double(0), ctypes.c_double(0)
@@ -319,6 +329,12 @@ class Plan:
 
     def set_tuning(self, rpc=0, chunk_nodes=0):
         check(lib().dgfs_plan_set_tuning(self.handle, int(rpc), ctypes.c_int64(chunk_nodes)), "dgfs_plan_set_tuning")
+
+    def fingerprint(self):
+        """64-bit fingerprint of the plan's tables (dgfs_plan_fingerprint)."""
+        out = ctypes.c_uint64(0)
+        check(lib().dgfs_plan_fingerprint(self.handle, ctypes.byref(out)), "dgfs_plan_fingerprint")
+        return out.value
 
     def profile_begin(self):
         check(lib().dgfs_profile_begin(self.handle), "dgfs_profile_begin")

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/dgfs.h"
 #include "launchers.h"
@@ -125,6 +126,20 @@ struct dgfs_plan_s {
 };
 
 namespace {
+
+// NVTX range around a phase of a call (visible in a profiler's timeline; no cost without one).
+// end() closes it early; the destructor closes it otherwise.
+struct NvtxRange {
+    bool open = true;
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    void end() {
+        if (open) nvtxRangePop();
+        open = false;
+    }
+    ~NvtxRange() { end(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 bool is_tc(int prec) {
     return prec == DGFS_PREC_F16S || prec == DGFS_PREC_BF16S || prec == DGFS_PREC_F16X3 || prec == DGFS_PREC_BF16X3;
@@ -322,6 +337,7 @@ dgfs_status vss_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
                       cudaStream_t s) {
     if (op == Op::Vjp || op == Op::Dgamma)
         return fail(DGFS_ERR_UNSUPPORTED, "the VSS kernel (alpha != 1) supports Q(f,f), Q(f,g) and the JVP");
+    NvtxRange range("dgfs VSS chunk");
     if (offs) return fail(DGFS_ERR_UNSUPPORTED, "the VSS kernel (alpha != 1) takes no node offsets");
     const DevTables<T>& t = tables<T>(p);
     const int N = t.N, np = t.npairs, Nr = t.Nrho, nw = (np + 1) / 2;
@@ -444,6 +460,7 @@ template <typename T>
 dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, const int64_t* offs,
                       NodeParams np, int64_t nodes, cudaStream_t s) {
     if (p->hp.aniso) return vss_chunk<T>(p, op, f, g, out, offs, nodes, s);
+    NvtxRange chunk_range("dgfs chunk");
     const DevTables<T>& t = tables<T>(p);
     const int xf = p->xfields;
     T* P = reinterpret_cast<T*>(ws(p, p->off_P));
@@ -479,6 +496,7 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
     }
     // gain products: Q(f,f) and dQ/dgamma use (f, f); Q(f,g) uses (f, g); JVP uses (f, v)
     const T* gg = (op == Op::Collide || op == Op::Dgamma) ? nullptr : g;
+    NvtxRange translate_range("dgfs translate products");
     if (p->prof) {
         p->prof_launches += (spectral_supported(tables<T>(p)) ? 5 : 11 + (op == Op::Jvp ? 1 : 0)) +
                             tc_extra_launches(p->prec);
@@ -510,6 +528,8 @@ dgfs_status run_chunk(dgfs_plan_s* p, Op op, const T* f, const T* g, T* out, con
         e = launch_gain_products(t, f, gg, offs, nodes, P, s);
     }
     if (e) return cuda_fail(e, "translate-product kernel");
+    translate_range.end();
+    NvtxRange fourier_range("dgfs Fourier stage");
     if (p->prof && p->prof_timed < (int64_t)p->ev.size() / 2) {
         cudaEventRecord(p->ev[2 * p->prof_timed + 1], s);
         p->prof_timed += 1;
@@ -841,6 +861,7 @@ dgfs_status dgfs_collide_ragged(const dgfs_plan_t* plans, int nplans, const int3
     if (!aligned16(f) || !aligned16(Q)) return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
     if (f == Q) return fail(DGFS_ERR_INVALID_ARG, "output aliases the input");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    NvtxRange range("dgfs ragged batch");
     for (int pi = 0; pi < nplans; ++pi) {
         dgfs_plan_s* p = plans[pi];
         std::lock_guard<std::mutex> lock(p->host_mu);
@@ -940,6 +961,7 @@ dgfs_status dgfs_ragged_create(const dgfs_plan_t* plans, int nplans, const int32
 
 dgfs_status dgfs_ragged_collide(dgfs_ragged_t r, const void* f, void* Q, void* stream) {
     if (!check_ragged_handle(r)) return fail(DGFS_ERR_STATE, "invalid or destroyed ragged schedule");
+    NvtxRange range("dgfs ragged schedule");
     int64_t B = 0;
     for (int64_t c : r->count) B += c;
     if (B == 0) return DGFS_OK;
@@ -1039,6 +1061,7 @@ dgfs_status dgfs_ssprk(dgfs_plan_t plan, int order, void* f, int64_t B, double d
                        void* stream) {
     if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
     if (order != 2 && order != 3) return fail(DGFS_ERR_INVALID_ARG, "order must be 2 or 3");
+    NvtxRange range("dgfs SSP-RK steps");
     if (B < 0 || nsteps < 0) return fail(DGFS_ERR_INVALID_ARG, "B and nsteps must be >= 0");
     if (!std::isfinite(dt) || !std::isfinite(scale)) return fail(DGFS_ERR_INVALID_ARG, "dt and scale must be finite");
     if (B == 0 || nsteps == 0) return DGFS_OK;
@@ -1243,6 +1266,7 @@ dgfs_status dgfs_dg_collide(dgfs_dg_t dg, const void* F, void* C, int64_t E, voi
     if (!check_dg(dg)) return fail(DGFS_ERR_STATE, "invalid or destroyed DG operator");
     if (!check_plan(dg->plan)) return fail(DGFS_ERR_STATE, "the DG operator's plan was destroyed");
     if (E < 0) return fail(DGFS_ERR_INVALID_ARG, "E must be >= 0");
+    NvtxRange range("dgfs DG element collision");
     if (E == 0) return DGFS_OK;
     if (!F || !C) return fail(DGFS_ERR_INVALID_ARG, "NULL field pointer");
     if (!aligned16(F) || !aligned16(C)) return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
@@ -1457,6 +1481,7 @@ dgfs_status dgfs_slab_rhs(dgfs_slab_t slab, const void* F, void* dFdt, void* str
     if (F == dFdt) return fail(DGFS_ERR_INVALID_ARG, "output aliases the input");
     DGFS_ON_DEVICE(slab->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    NvtxRange range("dgfs slab right-hand side");
     return slab->plan->prec == DGFS_PREC_FP64
                ? slab_rhs<double>(slab, static_cast<const double*>(F), static_cast<double*>(dFdt), s)
                : slab_rhs<float>(slab, static_cast<const float*>(F), static_cast<float*>(dFdt), s);
@@ -1468,6 +1493,7 @@ dgfs_status dgfs_slab_ssprk(dgfs_slab_t slab, int order, void* F, double dt, int
     if (nsteps < 0 || !std::isfinite(dt)) return fail(DGFS_ERR_INVALID_ARG, "nsteps >= 0 and finite dt required");
     if (nsteps == 0) return DGFS_OK;
     if (!F) return fail(DGFS_ERR_INVALID_ARG, "NULL field pointer");
+    NvtxRange range("dgfs slab SSP-RK steps");
     if (!aligned16(F)) return fail(DGFS_ERR_INVALID_ARG, "field pointer must be 16-byte aligned");
     DGFS_ON_DEVICE(slab->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1500,6 +1526,7 @@ dgfs_status dgfs_host_dg_stiffness(int K, double* S, double* Minv) {
 dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host, int64_t B,
                               void* stream) {
     if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    NvtxRange range("dgfs host-buffer pipeline");
     if (B < 0) return fail(DGFS_ERR_INVALID_ARG, "B must be >= 0");
     if (B == 0) return DGFS_OK;
     if (!f_host || !Q_host) return fail(DGFS_ERR_INVALID_ARG, "NULL argument");
@@ -1615,6 +1642,7 @@ dgfs_status dgfs_plan_autotune(dgfs_plan_t plan, const void* f, int64_t B, void*
     if (B < 1 || !f || !report) return fail(DGFS_ERR_INVALID_ARG, "autotune needs B >= 1, f and a report");
     if (!aligned16(f)) return fail(DGFS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
     if (plan->hp.aniso) return fail(DGFS_ERR_UNSUPPORTED, "autotune of a VSS plan (alpha != 1)");
+    NvtxRange range("dgfs autotune");
     dgfs_plan_s* p = plan;
     const int64_t nodes = std::min<int64_t>(B, p->chunk);
     const TuneKey key{p->hp.N, p->hp.npairs, p->hp.Nrho, p->hp.rank, p->prec, floor_log2(nodes)};
@@ -1782,6 +1810,23 @@ dgfs_status dgfs_host_quadrature(const dgfs_plan_desc* desc, double* c_r, double
             sigma_xyzw[4 * i + 2] = hp.sig[3 * i + 2];
             sigma_xyzw[4 * i + 3] = hp.wsig[i];
         }
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_host_plan_fingerprint(const dgfs_plan_desc* desc, uint64_t* fingerprint) {
+    if (!desc || !fingerprint) return fail(DGFS_ERR_INVALID_ARG, "NULL argument");
+    HostPlan hp;
+    std::string err;
+    const dgfs_status st = build_host_plan(*desc, hp, err);
+    if (st != DGFS_OK) return fail(st, err);
+    *fingerprint = plan_fingerprint(hp, desc->precision);
+    return DGFS_OK;
+}
+
+dgfs_status dgfs_plan_fingerprint(dgfs_plan_t plan, uint64_t* fingerprint) {
+    if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
+    if (!fingerprint) return fail(DGFS_ERR_INVALID_ARG, "NULL argument");
+    *fingerprint = plan_fingerprint(plan->hp, plan->prec);
     return DGFS_OK;
 }
 

@@ -782,4 +782,37 @@ dgfs_status build_host_plan(const dgfs_plan_desc& d, HostPlan& p, std::string& e
     return DGFS_OK;
 }
 
+uint64_t plan_fingerprint(const HostPlan& hp, int prec) {
+    uint64_t h = 1469598103934665603ull;   // FNV-1a offset basis
+    auto bytes = [&](const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) {
+            h ^= c[i];
+            h *= 1099511628211ull;   // FNV prime
+        }
+    };
+    auto i64 = [&](int64_t v) { bytes(&v, sizeof v); };
+    auto f64 = [&](double v) { bytes(&v, sizeof v); };
+    auto vec = [&](const std::vector<double>& v) {
+        i64((int64_t)v.size());
+        if (!v.empty()) bytes(v.data(), v.size() * sizeof(double));
+    };
+    i64(prec);
+    i64(hp.N);
+    i64(hp.Nrho);
+    i64(hp.npairs);
+    i64(hp.rank);
+    i64(hp.loss_mode);
+    i64(hp.aniso ? 1 : 0);
+    f64(hp.L);
+    f64(hp.R);
+    f64(hp.gamma);
+    f64(hp.b);
+    f64(hp.alpha);
+    for (const std::vector<double>* v : {&hp.cr, &hp.wr, &hp.sig, &hp.wsig, &hp.filt, &hp.Uk, &hp.Vr, &hp.Lr, &hp.Fa,
+                                         &hp.GLa, &hp.mu})
+        vec(*v);
+    return h;
+}
+
 }  // namespace dgfs

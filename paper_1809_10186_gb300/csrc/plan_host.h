@@ -39,6 +39,11 @@ struct HostPlan {
 // Funk-Hecke series of its Legendre expansion; k_abs = |k|, mu = sigma.k / |k|.
 double vss_F(double b, double gamma, double alpha, double L, double k_abs, double mu, double c_r);
 
+// 64-bit FNV-1a hash of everything a plan of precision prec is built from: the sizes, the scalars
+// and every table of the host plan (doubles by their bit patterns, in a fixed order). Two plans
+// with the same fingerprint compute the same arithmetic.
+uint64_t plan_fingerprint(const HostPlan& hp, int prec);
+
 // Gauss-Legendre rule on [a, b] by Newton iteration on the Legendre recurrence.
 void gauss_legendre(int n, double a, double b, std::vector<double>& x, std::vector<double>& w);
 

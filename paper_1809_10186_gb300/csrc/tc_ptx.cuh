@@ -46,8 +46,13 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
+// try_wait rounds before a wait gives up: about a second on a GB300 (each round may suspend the
+// thread for a few microseconds), three orders of magnitude above the longest legitimate wait of
+// the kernels (one work item, under a millisecond).
+constexpr uint32_t kWaitRounds = 1u << 18;
+
 // Bounded wait on the phase with the given parity; false if it did not complete in time.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_iter = (1u << 20)) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_iter = kWaitRounds) {
     const uint32_t a = smem_u32(bar);
     for (uint32_t it = 0; it < max_iter; ++it) {
         uint32_t done;
@@ -63,7 +68,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
 // Bounded wait that also gives up as soon as another role of the CTA has raised *abort.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort) {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < (1u << 20); ++it) {
+    for (uint32_t it = 0; it < kWaitRounds; ++it) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\t"
                      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -219,7 +224,7 @@ __device__ __forceinline__ void mma_commit_warp(uint64_t* bar) {
 // than the wait itself). False, with *abort raised, on timeout or when another role aborted.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < (1u << 20); ++it) {
+    for (uint32_t it = 0; it < kWaitRounds; ++it) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\t"
                      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -272,7 +277,7 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
 // As warp_wait, acquiring at cluster scope: for barriers that threads of another CTA arrive on.
 __device__ __forceinline__ bool warp_wait_cluster(uint64_t* bar, uint32_t parity, volatile int* abort) {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < (1u << 20); ++it) {
+    for (uint32_t it = 0; it < kWaitRounds; ++it) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\t"
                      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"

@@ -175,3 +175,16 @@ def test_dg_stiffness_matches_oracle(lib, K):
     np.testing.assert_allclose(Minv, np.linalg.inv(dg_tensors(K)[1]), rtol=1e-11, atol=1e-11)
     with pytest.raises(binding.DGFSError):
         binding.host_dg_stiffness(1)
+
+
+def test_plan_fingerprint_tracks_every_input(lib):
+    """dgfs_host_plan_fingerprint: a pure function of the descriptor (the same descriptor twice gives
+    the same value); any change of a parameter that enters the tables (gamma, N_rho, the sphere rule,
+    the SVD truncation) or of the precision changes it."""
+    base = dict(N=16, L=5.0, gamma=0.52, M=12, N_rho=12, svd_tol=1e-8, precision="f16s")
+    f0 = binding.host_plan_fingerprint(**base)
+    assert f0 == binding.host_plan_fingerprint(**base)
+    for change in (dict(gamma=0.53), dict(N_rho=16), dict(M=26), dict(svd_tol=1e-6), dict(precision="fp32"),
+                   dict(L=5.5), dict(N=24)):
+        other = dict(base, **change)
+        assert binding.host_plan_fingerprint(**other) != f0, change

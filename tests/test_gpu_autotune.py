@@ -88,3 +88,11 @@ def test_set_tuning_rejects_a_radial_split_that_does_not_divide_n_rho():
     with pytest.raises(binding.DGFSError):
         plan.set_tuning(5, 0)
     plan.close()
+
+
+def test_plan_fingerprint_equals_the_host_builders():
+    """dgfs_plan_fingerprint of a device plan equals dgfs_host_plan_fingerprint of its descriptor."""
+    kw = dict(N=32, L=7.0, gamma=0.52, M=38, N_rho=32, svd_tol=1e-8, precision="f16s")
+    plan = binding.Plan(max_batch=16, **kw)
+    assert plan.fingerprint() == binding.host_plan_fingerprint(**kw)
+    plan.close()
