@@ -9,8 +9,8 @@
 //                operand(s), packed two real fields per complex slot; forward FFT along x and z
 //   k_spec_y     the planes kx and -kx of every slot: forward FFT along y (each thread one line,
 //                loaded straight into registers), the spectra of the packed fields separated with
-//                the mirror point -k (in the other plane), gain^ = sum_s Uk[s] X^_s and
-//                loss^ = GL(k) g^; inverse FFT along y and z
+//                the mirror point -k (in the other plane), gain^ = sum_s Uk[s] X^_s (the factors
+//                staged in shared memory by |k|^2) and loss^ = GL(k) g^; inverse FFT along y and z
 //   k_spec_xout  inverse FFT along x (each thread one line per field, in registers) and
 //                Q = gain - f (K_L g)
 //
@@ -38,8 +38,6 @@ struct SpecGeo {
     static constexpr int V = N2 / T1;
     static constexpr int RB = N == 32 ? 5 : 8;                  // radial points of P in flight per thread
     static constexpr int T2 = 256;                             // k_spec_y
-    static constexpr int GS = T2 / (2 * N);                    // slots per group: one y line per thread
-    static constexpr int PT = (2 * N2 + T2 - 1) / T2;          // combine points per thread
     static constexpr int YP = N * N <= 256 ? N : 256 / N;      // k_spec_xout: planes y per CTA
     static_assert(V == 1 || V == 4, "points per thread");
 };
@@ -324,23 +322,44 @@ k_spec_xz(const T* __restrict__ P, const T* __restrict__ Cg, int64_t c_stride, i
 }
 
 // ---- kernel 2: FFT along y, combine, inverse FFT along y and z of the planes kx, -kx ----------
-// CTA pp of a node: planes {pp, N - pp} (mirrors of each other), or {0, N/2} for pp = 0 (each its
-// own mirror). Thread t transforms the y line (slot t / 2N of the group, plane (t / N) % 2,
-// column t % N), loaded from X into registers; the next group's line is in flight during the
-// current group's combine.
+// CTA c of a node, c = 0 .. N/2: planes {c, N - c} for 0 < c < N/2 (mirrors of each other), the
+// single planes {0} and {N/2} (each its own mirror) for c = 0 and N/2; both planes of a CTA share
+// |kx|^2. A group holds GS = T2 / (npl N) slots; thread t transforms the y line (slot t / (npl N),
+// plane (t / N) % npl, column t % N), loaded from X into registers, and the next group's line is in
+// flight during the current group's combine. The radial factors of the group's fields are staged
+// in shared memory by |ky|^2 + |kz|^2 (U_s depends on |k|^2 only), zero for the fields past the
+// rank, so the gain sum runs without branches. The loss field(s) are picked up in a separate pass
+// of the group that holds them and parked, times their multiplier, in this CTA's planes of Y until
+// the inverse transforms.
+template <int N>
+constexpr int ilog2() { return N == 8 ? 3 : N == 16 ? 4 : 5; }
+
+// Row stride of k_spec_y's factor table: every field of a slot group, plus one pair of padding (an
+// even stride, so that a pair of factors loads as 8 bytes; 18 at N = 32 spreads a warp's rows over
+// the banks).
+template <int N>
+constexpr int spec_y_table_stride() { return 2 * (256 / N) + 2; }
+
 template <typename T, int N, int NL>
 __global__ void __launch_bounds__(SpecGeo<N>::T2, 2)
 k_spec_y(const Cplx<T>* __restrict__ X, int xs, const T* __restrict__ Uq, int nq2, const T* __restrict__ Lr,
          const T* __restrict__ GL0, const T* __restrict__ GLd, const double* __restrict__ cr, NodeParams np,
          int Nrho, int rank, int lf0, int lf1, T gscale, T lscale, Cplx<T>* __restrict__ Y, int yf) {
     using G = SpecGeo<N>;
-    constexpr int GS = G::GS, PT = G::PT;
+    constexpr int LN = ilog2<N>();
+    constexpr int GSX = G::T2 / N;                      // slots (planes) of the buffer: a group of one-plane CTAs
+    constexpr int PT = (2 * G::N2 + G::T2 - 1) / G::T2; // combine points per thread (two planes)
+    constexpr int MR = 2 * (N / 2) * (N / 2) + 1;       // |ky|^2 + |kz|^2 = 0 .. 2 (N/2)^2
+    constexpr int US = spec_y_table_stride<N>();        // row of the factor table (even: pairs load as 8 bytes)
+    constexpr int MRW = (MR + 31) / 32;                 // table rows per lane
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    Cplx<T>* buf = reinterpret_cast<Cplx<T>*>(sm_raw);         // [GS][2][PLANE]; later [yf][2][PLANE]
-    double* rho = reinterpret_cast<double*>(buf + GS * 2 * G::PLANE);   // [Nrho]
-    const int pp = blockIdx.x, t = threadIdx.x;
-    const bool self = pp == 0;
-    const int kx0 = pp, kx1 = self ? N / 2 : N - pp;
+    Cplx<T>* buf = reinterpret_cast<Cplx<T>*>(sm_raw);  // [GSX][PLANE]: slot jm, plane pl at jm npl + pl
+    T* Us = reinterpret_cast<T*>(buf + GSX * G::PLANE); // [MR][US]
+    double* rho = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(Us + MR * US) + 15) & ~uintptr_t(15));
+    const int c = blockIdx.x, t = threadIdx.x;
+    const int npl = (c == 0 || c == N / 2) ? 1 : 2, sh = npl - 1;
+    const int kx0 = c, kx1 = N - c, GS = G::T2 >> (LN + sh);
+    const int kq = signed_q<N>(kx0), kx2 = kq * kq;
     const int64_t node = blockIdx.y, n3 = (int64_t)N * G::N2;
     const bool per_node = np.gamma || np.b;
     if (per_node) {
@@ -350,23 +369,32 @@ k_spec_y(const Cplx<T>* __restrict__ X, int xs, const T* __restrict__ Uq, int nq
     }
     const Cplx<T>* Xn = X + node * (int64_t)xs * n3;
     // this thread's y line
-    const int ljm = t / (2 * N), lpl = (t / N) % 2, lkz = t % N;
+    const int ljm = t >> (LN + sh), lpl = (t >> LN) & sh, lkz = t & (N - 1);
     const int64_t loff = (int64_t)(lpl ? kx1 : kx0) * G::N2 + lkz;   // X[m][kx][y][kz] at y = 0
-    // this thread's combine points e = t + i T2: plane e / N^2, (ky, kz)
-    int q2[PT];
+    const int npts = npl * G::N2;
+    // this thread's combine points e = t + i T2: plane e / N^2, (ky, kz); row |ky|^2 + |kz|^2 of the table
+    int mrow[PT];
     T gr[PT], gi[PT];
-    Cplx<T> l0[PT], l1[NL == 2 ? PT : 1];
 #pragma unroll
     for (int i = 0; i < PT; ++i) {
-        const int e = t + i * G::T2;
-        const int pl = e / G::N2, ky = (e / N) % N, kz = e % N;
-        const int kxp = pl ? kx1 : kx0;
-        q2[i] = signed_q<N>(kxp) * signed_q<N>(kxp) + signed_q<N>(ky) * signed_q<N>(ky) +
-                signed_q<N>(kz) * signed_q<N>(kz);   // Uk[s](k) = Uq[s][|k|^2]
+        const int e = t + i * G::T2, ky = (e >> LN) & (N - 1), kz = e & (N - 1);
+        mrow[i] = signed_q<N>(ky) * signed_q<N>(ky) + signed_q<N>(kz) * signed_q<N>(kz);
         gr[i] = gi[i] = T(0);
-        l0[i] = Cplx<T>{T(0), T(0)};
-        if constexpr (NL == 2) l1[i] = Cplx<T>{T(0), T(0)};
     }
+    Cplx<T>* Yn = Y + node * (int64_t)yf * n3;
+    auto kidx = [&](int e) {   // spectrum index of point e
+        const int pl = e >> (2 * LN), ky = (e >> LN) & (N - 1), kz = e & (N - 1);
+        return ((int64_t)(pl ? kx1 : kx0) * N + ky) * N + kz;
+    };
+    // the two spectra a slot packs at point e (times 2): field 2m in fa, field 2m + 1 in fb
+    auto unpack = [&](int e, int jm, Cplx<T>& fa, Cplx<T>& fb) {
+        const int pl = e >> (2 * LN), ky = (e >> LN) & (N - 1), kz = e & (N - 1);
+        const int pm = npl == 2 ? 1 - pl : pl, kym = (N - ky) & (N - 1), kzm = (N - kz) & (N - 1);
+        const Cplx<T> z = ldc(buf + (jm * npl + pl) * G::PLANE + ky * G::ROW + kz);
+        const Cplx<T> w = ldc(buf + (jm * npl + pm) * G::PLANE + kym * G::ROW + kzm);
+        fa = Cplx<T>{z.x + w.x, z.y - w.y};
+        fb = Cplx<T>{z.y + w.y, w.x - z.x};
+    };
     Cplx<T> a[N];
     auto load_line = [&](int g0) {
         if (g0 + ljm < xs) {
@@ -375,81 +403,99 @@ k_spec_y(const Cplx<T>* __restrict__ X, int xs, const T* __restrict__ Uq, int nq
             for (int k = 0; k < N; ++k) a[bitrev<N>(k)] = ldgc(src + k * N);
         }
     };
+    // factors of the group's fields [f0, f0 + nf) at |k|^2 = |kx|^2 + row, into table columns
+    // [c0, c0 + nf) (zero past the rank): one field per warp, rows along the lanes (coalesced reads of
+    // the compact table), every load of a lane in flight before its stores
+    auto fill = [&](int f0, int nf, int c0) {
+        for (int j = t >> 5; j < nf; j += G::T2 / 32) {
+            const int fi = f0 + j, lane = t & 31;
+            const T* src = Uq + (int64_t)fi * nq2 + kx2;
+            T v[MRW];
+#pragma unroll
+            for (int r = 0; r < MRW; ++r) v[r] = fi < rank && lane + 32 * r < MR ? __ldg(src + lane + 32 * r) : T(0);
+#pragma unroll
+            for (int r = 0; r < MRW; ++r)
+                if (lane + 32 * r < MR) Us[(lane + 32 * r) * US + c0 + j] = v[r];
+        }
+    };
     load_line(0);
     for (int g0 = 0; g0 < xs; g0 += GS) {
-        const int ng = xs - g0 < GS ? xs - g0 : GS;
+        const int ng = xs - g0 < GS ? xs - g0 : GS, f0 = 2 * g0, nf = 2 * ng;
         const bool mine = ljm < ng;
         if (mine) fftc<T, N, true>(a);
-        __syncthreads();   // the previous group's combine has read buf
+        __syncthreads();   // the previous group's combine has read buf and the factor table
         if (mine) {
-            Cplx<T>* d = buf + (ljm * 2 + lpl) * G::PLANE + lkz;
+            Cplx<T>* d = buf + (ljm * npl + lpl) * G::PLANE + lkz;
 #pragma unroll
             for (int k = 0; k < N; ++k) stc(d + k * G::ROW, a[k]);
         }
+        fill(f0, nf, 0);
         __syncthreads();
         if (g0 + GS < xs) load_line(g0 + GS);   // in flight during the combine below
 #pragma unroll
         for (int i = 0; i < PT; ++i) {
             const int e = t + i * G::T2;
-            if (e >= 2 * G::N2) continue;
-            const int pl = e / G::N2, ky = (e / N) % N, kz = e % N;
-            const int pm = self ? pl : 1 - pl, kym = (N - ky) % N, kzm = (N - kz) % N;
-            const Cplx<T>* zp = buf + pl * G::PLANE + ky * G::ROW + kz;
-            const Cplx<T>* wp = buf + pm * G::PLANE + kym * G::ROW + kzm;
+            if (e >= npts) continue;
+            const T* urow = Us + mrow[i] * US;
 #pragma unroll
-            for (int jm = 0; jm < GS; ++jm) {
+            for (int jm = 0; jm < GSX; ++jm) {
                 if (jm >= ng) break;
-                const Cplx<T> z = ldc(zp + jm * 2 * G::PLANE), w = ldc(wp + jm * 2 * G::PLANE);
-                // twice the spectra of the real fields 2m and 2m + 1 packed in slot m
-                const Cplx<T> fa{z.x + w.x, z.y - w.y};
-                const Cplx<T> fb{z.y + w.y, w.x - z.x};
-                const int m = g0 + jm;
+                Cplx<T> fa, fb;
+                unpack(e, jm, fa, fb);
+                const typename Vec2<T>::type uu = *reinterpret_cast<const typename Vec2<T>::type*>(urow + 2 * jm);
+                const T ua = uu.x, ub = uu.y;
+                gr[i] = fma(ua, fa.x, gr[i]);
+                gi[i] = fma(ua, fa.y, gi[i]);
+                gr[i] = fma(ub, fb.x, gr[i]);
+                gi[i] = fma(ub, fb.y, gi[i]);
+            }
+        }
+        // the loss operand(s) of this group, times the loss multiplier, parked in Y (field 1 + jl)
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int fi = 2 * m + h;
-                    const Cplx<T> v = h ? fb : fa;
-                    if (fi < rank) {
-                        const T u = __ldg(Uq + fi * nq2 + q2[i]);
-                        gr[i] = fma(u, v.x, gr[i]);
-                        gi[i] = fma(u, v.y, gi[i]);
-                    } else if (fi == lf0) {
-                        l0[i] = v;
-                    } else if (NL == 2 && fi == lf1) {
-                        l1[NL == 2 ? i : 0] = v;
-                    }
-                }
+        for (int jl = 0; jl < NL; ++jl) {
+            const int lf = jl ? lf1 : lf0;
+            if (lf < f0 || lf >= f0 + nf) continue;
+            const int jm = (lf - f0) >> 1, h = (lf - f0) & 1;
+#pragma unroll
+            for (int i = 0; i < PT; ++i) {
+                const int e = t + i * G::T2;
+                if (e >= npts) continue;
+                Cplx<T> fa, fb;
+                unpack(e, jm, fa, fb);
+                const Cplx<T> v = h ? fb : fa;
+                const int64_t k = kidx(e);
+                const T GL = lscale * loss_multiplier<T>(GL0, GLd, Lr, rho, per_node, np.dlog, Nrho, n3, k);
+                stc(Yn + (1 + jl) * n3 + k, Cplx<T>{GL * v.x, GL * v.y});
             }
         }
     }
-    __syncthreads();   // every combine has read buf: it now holds the result fields
+    __syncthreads();   // every combine has read buf, every parked loss value is written (block scope)
+    // the result fields [field][plane] into buf: gain from registers, loss back from Y
 #pragma unroll
     for (int i = 0; i < PT; ++i) {
         const int e = t + i * G::T2;
-        if (e >= 2 * G::N2) continue;
-        const int pl = e / G::N2, ky = (e / N) % N, kz = e % N;
-        const int64_t k = ((int64_t)(pl ? kx1 : kx0) * N + ky) * N + kz;
-        const T GL = lscale * loss_multiplier<T>(GL0, GLd, Lr, rho, per_node, np.dlog, Nrho, n3, k);
+        if (e >= npts) continue;
+        const int pl = e >> (2 * LN), ky = (e >> LN) & (N - 1), kz = e & (N - 1);
+        const int64_t k = kidx(e);
         const int o = pl * G::PLANE + ky * G::ROW + kz;
         stc(buf + o, Cplx<T>{gscale * gr[i], gscale * gi[i]});
-        stc(buf + 2 * G::PLANE + o, Cplx<T>{GL * l0[i].x, GL * l0[i].y});
-        if constexpr (NL == 2) stc(buf + 4 * G::PLANE + o, Cplx<T>{GL * l1[i].x, GL * l1[i].y});
+#pragma unroll
+        for (int jl = 0; jl < NL; ++jl) stc(buf + (1 + jl) * npl * G::PLANE + o, ldc(Yn + (1 + jl) * n3 + k));
     }
     __syncthreads();
-    for (int id = t; id < yf * 2 * N; id += G::T2) {   // inverse along y: line (field, plane, kz)
-        const int fo = id / (2 * N), pl = (id / N) % 2, kz = id % N;
-        fftc_smem_line<T, N, false>(buf + (fo * 2 + pl) * G::PLANE + kz, G::ROW);
+    for (int id = t; id < yf * npl * N; id += G::T2) {   // inverse along y: line (field, plane, kz)
+        const int fp = id >> LN, kz = id & (N - 1);     // fp = field npl + plane
+        fftc_smem_line<T, N, false>(buf + fp * G::PLANE + kz, G::ROW);
     }
     __syncthreads();
-    for (int id = t; id < yf * 2 * N; id += G::T2) {   // inverse along z: line (field, plane, y)
-        const int fo = id / (2 * N), pl = (id / N) % 2, yy = id % N;
-        fftc_smem_line<T, N, false>(buf + (fo * 2 + pl) * G::PLANE + yy * G::ROW, 1);
+    for (int id = t; id < yf * npl * N; id += G::T2) {   // inverse along z: line (field, plane, y)
+        const int fp = id >> LN, yy = id & (N - 1);
+        fftc_smem_line<T, N, false>(buf + fp * G::PLANE + yy * G::ROW, 1);
     }
     __syncthreads();
-    Cplx<T>* Yn = Y + node * (int64_t)yf * n3;
-    for (int e = t; e < yf * 2 * G::N2; e += G::T2) {   // Y[field][kx][y][z]
-        const int fo = e / (2 * G::N2), pl = (e / G::N2) % 2, yy = (e / N) % N, z = e % N;
-        stc(Yn + fo * n3 + ((int64_t)(pl ? kx1 : kx0) * N + yy) * N + z,
-            ldc(buf + (fo * 2 + pl) * G::PLANE + yy * G::ROW + z));
+    for (int e = t; e < yf * npl * G::N2; e += G::T2) {   // Y[field][kx][y][z]
+        const int fp = e >> (2 * LN), fo = fp >> sh, pl = fp & sh, yy = (e >> LN) & (N - 1), z = e & (N - 1);
+        stc(Yn + fo * n3 + ((int64_t)(pl ? kx1 : kx0) * N + yy) * N + z, ldc(buf + fp * G::PLANE + yy * G::ROW + z));
     }
 }
 
@@ -535,11 +581,13 @@ cudaError_t spectral_n(const DevTables<T>& t, const T* P, NodeParams np, int64_t
     {
         // the forward transforms are unnormalised (1 / N^3) and the unpacked spectra carry a factor 2
         const T post = T(0.5) / (T(N) * T(N) * T(N));
-        const size_t sm = sizeof(Cplx<T>) * (size_t)G::GS * 2 * G::PLANE + sizeof(double) * (size_t)t.Nrho;
+        constexpr int GSX = G::T2 / N, MR = 2 * (N / 2) * (N / 2) + 1, US = spec_y_table_stride<N>();
+        const size_t sm = sizeof(Cplx<T>) * (size_t)GSX * G::PLANE + (sizeof(T) * (size_t)MR * US + 15) / 16 * 16 +
+                          sizeof(double) * (size_t)t.Nrho;
         auto kern = lb ? k_spec_y<T, N, 2> : k_spec_y<T, N, 1>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        kern<<<dim3(N / 2, nn), G::T2, sm, s>>>(X, xs, t.Uq, 3 * (N / 2) * (N / 2) + 1, t.Lr, t.GL0, t.GLd, t.cr, np,
+        kern<<<dim3(N / 2 + 1, nn), G::T2, sm, s>>>(X, xs, t.Uq, 3 * (N / 2) * (N / 2) + 1, t.Lr, t.GL0, t.GLd, t.cr, np,
                                                 t.Nrho, t.rank, t.rank, lb ? t.rank + 1 : -1, gain_scale * post, post,
                                                 Y, yf);
         e = cudaGetLastError();
