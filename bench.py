@@ -31,8 +31,10 @@ sys.path.insert(0, ROOT)
 METRIC = "Q(f,f) node-evals/s at N=32 VHS, % roofline, mixed-prec vs FP32 at stated err"
 WORKLOAD = "vhs_n32"
 # Tolerances of the relative L2 error against the FP64 oracle, over the sampled nodes as one
-# vector, normalised by ||Q|| and by the loss term ||Q-||.
-TOL_Q = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-2, "bf16s": 5e-2, "f16x3": 1e-5, "bf16x3": 1e-3}
+# vector, normalised by ||Q|| and by the loss term ||Q-||. At this workload F16S is held to the
+# 1e-3 of ||Q|| stated for the split 16-bit forms (the tests allow 1e-2 on rougher inputs); BF16S
+# keeps its own wider tolerance (it does not reach 1e-3).
+TOL_Q = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-3, "bf16s": 5e-2, "f16x3": 1e-5, "bf16x3": 1e-3}
 TOL_L = {"fp64": 1e-10, "fp32": 1e-5, "f16s": 1e-3, "bf16s": 5e-3, "f16x3": 1e-5, "bf16x3": 1e-4}
 MODES = ("fp32", "f16s", "bf16s", "f16x3", "bf16x3")
 DTYPES = {"fp32": "f32", "fp64": "f64", "f16s": "f16 data, f16 hi+lo filters, f32 accumulate",
