@@ -1534,29 +1534,44 @@ dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host
     DGFS_ON_DEVICE(plan->device);
     const size_t es = elem_size(plan->prec);
     const int64_t n3 = (int64_t)plan->hp.N * plan->hp.N * plan->hp.N;
-    // The staging area (2 chunk fields) holds nbuf buffers of S nodes in and S nodes out. Sub-batch i
-    // uses buffer i % nbuf: its host-to-device copy (copy stream 1) overlaps the compute of sub-batch
-    // i - 1 (stream s), and the device-to-host copy of sub-batch i - 1 (copy stream 2) overlaps the
-    // compute of sub-batch i. A buffer is refilled once the compute that read it has finished, and
-    // its output half is rewritten once the copy that read it has finished.
+    // The staging area (2 chunk fields) holds nbuf buffers of up to H nodes in and H nodes out.
+    // Sub-batch i uses buffer i % nbuf: its host-to-device copy (copy stream 1) overlaps the compute of
+    // sub-batch i - 1 (stream s), and the device-to-host copy of sub-batch i - 1 (copy stream 2)
+    // overlaps the compute of sub-batch i. A buffer is refilled once the compute that read it has
+    // finished, and its output half is rewritten once the copy that read it has finished. Only the
+    // first sub-batch's input copy and the last one's output copy are exposed, so those two are short
+    // (B / 16 nodes: their compute still covers the neighbouring copies about forty times over), and
+    // the rest is split into as few sub-batches of at most H nodes as fit (each boundary costs about
+    // half a work item of the persistent translate kernel's tail).
     const int nbuf = plan->chunk >= 2 ? 2 : 1;
-    const int64_t S = std::min<int64_t>(plan->chunk / nbuf, std::max<int64_t>(1, (B + 3) / 4));
+    const int64_t H = plan->chunk / nbuf;
+    const int64_t ramp = std::min<int64_t>(H, std::max<int64_t>(1, (B + 15) / 16));
+    const int64_t mid = B > 2 * ramp ? B - 2 * ramp : 0;
+    const int64_t nmid = (mid + H - 1) / H;
+    std::vector<int64_t> sizes;
+    if (B <= 2 * ramp) {
+        for (int64_t n0 = 0; n0 < B; n0 += ramp) sizes.push_back(std::min<int64_t>(ramp, B - n0));
+    } else {
+        sizes.push_back(ramp);
+        for (int64_t k = 0; k < nmid; ++k) sizes.push_back(mid / nmid + (k < mid % nmid ? 1 : 0));
+        sizes.push_back(ramp);
+    }
     DGFS_CUDA(cudaEventRecord(plan->ev_start, s), "event record");   // earlier work on s that used the plan
     DGFS_CUDA(cudaStreamWaitEvent(plan->cs_h2d, plan->ev_start, 0), "stream wait");
     DGFS_CUDA(cudaStreamWaitEvent(plan->cs_d2h, plan->ev_start, 0), "stream wait");
-    int64_t i = 0;
-    for (int64_t n0 = 0; n0 < B; n0 += S, ++i) {
+    int64_t n0 = 0;
+    for (size_t i = 0; i < sizes.size(); n0 += sizes[i], ++i) {
         const int b = (int)(i % nbuf);
-        unsigned char* fin = ws(plan, plan->off_io) + (size_t)b * 2 * S * n3 * es;
-        unsigned char* qout = fin + (size_t)S * n3 * es;
-        const int64_t nn = std::min<int64_t>(S, B - n0);
+        unsigned char* fin = ws(plan, plan->off_io) + (size_t)b * 2 * H * n3 * es;
+        unsigned char* qout = fin + (size_t)H * n3 * es;
+        const int64_t nn = sizes[i];
         const size_t bytes = (size_t)nn * n3 * es;
-        if (i >= nbuf) DGFS_CUDA(cudaStreamWaitEvent(plan->cs_h2d, plan->ev_comp[b], 0), "stream wait");
+        if ((int)i >= nbuf) DGFS_CUDA(cudaStreamWaitEvent(plan->cs_h2d, plan->ev_comp[b], 0), "stream wait");
         DGFS_CUDA(cudaMemcpyAsync(fin, static_cast<const unsigned char*>(f_host) + (size_t)n0 * n3 * es, bytes,
                                   cudaMemcpyHostToDevice, plan->cs_h2d), "host to device");
         DGFS_CUDA(cudaEventRecord(plan->ev_h2d[b], plan->cs_h2d), "event record");
         DGFS_CUDA(cudaStreamWaitEvent(s, plan->ev_h2d[b], 0), "stream wait");
-        if (i >= nbuf) DGFS_CUDA(cudaStreamWaitEvent(s, plan->ev_d2h[b], 0), "stream wait");
+        if ((int)i >= nbuf) DGFS_CUDA(cudaStreamWaitEvent(s, plan->ev_d2h[b], 0), "stream wait");
         dgfs_status st = plan->prec == DGFS_PREC_FP64
             ? run_chunk<double>(plan, Op::Collide, reinterpret_cast<const double*>(fin), nullptr,
                                 reinterpret_cast<double*>(qout), nullptr,

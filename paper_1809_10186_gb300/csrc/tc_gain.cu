@@ -30,7 +30,9 @@
 // slots, and epilogue warpgroup 1 writes each pass-2 result into the pass-3 operands (both signs'
 // full fields, in shared memory); every ring is two deep, so consecutive tiles overlap. The back
 // (pass 3) starts once every pass-2 tile is stored: pass-3 MMA warp b fills slot b with the tiles
-// u = b (mod 2), and epilogue warpgroup b forms their products (one TMEM lane per thread).
+// u = b (mod 2), and epilogue warpgroup b forms their products (one TMEM lane per thread). While
+// it waits for the pass-3 operands, warpgroup 0 already turns the first two pass-1 tiles of the
+// next step of the item into pass-2 operands (N = 32), so the next front starts two tiles in.
 // Barriers shared by several MMA warps (filter buffer done, final drain, pass-3 operands released)
 // take one commit from each warp that uses the resource. All hand-offs
 // are mbarriers; every lane of the epilogue warps arrives and every wait loop branches on warp
@@ -69,6 +71,10 @@ struct Geo {
     static constexpr int EPI_WARPS = 8;           // epilogue warpgroups 0 and 1 (warp / 4)
     static constexpr int THREADS = 32 * EPI_WARPS + 128;   // + a warpgroup holding the MMA warp
     static constexpr int ISSUER = EPI_WARPS;      // first MMA warp (pass 1); then pass 2, pass 3 of slots 0, 1
+    // pass-1 tiles of the next step that warpgroup 0 turns into pass-2 operands while it waits for
+    // the pass-3 operands of the current one (at most the two operand buffers; none when a step
+    // has only two tiles)
+    static constexpr int LOOKAHEAD = T >= 4 ? 2 : 0;
     // registers per thread: 168 at launch (65536 / 384, rounded down to a multiple of 8), then
     // 216 for the epilogue warpgroups and 72 for the third: 256 * 216 + 128 * 72 = 384 * 168
     static constexpr uint32_t REG_LAUNCH = 168, REG_EPI = 216, REG_MMA = 72;
@@ -237,9 +243,11 @@ __device__ __forceinline__ void mma_p1_loop(Bars& bars, unsigned char* smem, uin
                 }
                 tc::mma_commit_warp(&bars.full1[b]);
                 // the other filter buffer (step g - 1, whose MMAs are complete by now) takes step g + 1;
-                // the set-up copied steps 0 and 1, unless step 1 belongs to the next item (one-step items)
+                // the set-up copied steps 0 and 1, unless step 1 belongs to the next item (one-step items).
+                // With the epilogue's look-ahead the wait comes after tile 1: step g - 1 completes only
+                // after warpgroup 0 has turned tiles 0 and 1 of step g into pass-2 operands.
                 const unsigned char* src = s + 1 < it.nseq ? fcur + (size_t)(s + 1) * G::F_BLOCK : fnxt;
-                if (t == 0 && (g >= 1 || it.nseq == 1) && src) {
+                if (t == (G::LOOKAHEAD ? 1 : 0) && (g >= 1 || it.nseq == 1) && src) {
                     const int nb = (int)((g + 1) & 1);
                     if (g >= 1) {   // buffer nb held step g - 1
                         DGFS_WAITW(&bars.fdone[nb], (ph_fdone >> nb) & 1u);
@@ -567,12 +575,18 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
           }
           tc::tc_fence_before();
           tc::mbar_arrive(&bars.f_ready);
+          int ahead = 0;   // pass-1 tiles of the current step that warpgroup 0 handled during the last back
           for (int rr = 0; rr < it.rpc; ++rr) {
           for (int pp = 0; pp < npairs; ++pp, ++g) {
             if (w == 0) {
-                for (int t = 0; t < G::T; ++t) {   // pass-1 tile t (slot t % 2) -> pass-2 operands (buffer t % 2)
+                // the step's remaining tiles, then, when the next step belongs to this item, its first
+                // LOOKAHEAD tiles (virtual tiles T, T + 1): their pass-1 MMAs and operand buffers do not
+                // depend on this step's pass 3, so warpgroup 0 fills the wait for the pass-3 operands
+                // with them (a third would wait for the next step's pass 2, i.e. for this step's back)
+                const int tend = G::T + ((pp + 1 < npairs || rr + 1 < it.rpc) ? G::LOOKAHEAD : 0);
+                for (int t = ahead; t < tend; ++t) {   // pass-1 tile t (slot t % 2) -> pass-2 operands (buffer t % 2)
                     const int b = t & 1;
-                    if (g > 0 || t >= 2) {   // pass 2 of tile t - 2 has read buffer b
+                    if (g > 0 || t >= 2) {   // pass 2 of tile t - 2 (of this or the previous step) has read buffer b
                         DGFS_WAITE(&bars.a2_free[b], (ph_a2free >> b) & 1u);
                         ph_a2free ^= 1u << b;
                     }
@@ -601,6 +615,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                     tc::fence_proxy_async();
                     tc::mbar_arrive(&bars.a2_full[b]);
                 }
+                ahead = tend - G::T;
             } else {
                 for (int t = 0; t < G::T; ++t) {   // pass-2 tile t (slot t % 2) -> rows of the pass-3 operands
                     const int b = t & 1, y = t * G::ZT + yl;
