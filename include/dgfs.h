@@ -231,10 +231,11 @@ dgfs_status dgfs_host_dg_stiffness(int K, double* S, double* Minv);
 /* dgfs_collide with HOST buffers: copies f to the device, computes, copies Q back and
    synchronises before returning. f_host/Q_host may be pageable or pinned (pinned lets the
    copies overlap the compute). The batch is split into sub-batches that fit the plan's staging
-   buffers (at most half the plan's chunk each): a short first and last one (B / 16 nodes), whose
-   copies are the only ones not hidden, and as few as fit in between. The copies run on two copy
-   streams owned by the plan, so the host-to-device copy of one sub-batch and the device-to-host
-   copy of the previous one overlap the compute on `stream`. */
+   buffers (at most half the plan's chunk each): their sizes ramp up from B / 32 nodes by a factor
+   of 4 and down again at the end (only the first input copy and the last output copy are not
+   hidden), with as few as fit in between. The copies run on two copy streams owned by the plan,
+   so the host-to-device copy of one sub-batch and the device-to-host copy of the previous one
+   overlap the compute on `stream`. */
 dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host, int64_t B,
                               void* stream);
 

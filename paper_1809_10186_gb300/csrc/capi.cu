@@ -1539,23 +1539,25 @@ dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host
     // sub-batch i - 1 (stream s), and the device-to-host copy of sub-batch i - 1 (copy stream 2)
     // overlaps the compute of sub-batch i. A buffer is refilled once the compute that read it has
     // finished, and its output half is rewritten once the copy that read it has finished. Only the
-    // first sub-batch's input copy and the last one's output copy are exposed, so those two are short
-    // (B / 16 nodes: their compute still covers the neighbouring copies about forty times over), and
-    // the rest is split into as few sub-batches of at most H nodes as fit (each boundary costs about
-    // half a work item of the persistent translate kernel's tail).
+    // first sub-batch's input copy and the last one's output copy are exposed, so the sizes ramp up
+    // from B / 32 nodes by a factor of 4 and down again at the end: each copy then hides behind a
+    // compute about ten times longer even when host copies run an order of magnitude below their
+    // usual 200 GB/s (the compute takes ~25 us per node at N = 32, a copy ~0.65 us); the middle is
+    // split into as few sub-batches of at most H nodes as fit (each boundary costs about half a work
+    // item of the persistent translate kernel's tail).
     const int nbuf = plan->chunk >= 2 ? 2 : 1;
     const int64_t H = plan->chunk / nbuf;
-    const int64_t ramp = std::min<int64_t>(H, std::max<int64_t>(1, (B + 15) / 16));
-    const int64_t mid = B > 2 * ramp ? B - 2 * ramp : 0;
-    const int64_t nmid = (mid + H - 1) / H;
-    std::vector<int64_t> sizes;
-    if (B <= 2 * ramp) {
-        for (int64_t n0 = 0; n0 < B; n0 += ramp) sizes.push_back(std::min<int64_t>(ramp, B - n0));
-    } else {
-        sizes.push_back(ramp);
-        for (int64_t k = 0; k < nmid; ++k) sizes.push_back(mid / nmid + (k < mid % nmid ? 1 : 0));
-        sizes.push_back(ramp);
+    std::vector<int64_t> front;
+    int64_t ramp_sum = 0;
+    for (int64_t r = std::max<int64_t>(1, (B + 31) / 32); r < H && 2 * (ramp_sum + r) <= B; r *= 4) {
+        front.push_back(r);
+        ramp_sum += r;
     }
+    const int64_t mid = B - 2 * ramp_sum;
+    const int64_t nmid = (mid + H - 1) / H;
+    std::vector<int64_t> sizes(front);
+    for (int64_t k = 0; k < nmid; ++k) sizes.push_back(mid / nmid + (k < mid % nmid ? 1 : 0));
+    sizes.insert(sizes.end(), front.rbegin(), front.rend());
     DGFS_CUDA(cudaEventRecord(plan->ev_start, s), "event record");   // earlier work on s that used the plan
     DGFS_CUDA(cudaStreamWaitEvent(plan->cs_h2d, plan->ev_start, 0), "stream wait");
     DGFS_CUDA(cudaStreamWaitEvent(plan->cs_d2h, plan->ev_start, 0), "stream wait");

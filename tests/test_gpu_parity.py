@@ -489,8 +489,8 @@ def test_chunking_batch_order_and_determinism():
                                                 (4, 37, True), (64, 300, True), (0, 2, True)])
 def test_host_buffer_entry_point_matches_device(max_batch, B, pinned):
     """The host-buffer call pipelines its copies over sub-batches (one staging buffer when the
-    plan's chunk is one node, two otherwise; short first and last sub-batches, the middle ones
-    up to half the chunk); every node's result equals the device call's, on two consecutive
+    plan's chunk is one node, two otherwise; sizes ramping up from B / 32 and down at the end,
+    the middle ones up to half the chunk); every node's result equals the device call's, on two consecutive
     calls (the second reuses the staging buffers while the first's are fresh)."""
     N, L = 16, 5.0
     plan = binding.Plan(N=N, L=L, gamma=0.38, M=12, N_rho=N, precision="fp32", max_batch=max_batch)
