@@ -304,6 +304,11 @@ def test_slab_n24_fp32_all_nodes():
 N32_NODES = 24   # nodes of the 2048-node launch checked against the oracle
 
 
+# the primary workload's stated tolerance of the split 16-bit forms (1e-3 relative, by ||Q||), which
+# F16S meets there although coarse grids need its general 1e-2
+PRIMARY_TOL_Q = {"f16s": 1e-3}
+
+
 def _vhs32(cfg_name, prec, nodes_checked=N32_NODES):
     """The whole 2048-node launch on the device; batch errors on `nodes_checked` sampled nodes."""
     cfg = W.CONFIGS[cfg_name]
@@ -317,7 +322,8 @@ def _vhs32(cfg_name, prec, nodes_checked=N32_NODES):
     idx = sample_nodes(B, nodes_checked)
     refs = references("Q", cfg_name, idx, plan.info["svd_rank_used"] if cfg.get("svd_tol") else 0)
     e = _check(prec, [q[i] for i in idx], [refs[i]["Q"] for i in idx], [refs[i]["loss"] for i in idx],
-               "N=32 %d-node launch, %d nodes checked (rank %d)" % (B, len(idx), plan.info["svd_rank_used"]))
+               "N=32 %d-node launch, %d nodes checked (rank %d)" % (B, len(idx), plan.info["svd_rank_used"]),
+               tol_q=PRIMARY_TOL_Q.get(prec) if cfg_name == "vhs_n32" else None)
     return e, plan
 
 
