@@ -600,9 +600,9 @@ def run_grad(a):
 
 def run_ragged(a):
     """The ragged cavity mesh: 9216 near-equilibrium nodes, N in {16, 24, 32} (40/40/20 %), per-node
-    VHS omega in {0.5, 0.74, 0.81}, M = 26; one plan per N (the --prec mode where the tensor cores
-    support the grid: every N for F16S / BF16S, N = 24 on the 32-point tiles; FP32 otherwise), all
-    classes in one dgfs_ragged schedule captured as one CUDA graph and replayed."""
+    VHS omega in {0.5, 0.74, 0.81}, M = 26; one plan per N in the --prec mode (every tensor-core
+    precision takes N = 24 on the 32-point tiles), all classes in one dgfs_ragged schedule captured
+    as one CUDA graph and replayed."""
     import numpy as np
     import torch
     from paper_1809_10186_gb300 import binding, workloads as W
@@ -620,7 +620,7 @@ def run_ragged(a):
             packed[offs[i]:offs[i] + n ** 3] = fields[j].ravel()
     gam = 2.0 * (1.0 - node_omega)
     bb = 1.0 / (2.0 ** (3.0 - node_omega) * np.array([math.gamma(2.5 - w) for w in node_omega]) * math.pi)
-    precs = {n: (a.prec if (a.prec in ("fp32", "f16s", "bf16s") or n in (16, 32)) else "fp32") for n in Ns}
+    precs = {n: a.prec for n in Ns}
     plans = [binding.Plan(N=n, L=L, M=M, N_rho=n, precision=precs[n]) for n in Ns]
     cls = [list(Ns).index(int(n)) for n in node_N]
     sched = binding.RaggedSchedule(plans, cls, offs, node_gamma=gam, node_b=bb)

@@ -78,7 +78,8 @@ typedef enum {
                              products per contraction (hi hi, hi lo, lo hi), FP32 accumulation, so
                              the translates carry about FP32 accuracy (8e-6 of ||Q||, 4e-7 of ||Q-||,
                              as FP32); the two CTAs of a thread-block cluster share the field of one
-                             (node, radial points) item. FP32 elsewhere. N = 16, 32                  */
+                             (node, radial points) item. FP32 elsewhere. N = 16, 32, and 24 on the
+                             32-point tiles as for F16S                                              */
     DGFS_PREC_BF16X3 = 5  /* as F16X3 with bf16 hi and lo parts (lo times 2^8), 16 significand
                              bits: about 2e-5 of ||Q||, within 1e-3 of ||Q|| at every node          */
 } dgfs_precision;
@@ -94,7 +95,7 @@ typedef enum {
 
 typedef struct {
     int N;                     /* grid points per velocity axis: 8, 12, 16, 24 or 32 (tensor-core
-                                  precisions: 16 or 32; F16S and BF16S also 24)               */
+                                  precisions: 16, 24 or 32; 24 on the 32-point tiles)         */
     double L;                  /* velocity domain [-L, L]^3 (Sec. 3.3), L > 0                   */
     double R;                  /* ball radius of the c_r integral; <= 0: 4L/(3+sqrt 2) (Appendix) */
     double gamma;              /* VHS exponent 2(1 - omega) of |c - c_*| (eq. B_gen)            */

@@ -795,7 +795,10 @@ double bf16_bits_value(uint16_t b) {
 
 }  // namespace
 
-bool tc_supported(int N, int prec) { return N == 16 || N == 32 || (N == 24 && !tc3_precision(prec)); }
+bool tc_supported(int N, int prec) {
+    (void)prec;
+    return N == 16 || N == 32 || N == 24;
+}
 
 int tc_resolve_rpc(const TcTables& t, int prec, int64_t nodes, int sms) {
     if (t.rpc > 0 && t.Nrho % t.rpc == 0) return t.rpc;

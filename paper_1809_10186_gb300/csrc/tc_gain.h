@@ -24,7 +24,7 @@ struct TcTables {
 // the GPU's `sms` SMs at least 16 times over.
 int tc_resolve_rpc(const TcTables& t, int prec, int64_t nodes, int sms);
 
-// N = 16, 32; N = 24 on the 32-point tiles for F16S / BF16S (zero-padded filters and data).
+// N = 16, 32; N = 24 on the 32-point tiles (zero-padded filters and data), every tensor-core precision.
 bool tc_supported(int N, int prec);
 int tc_extra_launches(int prec);   // launches the tensor-core path adds per chunk (beyond one)
 size_t build_tc_tables(const HostPlan& hp, int prec, std::vector<unsigned char>& blob, TcTables& t);

@@ -54,7 +54,7 @@ constexpr int kLoShiftBF16 = 8;
 
 template <int N>
 struct Geo3 {
-    static_assert(N == 16 || N == 32, "split-data tensor-core translates support N = 16 and 32");
+    static_assert(N == 16 || N == 32, "split-data tensor-core tiles of N = 16 and 32 (N = 24 runs on 32)");
     static constexpr int N2 = N * N;
     static constexpr int T = N2 / 128;            // 128-row tiles of one field
     static constexpr int TH = T / 2;              // front (y) tiles and back (x') tiles of one CTA
@@ -294,10 +294,13 @@ __device__ __forceinline__ void mma3_p3_loop(Bars3& bars, uint32_t sb, uint32_t 
 #undef DGFS_WAITW
 #undef DGFS_WAITWC
 
-template <int N, bool BF>
+// PAD: f and P_r on an nsrc^3 grid, nsrc < N (N = 24 on the 32-point tiles: the filters are zero
+// outside the nsrc x nsrc block, f is read with zeros outside it and only the nsrc^3 block of P_r is
+// written).
+template <int N, bool BF, bool PAD>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo3<N>::THREADS, 1)
 k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const unsigned char* __restrict__ filt,
-           int npairs, int Nrho, int rpc, float* __restrict__ P, int* __restrict__ flags, int fault,
+           int npairs, int Nrho, int rpc, int nsrc, float* __restrict__ P, int* __restrict__ flags, int fault,
            const float* __restrict__ coef, int accum) {
     using G = Geo3<N>;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -313,7 +316,8 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
     const int r0 = (blockIdx.x >> 1) * rpc, nseq = npairs * rpc;
     const int64_t node = blockIdx.y;
     constexpr int64_t n3 = (int64_t)N * N * N;
-    const float* fb = f + (offs ? offs[node] : node * n3);
+    const int64_t n3s = PAD ? (int64_t)nsrc * nsrc * nsrc : n3;
+    const float* fb = f + (offs ? offs[node] : node * n3s);
     const uint32_t sb = tc::smem_u32(smem);
     const unsigned char* fglob = filt + (size_t)r0 * npairs * G::F_BLOCK;
 
@@ -354,8 +358,15 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
         float m8[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) m8[j] = 0.f;
+        if constexpr (!PAD) {
 #pragma unroll
-        for (int i = 0; i < PER; ++i) m8[i & 7] = fmaxf(m8[i & 7], fabsf(__ldg(fb + tid + i * STRIDE)));
+            for (int i = 0; i < PER; ++i) m8[i & 7] = fmaxf(m8[i & 7], fabsf(__ldg(fb + tid + i * STRIDE)));
+        } else {
+            for (int64_t i0 = tid; i0 < n3s; i0 += 8 * STRIDE)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (i0 + j * STRIDE < n3s) m8[j] = fmaxf(m8[j], fabsf(__ldg(fb + i0 + j * STRIDE)));
+        }
         float mx = fmaxf(fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3])), fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7])));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -383,12 +394,25 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
 #pragma unroll 1
         for (int i = w; i < G::TH; i += 2) {
             const int t = (int)crank * G::TH + i;
-            const float* src = fb + (size_t)(t * G::ZT + yl) * N + z;
             uint32_t hi[N / 2], lo[N / 2];
+            if constexpr (!PAD) {
+                const float* src = fb + (size_t)(t * G::ZT + yl) * N + z;
 #pragma unroll
-            for (int c = 0; c < N / 2; ++c)
-                split2<BF>(__ldg(src + (size_t)(2 * c) * G::N2) * sf, __ldg(src + (size_t)(2 * c + 1) * G::N2) * sf,
-                           hi[c], lo[c]);
+                for (int c = 0; c < N / 2; ++c)
+                    split2<BF>(__ldg(src + (size_t)(2 * c) * G::N2) * sf, __ldg(src + (size_t)(2 * c + 1) * G::N2) * sf,
+                               hi[c], lo[c]);
+            } else {   // zeros outside the nsrc^3 block
+                const int y = t * G::ZT + yl;
+                const bool in = y < nsrc && z < nsrc;
+                const float* src = fb + ((size_t)y * nsrc + z);
+                const size_t sx = (size_t)nsrc * nsrc;
+#pragma unroll
+                for (int c = 0; c < N / 2; ++c) {
+                    const float a = in && 2 * c < nsrc ? __ldg(src + (size_t)(2 * c) * sx) * sf : 0.f;
+                    const float b = in && 2 * c + 1 < nsrc ? __ldg(src + (size_t)(2 * c + 1) * sx) * sf : 0.f;
+                    split2<BF>(a, b, hi[c], lo[c]);
+                }
+            }
             const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
             if constexpr (N == 32) {
                 tc::tmem_st16(lanebase + G::C_FH + i * (N / 2), hi);
@@ -555,18 +579,28 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
           }
           // radial point r0 + rr done: P_r of this warpgroup's back tiles out, sums cleared
           if (!*abort) {
-              float* dst = P + ((size_t)node * Nrho + r0 + rr) * n3;
+              float* dst = P + ((size_t)node * Nrho + r0 + rr) * n3s;
               const float sc = out_scale * (coef ? coef[node] : 1.f);   // per-node factor (polarisation)
 #pragma unroll
               for (int n = 0; n < NB; ++n) {
                   const int k = w + 2 * n;
                   if (k >= G::TH) break;
                   const int m3 = ((int)crank * G::TH + k) * 128 + l, xp = m3 / N, zp = m3 % N;
-                  float* o = dst + (size_t)xp * G::N2 + zp;
+                  if constexpr (!PAD) {
+                      float* o = dst + (size_t)xp * G::N2 + zp;
 #pragma unroll
-                  for (int j = 0; j < N; ++j) {
-                      if (accum) o[(size_t)j * N] += acc[n][j] * sc;
-                      else o[(size_t)j * N] = acc[n][j] * sc;
+                      for (int j = 0; j < N; ++j) {
+                          if (accum) o[(size_t)j * N] += acc[n][j] * sc;
+                          else o[(size_t)j * N] = acc[n][j] * sc;
+                      }
+                  } else if (xp < nsrc && zp < nsrc) {   // the nsrc^3 block only
+                      float* o = dst + (size_t)xp * nsrc * nsrc + zp;
+#pragma unroll
+                      for (int j = 0; j < N; ++j) {
+                          if (j >= nsrc) continue;
+                          if (accum) o[(size_t)j * nsrc] += acc[n][j] * sc;
+                          else o[(size_t)j * nsrc] = acc[n][j] * sc;
+                      }
                   }
               }
           }
@@ -610,10 +644,11 @@ template <int N, bool BF>
 cudaError_t launch3_n(const TcTables& t, const float* f, const int64_t* offs, int64_t nodes, float* P, int* flags,
                       cudaStream_t s, int fault, const float* coef, int accum) {
     using G = Geo3<N>;
-    auto kern = k_tc3_gain<N, BF>;
+    const int nsrc = t.nsrc > 0 ? t.nsrc : N;
+    auto kern = nsrc == N ? k_tc3_gain<N, BF, false> : k_tc3_gain<N, BF, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::S_TOTAL);
     if (e != cudaSuccess) return e;
-    const int64_t n3 = (int64_t)N * N * N;
+    const int64_t n3 = (int64_t)nsrc * nsrc * nsrc;   // f and P_r grid
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -623,7 +658,7 @@ cudaError_t launch3_n(const TcTables& t, const float* f, const int64_t* offs, in
         const int64_t nn = nodes - n0 < 65535 ? nodes - n0 : 65535;
         kern<<<dim3(2 * (t.Nrho / rpc), (unsigned)nn), G::THREADS, G::S_TOTAL, s>>>(
             f + (offs ? 0 : n0 * n3), offs ? offs + n0 : nullptr, static_cast<const unsigned char*>(t.mats),
-            t.npairs, t.Nrho, rpc, P + n0 * t.Nrho * n3, flags, n0 == 0 ? fault : 0, coef ? coef + n0 : nullptr,
+            t.npairs, t.Nrho, rpc, nsrc, P + n0 * t.Nrho * n3, flags, n0 == 0 ? fault : 0, coef ? coef + n0 : nullptr,
             accum);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -659,7 +694,9 @@ double bf16_value(uint16_t b) {
 bool tc3_precision(int prec) { return prec == DGFS_PREC_F16X3 || prec == DGFS_PREC_BF16X3; }
 
 size_t build_tc3_tables(const HostPlan& hp, int prec, std::vector<unsigned char>& blob, TcTables& t) {
-    const int N = hp.N, np = hp.npairs, Nr = hp.Nrho;
+    // N = 24 runs on the 32-point tiles: each 24-point circulant sits in the top-left block of a
+    // zero 32 x 32 matrix, so the padded passes give the 24-point translates of the zero-padded field
+    const int Nd = hp.N, N = Nd == 24 ? 32 : Nd, np = hp.npairs, Nr = hp.Nrho;
     const bool bf = prec == DGFS_PREC_BF16X3;
     const double ls = std::ldexp(1.0, bf ? kLoShiftBF16 : kLoShiftF16);
     const size_t sbytes = (size_t)2 * N * N * 2, block = 6 * sbytes;
@@ -673,9 +710,10 @@ size_t build_tc3_tables(const HostPlan& hp, int prec, std::vector<unsigned char>
             unsigned char* blk = blob.data() + ((size_t)r * np + p) * block;
             // F_+[i][j] = a[(i - j) mod N] (translate by +s along the axis); F_- = F_+^T (T_-s = T_s^T)
             auto F = [&](int axis, int sign, int i, int j) {
-                const double* fl = &hp.filt[(((size_t)r * np + p) * 3 + axis) * N];
+                if (i >= Nd || j >= Nd) return 0.0;
+                const double* fl = &hp.filt[(((size_t)r * np + p) * 3 + axis) * Nd];
                 const int d = sign == 0 ? i - j : j - i;
-                return fl[((d % N) + N) % N];
+                return fl[((d % Nd) + Nd) % Nd];
             };
             const double w2 = 2.0 * hp.wsig[p];
             for (int sign = 0; sign < 2; ++sign)
@@ -701,6 +739,7 @@ size_t build_tc3_tables(const HostPlan& hp, int prec, std::vector<unsigned char>
                     }
         }
     t.N = N;
+    t.nsrc = Nd;
     t.Nrho = Nr;
     t.npairs = np;
     t.mats = reinterpret_cast<const void*>((uintptr_t)0);
