@@ -149,6 +149,16 @@ struct Bars {
     uint64_t drain;
 };
 
+// Two FP32 FMAs in one instruction, each rounded as fmaf: d = a * b + c elementwise.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
+          "l"(*reinterpret_cast<unsigned long long*>(&c)));
+    return *reinterpret_cast<float2*>(&d);
+}
+
 template <bool BF>
 __device__ __forceinline__ void pack8(const float (&v)[8], uint32_t (&u)[4]) {
 #pragma unroll
@@ -479,12 +489,14 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
         const uint32_t a2_row = sb + G::S_A2 + ((uint32_t)(yl * N) >> 3) * G::A2_SBO + (lz >> 3) * G::A2_LBO + (lz & 7) * 16;
         const int mg3 = (lz * N) >> 3;
         uint32_t ph_f = 0, ph_a2free = 0, ph_a3free = 0, ph_f3 = 0;   // phase bits (bit b = ring slot b)
-        const float eps = exp2f(-(float)(BF ? kLoShiftBF16 : kLoShiftF16));
-        float acc[G::TW][N];
+        float2 acc[G::TW][N / 2];   // P_r of the warpgroup's pass-3 tiles: (y' = 2j, 2j + 1) per entry
 #pragma unroll
         for (int k = 0; k < G::TW; ++k)
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[k][j] = 0.f;
+            for (int j = 0; j < N / 2; ++j) acc[k][j] = make_float2(0.f, 0.f);
+        // 2^-e, the weight of the lo parts of passes 2 and 3, as a pair for the packed FMAs
+        const float2 eps2 = make_float2(exp2f(-(float)(BF ? kLoShiftBF16 : kLoShiftF16)),
+                                        exp2f(-(float)(BF ? kLoShiftBF16 : kLoShiftF16)));
 #define DGFS_WAITE(bar, ph)                                             \
     do {                                                                \
         if (!tc::warp_wait((bar), (ph), abort)) goto epi_done;          \
@@ -643,11 +655,13 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                         }
 #pragma unroll
                         for (int c = 0; c < N / 8; ++c) {   // 8 columns z' = 8c .. 8c + 7
-                            float v[8];
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) v[j] = fmaf(lo[8 * c + j], eps, hi[8 * c + j]);
                             uint32_t u[4];
-                            pack8<BF>(v, u);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {   // hi + 2^-e lo, two columns per packed FMA
+                                const float2 v = ffma2(make_float2(lo[8 * c + 2 * j], lo[8 * c + 2 * j + 1]), eps2,
+                                                       make_float2(hi[8 * c + 2 * j], hi[8 * c + 2 * j + 1]));
+                                u[j] = pack2<BF>(v.x, v.y);
+                            }
                             const int mg = mg3 + c;
                             tc::st_shared_v4(sb + G::S_A3 + gs * G::A3_BYTES + (mg >> 4) * G::A3_TS + (mg & 15) * G::A3_SBO + ky,
                                              u[0], u[1], u[2], u[3]);
@@ -679,8 +693,13 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                         if (k == G::TW - 1) tc::mbar_arrive(&bars.free3x[w]);
                     }
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        acc[k][16 * c + j] = fmaf(fmaf(lp[j], eps, hp[j]), fmaf(lm[j], eps, hm[j]), acc[k][16 * c + j]);
+                    for (int j = 0; j < 8; ++j) {   // two y' per packed FMA, the same roundings as fmaf
+                        const float2 xp = ffma2(make_float2(lp[2 * j], lp[2 * j + 1]), eps2,
+                                                make_float2(hp[2 * j], hp[2 * j + 1]));
+                        const float2 xm = ffma2(make_float2(lm[2 * j], lm[2 * j + 1]), eps2,
+                                                make_float2(hm[2 * j], hm[2 * j + 1]));
+                        acc[k][8 * c + j] = ffma2(xp, xm, acc[k][8 * c + j]);
+                    }
                 }
             }
           }
@@ -695,16 +714,18 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                       float* o = dst + (size_t)xp * G::N2 + zp;
 #pragma unroll
                       for (int j = 0; j < N; ++j) {
-                          if (accum) o[(size_t)j * N] += acc[k][j] * sc;
-                          else o[(size_t)j * N] = acc[k][j] * sc;
+                          const float a = (j & 1) ? acc[k][j / 2].y : acc[k][j / 2].x;
+                          if (accum) o[(size_t)j * N] += a * sc;
+                          else o[(size_t)j * N] = a * sc;
                       }
                   } else if (xp < nsrc && zp < nsrc) {   // the nsrc^3 block only
                       float* o = dst + (size_t)xp * nsrc * nsrc + zp;
 #pragma unroll
                       for (int j = 0; j < N; ++j) {
                           if (j >= nsrc) continue;
-                          if (accum) o[(size_t)j * nsrc] += acc[k][j] * sc;
-                          else o[(size_t)j * nsrc] = acc[k][j] * sc;
+                          const float a = (j & 1) ? acc[k][j / 2].y : acc[k][j / 2].x;
+                          if (accum) o[(size_t)j * nsrc] += a * sc;
+                          else o[(size_t)j * nsrc] = a * sc;
                       }
                   }
               }
@@ -712,7 +733,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
 #pragma unroll
           for (int k = 0; k < G::TW; ++k)
 #pragma unroll
-              for (int j = 0; j < N; ++j) acc[k][j] = 0.f;
+              for (int j = 0; j < N / 2; ++j) acc[k][j] = make_float2(0.f, 0.f);
           }
         }
 #undef DGFS_WAITE
