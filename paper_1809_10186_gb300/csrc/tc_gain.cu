@@ -149,16 +149,6 @@ struct Bars {
     uint64_t drain;
 };
 
-// Two FP32 FMAs in one instruction, each rounded as fmaf: d = a * b + c elementwise.
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;"
-        : "=l"(d)
-        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
-          "l"(*reinterpret_cast<unsigned long long*>(&c)));
-    return *reinterpret_cast<float2*>(&d);
-}
-
 template <bool BF>
 __device__ __forceinline__ void pack8(const float (&v)[8], uint32_t (&u)[4]) {
 #pragma unroll
@@ -658,7 +648,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                             uint32_t u[4];
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {   // hi + 2^-e lo, two columns per packed FMA
-                                const float2 v = ffma2(make_float2(lo[8 * c + 2 * j], lo[8 * c + 2 * j + 1]), eps2,
+                                const float2 v = tc::ffma2(make_float2(lo[8 * c + 2 * j], lo[8 * c + 2 * j + 1]), eps2,
                                                        make_float2(hi[8 * c + 2 * j], hi[8 * c + 2 * j + 1]));
                                 u[j] = pack2<BF>(v.x, v.y);
                             }
@@ -694,11 +684,11 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                     }
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {   // two y' per packed FMA, the same roundings as fmaf
-                        const float2 xp = ffma2(make_float2(lp[2 * j], lp[2 * j + 1]), eps2,
+                        const float2 xp = tc::ffma2(make_float2(lp[2 * j], lp[2 * j + 1]), eps2,
                                                 make_float2(hp[2 * j], hp[2 * j + 1]));
-                        const float2 xm = ffma2(make_float2(lm[2 * j], lm[2 * j + 1]), eps2,
+                        const float2 xm = tc::ffma2(make_float2(lm[2 * j], lm[2 * j + 1]), eps2,
                                                 make_float2(hm[2 * j], hm[2 * j + 1]));
-                        acc[k][8 * c + j] = ffma2(xp, xm, acc[k][8 * c + j]);
+                        acc[k][8 * c + j] = tc::ffma2(xp, xm, acc[k][8 * c + j]);
                     }
                 }
             }

@@ -385,7 +385,9 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
         for (int i = 1; i < G::EPI_WARPS; ++i) mx = fmaxf(mx, s_red[i]);
         if (mx > 0.f && isfinite(mx)) sf = exp2f(fminf(60.f, fmaxf(-60.f, floorf(log2f(2.f / mx)))));
     }
-    const float eps = exp2f(-(float)(BF ? kLoShiftBF16 : kLoShiftF16));
+    // 2^-e, the weight of the lo parts, as a pair for the packed FMAs
+    const float2 eps2 = make_float2(exp2f(-(float)(BF ? kLoShiftBF16 : kLoShiftF16)),
+                                    exp2f(-(float)(BF ? kLoShiftBF16 : kLoShiftF16)));
     const float out_scale = 1.f / (sf * sf);
 
     // ---- f -> TMEM (f_hi, f_lo) for the front tiles i: y-tile t = crank TH + i, lane l = yl N + z --
@@ -456,11 +458,11 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
         uint32_t ph_f1 = 0, ph_a2free = 0, ph_a3free = 0, ph_f2 = 0, ph_f3 = 0;   // ph_f2: bit per slot
         int p1uses = 0;
         constexpr int NB = (G::TH + 1) / 2;   // back tiles of one warpgroup
-        float acc[NB][N];
+        float2 acc[NB][N / 2];   // P_r of the warpgroup's back tiles: (y' = 2j, 2j + 1) per entry
 #pragma unroll
         for (int k = 0; k < NB; ++k)
 #pragma unroll
-            for (int j = 0; j < N; ++j) acc[k][j] = 0.f;
+            for (int j = 0; j < N / 2; ++j) acc[k][j] = make_float2(0.f, 0.f);
 #define DGFS_WAITE(bar, ph)                                             \
     do {                                                                \
         if (!tc::warp_wait((bar), (ph), abort)) goto epi_done;          \
@@ -497,8 +499,11 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
                         uint32_t uh[4], ulo[4];
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
-                            split2<BF>(fmaf(lv[8 * c + 2 * j], eps, hv[8 * c + 2 * j]),
-                                       fmaf(lv[8 * c + 2 * j + 1], eps, hv[8 * c + 2 * j + 1]), uh[j], ulo[j]);
+                        {
+                            const float2 v = tc::ffma2(make_float2(lv[8 * c + 2 * j], lv[8 * c + 2 * j + 1]), eps2,
+                                                       make_float2(hv[8 * c + 2 * j], hv[8 * c + 2 * j + 1]));
+                            split2<BF>(v.x, v.y, uh[j], ulo[j]);
+                        }
                         tc::st_shared_v4(a2_row + c * G::A2_SBO, uh[0], uh[1], uh[2], uh[3]);
                         tc::st_shared_v4(a2_row + G::A2_BYTES + c * G::A2_SBO, ulo[0], ulo[1], ulo[2], ulo[3]);
                     }
@@ -532,8 +537,11 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
                             uint32_t uh[4], ulo[4];
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
-                                split2<BF>(fmaf(lv[8 * h + 2 * j], eps, hv[8 * h + 2 * j]),
-                                           fmaf(lv[8 * h + 2 * j + 1], eps, hv[8 * h + 2 * j + 1]), uh[j], ulo[j]);
+                            {
+                                const float2 v = tc::ffma2(make_float2(lv[8 * h + 2 * j], lv[8 * h + 2 * j + 1]), eps2,
+                                                           make_float2(hv[8 * h + 2 * j], hv[8 * h + 2 * j + 1]));
+                                split2<BF>(v.x, v.y, uh[j], ulo[j]);
+                            }
                             const uint32_t o = a3_dst + (rg0 + 2 * cc + h) * G::A3_SBO + ky;
                             tc::st_cluster_v4(o, uh[0], uh[1], uh[2], uh[3]);
                             tc::st_cluster_v4(o + G::A3_BYTES, ulo[0], ulo[1], ulo[2], ulo[3]);
@@ -572,8 +580,13 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
                         if (k + 2 >= G::TH) tc::mbar_arrive(&bars.free3x[w]);
                     }
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        acc[n][16 * c + j] = fmaf(fmaf(lp[j], eps, hp[j]), fmaf(lm[j], eps, hm[j]), acc[n][16 * c + j]);
+                    for (int j = 0; j < 8; ++j) {   // two y' per packed FMA, the same roundings as fmaf
+                        const float2 xp = tc::ffma2(make_float2(lp[2 * j], lp[2 * j + 1]), eps2,
+                                                    make_float2(hp[2 * j], hp[2 * j + 1]));
+                        const float2 xm = tc::ffma2(make_float2(lm[2 * j], lm[2 * j + 1]), eps2,
+                                                    make_float2(hm[2 * j], hm[2 * j + 1]));
+                        acc[n][8 * c + j] = tc::ffma2(xp, xm, acc[n][8 * c + j]);
+                    }
                 }
             }
           }
@@ -590,16 +603,18 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
                       float* o = dst + (size_t)xp * G::N2 + zp;
 #pragma unroll
                       for (int j = 0; j < N; ++j) {
-                          if (accum) o[(size_t)j * N] += acc[n][j] * sc;
-                          else o[(size_t)j * N] = acc[n][j] * sc;
+                          const float a = (j & 1) ? acc[n][j / 2].y : acc[n][j / 2].x;
+                          if (accum) o[(size_t)j * N] += a * sc;
+                          else o[(size_t)j * N] = a * sc;
                       }
                   } else if (xp < nsrc && zp < nsrc) {   // the nsrc^3 block only
                       float* o = dst + (size_t)xp * nsrc * nsrc + zp;
 #pragma unroll
                       for (int j = 0; j < N; ++j) {
                           if (j >= nsrc) continue;
-                          if (accum) o[(size_t)j * nsrc] += acc[n][j] * sc;
-                          else o[(size_t)j * nsrc] = acc[n][j] * sc;
+                          const float a = (j & 1) ? acc[n][j / 2].y : acc[n][j / 2].x;
+                          if (accum) o[(size_t)j * nsrc] += a * sc;
+                          else o[(size_t)j * nsrc] = a * sc;
                       }
                   }
               }
@@ -607,7 +622,7 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
 #pragma unroll
           for (int k = 0; k < NB; ++k)
 #pragma unroll
-              for (int j = 0; j < N; ++j) acc[k][j] = 0.f;
+              for (int j = 0; j < N / 2; ++j) acc[k][j] = make_float2(0.f, 0.f);
         }
 #undef DGFS_WAITE
 #undef DGFS_WAITEC
