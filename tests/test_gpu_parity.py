@@ -491,6 +491,33 @@ def test_chunking_batch_order_and_determinism():
     assert torch.equal(a[perm], p1.collide(f[perm].contiguous()))
 
 
+@pytest.mark.parametrize("prec,N", [("fp64", 8), ("fp32", 16), ("f16s", 32), ("f16s", 24), ("bf16s", 16),
+                                    ("f16x3", 32), ("f16x3", 24), ("bf16x3", 16)])
+def test_zero_field_sign_and_scale_invariants(prec, N):
+    """Degenerate and scaled inputs in one batch with ordinary nodes: a zero field gives exactly zero
+    (no NaN flag: the 16-bit forms' per-node scale falls back to 1), Q is even (Q(-f) equals Q(f)
+    bitwise: negation commutes with every rounding, the 16-bit scale is taken from |f|) and
+    homogeneous of degree 2 (Q(2^k f) = 4^k Q(f): power-of-two factors are exact in every form, the
+    16-bit data being rescaled per node, so only values that cross the FP32 subnormal range differ)."""
+    L = {8: 3.0, 16: 5.0, 24: 6.0, 32: 7.0}[N]
+    F, _ = W.two_maxwellian(2, N, L, 91, dtype=np.float32)
+    F = F.astype(np.float32)
+    zero = np.zeros((1, N, N, N), np.float32)
+    batch = np.concatenate([zero, F, -F, F * np.float32(2.0 ** -8), F * np.float32(2.0 ** 8)])
+    plan = binding.Plan(N=N, L=L, gamma=0.52, M=12, N_rho=8, precision=prec)
+    q = plan.collide(_dev(batch, prec)).double().cpu()
+    plan.stream_status()   # raises on a NaN / infinity flag
+    assert torch.isfinite(q).all()
+    assert torch.equal(q[0], torch.zeros_like(q[0]))
+    base = q[1:3]
+    assert torch.equal(q[3:5], base)
+    for i, k in ((5, -8), (7, 8)):
+        scaled = q[i:i + 2] * 4.0 ** (-k)
+        rel = (torch.linalg.norm((scaled - base).flatten()) / torch.linalg.norm(base.flatten())).item()
+        assert rel < 1e-6, (prec, N, k, rel)
+    plan.close()
+
+
 @pytest.mark.parametrize("max_batch,B,pinned", [(1, 3, True), (2, 5, True), (7, 5, False), (0, 9, True),
                                                 (4, 37, True), (64, 300, True), (0, 2, True)])
 def test_host_buffer_entry_point_matches_device(max_batch, B, pinned):
