@@ -78,6 +78,9 @@ struct Geo3 {
     // tile ul = m3 / 128 - c TH), k = y; padded so that a warp's 16-byte stores spread over bank groups
     static constexpr uint32_t A3_SBO = 144, A3_TS = 16 * 144 + 16, A3_LBO = TH * A3_TS;
     static constexpr uint32_t A3_BYTES = KG * A3_LBO;
+    // bytes of pass-3 operand rows one CTA's epilogue sends to its peer per sphere pair: the 128 threads
+    // whose rows the peer owns, per front tile 2 row groups per 16 columns z', hi and lo, 16 bytes each
+    static constexpr uint32_t A3_REMOTE_BYTES = 128u * TH * (N / 16) * 2 * 2 * 16;
     // TMEM columns: pass-1 slot [+main | -main | +lo | -lo], pass-2/3 slots 2, 3 [+hi | +lo | -hi | -lo],
     // then f_hi and f_lo of the TH front tiles
     static constexpr uint32_t C_P1 = 0, C_S2 = 4 * N, C_S3 = 8 * N;
@@ -264,6 +267,7 @@ __device__ __forceinline__ void mma3_p3_loop(Bars3& bars, uint32_t sb, uint32_t 
         const uint32_t f16 = sb16 + (G::S_F + fbuf * G::F_BLOCK) / 16;
         DGFS_WAITWC(&bars.a3_full, ph_a3full);
         ph_a3full ^= 1u;
+        tc::fence_proxy_async();   // the peer's st.async rows, acquired with the barrier, to the tensor core
         tc::tc_fence_after();
         int n = 0;
         for (int k = b; k < G::TH; k += 2, ++n) {
@@ -340,7 +344,9 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
                 tc::mbar_init(&bars.filt[i], 1);
                 tc::mbar_init(&bars.fdone[i], 4);
             }
-            tc::mbar_init(&bars.a3_full, 256);   // the epilogue threads of both CTAs whose pass-3 rows are here
+            // the epilogue threads of this CTA whose pass-3 rows are here; the peer's rows arrive as
+            // st.async bytes (expect_tx registered by one of these arrivals)
+            tc::mbar_init(&bars.a3_full, 128);
             tc::mbar_init(&bars.a3_free, 4);     // the pass-3 MMA warps of both CTAs
             tc::mbar_init(&bars.drain, 4);
             tc::fence_mbar_init();
@@ -455,6 +461,8 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
         const int rg0 = ((lz * N) & 127) >> 3;   // row group of z' = 0 within the tile
         const bool remote = owner != (int)crank;   // this thread's pass-3 rows live in the peer
         const uint32_t a3full_owner = tc::map_peer(tc::smem_u32(&bars.a3_full), (uint32_t)owner);
+        // the first local thread registers the bytes the peer sends with its arrival
+        const bool a3_expect = warp == 0 && lane == (crank ? N / 2 : 0);
         uint32_t ph_f1 = 0, ph_a2free = 0, ph_a3free = 0, ph_f2 = 0, ph_f3 = 0;   // ph_f2: bit per slot
         int p1uses = 0;
         constexpr int NB = (G::TH + 1) / 2;   // back tiles of one warpgroup
@@ -543,19 +551,26 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
                                 split2<BF>(v.x, v.y, uh[j], ulo[j]);
                             }
                             const uint32_t o = a3_dst + (rg0 + 2 * cc + h) * G::A3_SBO + ky;
-                            tc::st_cluster_v4(o, uh[0], uh[1], uh[2], uh[3]);
-                            tc::st_cluster_v4(o + G::A3_BYTES, ulo[0], ulo[1], ulo[2], ulo[3]);
+                            if (remote) {   // non-blocking, counted on the owner's a3_full
+                                tc::st_async_v4(o, uh[0], uh[1], uh[2], uh[3], a3full_owner);
+                                tc::st_async_v4(o + G::A3_BYTES, ulo[0], ulo[1], ulo[2], ulo[3], a3full_owner);
+                            } else {
+                                tc::st_cluster_v4(o, uh[0], uh[1], uh[2], uh[3]);
+                                tc::st_cluster_v4(o + G::A3_BYTES, ulo[0], ulo[1], ulo[2], ulo[3]);
+                            }
                         }
                     }
                 }
             }
-            // this warpgroup's rows of the pair are written: visible to the owner's tensor core (a thread
-            // writes rows of one CTA only, so it arrives on that CTA's barrier alone)
-            if (remote) tc::fence_proxy_async_cluster();
-            else tc::fence_proxy_async();
-            if (!(fault == 1 && p == 0 && blockIdx.x == 0 && blockIdx.y == 0)) {
-                if (remote) tc::mbar_arrive_cluster(a3full_owner);
-                else tc::mbar_arrive(&bars.a3_full);
+            // this warpgroup's rows of the pair are written: a thread whose rows are local makes them
+            // visible to its tensor core and arrives (the first one with the bytes the peer sends);
+            // rows sent to the peer are counted there as st.async bytes
+            if (!remote) {
+                tc::fence_proxy_async();
+                if (!(fault == 1 && p == 0 && blockIdx.x == 0 && blockIdx.y == 0)) {
+                    if (a3_expect) tc::mbar_expect_tx(&bars.a3_full, G::A3_REMOTE_BYTES);
+                    else tc::mbar_arrive(&bars.a3_full);
+                }
             }
             // back: pass-3 tiles k = w, w + 2, ... in slot 2 + w, products of the two translates
             const uint32_t tB = trow + (w ? G::C_S3 : G::C_S2);

@@ -280,6 +280,15 @@ __device__ __forceinline__ void st_cluster_v4(uint32_t caddr, uint32_t a, uint32
 
 // Arrive (count 1) on an mbarrier of another CTA (shared::cluster address), releasing this
 // thread's earlier memory operations at cluster scope.
+// Non-blocking 16-byte store into a peer CTA's shared memory whose bytes count as complete_tx on the
+// mbarrier at mbar in that CTA (both shared::cluster addresses); the receiver acquires the data by
+// waiting on that barrier (expect_tx registered by one of its own arrivals).
+__device__ __forceinline__ void st_async_v4(uint32_t caddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d,
+                                            uint32_t mbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
+                 ::"r"(caddr), "r"(a), "r"(b), "r"(c), "r"(d), "r"(mbar) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
 }
