@@ -248,7 +248,7 @@ def fft_algorithmic_flops_per_node(N, Nrho, npairs):
 # from the ncu capture of a 512-node launch summarised in profiles/ (None for configurations
 # without a capture of the current kernel version).
 TRAFFIC_PER_NODE = {("f16s", 32, 32, 38): (231980544 + 2088668416) / 512, ("bf16s", 32, 32, 38): (253785344 + 2089054464) / 512,
-                    ("f16x3", 32, 32, 38): (106565888 + 2091562240) / 512,
+                    ("f16x3", 32, 32, 38): (108751616 + 2091174912) / 512,
                     ("fp32", 32, 32, 38): None}
 
 
