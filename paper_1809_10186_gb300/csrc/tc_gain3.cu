@@ -18,11 +18,12 @@
 // points) item. CTA c runs passes 1 and 2 of the y-tiles [c T/2, (c + 1) T/2) (pass-1/2 tiles are
 // blocks of y) and pass 3 of the x'-tiles [c T/2, (c + 1) T/2) (pass-3 tiles are blocks of x'),
 // both signs. The pass-2 epilogue writes every result row straight into the pass-3 operand of the
-// CTA that owns its x' (its own shared memory or, through distributed shared memory, the peer's);
+// CTA that owns its x' (its own shared memory, or the peer's through non-blocking st.async stores);
 // each CTA then forms the products of its x'-tiles with both signs in its own TMEM. Two cluster
-// hand-offs per sphere pair: "pass-3 operands complete" (every thread of both CTAs' pass-2
-// epilogues arrives on the barrier of the CTA whose rows it wrote) and "pass-3 operands released"
-// (both CTAs' pass-3 MMA warps commit to both CTAs' barriers by a multicast commit). The pass-2
+// hand-offs per sphere pair: "pass-3 operands complete" (the threads of a CTA whose rows are local
+// arrive on its barrier, one of them registering the bytes the peer sends, and the peer's st.async
+// stores complete those bytes) and "pass-3 operands released" (both CTAs' pass-3 MMA warps commit
+// to both CTAs' barriers by a multicast commit). The pass-2
 // operands are handed over one sign at a time, so warpgroup 0 writes one sign while the pass-2 MMAs
 // read the other.
 //
