@@ -389,6 +389,13 @@ dgfs_status dgfs_host_quadrature(const dgfs_plan_desc* desc, double* c_r, double
    give different fingerprints for one descriptor. No GPU needed. */
 dgfs_status dgfs_host_plan_fingerprint(const dgfs_plan_desc* desc, uint64_t* fingerprint);
 
+/* Sub-batch sizes dgfs_collide_host uses for B nodes on a plan whose chunk is `chunk` nodes: at most
+   chunk / 2 each (chunk >= 2; 1 for a one-node chunk), ramping up from B / 32 by a factor of 4 and
+   down again, with as few as fit in between; they sum to B. Writes min(count, cap) sizes (sizes may
+   be NULL to query the count) and the count to *count. B >= 0, chunk >= 1, else DGFS_ERR_INVALID_ARG.
+   No GPU needed. */
+dgfs_status dgfs_host_pipeline_schedule(int64_t B, int64_t chunk, int64_t* sizes, int64_t cap, int64_t* count);
+
 /* Circulant translate filter a[N] of the shift t along one axis: (T_t f)_j =
    sum_j' a[(j - j') mod N] f_j', the grid restriction of the trigonometric interpolant
    shifted by t (multiplier e^{i pi k t / L}, Nyquist: cos(pi N t / 2L)). */

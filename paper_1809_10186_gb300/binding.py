@@ -77,6 +77,8 @@ _SIGNATURES = {
     "dgfs_device_mma_cycles": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
     "dgfs_plan_fingerprint": [_P, ctypes.POINTER(ctypes.c_uint64)],
     "dgfs_host_plan_fingerprint": [ctypes.POINTER(dgfs_plan_desc), ctypes.POINTER(ctypes.c_uint64)],
+    "dgfs_host_pipeline_schedule": [ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+                                    ctypes.POINTER(ctypes.c_int64)],
     "dgfs_plan_autotune": [_P, _P, _I64, _P, ctypes.POINTER(dgfs_tune_report)],
     "dgfs_plan_set_tuning": [_P, ctypes.c_int, _I64],
     "dgfs_profile_begin": [_P],
@@ -219,6 +221,15 @@ def host_plan_fingerprint(**kw):
     out = ctypes.c_uint64(0)
     check(lib().dgfs_host_plan_fingerprint(ctypes.byref(d), ctypes.byref(out)), "dgfs_host_plan_fingerprint")
     return out.value
+
+
+def host_pipeline_schedule(B, chunk):
+    """Sub-batch sizes of the host-buffer pipeline for B nodes and a plan chunk (no GPU)."""
+    n = ctypes.c_int64(0)
+    check(lib().dgfs_host_pipeline_schedule(B, chunk, None, 0, ctypes.byref(n)), "dgfs_host_pipeline_schedule")
+    buf = (ctypes.c_int64 * max(1, n.value))()
+    check(lib().dgfs_host_pipeline_schedule(B, chunk, buf, n.value, ctypes.byref(n)), "dgfs_host_pipeline_schedule")
+    return [buf[i] for i in range(n.value)]
 
 
 def device_fma_peaks():

@@ -1523,6 +1523,35 @@ dgfs_status dgfs_host_dg_stiffness(int K, double* S, double* Minv) {
     return DGFS_OK;
 }
 
+// Sub-batch sizes of the host-buffer pipeline (B >= 1, chunk >= 1): at most H = chunk / 2 nodes each
+// (one staging buffer of one node when chunk == 1), ramping up from B / 32 by a factor of 4 while the
+// ramp fits twice into B, the rest split evenly into as few sub-batches of at most H as possible,
+// then the ramp down.
+static std::vector<int64_t> host_pipeline_sizes(int64_t B, int64_t chunk) {
+    const int64_t H = chunk >= 2 ? chunk / 2 : 1;
+    std::vector<int64_t> front;
+    int64_t ramp_sum = 0;
+    for (int64_t r = std::max<int64_t>(1, (B + 31) / 32); r < H && 2 * (ramp_sum + r) <= B; r *= 4) {
+        front.push_back(r);
+        ramp_sum += r;
+    }
+    const int64_t mid = B - 2 * ramp_sum;
+    const int64_t nmid = (mid + H - 1) / H;
+    std::vector<int64_t> sizes(front);
+    for (int64_t k = 0; k < nmid; ++k) sizes.push_back(mid / nmid + (k < mid % nmid ? 1 : 0));
+    sizes.insert(sizes.end(), front.rbegin(), front.rend());
+    return sizes;
+}
+
+dgfs_status dgfs_host_pipeline_schedule(int64_t B, int64_t chunk, int64_t* sizes, int64_t cap, int64_t* count) {
+    if (!count || B < 0 || chunk < 1 || cap < 0) return fail(DGFS_ERR_INVALID_ARG, "B >= 0, chunk >= 1, cap >= 0, count non-NULL");
+    const std::vector<int64_t> v = B > 0 ? host_pipeline_sizes(B, chunk) : std::vector<int64_t>();
+    *count = (int64_t)v.size();
+    if (sizes)
+        for (int64_t i = 0; i < std::min<int64_t>(cap, (int64_t)v.size()); ++i) sizes[i] = v[(size_t)i];
+    return DGFS_OK;
+}
+
 dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host, int64_t B,
                               void* stream) {
     if (!check_plan(plan)) return fail(DGFS_ERR_STATE, "invalid or destroyed plan");
@@ -1547,17 +1576,7 @@ dgfs_status dgfs_collide_host(dgfs_plan_t plan, const void* f_host, void* Q_host
     // item of the persistent translate kernel's tail).
     const int nbuf = plan->chunk >= 2 ? 2 : 1;
     const int64_t H = plan->chunk / nbuf;
-    std::vector<int64_t> front;
-    int64_t ramp_sum = 0;
-    for (int64_t r = std::max<int64_t>(1, (B + 31) / 32); r < H && 2 * (ramp_sum + r) <= B; r *= 4) {
-        front.push_back(r);
-        ramp_sum += r;
-    }
-    const int64_t mid = B - 2 * ramp_sum;
-    const int64_t nmid = (mid + H - 1) / H;
-    std::vector<int64_t> sizes(front);
-    for (int64_t k = 0; k < nmid; ++k) sizes.push_back(mid / nmid + (k < mid % nmid ? 1 : 0));
-    sizes.insert(sizes.end(), front.rbegin(), front.rend());
+    const std::vector<int64_t> sizes = host_pipeline_sizes(B, plan->chunk);
     DGFS_CUDA(cudaEventRecord(plan->ev_start, s), "event record");   // earlier work on s that used the plan
     DGFS_CUDA(cudaStreamWaitEvent(plan->cs_h2d, plan->ev_start, 0), "stream wait");
     DGFS_CUDA(cudaStreamWaitEvent(plan->cs_d2h, plan->ev_start, 0), "stream wait");

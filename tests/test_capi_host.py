@@ -188,3 +188,36 @@ def test_plan_fingerprint_tracks_every_input(lib):
                    dict(L=5.5), dict(N=24)):
         other = dict(base, **change)
         assert binding.host_plan_fingerprint(**other) != f0, change
+
+
+@pytest.mark.parametrize("B,chunk", [(2048, 2048), (2048, 1024), (3, 1), (5, 2), (5, 7), (9, 4096), (37, 4),
+                                     (300, 64), (2, 4096), (1, 4096), (100000, 2048), (9216, 2048), (167, 10 ** 6)])
+def test_host_pipeline_schedule_covers_the_batch(B, chunk):
+    """dgfs_host_pipeline_schedule (the sub-batches of dgfs_collide_host): sizes in [1, chunk / 2]
+    (1 for a one-node chunk) that sum to B; it starts at ceil(B / 32) when that is below the staging
+    half (else the batch is split evenly) and grows by 4 while ramping up, the same steps mirrored at
+    the end, and no sub-batch is more
+    than 8 times its predecessor (its input copy hides behind the predecessor's compute)."""
+    sizes = binding.host_pipeline_schedule(B, chunk)
+    H = chunk // 2 if chunk >= 2 else 1
+    assert sum(sizes) == B
+    assert all(1 <= s <= H for s in sizes), sizes
+    r0 = max(1, -(-B // 32))
+    if r0 < H and 2 * r0 <= B:   # a ramp: it starts at ceil(B / 32)
+        assert sizes[0] == r0, sizes
+    else:                        # none: the batch split evenly into sub-batches of at most H
+        assert max(sizes) - min(sizes) <= 1, sizes
+    k = 0   # ramp steps: while the next size is 4 times the previous
+    while k + 1 < len(sizes) and sizes[k + 1] == 4 * sizes[k]:
+        k += 1
+    assert sizes[:k] == sizes[::-1][:k], sizes
+    assert all(b <= 8 * a for a, b in zip(sizes, sizes[1:])), sizes
+
+
+def test_host_pipeline_schedule_of_the_headline_batch_and_errors():
+    assert binding.host_pipeline_schedule(2048, 2048) == [64, 256, 704, 704, 256, 64]
+    assert binding.host_pipeline_schedule(0, 16) == []
+    with pytest.raises(binding.DGFSError):
+        binding.host_pipeline_schedule(-1, 16)
+    with pytest.raises(binding.DGFSError):
+        binding.host_pipeline_schedule(8, 0)
