@@ -189,8 +189,11 @@ dgfs_status dgfs_collide_ragged(const dgfs_plan_t* plans, int nplans, const int3
    groups the nodes by plan and copies the per-class offsets, gamma and b to device memory the
    schedule owns (it allocates; the call is synchronous). dgfs_ragged_collide then computes
    Q(f,f) for every node with stream-ordered kernel launches only, no host staging, so a whole
-   mixed-N batch can be captured in one CUDA graph. The plans must outlive the schedule; calls
-   through one schedule (or its plans) must not run concurrently on different streams.
+   mixed-N batch can be captured in one CUDA graph. When the classes with nodes use distinct plans,
+   they run concurrently on streams the schedule owns, forked from `stream` at the call and joined
+   back to it before the call's later work (a graph capture records them as parallel branches). The
+   plans must outlive the schedule; calls through one schedule (or its plans) must not run
+   concurrently on different streams.
    The paper has no counterpart (its element-local parallelism, Sec. 3, is the reason nodes are
    independent). Arguments as dgfs_collide_ragged; node_plan, node_offset, node_gamma, node_b
    are HOST arrays, read during the create call only. */
@@ -199,7 +202,7 @@ dgfs_status dgfs_ragged_create(const dgfs_plan_t* plans, int nplans, const int32
                                const int64_t* node_offset, const double* node_gamma,
                                const double* node_b, int64_t B, dgfs_ragged_t* out);
 dgfs_status dgfs_ragged_collide(dgfs_ragged_t ragged, const void* f, void* Q, void* stream);
-/* Releases the schedule's device arrays (synchronises the device first). NULL is a no-op. */
+/* Releases the schedule's device arrays and streams (synchronises the device first). NULL is a no-op. */
 dgfs_status dgfs_ragged_destroy(dgfs_ragged_t ragged);
 
 /* ---- 1-D DGFS solver (Sec. 3: eq. eq_weakForm, the upwind flux eq. eq_numericalFlux_upwind,

@@ -910,7 +910,25 @@ struct dgfs_ragged_s {
     std::vector<size_t> base;          // first index of the class in the device arrays
     int device = 0;
     void* d_mem = nullptr;             // [B] offsets (int64), [B] gamma, [B] b (double), by class
+    // classes with nodes run concurrently, one schedule-owned stream each (forked from and joined
+    // back to the caller's stream), when their plans are distinct; else one after the other
+    bool concurrent = false;
+    std::vector<cudaStream_t> streams; // per class (nullptr for an empty class)
+    std::vector<cudaEvent_t> done;     // per class: its work on its stream is enqueued
+    cudaEvent_t fork = nullptr;
 };
+
+static void ragged_release_streams(dgfs_ragged_s* r) {
+    for (cudaStream_t st : r->streams)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : r->done)
+        if (ev) cudaEventDestroy(ev);
+    if (r->fork) cudaEventDestroy(r->fork);
+    r->streams.clear();
+    r->done.clear();
+    r->fork = nullptr;
+    r->concurrent = false;
+}
 
 static bool check_ragged_handle(dgfs_ragged_t r) { return r && r->magic == kRaggedMagic; }
 
@@ -954,6 +972,32 @@ dgfs_status dgfs_ragged_create(const dgfs_plan_t* plans, int nplans, const int32
             cudaFree(r->d_mem);
             return cuda_fail(e, "ragged schedule: upload");
         }
+        // concurrency: at least two classes with nodes, on distinct plans (each plan owns its
+        // workspace, flag word and work-item queue)
+        int active = 0;
+        bool distinct = true;
+        for (int c = 0; c < nplans; ++c) {
+            if (r->count[c] == 0) continue;
+            ++active;
+            for (int d = 0; d < c; ++d)
+                if (r->count[d] > 0 && plans[d] == plans[c]) distinct = false;
+        }
+        if (active >= 2 && distinct) {
+            r->streams.assign(nplans, nullptr);
+            r->done.assign(nplans, nullptr);
+            e = cudaEventCreateWithFlags(&r->fork, cudaEventDisableTiming);
+            for (int c = 0; c < nplans && e == cudaSuccess; ++c) {
+                if (r->count[c] == 0) continue;
+                e = cudaStreamCreateWithFlags(&r->streams[c], cudaStreamNonBlocking);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done[c], cudaEventDisableTiming);
+            }
+            if (e != cudaSuccess) {
+                ragged_release_streams(r.get());
+                cudaFree(r->d_mem);
+                return cuda_fail(e, "ragged schedule: streams");
+            }
+            r->concurrent = true;
+        }
     }
     *out = r.release();
     return DGFS_OK;
@@ -975,22 +1019,35 @@ dgfs_status dgfs_ragged_collide(dgfs_ragged_t r, const void* f, void* Q, void* s
     const int64_t* d_offs = reinterpret_cast<const int64_t*>(m);
     const double* d_gam = reinterpret_cast<const double*>(m + (size_t)B * sizeof(int64_t));
     const double* d_b = d_gam + B;
+    DGFS_ON_DEVICE(r->device);
+    if (r->concurrent) DGFS_CUDA(cudaEventRecord(r->fork, s), "event record");   // work before the call
+    dgfs_status result = DGFS_OK;
     for (size_t c = 0; c < r->plans.size(); ++c) {
         dgfs_plan_s* p = r->plans[c];
         if (r->count[c] == 0) continue;
-        std::lock_guard<std::mutex> lock(p->host_mu);
-        DGFS_ON_DEVICE(p->device);
-        for (int64_t n0 = 0; n0 < r->count[c]; n0 += p->chunk) {
-            const int64_t nn = std::min<int64_t>(p->chunk, r->count[c] - n0);
-            const size_t k = r->base[c] + (size_t)n0;
-            NodeParams np{d_gam + k, d_b + k, p->hp.gamma, p->hp.b, 0};
-            const dgfs_status st = p->prec == DGFS_PREC_FP64
-                ? run_chunk<double>(p, Op::Collide, static_cast<const double*>(f), nullptr, static_cast<double*>(Q),
-                                    d_offs + k, np, nn, s)
-                : run_chunk<float>(p, Op::Collide, static_cast<const float*>(f), nullptr, static_cast<float*>(Q),
-                                   d_offs + k, np, nn, s);
-            if (st != DGFS_OK) return st;
+        cudaStream_t sc = s;
+        if (r->concurrent) {
+            sc = r->streams[c];
+            DGFS_CUDA(cudaStreamWaitEvent(sc, r->fork, 0), "stream wait");
         }
+        {
+            std::lock_guard<std::mutex> lock(p->host_mu);
+            for (int64_t n0 = 0; n0 < r->count[c] && result == DGFS_OK; n0 += p->chunk) {
+                const int64_t nn = std::min<int64_t>(p->chunk, r->count[c] - n0);
+                const size_t k = r->base[c] + (size_t)n0;
+                NodeParams np{d_gam + k, d_b + k, p->hp.gamma, p->hp.b, 0};
+                result = p->prec == DGFS_PREC_FP64
+                    ? run_chunk<double>(p, Op::Collide, static_cast<const double*>(f), nullptr, static_cast<double*>(Q),
+                                        d_offs + k, np, nn, sc)
+                    : run_chunk<float>(p, Op::Collide, static_cast<const float*>(f), nullptr, static_cast<float*>(Q),
+                                       d_offs + k, np, nn, sc);
+            }
+        }
+        if (r->concurrent) {   // joined back to the caller's stream even after a failed launch
+            DGFS_CUDA(cudaEventRecord(r->done[c], sc), "event record");
+            DGFS_CUDA(cudaStreamWaitEvent(s, r->done[c], 0), "stream wait");
+        }
+        if (result != DGFS_OK) return result;
     }
     return DGFS_OK;
 }
@@ -1001,6 +1058,7 @@ dgfs_status dgfs_ragged_destroy(dgfs_ragged_t r) {
     {
         DeviceScope scope(r->device);
         cudaDeviceSynchronize();
+        ragged_release_streams(r);
         cudaFree(r->d_mem);
     }
     r->magic = 0;
