@@ -226,7 +226,13 @@ dgfs_status dgfs_slab_create(dgfs_plan_t plan, int K, int I, const double* edges
 dgfs_status dgfs_slab_set_walls(dgfs_slab_t slab, const double* wall_left, const double* wall_right);
 /* dFdt = the right-hand side at F (both device [I][K][N^3], distinct). */
 dgfs_status dgfs_slab_rhs(dgfs_slab_t slab, const void* F, void* dFdt, void* stream);
-/* nsteps SSP-RK steps (order 2 or 3) of size dt, in place on F. */
+/* nsteps SSP-RK steps (order 2 or 3) of size dt, in place on F. With nsteps >= 2, a plan that is not
+   profiling and a stream that is not being captured, the first step runs eagerly and one step is then
+   captured as a CUDA graph (on a slab-owned stream) and replayed for the rest; the graph is kept for
+   later calls with the same F, dt, order and plan tuning, and dropped by dgfs_slab_set_walls.
+   Otherwise every step is launched eagerly (on a capturing stream, into the caller's graph). Both
+   give the same bits. F must stay valid while a graph built on it is kept (until another F, or
+   dgfs_slab_destroy). */
 dgfs_status dgfs_slab_ssprk(dgfs_slab_t slab, int order, void* F, double dt, int nsteps, void* stream);
 dgfs_status dgfs_slab_destroy(dgfs_slab_t slab);
 /* Host: S [K][K] (eq. eq_stiffMatrix1 on [-1, 1]) and the inverse mass matrix [K][K]; either NULL. */

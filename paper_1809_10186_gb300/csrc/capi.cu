@@ -1374,11 +1374,26 @@ struct dgfs_slab_s {
     SlabMatrices mats{};
     void* d_mem = nullptr;     // fw [2][N^3] | num [2] | 2/h [I] | C | stage | q ([I][K][N^3] each)
     size_t off_fw = 0, off_num = 0, off_h = 0, off_C = 0, off_stage = 0, off_q = 0;
+    // one SSP-RK step captured as a CUDA graph and replayed: the step's ~100 small launches cost one
+    // graph launch. Valid for the field, step size, order and plan tuning it was captured with; the
+    // wall update drops it (the wall denominators are kernel arguments).
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void* gF = nullptr;
+    double gdt = 0.0;
+    int gorder = 0, grpc = 0;
+    int64_t gchunk = 0;
 };
 
 namespace {
 
 bool check_slab(dgfs_slab_t s) { return s && s->magic == kSlabMagic; }
+
+void slab_release_graph(dgfs_slab_s* sl) {
+    if (sl->gexec) cudaGraphExecDestroy(sl->gexec);
+    sl->gexec = nullptr;
+    sl->gF = nullptr;
+}
 
 // Wall Maxwellians f_w = exp(-|c - u_w|^2 / T_w) in the compute type and the FP64 denominators
 // sum over the incoming velocities of |c_1| f_w (left wall: c_1 > 0, right wall: c_1 < 0).
@@ -1415,6 +1430,7 @@ dgfs_status slab_walls(dgfs_slab_s* sl, const double* wl, const double* wr) {
     DGFS_CUDA(cudaDeviceSynchronize(), "synchronise before the wall update");
     DGFS_CUDA(cudaMemcpy(static_cast<unsigned char*>(sl->d_mem) + sl->off_fw, blob.data(), blob.size(),
                          cudaMemcpyHostToDevice), "wall tables upload");
+    slab_release_graph(sl);
     return DGFS_OK;
 }
 
@@ -1437,34 +1453,80 @@ dgfs_status slab_rhs(dgfs_slab_s* sl, const T* F, T* out, cudaStream_t s) {
     return DGFS_OK;
 }
 
-// SSP-RK2 / RK3 (eqs. SSPRK2, SSPRK3) of dF/dt = rhs(F), in place, stages in the slab's buffers
+// One SSP-RK2 / RK3 step (eqs. SSPRK2, SSPRK3) of dF/dt = rhs(F), in place, stages in the slab's buffers
 template <typename T>
-dgfs_status slab_ssprk(dgfs_slab_s* sl, int order, T* F, double dt, int nsteps, cudaStream_t s) {
+dgfs_status slab_step(dgfs_slab_s* sl, int order, T* F, double dt, cudaStream_t s) {
     unsigned char* base = static_cast<unsigned char*>(sl->d_mem);
     T* stage = reinterpret_cast<T*>(base + sl->off_stage);
     T* q = reinterpret_cast<T*>(base + sl->off_q);
     const int64_t n = (int64_t)sl->I * sl->K * sl->plan->hp.N * sl->plan->hp.N * sl->plan->hp.N;
     int* flags = sl->plan->d_flags;
-    for (int it = 0; it < nsteps; ++it) {
-        dgfs_status st = slab_rhs<T>(sl, F, q, s);
-        if (st != DGFS_OK) return st;
-        cudaError_t e = launch_rk_combine<T>(n, 1.0, F, 0.0, nullptr, dt, q, stage, flags, s);
-        if (e) return cuda_fail(e, "slab SSP-RK stage");
-        st = slab_rhs<T>(sl, stage, q, s);
-        if (st != DGFS_OK) return st;
-        if (order == 2) {
-            e = launch_rk_combine<T>(n, 0.5, F, 0.5, stage, 0.5 * dt, q, F, flags, s);
-        } else {
-            e = launch_rk_combine<T>(n, 0.75, F, 0.25, stage, 0.25 * dt, q, stage, flags, s);
-            if (!e) {
-                st = slab_rhs<T>(sl, stage, q, s);
-                if (st != DGFS_OK) return st;
-                e = launch_rk_combine<T>(n, 1.0 / 3.0, F, 2.0 / 3.0, stage, 2.0 / 3.0 * dt, q, F, flags, s);
-            }
+    dgfs_status st = slab_rhs<T>(sl, F, q, s);
+    if (st != DGFS_OK) return st;
+    cudaError_t e = launch_rk_combine<T>(n, 1.0, F, 0.0, nullptr, dt, q, stage, flags, s);
+    if (e) return cuda_fail(e, "slab SSP-RK stage");
+    st = slab_rhs<T>(sl, stage, q, s);
+    if (st != DGFS_OK) return st;
+    if (order == 2) {
+        e = launch_rk_combine<T>(n, 0.5, F, 0.5, stage, 0.5 * dt, q, F, flags, s);
+    } else {
+        e = launch_rk_combine<T>(n, 0.75, F, 0.25, stage, 0.25 * dt, q, stage, flags, s);
+        if (!e) {
+            st = slab_rhs<T>(sl, stage, q, s);
+            if (st != DGFS_OK) return st;
+            e = launch_rk_combine<T>(n, 1.0 / 3.0, F, 2.0 / 3.0, stage, 2.0 / 3.0 * dt, q, F, flags, s);
         }
-        if (e) return cuda_fail(e, "slab SSP-RK stage");
-        if (sl->plan->prof) sl->plan->prof_launches += order;
     }
+    if (e) return cuda_fail(e, "slab SSP-RK stage");
+    if (sl->plan->prof) sl->plan->prof_launches += order;
+    return DGFS_OK;
+}
+
+// nsteps steps. Two or more steps on a stream that is not being captured, with the plan not
+// profiling (its counters and events follow eager launches), replay one captured step. A new graph
+// is captured after one eager step, so that every kernel's one-time setup has run outside capture.
+template <typename T>
+dgfs_status slab_ssprk(dgfs_slab_s* sl, int order, T* F, double dt, int nsteps, cudaStream_t s) {
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    DGFS_CUDA(cudaStreamIsCapturing(s, &capturing), "stream capture status");
+    dgfs_plan_s* p = sl->plan;
+    if (nsteps < 2 || p->prof || capturing != cudaStreamCaptureStatusNone) {
+        for (int it = 0; it < nsteps; ++it) {
+            const dgfs_status st = slab_step<T>(sl, order, F, dt, s);
+            if (st != DGFS_OK) return st;
+        }
+        return DGFS_OK;
+    }
+    int done = 0;
+    if (!sl->gexec || sl->gF != F || sl->gdt != dt || sl->gorder != order || sl->grpc != p->tc.rpc ||
+        sl->gchunk != p->run_chunk) {
+        slab_release_graph(sl);
+        dgfs_status st = slab_step<T>(sl, order, F, dt, s);
+        if (st != DGFS_OK) return st;
+        done = 1;
+        if (!sl->cap) DGFS_CUDA(cudaStreamCreateWithFlags(&sl->cap, cudaStreamNonBlocking), "stream create");
+        cudaGraph_t g = nullptr;
+        DGFS_CUDA(cudaStreamBeginCapture(sl->cap, cudaStreamCaptureModeThreadLocal), "graph capture");
+        st = slab_step<T>(sl, order, F, dt, sl->cap);
+        const cudaError_t ec = cudaStreamEndCapture(sl->cap, &g);
+        if (st != DGFS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (ec != cudaSuccess) return cuda_fail(ec, "graph capture of a slab step");
+        const cudaError_t ei = cudaGraphInstantiate(&sl->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            sl->gexec = nullptr;
+            return cuda_fail(ei, "graph instantiation of a slab step");
+        }
+        sl->gF = F;
+        sl->gdt = dt;
+        sl->gorder = order;
+        sl->grpc = p->tc.rpc;
+        sl->gchunk = p->run_chunk;
+    }
+    for (int it = done; it < nsteps; ++it) DGFS_CUDA(cudaGraphLaunch(sl->gexec, s), "graph launch");
     return DGFS_OK;
 }
 
@@ -1565,6 +1627,8 @@ dgfs_status dgfs_slab_destroy(dgfs_slab_t slab) {
     {
         DeviceScope scope(slab->device);
         cudaDeviceSynchronize();
+        slab_release_graph(slab);
+        if (slab->cap) cudaStreamDestroy(slab->cap);
         if (slab->dg) dgfs_dg_destroy(slab->dg);
         cudaFree(slab->d_mem);
     }

@@ -176,3 +176,45 @@ def test_slab_single_element_between_walls():
     plan.stream_status()
     ref = SL.SlabOracle(op, K, edges, 0.6, wl, wr, svd_tol=0.0).rhs(F)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("prec,order", [("fp64", 3), ("fp32", 2)])
+def test_slab_graph_replay_equals_eager_steps(prec, order):
+    """Several steps in one call replay a captured step; single-step calls run eagerly. Both give the
+    same bits, also after the step size, the plan's tuning and the walls change (each rebuilds the
+    graph), and inside a caller's own graph capture (which takes the eager path)."""
+    N, L, K = 8, 4.0, 3
+    edges = np.linspace(0, 1, 6)
+    wl, wr = (0.0, 0.1, 0.0, 0.9), (0.0, -0.2, 0.0, 1.1)
+    plan = binding.Plan(N=N, L=L, gamma=0.38, M=12, N_rho=6, precision=prec)
+    slab = binding.Slab(plan, K, edges, 0.7, wl, wr)
+    op = O.OraclePlan(N, L, gamma=0.38, M=12, Nrho=6, nyquist="sym")
+    F = _state(op, 5, K, 51, prec)
+    a, b = _dev(F, prec), _dev(F, prec)
+
+    def both(dt, n):
+        slab.ssprk(a, dt, n, order=order)
+        for _ in range(n):
+            slab.ssprk(b, dt, 1, order=order)
+        plan.stream_status()
+        assert torch.equal(a, b)
+
+    both(0.004, 5)
+    both(0.004, 3)
+    both(0.002, 4)
+    plan.set_tuning(2, 0)
+    both(0.002, 2)
+    slab.set_walls((0.0, 0.3, 0.0, 1.0), (0.0, 0.0, 0.1, 1.2))
+    both(0.002, 3)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        slab.ssprk(a, 0.002, 2, order=order, stream=s)
+    g.replay()
+    for _ in range(2):
+        slab.ssprk(b, 0.002, 1, order=order)
+    torch.cuda.synchronize()
+    plan.stream_status()
+    assert torch.equal(a, b)
+    slab.close()
