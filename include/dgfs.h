@@ -231,8 +231,8 @@ dgfs_status dgfs_slab_rhs(dgfs_slab_t slab, const void* F, void* dFdt, void* str
    captured as a CUDA graph (on a slab-owned stream) and replayed for the rest; the graph is kept for
    later calls with the same F, dt, order and plan tuning, and dropped by dgfs_slab_set_walls.
    Otherwise every step is launched eagerly (on a capturing stream, into the caller's graph). Both
-   give the same bits. F must stay valid while a graph built on it is kept (until another F, or
-   dgfs_slab_destroy). */
+   give the same bits. The graph is keyed by F's address: a new field buffer at the same address
+   (of the slab's fixed size) reuses it. */
 dgfs_status dgfs_slab_ssprk(dgfs_slab_t slab, int order, void* F, double dt, int nsteps, void* stream);
 dgfs_status dgfs_slab_destroy(dgfs_slab_t slab);
 /* Host: S [K][K] (eq. eq_stiffMatrix1 on [-1, 1]) and the inverse mass matrix [K][K]; either NULL. */
