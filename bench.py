@@ -247,7 +247,7 @@ def fft_algorithmic_flops_per_node(N, Nrho, npairs):
 # DRAM bytes (read + write) per node of one translate-product launch at N = 32, N_rho = 32, M = 38,
 # from the ncu capture of a 512-node launch summarised in profiles/ (None for configurations
 # without a capture of the current kernel version).
-TRAFFIC_PER_NODE = {("f16s", 32, 32, 38): (231980544 + 2088668416) / 512, ("bf16s", 32, 32, 38): (253785344 + 2089054464) / 512,
+TRAFFIC_PER_NODE = {("f16s", 32, 32, 38): (180026368 + 2091159552) / 512, ("bf16s", 32, 32, 38): (185963520 + 2090830592) / 512,
                     ("f16x3", 32, 32, 38): (108751616 + 2091174912) / 512,
                     ("fp32", 32, 32, 38): None}
 

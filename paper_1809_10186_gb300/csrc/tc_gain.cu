@@ -30,7 +30,9 @@
 // slots, and epilogue warpgroup 1 writes each pass-2 result into the pass-3 operands (both signs'
 // full fields, in shared memory); every ring is two deep, so consecutive tiles overlap. The back
 // (pass 3) starts once every pass-2 tile is stored: pass-3 MMA warp b fills slot b with the tiles
-// u = b (mod 2), and epilogue warpgroup b forms their products (one TMEM lane per thread). While
+// u = b (mod 2), and epilogue warpgroup b forms their products (one TMEM lane per thread); the two
+// signs' halves of the slot are handed over separately, so the + MMAs of the next tile overlap
+// the read of the - half and the products. While
 // it waits for the pass-3 operands, warpgroup 0 already turns the first two pass-1 tiles of the
 // next step of the item into pass-2 operands (N = 32), so the next front starts two tiles in.
 // Barriers shared by several MMA warps (filter buffer done, final drain, pass-3 operands released)
@@ -138,7 +140,8 @@ struct Bars {
     // TMEM slot rings (index = tile % 2): MMA completion -> epilogue, epilogue drained -> MMA
     uint64_t full1[2], free1[2];       // pass-1 slots (pass-1 epilogue, warpgroup 0)
     uint64_t full2[2], free2[2];       // pass-2/3 slots used by pass 2 (pass-2 epilogue, warpgroup 1)
-    uint64_t full3[2], free3[2];       // pass-2/3 slots used by pass 3 (warpgroup = slot)
+    uint64_t full3p[2], free3p[2];     // pass-2/3 slots used by pass 3 (warpgroup = slot): + sign columns
+    uint64_t full3m[2], free3m[2];     // and - sign columns, each half released as soon as it is read
     uint64_t free3x[2];                // last pass-3 drain of a slot in a pair (next pair's pass 2 may start)
     uint64_t a2_full[2], a2_free[2];   // pass-2 operand ring: epilogue -> MMA, MMA completion -> epilogue
     uint64_t a3_full, a3_free;         // pass-3 operands (both signs)
@@ -322,8 +325,10 @@ __device__ __forceinline__ void mma_p2_loop(Bars& bars, uint32_t sb, uint32_t tm
 }
 
 // Pass 3 of the tiles u = 2k + b into slot b once every pass-2 tile is in shared memory (a3_full
-// also orders every pass-2 drain of the slot before these MMAs); reuse within the step waits
-// for the warpgroup's drains (free3, completions 0..2 of the step's four).
+// also orders every pass-2 drain of the slot before these MMAs). Each sign's half of the slot has
+// its own completion (full3p / full3m) and release (free3p / free3m): the + MMAs of tile k + 1 wait
+// only for the + half of tile k to be read, so they run while the epilogue reads the - half and
+// forms the products (completions 0..2 of the step's four).
 template <int N, bool BF, int b>
 __device__ __forceinline__ void mma_p3_loop(Bars& bars, uint32_t sb, uint32_t tmem, const Items& it,
                                             const volatile long long* s_item, volatile int* abort) {
@@ -346,21 +351,22 @@ __device__ __forceinline__ void mma_p3_loop(Bars& bars, uint32_t sb, uint32_t tm
             tc::tc_fence_after();
             for (int k = 0; k < G::TW; ++k) {
                 const int u = 2 * k + b;
-                if (k > 0) {
-                    DGFS_WAITW(&bars.free3[b], (uint32_t)((k - 1) & 1));   // four completions per step
-                    tc::tc_fence_after();
-                }
                 const uint32_t d = tmem + (b ? G::C_S3 : G::C_S2);
                 const uint32_t a16 = sb16 + G::S_A3 / 16 + u * (G::A3_TS / 16);
 #pragma unroll
-                for (int gs = 0; gs < 2; ++gs)
+                for (int gs = 0; gs < 2; ++gs) {   // sign +, then sign -
+                    if (k > 0) {
+                        DGFS_WAITW(gs ? &bars.free3m[b] : &bars.free3p[b], (uint32_t)((k - 1) & 1));   // four per step
+                        tc::tc_fence_after();
+                    }
 #pragma unroll
                     for (int ks = 0; ks < G::KSTEPS; ++ks)
                         tc::mma_ss_warp(d + gs * 2 * N,
                                         tc::sdesc_at(dA3, a16 + (gs * G::A3_BYTES + ks * 2 * G::A3_LBO) / 16),
                                         tc::sdesc_at(dF, f16 + (G::OFF_B3 + gs * G::B23_BYTES + ks * 2 * G::FB_LBO) / 16),
                                         id23, ks);
-                tc::mma_commit_warp(&bars.full3[b]);
+                    tc::mma_commit_warp(gs ? &bars.full3m[b] : &bars.full3p[b]);
+                }
             }
             tc::mma_commit_warp(&bars.a3_free);
             tc::mma_commit_warp(&bars.fdone[fbuf]);
@@ -408,8 +414,10 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
                 tc::mbar_init(&bars.free1[i], 128);
                 tc::mbar_init(&bars.full2[i], 1);
                 tc::mbar_init(&bars.free2[i], 128);
-                tc::mbar_init(&bars.full3[i], 1);
-                tc::mbar_init(&bars.free3[i], 128);
+                tc::mbar_init(&bars.full3p[i], 1);
+                tc::mbar_init(&bars.free3p[i], 128);
+                tc::mbar_init(&bars.full3m[i], 1);
+                tc::mbar_init(&bars.free3m[i], 128);
                 tc::mbar_init(&bars.free3x[i], 128);
                 tc::mbar_init(&bars.a2_full[i], 128);
                 tc::mbar_init(&bars.a2_free[i], 1);
@@ -478,7 +486,7 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
         // k = z = lz; A3 rows x' N + z' with x' = lz, k = y
         const uint32_t a2_row = sb + G::S_A2 + ((uint32_t)(yl * N) >> 3) * G::A2_SBO + (lz >> 3) * G::A2_LBO + (lz & 7) * 16;
         const int mg3 = (lz * N) >> 3;
-        uint32_t ph_f = 0, ph_a2free = 0, ph_a3free = 0, ph_f3 = 0;   // phase bits (bit b = ring slot b)
+        uint32_t ph_f = 0, ph_a2free = 0, ph_a3free = 0, ph_f3p = 0, ph_f3m = 0;   // phase bits (bit b = ring slot b)
         float2 acc[G::TW][N / 2];   // P_r of the warpgroup's pass-3 tiles: (y' = 2j, 2j + 1) per entry
 #pragma unroll
         for (int k = 0; k < G::TW; ++k)
@@ -666,29 +674,45 @@ k_tc_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const u
             const uint32_t tB = trow + (w ? G::C_S3 : G::C_S2);
 #pragma unroll
             for (int k = 0; k < G::TW; ++k) {
-                DGFS_WAITE(&bars.full3[w], ph_f3);
-                ph_f3 ^= 1u;
+                // + half, released before the - half is awaited
+                DGFS_WAITE(&bars.full3p[w], ph_f3p);
+                ph_f3p ^= 1u;
                 tc::tc_fence_after();
+                float2 xp[N / 2];   // + translate at y' = 2j, 2j + 1
 #pragma unroll
                 for (int c = 0; c < N / 16; ++c) {   // 16 columns y' = 16c .. 16c + 15 behind one wait
-                    float hp[16], lp[16], hm[16], lm[16];
+                    float hp[16], lp[16];
                     tc::tmem_ld16(tB + 16 * c, hp);
                     tc::tmem_ld16(tB + N + 16 * c, lp);
+                    tc::tmem_wait_ld();
+                    if (c == N / 16 - 1) {
+                        tc::tc_fence_before();
+                        tc::mbar_arrive(&bars.free3p[w]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)   // two y' per packed FMA, the same roundings as fmaf
+                        xp[8 * c + j] = tc::ffma2(make_float2(lp[2 * j], lp[2 * j + 1]), eps2,
+                                                  make_float2(hp[2 * j], hp[2 * j + 1]));
+                }
+                DGFS_WAITE(&bars.full3m[w], ph_f3m);
+                ph_f3m ^= 1u;
+                tc::tc_fence_after();
+#pragma unroll
+                for (int c = 0; c < N / 16; ++c) {   // - half: 16 columns y' = 16c .. 16c + 15 behind one wait
+                    float hm[16], lm[16];
                     tc::tmem_ld16(tB + 2 * N + 16 * c, hm);
                     tc::tmem_ld16(tB + 3 * N + 16 * c, lm);
                     tc::tmem_wait_ld();
                     if (c == N / 16 - 1) {
                         tc::tc_fence_before();
-                        tc::mbar_arrive(&bars.free3[w]);
+                        tc::mbar_arrive(&bars.free3m[w]);
                         if (k == G::TW - 1) tc::mbar_arrive(&bars.free3x[w]);
                     }
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {   // two y' per packed FMA, the same roundings as fmaf
-                        const float2 xp = tc::ffma2(make_float2(lp[2 * j], lp[2 * j + 1]), eps2,
-                                                make_float2(hp[2 * j], hp[2 * j + 1]));
+                    for (int j = 0; j < 8; ++j) {
                         const float2 xm = tc::ffma2(make_float2(lm[2 * j], lm[2 * j + 1]), eps2,
                                                 make_float2(hm[2 * j], hm[2 * j + 1]));
-                        acc[k][8 * c + j] = tc::ffma2(xp, xm, acc[k][8 * c + j]);
+                        acc[k][8 * c + j] = tc::ffma2(xp[8 * c + j], xm, acc[k][8 * c + j]);
                     }
                 }
             }
