@@ -248,7 +248,7 @@ def fft_algorithmic_flops_per_node(N, Nrho, npairs):
 # from the ncu capture of a 512-node launch summarised in profiles/ (None for configurations
 # without a capture of the current kernel version).
 TRAFFIC_PER_NODE = {("f16s", 32, 32, 38): (180026368 + 2091159552) / 512, ("bf16s", 32, 32, 38): (185963520 + 2090830592) / 512,
-                    ("f16x3", 32, 32, 38): (108751616 + 2091174912) / 512,
+                    ("f16x3", 32, 32, 38): (109169920 + 2091046656) / 512,
                     ("fp32", 32, 32, 38): None}
 
 

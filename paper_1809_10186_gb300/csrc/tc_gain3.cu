@@ -32,7 +32,9 @@
 // it turns the sign-w columns of each pass-1 result into the sign-w pass-2 operands and of each
 // pass-2 result into sign-w pass-3 operand rows, software-pipelined (the pass-1 epilogue of front
 // tile i, then the pass-2 epilogue of tile i - 1, whose MMAs ran meanwhile); in the back it forms
-// the products of the pass-3 tiles in slot 2 + w, accumulating P_r in registers. Every wait is bounded; on
+// the products of the pass-3 tiles in slot 2 + w, accumulating P_r in registers (the slot's two sign
+// halves are completed and released separately, so the next tile's + MMAs overlap the read of the
+// - half). Every wait is bounded; on
 // timeout the CTA raises flag bit 0, every role stops at its next wait, the MMAs and copies in
 // flight are drained, TMEM is freed and no P_r is written; both CTAs meet at a final cluster barrier.
 #include <cmath>
@@ -122,7 +124,8 @@ struct Bars3 {
     uint64_t full1, free1;             // pass-1 slot: MMA -> both warpgroups, both warpgroups -> MMA
     uint64_t a2_full[2], a2_free[2];   // pass-2 operands of sign s: warpgroup s -> MMA, MMA completion -> warpgroup s
     uint64_t full2[2], free2[2];       // slots 2, 3 used by pass 2 (both warpgroups drain, one sign each)
-    uint64_t full3[2], free3[2];       // slots 2, 3 used by pass 3 (warpgroup b drains slot 2 + b)
+    uint64_t full3p[2], free3p[2];     // slots 2, 3 used by pass 3 (warpgroup b drains slot 2 + b): + sign
+    uint64_t full3m[2], free3m[2];     // and - sign columns, each half released as soon as it is read
     uint64_t free3x[2];                // last pass-3 drain of a slot in a pair
     uint64_t a3_full;                  // the 128 pass-2 epilogue threads (of both CTAs) that own rows here wrote them
     uint64_t a3_free;                  // both CTAs' pass-3 MMAs read this pair's operands
@@ -256,7 +259,7 @@ __device__ __forceinline__ void mma3_p2_loop(Bars3& bars, uint32_t sb, uint32_t 
 template <int N, bool BF, int b>
 __device__ __forceinline__ void mma3_p3_loop(Bars3& bars, uint32_t sb, uint32_t tmem, int nseq, volatile int* abort) {
     using G = Geo3<N>;
-    uint32_t ph_a3full = 0, ph_f3 = 0;
+    uint32_t ph_a3full = 0, ph_f3p = 0, ph_f3m = 0;
     constexpr uint32_t idw = tc::idesc_f16(BF, true, false, 2 * N, 128);
     constexpr uint32_t idn = tc::idesc_f16(BF, true, false, N, 128);
     constexpr uint64_t dF = tc::sdesc_base(G::FB_LBO, G::FB_SBO);
@@ -272,14 +275,19 @@ __device__ __forceinline__ void mma3_p3_loop(Bars3& bars, uint32_t sb, uint32_t 
         tc::tc_fence_after();
         int n = 0;
         for (int k = b; k < G::TH; k += 2, ++n) {
-            if (n > 0) {
-                DGFS_WAITW(&bars.free3[b], ph_f3);
-                ph_f3 ^= 1u;
-                tc::tc_fence_after();
-            }
             const uint32_t d = tmem + (b ? G::C_S3 : G::C_S2);
 #pragma unroll
-            for (int sg = 0; sg < 2; ++sg) {
+            for (int sg = 0; sg < 2; ++sg) {   // sign +, then sign -; each half reused once it is read
+                if (n > 0) {
+                    if (sg) {
+                        DGFS_WAITW(&bars.free3m[b], ph_f3m);
+                        ph_f3m ^= 1u;
+                    } else {
+                        DGFS_WAITW(&bars.free3p[b], ph_f3p);
+                        ph_f3p ^= 1u;
+                    }
+                    tc::tc_fence_after();
+                }
                 const uint32_t a16 = sb16 + (G::S_A3 + sg * 2 * G::A3_BYTES + k * G::A3_TS) / 16;
 #pragma unroll
                 for (int ks = 0; ks < G::KSTEPS; ++ks) {
@@ -288,10 +296,13 @@ __device__ __forceinline__ void mma3_p3_loop(Bars3& bars, uint32_t sb, uint32_t 
                     tc::mma_ss_warp(d + sg * 2 * N + N, tc::sdesc_at(dA3, a16 + (G::A3_BYTES + ks * 2 * G::A3_LBO) / 16),
                                     bd, idn, 1);
                 }
+                tc::mma_commit_warp(sg ? &bars.full3m[b] : &bars.full3p[b]);
             }
-            tc::mma_commit_warp(&bars.full3[b]);
         }
-        if (n > 0) ph_f3 ^= 1u;   // the pair's last drain of the slot (not waited here)
+        if (n > 0) {   // the pair's last drains of the slot (not waited here)
+            ph_f3p ^= 1u;
+            ph_f3m ^= 1u;
+        }
         tc::mma_commit_multicast_warp(&bars.a3_free, 0x3);
         tc::mma_commit_warp(&bars.fdone[fbuf]);
     }
@@ -339,8 +350,10 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
             for (int i = 0; i < 2; ++i) {
                 tc::mbar_init(&bars.full2[i], 1);
                 tc::mbar_init(&bars.free2[i], 256);
-                tc::mbar_init(&bars.full3[i], 1);
-                tc::mbar_init(&bars.free3[i], 128);
+                tc::mbar_init(&bars.full3p[i], 1);
+                tc::mbar_init(&bars.free3p[i], 128);
+                tc::mbar_init(&bars.full3m[i], 1);
+                tc::mbar_init(&bars.free3m[i], 128);
                 tc::mbar_init(&bars.free3x[i], 128);
                 tc::mbar_init(&bars.filt[i], 1);
                 tc::mbar_init(&bars.fdone[i], 4);
@@ -464,7 +477,7 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
         const uint32_t a3full_owner = tc::map_peer(tc::smem_u32(&bars.a3_full), (uint32_t)owner);
         // the first local thread registers the bytes the peer sends with its arrival
         const bool a3_expect = warp == 0 && lane == (crank ? N / 2 : 0);
-        uint32_t ph_f1 = 0, ph_a2free = 0, ph_a3free = 0, ph_f2 = 0, ph_f3 = 0;   // ph_f2: bit per slot
+        uint32_t ph_f1 = 0, ph_a2free = 0, ph_a3free = 0, ph_f2 = 0, ph_f3p = 0, ph_f3m = 0;   // ph_f2: bit per slot
         int p1uses = 0;
         constexpr int NB = (G::TH + 1) / 2;   // back tiles of one warpgroup
         float2 acc[NB][N / 2];   // P_r of the warpgroup's back tiles: (y' = 2j, 2j + 1) per entry
@@ -579,29 +592,47 @@ k_tc3_gain(const float* __restrict__ f, const int64_t* __restrict__ offs, const 
             for (int n = 0; n < NB; ++n) {
                 const int k = w + 2 * n;   // warp-uniform
                 if (k >= G::TH) break;
-                DGFS_WAITE(&bars.full3[w], ph_f3);
-                ph_f3 ^= 1u;
+                // + half (every column behind one wait), released before the - half is awaited
+                DGFS_WAITE(&bars.full3p[w], ph_f3p);
+                ph_f3p ^= 1u;
+                tc::tc_fence_after();
+                float2 xp[N / 2];   // + translate at y' = 2j, 2j + 1
+                {
+                    float hp[N / 16][16], lp[N / 16][16];
+#pragma unroll
+                    for (int c = 0; c < N / 16; ++c) {
+                        tc::tmem_ld16(tB + 16 * c, hp[c]);
+                        tc::tmem_ld16(tB + N + 16 * c, lp[c]);
+                    }
+                    tc::tmem_wait_ld();
+                    tc::tc_fence_before();
+                    tc::mbar_arrive(&bars.free3p[w]);
+#pragma unroll
+                    for (int c = 0; c < N / 16; ++c)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)   // two y' per packed FMA, the same roundings as fmaf
+                            xp[8 * c + j] = tc::ffma2(make_float2(lp[c][2 * j], lp[c][2 * j + 1]), eps2,
+                                                      make_float2(hp[c][2 * j], hp[c][2 * j + 1]));
+                }
+                DGFS_WAITE(&bars.full3m[w], ph_f3m);
+                ph_f3m ^= 1u;
                 tc::tc_fence_after();
 #pragma unroll
-                for (int c = 0; c < N / 16; ++c) {   // 16 columns y' behind one wait
-                    float hp[16], lp[16], hm[16], lm[16];
-                    tc::tmem_ld16(tB + 16 * c, hp);
-                    tc::tmem_ld16(tB + N + 16 * c, lp);
+                for (int c = 0; c < N / 16; ++c) {   // - half: 16 columns y' behind one wait
+                    float hm[16], lm[16];
                     tc::tmem_ld16(tB + 2 * N + 16 * c, hm);
                     tc::tmem_ld16(tB + 3 * N + 16 * c, lm);
                     tc::tmem_wait_ld();
                     if (c == N / 16 - 1) {
                         tc::tc_fence_before();
-                        tc::mbar_arrive(&bars.free3[w]);
+                        tc::mbar_arrive(&bars.free3m[w]);
                         if (k + 2 >= G::TH) tc::mbar_arrive(&bars.free3x[w]);
                     }
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {   // two y' per packed FMA, the same roundings as fmaf
-                        const float2 xp = tc::ffma2(make_float2(lp[2 * j], lp[2 * j + 1]), eps2,
-                                                    make_float2(hp[2 * j], hp[2 * j + 1]));
+                    for (int j = 0; j < 8; ++j) {
                         const float2 xm = tc::ffma2(make_float2(lm[2 * j], lm[2 * j + 1]), eps2,
                                                     make_float2(hm[2 * j], hm[2 * j + 1]));
-                        acc[n][8 * c + j] = tc::ffma2(xp, xm, acc[n][8 * c + j]);
+                        acc[n][8 * c + j] = tc::ffma2(xp[8 * c + j], xm, acc[n][8 * c + j]);
                     }
                 }
             }
