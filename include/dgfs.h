@@ -230,8 +230,9 @@ dgfs_status dgfs_slab_rhs(dgfs_slab_t slab, const void* F, void* dFdt, void* str
    profiling and a stream that is not being captured, the first step runs eagerly and one step is then
    captured as a CUDA graph (on a slab-owned stream) and replayed for the rest; the graph is kept for
    later calls with the same F, dt, order and plan tuning, and dropped by dgfs_slab_set_walls.
-   Otherwise every step is launched eagerly (on a capturing stream, into the caller's graph). Both
-   give the same bits. The graph is keyed by F's address: a new field buffer at the same address
+   Otherwise every step is launched eagerly (on a capturing stream, into the caller's graph), and so
+   are the remaining steps when capturing or instantiating the graph fails (that error is cleared).
+   Both give the same bits. The graph is keyed by F's address: a new field buffer at the same address
    (of the slab's fixed size) reuses it. */
 dgfs_status dgfs_slab_ssprk(dgfs_slab_t slab, int order, void* F, double dt, int nsteps, void* stream);
 dgfs_status dgfs_slab_destroy(dgfs_slab_t slab);

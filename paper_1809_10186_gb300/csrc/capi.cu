@@ -1504,21 +1504,25 @@ dgfs_status slab_ssprk(dgfs_slab_s* sl, int order, T* F, double dt, int nsteps, 
         dgfs_status st = slab_step<T>(sl, order, F, dt, s);
         if (st != DGFS_OK) return st;
         done = 1;
-        if (!sl->cap) DGFS_CUDA(cudaStreamCreateWithFlags(&sl->cap, cudaStreamNonBlocking), "stream create");
-        cudaGraph_t g = nullptr;
-        DGFS_CUDA(cudaStreamBeginCapture(sl->cap, cudaStreamCaptureModeThreadLocal), "graph capture");
-        st = slab_step<T>(sl, order, F, dt, sl->cap);
-        const cudaError_t ec = cudaStreamEndCapture(sl->cap, &g);
-        if (st != DGFS_OK) {
+        // the graph only saves launches: if creating the stream, capturing or instantiating fails,
+        // that error is cleared and the remaining steps run eagerly
+        bool ok = sl->cap || cudaStreamCreateWithFlags(&sl->cap, cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) ok = cudaStreamBeginCapture(sl->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            cudaGraph_t g = nullptr;
+            const dgfs_status sc = slab_step<T>(sl, order, F, dt, sl->cap);
+            const cudaError_t ec = cudaStreamEndCapture(sl->cap, &g);
+            ok = sc == DGFS_OK && ec == cudaSuccess && g && cudaGraphInstantiate(&sl->gexec, g, 0) == cudaSuccess;
             if (g) cudaGraphDestroy(g);
-            return st;
         }
-        if (ec != cudaSuccess) return cuda_fail(ec, "graph capture of a slab step");
-        const cudaError_t ei = cudaGraphInstantiate(&sl->gexec, g, 0);
-        cudaGraphDestroy(g);
-        if (ei != cudaSuccess) {
+        if (!ok) {
             sl->gexec = nullptr;
-            return cuda_fail(ei, "graph instantiation of a slab step");
+            (void)cudaGetLastError();
+            for (int it = done; it < nsteps; ++it) {
+                st = slab_step<T>(sl, order, F, dt, s);
+                if (st != DGFS_OK) return st;
+            }
+            return DGFS_OK;
         }
         sl->gF = F;
         sl->gdt = dt;
