@@ -221,3 +221,59 @@ def test_host_pipeline_schedule_of_the_headline_batch_and_errors():
         binding.host_pipeline_schedule(-1, 16)
     with pytest.raises(binding.DGFSError):
         binding.host_pipeline_schedule(8, 0)
+
+
+def _handle_calls():
+    """Every declared call that takes a plan, DG operator, slab or ragged schedule, with a NULL
+    handle (or an empty plan list) and otherwise well-formed arguments."""
+    n, i, d, q = ctypes.c_void_p(None), ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    return {
+        "dgfs_plan_info": (n, n),
+        "dgfs_collide": (n, n, n, q(1), n),
+        "dgfs_collide2": (n, n, n, n, q(1), n),
+        "dgfs_collide_jvp": (n, n, n, n, q(1), n),
+        "dgfs_collide_vjp": (n, n, n, n, q(1), n),
+        "dgfs_collide_dgamma": (n, n, n, q(1), n),
+        "dgfs_collide_host": (n, n, n, q(1), n),
+        "dgfs_collide_noalloc": (n, n, n, q(1), n),
+        "dgfs_collide_ragged": (n, i(0), n, n, n, n, q(1), n, n, n),
+        "dgfs_ragged_create": (n, i(0), n, n, n, n, q(1), n),
+        "dgfs_ragged_collide": (n, n, n, n),
+        "dgfs_slab_create": (n, i(3), i(2), n, d(1.0), n, n, d(0.0), n),
+        "dgfs_slab_set_walls": (n, n, n),
+        "dgfs_slab_rhs": (n, n, n, n),
+        "dgfs_slab_ssprk": (n, i(2), n, d(0.01), i(2), n),
+        "dgfs_stream_status": (n, n),
+        "dgfs_ssprk": (n, i(2), n, q(1), d(0.01), d(1.0), i(1), n),
+        "dgfs_moments": (n, n, n, q(1), n),
+        "dgfs_dg_create": (n, i(3), n, d(0.0), q(1), n),
+        "dgfs_dg_info": (n, n, n),
+        "dgfs_dg_collide": (n, n, n, q(1), n),
+        "dgfs_debug_inject": (n, i(0)),
+        "dgfs_profile_begin": (n,),
+        "dgfs_profile_end": (n, n),
+        "dgfs_plan_autotune": (n, n, q(1), n, n),
+        "dgfs_plan_set_tuning": (n, i(0), q(0)),
+        "dgfs_plan_fingerprint": (n, n),
+    }
+
+
+def test_every_handle_call_rejects_a_null_handle_before_cuda(lib):
+    """Argument and state errors return before any CUDA call: on a machine without a GPU a call
+    that reached CUDA would answer DGFS_ERR_CUDA (4); these answer DGFS_ERR_INVALID_ARG (1) or
+    DGFS_ERR_STATE (7) with a message. The list is checked against the header, so a new call that
+    takes a handle must be added here."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "dgfs.h")).read(), flags=re.S)
+    takes_handle = {m.group(1) for m in re.finditer(
+        r"\b(dgfs_\w+)\s*\(\s*(?:const\s+)?dgfs_(?:plan|dg|slab|ragged)_t\b", src)}
+    destroys = {f for f in takes_handle if f.endswith("_destroy")}
+    calls = _handle_calls()
+    assert takes_handle - destroys == set(calls)
+    raw = ctypes.CDLL(lib._name)   # a separate handle: no argument conversions of the binding
+    raw.dgfs_last_error_message.restype = ctypes.c_char_p
+    for name, args in calls.items():
+        st = getattr(raw, name)(*args)
+        assert st in (1, 7), (name, st)
+        assert raw.dgfs_last_error_message(), name
+    for name in destroys:   # destroying NULL is a no-op
+        assert getattr(raw, name)(ctypes.c_void_p(None)) == 0, name
