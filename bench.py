@@ -814,7 +814,7 @@ def main():
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
         roof = {"bound": "tensor", "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"
                 if peaks.get("bf16_tflops_sustained") else "fallback 1.7 PFLOP/s sustained"}
-    # the method's own work (FFT-counted translates) over the same kernel time
+    # the method's own work (the translates counted as radix-2 FFTs, Appendix) over the same kernel time
     alg_node = fft_algorithmic_flops_per_node(N, Nr, npairs)
     alg_rate = alg_node * nodes_per_launch / (per_launch_ms / 1e3) / 1e12
     alg_peak = measured["fp32_fma_tflops"] if prec in ("fp32", "fp64") else measured["fp16_dense_tflops"]
