@@ -48,7 +48,7 @@ typedef struct dgfs_plan_s* dgfs_plan_t;
 typedef enum {
     DGFS_OK = 0,
     DGFS_ERR_INVALID_ARG = 1,  /* bad size, NULL or misaligned pointer, bad descriptor    */
-    DGFS_ERR_UNSUPPORTED = 2,  /* valid request that this build does not implement        */
+    DGFS_ERR_UNSUPPORTED = 2,  /* valid request that the library does not implement       */
     DGFS_ERR_OOM = 3,          /* device or host allocation failed (plan creation only)    */
     DGFS_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed              */
     DGFS_ERR_TIMEOUT = 5,      /* a device-side bounded wait gave up (see stream_status)   */
